@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Throughput of the Approx-FIRAL Relax mirror-descent iteration (Algorithm 2) on GB300.
+
+One step = one MD iteration over the whole pool: probes, preconditioner blocks and their
+FP64 factorisation, two block-Jacobi PCG solves of s columns with a fixed number of CG
+iterations, the H_p apply and f^, the per-point gradient and the MD update.  The default
+workload is the ImageNet-shaped pool (n = 1,000,000, d = 64, c = 1000, s = 16, X bf16,
+h f32, 10 CG iterations per solve) in the mixed bf16 tensor-core precision.
+
+Printed: one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle instead
+(on host cores, on a bounded subsample scaled to the full pool).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Relax MD iters/s at n=1M,c=1000 (mixed vs FP32 @≤1e-3 rel err); % TC peak"
+UNIT = "MD iters/s"
+FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="imagenet_like")
+    ap.add_argument("--n", type=int, default=None, help="pool size override (smaller runs)")
+    ap.add_argument("--cg-iters", type=int, default=10)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32", "fp64"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def workload(args):
+    from paper_2409_07392_gb300.synth import CONFIGS
+    cfg = dict(CONFIGS[args.workload])
+    if args.n is not None:
+        cfg["n"] = args.n
+    return cfg
+
+
+def describe(cfg, args):
+    return (f"{args.workload}: n={cfg['n']} d={cfg['d']} c={cfg['c']} s={cfg['s']} "
+            f"cg_iters/solve={args.cg_iters} X={cfg['x_dtype']} h={cfg['h_dtype']}")
+
+
+# ------------------------------------------------------------------------------ distributed
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------ roofline
+def algorithmic_flops(kind, cfg, n_all, s):
+    """Algorithmic flops of one timed group of a kernel class."""
+    n, d, c = cfg["n"], cfg["d"], cfg["c"]
+    if kind in ("apply_alpha", "apply_dterm"):
+        return 2.0 * n_all * c * d * s
+    if kind == "syrk_blocks":
+        return 2 * 2.0 * n_all * c * d * d          # S_k and B_k(Sigma_z) blocks together
+    if kind == "quad_forms":
+        return 4.0 * n * c * d * s
+    return None
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, \
+            "fallback"
+
+
+# ------------------------------------------------------------------------------ oracle timing
+def oracle_md_iteration_rate(cfg, cg_iters, seconds, seed=0):
+    """Time one oracle MD iteration on a subsample sized for ~`seconds` of CPU work and scale
+    to the full pool (the per-point work is linear in n).  Returns (iters/s, sample, cores)."""
+    from oracle import approx
+    from paper_2409_07392_gb300.synth import make_problem
+    n_full, d, c, s = cfg["n"], cfg["d"], cfg["c"], cfg["s"]
+    # calibrate on a small pool: one Sigma apply
+    n0 = max(200, min(2000, n_full))
+    p0 = make_problem(n0, d, c, seed=seed, x_dtype=cfg["x_dtype"], h_dtype=cfg["h_dtype"])
+    ops = approx.Operators(p0)
+    V = np.ones((d * c, s))
+    t0 = time.perf_counter()
+    ops.sigma_apply(np.full(n0, 1.0 / n0), V)
+    t_apply = time.perf_counter() - t0
+    per_iter_est = t_apply * (2 * cg_iters + 4) * 1.3
+    n1 = int(max(n0, min(n_full, n0 * seconds / max(per_iter_est, 1e-3))))
+    p1 = make_problem(n1, d, c, seed=seed, x_dtype=cfg["x_dtype"], h_dtype=cfg["h_dtype"])
+    t0 = time.perf_counter()
+    approx.relax(p1, float(cfg["b"]) * n1 / n_full if n1 < n_full else float(cfg["b"]), s=s,
+                 T=1, seed=1, fixed_iters=cg_iters)
+    dt = time.perf_counter() - t0
+    per_full = dt * n_full / n1
+    return 1.0 / per_full, f"one MD iteration ({cg_iters} CG iterations per solve) on n={n1} " \
+        f"of {n_full} points, scaled by n", os.cpu_count()
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    cfg = workload(args)
+    rates = []
+    sample = cores = None
+    for i in range(args.warmup + args.steps):
+        r, sample, cores = oracle_md_iteration_rate(cfg, args.cg_iters,
+                                                    seconds=max(2.0, 120.0 / (args.warmup +
+                                                                              args.steps)))
+        if i >= args.warmup:
+            rates.append(r)
+    v = float(np.mean(rates))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": describe(cfg, args)},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------ our arm
+def run_ours(args):
+    import torch
+
+    from paper_2409_07392_gb300 import _lib, api, build
+    from paper_2409_07392_gb300.synth import make_problem
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    build.build()
+    lib = _lib.load()
+    cfg = workload(args)
+    n, d, c, s, b = cfg["n"], cfg["d"], cfg["c"], cfg["s"], float(cfg["b"])
+    p = make_problem(n, d, c, seed=rank, x_dtype=cfg["x_dtype"], h_dtype=cfg["h_dtype"],
+                     anisotropic=cfg.get("anisotropic", False), zipf=cfg.get("zipf"))
+    xdt = torch.bfloat16 if p.x_bf16 else torch.float32
+
+    def host(a, dt=None):
+        t = torch.from_numpy(np.ascontiguousarray(a))
+        return (t.to(dt) if dt is not None else t).pin_memory()
+
+    Xh, hh, Xoh, hoh = host(p.X, xdt), host(p.h), host(p.Xo, xdt), host(p.ho)
+    X, h, Xo, ho = (t.cuda(non_blocking=True) for t in (Xh, hh, Xoh, hoh))
+    H = api.Handle()
+    prob = api.Problem(H, X, h, Xo, ho, p.lam, precision=args.precision)
+    z = torch.full((n,), b / n, dtype=prob.vdt, device="cuda")
+    opts = prob.relax_opts(s=s, T=args.warmup + args.steps, fixed_iters=args.cg_iters, seed=1)
+    for t in range(args.warmup):
+        prob.relax_step(opts, t, b, z, stats=False)
+    torch.cuda.synchronize()
+
+    # ---------------- timed region (device events on the library's stream = torch's current)
+    lib.firal_profile(1)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    launches0 = lib.firal_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for t in range(args.steps):
+        prob.relax_step(opts, args.warmup + t, b, z, stats=False)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = lib.firal_launch_count() - launches0
+    clk = clocks.stop()
+    ms_ev = e0.elapsed_time(e1)
+    ms_max = max_over_ranks(ms_ev, world)
+    nk = _lib.FiralStepStats  # noqa: F841
+    ncls = 12
+    ms_k = (ctypes_arr := __import__("ctypes").c_double * ncls)()
+    calls_k = (__import__("ctypes").c_int64 * ncls)()
+    lib.firal_profile_read(ms_k, calls_k, ncls)
+    lib.firal_profile(0)
+    kernels = {lib.firal_profile_name(i).decode(): {"ms_per_step": ms_k[i] / args.steps,
+                                                   "groups_per_step": calls_k[i] / args.steps}
+               for i in range(ncls) if calls_k[i] > 0}
+    value = world * args.steps / (ms_max / 1000.0)
+
+    # ---------------- roofline of the dominant kernel class
+    pk, pk_src = peaks()
+    top = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
+    n_all = n + p.Xo.shape[0]
+    fl = algorithmic_flops(top, cfg, n_all, s)
+    roof = None
+    if fl is not None:
+        per_launch_ms = kernels[top]["ms_per_step"] / kernels[top]["groups_per_step"]
+        achieved = fl / (per_launch_ms / 1000.0) / 1e12
+        tensor = args.precision == "mixed" and top in ("apply_alpha", "apply_dterm")
+        peak = pk["bf16_tflops_sustained"] if tensor else FP32_ALU_PEAK_TFLOPS
+        roof = {"kernel": top, "bound": "tensor" if tensor else "alu", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": (f"{pk_src} bf16 sustained" if tensor else
+                                "derived FP32 FMA peak: 152 SMs x 128 lanes x 2 x 2.07 GHz")}
+    # the Hessian apply as a whole (alpha + D + combine), the operation the metric counts
+    apply_ms = sum(kernels.get(k, {}).get("ms_per_step", 0.0)
+                   for k in ("apply_alpha", "apply_dterm", "apply_combine"))
+    applies_per_step = 2 * args.cg_iters + 1
+    apply_tflops = (4.0 * n_all * c * d * s * applies_per_step) / (apply_ms / 1000.0) / 1e12 \
+        if apply_ms > 0 else None
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"mixed": "bf16", "fp32": "f32", "fp64": "f64"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": describe(cfg, args), "precision": args.precision,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (h alone is %.1f GB)" % (p.h.nbytes / 1e9)},
+            "roofline": roof, "gpu_launches": int(launches), "clocks": clk,
+            "kernels": kernels,
+            "hessian_apply": {"tflops_algorithmic": apply_tflops,
+                              "frac_of_bf16_sustained": (apply_tflops / pk["bf16_tflops_sustained"]
+                                                         if apply_tflops else None)}}
+
+    # ---------------- end to end through the public API with host (pinned) buffers
+    if not args.no_e2e:
+        zh = torch.full((n,), b / n, dtype=prob.vdt).pin_memory()
+        k_e2e = max(1, min(args.steps, 3))
+        barrier(world)
+        t0 = time.perf_counter()
+        for t in range(k_e2e):
+            zout, _ = api.relax(Xh, hh, Xoh, hoh, p.lam, b, s=s, T=1, fixed_iters=args.cg_iters,
+                                seed=1 + t, precision=args.precision, z0=zh, handle=H)
+            zh.copy_(zout)
+        dt = max_over_ranks(time.perf_counter() - t0, world)
+        bi = sum(t.numel() * t.element_size() for t in (Xh, hh, Xoh, hoh, zh))
+        line["e2e"] = {"value": world * k_e2e / dt, "unit": UNIT, "h2d_bytes_per_step": bi,
+                       "d2h_bytes_per_step": zh.numel() * zh.element_size(), "steps": k_e2e,
+                       "note": "each step is one api.relax(T=1) call on pinned host tensors: "
+                               "H2D copies, problem preparation, one MD iteration, D2H of z"}
+
+    if rank == 0:
+        # ---------------- plain FP32 form on the same GPU and its agreement with mixed
+        if not args.no_fp32 and args.precision == "mixed":
+            del prob
+            torch.cuda.empty_cache()
+            p32 = api.Problem(H, X, h, Xo, ho, p.lam, precision="fp32")
+            pmx = api.Problem(H, X, h, Xo, ho, p.lam, precision="mixed")
+            z32 = torch.full((n,), b / n, dtype=torch.float32, device="cuda")
+            zmx = z32.clone()
+            o = p32.relax_opts(s=s, T=4, fixed_iters=args.cg_iters, seed=1)
+            st32 = p32.relax_step(o, 0, b, z32)
+            stmx = pmx.relax_step(o, 0, b, zmx)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            p32.relax_step(o, 1, b, z32, stats=False)
+            torch.cuda.synchronize()
+            dt32 = time.perf_counter() - t0
+            line["fp32"] = {"value": 1.0 / dt32, "unit": UNIT, "steps": 1, "warmup": 1,
+                            "fhat_rel_diff_mixed_vs_fp32":
+                                abs(stmx["fhat"] - st32["fhat"]) / abs(st32["fhat"]),
+                            "z_rel_diff_mixed_vs_fp32":
+                                float((zmx - z32).norm() / z32.norm()),
+                            "speedup_mixed_over_fp32": value / world * dt32}
+            del p32, pmx
+        # ---------------- CPU oracle baseline
+        if not args.no_cpu:
+            v, sample, cores = oracle_md_iteration_rate(cfg, args.cg_iters, args.cpu_seconds)
+            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                    "sample": sample}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

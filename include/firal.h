@@ -1,0 +1,296 @@
+/*
+ * firal.h -- C-ABI of the GB300 (sm_103a) Approx-FIRAL hot path.
+ *
+ * Approx-FIRAL (Chen, Wen, Biros, "A Scalable Algorithm for Active Learning",
+ * SC24) selects b points of an unlabelled pool for labelling under a
+ * multinomial logistic-regression model.  This library implements its
+ * data-parallel hot path on one GPU:
+ *
+ *   Relax (Algorithm 2): entropic mirror descent on
+ *        f(z) = Tr(Sigma_z^{-1} H_p),   Sigma_z = H_o + sum_i z_i H_i     (eqs. 4-7)
+ *     with Hutchinson probes (eq. 11), the matrix-free Hessian apply of
+ *     Lemma 1, and block-Jacobi preconditioned CG (Definition 1, eq. 13).
+ *   Round (Algorithm 3): greedy block-diagonal FTRL selection with the
+ *     Proposition 1 score (eq. 14), Lemma 2 updates and the eq. 10 root.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Pointers named "device" must point to device memory of the handle's
+ *    device; "host" pointers to host memory.  The caller owns every buffer it
+ *    passes; the library never frees caller memory.  The library allocates its
+ *    own workspace (cudaMalloc) inside a handle or problem and frees it in the
+ *    matching destroy call.
+ *  - All device work is enqueued on the handle's stream.  Calls return after
+ *    enqueueing unless they fill a host output (stats, histories, scalars), in
+ *    which case they synchronise the stream first.
+ *  - Matrices are row-major.  A vector of length dt = d*c is vec(V) of a d x c
+ *    matrix (columns stacked, as in the paper's notation table): element
+ *    k*d + e is V[e][k].  A block of s such vectors is stored probe-major:
+ *    vector j occupies [j*dt, (j+1)*dt).
+ *  - "vec type" is double for FIRAL_FP64 and float for FIRAL_FP32 and
+ *    FIRAL_MIXED_BF16; z, probe blocks, CG iterates and gradients use it.
+ *  - The status code is the only error channel; no exception crosses the ABI.
+ *    After an error, firal_last_error() gives a one-line detail.  A CUDA
+ *    error maps to FIRAL_ERR_CUDA; a non-positive Cholesky pivot to
+ *    FIRAL_ERR_NOT_SPD (the outputs then hold the best values reached).
+ *  - H_o = sum_{labelled} H_i + lambda I (full c-class softmax, d~ = dc);
+ *    H_p = (1/n) sum_{pool} H_i (the pool average).
+ */
+#ifndef FIRAL_H
+#define FIRAL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FIRAL_OK = 0,
+  FIRAL_ERR_ARG = -1,              /* invalid argument (null pointer, bad size or dtype)      */
+  FIRAL_ERR_CUDA = -2,             /* a CUDA runtime or driver call failed                    */
+  FIRAL_ERR_NOT_SPD = -3,          /* a block Cholesky met a non-positive pivot              */
+  FIRAL_ERR_CG_NOT_CONVERGED = -4, /* PCG hit its iteration limit above tolerance           */
+  FIRAL_ERR_NONFINITE = -5,        /* NaN or Inf in the objective or gradient               */
+  FIRAL_ERR_TIMEOUT = -6,          /* a bounded device-side wait gave up                      */
+  FIRAL_ERR_NOMEM = -7,            /* workspace allocation failed                             */
+  FIRAL_ERR_UNSUPPORTED = -8       /* shape or precision outside what this build supports   */
+} firal_status;
+
+typedef enum {
+  FIRAL_FP64 = 0,       /* every step in double (SIMT kernels)                                  */
+  FIRAL_FP32 = 1,       /* contractions and vectors in float (SIMT); FP64 dots and factors       */
+  FIRAL_MIXED_BF16 = 2  /* X, h contractions on bf16 tensor cores (tcgen05), FP32 accumulate;    */
+                        /* float vectors, FP64 dots, FP64 block factorisations                    */
+} firal_precision;
+
+typedef enum { FIRAL_DT_F64 = 0, FIRAL_DT_F32 = 1, FIRAL_DT_BF16 = 2 } firal_dtype;
+
+/* The unlabelled pool X_u: embeddings x_i (n x d) and class probabilities h_i (n x c),
+ * device pointers, row-major, rows contiguous.  h rows are used as given (not renormalised). */
+typedef struct {
+  const void* X;     /* device, n*d elements of x_dtype                      */
+  const void* h;     /* device, n*c elements of h_dtype (F32 or F64)         */
+  int64_t n;         /* pool size, >= 1                                      */
+  int32_t d;         /* feature dimension, 1..128                            */
+  int32_t c;         /* classes, 2..4096                                     */
+  int32_t x_dtype;   /* firal_dtype                                          */
+  int32_t h_dtype;   /* firal_dtype (F32 or F64)                             */
+} firal_pool;
+
+/* The labelled set X_o that defines H_o (eq. 3) plus the ridge lambda (same dtypes as the pool). */
+typedef struct {
+  const void* Xo;    /* device, m*d, may be NULL when m == 0 */
+  const void* ho;    /* device, m*c                          */
+  int64_t m;         /* labelled points, >= 0                */
+  double lambda;     /* ridge, > 0 unless the labelled Hessians alone are SPD */
+} firal_hess0;
+
+/* Preconditioned CG controls (Algorithm 2 lines 5-8).  x0 = 0; column j stops when its
+ * recursive residual satisfies ||r_j|| <= tol ||b_j|| (unpreconditioned 2-norm) or when
+ * p^T Sigma p <= 0.  fixed_iters > 0 runs exactly that many iterations on every column and
+ * ignores tol (no host synchronisation inside the solve). */
+typedef struct {
+  double tol;           /* default 0.1 (Section 5 of the paper)  */
+  int32_t maxit;        /* default 100                           */
+  int32_t fixed_iters;  /* 0 = tolerance mode                    */
+} firal_cg_opts;
+
+/* Relax controls.  Defaults: s = 10, T = 20, beta0 = 1, seed = 1, cg = {0.1, 100, 0}. */
+typedef struct {
+  int32_t s;            /* Hutchinson probes per MD iteration (eq. 11)                        */
+  int32_t T;            /* mirror-descent iterations                                          */
+  firal_cg_opts cg;     /* both CG solves of an iteration                                     */
+  double beta0;         /* step size beta_t = beta0 / ||g_t||_inf                              */
+  uint64_t seed;        /* probe seed: v[t][j][q] from SplitMix64 (see firal_probes)          */
+  int32_t precision;    /* firal_precision                                                    */
+  int32_t estimator;    /* 0 = paper eq. 11 (W = S^-1 H_p S^-1 V); 1 = derivative of f^ (U,Y) */
+  double md_tol;        /* > 0: stop when |f^_t - f^_{t-1}| <= md_tol |f^_{t-1}| (Section 5)  */
+} firal_relax_opts;
+
+/* Per-iteration record of a relax step (host). */
+typedef struct {
+  double fhat;          /* (1/s) sum_j <v_j, H_p Sigma_z^{-1} v_j> before the z update        */
+  double gmax;          /* ||g||_inf                                                           */
+  double zmax;          /* max_i z_i after the update (the box z <= 1 is not enforced)        */
+  int32_t cg_iters[2];  /* iterations of the two solves (max over columns)                    */
+  double cg_relres[2];  /* largest final relative residual over columns                        */
+} firal_step_stats;
+
+typedef struct {
+  int32_t iters_done;   /* MD iterations run                                                   */
+  double fhat_last;
+  int32_t cg_iters_total;
+} firal_relax_stats;
+
+/* Round controls.  eta <= 0 selects eta = 8 sqrt(d c) (Theorem 1 with epsilon = 1). */
+typedef struct {
+  double eta;
+  int32_t exclude_selected;  /* 1 (default): never select a point twice                       */
+  int32_t precision;         /* firal_precision of the score contraction                      */
+} firal_round_opts;
+
+typedef struct {
+  double nu_last;       /* nu_{b+1} of eq. 10                                                  */
+  double score_last;    /* eq. 14 score of the last pick                                       */
+} firal_round_stats;
+
+typedef struct firal_handle firal_handle;
+typedef struct firal_problem firal_problem;
+
+/* ---------------------------------------------------------------- library and handles */
+
+/* Human-readable name of a status code (static string). */
+const char* firal_status_string(int32_t status);
+
+/* Create a handle bound to the current CUDA device and to `stream` (a cudaStream_t passed
+ * as void*; NULL = the legacy default stream).  *out receives the handle. */
+int32_t firal_create(firal_handle** out, void* stream);
+
+/* Destroy a handle (NULL is ignored).  Problems created from it must be destroyed first. */
+int32_t firal_destroy(firal_handle* handle);
+
+/* Rebind the handle (and its problems) to another stream of the same device. */
+int32_t firal_set_stream(firal_handle* handle, void* stream);
+
+/* Copy the last error detail of `handle` (NUL-terminated, truncated to len). */
+int32_t firal_last_error(firal_handle* handle, char* buf, size_t len);
+
+/* Bit-width and precision flags this build was compiled with: bit 0 = SIMT paths,
+ * bit 1 = tcgen05 (sm_103a) tensor-core path. */
+int32_t firal_build_info(void);
+
+/* ---------------------------------------------------------------- instrumentation */
+
+/* Number of kernels this library has launched in the process so far (all handles). */
+int64_t firal_launch_count(void);
+
+/* Enable (1) or disable (0) the kernel-class timers and reset their totals.  When enabled,
+ * each group of launches records a CUDA event pair on the stream it is launched on; the
+ * timers add that overhead and nothing else.  Not thread-safe across concurrent calls that
+ * use different streams of different devices. */
+int32_t firal_profile(int32_t enable);
+
+/* Synchronise on the recorded events and copy, for each kernel class 0..count-1, the total
+ * elapsed milliseconds (ms_out, host, may be NULL) and the number of timed groups
+ * (calls_out, host, may be NULL).  Returns the number of kernel classes. */
+int32_t firal_profile_read(double* ms_out, int64_t* calls_out, int32_t count);
+
+/* Name of kernel class `id` (static string). */
+const char* firal_profile_name(int32_t id);
+
+/* ---------------------------------------------------------------- prepared problems */
+
+/* Prepare one problem for repeated calls: copies the pool and labelled set into the
+ * library's device layout for `precision` (labelled rows first, then pool rows; bf16 and
+ * transposed copies for FIRAL_MIXED_BF16) and allocates the iteration workspace.  The
+ * caller's X, h, Xo, ho may be freed after this call returns. */
+int32_t firal_problem_create(firal_handle* handle, const firal_pool* pool,
+                             const firal_hess0* hess0, int32_t precision,
+                             firal_problem** out);
+int32_t firal_problem_destroy(firal_problem* problem);
+
+/* ---------------------------------------------------------------- Relax (Algorithm 2) */
+
+/* Full Relax solve.  z0: device, n values of the vec type on the budget simplex
+ * (z >= 0, sum z = budget) or NULL for z0 = budget/n.  z_out: device, n values; it holds
+ * z_diamond on return (the iterates stay on the budget simplex, so no final rescale).
+ * fhat_hist: host, opts->T doubles or NULL.  stats: host or NULL. */
+int32_t firal_relax(firal_handle* handle, const firal_pool* pool, const firal_hess0* hess0,
+                    double budget, const void* z0, const firal_relax_opts* opts, void* z_out,
+                    double* fhat_hist, firal_relax_stats* stats);
+
+/* One mirror-descent iteration t (0-based) of Algorithm 2 on a prepared problem:
+ * probes V_t (line 4), preconditioner B(Sigma_z)^{-1} (line 5), U = Sigma_z^{-1} V (line 6),
+ * H_p U and f^ (line 7), the second solve (line 8), the gradient (line 9) and the MD update
+ * (lines 10-11).  z: device, n values, updated in place.  stats: host or NULL (NULL keeps
+ * the call free of host synchronisation when opts->cg.fixed_iters > 0). */
+int32_t firal_relax_step(firal_problem* problem, const firal_relax_opts* opts, int32_t t,
+                         double budget, void* z, firal_step_stats* stats);
+
+/* ---------------------------------------------------------------- Round (Algorithm 3) */
+
+/* Diagonal Round step: selects `budget` pool indices (0-based) into selected_out (device,
+ * int32, budget entries), in selection order.  z_relaxed: device, n values of the vec type
+ * (z_diamond).  Ties in eq. 14 go to the lowest index. */
+int32_t firal_round(firal_handle* handle, const firal_pool* pool, const firal_hess0* hess0,
+                    const void* z_relaxed, int32_t budget, const firal_round_opts* opts,
+                    int32_t* selected_out, firal_round_stats* stats);
+
+/* Same on a prepared problem (its precision governs the score contraction). */
+int32_t firal_round_problem(firal_problem* problem, const void* z_relaxed, int32_t budget,
+                            const firal_round_opts* opts, int32_t* selected_out,
+                            firal_round_stats* stats);
+
+/* ---------------------------------------------------------------- building blocks */
+
+/* Rademacher probe block of MD iteration t (Algorithm 2 line 4): V_out (device, s*dt of
+ * the vec type, probe-major) with v[t][j][q] = +1 if the top bit of
+ * splitmix64(seed ^ splitmix64((t*s + j)*dt + q)) is 0, else -1, where splitmix64(x) is
+ * the SplitMix64 output for state x (Steele, Lea, Flood 2014). */
+int32_t firal_probes(firal_problem* problem, uint64_t seed, int32_t t, int32_t s,
+                     void* V_out);
+
+/* Hessian apply by Lemma 1 (Section 3.1) on s vectors: op 0 gives Sigma_z V
+ * = H_o V + sum_pool z_i H_i V (z: device, n values); op 1 gives H_p V (z ignored).
+ * V, out: device, s*dt of the vec type, probe-major; out must not alias V. */
+int32_t firal_hessian_apply(firal_problem* problem, int32_t op, const void* z, const void* V,
+                            int32_t s, void* out);
+
+/* Preconditioner blocks B_k(Sigma_z) = B_k(H_o) + sum_pool z_i h_ik (1 - h_ik) x_i x_i^T
+ * (Definition 1, eq. 13), k = 0..c-1: blocks_out (device, c*d*d doubles, block k row-major).
+ * z == NULL gives B_k(H_o). */
+int32_t firal_precond_blocks(firal_problem* problem, const void* z, double* blocks_out);
+
+/* Block-Jacobi preconditioned CG on Sigma_z X = B (Algorithm 2 lines 5-8) for s columns.
+ * B, X_out: device, s*dt of the vec type.  iters_out (host, s int32) and relres_out (host,
+ * s doubles) may be NULL; when either is given the call synchronises.  Returns
+ * FIRAL_ERR_CG_NOT_CONVERGED (with X_out filled) if a column stayed above tol in tolerance
+ * mode. */
+int32_t firal_pcg(firal_problem* problem, const void* z, const void* B, int32_t s,
+                  const firal_cg_opts* cg, void* X_out, int32_t* iters_out,
+                  double* relres_out);
+
+/* Per-point quadratic forms g_i = -(scale/s) sum_j a_j^T H_i b_j for the n pool points
+ * (eq. 11 with a = v, b = w; the autograd backward with a = u, b = y).  A, B: device,
+ * s*dt of the vec type; g_out: device, n values of the vec type. */
+int32_t firal_quad_forms(firal_problem* problem, const void* A, const void* B, int32_t s,
+                         double scale, void* g_out);
+
+/* Mirror-descent update (Algorithm 2 lines 10-11) on the budget simplex:
+ * z <- z exp(-beta g), z <- budget z / sum(z), beta = beta0 / ||g||_inf.  z, g: device,
+ * n values of the vec type; z updated in place. */
+int32_t firal_md_step(firal_problem* problem, void* z, const void* g, double budget,
+                      double beta0);
+
+/* Objective forward for the autograd Function: with probes V_t(seed, t), U = Sigma_z^{-1} V
+ * and Y = Sigma_z^{-1} H_p V (one 2s-column PCG), f^ = (1/s) sum_j <H_p v_j, u_j>.
+ * fhat_out: host double (the call synchronises).  U_out, Y_out: device, s*dt each (may be
+ * NULL to discard; the backward can recompute them). */
+int32_t firal_objective_fwd(firal_problem* problem, const void* z, uint64_t seed, int32_t t,
+                            int32_t s, const firal_cg_opts* cg, double* fhat_out,
+                            void* U_out, void* Y_out);
+
+/* Objective backward: g_out = grad_out * d f^/d z_i = -(grad_out/s) sum_j u_j^T H_i y_j
+ * (the exact derivative of f^ for fixed probes).  U, Y: device, from the forward; pass NULL
+ * for both to recompute them with the forward's (z, seed, t, s, cg). */
+int32_t firal_objective_bwd(firal_problem* problem, const void* z, uint64_t seed, int32_t t,
+                            int32_t s, const firal_cg_opts* cg, const void* U, const void* Y,
+                            double grad_out, void* g_out);
+
+/* Eigenvalues of L_k^{-1} H_k L_k^{-T} for c blocks (Algorithm 3 line 9), FP64 Householder
+ * tridiagonalisation and Sturm bisection.  Sig, H: device, c*d*d doubles (Sig_k SPD; L_k its
+ * Cholesky factor); eig_out: device, c*d doubles, ascending per block. */
+int32_t firal_block_eigvals(firal_handle* handle, int32_t c, int32_t d, const double* Sig,
+                            const double* H, double* eig_out);
+
+/* Root of sum_j (nu + mu_j)^{-2} = 1 (eq. 10, Algorithm 3 line 10) for count values
+ * mu (device doubles); nu_out: host double (synchronises). */
+int32_t firal_nu_bisect(firal_handle* handle, const double* mu, int64_t count, double* nu_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FIRAL_H */

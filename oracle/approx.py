@@ -55,7 +55,7 @@ def hessian_apply(X, h, w, V, chunk=None):
     s = V.shape[1]
     out = np.zeros((c, d, s))
     Vm = V.reshape(c, d, s)                          # Vm[k, e, j] = V_j[e, k]
-    step = n if chunk is None else chunk
+    step = max(n, 1) if chunk is None else chunk
     for a in range(0, n, step):
         Xa, ha, wa = X[a:a + step], h[a:a + step], w[a:a + step]
         for j in range(s):

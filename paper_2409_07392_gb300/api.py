@@ -1,0 +1,292 @@
+"""Python binding of the C-ABI: torch tensors in, torch tensors out.
+
+Every step runs in the CUDA library; this module only checks shapes, allocates outputs
+with torch (device memory and streams are torch's), and marshals pointers.
+"""
+from __future__ import annotations
+
+import atexit
+import ctypes
+import sys
+import weakref
+
+import torch
+
+from . import _lib as L
+
+PRECISIONS = {"fp64": L.FIRAL_FP64, "fp32": L.FIRAL_FP32, "mixed": L.FIRAL_MIXED_BF16}
+
+
+_LIVE_PROBLEMS = weakref.WeakSet()
+_LIVE_HANDLES = weakref.WeakSet()
+
+
+@atexit.register
+def _close_all():
+    """Release library objects before interpreter teardown (the CUDA runtime may be gone later)."""
+    for p in list(_LIVE_PROBLEMS):
+        p.close()
+    for h in list(_LIVE_HANDLES):
+        h.close()
+
+
+def _dt(t: torch.Tensor) -> int:
+    return {torch.float64: L.FIRAL_DT_F64, torch.float32: L.FIRAL_DT_F32,
+            torch.bfloat16: L.FIRAL_DT_BF16}[t.dtype]
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def vec_dtype(precision: str):
+    return torch.float64 if precision == "fp64" else torch.float32
+
+
+class Handle:
+    """A library handle bound to the current device and torch's current stream."""
+
+    def __init__(self, stream: torch.cuda.Stream | None = None):
+        self.lib = L.load()
+        st = stream if stream is not None else torch.cuda.current_stream()
+        self._h = ctypes.c_void_p()
+        L.check(self.lib.firal_create(ctypes.byref(self._h), ctypes.c_void_p(st.cuda_stream)))
+        _LIVE_HANDLES.add(self)
+
+    @property
+    def ptr(self):
+        return self._h
+
+    def set_stream(self, stream: torch.cuda.Stream):
+        L.check(self.lib.firal_set_stream(self._h, ctypes.c_void_p(stream.cuda_stream)), self._h)
+
+    def close(self):
+        if self._h:
+            self.lib.firal_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        if sys.is_finalizing():
+            return
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- standalone building blocks
+    def block_eigvals(self, Sig: torch.Tensor, H: torch.Tensor) -> torch.Tensor:
+        c, d, _ = Sig.shape
+        Sig = Sig.contiguous().to(torch.float64)
+        H = H.contiguous().to(torch.float64)
+        out = torch.empty((c, d), dtype=torch.float64, device=Sig.device)
+        L.check(self.lib.firal_block_eigvals(self._h, c, d, _ptr(Sig), _ptr(H), _ptr(out)),
+                self._h)
+        return out
+
+    def nu_bisect(self, mu: torch.Tensor) -> float:
+        mu = mu.contiguous().to(torch.float64)
+        nu = ctypes.c_double()
+        L.check(self.lib.firal_nu_bisect(self._h, _ptr(mu), mu.numel(), ctypes.byref(nu)),
+                self._h)
+        return nu.value
+
+
+def _pool(X, h):
+    return L.FiralPool(ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(h.data_ptr()), X.shape[0],
+                       X.shape[1], h.shape[1], _dt(X), _dt(h))
+
+
+def _hess0(Xo, ho, lam):
+    if Xo is None or Xo.shape[0] == 0:
+        return L.FiralHess0(None, None, 0, lam)
+    return L.FiralHess0(ctypes.c_void_p(Xo.data_ptr()), ctypes.c_void_p(ho.data_ptr()),
+                        Xo.shape[0], lam)
+
+
+def _cg(tol=0.1, maxit=100, fixed_iters=0):
+    return L.FiralCGOpts(tol, maxit, fixed_iters)
+
+
+class Problem:
+    """A prepared problem (pool, labelled set, lambda) for one precision."""
+
+    def __init__(self, handle: Handle, X, h, Xo=None, ho=None, lam=1e-3, precision="fp32"):
+        self.handle = handle
+        self.lib = handle.lib
+        self.precision = precision
+        self.vdt = vec_dtype(precision)
+        for t in (X, h):
+            assert t.is_cuda and t.is_contiguous()
+        self.n, self.d = X.shape
+        self.c = h.shape[1]
+        self.D = self.d * self.c
+        self.device = X.device
+        pool = _pool(X, h)
+        h0 = _hess0(Xo, ho, lam)
+        self._p = ctypes.c_void_p()
+        L.check(self.lib.firal_problem_create(handle.ptr, ctypes.byref(pool), ctypes.byref(h0),
+                                              PRECISIONS[precision], ctypes.byref(self._p)),
+                handle.ptr)
+        _LIVE_PROBLEMS.add(self)
+
+    def close(self):
+        if self._p:
+            self.lib.firal_problem_destroy(self._p)
+            self._p = ctypes.c_void_p()
+
+    def __del__(self):
+        if sys.is_finalizing():
+            return
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, code):
+        L.check(code, self.handle.ptr)
+
+    def _vec(self, t):
+        t = t.to(self.device, self.vdt).contiguous()
+        return t
+
+    def probes(self, seed: int, t: int, s: int) -> torch.Tensor:
+        V = torch.empty((s, self.D), dtype=self.vdt, device=self.device)
+        self._chk(self.lib.firal_probes(self._p, seed, t, s, _ptr(V)))
+        return V
+
+    def hessian_apply(self, V: torch.Tensor, z: torch.Tensor | None = None, op: int = 0):
+        """op 0: Sigma_z V; op 1: H_p V.  V is (s, D) probe-major."""
+        V = self._vec(V)
+        zz = self._vec(z) if z is not None else None
+        out = torch.empty_like(V)
+        self._chk(self.lib.firal_hessian_apply(self._p, op, _ptr(zz), _ptr(V), V.shape[0],
+                                               _ptr(out)))
+        return out
+
+    def precond_blocks(self, z: torch.Tensor | None = None) -> torch.Tensor:
+        zz = self._vec(z) if z is not None else None
+        out = torch.empty((self.c, self.d, self.d), dtype=torch.float64, device=self.device)
+        self._chk(self.lib.firal_precond_blocks(self._p, _ptr(zz), _ptr(out)))
+        return out
+
+    def pcg(self, z, B, tol=0.1, maxit=100, fixed_iters=0, check=True):
+        z, B = self._vec(z), self._vec(B)
+        s = B.shape[0]
+        X = torch.empty_like(B)
+        iters = (ctypes.c_int32 * s)()
+        relres = (ctypes.c_double * s)()
+        cg = _cg(tol, maxit, fixed_iters)
+        code = self.lib.firal_pcg(self._p, _ptr(z), _ptr(B), s, ctypes.byref(cg), _ptr(X), iters,
+                                  relres)
+        if check or code not in (0, -4):
+            self._chk(code)
+        return X, list(iters), list(relres)
+
+    def quad_forms(self, A, B, scale=1.0):
+        A, B = self._vec(A), self._vec(B)
+        g = torch.empty(self.n, dtype=self.vdt, device=self.device)
+        self._chk(self.lib.firal_quad_forms(self._p, _ptr(A), _ptr(B), A.shape[0], scale, _ptr(g)))
+        return g
+
+    def md_step(self, z, g, budget, beta0=1.0):
+        z = self._vec(z).clone()
+        g = self._vec(g)
+        self._chk(self.lib.firal_md_step(self._p, _ptr(z), _ptr(g), budget, beta0))
+        return z
+
+    def relax_opts(self, s=10, T=20, tol=0.1, maxit=100, fixed_iters=0, beta0=1.0, seed=1,
+                   estimator=0, md_tol=0.0):
+        return L.FiralRelaxOpts(s, T, _cg(tol, maxit, fixed_iters), beta0, seed,
+                                PRECISIONS[self.precision], estimator, md_tol)
+
+    def relax_step(self, opts, t, budget, z, stats=True):
+        st = L.FiralStepStats()
+        self._chk(self.lib.firal_relax_step(self._p, ctypes.byref(opts), t, budget, _ptr(z),
+                                            ctypes.byref(st) if stats else None))
+        if not stats:
+            return None
+        return dict(fhat=st.fhat, gmax=st.gmax, zmax=st.zmax, cg_iters=list(st.cg_iters),
+                    cg_relres=list(st.cg_relres))
+
+    def objective_fwd(self, z, seed, t, s, tol=0.1, maxit=100, fixed_iters=0, keep=True):
+        z = self._vec(z)
+        cg = _cg(tol, maxit, fixed_iters)
+        U = torch.empty((s, self.D), dtype=self.vdt, device=self.device) if keep else None
+        Y = torch.empty_like(U) if keep else None
+        f = ctypes.c_double()
+        self._chk(self.lib.firal_objective_fwd(self._p, _ptr(z), seed, t, s, ctypes.byref(cg),
+                                               ctypes.byref(f), _ptr(U), _ptr(Y)))
+        return f.value, U, Y
+
+    def objective_bwd(self, z, seed, t, s, U=None, Y=None, grad_out=1.0, tol=0.1, maxit=100,
+                      fixed_iters=0):
+        z = self._vec(z)
+        cg = _cg(tol, maxit, fixed_iters)
+        g = torch.empty(self.n, dtype=self.vdt, device=self.device)
+        self._chk(self.lib.firal_objective_bwd(self._p, _ptr(z), seed, t, s, ctypes.byref(cg),
+                                               _ptr(U), _ptr(Y), grad_out, _ptr(g)))
+        return g
+
+    def round(self, z, budget, eta=0.0, exclude_selected=True):
+        z = self._vec(z)
+        sel = torch.empty(budget, dtype=torch.int32, device=self.device)
+        o = L.FiralRoundOpts(eta, 1 if exclude_selected else 0, PRECISIONS[self.precision])
+        st = L.FiralRoundStats()
+        self._chk(self.lib.firal_round_problem(self._p, _ptr(z), budget, ctypes.byref(o),
+                                               _ptr(sel), ctypes.byref(st)))
+        return sel, dict(nu_last=st.nu_last, score_last=st.score_last)
+
+
+def _to_device(t, device, dtype=None, non_blocking=True):
+    if t is None:
+        return None
+    if dtype is not None and t.dtype != dtype:
+        t = t.to(dtype)
+    return t.to(device, non_blocking=non_blocking).contiguous()
+
+
+def relax(X, h, Xo=None, ho=None, lam=1e-3, budget=10.0, *, s=10, T=20, tol=0.1, maxit=100,
+          fixed_iters=0, beta0=1.0, seed=1, precision="fp32", estimator=0, md_tol=0.0, z0=None,
+          handle: Handle | None = None, device="cuda"):
+    """Relax solve (Algorithm 2).  Host (CPU, ideally pinned) or device tensors are accepted;
+    host inputs are copied to the device inside the call and z is returned on the inputs'
+    device.  Returns ``(z, fhat_history)``."""
+    host = not X.is_cuda
+    dev = torch.device(device) if host else X.device
+    Xd, hd = _to_device(X, dev), _to_device(h, dev)
+    Xod, hod = _to_device(Xo, dev), _to_device(ho, dev)
+    H = handle or Handle()
+    vdt = vec_dtype(precision)
+    z = torch.empty(Xd.shape[0], dtype=vdt, device=dev)
+    z0d = _to_device(z0, dev, vdt) if z0 is not None else None
+    opts = L.FiralRelaxOpts(s, T, _cg(tol, maxit, fixed_iters), beta0, seed,
+                            PRECISIONS[precision], estimator, md_tol)
+    hist = (ctypes.c_double * max(T, 1))()
+    st = L.FiralRelaxStats()
+    pool = _pool(Xd, hd)
+    h0 = _hess0(Xod, hod, lam)
+    L.check(H.lib.firal_relax(H.ptr, ctypes.byref(pool), ctypes.byref(h0), budget, _ptr(z0d),
+                              ctypes.byref(opts), _ptr(z), hist, ctypes.byref(st)), H.ptr)
+    fh = list(hist)[:st.iters_done]
+    if host:
+        z = z.to("cpu")
+    return z, fh
+
+
+def round_select(X, h, z, budget, Xo=None, ho=None, lam=1e-3, *, eta=0.0, precision="fp32",
+                 handle: Handle | None = None, device="cuda"):
+    """Round step (Algorithm 3): returns the selected pool indices (int32, selection order)."""
+    host = not X.is_cuda
+    dev = torch.device(device) if host else X.device
+    Xd, hd = _to_device(X, dev), _to_device(h, dev)
+    Xod, hod = _to_device(Xo, dev), _to_device(ho, dev)
+    H = handle or Handle()
+    zd = _to_device(z, dev, vec_dtype(precision))
+    sel = torch.empty(budget, dtype=torch.int32, device=dev)
+    o = L.FiralRoundOpts(eta, 1, PRECISIONS[precision])
+    st = L.FiralRoundStats()
+    pool = _pool(Xd, hd)
+    h0 = _hess0(Xod, hod, lam)
+    L.check(H.lib.firal_round(H.ptr, ctypes.byref(pool), ctypes.byref(h0), _ptr(zd), budget,
+                              ctypes.byref(o), _ptr(sel), ctypes.byref(st)), H.ptr)
+    return (sel.to("cpu") if host else sel), dict(nu_last=st.nu_last, score_last=st.score_last)

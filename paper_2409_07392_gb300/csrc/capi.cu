@@ -1,0 +1,817 @@
+// C-ABI entry points (include/firal.h) and host orchestration of the Relax and Round steps.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "firal_internal.cuh"
+
+namespace firal {
+
+static thread_local std::string g_detail;
+
+int32_t fail(int32_t code, const std::string& msg) {
+  g_detail = msg;
+  return code;
+}
+const std::string& last_detail() { return g_detail; }
+
+// ---------------------------------------------------------------------------- profiling
+std::atomic<long long> g_launches{0};
+
+namespace {
+struct Pending {
+  int id;
+  cudaEvent_t a, b;
+};
+struct Profiler {
+  std::mutex mu;
+  bool on = false;
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  double ms[PF_COUNT] = {};
+  long long calls[PF_COUNT] = {};
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void drain() {
+    for (auto& p : pending) {
+      float t = 0.f;
+      if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) {
+        ms[p.id] += t;
+        calls[p.id] += 1;
+      }
+      pool.push_back(p.a);
+      pool.push_back(p.b);
+    }
+    pending.clear();
+  }
+};
+Profiler& prof() {
+  static Profiler* p = new Profiler();   // never destroyed: no CUDA calls at process exit
+  return *p;
+}
+}  // namespace
+
+ProfScope::ProfScope(cudaStream_t s, int i) : st(s), id(i) {
+  Profiler& P = prof();
+  if (!P.on) return;
+  std::lock_guard<std::mutex> g(P.mu);
+  a = P.get();
+  cudaEventRecord(a, st);
+}
+ProfScope::~ProfScope() {
+  if (!a) return;
+  Profiler& P = prof();
+  std::lock_guard<std::mutex> g(P.mu);
+  cudaEvent_t b = P.get();
+  cudaEventRecord(b, st);
+  P.pending.push_back({id, a, b});
+  if (P.pending.size() > 4096) P.drain();
+}
+
+int32_t DBuf::ensure(size_t nbytes) {
+  if (nbytes <= bytes && p) return FIRAL_OK;
+  if (p) {
+    cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  if (nbytes == 0) nbytes = 16;
+  cudaError_t e = cudaMalloc(&p, nbytes);
+  if (e != cudaSuccess) {
+    p = nullptr;
+    return fail(FIRAL_ERR_NOMEM, std::string("cudaMalloc(") + std::to_string(nbytes) +
+                                     "): " + cudaGetErrorString(e));
+  }
+  bytes = nbytes;
+  return FIRAL_OK;
+}
+
+void DBuf::release() {
+  if (p) cudaFree(p);
+  p = nullptr;
+  bytes = 0;
+}
+
+// tensor-core entry points (k_tc.cu); return FIRAL_ERR_UNSUPPORTED when not built
+int32_t tc_prepare(firal_problem* P);
+int32_t tc_hessian_apply(firal_problem* P, const void* w, const void* Sblk, const void* V, int s,
+                         void* out, double* pq, double lam_null);
+int32_t tc_quad_forms(firal_problem* P, const void* A, const void* B, int s, double scale,
+                      void* g);
+bool tc_available();
+
+}  // namespace firal
+
+using namespace firal;
+
+namespace {
+
+inline size_t vsize(const firal_problem* P) { return P->dbl ? sizeof(double) : sizeof(float); }
+
+int32_t record(firal_handle* H, int32_t code) {
+  if (H && code != FIRAL_OK) H->err = last_detail();
+  return code;
+}
+
+int32_t read_flags(firal_handle* H) {
+  DevFlags f;
+  FIRAL_CUDA_TRY(cudaMemcpyAsync(&f, H->flags.p, sizeof(f), cudaMemcpyDeviceToHost, H->stream));
+  FIRAL_CUDA_TRY(cudaStreamSynchronize(H->stream));
+  if (f.not_spd || f.nonfinite || f.pad[0]) {
+    FIRAL_CUDA_TRY(cudaMemsetAsync(H->flags.p, 0, sizeof(DevFlags), H->stream));
+    if (f.pad[0])
+      return fail(FIRAL_ERR_TIMEOUT, "a tensor-core kernel wait gave up (site " +
+                                         std::to_string(f.pad[0]) + ")");
+    if (f.not_spd) return fail(FIRAL_ERR_NOT_SPD, "a block Cholesky met a non-positive pivot");
+    return fail(FIRAL_ERR_NONFINITE, "non-finite value in a reduction");
+  }
+  return FIRAL_OK;
+}
+
+int32_t* not_spd_flag(firal_handle* H) { return &H->flags.as<DevFlags>()->not_spd; }
+
+// Hessian apply dispatch (tensor cores for FIRAL_MIXED_BF16)
+int32_t apply(firal_problem* P, const void* w, const void* Sblk, const void* V, int s, void* out,
+              double* pq) {
+  if (P->prec == FIRAL_MIXED_BF16)
+    return tc_hessian_apply(P, w, Sblk, V, s, out, pq, w == P->w_sig.p ? P->lambda : 0.0);
+  return hessian_apply_simt(P, w, Sblk, V, s, out, pq);
+}
+
+int32_t quad(firal_problem* P, const void* A, const void* B, int s, double scale, void* g) {
+  if (P->prec == FIRAL_MIXED_BF16) return tc_quad_forms(P, A, B, s, scale, g);
+  return quad_forms_simt(P, A, B, s, scale, g);
+}
+
+// w_sig = [1 (labelled), z (pool)]; S_sig = diag-part operator with lambda; optional blocks
+int32_t setup_sigma(firal_problem* P, const void* z, bool want_precond) {
+  cudaStream_t st = P->H->stream;
+  if (z) {
+    FIRAL_CUDA_TRY(cudaMemcpyAsync((char*)P->w_sig.p + P->m * vsize(P), z, P->n * vsize(P),
+                                   cudaMemcpyDeviceToDevice, st));
+  }
+  FIRAL_TRY(syrk_blocks(P, P->w_sig.p, P->lambda, P->S_sig.p, P->lambda,
+                        want_precond ? P->Pblk.as<double>() : nullptr));
+  if (want_precond)
+    FIRAL_TRY(chol_inv(P->dbl, P->Pblk.as<double>(), P->c, P->d, P->Minv.p, nullptr, nullptr,
+                       not_spd_flag(P->H), st));
+  return FIRAL_OK;
+}
+
+int32_t ensure_sp(firal_problem* P) {
+  if (P->S_p_ready) return FIRAL_OK;
+  FIRAL_TRY(syrk_blocks(P, P->w_p.p, 0.0, P->S_p.p, 0.0, nullptr));
+  P->S_p_ready = true;
+  return FIRAL_OK;
+}
+
+int32_t ensure_cg(firal_problem* P, int s) {
+  const size_t vb = (size_t)s * P->D * vsize(P);
+  FIRAL_TRY(P->cgX.ensure(vb));
+  FIRAL_TRY(P->cgR.ensure(vb));
+  FIRAL_TRY(P->cgP.ensure(vb));
+  FIRAL_TRY(P->cgQ.ensure(vb));
+  FIRAL_TRY(P->cgZ.ensure(vb));
+  FIRAL_TRY(P->cgcols.ensure((size_t)s * sizeof(CGCol)));
+  FIRAL_TRY(P->cgpart1.ensure((size_t)s * P->c * sizeof(double)));
+  FIRAL_TRY(P->cgpart2.ensure((size_t)s * P->c * sizeof(double)));
+  return FIRAL_OK;
+}
+
+struct CGResult {
+  int32_t max_iters = 0;
+  double max_relres = 0.0;
+  bool converged = true;
+};
+
+// PCG on Sigma_z (w_sig, S_sig, Minv already set up).  X_out may alias nothing of the CG state.
+int32_t pcg_run(firal_problem* P, const void* B, int s, const firal_cg_opts& cg, void* X_out,
+                bool want_result, CGResult* res, std::vector<CGCol>* cols_out) {
+  cudaStream_t st = P->H->stream;
+  FIRAL_TRY(ensure_cg(P, s));
+  const int fixed = cg.fixed_iters > 0 ? 1 : 0;
+  const int iters = fixed ? cg.fixed_iters : (cg.maxit > 0 ? cg.maxit : 100);
+  const double tol = cg.tol;
+  FIRAL_TRY(cg_init(P, B, s, tol, fixed));
+  std::vector<CGCol> cols(s);
+  for (int it = 0; it < iters; ++it) {
+    if (!fixed) {
+      FIRAL_CUDA_TRY(cudaMemcpyAsync(cols.data(), P->cgcols.p, s * sizeof(CGCol),
+                                     cudaMemcpyDeviceToHost, st));
+      FIRAL_CUDA_TRY(cudaStreamSynchronize(st));
+      bool any = false;
+      for (int j = 0; j < s; ++j) any |= cols[j].active != 0;
+      if (!any) break;
+    }
+    FIRAL_TRY(apply(P, P->w_sig.p, P->S_sig.p, P->cgP.p, s, P->cgQ.p, P->cgpart1.as<double>()));
+    FIRAL_TRY(cg_iterate_tail(P, s, tol, fixed));
+  }
+  FIRAL_CUDA_TRY(cudaMemcpyAsync(X_out, P->cgX.p, (size_t)s * P->D * vsize(P),
+                                 cudaMemcpyDeviceToDevice, st));
+  if (want_result || !fixed) {
+    FIRAL_CUDA_TRY(cudaMemcpyAsync(cols.data(), P->cgcols.p, s * sizeof(CGCol),
+                                   cudaMemcpyDeviceToHost, st));
+    FIRAL_CUDA_TRY(cudaStreamSynchronize(st));
+    if (res) {
+      res->max_iters = 0;
+      res->max_relres = 0.0;
+      res->converged = true;
+      for (int j = 0; j < s; ++j) {
+        res->max_iters = std::max(res->max_iters, cols[j].iters);
+        res->max_relres = std::max(res->max_relres, cols[j].relres);
+        if (!fixed && cols[j].relres > tol && cols[j].bnorm2 > 0) res->converged = false;
+      }
+    }
+    if (cols_out) *cols_out = cols;
+  }
+  return FIRAL_OK;
+}
+
+int32_t validate_pool(const firal_pool* pool, const firal_hess0* h0) {
+  if (!pool || !pool->X || !pool->h) return fail(FIRAL_ERR_ARG, "pool, X and h must be non-null");
+  if (pool->n < 1) return fail(FIRAL_ERR_ARG, "pool size n must be >= 1");
+  if (pool->d < 1 || pool->d > 128) return fail(FIRAL_ERR_UNSUPPORTED, "d must be in [1, 128]");
+  if (pool->c < 2 || pool->c > 4096) return fail(FIRAL_ERR_UNSUPPORTED, "c must be in [2, 4096]");
+  if (pool->x_dtype < 0 || pool->x_dtype > 2) return fail(FIRAL_ERR_ARG, "bad x_dtype");
+  if (pool->h_dtype != FIRAL_DT_F32 && pool->h_dtype != FIRAL_DT_F64)
+    return fail(FIRAL_ERR_ARG, "h_dtype must be F32 or F64");
+  if (h0 && h0->m > 0 && (!h0->Xo || !h0->ho))
+    return fail(FIRAL_ERR_ARG, "labelled set pointers must be non-null when m > 0");
+  if (h0 && (h0->m < 0 || !(h0->lambda >= 0.0)))
+    return fail(FIRAL_ERR_ARG, "m must be >= 0 and lambda >= 0");
+  return FIRAL_OK;
+}
+
+int32_t problem_create_impl(firal_handle* H, const firal_pool* pool, const firal_hess0* h0,
+                            int32_t precision, firal_problem** out) {
+  if (!H || !out) return fail(FIRAL_ERR_ARG, "handle and out must be non-null");
+  FIRAL_TRY(validate_pool(pool, h0));
+  if (precision < FIRAL_FP64 || precision > FIRAL_MIXED_BF16)
+    return fail(FIRAL_ERR_ARG, "unknown precision");
+  if (precision == FIRAL_MIXED_BF16 && !tc_available())
+    return fail(FIRAL_ERR_UNSUPPORTED, "tensor-core path not built");
+  FIRAL_CUDA_TRY(cudaSetDevice(H->device));
+  auto* P = new firal_problem();
+  P->H = H;
+  P->prec = precision;
+  P->dbl = precision == FIRAL_FP64;
+  P->n = pool->n;
+  P->m = h0 ? h0->m : 0;
+  P->N = P->n + P->m;
+  P->d = pool->d;
+  P->c = pool->c;
+  P->D = (int64_t)P->d * P->c;
+  P->lambda = h0 ? h0->lambda : 0.0;
+  cudaStream_t st = H->stream;
+  const size_t vs = vsize(P);
+  auto cleanup = [&](int32_t code) {
+    firal_problem_destroy(P);
+    return code;
+  };
+  int32_t rc;
+#define TRYC(x)                     \
+  do {                              \
+    rc = (x);                       \
+    if (rc != FIRAL_OK) return cleanup(rc); \
+  } while (0)
+  TRYC(P->Xa.ensure((size_t)P->N * P->d * vs));
+  TRYC(P->Ha.ensure((size_t)P->N * P->c * vs));
+  TRYC(P->HaT.ensure((size_t)P->N * P->c * vs));
+  TRYC(copy_rows(P->dbl, P->Xa.p, h0 ? h0->Xo : nullptr, P->m, pool->X, P->n, P->d,
+                 pool->x_dtype, st));
+  TRYC(copy_rows(P->dbl, P->Ha.p, h0 ? h0->ho : nullptr, P->m, pool->h, P->n, P->c,
+                 pool->h_dtype, st));
+  TRYC(transpose(P->dbl, P->HaT.p, P->Ha.p, P->N, P->c, st));
+  TRYC(P->w_sig.ensure((size_t)P->N * vs));
+  TRYC(P->w_p.ensure((size_t)P->N * vs));
+  TRYC(P->zsave.ensure((size_t)P->N * vs));
+  TRYC(fill_weights(P->dbl, P->w_sig.p, P->m, 1.0, nullptr, 1.0 / P->n, P->n, st));
+  TRYC(fill_weights(P->dbl, P->w_p.p, P->m, 0.0, nullptr, 1.0 / P->n, P->n, st));
+  const size_t blk = (size_t)P->c * P->d * P->d;
+  TRYC(P->S_p.ensure(blk * vs));
+  TRYC(P->S_sig.ensure(blk * vs));
+  TRYC(P->Minv.ensure(blk * vs));
+  TRYC(P->Pblk.ensure(blk * sizeof(double)));
+  TRYC(P->HoBlk.ensure(blk * sizeof(double)));
+  TRYC(P->red.ensure(2048 * sizeof(double)));
+  TRYC(P->g.ensure((size_t)P->n * vs));
+  if (precision == FIRAL_MIXED_BF16) TRYC(tc_prepare(P));
+#undef TRYC
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cleanup(fail(FIRAL_ERR_CUDA, cudaGetErrorString(e)));
+  *out = P;
+  return FIRAL_OK;
+}
+
+int32_t relax_step_impl(firal_problem* P, const firal_relax_opts* o, int32_t t, double budget,
+                        void* z, firal_step_stats* stats) {
+  if (!P || !o || !z) return fail(FIRAL_ERR_ARG, "problem, opts and z must be non-null");
+  if (o->s < 1 || o->s > 256) return fail(FIRAL_ERR_ARG, "s must be in [1, 256]");
+  if (!(budget > 0)) return fail(FIRAL_ERR_ARG, "budget must be > 0");
+  cudaStream_t st = P->H->stream;
+  const int s = o->s;
+  const size_t vb = (size_t)s * P->D * vsize(P);
+  FIRAL_TRY(P->V.ensure(vb));
+  FIRAL_TRY(P->U.ensure(vb));
+  FIRAL_TRY(P->W.ensure(vb));
+  FIRAL_TRY(P->HU.ensure(vb));
+  // line 4: probes
+  FIRAL_TRY(probes(P->dbl, P->V.p, o->seed, t, s, P->D, st));
+  // line 5: preconditioner from Sigma_z (z copied into the pool part of w_sig)
+  FIRAL_TRY(setup_sigma(P, z, true));
+  FIRAL_TRY(ensure_sp(P));
+  CGResult r1, r2;
+  const bool want = stats != nullptr;
+  // line 6: U = Sigma^{-1} V
+  FIRAL_TRY(pcg_run(P, P->V.p, s, o->cg, P->U.p, want, &r1, nullptr));
+  // line 7: HU = H_p U, f^ = <V, HU>/s
+  FIRAL_TRY(apply(P, P->w_p.p, P->S_p.p, P->U.p, s, P->HU.p, nullptr));
+  double* red = P->red.as<double>();
+  FIRAL_TRY(dot_scaled(P->dbl, P->V.p, P->HU.p, (int64_t)s * P->D, 1.0 / s, red + 1024,
+                       red + 1536, st));
+  // line 8 (paper estimator) or the derivative of f^ (estimator 1)
+  const void* first;
+  if (o->estimator == 0) {
+    FIRAL_TRY(pcg_run(P, P->HU.p, s, o->cg, P->W.p, want, &r2, nullptr));
+    first = P->V.p;
+  } else {
+    FIRAL_TRY(apply(P, P->w_p.p, P->S_p.p, P->V.p, s, P->HU.p, nullptr));
+    FIRAL_TRY(pcg_run(P, P->HU.p, s, o->cg, P->W.p, want, &r2, nullptr));
+    first = P->U.p;
+  }
+  // line 9: gradient
+  FIRAL_TRY(quad(P, first, P->W.p, s, 1.0, P->g.p));
+  // lines 10-11: MD update on the budget simplex (in the pool part of w_sig), then copy out
+  void* zdev = (char*)P->w_sig.p + P->m * vsize(P);
+  FIRAL_TRY(md_step_simt(P->dbl, zdev, P->g.p, P->n, budget, o->beta0, red, st));
+  FIRAL_CUDA_TRY(cudaMemcpyAsync(z, zdev, P->n * vsize(P), cudaMemcpyDeviceToDevice, st));
+  if (stats) {
+    double h[4];
+    FIRAL_CUDA_TRY(cudaMemcpyAsync(h, red + 1536, sizeof(double), cudaMemcpyDeviceToHost, st));
+    FIRAL_CUDA_TRY(cudaMemcpyAsync(h + 1, red + 512, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                                   st));
+    FIRAL_CUDA_TRY(cudaStreamSynchronize(st));
+    stats->fhat = h[0];
+    stats->gmax = h[1];
+    stats->zmax = h[2];
+    stats->cg_iters[0] = r1.max_iters;
+    stats->cg_iters[1] = r2.max_iters;
+    stats->cg_relres[0] = r1.max_relres;
+    stats->cg_relres[1] = r2.max_relres;
+    FIRAL_TRY(read_flags(P->H));
+    if (!std::isfinite(h[0]) || !std::isfinite(h[1]))
+      return fail(FIRAL_ERR_NONFINITE, "non-finite objective or gradient");
+  }
+  return FIRAL_OK;
+}
+
+int32_t round_impl(firal_problem* P, const void* zr, int32_t b, const firal_round_opts* o,
+                   int32_t* sel, firal_round_stats* stats) {
+  if (!P || !zr || !sel) return fail(FIRAL_ERR_ARG, "problem, z and selected_out must be non-null");
+  if (b < 1 || b > P->n) return fail(FIRAL_ERR_ARG, "budget must be in [1, n]");
+  if (P->dbl && P->d > 90) return fail(FIRAL_ERR_UNSUPPORTED, "FP64 Round supports d <= 90");
+  cudaStream_t st = P->H->stream;
+  const int c = P->c, d = P->d;
+  const int64_t D = P->D;
+  const double eta = (o && o->eta > 0) ? o->eta : 8.0 * std::sqrt((double)D);
+  const size_t blk = (size_t)c * d * d;
+  DBuf Sig, L, Bm, Binv, Hk, M1, M2, eig, nu, mask, pv, pi, score;
+  auto rel = [&]() {
+    for (DBuf* bf : {&Sig, &L, &Bm, &Binv, &Hk, &M1, &M2, &eig, &nu, &mask, &pv, &pi, &score})
+      bf->release();
+  };
+  const int np = (int)((P->n + 127) / 128);
+  int32_t rc = FIRAL_OK;
+#define TRYR(x)                    \
+  do {                             \
+    rc = (x);                      \
+    if (rc != FIRAL_OK) {          \
+      rel();                       \
+      return rc;                   \
+    }                              \
+  } while (0)
+  TRYR(Sig.ensure(blk * 8));
+  TRYR(L.ensure(blk * 8));
+  TRYR(Bm.ensure(blk * 8));
+  TRYR(Binv.ensure(blk * 8));
+  TRYR(Hk.ensure(blk * 8));
+  TRYR(M1.ensure(blk * vsize(P)));
+  TRYR(M2.ensure(blk * vsize(P)));
+  TRYR(eig.ensure((size_t)c * d * 8));
+  TRYR(nu.ensure(8));
+  TRYR(mask.ensure((size_t)P->n));
+  TRYR(pv.ensure((size_t)np * 8));
+  TRYR(pi.ensure((size_t)np * 8));
+  TRYR(score.ensure(8));
+  // B(H_o): weights 1 on labelled rows, 0 on the pool; Sigma_diamond: z on the pool (C-15)
+  TRYR(fill_weights(P->dbl, P->zsave.p, P->m, 1.0, nullptr, 0.0, P->n, st));
+  TRYR(syrk_blocks(P, P->zsave.p, 0.0, nullptr, P->lambda, P->HoBlk.as<double>()));
+  TRYR(fill_weights(P->dbl, P->zsave.p, P->m, 1.0, zr, 0.0, P->n, st));
+  TRYR(syrk_blocks(P, P->zsave.p, 0.0, nullptr, P->lambda, Sig.as<double>()));
+  TRYR(chol_inv(P->dbl, Sig.as<double>(), c, d, nullptr, nullptr, L.as<double>(),
+                not_spd_flag(P->H), st));
+  const int64_t tot = (int64_t)blk;
+  // line 4: B_1 = sqrt(d~) Sigma + (eta/b) H_o
+  TRYR(lincomb(Bm.as<double>(), std::sqrt((double)D), Sig.as<double>(), eta / b,
+               P->HoBlk.as<double>(), 0.0, nullptr, tot, st));
+  TRYR(chol_inv(P->dbl, Bm.as<double>(), c, d, nullptr, Binv.as<double>(), nullptr,
+                not_spd_flag(P->H), st));
+  TRYR(round_m(P->dbl, Binv.as<double>(), Sig.as<double>(), c, d, M1.p, M2.p, st));
+  FIRAL_CUDA_TRY(cudaMemsetAsync(Hk.p, 0, blk * 8, st));
+  FIRAL_CUDA_TRY(cudaMemsetAsync(mask.p, 0, (size_t)P->n, st));
+  for (int t = 0; t < b; ++t) {
+    // line 7: eq. 14 scores and the masked argmax
+    TRYR(round_scores(P, M1.p, M2.p, mask.as<uint8_t>(), eta, pv.as<double>(), pi.as<int64_t>(),
+                      np));
+    TRYR(round_pick(pv.as<double>(), pi.as<int64_t>(), np, mask.as<uint8_t>(), sel, t,
+                    score.as<double>(), st));
+    // line 8: H_k += B_k(H_o)/b + w x x^T
+    TRYR(round_hupdate(P, Hk.as<double>(), P->HoBlk.as<double>(), 1.0 / b, sel, t));
+    // line 9: eigenvalues of H~_k
+    TRYR(tilde_eigvals(L.as<double>(), Hk.as<double>(), c, d, eig.as<double>(), st));
+    // line 10: nu
+    TRYR(nu_bisect_dev(eig.as<double>(), (int64_t)c * d, eta, nu.as<double>(), st));
+    // line 11: B = nu Sigma + eta H + (eta/b) H_o, inverted
+    TRYR(lincomb_nu(Bm.as<double>(), nu.as<double>(), Sig.as<double>(), eta, Hk.as<double>(),
+                    eta / b, P->HoBlk.as<double>(), tot, st));
+    TRYR(chol_inv(P->dbl, Bm.as<double>(), c, d, nullptr, Binv.as<double>(), nullptr,
+                  not_spd_flag(P->H), st));
+    TRYR(round_m(P->dbl, Binv.as<double>(), Sig.as<double>(), c, d, M1.p, M2.p, st));
+  }
+  if (stats) {
+    double h[2];
+    FIRAL_CUDA_TRY(cudaMemcpyAsync(h, nu.p, 8, cudaMemcpyDeviceToHost, st));
+    FIRAL_CUDA_TRY(cudaMemcpyAsync(h + 1, score.p, 8, cudaMemcpyDeviceToHost, st));
+    FIRAL_CUDA_TRY(cudaStreamSynchronize(st));
+    stats->nu_last = h[0];
+    stats->score_last = h[1];
+  }
+  FIRAL_CUDA_TRY(cudaStreamSynchronize(st));
+  rel();
+#undef TRYR
+  return read_flags(P->H);
+}
+
+firal_relax_opts default_relax_opts() {
+  firal_relax_opts o;
+  o.s = 10;
+  o.T = 20;
+  o.cg.tol = 0.1;
+  o.cg.maxit = 100;
+  o.cg.fixed_iters = 0;
+  o.beta0 = 1.0;
+  o.seed = 1;
+  o.precision = FIRAL_FP32;
+  o.estimator = 0;
+  o.md_tol = 0.0;
+  return o;
+}
+
+}  // namespace
+
+// =========================================================================================
+// C-ABI
+// =========================================================================================
+extern "C" {
+
+const char* firal_status_string(int32_t s) {
+  switch (s) {
+    case FIRAL_OK: return "FIRAL_OK";
+    case FIRAL_ERR_ARG: return "FIRAL_ERR_ARG";
+    case FIRAL_ERR_CUDA: return "FIRAL_ERR_CUDA";
+    case FIRAL_ERR_NOT_SPD: return "FIRAL_ERR_NOT_SPD";
+    case FIRAL_ERR_CG_NOT_CONVERGED: return "FIRAL_ERR_CG_NOT_CONVERGED";
+    case FIRAL_ERR_NONFINITE: return "FIRAL_ERR_NONFINITE";
+    case FIRAL_ERR_TIMEOUT: return "FIRAL_ERR_TIMEOUT";
+    case FIRAL_ERR_NOMEM: return "FIRAL_ERR_NOMEM";
+    case FIRAL_ERR_UNSUPPORTED: return "FIRAL_ERR_UNSUPPORTED";
+    default: return "FIRAL_ERR_UNKNOWN";
+  }
+}
+
+int32_t firal_build_info(void) { return 1 | (tc_available() ? 2 : 0); }
+
+int64_t firal_launch_count(void) { return g_launches.load(); }
+
+int32_t firal_profile(int32_t enable) {
+  Profiler& P = prof();
+  std::lock_guard<std::mutex> g(P.mu);
+  P.drain();
+  for (int i = 0; i < PF_COUNT; ++i) {
+    P.ms[i] = 0.0;
+    P.calls[i] = 0;
+  }
+  P.on = enable != 0;
+  return FIRAL_OK;
+}
+
+int32_t firal_profile_read(double* ms_out, int64_t* calls_out, int32_t count) {
+  if (count < 0) return FIRAL_ERR_ARG;
+  Profiler& P = prof();
+  std::lock_guard<std::mutex> g(P.mu);
+  P.drain();
+  for (int i = 0; i < count && i < PF_COUNT; ++i) {
+    if (ms_out) ms_out[i] = P.ms[i];
+    if (calls_out) calls_out[i] = P.calls[i];
+  }
+  return PF_COUNT;
+}
+
+const char* firal_profile_name(int32_t id) {
+  static const char* names[PF_COUNT] = {"prep", "probes", "syrk_blocks", "chol_inv",
+                                        "apply_alpha", "apply_dterm", "apply_combine", "cg_vec",
+                                        "quad_forms", "md_step", "dot", "round"};
+  return (id >= 0 && id < PF_COUNT) ? names[id] : "unknown";
+}
+
+int32_t firal_create(firal_handle** out, void* stream) {
+  if (!out) return fail(FIRAL_ERR_ARG, "out must be non-null");
+  auto* H = new firal_handle();
+  cudaError_t e = cudaGetDevice(&H->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&H->sm_count, cudaDevAttrMultiProcessorCount, H->device);
+  if (e != cudaSuccess) {
+    delete H;
+    return fail(FIRAL_ERR_CUDA, cudaGetErrorString(e));
+  }
+  H->stream = (cudaStream_t)stream;
+  int32_t rc = H->flags.ensure(sizeof(DevFlags));
+  if (rc == FIRAL_OK) rc = H->scratch.ensure(4096);
+  if (rc != FIRAL_OK) {
+    delete H;
+    return rc;
+  }
+  e = cudaMemsetAsync(H->flags.p, 0, sizeof(DevFlags), H->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(H->stream);
+  if (e != cudaSuccess) {
+    H->flags.release();
+    H->scratch.release();
+    delete H;
+    return fail(FIRAL_ERR_CUDA, cudaGetErrorString(e));
+  }
+  *out = H;
+  return FIRAL_OK;
+}
+
+int32_t firal_destroy(firal_handle* H) {
+  if (!H) return FIRAL_OK;
+  cudaStreamSynchronize(H->stream);
+  H->flags.release();
+  H->scratch.release();
+  delete H;
+  return FIRAL_OK;
+}
+
+int32_t firal_set_stream(firal_handle* H, void* stream) {
+  if (!H) return fail(FIRAL_ERR_ARG, "handle must be non-null");
+  H->stream = (cudaStream_t)stream;
+  return FIRAL_OK;
+}
+
+int32_t firal_last_error(firal_handle* H, char* buf, size_t len) {
+  if (!buf || len == 0) return FIRAL_ERR_ARG;
+  const std::string& s = H ? H->err : last_detail();
+  std::strncpy(buf, s.c_str(), len - 1);
+  buf[len - 1] = 0;
+  return FIRAL_OK;
+}
+
+int32_t firal_problem_create(firal_handle* H, const firal_pool* pool, const firal_hess0* h0,
+                             int32_t precision, firal_problem** out) {
+  return record(H, problem_create_impl(H, pool, h0, precision, out));
+}
+
+int32_t firal_problem_destroy(firal_problem* P) {
+  if (!P) return FIRAL_OK;
+  cudaStreamSynchronize(P->H->stream);
+  for (DBuf* b : {&P->Xa, &P->Ha, &P->HaT, &P->w_sig, &P->w_p, &P->S_p, &P->S_sig, &P->Pblk,
+                  &P->Minv, &P->HoBlk, &P->walpha, &P->Dpart, &P->syrk_part, &P->cgX, &P->cgR,
+                  &P->cgP, &P->cgQ, &P->cgZ, &P->cgcols, &P->cgpart1, &P->cgpart2, &P->V, &P->U,
+                  &P->W, &P->HU, &P->g, &P->red, &P->zsave, &P->Xb, &P->Hb, &P->HbT, &P->Pb, &P->vmean, &P->qmean})
+    b->release();
+  delete P;
+  return FIRAL_OK;
+}
+
+int32_t firal_relax_step(firal_problem* P, const firal_relax_opts* o, int32_t t, double budget,
+                         void* z, firal_step_stats* stats) {
+  return record(P ? P->H : nullptr, relax_step_impl(P, o, t, budget, z, stats));
+}
+
+int32_t firal_relax(firal_handle* H, const firal_pool* pool, const firal_hess0* h0, double budget,
+                    const void* z0, const firal_relax_opts* opts, void* z_out, double* fhat_hist,
+                    firal_relax_stats* stats) {
+  if (!H || !z_out) return record(H, fail(FIRAL_ERR_ARG, "handle and z_out must be non-null"));
+  firal_relax_opts o = opts ? *opts : default_relax_opts();
+  if (o.T < 0) return record(H, fail(FIRAL_ERR_ARG, "T must be >= 0"));
+  firal_problem* P = nullptr;
+  int32_t rc = problem_create_impl(H, pool, h0, o.precision, &P);
+  if (rc != FIRAL_OK) return record(H, rc);
+  const size_t vs = P->dbl ? 8 : 4;
+  if (z0) {
+    rc = cudaMemcpyAsync(z_out, z0, P->n * vs, cudaMemcpyDeviceToDevice, H->stream) == cudaSuccess
+             ? FIRAL_OK
+             : fail(FIRAL_ERR_CUDA, "copy of z0 failed");
+  } else {
+    rc = fill_weights(P->dbl, z_out, 0, 0.0, nullptr, budget / P->n, P->n, H->stream);
+  }
+  firal_step_stats ss{};
+  const bool need_stats = fhat_hist || stats || o.md_tol > 0;
+  int it = 0, cg_total = 0;
+  double prev = 0.0, last = 0.0;
+  for (; rc == FIRAL_OK && it < o.T; ++it) {
+    rc = relax_step_impl(P, &o, it, budget, z_out, need_stats ? &ss : nullptr);
+    if (rc != FIRAL_OK) break;
+    if (need_stats) {
+      if (fhat_hist) fhat_hist[it] = ss.fhat;
+      cg_total += ss.cg_iters[0] + ss.cg_iters[1];
+      last = ss.fhat;
+      if (o.md_tol > 0 && it > 0 && std::fabs(ss.fhat - prev) <= o.md_tol * std::fabs(prev)) {
+        ++it;
+        break;
+      }
+      prev = ss.fhat;
+    }
+  }
+  if (rc == FIRAL_OK) rc = read_flags(H);
+  if (stats) {
+    stats->iters_done = it;
+    stats->fhat_last = last;
+    stats->cg_iters_total = cg_total;
+  }
+  firal_problem_destroy(P);
+  return record(H, rc);
+}
+
+int32_t firal_round_problem(firal_problem* P, const void* zr, int32_t b,
+                            const firal_round_opts* o, int32_t* sel, firal_round_stats* stats) {
+  return record(P ? P->H : nullptr, round_impl(P, zr, b, o, sel, stats));
+}
+
+int32_t firal_round(firal_handle* H, const firal_pool* pool, const firal_hess0* h0,
+                    const void* zr, int32_t b, const firal_round_opts* o, int32_t* sel,
+                    firal_round_stats* stats) {
+  const int32_t prec = o ? o->precision : FIRAL_FP32;
+  firal_problem* P = nullptr;
+  int32_t rc = problem_create_impl(H, pool, h0, prec == FIRAL_MIXED_BF16 ? FIRAL_FP32 : prec, &P);
+  if (rc != FIRAL_OK) return record(H, rc);
+  rc = round_impl(P, zr, b, o, sel, stats);
+  firal_problem_destroy(P);
+  return record(H, rc);
+}
+
+int32_t firal_probes(firal_problem* P, uint64_t seed, int32_t t, int32_t s, void* V) {
+  if (!P || !V || s < 1 || t < 0) return record(P ? P->H : nullptr, fail(FIRAL_ERR_ARG, "bad probe arguments"));
+  return record(P->H, probes(P->dbl, V, seed, t, s, P->D, P->H->stream));
+}
+
+int32_t firal_hessian_apply(firal_problem* P, int32_t op, const void* z, const void* V, int32_t s,
+                            void* out) {
+  firal_handle* H = P ? P->H : nullptr;
+  if (!P || !V || !out || s < 1 || (op == 0 && !z) || op < 0 || op > 1)
+    return record(H, fail(FIRAL_ERR_ARG, "bad hessian_apply arguments"));
+  if (V == out) return record(H, fail(FIRAL_ERR_ARG, "out must not alias V"));
+  int32_t rc;
+  if (op == 0) {
+    rc = setup_sigma(P, z, false);
+    if (rc == FIRAL_OK) rc = apply(P, P->w_sig.p, P->S_sig.p, V, s, out, nullptr);
+  } else {
+    rc = ensure_sp(P);
+    if (rc == FIRAL_OK) rc = apply(P, P->w_p.p, P->S_p.p, V, s, out, nullptr);
+  }
+  return record(H, rc);
+}
+
+int32_t firal_precond_blocks(firal_problem* P, const void* z, double* out) {
+  firal_handle* H = P ? P->H : nullptr;
+  if (!P || !out) return record(H, fail(FIRAL_ERR_ARG, "bad precond_blocks arguments"));
+  cudaStream_t st = P->H->stream;
+  int32_t rc = fill_weights(P->dbl, P->zsave.p, P->m, 1.0, z, 0.0, P->n, st);
+  if (rc == FIRAL_OK) rc = syrk_blocks(P, P->zsave.p, 0.0, nullptr, P->lambda, out);
+  return record(H, rc);
+}
+
+int32_t firal_pcg(firal_problem* P, const void* z, const void* B, int32_t s,
+                  const firal_cg_opts* cg, void* X_out, int32_t* iters_out, double* relres_out) {
+  firal_handle* H = P ? P->H : nullptr;
+  if (!P || !z || !B || !X_out || !cg || s < 1)
+    return record(H, fail(FIRAL_ERR_ARG, "bad pcg arguments"));
+  int32_t rc = setup_sigma(P, z, true);
+  CGResult res;
+  std::vector<CGCol> cols;
+  const bool want = iters_out || relres_out;
+  if (rc == FIRAL_OK) rc = pcg_run(P, B, s, *cg, X_out, want, &res, &cols);
+  if (rc == FIRAL_OK && want) {
+    for (int j = 0; j < s; ++j) {
+      if (iters_out) iters_out[j] = cols[j].iters;
+      if (relres_out) relres_out[j] = cols[j].relres;
+    }
+    rc = read_flags(P->H);
+    if (rc == FIRAL_OK && cg->fixed_iters <= 0 && !res.converged)
+      rc = fail(FIRAL_ERR_CG_NOT_CONVERGED, "PCG reached maxit above tolerance");
+  }
+  return record(H, rc);
+}
+
+int32_t firal_quad_forms(firal_problem* P, const void* A, const void* B, int32_t s, double scale,
+                         void* g) {
+  firal_handle* H = P ? P->H : nullptr;
+  if (!P || !A || !B || !g || s < 1) return record(H, fail(FIRAL_ERR_ARG, "bad quad_forms arguments"));
+  return record(H, quad(P, A, B, s, scale, g));
+}
+
+int32_t firal_md_step(firal_problem* P, void* z, const void* g, double budget, double beta0) {
+  firal_handle* H = P ? P->H : nullptr;
+  if (!P || !z || !g || !(budget > 0)) return record(H, fail(FIRAL_ERR_ARG, "bad md_step arguments"));
+  return record(H, md_step_simt(P->dbl, z, g, P->n, budget, beta0, P->red.as<double>(),
+                                P->H->stream));
+}
+
+int32_t firal_objective_fwd(firal_problem* P, const void* z, uint64_t seed, int32_t t, int32_t s,
+                            const firal_cg_opts* cg, double* fhat_out, void* U_out, void* Y_out) {
+  firal_handle* H = P ? P->H : nullptr;
+  if (!P || !z || !cg || !fhat_out || s < 1 || s > 128)
+    return record(H, fail(FIRAL_ERR_ARG, "bad objective_fwd arguments"));
+  cudaStream_t st = P->H->stream;
+  const size_t vs = vsize(P);
+  const int64_t sD = (int64_t)s * P->D;
+  int32_t rc = FIRAL_OK;
+#define TRYF(x)                          \
+  do {                                   \
+    rc = (x);                            \
+    if (rc != FIRAL_OK) return record(H, rc); \
+  } while (0)
+  TRYF(P->V.ensure(2 * sD * vs));
+  TRYF(P->U.ensure(2 * sD * vs));
+  TRYF(P->HU.ensure(2 * sD * vs));
+  TRYF(probes(P->dbl, P->V.p, seed, t, s, P->D, st));
+  TRYF(setup_sigma(P, z, true));
+  TRYF(ensure_sp(P));
+  // right-hand sides [V, H_p V] solved together as one 2s-column PCG
+  FIRAL_CUDA_TRY(cudaMemcpyAsync(P->HU.p, P->V.p, sD * vs, cudaMemcpyDeviceToDevice, st));
+  TRYF(apply(P, P->w_p.p, P->S_p.p, P->V.p, s, (char*)P->HU.p + sD * vs, nullptr));
+  CGResult res;
+  TRYF(pcg_run(P, P->HU.p, 2 * s, *cg, P->U.p, true, &res, nullptr));
+  double* red = P->red.as<double>();
+  // f^ = (1/s) sum_j <H_p v_j, u_j>
+  TRYF(dot_scaled(P->dbl, (char*)P->HU.p + sD * vs, P->U.p, sD, 1.0 / s, red + 1024, red + 1536,
+                  st));
+  FIRAL_CUDA_TRY(cudaMemcpyAsync(fhat_out, red + 1536, 8, cudaMemcpyDeviceToHost, st));
+  if (U_out) FIRAL_CUDA_TRY(cudaMemcpyAsync(U_out, P->U.p, sD * vs, cudaMemcpyDeviceToDevice, st));
+  if (Y_out)
+    FIRAL_CUDA_TRY(cudaMemcpyAsync(Y_out, (char*)P->U.p + sD * vs, sD * vs,
+                                   cudaMemcpyDeviceToDevice, st));
+  FIRAL_CUDA_TRY(cudaStreamSynchronize(st));
+#undef TRYF
+  return record(H, read_flags(P->H));
+}
+
+int32_t firal_objective_bwd(firal_problem* P, const void* z, uint64_t seed, int32_t t, int32_t s,
+                            const firal_cg_opts* cg, const void* U, const void* Y, double grad_out,
+                            void* g_out) {
+  firal_handle* H = P ? P->H : nullptr;
+  if (!P || !g_out || s < 1) return record(H, fail(FIRAL_ERR_ARG, "bad objective_bwd arguments"));
+  if ((U == nullptr) != (Y == nullptr))
+    return record(H, fail(FIRAL_ERR_ARG, "pass both U and Y, or neither"));
+  if (U) return record(H, quad(P, U, Y, s, grad_out, g_out));
+  // recompute the probe solves
+  double fh = 0.0;
+  int32_t rc = firal_objective_fwd(P, z, seed, t, s, cg, &fh, nullptr, nullptr);
+  if (rc != FIRAL_OK) return rc;
+  const size_t off = (size_t)s * P->D * vsize(P);
+  return record(H, quad(P, P->U.p, (char*)P->U.p + off, s, grad_out, g_out));
+}
+
+int32_t firal_block_eigvals(firal_handle* H, int32_t c, int32_t d, const double* Sig,
+                            const double* Hm, double* eig) {
+  if (!H || !Sig || !Hm || !eig || c < 1 || d < 1 || d > 128)
+    return record(H, fail(FIRAL_ERR_ARG, "bad block_eigvals arguments"));
+  DBuf L;
+  int32_t rc = L.ensure((size_t)c * d * d * 8);
+  if (rc == FIRAL_OK)
+    rc = chol_inv(true, Sig, c, d, nullptr, nullptr, L.as<double>(), not_spd_flag(H), H->stream);
+  if (rc == FIRAL_OK) rc = tilde_eigvals(L.as<double>(), Hm, c, d, eig, H->stream);
+  if (rc == FIRAL_OK) rc = read_flags(H);
+  L.release();
+  return record(H, rc);
+}
+
+int32_t firal_nu_bisect(firal_handle* H, const double* mu, int64_t count, double* nu_out) {
+  if (!H || !mu || !nu_out || count < 1) return record(H, fail(FIRAL_ERR_ARG, "bad nu arguments"));
+  int32_t rc = nu_bisect_dev(mu, count, 1.0, H->scratch.as<double>(), H->stream);
+  if (rc == FIRAL_OK) {
+    if (cudaMemcpyAsync(nu_out, H->scratch.p, 8, cudaMemcpyDeviceToHost, H->stream) != cudaSuccess ||
+        cudaStreamSynchronize(H->stream) != cudaSuccess)
+      rc = fail(FIRAL_ERR_CUDA, "nu readback failed");
+  }
+  return record(H, rc);
+}
+
+}  // extern "C"

@@ -1,0 +1,170 @@
+// Internal declarations of the Approx-FIRAL GB300 library (not part of the C-ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <atomic>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "firal.h"
+
+namespace firal {
+
+// ------------------------------------------------------------------------------------------
+// Error plumbing: every host helper returns a firal_status; CUDA failures carry a detail.
+// ------------------------------------------------------------------------------------------
+struct Err {
+  int32_t code = FIRAL_OK;
+  std::string msg;
+};
+
+#define FIRAL_CUDA_TRY(expr)                                                              \
+  do {                                                                                    \
+    cudaError_t e_ = (expr);                                                              \
+    if (e_ != cudaSuccess) {                                                              \
+      return ::firal::fail(FIRAL_ERR_CUDA, std::string(#expr) + ": " +                    \
+                                               cudaGetErrorString(e_));                   \
+    }                                                                                     \
+  } while (0)
+
+#define FIRAL_TRY(expr)                \
+  do {                                 \
+    int32_t s_ = (expr);               \
+    if (s_ != FIRAL_OK) return s_;     \
+  } while (0)
+
+int32_t fail(int32_t code, const std::string& msg);   // records the detail in thread-local storage
+const std::string& last_detail();
+
+// ------------------------------------------------------------------------------------------
+// Device memory owned by the library.
+// ------------------------------------------------------------------------------------------
+struct DBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  int32_t ensure(size_t nbytes);   // grow (never shrink); contents not preserved
+  void release();
+  template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+// Per-column PCG state kept on the device (one entry per right-hand side).
+struct CGCol {
+  double rho;       // r^T z
+  double bnorm2;    // ||b||^2
+  double alpha;     // step of the current iteration (0 when inactive)
+  double beta;
+  double relres;    // ||r|| / ||b|| after the last update
+  int32_t active;   // 1 while the column iterates
+  int32_t iters;    // iterations taken
+};
+
+// Device-side status words written by kernels and read by the host on synchronising calls.
+struct DevFlags {
+  int32_t not_spd;     // set by a Cholesky that met a non-positive pivot
+  int32_t nonfinite;   // set when a reduction meets NaN/Inf
+  int32_t pad[2];
+};
+
+}  // namespace firal
+
+namespace firal {
+// Kernel-class timers and the launch counter (see firal_profile* in firal.h).
+enum ProfId {
+  PF_PREP = 0, PF_PROBES, PF_SYRK, PF_CHOL, PF_ALPHA, PF_DTERM, PF_COMBINE, PF_CG, PF_QUAD,
+  PF_MD, PF_DOT, PF_ROUND, PF_COUNT
+};
+extern std::atomic<long long> g_launches;
+inline void count_launch(int n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+struct ProfScope {
+  ProfScope(cudaStream_t st, int id);
+  ~ProfScope();
+  cudaStream_t st;
+  int id;
+  cudaEvent_t a = nullptr;
+};
+}  // namespace firal
+
+struct firal_handle {
+  int device = 0;
+  int sm_count = 148;
+  cudaStream_t stream = nullptr;
+  firal::DBuf flags;       // firal::DevFlags
+  firal::DBuf scratch;     // small reductions
+  std::string err;
+};
+
+struct firal_problem {
+  firal_handle* H = nullptr;
+  int32_t prec = FIRAL_FP32;
+  bool dbl = false;            // vec type is double
+  int64_t n = 0, m = 0, N = 0; // pool, labelled, total rows (labelled first)
+  int32_t d = 0, c = 0;
+  int64_t D = 0;               // d * c
+  double lambda = 0.0;
+
+  // SIMT layout, vec type: X (N x d), h (N x c), h^T (c x N)
+  firal::DBuf Xa, Ha, HaT;
+  // weights over all N rows: Sigma_z (1 on labelled, z on pool) and H_p (0 / 1/n)
+  firal::DBuf w_sig, w_p;
+  // block matrices (c x d x d): H_p diagonal-part operator, Sigma_z diagonal-part operator,
+  // preconditioner blocks (double), their inverse (vec type), B(H_o) (double)
+  firal::DBuf S_p, S_sig, Pblk, Minv, HoBlk;
+  bool S_p_ready = false;
+  // scratch of the Hessian apply
+  firal::DBuf walpha, Dpart, syrk_part;
+  // PCG
+  firal::DBuf cgX, cgR, cgP, cgQ, cgZ, cgcols, cgpart1, cgpart2;
+  // Relax iteration buffers
+  firal::DBuf V, U, W, HU, g, red, zsave;
+
+  // tensor-core layout (FIRAL_MIXED_BF16): bf16 X (N x dp), bf16 h (Np x cp), its transpose
+  firal::DBuf Xb, Hb, HbT, Pb;   // Pb: bf16 (hi/lo) operand of the probe block
+  firal::DBuf vmean, qmean;      // class means of the probe block / of the raw apply (s x d)
+  int32_t dp = 0, cp = 0;
+  int64_t Np = 0;
+};
+
+namespace firal {
+// ---- k_simt.cu
+int32_t copy_rows(bool dbl, void* dst, const void* a, int64_t ma, const void* b, int64_t nb,
+                  int cols, int32_t src_dtype, cudaStream_t st);
+int32_t transpose(bool dbl, void* dst, const void* src, int64_t rows, int cols, cudaStream_t st);
+int32_t fill_weights(bool dbl, void* w, int64_t m, double lab_val, const void* z, double zconst,
+                     int64_t n, cudaStream_t st);
+int32_t probes(bool dbl, void* V, uint64_t seed, int64_t t, int s, int64_t D, cudaStream_t st);
+int32_t syrk_blocks(firal_problem* P, const void* w, double lamS, void* outS, double lamP,
+                    double* outP);
+int32_t hessian_apply_simt(firal_problem* P, const void* w, const void* Sblk, const void* V,
+                           int s, void* out, double* pq);
+int32_t combine_f32(firal_problem* P, const float* Sblk, const float* V, int splits, int s,
+                    float* out, double* pq, const float* vmean);
+int32_t cg_init(firal_problem* P, const void* B, int s, double tol, int fixed);
+int32_t cg_iterate_tail(firal_problem* P, int s, double tol, int fixed);
+int32_t quad_forms_simt(firal_problem* P, const void* A, const void* B, int s, double scale,
+                        void* g);
+int32_t dot_scaled(bool dbl, const void* a, const void* b, int64_t total, double scale,
+                   double* part, double* out, cudaStream_t st);
+int32_t md_step_simt(bool dbl, void* z, const void* g, int64_t n, double budget, double beta0,
+                     double* red, cudaStream_t st);
+// ---- k_linalg.cu
+int32_t chol_inv(bool dbl, const double* A, int c, int d, void* inv_t, double* inv_d,
+                 double* L_out, int32_t* not_spd, cudaStream_t st);
+int32_t tilde_eigvals(const double* L, const double* H, int c, int d, double* eig,
+                      cudaStream_t st);
+int32_t nu_bisect_dev(const double* lam, int64_t count, double scale, double* nu_out,
+                      cudaStream_t st);
+int32_t round_scores(firal_problem* P, const void* M1, const void* M2, const uint8_t* mask,
+                     double eta, double* pv, int64_t* pi, int np);
+int32_t round_pick(const double* pv, const int64_t* pi, int np, uint8_t* mask, int32_t* sel,
+                   int32_t t, double* score_out, cudaStream_t st);
+int32_t round_m(bool dbl, const double* Binv, const double* Sig, int c, int d, void* M1, void* M2,
+                cudaStream_t st);
+int32_t round_hupdate(firal_problem* P, double* H, const double* Ho, double invb,
+                      const int32_t* sel, int32_t t);
+int32_t lincomb(double* out, double a, const double* X, double b, const double* Y, double cc,
+                const double* Z, int64_t total, cudaStream_t st);
+int32_t lincomb_nu(double* out, const double* nu, const double* X, double b, const double* Y,
+                   double cc, const double* Z, int64_t total, cudaStream_t st);
+}  // namespace firal

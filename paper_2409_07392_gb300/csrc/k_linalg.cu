@@ -1,0 +1,583 @@
+// FP64 block linear algebra and the Round-step kernels (Algorithm 3).
+//
+//  * k_chol_inv   -- Cholesky of c SPD d x d blocks (one CTA per block, shared memory),
+//                    explicit inverse A^{-1} = L^{-T} L^{-1}; a non-positive pivot raises a
+//                    device flag (FIRAL_ERR_NOT_SPD) instead of trapping.
+//  * k_tilde_eig  -- eigenvalues of L^{-1} H L^{-T} (similar to Sigma^{-1/2} H Sigma^{-1/2}):
+//                    two in-place triangular solves, Householder tridiagonalisation and
+//                    Sturm-sequence bisection (Golub & Van Loan, Sections 8.3 and 8.4).
+//  * k_nu         -- the root of sum_j (nu + mu_j)^{-2} = 1 (eq. 10) by bisection.
+//  * Round kernels -- eq. 14 scores with a masked argmax, the block update of H, and the
+//                    assembly of B_t (Algorithm 3 lines 7-11).
+#include "firal_internal.cuh"
+
+namespace firal {
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ double block_sum_d(double v, double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum_d(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double r = 0;
+  for (int i = 0; i < nw; ++i) r += red[i];
+  __syncthreads();
+  return r;
+}
+
+// ------------------------------------------------------------------------------------------
+// Cholesky + inverse of c blocks
+// ------------------------------------------------------------------------------------------
+template <class T>
+__global__ void k_chol_inv(const double* __restrict__ A, int d, T* __restrict__ inv_t,
+                           double* __restrict__ inv_d, double* __restrict__ L_out,
+                           int32_t* not_spd) {
+  extern __shared__ double sh[];
+  double* Ls = sh;             // d*d
+  double* yd = sh + d * d;     // d
+  const int k = blockIdx.x, tid = threadIdx.x, bd = blockDim.x;
+  const double* Ak = A + (int64_t)k * d * d;
+  for (int t = tid; t < d * d; t += bd) Ls[t] = Ak[t];
+  __syncthreads();
+  for (int j = 0; j < d; ++j) {
+    if (tid == 0) {
+      double v = Ls[j * d + j];
+      if (!(v > 0.0)) {
+        atomicExch(not_spd, 1);
+        v = fabs(v) > 1e-300 ? fabs(v) : 1e-300;
+      }
+      Ls[j * d + j] = sqrt(v);
+    }
+    __syncthreads();
+    const double ljj = Ls[j * d + j];
+    for (int i = j + 1 + tid; i < d; i += bd) Ls[i * d + j] /= ljj;
+    __syncthreads();
+    const int rem = d - j - 1;
+    for (int t = tid; t < rem * rem; t += bd) {
+      const int ii = j + 1 + t / rem, kk = j + 1 + t % rem;
+      if (kk <= ii) Ls[ii * d + kk] -= Ls[ii * d + j] * Ls[kk * d + j];
+    }
+    __syncthreads();
+  }
+  if (L_out) {
+    for (int t = tid; t < d * d; t += bd) {
+      const int i = t / d, jj = t % d;
+      L_out[(int64_t)k * d * d + t] = jj <= i ? Ls[t] : 0.0;
+    }
+  }
+  __syncthreads();
+  if (!inv_t && !inv_d) return;
+  // Y = L^{-1}: column col by forward substitution; y[i] (i > col) kept in Ls[col][i]
+  for (int col = tid; col < d; col += bd) {
+    yd[col] = 1.0 / Ls[col * d + col];
+    for (int i = col + 1; i < d; ++i) {
+      double acc = Ls[i * d + col] * yd[col];
+      for (int p = col + 1; p < i; ++p) acc += Ls[i * d + p] * Ls[col * d + p];
+      Ls[col * d + i] = -acc / Ls[i * d + i];
+    }
+  }
+  __syncthreads();
+  // A^{-1}[a][b] = sum_{i >= max(a,b)} Y[i][a] Y[i][b]
+  for (int t = tid; t < d * d; t += bd) {
+    const int a = t / d, b = t % d;
+    const int lo = a > b ? a : b;
+    double acc = 0.0;
+    for (int i = lo; i < d; ++i) {
+      const double ya = i == a ? yd[a] : Ls[a * d + i];
+      const double yb = i == b ? yd[b] : Ls[b * d + i];
+      acc += ya * yb;
+    }
+    if (inv_t) inv_t[(int64_t)k * d * d + t] = (T)acc;
+    if (inv_d) inv_d[(int64_t)k * d * d + t] = acc;
+  }
+}
+
+static int threads_for(int d) {
+  int t = ((d * 2 + 31) / 32) * 32;
+  if (t < 64) t = 64;
+  if (t > 256) t = 256;
+  return t;
+}
+
+int32_t chol_inv(bool dbl, const double* A, int c, int d, void* inv_t, double* inv_d,
+                 double* L_out, int32_t* not_spd, cudaStream_t st) {
+  const size_t smem = ((size_t)d * d + d) * sizeof(double);
+  const int thr = threads_for(d);
+  ProfScope ps(st, PF_CHOL);
+  count_launch();
+  if (dbl) {
+    FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_chol_inv<double>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    k_chol_inv<double><<<c, thr, smem, st>>>(A, d, (double*)inv_t, inv_d, L_out, not_spd);
+  } else {
+    FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_chol_inv<float>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    k_chol_inv<float><<<c, thr, smem, st>>>(A, d, (float*)inv_t, inv_d, L_out, not_spd);
+  }
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  return FIRAL_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// eigenvalues of L^{-1} H L^{-T}, per block
+// ------------------------------------------------------------------------------------------
+__device__ int sturm_count(const double* dg, const double* e2, int d, double x) {
+  int cnt = 0;
+  double q = dg[0] - x;
+  if (q < 0) ++cnt;
+  for (int i = 1; i < d; ++i) {
+    if (q == 0.0) q = 1e-300;
+    q = dg[i] - x - e2[i - 1] / q;
+    if (q < 0) ++cnt;
+  }
+  return cnt;
+}
+
+__global__ void k_tilde_eig(const double* __restrict__ L, const double* __restrict__ H, int d,
+                            double* __restrict__ eig) {
+  extern __shared__ double sh[];
+  double* M = sh;              // d*d
+  double* v = M + d * d;       // d
+  double* p = v + d;           // d
+  double* dg = p + d;          // d
+  double* e2 = dg + d;         // d  (squared off-diagonal)
+  __shared__ double red[32];
+  __shared__ double s_bcast[4];
+  const int k = blockIdx.x, tid = threadIdx.x, bd = blockDim.x;
+  const double* Lk = L + (int64_t)k * d * d;
+  const double* Hk = H + (int64_t)k * d * d;
+  // pass 1: column col of A = L^{-1} H, stored transposed in row col of M
+  for (int col = tid; col < d; col += bd) {
+    for (int i = 0; i < d; ++i) {
+      double acc = Hk[(int64_t)i * d + col];
+      for (int q = 0; q < i; ++q) acc -= Lk[(int64_t)i * d + q] * M[col * d + q];
+      M[col * d + i] = acc / Lk[(int64_t)i * d + i];
+    }
+  }
+  __syncthreads();
+  // pass 2: column col of M currently holds row col of A; solve L m = that column in place
+  for (int col = tid; col < d; col += bd) {
+    for (int i = 0; i < d; ++i) {
+      double acc = M[i * d + col];
+      for (int q = 0; q < i; ++q) acc -= Lk[(int64_t)i * d + q] * M[q * d + col];
+      M[i * d + col] = acc / Lk[(int64_t)i * d + i];
+    }
+  }
+  __syncthreads();
+  // symmetrise (rounding)
+  for (int t = tid; t < d * d; t += bd) {
+    const int i = t / d, j = t % d;
+    if (j < i) {
+      const double a = 0.5 * (M[i * d + j] + M[j * d + i]);
+      M[i * d + j] = a;
+      M[j * d + i] = a;
+    }
+  }
+  __syncthreads();
+  // Householder tridiagonalisation
+  for (int kk = 0; kk + 2 < d; ++kk) {
+    double part = 0.0;
+    for (int i = kk + 2 + tid; i < d; i += bd) part += M[i * d + kk] * M[i * d + kk];
+    const double sigma = block_sum_d(part, red);
+    const double x0 = M[(kk + 1) * d + kk];
+    if (sigma == 0.0) {
+      if (tid == 0) e2[kk] = x0 * x0;
+      __syncthreads();
+      continue;
+    }
+    const double mu = sqrt(x0 * x0 + sigma);
+    const double alpha = x0 > 0 ? -mu : mu;
+    for (int i = kk + 1 + tid; i < d; i += bd) v[i] = i == kk + 1 ? x0 - alpha : M[i * d + kk];
+    __syncthreads();
+    const double vtv = (x0 - alpha) * (x0 - alpha) + sigma;
+    const double tau = 2.0 / vtv;
+    for (int i = kk + 1 + tid; i < d; i += bd) {
+      double acc = 0.0;
+      for (int j = kk + 1; j < d; ++j) acc += M[i * d + j] * v[j];
+      p[i] = tau * acc;
+    }
+    __syncthreads();
+    double pv = 0.0;
+    for (int i = kk + 1 + tid; i < d; i += bd) pv += p[i] * v[i];
+    const double Kc = 0.5 * tau * block_sum_d(pv, red);
+    for (int i = kk + 1 + tid; i < d; i += bd) p[i] -= Kc * v[i];   // p becomes w
+    __syncthreads();
+    const int rem = d - kk - 1;
+    for (int t = tid; t < rem * rem; t += bd) {
+      const int i = kk + 1 + t / rem, j = kk + 1 + t % rem;
+      M[i * d + j] -= v[i] * p[j] + p[i] * v[j];
+    }
+    if (tid == 0) e2[kk] = alpha * alpha;
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (d >= 2) e2[d - 2] = M[(d - 1) * d + (d - 2)] * M[(d - 1) * d + (d - 2)];
+  }
+  for (int i = tid; i < d; i += bd) dg[i] = M[i * d + i];
+  __syncthreads();
+  // Gershgorin interval (thread 0)
+  if (tid == 0) {
+    double lo = 1e300, hi = -1e300;
+    for (int i = 0; i < d; ++i) {
+      const double r = (i > 0 ? sqrt(e2[i - 1]) : 0.0) + (i + 1 < d ? sqrt(e2[i]) : 0.0);
+      lo = fmin(lo, dg[i] - r);
+      hi = fmax(hi, dg[i] + r);
+    }
+    const double pad = 1e-12 * fmax(fabs(lo), fabs(hi)) + 1e-300;
+    s_bcast[0] = lo - pad;
+    s_bcast[1] = hi + pad;
+  }
+  __syncthreads();
+  for (int mth = tid; mth < d; mth += bd) {
+    double lo = s_bcast[0], hi = s_bcast[1];
+    for (int it = 0; it < 200; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (mid <= lo || mid >= hi) break;
+      if (sturm_count(dg, e2, d, mid) > mth) hi = mid;
+      else lo = mid;
+      if (hi - lo <= 4e-16 * fmax(fabs(lo), fabs(hi))) break;
+    }
+    eig[(int64_t)k * d + mth] = 0.5 * (lo + hi);
+  }
+}
+
+int32_t tilde_eigvals(const double* L, const double* H, int c, int d, double* eig,
+                      cudaStream_t st) {
+  const size_t smem = ((size_t)d * d + 4 * (size_t)d) * sizeof(double);
+  FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tilde_eig, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      200 * 1024));
+  ProfScope ps(st, PF_ROUND);
+  count_launch();
+  k_tilde_eig<<<c, threads_for(d), smem, st>>>(L, H, d, eig);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  return FIRAL_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// nu of eq. 10: sum_j (nu + scale*lam_j)^{-2} = 1, one block
+// ------------------------------------------------------------------------------------------
+__global__ void k_nu(const double* lam, int64_t count, double scale, double* nu_out) {
+  __shared__ double red[32];
+  __shared__ double s_lo, s_hi;
+  double mn = 1e300;
+  for (int64_t i = threadIdx.x; i < count; i += blockDim.x) mn = fmin(mn, scale * lam[i]);
+  // block min
+  for (int o = 16; o > 0; o >>= 1) mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mn;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 1e300;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = fmin(m, red[i]);
+    s_lo = -m;
+    s_hi = sqrt((double)count) - m;
+  }
+  __syncthreads();
+  double lo = s_lo, hi = s_hi;
+  for (int it = 0; it < 400; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    double part = 0.0;
+    for (int64_t i = threadIdx.x; i < count; i += blockDim.x) {
+      const double a = mid + scale * lam[i];
+      part += 1.0 / (a * a);
+    }
+    const double f = block_sum_d(part, red) - 1.0;
+    if (f > 0) lo = mid;
+    else hi = mid;
+    if (hi - lo <= 1e-15 * fmax(fabs(hi), 1.0)) break;
+  }
+  if (threadIdx.x == 0) *nu_out = 0.5 * (lo + hi);
+}
+
+int32_t nu_bisect_dev(const double* lam, int64_t count, double scale, double* nu_out,
+                      cudaStream_t st) {
+  ProfScope ps(st, PF_ROUND);
+  count_launch();
+  k_nu<<<1, 256, 0, st>>>(lam, count, scale, nu_out);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  return FIRAL_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Round kernels
+// ------------------------------------------------------------------------------------------
+// out = a*X + b*Y + c*Z (elementwise over c*d*d doubles); Y, Z may be null
+__global__ void k_axpbypcz(double* out, double a, const double* X, double b, const double* Y,
+                           double cc, const double* Z, int64_t total) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double v = a * X[i];
+    if (Y) v += b * Y[i];
+    if (Z) v += cc * Z[i];
+    out[i] = v;
+  }
+}
+
+__global__ void k_axpbypcz_nu(double* out, const double* nu, const double* X, double b,
+                              const double* Y, double cc, const double* Z, int64_t total) {
+  const double a = *nu;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = a * X[i] + b * Y[i] + cc * Z[i];
+}
+
+// M1_k = Binv_k Sig_k Binv_k (double in, T out); M2_k = Binv_k as T
+template <class T>
+__global__ void k_round_m(const double* __restrict__ Binv, const double* __restrict__ Sig, int d,
+                          T* __restrict__ M1, T* __restrict__ M2) {
+  extern __shared__ double sh[];
+  double* Bs = sh;           // d*d
+  double* Ts = sh + d * d;   // d*d: Sig * Binv
+  const int k = blockIdx.x, tid = threadIdx.x, bd = blockDim.x;
+  const double* Bk = Binv + (int64_t)k * d * d;
+  const double* Sk = Sig + (int64_t)k * d * d;
+  for (int t = tid; t < d * d; t += bd) Bs[t] = Bk[t];
+  __syncthreads();
+  for (int t = tid; t < d * d; t += bd) {
+    const int i = t / d, j = t % d;
+    double acc = 0.0;
+    for (int q = 0; q < d; ++q) acc += Sk[(int64_t)i * d + q] * Bs[q * d + j];
+    Ts[t] = acc;
+  }
+  __syncthreads();
+  for (int t = tid; t < d * d; t += bd) {
+    const int i = t / d, j = t % d;
+    double acc = 0.0;
+    for (int q = 0; q < d; ++q) acc += Bs[i * d + q] * Ts[q * d + j];
+    M1[(int64_t)k * d * d + t] = (T)acc;
+    M2[(int64_t)k * d * d + t] = (T)Bs[t];
+  }
+}
+
+// H_k += Ho_k / b + h_{it,k}(1 - h_{it,k}) x_it x_it^T   (pool row it, read from the device)
+template <class T>
+__global__ void k_round_hupdate(double* H, const double* Ho, double invb, const T* Xa,
+                                const T* Ha, int64_t m, int d, int c, const int32_t* it_ptr,
+                                int32_t t_index) {
+  const int k = blockIdx.x;
+  const int64_t row = m + it_ptr[t_index];
+  const double hv = (double)Ha[row * c + k];
+  const double wk = hv * (1.0 - hv);
+  for (int t = threadIdx.x; t < d * d; t += blockDim.x) {
+    const int e = t / d, f = t % d;
+    const double xe = (double)Xa[row * d + e], xf = (double)Xa[row * d + f];
+    H[(int64_t)k * d * d + t] += Ho[(int64_t)k * d * d + t] * invb + wk * xe * xf;
+  }
+}
+
+// eq. 14 scores for pool rows, masked argmax partial per block
+template <class T>
+__global__ __launch_bounds__(128) void k_round_scores(const T* __restrict__ Xa,
+                                                      const T* __restrict__ HaT,
+                                                      const T* __restrict__ M1,
+                                                      const T* __restrict__ M2,
+                                                      const uint8_t* __restrict__ mask,
+                                                      int64_t m, int64_t N, int d, int c,
+                                                      double eta, double* part_val,
+                                                      int64_t* part_idx) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* xs = (T*)smem_raw;           // [d][128]
+  T* Ms = xs + (size_t)d * 128;   // d*d
+  __shared__ double bv[4];
+  __shared__ int64_t bi[4];
+  const int tid = threadIdx.x;
+  const int64_t r0 = m + (int64_t)blockIdx.x * 128;
+  const int64_t row = r0 + tid;
+  for (int idx = tid; idx < d * 128; idx += 128) {
+    const int r = idx / d, e = idx - r * d;
+    const int64_t ii = r0 + r;
+    xs[e * 128 + r] = ii < N ? Xa[ii * d + e] : T(0);
+  }
+  double score = 0.0;
+  for (int k = 0; k < c; ++k) {
+    double q[2];
+    for (int which = 0; which < 2; ++which) {
+      const T* Mk = (which == 0 ? M1 : M2) + (int64_t)k * d * d;
+      __syncthreads();
+      for (int t = tid; t < d * d; t += 128) Ms[t] = Mk[t];
+      __syncthreads();
+      double acc = 0.0;
+      for (int e0 = 0; e0 < d; e0 += 16) {
+        T y[16];
+#pragma unroll
+        for (int ee = 0; ee < 16; ++ee) y[ee] = T(0);
+        for (int f = 0; f < d; ++f) {
+          const T xf = xs[f * 128 + tid];
+#pragma unroll
+          for (int ee = 0; ee < 16; ++ee)
+            if (e0 + ee < d) y[ee] = fma(Ms[f * d + e0 + ee], xf, y[ee]);   // M symmetric
+        }
+#pragma unroll
+        for (int ee = 0; ee < 16; ++ee)
+          if (e0 + ee < d) acc += (double)y[ee] * (double)xs[(e0 + ee) * 128 + tid];
+      }
+      q[which] = acc;
+    }
+    if (row < N) {
+      const double hv = (double)HaT[(int64_t)k * N + row];
+      const double wk = hv * (1.0 - hv);
+      score += wk * q[0] / (1.0 + eta * wk * q[1]);
+    }
+  }
+  double val = -INFINITY;
+  int64_t idx = INT64_MAX;
+  if (row < N && !mask[row - m] && score == score) {
+    val = score;
+    idx = row - m;
+  }
+  // block argmax, lowest index on ties
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, val, o);
+    const int64_t oi = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (ov > val || (ov == val && oi < idx)) {
+      val = ov;
+      idx = oi;
+    }
+  }
+  if ((tid & 31) == 0) {
+    bv[tid >> 5] = val;
+    bi[tid >> 5] = idx;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int w = 1; w < 4; ++w)
+      if (bv[w] > val || (bv[w] == val && bi[w] < idx)) {
+        val = bv[w];
+        idx = bi[w];
+      }
+    part_val[blockIdx.x] = val;
+    part_idx[blockIdx.x] = idx;
+  }
+}
+
+__global__ void k_round_pick(const double* part_val, const int64_t* part_idx, int np,
+                             uint8_t* mask, int32_t* sel, int32_t t, double* score_out) {
+  __shared__ double bv[32];
+  __shared__ int64_t bi[32];
+  double val = -INFINITY;
+  int64_t idx = INT64_MAX;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) {
+    const double v = part_val[i];
+    const int64_t ix = part_idx[i];
+    if (v > val || (v == val && ix < idx)) {
+      val = v;
+      idx = ix;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, val, o);
+    const int64_t oi = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (ov > val || (ov == val && oi < idx)) {
+      val = ov;
+      idx = oi;
+    }
+  }
+  if ((threadIdx.x & 31) == 0) {
+    bv[threadIdx.x >> 5] = val;
+    bi[threadIdx.x >> 5] = idx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+      if (bv[w] > val || (bv[w] == val && bi[w] < idx)) {
+        val = bv[w];
+        idx = bi[w];
+      }
+    if (idx == INT64_MAX) idx = 0;   // nothing selectable (caller validated budget <= n)
+    sel[t] = (int32_t)idx;
+    mask[idx] = 1;
+    *score_out = val;
+  }
+}
+
+template <class T>
+static int32_t round_scores_t(firal_problem* P, const void* M1, const void* M2,
+                              const uint8_t* mask, double eta, double* pv, int64_t* pi, int np) {
+  const int d = P->d;
+  const size_t smem = ((size_t)d * 128 + (size_t)d * d) * sizeof(T);
+  FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_round_scores<T>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  ProfScope ps(P->H->stream, PF_ROUND);
+  count_launch();
+  k_round_scores<T><<<np, 128, smem, P->H->stream>>>(P->Xa.as<T>(), P->HaT.as<T>(), (const T*)M1,
+                                                     (const T*)M2, mask, P->m, P->N, d, P->c, eta,
+                                                     pv, pi);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  return FIRAL_OK;
+}
+
+int32_t round_scores(firal_problem* P, const void* M1, const void* M2, const uint8_t* mask,
+                     double eta, double* pv, int64_t* pi, int np) {
+  if (P->dbl) return round_scores_t<double>(P, M1, M2, mask, eta, pv, pi, np);
+  return round_scores_t<float>(P, M1, M2, mask, eta, pv, pi, np);
+}
+
+int32_t round_pick(const double* pv, const int64_t* pi, int np, uint8_t* mask, int32_t* sel,
+                   int32_t t, double* score_out, cudaStream_t st) {
+  ProfScope ps(st, PF_ROUND);
+  count_launch();
+  k_round_pick<<<1, 256, 0, st>>>(pv, pi, np, mask, sel, t, score_out);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  return FIRAL_OK;
+}
+
+int32_t round_m(bool dbl, const double* Binv, const double* Sig, int c, int d, void* M1, void* M2,
+                cudaStream_t st) {
+  const size_t smem = 2 * (size_t)d * d * sizeof(double);
+  ProfScope ps(st, PF_ROUND);
+  count_launch();
+  if (dbl) {
+    FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_round_m<double>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    k_round_m<double><<<c, threads_for(d), smem, st>>>(Binv, Sig, d, (double*)M1, (double*)M2);
+  } else {
+    FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_round_m<float>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    k_round_m<float><<<c, threads_for(d), smem, st>>>(Binv, Sig, d, (float*)M1, (float*)M2);
+  }
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  return FIRAL_OK;
+}
+
+int32_t round_hupdate(firal_problem* P, double* H, const double* Ho, double invb,
+                      const int32_t* sel, int32_t t) {
+  cudaStream_t st = P->H->stream;
+  ProfScope ps(st, PF_ROUND);
+  count_launch();
+  if (P->dbl)
+    k_round_hupdate<double><<<P->c, 256, 0, st>>>(H, Ho, invb, P->Xa.as<double>(),
+                                                  P->Ha.as<double>(), P->m, P->d, P->c, sel, t);
+  else
+    k_round_hupdate<float><<<P->c, 256, 0, st>>>(H, Ho, invb, P->Xa.as<float>(),
+                                                 P->Ha.as<float>(), P->m, P->d, P->c, sel, t);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  return FIRAL_OK;
+}
+
+int32_t lincomb(double* out, double a, const double* X, double b, const double* Y, double cc,
+                const double* Z, int64_t total, cudaStream_t st) {
+  ProfScope ps(st, PF_ROUND);
+  count_launch();
+  k_axpbypcz<<<(unsigned)((total + 255) / 256 > 4096 ? 4096 : (total + 255) / 256), 256, 0, st>>>(
+      out, a, X, b, Y, cc, Z, total);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  return FIRAL_OK;
+}
+
+int32_t lincomb_nu(double* out, const double* nu, const double* X, double b, const double* Y,
+                   double cc, const double* Z, int64_t total, cudaStream_t st) {
+  ProfScope ps(st, PF_ROUND);
+  count_launch();
+  k_axpbypcz_nu<<<(unsigned)((total + 255) / 256 > 4096 ? 4096 : (total + 255) / 256), 256, 0,
+                  st>>>(out, nu, X, b, Y, cc, Z, total);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  return FIRAL_OK;
+}
+
+}  // namespace firal

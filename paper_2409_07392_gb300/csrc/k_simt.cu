@@ -1,0 +1,1039 @@
+// SIMT (CUDA-core) kernels of the Approx-FIRAL hot path, templated on the vector type
+// (float for FIRAL_FP32, double for FIRAL_FP64).
+//
+// Hessian apply (Lemma 1, Section 3.1).  For weights w over all rows (labelled rows first),
+//   sum_i w_i H_i v = blockdiag_k(S_k) v  -  K^T diag(w) K v,
+//   S_k = sum_i w_i h_ik x_i x_i^T,   K = rows (h_i (x) x_i),
+// because [diag(h_i) - h_i h_i^T] (x) x_i x_i^T = diag(h_i) (x) x_i x_i^T - (h_i (x) x_i)(h_i (x) x_i)^T.
+// The low-rank part is alpha_ij = (h_i (x) x_i) . v_j = sum_k h_ik (x_i . V_j[:,k]) (the
+// alpha of Lemma 1), followed by out_j[k] -= sum_i w_i alpha_ij h_ik x_i.  The diagonal part
+// costs 2 c d^2 s flops per apply once S_k is formed (once per weight vector).
+#include <cuda_bf16.h>
+
+#include "firal_internal.cuh"
+
+
+namespace firal {
+
+// ------------------------------------------------------------------------------------------
+// small helpers
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ double to_double(float v) { return (double)v; }
+__device__ __forceinline__ double to_double(double v) { return v; }
+__device__ __forceinline__ double to_double(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide deterministic sum (fixed tree); result valid in every thread.
+template <class T>
+__device__ T block_sum(T v, T* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  T r = 0;
+  for (int i = 0; i < nw; ++i) r += red[i];
+  __syncthreads();
+  return r;
+}
+
+static inline int grid_for(int64_t total, int threads, int cap = 65535 * 8) {
+  int64_t g = (total + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (int)g;
+}
+
+// ------------------------------------------------------------------------------------------
+// input preparation
+// ------------------------------------------------------------------------------------------
+template <class T, class Tin>
+__global__ void k_copy_rows(T* dst, const Tin* a, int64_t ma, const Tin* b, int64_t nb, int cols) {
+  const int64_t total = (ma + nb) * cols;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = idx / cols;
+    const int col = (int)(idx - r * cols);
+    const double v = r < ma ? to_double(a[r * cols + col]) : to_double(b[(r - ma) * cols + col]);
+    dst[idx] = (T)v;
+  }
+}
+
+template <class T>
+__global__ void k_transpose(T* dst, const T* src, int64_t rows, int cols) {
+  __shared__ T tile[32][33];
+  const int64_t rb = (int64_t)blockIdx.x * 32;
+  const int cb = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int64_t r = rb + i;
+    const int col = cb + threadIdx.x;
+    if (r < rows && col < cols) tile[i][threadIdx.x] = src[r * cols + col];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int col = cb + i;
+    const int64_t r = rb + threadIdx.x;
+    if (r < rows && col < cols) dst[(int64_t)col * rows + r] = tile[threadIdx.x][i];
+  }
+}
+
+template <class T, class Tin>
+static int32_t copy_rows_t(void* dst, const void* a, int64_t ma, const void* b, int64_t nb,
+                           int cols, cudaStream_t st) {
+  const int64_t total = (ma + nb) * cols;
+  ProfScope ps(st, PF_PREP);
+  count_launch();
+  k_copy_rows<T, Tin><<<grid_for(total, 256), 256, 0, st>>>(
+      (T*)dst, (const Tin*)a, ma, (const Tin*)b, nb, cols);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  return FIRAL_OK;
+}
+
+int32_t copy_rows(bool dbl, void* dst, const void* a, int64_t ma, const void* b, int64_t nb,
+                  int cols, int32_t src_dtype, cudaStream_t st) {
+  if (dbl) {
+    if (src_dtype == FIRAL_DT_F64) return copy_rows_t<double, double>(dst, a, ma, b, nb, cols, st);
+    if (src_dtype == FIRAL_DT_F32) return copy_rows_t<double, float>(dst, a, ma, b, nb, cols, st);
+    return copy_rows_t<double, __nv_bfloat16>(dst, a, ma, b, nb, cols, st);
+  }
+  if (src_dtype == FIRAL_DT_F64) return copy_rows_t<float, double>(dst, a, ma, b, nb, cols, st);
+  if (src_dtype == FIRAL_DT_F32) return copy_rows_t<float, float>(dst, a, ma, b, nb, cols, st);
+  return copy_rows_t<float, __nv_bfloat16>(dst, a, ma, b, nb, cols, st);
+}
+
+int32_t transpose(bool dbl, void* dst, const void* src, int64_t rows, int cols, cudaStream_t st) {
+  dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((cols + 31) / 32));
+  dim3 blk(32, 8);
+  ProfScope ps(st, PF_PREP);
+  count_launch();
+  if (dbl)
+    k_transpose<double><<<grid, blk, 0, st>>>((double*)dst, (const double*)src, rows, cols);
+  else
+    k_transpose<float><<<grid, blk, 0, st>>>((float*)dst, (const float*)src, rows, cols);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  return FIRAL_OK;
+}
+
+// weights over all rows: [lab_val] * m, then z (or zconst) on the pool rows
+template <class T>
+__global__ void k_fill_w(T* w, int64_t m, T lab_val, const T* z, T zconst, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m + n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    w[i] = i < m ? lab_val : (z ? z[i - m] : zconst);
+}
+
+int32_t fill_weights(bool dbl, void* w, int64_t m, double lab_val, const void* z, double zconst,
+                     int64_t n, cudaStream_t st) {
+  const int g = grid_for(m + n, 256);
+  ProfScope ps(st, PF_PREP);
+  count_launch();
+  if (dbl)
+    k_fill_w<double><<<g, 256, 0, st>>>((double*)w, m, lab_val, (const double*)z, zconst, n);
+  else
+    k_fill_w<float><<<g, 256, 0, st>>>((float*)w, m, (float)lab_val, (const float*)z,
+                                       (float)zconst, n);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  return FIRAL_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Rademacher probes (Algorithm 2 line 4), SplitMix64 counter rule
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+template <class T>
+__global__ void k_probes(T* V, uint64_t seed, uint64_t t, int s, int64_t D) {
+  const int64_t total = (int64_t)s * D;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t j = (uint64_t)(idx / D), q = (uint64_t)(idx % D);
+    const uint64_t ctr = (t * (uint64_t)s + j) * (uint64_t)D + q;
+    const uint64_t bits = splitmix64(seed ^ splitmix64(ctr));
+    V[idx] = (bits >> 63) ? T(-1) : T(1);
+  }
+}
+
+int32_t probes(bool dbl, void* V, uint64_t seed, int64_t t, int s, int64_t D, cudaStream_t st) {
+  const int g = grid_for((int64_t)s * D, 256);
+  ProfScope ps(st, PF_PROBES);
+  count_launch();
+  if (dbl) k_probes<double><<<g, 256, 0, st>>>((double*)V, seed, (uint64_t)t, s, D);
+  else k_probes<float><<<g, 256, 0, st>>>((float*)V, seed, (uint64_t)t, s, D);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  return FIRAL_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Weighted block sums (eq. 13 and the diagonal part of the apply), partial over row splits:
+//   partS[split][k][e][f] = sum_{i in split} w_i h_ik x_ie x_if
+//   partP[split][k][e][f] = sum_{i in split} w_i h_ik (1 - h_ik) x_ie x_if
+// 256 threads as 16 x 16, each owning a TE x TE tile of the (16 TE)^2 output; G classes per CTA.
+// ------------------------------------------------------------------------------------------
+template <class T, int TE, int G>
+__global__ __launch_bounds__(256) void k_syrk(const T* __restrict__ Xa, const T* __restrict__ HaT,
+                                              const T* __restrict__ w, int64_t N, int d, int c,
+                                              int64_t rows_per_split, T* partS, T* partP) {
+  constexpr int DP = 16 * TE;
+  constexpr int PC = 32;
+  __shared__ __align__(16) T xs[PC][DP];
+  __shared__ T wsS[G][PC];
+  __shared__ T wsP[G][PC];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int k0 = blockIdx.x * G;
+  const int split = blockIdx.y;
+  const int64_t i0 = (int64_t)split * rows_per_split;
+  const int64_t i1 = min(N, i0 + rows_per_split);
+  T accS[G][TE][TE], accP[G][TE][TE];
+#pragma unroll
+  for (int g = 0; g < G; ++g)
+#pragma unroll
+    for (int r = 0; r < TE; ++r)
+#pragma unroll
+      for (int q = 0; q < TE; ++q) accS[g][r][q] = accP[g][r][q] = T(0);
+
+  for (int64_t ib = i0; ib < i1; ib += PC) {
+    for (int idx = threadIdx.x; idx < PC * DP; idx += 256) {
+      const int p = idx / DP, e = idx - p * DP;
+      const int64_t i = ib + p;
+      xs[p][e] = (i < i1 && e < d) ? Xa[i * d + e] : T(0);
+    }
+    for (int idx = threadIdx.x; idx < G * PC; idx += 256) {
+      const int g = idx / PC, p = idx - g * PC;
+      const int64_t i = ib + p;
+      const int k = k0 + g;
+      const T hv = (i < i1 && k < c) ? HaT[(int64_t)k * N + i] : T(0);
+      const T wv = (i < i1) ? w[i] : T(0);
+      wsS[g][p] = wv * hv;
+      wsP[g][p] = wv * hv * (T(1) - hv);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int p = 0; p < PC; ++p) {
+      T a[TE], b[TE];
+#pragma unroll
+      for (int r = 0; r < TE; ++r) {
+        a[r] = xs[p][ty * TE + r];
+        b[r] = xs[p][tx * TE + r];
+      }
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const T sS = wsS[g][p], sP = wsP[g][p];
+#pragma unroll
+        for (int r = 0; r < TE; ++r) {
+          const T as = sS * a[r], ap = sP * a[r];
+#pragma unroll
+          for (int q = 0; q < TE; ++q) {
+            accS[g][r][q] = fma(as, b[q], accS[g][r][q]);
+            accP[g][r][q] = fma(ap, b[q], accP[g][r][q]);
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const int k = k0 + g;
+    if (k >= c) continue;
+#pragma unroll
+    for (int r = 0; r < TE; ++r) {
+      const int e = ty * TE + r;
+      if (e >= d) continue;
+#pragma unroll
+      for (int q = 0; q < TE; ++q) {
+        const int f = tx * TE + q;
+        if (f >= d) continue;
+        const int64_t o = (((int64_t)split * c + k) * d + e) * d + f;
+        if (partS) partS[o] = accS[g][r][q];
+        if (partP) partP[o] = accP[g][r][q];
+      }
+    }
+  }
+}
+
+// out[k][e][f] = sum_split part[split][k][e][f] (+ lam on the diagonal), as double and/or T
+template <class T>
+__global__ void k_syrk_reduce(const T* part, int splits, int64_t per, int d, double lam,
+                              double* out_d, T* out_t) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < per;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int sp = 0; sp < splits; ++sp) acc += (double)part[(int64_t)sp * per + idx];
+    const int64_t ef = idx % ((int64_t)d * d);
+    const int e = (int)(ef / d), f = (int)(ef % d);
+    if (e == f) acc += lam;
+    if (out_d) out_d[idx] = acc;
+    if (out_t) out_t[idx] = (T)acc;
+  }
+}
+
+static int syrk_splits(int64_t N, int cgroups, int sms) {
+  int64_t want = (4LL * sms + cgroups - 1) / cgroups;
+  int64_t by_rows = (N + 65535) / 65536;
+  int64_t s = want > by_rows ? want : by_rows;
+  int64_t max_by_size = (N + 255) / 256;
+  if (s > max_by_size) s = max_by_size;
+  if (s < 1) s = 1;
+  if (s > 4096) s = 4096;
+  return (int)s;
+}
+
+template <class T>
+static int32_t syrk_t(firal_problem* P, const T* w, double lamS, T* outS, double lamP,
+                      double* outP) {
+  cudaStream_t st = P->H->stream;
+  const int d = P->d, c = P->c;
+  const int TE = d <= 32 ? 2 : (d <= 64 ? 4 : 8);
+  const int G = (sizeof(T) == 8 || TE == 8) ? 1 : 4;
+  const int cgroups = (c + G - 1) / G;
+  const int splits = syrk_splits(P->N, cgroups, P->H->sm_count);
+  const int64_t rps = (P->N + splits - 1) / splits;
+  const int64_t per = (int64_t)c * d * d;
+  FIRAL_TRY(P->syrk_part.ensure((size_t)per * splits * 2 * sizeof(T)));
+  T* partS = outS ? P->syrk_part.as<T>() : nullptr;
+  T* partP = outP ? P->syrk_part.as<T>() + per * splits : nullptr;
+  dim3 grid(cgroups, splits);
+  ProfScope ps(st, PF_SYRK);
+  count_launch(1 + (outS ? 1 : 0) + (outP ? 1 : 0));
+  const T* Xa = P->Xa.as<T>();
+  const T* HaT = P->HaT.as<T>();
+#define FIRAL_SYRK(TE_, G_) \
+  k_syrk<T, TE_, G_><<<grid, 256, 0, st>>>(Xa, HaT, w, P->N, d, c, rps, partS, partP)
+  if (TE == 2) { if (G == 4) FIRAL_SYRK(2, 4); else FIRAL_SYRK(2, 1); }
+  else if (TE == 4) { if (G == 4) FIRAL_SYRK(4, 4); else FIRAL_SYRK(4, 1); }
+  else FIRAL_SYRK(8, 1);
+#undef FIRAL_SYRK
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  const int g = grid_for(per, 256, 4096);
+  if (outS) k_syrk_reduce<T><<<g, 256, 0, st>>>(partS, splits, per, d, lamS, nullptr, outS);
+  if (outP) k_syrk_reduce<T><<<g, 256, 0, st>>>(partP, splits, per, d, lamP, outP, nullptr);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  return FIRAL_OK;
+}
+
+int32_t syrk_blocks(firal_problem* P, const void* w, double lamS, void* outS, double lamP,
+                    double* outP) {
+  if (P->dbl) return syrk_t<double>(P, (const double*)w, lamS, (double*)outS, lamP, outP);
+  return syrk_t<float>(P, (const float*)w, lamS, (float*)outS, lamP, outP);
+}
+
+// ------------------------------------------------------------------------------------------
+// Low-rank part of the apply, step 1:  walpha[i][j] = w_i sum_k h_ik (x_i . V_j[:,k]).
+// One thread per row; x_i staged (transposed) in shared memory; probe block in chunks.
+// ------------------------------------------------------------------------------------------
+template <class T, int KC>
+__global__ __launch_bounds__(128) void k_alpha(const T* __restrict__ Xa, const T* __restrict__ HaT,
+                                               const T* __restrict__ w, const T* __restrict__ V,
+                                               int64_t N, int d, int c, int s, int64_t D,
+                                               T* __restrict__ walpha) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* xs = (T*)smem_raw;              // [d][128]
+  T* Vs = xs + (size_t)d * 128;      // [d][KC]
+  T* hs = Vs + (size_t)d * KC;       // [KC][128]
+  const int tid = threadIdx.x;
+  const int64_t i0 = (int64_t)blockIdx.x * 128;
+  const int64_t i = i0 + tid;
+  for (int idx = tid; idx < d * 128; idx += 128) {
+    const int r = idx / d, e = idx - r * d;     // coalesced read of row-major X
+    const int64_t ii = i0 + r;
+    xs[e * 128 + r] = ii < N ? Xa[ii * d + e] : T(0);
+  }
+  const T wi = i < N ? w[i] : T(0);
+  for (int j = 0; j < s; ++j) {
+    T acc = T(0);
+    for (int k0 = 0; k0 < c; k0 += KC) {
+      __syncthreads();
+      for (int idx = tid; idx < KC * d; idx += 128) {
+        const int kk = idx / d, e = idx - kk * d;
+        const int k = k0 + kk;
+        Vs[e * KC + kk] = k < c ? V[(int64_t)j * D + (int64_t)k * d + e] : T(0);
+      }
+      for (int idx = tid; idx < KC * 128; idx += 128) {
+        const int kk = idx / 128, r = idx - kk * 128;
+        const int k = k0 + kk;
+        const int64_t ii = i0 + r;
+        hs[kk * 128 + r] = (k < c && ii < N) ? HaT[(int64_t)k * N + ii] : T(0);
+      }
+      __syncthreads();
+      T gam[KC];
+#pragma unroll
+      for (int kk = 0; kk < KC; ++kk) gam[kk] = T(0);
+      for (int e = 0; e < d; ++e) {
+        const T xe = xs[e * 128 + tid];
+#pragma unroll
+        for (int kk = 0; kk < KC; ++kk) gam[kk] = fma(xe, Vs[e * KC + kk], gam[kk]);
+      }
+#pragma unroll
+      for (int kk = 0; kk < KC; ++kk) acc = fma(hs[kk * 128 + tid], gam[kk], acc);
+    }
+    if (i < N) walpha[i * s + j] = wi * acc;
+  }
+}
+
+// Low-rank part, step 2:  Dpart[split][k][j d + e] = sum_{i in split} h_ik walpha[i][j] x_ie.
+// 64 (j,e) x 64 k tile per CTA; 256 threads, 4 x 4 register tiles; rows in chunks of 32.
+template <class T>
+__global__ __launch_bounds__(256) void k_dterm(const T* __restrict__ Xa, const T* __restrict__ Ha,
+                                               const T* __restrict__ walpha, int64_t N, int d,
+                                               int c, int s, int64_t rows_per_split,
+                                               T* __restrict__ Dpart) {
+  constexpr int PC = 32;
+  __shared__ __align__(16) T Ys[PC][64];
+  __shared__ __align__(16) T Hs[PC][64];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int r0 = blockIdx.x * 64, k0 = blockIdx.y * 64;
+  const int split = blockIdx.z;
+  const int sd = s * d;
+  const int64_t i0 = (int64_t)split * rows_per_split;
+  const int64_t i1 = min(N, i0 + rows_per_split);
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+  for (int64_t ib = i0; ib < i1; ib += PC) {
+    for (int idx = threadIdx.x; idx < PC * 64; idx += 256) {
+      const int p = idx >> 6, col = idx & 63;
+      const int64_t i = ib + p;
+      const int r = r0 + col;
+      T y = T(0);
+      if (i < i1 && r < sd) {
+        const int j = r / d, e = r - j * d;
+        y = walpha[i * s + j] * Xa[i * d + e];
+      }
+      Ys[p][col] = y;
+      const int k = k0 + col;
+      Hs[p][col] = (i < i1 && k < c) ? Ha[i * c + k] : T(0);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int p = 0; p < PC; ++p) {
+      T a[4], b[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        a[q] = Ys[p][ty * 4 + q];
+        b[q] = Hs[p][tx * 4 + q];
+      }
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int y = 0; y < 4; ++y) {
+    const int k = k0 + tx * 4 + y;
+    if (k >= c) continue;
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      const int r = r0 + ty * 4 + x;
+      if (r < sd) Dpart[((int64_t)split * c + k) * sd + r] = acc[x][y];
+    }
+  }
+}
+
+// out_j[k] = S_k V_j[k] - sum_split Dpart[split][k][j d + .]; optional pq[j c + k] = V_j[k].out_j[k]
+template <class T, int JB>
+__global__ void k_combine(const T* __restrict__ S, const T* __restrict__ V,
+                          const T* __restrict__ Dpart, int splits, int d, int c, int s, int64_t D,
+                          T* __restrict__ out, double* pq, const T* __restrict__ vmean) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Ss = (T*)smem_raw;            // d*d
+  T* vs = Ss + (size_t)d * d;      // JB*d
+  __shared__ double red[32];
+  const int k = blockIdx.x;
+  const int j0 = blockIdx.y * JB;
+  const int e = threadIdx.x;
+  for (int idx = threadIdx.x; idx < d * d; idx += blockDim.x) Ss[idx] = S[(int64_t)k * d * d + idx];
+  for (int idx = threadIdx.x; idx < JB * d; idx += blockDim.x) {
+    const int jj = idx / d, f = idx - jj * d;
+    vs[idx] = (j0 + jj < s) ? V[(int64_t)(j0 + jj) * D + (int64_t)k * d + f] -
+                                  (vmean ? vmean[(j0 + jj) * d + f] : T(0))
+                            : T(0);
+  }
+  __syncthreads();
+  const int sd = s * d;
+  for (int jj = 0; jj < JB; ++jj) {
+    const int j = j0 + jj;
+    if (j >= s) break;
+    T q = T(0);
+    if (e < d) {
+      T acc = T(0);
+      for (int f = 0; f < d; ++f) acc = fma(Ss[f * d + e], vs[jj * d + f], acc);   // S symmetric
+      T dsum = T(0);
+      for (int sp = 0; sp < splits; ++sp) dsum += Dpart[((int64_t)sp * c + k) * sd + j * d + e];
+      q = acc - dsum;
+      out[(int64_t)j * D + (int64_t)k * d + e] = q;
+    }
+    if (pq) {
+      const double contrib = e < d ? (double)vs[jj * d + e] * (double)q : 0.0;
+      const double tot = block_sum(contrib, red);
+      if (threadIdx.x == 0) pq[(int64_t)j * c + k] = tot;
+    }
+  }
+}
+
+static int dterm_splits(int tiles, int64_t N, int sms) {
+  int64_t want = (3LL * sms + tiles - 1) / tiles;
+  int64_t max_by_rows = (N + 1023) / 1024;
+  if (want > max_by_rows) want = max_by_rows;
+  if (want < 1) want = 1;
+  if (want > 256) want = 256;
+  return (int)want;
+}
+
+template <class T>
+static int32_t apply_t(firal_problem* P, const T* w, const T* Sblk, const T* V, int s, T* out,
+                       double* pq) {
+  cudaStream_t st = P->H->stream;
+  const int d = P->d, c = P->c;
+  const int64_t N = P->N, D = P->D;
+  FIRAL_TRY(P->walpha.ensure((size_t)N * s * sizeof(T)));
+  constexpr int KC = 16;
+  const size_t smem_a = ((size_t)d * 128 + (size_t)d * KC + (size_t)KC * 128) * sizeof(T);
+  static bool attr_set[2] = {false, false};
+  if (!attr_set[sizeof(T) == 8]) {
+    FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_alpha<T, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        200 * 1024));
+    FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_combine<T, 4>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr_set[sizeof(T) == 8] = true;
+  }
+  {
+  ProfScope ps(st, PF_ALPHA);
+  count_launch();
+  k_alpha<T, KC><<<(unsigned)((N + 127) / 128), 128, smem_a, st>>>(
+      P->Xa.as<T>(), P->HaT.as<T>(), w, V, N, d, c, s, D, P->walpha.as<T>());
+  }
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  const int sd = s * d;
+  const int tr = (sd + 63) / 64, tk = (c + 63) / 64;
+  const int splits = dterm_splits(tr * tk, N, P->H->sm_count);
+  const int64_t rps = (N + splits - 1) / splits;
+  FIRAL_TRY(P->Dpart.ensure((size_t)splits * c * sd * sizeof(T)));
+  {
+  ProfScope ps(st, PF_DTERM);
+  count_launch();
+  k_dterm<T><<<dim3(tr, tk, splits), 256, 0, st>>>(P->Xa.as<T>(), P->Ha.as<T>(),
+                                                   P->walpha.as<T>(), N, d, c, s, rps,
+                                                   P->Dpart.as<T>());
+  }
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  const int threads = ((d + 31) / 32) * 32;
+  const size_t smem_c = ((size_t)d * d + 4 * (size_t)d) * sizeof(T);
+  ProfScope ps(st, PF_COMBINE);
+  count_launch();
+  k_combine<T, 4><<<dim3(c, (s + 3) / 4), threads, smem_c, st>>>(Sblk, V, P->Dpart.as<T>(),
+                                                                  splits, d, c, s, D, out, pq,
+                                                                  nullptr);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  return FIRAL_OK;
+}
+
+int32_t combine_f32(firal_problem* P, const float* Sblk, const float* V, int splits, int s,
+                    float* out, double* pq, const float* vmean) {
+  const int d = P->d, c = P->c;
+  const int threads = ((d + 31) / 32) * 32;
+  const size_t smem_c = ((size_t)d * d + 4 * (size_t)d) * sizeof(float);
+  FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_combine<float, 4>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  ProfScope ps(P->H->stream, PF_COMBINE);
+  count_launch();
+  k_combine<float, 4><<<dim3(c, (s + 3) / 4), threads, smem_c, P->H->stream>>>(
+      Sblk, V, P->Dpart.as<float>(), splits, d, c, s, P->D, out, pq, vmean);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  return FIRAL_OK;
+}
+
+int32_t hessian_apply_simt(firal_problem* P, const void* w, const void* Sblk, const void* V,
+                           int s, void* out, double* pq) {
+  if (P->dbl)
+    return apply_t<double>(P, (const double*)w, (const double*)Sblk, (const double*)V, s,
+                           (double*)out, pq);
+  return apply_t<float>(P, (const float*)w, (const float*)Sblk, (const float*)V, s, (float*)out,
+                        pq);
+}
+
+// ------------------------------------------------------------------------------------------
+// Preconditioned CG (Algorithm 2 lines 5-8), per-column recurrences with FP64 scalars.
+// Partial sums are per (column j, class block k) and reduced in a fixed order.
+// ------------------------------------------------------------------------------------------
+template <class T, int JB>
+__global__ void k_cg_init(const T* __restrict__ Minv, const T* __restrict__ B, int d, int c,
+                          int s, int64_t D, T* X, T* R, T* Z, T* Pd, double* p_rz, double* p_bb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Ms = (T*)smem_raw;           // d*d
+  T* rs = Ms + (size_t)d * d;     // d
+  __shared__ double red[32];
+  const int k = blockIdx.x, e = threadIdx.x;
+  for (int idx = threadIdx.x; idx < d * d; idx += blockDim.x) Ms[idx] = Minv[(int64_t)k * d * d + idx];
+  for (int jj = 0; jj < JB; ++jj) {
+    const int j = blockIdx.y * JB + jj;
+    if (j >= s) break;
+    const int64_t base = (int64_t)j * D + (int64_t)k * d;
+    __syncthreads();
+    T r = T(0);
+    if (e < d) {
+      r = B[base + e];
+      rs[e] = r;
+    }
+    __syncthreads();
+    T z = T(0);
+    if (e < d) {
+      for (int f = 0; f < d; ++f) z = fma(Ms[f * d + e], rs[f], z);
+      X[base + e] = T(0);
+      R[base + e] = r;
+      Z[base + e] = z;
+      Pd[base + e] = z;
+    }
+    const double rz = block_sum(e < d ? (double)r * (double)z : 0.0, red);
+    const double bb = block_sum(e < d ? (double)r * (double)r : 0.0, red);
+    if (threadIdx.x == 0) {
+      p_rz[(int64_t)j * c + k] = rz;
+      p_bb[(int64_t)j * c + k] = bb;
+    }
+  }
+}
+
+// one warp per column: deterministic reduction of c partials
+__device__ __forceinline__ double warp_reduce_partials(const double* p, int c) {
+  const int lane = threadIdx.x & 31;
+  double acc = 0.0;
+  for (int k = lane; k < c; k += 32) acc += p[k];
+  return warp_sum(acc);
+}
+
+__global__ void k_cg_init_cols(const double* p_rz, const double* p_bb, int c, int s, double tol,
+                               int fixed, CGCol* cols) {
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (j >= s) return;
+  const double rz = warp_reduce_partials(p_rz + (int64_t)j * c, c);
+  const double bb = warp_reduce_partials(p_bb + (int64_t)j * c, c);
+  if ((threadIdx.x & 31) == 0) {
+    CGCol cc;
+    cc.rho = rz;
+    cc.bnorm2 = bb;
+    cc.alpha = 0.0;
+    cc.beta = 0.0;
+    cc.relres = bb > 0 ? 1.0 : 0.0;
+    cc.iters = 0;
+    cc.active = (bb > 0.0) && (fixed || !(1.0 <= tol)) ? 1 : 0;
+    cols[j] = cc;
+  }
+}
+
+__global__ void k_cg_alpha(const double* p_pq, int c, int s, CGCol* cols) {
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (j >= s) return;
+  const double pq = warp_reduce_partials(p_pq + (int64_t)j * c, c);
+  if ((threadIdx.x & 31) == 0) {
+    CGCol cc = cols[j];
+    if (cc.active && pq > 0.0 && isfinite(pq)) {
+      cc.alpha = cc.rho / pq;
+    } else {
+      cc.active = 0;
+      cc.alpha = 0.0;
+    }
+    cols[j] = cc;
+  }
+}
+
+template <class T, int JB>
+__global__ void k_cg_update(const T* __restrict__ Minv, int d, int c, int s, int64_t D,
+                            const CGCol* __restrict__ cols, T* X, T* R, const T* Pd,
+                            const T* Q, T* Z, double* p_rr, double* p_rz) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Ms = (T*)smem_raw;
+  T* rs = Ms + (size_t)d * d;
+  __shared__ double red[32];
+  const int k = blockIdx.x, e = threadIdx.x;
+  for (int idx = threadIdx.x; idx < d * d; idx += blockDim.x) Ms[idx] = Minv[(int64_t)k * d * d + idx];
+  for (int jj = 0; jj < JB; ++jj) {
+    const int j = blockIdx.y * JB + jj;
+    if (j >= s) break;
+    const CGCol cc = cols[j];
+    __syncthreads();
+    if (!cc.active) continue;   // uniform over the block
+    const int64_t base = (int64_t)j * D + (int64_t)k * d;
+    const T a = (T)cc.alpha;
+    T r = T(0);
+    if (e < d) {
+      X[base + e] = fma(a, Pd[base + e], X[base + e]);
+      r = fma(-a, Q[base + e], R[base + e]);
+      R[base + e] = r;
+      rs[e] = r;
+    }
+    __syncthreads();
+    T z = T(0);
+    if (e < d) {
+      for (int f = 0; f < d; ++f) z = fma(Ms[f * d + e], rs[f], z);
+      Z[base + e] = z;
+    }
+    const double rr = block_sum(e < d ? (double)r * (double)r : 0.0, red);
+    const double rz = block_sum(e < d ? (double)r * (double)z : 0.0, red);
+    if (threadIdx.x == 0) {
+      p_rr[(int64_t)j * c + k] = rr;
+      p_rz[(int64_t)j * c + k] = rz;
+    }
+  }
+}
+
+__global__ void k_cg_beta(const double* p_rr, const double* p_rz, int c, int s, double tol,
+                          int fixed, CGCol* cols) {
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (j >= s) return;
+  const double rr = warp_reduce_partials(p_rr + (int64_t)j * c, c);
+  const double rz = warp_reduce_partials(p_rz + (int64_t)j * c, c);
+  if ((threadIdx.x & 31) == 0) {
+    CGCol cc = cols[j];
+    if (cc.active) {
+      cc.iters += 1;
+      cc.relres = sqrt(rr / cc.bnorm2);
+      if (!fixed && cc.relres <= tol) {
+        cc.active = 0;
+      } else {
+        cc.beta = rz / cc.rho;
+        cc.rho = rz;
+      }
+    }
+    cols[j] = cc;
+  }
+}
+
+template <class T>
+__global__ void k_cg_pupdate(const CGCol* __restrict__ cols, int s, int64_t D, const T* Z, T* Pd) {
+  const int64_t total = (int64_t)s * D;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(idx / D);
+    const CGCol cc = cols[j];
+    if (cc.active) Pd[idx] = fma((T)cc.beta, Pd[idx], Z[idx]);
+  }
+}
+
+template <class T>
+static int32_t cg_setup_attrs() {
+  static bool done[2] = {false, false};
+  if (!done[sizeof(T) == 8]) {
+    FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_cg_init<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        200 * 1024));
+    FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_cg_update<T, 4>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    done[sizeof(T) == 8] = true;
+  }
+  return FIRAL_OK;
+}
+
+int32_t cg_init(firal_problem* P, const void* B, int s, double tol, int fixed) {
+  cudaStream_t st = P->H->stream;
+  const int d = P->d, c = P->c;
+  const int threads = ((d + 31) / 32) * 32;
+  double* p1 = P->cgpart1.as<double>();
+  double* p2 = P->cgpart2.as<double>();
+  CGCol* cols = P->cgcols.as<CGCol>();
+  ProfScope ps(st, PF_CG);
+  count_launch(2);
+  if (P->dbl) {
+    FIRAL_TRY(cg_setup_attrs<double>());
+    const size_t sm = ((size_t)d * d + d) * sizeof(double);
+    k_cg_init<double, 4><<<dim3(c, (s + 3) / 4), threads, sm, st>>>(
+        P->Minv.as<double>(), (const double*)B, d, c, s, P->D, P->cgX.as<double>(),
+        P->cgR.as<double>(), P->cgZ.as<double>(), P->cgP.as<double>(), p1, p2);
+  } else {
+    FIRAL_TRY(cg_setup_attrs<float>());
+    const size_t sm = ((size_t)d * d + d) * sizeof(float);
+    k_cg_init<float, 4><<<dim3(c, (s + 3) / 4), threads, sm, st>>>(
+        P->Minv.as<float>(), (const float*)B, d, c, s, P->D, P->cgX.as<float>(),
+        P->cgR.as<float>(), P->cgZ.as<float>(), P->cgP.as<float>(), p1, p2);
+  }
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  k_cg_init_cols<<<(s + 3) / 4, 128, 0, st>>>(p1, p2, c, s, tol, fixed, cols);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  return FIRAL_OK;
+}
+
+// one CG iteration after Q = A P with pq partials already in cgpart1
+int32_t cg_iterate_tail(firal_problem* P, int s, double tol, int fixed) {
+  cudaStream_t st = P->H->stream;
+  const int d = P->d, c = P->c;
+  const int threads = ((d + 31) / 32) * 32;
+  double* p1 = P->cgpart1.as<double>();
+  double* p2 = P->cgpart2.as<double>();
+  CGCol* cols = P->cgcols.as<CGCol>();
+  ProfScope ps(st, PF_CG);
+  count_launch(4);
+  k_cg_alpha<<<(s + 3) / 4, 128, 0, st>>>(p1, c, s, cols);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  const int64_t total = (int64_t)s * P->D;
+  if (P->dbl) {
+    const size_t sm = ((size_t)d * d + d) * sizeof(double);
+    k_cg_update<double, 4><<<dim3(c, (s + 3) / 4), threads, sm, st>>>(
+        P->Minv.as<double>(), d, c, s, P->D, cols, P->cgX.as<double>(), P->cgR.as<double>(),
+        P->cgP.as<double>(), P->cgQ.as<double>(), P->cgZ.as<double>(), p1, p2);
+    FIRAL_CUDA_TRY(cudaGetLastError());
+    k_cg_beta<<<(s + 3) / 4, 128, 0, st>>>(p1, p2, c, s, tol, fixed, cols);
+    k_cg_pupdate<double><<<grid_for(total, 256), 256, 0, st>>>(cols, s, P->D, P->cgZ.as<double>(),
+                                                              P->cgP.as<double>());
+  } else {
+    const size_t sm = ((size_t)d * d + d) * sizeof(float);
+    k_cg_update<float, 4><<<dim3(c, (s + 3) / 4), threads, sm, st>>>(
+        P->Minv.as<float>(), d, c, s, P->D, cols, P->cgX.as<float>(), P->cgR.as<float>(),
+        P->cgP.as<float>(), P->cgQ.as<float>(), P->cgZ.as<float>(), p1, p2);
+    FIRAL_CUDA_TRY(cudaGetLastError());
+    k_cg_beta<<<(s + 3) / 4, 128, 0, st>>>(p1, p2, c, s, tol, fixed, cols);
+    k_cg_pupdate<float><<<grid_for(total, 256), 256, 0, st>>>(cols, s, P->D, P->cgZ.as<float>(),
+                                                             P->cgP.as<float>());
+  }
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  return FIRAL_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Per-point quadratic forms (eq. 11):  g_i = -(scale/s) sum_j a_j^T H_i b_j for pool rows,
+//   a_j^T H_i b_j = sum_k h_ik (x_i.A_j[k]) (x_i.B_j[k]) - (sum_k h_ik x_i.A_j[k])(sum_k h_ik x_i.B_j[k]).
+// ------------------------------------------------------------------------------------------
+template <class T, int KC>
+__global__ __launch_bounds__(128) void k_quad(const T* __restrict__ Xa, const T* __restrict__ HaT,
+                                              const T* __restrict__ A, const T* __restrict__ B,
+                                              int64_t m, int64_t N, int d, int c, int s, int64_t D,
+                                              double scale, T* __restrict__ g) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* xs = (T*)smem_raw;               // [d][128]
+  T* As = xs + (size_t)d * 128;       // [d][KC]
+  T* Bs = As + (size_t)d * KC;        // [d][KC]
+  T* hs = Bs + (size_t)d * KC;        // [KC][128]
+  const int tid = threadIdx.x;
+  const int64_t i0 = m + (int64_t)blockIdx.x * 128;
+  const int64_t i = i0 + tid;
+  for (int idx = tid; idx < d * 128; idx += 128) {
+    const int r = idx / d, e = idx - r * d;
+    const int64_t ii = i0 + r;
+    xs[e * 128 + r] = ii < N ? Xa[ii * d + e] : T(0);
+  }
+  double q = 0.0;
+  for (int j = 0; j < s; ++j) {
+    T s1 = T(0), sa = T(0), sb = T(0);
+    for (int k0 = 0; k0 < c; k0 += KC) {
+      __syncthreads();
+      for (int idx = tid; idx < KC * d; idx += 128) {
+        const int kk = idx / d, e = idx - kk * d;
+        const int k = k0 + kk;
+        const int64_t src = (int64_t)j * D + (int64_t)k * d + e;
+        As[e * KC + kk] = k < c ? A[src] : T(0);
+        Bs[e * KC + kk] = k < c ? B[src] : T(0);
+      }
+      for (int idx = tid; idx < KC * 128; idx += 128) {
+        const int kk = idx / 128, r = idx - kk * 128;
+        const int k = k0 + kk;
+        const int64_t ii = i0 + r;
+        hs[kk * 128 + r] = (k < c && ii < N) ? HaT[(int64_t)k * N + ii] : T(0);
+      }
+      __syncthreads();
+      T ga[KC], gb[KC];
+#pragma unroll
+      for (int kk = 0; kk < KC; ++kk) ga[kk] = gb[kk] = T(0);
+      for (int e = 0; e < d; ++e) {
+        const T xe = xs[e * 128 + tid];
+#pragma unroll
+        for (int kk = 0; kk < KC; ++kk) {
+          ga[kk] = fma(xe, As[e * KC + kk], ga[kk]);
+          gb[kk] = fma(xe, Bs[e * KC + kk], gb[kk]);
+        }
+      }
+#pragma unroll
+      for (int kk = 0; kk < KC; ++kk) {
+        const T hv = hs[kk * 128 + tid];
+        const T ha = hv * ga[kk];
+        s1 = fma(ha, gb[kk], s1);
+        sa += ha;
+        sb = fma(hv, gb[kk], sb);
+      }
+    }
+    q += (double)s1 - (double)sa * (double)sb;
+  }
+  if (i < N) g[i - m] = (T)(-scale / s * q);
+}
+
+int32_t quad_forms_simt(firal_problem* P, const void* A, const void* B, int s, double scale,
+                        void* g) {
+  cudaStream_t st = P->H->stream;
+  const int d = P->d, c = P->c;
+  constexpr int KC = 16;
+  const unsigned grid = (unsigned)((P->n + 127) / 128);
+  ProfScope ps(st, PF_QUAD);
+  count_launch();
+  if (P->dbl) {
+    const size_t sm = ((size_t)d * 128 + 2 * (size_t)d * KC + KC * 128) * sizeof(double);
+    FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_quad<double, KC>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    k_quad<double, KC><<<grid, 128, sm, st>>>(P->Xa.as<double>(), P->HaT.as<double>(),
+                                              (const double*)A, (const double*)B, P->m, P->N, d,
+                                              c, s, P->D, scale, (double*)g);
+  } else {
+    const size_t sm = ((size_t)d * 128 + 2 * (size_t)d * KC + KC * 128) * sizeof(float);
+    FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_quad<float, KC>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    k_quad<float, KC><<<grid, 128, sm, st>>>(P->Xa.as<float>(), P->HaT.as<float>(),
+                                             (const float*)A, (const float*)B, P->m, P->N, d, c,
+                                             s, P->D, scale, (float*)g);
+  }
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  return FIRAL_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Dot products over probe blocks: out = (1/s) sum over all elements a*b (the f^ estimate)
+// ------------------------------------------------------------------------------------------
+template <class T>
+__global__ void k_dot_partial(const T* a, const T* b, int64_t total, double* part) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x)
+    acc += (double)a[idx] * (double)b[idx];
+  const double tot = block_sum(acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+__global__ void k_sum_partials(const double* part, int np, double scale, double* out) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) acc += part[i];
+  const double tot = block_sum(acc, red);
+  if (threadIdx.x == 0) *out = tot * scale;
+}
+
+int32_t dot_scaled(bool dbl, const void* a, const void* b, int64_t total, double scale,
+                   double* part /* >= 256 */, double* out, cudaStream_t st) {
+  const int np = 256;
+  ProfScope ps(st, PF_DOT);
+  count_launch(2);
+  if (dbl) k_dot_partial<double><<<np, 256, 0, st>>>((const double*)a, (const double*)b, total, part);
+  else k_dot_partial<float><<<np, 256, 0, st>>>((const float*)a, (const float*)b, total, part);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  k_sum_partials<<<1, 256, 0, st>>>(part, np, scale, out);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  return FIRAL_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Mirror-descent update (Algorithm 2 lines 10-11) on the budget simplex.
+// red layout: [0..255] max partials, [256..511] sum partials, [512] gmax, [513] zmax
+// ------------------------------------------------------------------------------------------
+template <class T>
+__global__ void k_absmax_partial(const T* g, int64_t n, double* part) {
+  __shared__ double red[32];
+  double mx = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = fabs((double)g[i]);
+    mx = (v > mx || v != v) ? v : mx;
+  }
+  // block max (fixed tree)
+  for (int o = 16; o > 0; o >>= 1) {
+    const double other = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = (other > mx || other != other) ? other : mx;
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r = (red[i] > r || red[i] != red[i]) ? red[i] : r;
+    part[blockIdx.x] = r;
+  }
+}
+
+template <class T>
+__global__ void k_md_exp(T* z, const T* g, int64_t n, double beta0, double* red) {
+  __shared__ double sh[32];
+  __shared__ double s_beta;
+  if (threadIdx.x == 0) {
+    double mx = 0.0;
+    for (int i = 0; i < 256; ++i) mx = (red[i] > mx || red[i] != red[i]) ? red[i] : mx;
+    s_beta = mx > 0.0 ? beta0 / mx : 0.0;
+    if (blockIdx.x == 0) red[512] = mx;
+  }
+  __syncthreads();
+  const double beta = s_beta;
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const T zn = (T)((double)z[i] * exp(-beta * (double)g[i]));
+    z[i] = zn;
+    acc += (double)zn;
+  }
+  const double tot = block_sum(acc, sh);
+  if (threadIdx.x == 0) red[256 + blockIdx.x] = tot;
+}
+
+template <class T>
+__global__ void k_md_scale(T* z, int64_t n, double budget, double* red) {
+  __shared__ double s_scale;
+  __shared__ double sh[32];
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int i = 0; i < 256; ++i) tot += red[256 + i];
+    s_scale = budget / tot;
+  }
+  __syncthreads();
+  const double sc = s_scale;
+  double mx = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const T v = (T)((double)z[i] * sc);
+    z[i] = v;
+    mx = (double)v > mx ? (double)v : mx;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double other = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = other > mx ? other : mx;
+  }
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r = sh[i] > r ? sh[i] : r;
+    red[768 + blockIdx.x] = r;
+  }
+}
+
+__global__ void k_md_zmax(double* red) {
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int i = 0; i < 256; ++i) r = red[768 + i] > r ? red[768 + i] : r;
+    red[513] = r;
+  }
+}
+
+int32_t md_step_simt(bool dbl, void* z, const void* g, int64_t n, double budget, double beta0,
+                     double* red, cudaStream_t st) {
+  ProfScope ps(st, PF_MD);
+  count_launch(4);
+  if (dbl) {
+    k_absmax_partial<double><<<256, 256, 0, st>>>((const double*)g, n, red);
+    k_md_exp<double><<<256, 256, 0, st>>>((double*)z, (const double*)g, n, beta0, red);
+    k_md_scale<double><<<256, 256, 0, st>>>((double*)z, n, budget, red);
+  } else {
+    k_absmax_partial<float><<<256, 256, 0, st>>>((const float*)g, n, red);
+    k_md_exp<float><<<256, 256, 0, st>>>((float*)z, (const float*)g, n, beta0, red);
+    k_md_scale<float><<<256, 256, 0, st>>>((float*)z, n, budget, red);
+  }
+  k_md_zmax<<<1, 32, 0, st>>>(red);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  return FIRAL_OK;
+}
+
+}  // namespace firal

@@ -1,0 +1,103 @@
+"""Mixed-precision (bf16 tcgen05) path vs the FP64 oracle, through the C-ABI (needs a GPU).
+
+Error budget of one Hessian apply: the diagonal part is FP32 on CUDA cores; the low-rank
+part rounds h and x (x exact when stored bf16) and walpha x to bf16 with independent
+per-element errors (2^-9) that average over the point sums, and feeds the CG direction as
+bf16 hi + lo (2^-17).  The relative error in norm shrinks like 1/sqrt(n); the bound asserted is 6 * 2^-9 / sqrt(n).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import approx  # noqa: E402
+from paper_2409_07392_gb300.synth import make_problem  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_2409_07392_gb300 import api as a, build
+    build.build()
+    return a
+
+
+@pytest.fixture(scope="module")
+def handle(api):
+    return api.Handle()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def relerr(a, b):
+    return np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b)
+
+
+def make(api, handle, p):
+    X = dev(p.X).to(torch.bfloat16) if p.x_bf16 else dev(p.X)
+    Xo = dev(p.Xo).to(torch.bfloat16) if p.x_bf16 else dev(p.Xo)
+    return api.Problem(handle, X, dev(p.h), Xo, dev(p.ho), p.lam, precision="mixed")
+
+
+MIXED_SHAPES = [(300, 20, 10, 3), (1000, 50, 10, 5), (517, 64, 37, 4), (260, 128, 4, 3),
+                (2049, 16, 17, 8), (2049, 33, 17, 20), (2049, 16, 17, 20), (4100, 64, 130, 16)]
+
+
+@pytest.mark.parametrize("n,d,c,s", MIXED_SHAPES)
+def test_mixed_hessian_apply(api, handle, n, d, c, s):
+    p = make_problem(n, d, c, seed=n + c, x_dtype="bf16", h_dtype="float32", m_o=c)
+    prob = make(api, handle, p)
+    rng = np.random.default_rng(0)
+    V = rng.standard_normal((d * c, s))
+    z = rng.uniform(0.1, 1.0, n)
+    ops = approx.Operators(p)
+    ref_sig = ops.sigma_apply(z, V)
+    ref_hp = ops.hp_apply(V)
+    got_sig = prob.hessian_apply(dev(V.T.astype(np.float32)), dev(z.astype(np.float32)),
+                                 op=0).cpu().numpy().T
+    got_hp = prob.hessian_apply(dev(V.T.astype(np.float32)), op=1).cpu().numpy().T
+    for name, g in (("sigma", got_sig), ("H_p", got_hp)):
+        bad = np.argwhere(~np.isfinite(g))
+        if bad.size:
+            q, j = bad[:, 0], bad[:, 1]
+            print(f"{name}: {bad.shape[0]} non-finite; probes {sorted(set(j.tolist()))[:20]} "
+                  f"classes {sorted(set((q // d).tolist()))[:20]} "
+                  f"features {sorted(set((q % d).tolist()))[:20]}")
+    e1, e2 = relerr(got_sig, ref_sig), relerr(got_hp, ref_hp)
+    print(f"mixed apply n={n} d={d} c={c} s={s}: sigma {e1:.2e}  H_p {e2:.2e}")
+    # per-element bf16 rounding (2^-9) of h and of walpha x averages over the n-point sums
+    tol = 6.0 * 2.0 ** -9 / np.sqrt(n) + 2e-6
+    assert e1 < tol and e2 < tol
+
+
+def test_mixed_apply_keeps_the_softmax_null_space(api, handle):
+    """Sigma_z (1_c (x) u) = lambda (1_c (x) u) and H_p (1_c (x) u) = 0 (rows of h sum to 1)."""
+    p = make_problem(3000, 32, 12, seed=5, x_dtype="bf16", h_dtype="float64", m_o=12)
+    p.h = p.h.astype(np.float32)
+    p.ho = p.ho.astype(np.float32)
+    prob = make(api, handle, p)
+    u = np.random.default_rng(1).standard_normal((3, 32))
+    V = np.concatenate([np.tile(u[j], 12)[None] for j in range(3)]).astype(np.float32)
+    z = np.full(p.n, 0.01, np.float32)
+    sig = prob.hessian_apply(dev(V), dev(z), op=0).cpu().numpy()
+    hp = prob.hessian_apply(dev(V), op=1).cpu().numpy()
+    assert relerr(sig, p.lam * V.astype(np.float64)) < 1e-4
+    assert np.abs(hp).max() < 1e-6 * np.abs(V).max()
+
+
+def test_mixed_relax_fhat_and_z_vs_exact_solve_oracle(api, handle):
+    """Mixed Relax (CG to 1e-5) vs the oracle with dense solves and the same probes:
+    f^ and z within 1e-3 relative (the stated accuracy target)."""
+    p = make_problem(20000, 16, 10, seed=3, x_dtype="bf16", h_dtype="float32")
+    prob = make(api, handle, p)
+    b, s, T = 20.0, 8, 3
+    z = torch.full((p.n,), b / p.n, dtype=torch.float32, device="cuda")
+    opts = prob.relax_opts(s=s, T=T, tol=1e-5, maxit=300, seed=4)
+    fh = [prob.relax_step(opts, t, b, z)["fhat"] for t in range(T)]
+    z_ref, info = approx.relax(p, b, s=s, T=T, seed=4, solve="direct")
+    ef, ez = relerr(fh, np.array(info["fhat"])), relerr(z.cpu().numpy(), z_ref)
+    print(f"mixed relax: fhat {ef:.2e}  z {ez:.2e}")
+    assert ef < 1e-3 and ez < 1e-3
