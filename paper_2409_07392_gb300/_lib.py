@@ -85,6 +85,8 @@ SIGNATURES = [
                             c_void_p, POINTER(c_int32), POINTER(c_double)]),
     ("firal_quad_forms", c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_double, c_void_p]),
     ("firal_md_step", c_int32, [c_void_p, c_void_p, c_void_p, c_double, c_double]),
+    ("firal_md_step_static", c_int32, [c_void_p, c_void_p, c_int64, c_int32, c_double, c_double,
+                                       c_void_p]),
     ("firal_objective_fwd", c_int32, [c_void_p, c_void_p, c_uint64, c_int32, c_int32,
                                       POINTER(FiralCGOpts), POINTER(c_double), c_void_p,
                                       c_void_p]),
