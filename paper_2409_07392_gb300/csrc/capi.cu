@@ -106,6 +106,8 @@ int32_t tc_hessian_apply(firal_problem* P, const void* w, const void* Sblk, cons
                          void* out, double* pq, double lam_null);
 int32_t tc_quad_forms(firal_problem* P, const void* A, const void* B, int s, double scale,
                       void* g);
+int32_t tc_syrk_blocks(firal_problem* P, const void* w, double lamS, void* outS, double lamP,
+                       double* outP);
 bool tc_available();
 
 }  // namespace firal
@@ -151,6 +153,13 @@ int32_t quad(firal_problem* P, const void* A, const void* B, int s, double scale
   return quad_forms_simt(P, A, B, s, scale, g);
 }
 
+// weighted block sums of the Relax operators (tensor cores for FIRAL_MIXED_BF16)
+int32_t blocks(firal_problem* P, const void* w, double lamS, void* outS, double lamP,
+               double* outP) {
+  if (P->prec == FIRAL_MIXED_BF16) return tc_syrk_blocks(P, w, lamS, outS, lamP, outP);
+  return syrk_blocks(P, w, lamS, outS, lamP, outP);
+}
+
 // w_sig = [1 (labelled), z (pool)]; S_sig = diag-part operator with lambda; optional blocks
 int32_t setup_sigma(firal_problem* P, const void* z, bool want_precond) {
   cudaStream_t st = P->H->stream;
@@ -158,8 +167,8 @@ int32_t setup_sigma(firal_problem* P, const void* z, bool want_precond) {
     FIRAL_CUDA_TRY(cudaMemcpyAsync((char*)P->w_sig.p + P->m * vsize(P), z, P->n * vsize(P),
                                    cudaMemcpyDeviceToDevice, st));
   }
-  FIRAL_TRY(syrk_blocks(P, P->w_sig.p, P->lambda, P->S_sig.p, P->lambda,
-                        want_precond ? P->Pblk.as<double>() : nullptr));
+  FIRAL_TRY(blocks(P, P->w_sig.p, P->lambda, P->S_sig.p, P->lambda,
+                   want_precond ? P->Pblk.as<double>() : nullptr));
   if (want_precond)
     FIRAL_TRY(chol_inv(P->dbl, P->Pblk.as<double>(), P->c, P->d, P->Minv.p, nullptr, nullptr,
                        not_spd_flag(P->H), st));
@@ -168,7 +177,7 @@ int32_t setup_sigma(firal_problem* P, const void* z, bool want_precond) {
 
 int32_t ensure_sp(firal_problem* P) {
   if (P->S_p_ready) return FIRAL_OK;
-  FIRAL_TRY(syrk_blocks(P, P->w_p.p, 0.0, P->S_p.p, 0.0, nullptr));
+  FIRAL_TRY(blocks(P, P->w_p.p, 0.0, P->S_p.p, 0.0, nullptr));
   P->S_p_ready = true;
   return FIRAL_OK;
 }
@@ -594,7 +603,8 @@ int32_t firal_problem_destroy(firal_problem* P) {
   for (DBuf* b : {&P->Xa, &P->Ha, &P->HaT, &P->w_sig, &P->w_p, &P->S_p, &P->S_sig, &P->Pblk,
                   &P->Minv, &P->HoBlk, &P->walpha, &P->Dpart, &P->syrk_part, &P->cgX, &P->cgR,
                   &P->cgP, &P->cgQ, &P->cgZ, &P->cgcols, &P->cgpart1, &P->cgpart2, &P->V, &P->U,
-                  &P->W, &P->HU, &P->g, &P->red, &P->zsave, &P->Xb, &P->Hb, &P->HbT, &P->Pb, &P->vmean, &P->qmean})
+                  &P->W, &P->HU, &P->g, &P->red, &P->zsave, &P->Xb, &P->Hb, &P->HbT, &P->Pb, &P->vmean, &P->qmean, &P->XwT, &P->gq_ab,
+                  &P->gq_m, &P->gq_part})
     b->release();
   delete P;
   return FIRAL_OK;

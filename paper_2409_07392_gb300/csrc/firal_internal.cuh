@@ -122,6 +122,8 @@ struct firal_problem {
   // tensor-core layout (FIRAL_MIXED_BF16): bf16 X (N x dp), bf16 h (Np x cp), its transpose
   firal::DBuf Xb, Hb, HbT, Pb;   // Pb: bf16 (hi/lo) operand of the probe block
   firal::DBuf vmean, qmean;      // class means of the probe block / of the raw apply (s x d)
+  firal::DBuf XwT;               // bf16 (h - bf16(h))^T, the low part of h for the block sums
+  firal::DBuf gq_ab, gq_m, gq_part;  // tensor-core quadratic forms: [A;B], M~ pairs, partials
   int32_t dp = 0, cp = 0;
   int64_t Np = 0;
 };
@@ -136,6 +138,8 @@ int32_t fill_weights(bool dbl, void* w, int64_t m, double lab_val, const void* z
 int32_t probes(bool dbl, void* V, uint64_t seed, int64_t t, int s, int64_t D, cudaStream_t st);
 int32_t syrk_blocks(firal_problem* P, const void* w, double lamS, void* outS, double lamP,
                     double* outP);
+int32_t syrk_reduce_f32(firal_problem* P, const float* partS, const float* partP, int splits,
+                        double lamS, float* outS, double lamP, double* outP);
 int32_t hessian_apply_simt(firal_problem* P, const void* w, const void* Sblk, const void* V,
                            int s, void* out, double* pq);
 int32_t combine_f32(firal_problem* P, const float* Sblk, const float* V, int splits, int s,

@@ -322,6 +322,19 @@ static int32_t syrk_t(firal_problem* P, const T* w, double lamS, T* outS, double
   return FIRAL_OK;
 }
 
+int32_t syrk_reduce_f32(firal_problem* P, const float* partS, const float* partP, int splits,
+                        double lamS, float* outS, double lamP, double* outP) {
+  cudaStream_t st = P->H->stream;
+  const int64_t per = (int64_t)P->c * P->d * P->d;
+  const int g = grid_for(per, 256, 4096);
+  ProfScope ps(st, PF_SYRK);
+  count_launch((outS ? 1 : 0) + (outP ? 1 : 0));
+  if (outS) k_syrk_reduce<float><<<g, 256, 0, st>>>(partS, splits, per, P->d, lamS, nullptr, outS);
+  if (outP) k_syrk_reduce<float><<<g, 256, 0, st>>>(partP, splits, per, P->d, lamP, outP, nullptr);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  return FIRAL_OK;
+}
+
 int32_t syrk_blocks(firal_problem* P, const void* w, double lamS, void* outS, double lamP,
                     double* outP) {
   if (P->dbl) return syrk_t<double>(P, (const double*)w, lamS, (double*)outS, lamP, outP);

@@ -171,6 +171,17 @@ __global__ void k_project(float* out, const float* qmean, const float* vmean, co
   }
 }
 
+// (e, e') of pair index p in the row-major triangle e <= e' < d
+__device__ __forceinline__ void pair_of(int p, int d, int& e, int& e2) {
+  int ee = 0, start = 0;
+  while (ee < d && start + (d - ee) <= p) {
+    start += d - ee;
+    ++ee;
+  }
+  e = ee;
+  e2 = ee + (p - start);
+}
+
 // ------------------------------------------------------------------------------------------
 // alpha-GEMM
 // ------------------------------------------------------------------------------------------
@@ -179,30 +190,35 @@ constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
 constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int SMEM_QUAD(int dp) { return SMEM + dp * BM * 2; }
 }  // namespace alpha_cfg
 
-struct TcCtl {
+struct TcCtl {   // < 256 bytes
   uint64_t full[4], empty[4], yfull[4], tfull[2], tempty[2], drain;
   uint32_t tmem_base;
   int abort_w;
 };
+static_assert(sizeof(TcCtl) <= 256, "control block must fit in 256 bytes");
 
 __device__ __forceinline__ void raise_abort(TcCtl* ctl, int32_t* err, int code) {
   ctl->abort_w = 1;
   atomicExch(err, code);
 }
 
-template <int DP>
+template <int DP, int MODE>
 __global__ void __launch_bounds__(256, 1)
     k_tc_alpha(const __grid_constant__ CUtensorMap mapH, const __grid_constant__ CUtensorMap mapP,
                const bf16* __restrict__ Xb, const float* __restrict__ w, bf16* __restrict__ aT,
-               int64_t N, int64_t Np, int s, int kblocks, int n_mt, int n_nt, int32_t* err) {
+               float* __restrict__ out32, int64_t N, int64_t Np, int s, int kblocks, int n_mt,
+               int n_nt, int npairs, int d, int32_t* err) {
   using namespace alpha_cfg;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   TcCtl* ctl = (TcCtl*)(sm + STAGES * STAGE_BYTES);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int PPN = BN / (2 * DP);   // probes per N tile
+  // MODE 2: the thread's x row, transposed (column = thread) so reads are conflict-free
+  bf16* xsT = (bf16*)(sm + STAGES * STAGE_BYTES + 256);   // after the control block
   if (threadIdx.x == 0) {
     for (int i = 0; i < STAGES; ++i) {
       mbar_init(&ctl->full[i], 1);
@@ -314,9 +330,38 @@ __global__ void __launch_bounds__(256, 1)
       tc_fence_after();
       const int64_t row = (int64_t)mt * BM + q * 32 + lane;
       const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + acc * BN;
-      const float wi = row < N ? w[row] : 0.0f;
+      const float wi = (MODE == 0) ? (row < N ? w[row] : 0.0f) : 1.0f;
+      if (MODE == 2) {
+        // term1 partial: sum over the 128 pairs of this tile of x_e x_e' (T_hi + T_lo)
+        const int tcol = q * 32 + lane;
+        const bf16* xr = Xb + row * DP;
+        for (int e = 0; e < DP; ++e) xsT[e * BM + tcol] = xr[e];
+        float acc1 = 0.0f;
+        int e = 0, e2 = 0;
+        const int p0 = nt * (BN / 2);
+        if (p0 < npairs) pair_of(p0, d, e, e2);
+        float xe = __bfloat162float(xsT[e * BM + tcol]);
 #pragma unroll 1
-      for (int jj = 0; jj < PPN; ++jj) {
+        for (int cc = 0; cc < BN / 2; cc += 32) {
+          float vh[32], vl[32];
+          tmem_ld32(tbase + cc, vh);
+          tmem_ld32(tbase + BN / 2 + cc, vl);
+#pragma unroll
+          for (int t = 0; t < 32; ++t) {
+            if (p0 + cc + t < npairs) {
+              acc1 = fmaf(xe * __bfloat162float(xsT[e2 * BM + tcol]), vh[t] + vl[t], acc1);
+              if (++e2 == d) {
+                ++e;
+                e2 = e;
+                xe = e < DP ? __bfloat162float(xsT[(e < DP ? e : 0) * BM + tcol]) : 0.0f;
+              }
+            }
+          }
+        }
+        if (row < N) out32[(int64_t)nt * Np + row] = acc1;
+      }
+#pragma unroll 1
+      for (int jj = 0; jj < (MODE == 2 ? 0 : PPN); ++jj) {
         const int j = nt * PPN + jj;
         float sum = 0.0f;
 #pragma unroll 1
@@ -348,7 +393,10 @@ __global__ void __launch_bounds__(256, 1)
               if (t < cw) sum = fmaf(xv[t], v[t], sum);
           }
         }
-        if (row < N && j < s) aT[(int64_t)j * Np + row] = __float2bfloat16_rn(wi * sum);
+        if (row < N && j < s) {
+          if (MODE == 0) aT[(int64_t)j * Np + row] = __float2bfloat16_rn(wi * sum);
+          else out32[(int64_t)j * Np + row] = sum;
+        }
       }
       tc_fence_before();
       __syncwarp();
@@ -525,19 +573,33 @@ __global__ void __launch_bounds__(256, 1)
         unsigned char* Y = st + A_BYTES;
         const unsigned char* XT = st + A_BYTES + Y_BYTES;
         const unsigned char* AT = XT + XT_MAX;
-        // chunk = (row r of Y, 8 consecutive points c8); 8 threads share a row
-        for (int ch = bw * 32 + lane; ch < BN * 8; ch += NBUILD * 32) {
-          const int r = ch >> 3, c8 = ch & 7;
-          const int jl = r / DP, e = r - jl * DP;
-          const uint4 xv = *reinterpret_cast<const uint4*>(XT + e * (BK * 2) + c8 * 16);
-          const uint4 av = *reinterpret_cast<const uint4*>(AT + jl * (BK * 2) + c8 * 16);
-          uint4 yv;
-          const __nv_bfloat162* x2 = reinterpret_cast<const __nv_bfloat162*>(&xv);
-          const __nv_bfloat162* a2 = reinterpret_cast<const __nv_bfloat162*>(&av);
-          __nv_bfloat162* y2 = reinterpret_cast<__nv_bfloat162*>(&yv);
+        // item = (feature e, 8 consecutive points c8).  A thread keeps one c8 (NBUILD*32 is a
+        // multiple of 8), holds walpha of its 8 points for every probe of the tile in registers,
+        // reads each x chunk once and writes one Y chunk per probe: rows r = jl*DP + e.  The 8
+        // threads of a quarter-warp share e, so loads and (swizzled) stores cover one 128-byte
+        // row each and are conflict-free.
+        {
+          const int tid_b = bw * 32 + lane;
+          const int c8 = tid_b & 7;
+          uint4 av[PPN];
 #pragma unroll
-          for (int h = 0; h < 4; ++h) y2[h] = __hmul2(x2[h], a2[h]);
-          *reinterpret_cast<uint4*>(Y + r * 128 + ((c8 ^ (r & 7)) << 4)) = yv;
+          for (int jl = 0; jl < PPN; ++jl)
+            av[jl] = *reinterpret_cast<const uint4*>(AT + jl * (BK * 2) + c8 * 16);
+          for (int it = tid_b; it < DP * 8; it += NBUILD * 32) {
+            const int e = it >> 3;
+            const uint4 xv = *reinterpret_cast<const uint4*>(XT + e * (BK * 2) + c8 * 16);
+            const __nv_bfloat162* x2 = reinterpret_cast<const __nv_bfloat162*>(&xv);
+#pragma unroll
+            for (int jl = 0; jl < PPN; ++jl) {
+              uint4 yv;
+              const __nv_bfloat162* a2 = reinterpret_cast<const __nv_bfloat162*>(&av[jl]);
+              __nv_bfloat162* y2 = reinterpret_cast<__nv_bfloat162*>(&yv);
+#pragma unroll
+              for (int h = 0; h < 4; ++h) y2[h] = __hmul2(x2[h], a2[h]);
+              const int r = jl * DP + e;
+              *reinterpret_cast<uint4*>(Y + r * 128 + ((c8 ^ (r & 7)) << 4)) = yv;
+            }
+          }
         }
         fence_async_smem();
         __syncwarp();
@@ -587,6 +649,309 @@ __global__ void __launch_bounds__(256, 1)
 }
 
 // ------------------------------------------------------------------------------------------
+// Block sums on tensor cores (eq. 13 and the diagonal-part operator), split over points:
+//   S[k,(e,e')] = sum_i h_ik (w_i x_ie x_ie'),   P[k,(e,e')] = sum_i h_ik (1 - h_ik) (w_i x_ie x_ie')
+// for the symmetric pairs e <= e' < d (row-major triangle).  S is the dominant term of every
+// Sigma_z apply, so it is carried to ~f32 accuracy with three bf16 products,
+//   S ~ H_hi Z_hi + H_lo Z_hi + H_hi Z_lo,   Z = w x_e x_e' (f32, split into hi + lo),
+// while P (the preconditioner) uses H_hi(1 - H_hi) Z_hi.  A = H^T tiles by TMA; Z and A_P are
+// built in shared memory.  Unit = (128 classes, 128 pairs, point range).
+// ------------------------------------------------------------------------------------------
+namespace s_cfg {
+constexpr int BM = 128, BN = 128, BK = 64;
+constexpr int A_BYTES = BM * BK * 2;
+constexpr int Z_BYTES = BN * BK * 2;
+constexpr int NBUILD = 6;
+template <int DP> struct Stage {
+  static constexpr int XT_BYTES = DP * BK * 2;
+  static constexpr int RAW = 3 * A_BYTES + 2 * Z_BYTES + XT_BYTES;
+  static constexpr int BYTES = (RAW + 1023) / 1024 * 1024;
+  static constexpr int STAGES = (3 * BYTES + 2048 <= 227 * 1024) ? 3 : 2;
+  static constexpr int SMEM = STAGES * BYTES + 1024 + 256;
+};
+}  // namespace s_cfg
+
+template <int DP>
+__global__ void __launch_bounds__(256, 1)
+    k_tc_syrk(const __grid_constant__ CUtensorMap mapHT, const __grid_constant__ CUtensorMap mapHL,
+              const __grid_constant__ CUtensorMap mapXT, const float* __restrict__ w,
+              float* __restrict__ partS, float* __restrict__ partP, int64_t N, int c, int d,
+              int npairs, int n_mt, int n_nt, int splits, int64_t kb_per_split, int64_t kb_total,
+              int32_t* err) {
+  using namespace s_cfg;
+  using St = Stage<DP>;
+  constexpr int STAGES = St::STAGES;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  TcCtl* ctl = (TcCtl*)(sm + STAGES * St::BYTES);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr uint32_t TX = 2 * A_BYTES + St::XT_BYTES;
+  // stage layout: A_hi | A_lo | A_P | Z_hi | Z_lo | x^T
+  constexpr int OFF_AL = A_BYTES, OFF_AP = 2 * A_BYTES, OFF_ZH = 3 * A_BYTES,
+                OFF_ZL = 3 * A_BYTES + Z_BYTES, OFF_XT = 3 * A_BYTES + 2 * Z_BYTES;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < STAGES; ++i) {
+      mbar_init(&ctl->full[i], 1);
+      mbar_init(&ctl->empty[i], 1);
+      mbar_init(&ctl->yfull[i], NBUILD);
+    }
+    mbar_init(&ctl->tfull[0], 1);
+    mbar_init(&ctl->tempty[0], 4);
+    mbar_init(&ctl->drain, 1);
+    ctl->abort_w = 0;
+    mbar_fence_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(&ctl->tmem_base, 256);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = ctl->tmem_base;
+  volatile int* abort_w = &ctl->abort_w;
+  const int nunits = n_mt * n_nt * splits;
+  auto unit_range = [&](int u, int& mt, int& nt, int& sp, int64_t& kb0, int64_t& kb1) {
+    mt = u % n_mt;
+    const int rest = u / n_mt;
+    nt = rest % n_nt;
+    sp = rest / n_nt;
+    kb0 = (int64_t)sp * kb_per_split;
+    kb1 = kb0 + kb_per_split < kb_total ? kb0 + kb_per_split : kb_total;
+  };
+
+  if (warp == 0 && lane == 0) {
+    tma_prefetch(&mapHT);
+    tma_prefetch(&mapHL);
+    tma_prefetch(&mapXT);
+    int stage = 0;
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; u < nunits && ok && !*abort_w; u += gridDim.x) {
+      int mt, nt, sp;
+      int64_t kb0, kb1;
+      unit_range(u, mt, nt, sp, kb0, kb1);
+      for (int64_t kb = kb0; kb < kb1; ++kb) {
+        if (!mbar_wait(&ctl->empty[stage], phase ^ 1, abort_w)) {
+          raise_abort(ctl, err, 21);
+          ok = false;
+          break;
+        }
+        unsigned char* st = sm + stage * St::BYTES;
+        mbar_expect_tx(&ctl->full[stage], TX);
+        const int x = (int)(kb * BK);
+        tma_load_2d(st, &mapHT, &ctl->full[stage], x, mt * BM);
+        tma_load_2d(st + OFF_AL, &mapHL, &ctl->full[stage], x, mt * BM);
+        tma_load_2d(st + OFF_XT, &mapXT, &ctl->full[stage], x, 0);
+        if (++stage == STAGES) {
+          stage = 0;
+          phase ^= 1;
+        }
+      }
+    }
+    for (int i = 0; i < STAGES; ++i) {
+      if (!mbar_wait(&ctl->empty[stage], phase ^ 1, abort_w)) break;
+      if (++stage == STAGES) {
+        stage = 0;
+        phase ^= 1;
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    constexpr uint32_t idesc = idesc_bf16_f32(BM, BN);
+    int stage = 0;
+    uint32_t phase = 0;
+    uint32_t acc_phase = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; u < nunits && ok && !*abort_w; u += gridDim.x) {
+      int mt, nt, sp;
+      int64_t kb0, kb1;
+      unit_range(u, mt, nt, sp, kb0, kb1);
+      if (!mbar_wait(&ctl->tempty[0], acc_phase ^ 1, abort_w)) {
+        raise_abort(ctl, err, 22);
+        break;
+      }
+      tc_fence_after();
+      for (int64_t kb = kb0; kb < kb1; ++kb) {
+        if (!mbar_wait(&ctl->yfull[stage], phase, abort_w)) {
+          raise_abort(ctl, err, 23);
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t ah = smem_u32(sm + stage * St::BYTES);
+        const uint32_t al = ah + OFF_AL, ap = ah + OFF_AP, zh = ah + OFF_ZH, zl = ah + OFF_ZL;
+#pragma unroll
+        for (int k = 0; k < BK / 16; ++k) {
+          const uint32_t acc = (kb != kb0) || k != 0;
+          const uint64_t dzh = sdesc_sw128(zh + k * 32);
+          umma_bf16(tmem, sdesc_sw128(ah + k * 32), dzh, idesc, acc);
+          umma_bf16(tmem, sdesc_sw128(al + k * 32), dzh, idesc, 1u);
+          umma_bf16(tmem, sdesc_sw128(ah + k * 32), sdesc_sw128(zl + k * 32), idesc, 1u);
+          umma_bf16(tmem + BN, sdesc_sw128(ap + k * 32), dzh, idesc, acc);
+        }
+        umma_commit(&ctl->empty[stage]);
+        if (++stage == STAGES) {
+          stage = 0;
+          phase ^= 1;
+        }
+      }
+      if (!ok) break;
+      umma_commit(&ctl->tfull[0]);
+      acc_phase ^= 1;
+    }
+    umma_commit(&ctl->drain);
+    mbar_wait_drain(&ctl->drain, 0);
+  } else if (warp >= 2) {
+    const int bw = warp - 2;
+    const int tid_b = bw * 32 + lane;
+    const int c8 = tid_b & 7;            // fixed point chunk of this thread
+    int stage = 0;
+    uint32_t phase = 0;
+    uint32_t acc_phase = 0;
+    bool ok = true;
+    const __nv_bfloat162 one2 = __floats2bfloat162_rn(1.0f, 1.0f);
+    constexpr int RPT = (BN + NBUILD * 4 - 1) / (NBUILD * 4);   // Z rows per thread
+    for (int u = blockIdx.x; u < nunits && ok && !*abort_w; u += gridDim.x) {
+      int mt, nt, sp;
+      int64_t kb0, kb1;
+      unit_range(u, mt, nt, sp, kb0, kb1);
+      // pairs of the rows this thread builds (fixed for the unit); -1 = padding row
+      int pe[RPT], pe2[RPT];
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) {
+        const int r = (tid_b >> 3) + q * (NBUILD * 4);
+        const int p = nt * BN + r;
+        pe[q] = -1;
+        pe2[q] = 0;
+        if (r < BN && p < npairs) pair_of(p, d, pe[q], pe2[q]);
+      }
+      for (int64_t kb = kb0; kb < kb1; ++kb) {
+        if (!mbar_wait(&ctl->full[stage], phase, abort_w)) {
+          raise_abort(ctl, err, 24);
+          ok = false;
+          break;
+        }
+        unsigned char* st = sm + stage * St::BYTES;
+        // A_P = A_hi (1 - A_hi), elementwise on the swizzled tile
+        for (int ch = tid_b; ch < BM * 8; ch += NBUILD * 32) {
+          const uint4 hv = *reinterpret_cast<const uint4*>(st + ch * 16);
+          uint4 pv;
+          const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&hv);
+          __nv_bfloat162* p2 = reinterpret_cast<__nv_bfloat162*>(&pv);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) p2[q] = __hmul2(h2[q], __hsub2(one2, h2[q]));
+          *reinterpret_cast<uint4*>(st + OFF_AP + ch * 16) = pv;
+        }
+        // weights of this thread's 8 points (zero beyond N)
+        float wv[8];
+        const int64_t i0 = kb * BK + c8 * 8;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) wv[q] = (i0 + q < N) ? w[i0 + q] : 0.0f;
+        const unsigned char* XT = st + OFF_XT;
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+          const int r = (tid_b >> 3) + q * (NBUILD * 4);
+          if (r >= BN) break;
+          uint4 zh4 = make_uint4(0, 0, 0, 0), zl4 = make_uint4(0, 0, 0, 0);
+          if (pe[q] >= 0) {
+            const uint4 xa = *reinterpret_cast<const uint4*>(XT + pe[q] * (BK * 2) + c8 * 16);
+            const uint4 xb = *reinterpret_cast<const uint4*>(XT + pe2[q] * (BK * 2) + c8 * 16);
+            const __nv_bfloat162* a2 = reinterpret_cast<const __nv_bfloat162*>(&xa);
+            const __nv_bfloat162* b2 = reinterpret_cast<const __nv_bfloat162*>(&xb);
+            __nv_bfloat162* h2 = reinterpret_cast<__nv_bfloat162*>(&zh4);
+            __nv_bfloat162* l2 = reinterpret_cast<__nv_bfloat162*>(&zl4);
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+              const float2 fa = __bfloat1622float2(a2[h]);
+              const float2 fb = __bfloat1622float2(b2[h]);
+              const float z0 = wv[2 * h] * fa.x * fb.x, z1 = wv[2 * h + 1] * fa.y * fb.y;
+              const __nv_bfloat162 hi = __floats2bfloat162_rn(z0, z1);
+              const float2 fh = __bfloat1622float2(hi);
+              h2[h] = hi;
+              l2[h] = __floats2bfloat162_rn(z0 - fh.x, z1 - fh.y);
+            }
+          }
+          const uint32_t off = (uint32_t)r * 128u + ((uint32_t)(c8 ^ (r & 7)) << 4);
+          *reinterpret_cast<uint4*>(st + OFF_ZH + off) = zh4;
+          *reinterpret_cast<uint4*>(st + OFF_ZL + off) = zl4;
+        }
+        fence_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ctl->yfull[stage]);
+        if (++stage == STAGES) {
+          stage = 0;
+          phase ^= 1;
+        }
+      }
+      if (!ok) break;
+      if (warp >= 4) {
+        const int q = warp & 3;
+        if (!mbar_wait(&ctl->tfull[0], acc_phase, abort_w)) {
+          raise_abort(ctl, err, 25);
+          break;
+        }
+        tc_fence_after();
+        const int k = mt * BM + q * 32 + lane;
+        for (int which = 0; which < 2; ++which) {
+          float* out = (which == 0 ? partS : partP) + ((int64_t)sp * c + k) * d * d;
+          for (int cc = 0; cc < BN; cc += 32) {
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + which * BN + cc, v);
+            if (k < c) {
+              int e = 0, e2 = 0;
+              const int p0 = nt * BN + cc;
+              if (p0 < npairs) pair_of(p0, d, e, e2);
+#pragma unroll
+              for (int t = 0; t < 32; ++t) {
+                if (p0 + t < npairs) {
+                  out[e * d + e2] = v[t];
+                  out[e2 * d + e] = v[t];
+                  if (++e2 == d) {
+                    ++e;
+                    e2 = e;
+                  }
+                }
+              }
+            }
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ctl->tempty[0]);
+      }
+      acc_phase ^= 1;
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc(tmem, 256);
+  }
+}
+
+// h_lo^T = bf16(h - bf16(h)), transposed and padded like HbT
+__global__ void k_h_lo_T(bf16* HlT, const float* Ha, int64_t N, int c, int64_t Np, int cp) {
+  __shared__ float tile[32][33];
+  const int64_t rb = (int64_t)blockIdx.x * 32;
+  const int cb = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int64_t r = rb + i;
+    const int col = cb + threadIdx.x;
+    tile[i][threadIdx.x] = (r < N && col < c) ? Ha[r * c + col] : 0.0f;
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int col = cb + i;
+    const int64_t r = rb + threadIdx.x;
+    if (r < Np && col < cp) {
+      const float v = tile[threadIdx.x][i];
+      HlT[(int64_t)col * Np + r] = __float2bfloat16_rn(v - __bfloat162float(__float2bfloat16_rn(v)));
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
 // host side
 // ------------------------------------------------------------------------------------------
 bool tc_available() { return true; }
@@ -619,6 +984,11 @@ int32_t tc_prepare(firal_problem* P) {
                      st>>>(P->HbT.as<bf16>(), P->Hb.as<bf16>(), Np, P->cp);
   k_transpose_bf16<<<dim3((unsigned)(Np / 32), (unsigned)((P->dp + 31) / 32)), dim3(32, 8), 0,
                      st>>>(P->Xb.as<bf16>() + tot_x, P->Xb.as<bf16>(), Np, P->dp);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  FIRAL_TRY(P->XwT.ensure((size_t)Np * P->cp * 2));
+  k_h_lo_T<<<dim3((unsigned)(Np / 32), (unsigned)((P->cp + 31) / 32)), dim3(32, 8), 0, st>>>(
+      P->XwT.as<bf16>(), P->Ha.as<float>(), P->N, P->c, Np, P->cp);
+  count_launch();
   FIRAL_CUDA_TRY(cudaGetLastError());
   return FIRAL_OK;
 }
@@ -659,8 +1029,8 @@ static int32_t tc_apply_t(firal_problem* P, const float* w, const float* Sblk, c
   static bool attr[4] = {false, false, false, false};
   const int ai = DP == 16 ? 0 : DP == 32 ? 1 : DP == 64 ? 2 : 3;
   if (!attr[ai]) {
-    FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tc_alpha<DP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        SMEM));
+    FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tc_alpha<DP, 0>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
     FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tc_dterm<DP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         d_cfg::SMEM));
     attr[ai] = true;
@@ -668,8 +1038,9 @@ static int32_t tc_apply_t(firal_problem* P, const float* w, const float* Sblk, c
   {
   ProfScope ps(st, PF_ALPHA);
   count_launch();
-  k_tc_alpha<DP><<<grid, 256, SMEM, st>>>(mH, mP, P->Xb.as<bf16>(), w, P->walpha.as<bf16>(),
-                                          P->N, Np, s, cp / BK, n_mt, n_nt, tc_error_word(P));
+  k_tc_alpha<DP, 0><<<grid, 256, SMEM, st>>>(mH, mP, P->Xb.as<bf16>(), w, P->walpha.as<bf16>(),
+                                             nullptr, P->N, Np, s, cp / BK, n_mt, n_nt, 0, P->d,
+                                             tc_error_word(P));
   }
   FIRAL_CUDA_TRY(cudaGetLastError());
   // D-GEMM
@@ -710,6 +1081,196 @@ static int32_t tc_apply_t(firal_problem* P, const float* w, const float* Sblk, c
   }
 }
 
+template <int DP>
+static int32_t tc_syrk_t(firal_problem* P, const float* w, double lamS, float* outS, double lamP,
+                         double* outP) {
+  using namespace s_cfg;
+  using St = Stage<DP>;
+  cudaStream_t st = P->H->stream;
+  const int64_t Np = P->Np;
+  const int cp = P->cp, c = P->c, d = P->d;
+  const int sms = P->H->sm_count;
+  const int npairs = d * (d + 1) / 2;
+  const int n_mt = cp / BM + (cp % BM ? 1 : 0);
+  const int n_nt = (npairs + BN - 1) / BN;
+  const int64_t kb_total = Np / BK;
+  const int tiles = n_mt * n_nt;
+  int splits = (int)std::max<int64_t>(1, std::min<int64_t>((4LL * sms + tiles - 1) / tiles,
+                                                          kb_total / 8 > 0 ? kb_total / 8 : 1));
+  const int64_t kbps = (kb_total + splits - 1) / splits;
+  splits = (int)((kb_total + kbps - 1) / kbps);
+  const int64_t per = (int64_t)c * d * d;
+  FIRAL_TRY(P->syrk_part.ensure((size_t)per * splits * 2 * sizeof(float)));
+  float* pS = P->syrk_part.as<float>();
+  float* pP = pS + per * splits;
+  CUtensorMap mHT, mHL, mXT;
+  FIRAL_TRY(make_map(&mHT, P->HbT.p, cp, Np, BM, BK, true));
+  FIRAL_TRY(make_map(&mHL, P->XwT.p, cp, Np, BM, BK, true));
+  FIRAL_TRY(make_map(&mXT, P->Xb.as<bf16>() + Np * DP, DP, Np, DP, BK, false));
+  static bool attr[4] = {false, false, false, false};
+  const int ai = DP == 16 ? 0 : DP == 32 ? 1 : DP == 64 ? 2 : 3;
+  if (!attr[ai]) {
+    FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tc_syrk<DP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        St::SMEM));
+    attr[ai] = true;
+  }
+  const int units = tiles * splits;
+  {
+    ProfScope ps(st, PF_SYRK);
+    count_launch();
+    k_tc_syrk<DP><<<std::min(units, sms), 256, St::SMEM, st>>>(
+        mHT, mHL, mXT, w, pS, pP, P->N, c, d, npairs, n_mt, n_nt, splits, kbps, kb_total,
+        tc_error_word(P));
+  }
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  return syrk_reduce_f32(P, pS, pP, splits, lamS, outS, lamP, outP);
+}
+
+int32_t tc_syrk_blocks(firal_problem* P, const void* w, double lamS, void* outS, double lamP,
+                       double* outP) {
+  switch (P->dp) {
+    case 16: return tc_syrk_t<16>(P, (const float*)w, lamS, (float*)outS, lamP, outP);
+    case 32: return tc_syrk_t<32>(P, (const float*)w, lamS, (float*)outS, lamP, outP);
+    case 64: return tc_syrk_t<64>(P, (const float*)w, lamS, (float*)outS, lamP, outP);
+    default: return tc_syrk_t<128>(P, (const float*)w, lamS, (float*)outS, lamP, outP);
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Per-point quadratic forms on tensor cores (eq. 11):
+//   q_i = sum_j a_j^T H_i b_j = sum_k h_ik x_i^T M_k x_i - sum_j (h_i.a_ij)(h_i.b_ij),
+//   M_k = sum_j A_j[:,k] B_j[:,k]^T,  a_ijk = x_i.A_j[:,k],  b_ijk = x_i.B_j[:,k].
+// A and B are first projected onto N^perp (class means removed): H_i vanishes on N, so the
+// value is unchanged, and bf16 rounding of h cannot act on the near-null directions.
+// term1 = rowdot(x (x) x, H . M~) with the symmetric part of M_k (alpha-GEMM, MODE 2);
+// term2 from the alpha-GEMM on [A; B] with f32 output (MODE 1).
+// ------------------------------------------------------------------------------------------
+__global__ void k_build_mpairs(bf16* Mt, const float* A, const float* B, const float* meanA,
+                               const float* meanB, int s, int c, int d, int64_t D, int cp,
+                               int npairs) {
+  extern __shared__ float Msh[];   // d*d
+  const int k = blockIdx.x;
+  for (int t = threadIdx.x; t < d * d; t += blockDim.x) {
+    const int e = t / d, e2 = t - e * d;
+    double acc = 0.0;
+    for (int j = 0; j < s; ++j) {
+      const float a = A[(int64_t)j * D + (int64_t)k * d + e] - meanA[j * d + e];
+      const float b = B[(int64_t)j * D + (int64_t)k * d + e2] - meanB[j * d + e2];
+      acc += (double)a * (double)b;
+    }
+    Msh[t] = (float)acc;
+  }
+  __syncthreads();
+  for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
+    int e, e2;
+    pair_of(p, d, e, e2);
+    const float v = e == e2 ? Msh[e * d + e] : Msh[e * d + e2] + Msh[e2 * d + e];
+    const bf16 hi = __float2bfloat16_rn(v);
+    const bf16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+    const int nt = p / 128, pl = p - nt * 128;
+    Mt[((int64_t)nt * 256 + pl) * cp + k] = hi;
+    Mt[((int64_t)nt * 256 + 128 + pl) * cp + k] = lo;
+  }
+}
+
+__global__ void k_quad_combine(const float* part1, int n_nt1, const float* a32, int s,
+                               int64_t m, int64_t N, int64_t Np, double scale, float* g) {
+  for (int64_t i = m + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double t1 = 0.0, t2 = 0.0;
+    for (int nt = 0; nt < n_nt1; ++nt) t1 += part1[(int64_t)nt * Np + i];
+    for (int j = 0; j < s; ++j)
+      t2 += (double)a32[(int64_t)j * Np + i] * (double)a32[(int64_t)(s + j) * Np + i];
+    g[i - m] = (float)(-scale / s * (t1 - t2));
+  }
+}
+
+template <int DP>
+static int32_t tc_quad_t(firal_problem* P, const float* A, const float* B, int s, double scale,
+                         float* g) {
+  using namespace alpha_cfg;
+  cudaStream_t st = P->H->stream;
+  const int64_t Np = P->Np;
+  const int cp = P->cp, c = P->c, d = P->d;
+  const int64_t D = P->D;
+  const int sms = P->H->sm_count;
+  const int mthreads = (d + 31) / 32 * 32;
+  // probe block [A; B] (2s columns) and its class means
+  FIRAL_TRY(P->gq_ab.ensure((size_t)2 * s * D * sizeof(float)));
+  float* AB = P->gq_ab.as<float>();
+  FIRAL_CUDA_TRY(cudaMemcpyAsync(AB, A, (size_t)s * D * 4, cudaMemcpyDeviceToDevice, st));
+  FIRAL_CUDA_TRY(cudaMemcpyAsync(AB + (size_t)s * D, B, (size_t)s * D * 4,
+                                 cudaMemcpyDeviceToDevice, st));
+  FIRAL_TRY(P->vmean.ensure((size_t)2 * s * d * sizeof(float)));
+  ProfScope ps(st, PF_QUAD);
+  count_launch(1);
+  k_class_mean<<<2 * s, mthreads, 0, st>>>(AB, 2 * s, c, d, D, P->vmean.as<float>());
+  // term 1: M~ pairs (hi | lo per 128-pair tile) and the quadratic alpha-GEMM
+  const int npairs = d * (d + 1) / 2;
+  const int n_nt1 = (npairs + 127) / 128;
+  const int64_t mrows = (int64_t)n_nt1 * 256;
+  FIRAL_TRY(P->gq_m.ensure((size_t)mrows * cp * 2));
+  FIRAL_CUDA_TRY(cudaMemsetAsync(P->gq_m.p, 0, (size_t)mrows * cp * 2, st));
+  FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_build_mpairs, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      128 * 128 * 4));
+  count_launch(1);
+  k_build_mpairs<<<c, 256, (size_t)d * d * sizeof(float), st>>>(
+      P->gq_m.as<bf16>(), AB, AB + (size_t)s * D, P->vmean.as<float>(),
+      P->vmean.as<float>() + s * d, s, c, d, D, cp, npairs);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  FIRAL_TRY(P->gq_part.ensure((size_t)(n_nt1 + 2 * s) * Np * sizeof(float)));
+  float* part1 = P->gq_part.as<float>();
+  float* a32 = part1 + (size_t)n_nt1 * Np;
+  static bool attr[4] = {false, false, false, false};
+  const int ai = DP == 16 ? 0 : DP == 32 ? 1 : DP == 64 ? 2 : 3;
+  if (!attr[ai]) {
+    FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tc_alpha<DP, 1>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
+    FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tc_alpha<DP, 2>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        SMEM_QUAD(DP)));
+    attr[ai] = true;
+  }
+  const int n_mt = (int)(Np / BM);
+  {
+    CUtensorMap mH, mM;
+    FIRAL_TRY(make_map(&mH, P->Hb.p, Np, cp, BM, BK, true));
+    FIRAL_TRY(make_map(&mM, P->gq_m.p, mrows, cp, BN, BK, true));
+    count_launch(1);
+    k_tc_alpha<DP, 2><<<std::min(n_mt * n_nt1, sms), 256, SMEM_QUAD(DP), st>>>(
+        mH, mM, P->Xb.as<bf16>(), nullptr, nullptr, part1, P->N, Np, 0, cp / BK, n_mt, n_nt1,
+        npairs, d, tc_error_word(P));
+    FIRAL_CUDA_TRY(cudaGetLastError());
+  }
+  // term 2: h.a_ij and h.b_ij for the projected [A; B]
+  {
+    const int s2 = 2 * s;
+    const int64_t prow = (int64_t)s2 * 2 * DP;
+    const int64_t prow_p = (prow + BN - 1) / BN * BN;
+    FIRAL_TRY(P->Pb.ensure((size_t)prow_p * cp * 2));
+    if (prow_p > prow)
+      FIRAL_CUDA_TRY(cudaMemsetAsync(P->Pb.as<bf16>() + prow * cp, 0, (prow_p - prow) * cp * 2, st));
+    count_launch(1);
+    k_split_probes<<<dim3((unsigned)(cp + 31) / 32, DP / 32 > 0 ? DP / 32 : 1, s2), dim3(32, 8), 0,
+                     st>>>(P->Pb.as<bf16>(), AB, P->vmean.as<float>(), s2, c, d, DP, cp, D);
+    FIRAL_CUDA_TRY(cudaGetLastError());
+    CUtensorMap mH, mP;
+    FIRAL_TRY(make_map(&mH, P->Hb.p, Np, cp, BM, BK, true));
+    FIRAL_TRY(make_map(&mP, P->Pb.p, prow_p, cp, BN, BK, true));
+    const int n_nt2 = (int)(prow_p / BN);
+    count_launch(1);
+    k_tc_alpha<DP, 1><<<std::min(n_mt * n_nt2, sms), 256, SMEM, st>>>(
+        mH, mP, P->Xb.as<bf16>(), nullptr, nullptr, a32, P->N, Np, s2, cp / BK, n_mt, n_nt2, 0,
+        d, tc_error_word(P));
+    FIRAL_CUDA_TRY(cudaGetLastError());
+  }
+  count_launch(1);
+  k_quad_combine<<<(unsigned)std::min<int64_t>((P->n + 255) / 256, 4096), 256, 0, st>>>(
+      part1, n_nt1, a32, s, P->m, P->N, Np, scale, g);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  return FIRAL_OK;
+}
+
 int32_t tc_hessian_apply(firal_problem* P, const void* w, const void* Sblk, const void* V, int s,
                          void* out, double* pq, double lam_null) {
   switch (P->dp) {
@@ -722,7 +1283,15 @@ int32_t tc_hessian_apply(firal_problem* P, const void* w, const void* Sblk, cons
 
 int32_t tc_quad_forms(firal_problem* P, const void* A, const void* B, int s, double scale,
                       void* g) {
-  return quad_forms_simt(P, A, B, s, scale, g);
+  const float* a = (const float*)A;
+  const float* b = (const float*)B;
+  float* gg = (float*)g;
+  switch (P->dp) {
+    case 16: return tc_quad_t<16>(P, a, b, s, scale, gg);
+    case 32: return tc_quad_t<32>(P, a, b, s, scale, gg);
+    case 64: return tc_quad_t<64>(P, a, b, s, scale, gg);
+    default: return tc_quad_t<128>(P, a, b, s, scale, gg);
+  }
 }
 
 }  // namespace firal

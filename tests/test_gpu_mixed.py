@@ -101,3 +101,24 @@ def test_mixed_relax_fhat_and_z_vs_exact_solve_oracle(api, handle):
     ef, ez = relerr(fh, np.array(info["fhat"])), relerr(z.cpu().numpy(), z_ref)
     print(f"mixed relax: fhat {ef:.2e}  z {ez:.2e}")
     assert ef < 1e-3 and ez < 1e-3
+
+
+@pytest.mark.parametrize("n,d,c,s", [(3000, 20, 10, 4), (2049, 64, 37, 8), (1500, 128, 5, 3),
+                                     (4100, 16, 130, 16)])
+def test_mixed_quad_forms(api, handle, n, d, c, s):
+    """Tensor-core per-point quadratic forms (eq. 11) vs the oracle; a large N-component added
+    to A must not change the result (H_i vanishes on N = {1_c (x) u})."""
+    p = make_problem(n, d, c, seed=n + 7, x_dtype="bf16", h_dtype="float64", m_o=c)
+    p.h = p.h.astype(np.float32).astype(np.float64)
+    prob = make(api, handle, p)
+    rng = np.random.default_rng(3)
+    A, B = rng.standard_normal((d * c, s)), rng.standard_normal((d * c, s))
+    ref = -approx.quad_forms(p.X, p.h, A, B)
+    got = prob.quad_forms(dev(A.T.astype(np.float32)), dev(B.T.astype(np.float32))).cpu().numpy()
+    e1 = relerr(got, ref)
+    u = rng.standard_normal((d, s))
+    An = A + 1e3 * np.tile(u, (c, 1))
+    got_n = prob.quad_forms(dev(An.T.astype(np.float32)), dev(B.T.astype(np.float32))).cpu().numpy()
+    e2 = relerr(got_n, ref)
+    print(f"mixed quad n={n} d={d} c={c} s={s}: {e1:.2e}  with N-component {e2:.2e}")
+    assert e1 < 2e-3 and e2 < 2e-3
