@@ -152,6 +152,21 @@ def algorithmic_flops(kind, cfg, n_all, s):
     return None
 
 
+def dram_traffic(kind, n_rows_padded):
+    """DRAM bytes per launch of a kernel class from the committed ncu capture, scaled by the
+    padded row count; None when the kernel source changed since the capture."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))
+        src = open(os.path.join(ROOT, rec["source"]), "rb").read()
+        if hashlib.sha256(src).hexdigest()[:16] != rec["source_sha256_16"]:
+            return None
+        k = rec["kernels"].get(kind)
+        return None if k is None else k["dram_bytes_per_padded_row"] * n_rows_padded
+    except Exception:
+        return None
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
@@ -261,7 +276,7 @@ def run_ours(args):
     ms_ev = e0.elapsed_time(e1)
     ms_max = max_over_ranks(ms_ev, world)
     nk = _lib.FiralStepStats  # noqa: F841
-    ncls = 12
+    ncls = 13
     ms_k = (ctypes_arr := __import__("ctypes").c_double * ncls)()
     calls_k = (__import__("ctypes").c_int64 * ncls)()
     lib.firal_profile_read(ms_k, calls_k, ncls)
@@ -282,8 +297,10 @@ def run_ours(args):
         achieved = fl / (per_launch_ms / 1000.0) / 1e12
         tensor = args.precision == "mixed" and top in ("apply_alpha", "apply_dterm")
         peak = pk["bf16_tflops_sustained"] if tensor else FP32_ALU_PEAK_TFLOPS
+        n_pad = (n_all + 127) // 128 * 128
         roof = {"kernel": top, "bound": "tensor" if tensor else "alu", "achieved": achieved,
-                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": dram_traffic(top, n_pad) if tensor else None,
                 "peak_source": (f"{pk_src} bf16 sustained" if tensor else
                                 "derived FP32 FMA peak: 152 SMs x 128 lanes x 2 x 2.07 GHz")}
     # the Hessian apply as a whole (alpha + D + combine), the operation the metric counts

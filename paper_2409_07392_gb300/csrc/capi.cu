@@ -1,5 +1,6 @@
 // C-ABI entry points (include/firal.h) and host orchestration of the Relax and Round steps.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -17,6 +18,16 @@ const std::string& last_detail() { return g_detail; }
 
 // ---------------------------------------------------------------------------- profiling
 std::atomic<long long> g_launches{0};
+
+// FIRAL_SPLITS=p forces p point-range partitions in the split-K reductions (row sharding of the
+// pool, Section 3.3); used by the virtual-shard tests.
+int forced_splits() {
+  static int v = [] {
+    const char* e = std::getenv("FIRAL_SPLITS");
+    return e ? std::atoi(e) : 0;
+  }();
+  return v;
+}
 
 namespace {
 struct Pending {
@@ -537,7 +548,8 @@ int32_t firal_profile_read(double* ms_out, int64_t* calls_out, int32_t count) {
 const char* firal_profile_name(int32_t id) {
   static const char* names[PF_COUNT] = {"prep", "probes", "syrk_blocks", "chol_inv",
                                         "apply_alpha", "apply_dterm", "apply_combine", "cg_vec",
-                                        "quad_forms", "md_step", "dot", "round"};
+                                        "quad_forms", "md_step", "dot", "round",
+                                        "apply_split"};
   return (id >= 0 && id < PF_COUNT) ? names[id] : "unknown";
 }
 

@@ -73,10 +73,12 @@ namespace firal {
 // Kernel-class timers and the launch counter (see firal_profile* in firal.h).
 enum ProfId {
   PF_PREP = 0, PF_PROBES, PF_SYRK, PF_CHOL, PF_ALPHA, PF_DTERM, PF_COMBINE, PF_CG, PF_QUAD,
-  PF_MD, PF_DOT, PF_ROUND, PF_COUNT
+  PF_MD, PF_DOT, PF_ROUND, PF_SPLIT, PF_COUNT
 };
 extern std::atomic<long long> g_launches;
 inline void count_launch(int n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+// Split-count override for tests of the row partition (0 = automatic).
+int forced_splits();
 struct ProfScope {
   ProfScope(cudaStream_t st, int id);
   ~ProfScope();

@@ -533,7 +533,8 @@ static int32_t apply_t(firal_problem* P, const T* w, const T* Sblk, const T* V, 
   FIRAL_CUDA_TRY(cudaGetLastError());
   const int sd = s * d;
   const int tr = (sd + 63) / 64, tk = (c + 63) / 64;
-  const int splits = dterm_splits(tr * tk, N, P->H->sm_count);
+  const int splits = forced_splits() > 0 ? (int)std::min<int64_t>(forced_splits(), (N + 31) / 32)
+                                         : dterm_splits(tr * tk, N, P->H->sm_count);
   const int64_t rps = (N + splits - 1) / splits;
   FIRAL_TRY(P->Dpart.ensure((size_t)splits * c * sd * sizeof(T)));
   {

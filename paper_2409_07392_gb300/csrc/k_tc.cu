@@ -1012,7 +1012,7 @@ static int32_t tc_apply_t(firal_problem* P, const float* w, const float* Sblk, c
   FIRAL_TRY(P->qmean.ensure((size_t)s * P->d * sizeof(float)));
   const int mthreads = (P->d + 31) / 32 * 32;
   {
-  ProfScope ps(st, PF_ALPHA);
+  ProfScope ps(st, PF_SPLIT);
   count_launch(2);
   k_class_mean<<<s, mthreads, 0, st>>>(V, s, P->c, P->d, P->D, P->vmean.as<float>());
   k_split_probes<<<dim3((unsigned)(cp + 31) / 32, DP / 32 > 0 ? DP / 32 : 1, s), dim3(32, 8), 0,
@@ -1053,6 +1053,7 @@ static int32_t tc_apply_t(firal_problem* P, const float* w, const float* Sblk, c
     const int tiles = n_mt2 * n_nt2;
     int splits = (int)std::max<int64_t>(1, std::min<int64_t>((4LL * sms + tiles - 1) / tiles,
                                                             kb_total / 4 > 0 ? kb_total / 4 : 1));
+    if (forced_splits() > 0) splits = (int)std::min<int64_t>(forced_splits(), kb_total);
     const int64_t kbps = (kb_total + splits - 1) / splits;
     splits = (int)((kb_total + kbps - 1) / kbps);
     FIRAL_TRY(P->Dpart.ensure((size_t)splits * P->c * sd * sizeof(float)));

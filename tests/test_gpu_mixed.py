@@ -122,3 +122,23 @@ def test_mixed_quad_forms(api, handle, n, d, c, s):
     e2 = relerr(got_n, ref)
     print(f"mixed quad n={n} d={d} c={c} s={s}: {e1:.2e}  with N-component {e2:.2e}")
     assert e1 < 2e-3 and e2 < 2e-3
+
+
+def test_fixed_iteration_relax_mixed_and_fp32_vs_oracle(api, handle):
+    """Two MD iterations with exactly 10 PCG iterations per solve (the timing configuration):
+    z from the mixed and the FP32 paths against the oracle running the same recurrences."""
+    p = make_problem(20000, 16, 10, seed=11, x_dtype="bf16", h_dtype="float32")
+    b, s, T = 20.0, 8, 2
+    z_ref, info = approx.relax(p, b, s=s, T=T, seed=4, fixed_iters=10)
+    errs = {}
+    for prec in ("mixed", "fp32"):
+        X = dev(p.X).to(torch.bfloat16)
+        Xo = dev(p.Xo).to(torch.bfloat16)
+        prob = api.Problem(handle, X, dev(p.h), Xo, dev(p.ho), p.lam, precision=prec)
+        z = torch.full((p.n,), b / p.n, dtype=torch.float32, device="cuda")
+        opts = prob.relax_opts(s=s, T=T, fixed_iters=10, seed=4)
+        fh = [prob.relax_step(opts, t, b, z)["fhat"] for t in range(T)]
+        errs[prec] = (relerr(fh, np.array(info["fhat"])), relerr(z.cpu().numpy(), z_ref))
+        prob.close()
+    print("fixed-iteration relax vs oracle (fhat, z):", errs)
+    assert errs["mixed"][0] < 1e-3 and errs["mixed"][1] < 1e-3
