@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-round", action="store_true")
+    ap.add_argument("--round-selections", type=int, default=20)
     return ap.parse_args()
 
 
@@ -200,6 +202,40 @@ def oracle_md_iteration_rate(cfg, cg_iters, seconds, seed=0):
     per_full = dt * n_full / n1
     return 1.0 / per_full, f"one MD iteration ({cg_iters} CG iterations per solve) on n={n1} " \
         f"of {n_full} points, scaled by n", os.cpu_count()
+
+
+def round_measure(args, H):
+    """Per-selection time of the Round scan (eq. 14 scores, block update, eigenvalues, nu,
+    B^-1) on the full_pipeline pool (n = 1M, d = 128, c = 100), mixed and plain FP32."""
+    import torch
+
+    from paper_2409_07392_gb300 import api
+    from paper_2409_07392_gb300.synth import CONFIGS, config_problem
+    cfg = CONFIGS["full_pipeline"]
+    p = config_problem("full_pipeline")
+    X = torch.from_numpy(p.X).cuda().to(torch.bfloat16)
+    Xo = torch.from_numpy(p.Xo).cuda().to(torch.bfloat16)
+    h, ho = torch.from_numpy(p.h).cuda(), torch.from_numpy(p.ho).cuda()
+    out = {"workload": f"full_pipeline: n={p.n} d={p.d} c={p.c} (anisotropic, Zipf 1.1)",
+           "unit": "selections/s"}
+    for prec, nsel in (("mixed", args.round_selections), ("fp32", 2)):
+        prob = api.Problem(H, X, h, Xo, ho, p.lam, precision=prec)
+        z = torch.full((p.n,), float(cfg["b"]) / p.n, dtype=torch.float32, device="cuda")
+        prob.round(z, 1)                       # warm-up (and set-up cost)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        prob.round(z, 1)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        prob.round(z, 1 + nsel)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        per = ((t2 - t1) - (t1 - t0)) / nsel
+        out[prec] = {"value": 1.0 / per, "ms_per_selection": 1000.0 * per, "selections": nsel,
+                     "setup_ms": 1000.0 * (t1 - t0)}
+        prob.close()
+    out["speedup_mixed_over_fp32"] = out["mixed"]["value"] / out["fp32"]["value"]
+    return out
 
 
 def run_reference(args):
@@ -365,6 +401,12 @@ def run_ours(args):
                                 float((zmx - z32).norm() / z32.norm()),
                             "speedup_mixed_over_fp32": value / world * dt32}
             del p32, pmx
+        # ---------------- Round (Algorithm 3) on the full-pipeline workload
+        if not args.no_round:
+            try:
+                line["round"] = round_measure(args, H)
+            except Exception as exc:   # reported in the line; the Relax metric stands
+                line["round"] = {"error": str(exc)[:300]}
         # ---------------- CPU oracle baseline
         if not args.no_cpu:
             v, sample, cores = oracle_md_iteration_rate(cfg, args.cg_iters, args.cpu_seconds)

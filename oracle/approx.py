@@ -359,7 +359,7 @@ def round_select(prob, z_diamond, b, eta=None, exclude_selected=True, numerator=
     L = np.linalg.cholesky(Sig)
     Binv = np.linalg.inv(np.sqrt(D) * Sig + (eta / b) * Ho)
     H = np.zeros((c, d, d))
-    chosen, nus, gaps = [], [], []
+    chosen, nus, gaps, scores = [], [], [], []
     mask = np.zeros(n, dtype=bool)
     for _ in range(b):
         sc = round_scores(X, wk, Binv, Sig, eta, numerator)
@@ -367,6 +367,7 @@ def round_select(prob, z_diamond, b, eta=None, exclude_selected=True, numerator=
             sc = np.where(mask, -np.inf, sc)
         it = int(np.argmax(sc))
         if record:
+            scores.append(sc.copy())
             top = np.sort(sc[np.isfinite(sc)])[::-1]
             gaps.append((top[0] - top[1]) / abs(top[0]) if top.size > 1 else np.inf)
         chosen.append(it)
@@ -377,5 +378,5 @@ def round_select(prob, z_diamond, b, eta=None, exclude_selected=True, numerator=
         nus.append(nu)
         Binv = np.linalg.inv(nu * Sig + eta * H + (eta / b) * Ho)
     if record:
-        return chosen, dict(nu=nus, gap=gaps, H=H, Sig=Sig)
+        return chosen, dict(nu=nus, gap=gaps, H=H, Sig=Sig, scores=scores)
     return chosen

@@ -119,6 +119,8 @@ int32_t tc_quad_forms(firal_problem* P, const void* A, const void* B, int s, dou
                       void* g);
 int32_t tc_syrk_blocks(firal_problem* P, const void* w, double lamS, void* outS, double lamP,
                        double* outP);
+int32_t tc_round_scores(firal_problem* P, const void* M1, const void* M2, const uint8_t* mask,
+                        double eta, double* pv, int64_t* pi, int* np_out);
 bool tc_available();
 
 }  // namespace firal
@@ -403,12 +405,12 @@ int32_t round_impl(firal_problem* P, const void* zr, int32_t b, const firal_roun
   const int64_t D = P->D;
   const double eta = (o && o->eta > 0) ? o->eta : 8.0 * std::sqrt((double)D);
   const size_t blk = (size_t)c * d * d;
-  DBuf Sig, L, Bm, Binv, Hk, M1, M2, eig, nu, mask, pv, pi, score;
+  DBuf Sig, L, Bm, Binv, Hk, M1, M2, eig, nu, mask, pv, pi, score, Tg;
   auto rel = [&]() {
-    for (DBuf* bf : {&Sig, &L, &Bm, &Binv, &Hk, &M1, &M2, &eig, &nu, &mask, &pv, &pi, &score})
+    for (DBuf* bf : {&Sig, &L, &Bm, &Binv, &Hk, &M1, &M2, &eig, &nu, &mask, &pv, &pi, &score, &Tg})
       bf->release();
   };
-  const int np = (int)((P->n + 127) / 128);
+  const int np = (int)std::max<int64_t>((P->n + 127) / 128, P->H->sm_count);
   int32_t rc = FIRAL_OK;
 #define TRYR(x)                    \
   do {                             \
@@ -431,6 +433,7 @@ int32_t round_impl(firal_problem* P, const void* zr, int32_t b, const firal_roun
   TRYR(pv.ensure((size_t)np * 8));
   TRYR(pi.ensure((size_t)np * 8));
   TRYR(score.ensure(8));
+  TRYR(Tg.ensure(blk * 8));
   // B(H_o): weights 1 on labelled rows, 0 on the pool; Sigma_diamond: z on the pool (C-15)
   TRYR(fill_weights(P->dbl, P->zsave.p, P->m, 1.0, nullptr, 0.0, P->n, st));
   TRYR(syrk_blocks(P, P->zsave.p, 0.0, nullptr, P->lambda, P->HoBlk.as<double>()));
@@ -444,14 +447,19 @@ int32_t round_impl(firal_problem* P, const void* zr, int32_t b, const firal_roun
                P->HoBlk.as<double>(), 0.0, nullptr, tot, st));
   TRYR(chol_inv(P->dbl, Bm.as<double>(), c, d, nullptr, Binv.as<double>(), nullptr,
                 not_spd_flag(P->H), st));
-  TRYR(round_m(P->dbl, Binv.as<double>(), Sig.as<double>(), c, d, M1.p, M2.p, st));
+  TRYR(round_m(P->dbl, Binv.as<double>(), Sig.as<double>(), c, d, M1.p, M2.p, Tg.as<double>(), st));
   FIRAL_CUDA_TRY(cudaMemsetAsync(Hk.p, 0, blk * 8, st));
   FIRAL_CUDA_TRY(cudaMemsetAsync(mask.p, 0, (size_t)P->n, st));
   for (int t = 0; t < b; ++t) {
-    // line 7: eq. 14 scores and the masked argmax
-    TRYR(round_scores(P, M1.p, M2.p, mask.as<uint8_t>(), eta, pv.as<double>(), pi.as<int64_t>(),
-                      np));
-    TRYR(round_pick(pv.as<double>(), pi.as<int64_t>(), np, mask.as<uint8_t>(), sel, t,
+    // line 7: eq. 14 scores and the masked argmax (tensor cores for FIRAL_MIXED_BF16)
+    int npart = np;
+    if (P->prec == FIRAL_MIXED_BF16)
+      TRYR(tc_round_scores(P, M1.p, M2.p, mask.as<uint8_t>(), eta, pv.as<double>(),
+                           pi.as<int64_t>(), &npart));
+    else
+      TRYR(round_scores(P, M1.p, M2.p, mask.as<uint8_t>(), eta, pv.as<double>(),
+                        pi.as<int64_t>(), np));
+    TRYR(round_pick(pv.as<double>(), pi.as<int64_t>(), npart, mask.as<uint8_t>(), sel, t,
                     score.as<double>(), st));
     // line 8: H_k += B_k(H_o)/b + w x x^T
     TRYR(round_hupdate(P, Hk.as<double>(), P->HoBlk.as<double>(), 1.0 / b, sel, t));
@@ -464,7 +472,7 @@ int32_t round_impl(firal_problem* P, const void* zr, int32_t b, const firal_roun
                     eta / b, P->HoBlk.as<double>(), tot, st));
     TRYR(chol_inv(P->dbl, Bm.as<double>(), c, d, nullptr, Binv.as<double>(), nullptr,
                   not_spd_flag(P->H), st));
-    TRYR(round_m(P->dbl, Binv.as<double>(), Sig.as<double>(), c, d, M1.p, M2.p, st));
+    TRYR(round_m(P->dbl, Binv.as<double>(), Sig.as<double>(), c, d, M1.p, M2.p, Tg.as<double>(), st));
   }
   if (stats) {
     double h[2];
@@ -616,7 +624,7 @@ int32_t firal_problem_destroy(firal_problem* P) {
                   &P->Minv, &P->HoBlk, &P->walpha, &P->Dpart, &P->syrk_part, &P->cgX, &P->cgR,
                   &P->cgP, &P->cgQ, &P->cgZ, &P->cgcols, &P->cgpart1, &P->cgpart2, &P->V, &P->U,
                   &P->W, &P->HU, &P->g, &P->red, &P->zsave, &P->Xb, &P->Hb, &P->HbT, &P->Pb, &P->vmean, &P->qmean, &P->XwT, &P->gq_ab,
-                  &P->gq_m, &P->gq_part})
+                  &P->gq_m, &P->gq_part, &P->rtab, &P->rM})
     b->release();
   delete P;
   return FIRAL_OK;
@@ -682,7 +690,7 @@ int32_t firal_round(firal_handle* H, const firal_pool* pool, const firal_hess0* 
                     firal_round_stats* stats) {
   const int32_t prec = o ? o->precision : FIRAL_FP32;
   firal_problem* P = nullptr;
-  int32_t rc = problem_create_impl(H, pool, h0, prec == FIRAL_MIXED_BF16 ? FIRAL_FP32 : prec, &P);
+  int32_t rc = problem_create_impl(H, pool, h0, prec, &P);
   if (rc != FIRAL_OK) return record(H, rc);
   rc = round_impl(P, zr, b, o, sel, stats);
   firal_problem_destroy(P);

@@ -126,6 +126,8 @@ struct firal_problem {
   firal::DBuf vmean, qmean;      // class means of the probe block / of the raw apply (s x d)
   firal::DBuf XwT;               // bf16 (h - bf16(h))^T, the low part of h for the block sums
   firal::DBuf gq_ab, gq_m, gq_part;  // tensor-core quadratic forms: [A;B], M~ pairs, partials
+  firal::DBuf rtab, rM;          // Round on tensor cores: 8-pair chunk table, M~ hi/lo rows
+  int rtab_d = -1, rtab_chunks = 0;
   int32_t dp = 0, cp = 0;
   int64_t Np = 0;
 };
@@ -166,7 +168,7 @@ int32_t round_scores(firal_problem* P, const void* M1, const void* M2, const uin
 int32_t round_pick(const double* pv, const int64_t* pi, int np, uint8_t* mask, int32_t* sel,
                    int32_t t, double* score_out, cudaStream_t st);
 int32_t round_m(bool dbl, const double* Binv, const double* Sig, int c, int d, void* M1, void* M2,
-                cudaStream_t st);
+                double* Tg, cudaStream_t st);
 int32_t round_hupdate(firal_problem* P, double* H, const double* Ho, double invb,
                       const int32_t* sel, int32_t t);
 int32_t lincomb(double* out, double a, const double* X, double b, const double* Y, double cc,

@@ -327,16 +327,17 @@ __global__ void k_axpbypcz_nu(double* out, const double* nu, const double* X, do
     out[i] = a * X[i] + b * Y[i] + cc * Z[i];
 }
 
-// M1_k = Binv_k Sig_k Binv_k (double in, T out); M2_k = Binv_k as T
+// M1_k = Binv_k Sig_k Binv_k (double in, T out); M2_k = Binv_k as T.  Binv_k sits in shared
+// memory; Sig_k Binv_k goes through the global scratch Tg (c*d*d doubles).
 template <class T>
 __global__ void k_round_m(const double* __restrict__ Binv, const double* __restrict__ Sig, int d,
-                          T* __restrict__ M1, T* __restrict__ M2) {
+                          T* __restrict__ M1, T* __restrict__ M2, double* __restrict__ Tg) {
   extern __shared__ double sh[];
   double* Bs = sh;           // d*d
-  double* Ts = sh + d * d;   // d*d: Sig * Binv
   const int k = blockIdx.x, tid = threadIdx.x, bd = blockDim.x;
   const double* Bk = Binv + (int64_t)k * d * d;
   const double* Sk = Sig + (int64_t)k * d * d;
+  double* Ts = Tg + (int64_t)k * d * d;
   for (int t = tid; t < d * d; t += bd) Bs[t] = Bk[t];
   __syncthreads();
   for (int t = tid; t < d * d; t += bd) {
@@ -528,18 +529,18 @@ int32_t round_pick(const double* pv, const int64_t* pi, int np, uint8_t* mask, i
 }
 
 int32_t round_m(bool dbl, const double* Binv, const double* Sig, int c, int d, void* M1, void* M2,
-                cudaStream_t st) {
-  const size_t smem = 2 * (size_t)d * d * sizeof(double);
+                double* Tg, cudaStream_t st) {
+  const size_t smem = (size_t)d * d * sizeof(double);
   ProfScope ps(st, PF_ROUND);
   count_launch();
   if (dbl) {
     FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_round_m<double>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    k_round_m<double><<<c, threads_for(d), smem, st>>>(Binv, Sig, d, (double*)M1, (double*)M2);
+    k_round_m<double><<<c, threads_for(d), smem, st>>>(Binv, Sig, d, (double*)M1, (double*)M2, Tg);
   } else {
     FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_round_m<float>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    k_round_m<float><<<c, threads_for(d), smem, st>>>(Binv, Sig, d, (float*)M1, (float*)M2);
+    k_round_m<float><<<c, threads_for(d), smem, st>>>(Binv, Sig, d, (float*)M1, (float*)M2, Tg);
   }
   FIRAL_CUDA_TRY(cudaGetLastError());
   return FIRAL_OK;

@@ -20,7 +20,9 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <climits>
 #include <mutex>
+#include <vector>
 
 #include "firal_internal.cuh"
 #include "tc_ptx.cuh"
@@ -952,6 +954,312 @@ __global__ void k_h_lo_T(bf16* HlT, const float* Ha, int64_t N, int c, int64_t N
 }
 
 // ------------------------------------------------------------------------------------------
+// Round scores on tensor cores (eq. 14, Proposition 1):
+//   q1_ik = x_i^T M1_k x_i,  q2_ik = x_i^T M2_k x_i,  score_i = sum_k w_ik q1_ik / (1 + eta w_ik q2_ik)
+// with w_ik = h_ik (1 - h_ik).  The quadratic forms are a GEMM over feature pairs:
+//   q_ik = sum_pairs Z_i(e,e') M~_k(e,e'),  Z_i(e,e') = x_ie x_ie',
+// pairs ordered by e with e' running over [8 floor(e/8), d8) so every 8-pair chunk is one
+// aligned 16-byte run of x (pairs with e' < e carry weight 0 in M~).  M~ = symmetric weights
+// (M_ee on the diagonal, M_ee' + M_e'e above it), fed as bf16 hi + lo.  One unit = one
+// 128-point tile; it loops over chunks of 128 classes (N = 256: M1 rows then M2 rows) and keeps
+// a running masked argmax per thread (ties to the lowest index).
+// ------------------------------------------------------------------------------------------
+namespace r_cfg {
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 2, NBUILD = 6;
+constexpr int Z_BYTES = BM * BK * 2;
+constexpr int M_BYTES = BN * BK * 2;
+constexpr int STAGE_BYTES = Z_BYTES + 2 * M_BYTES;       // 80 KB
+template <int DP> struct L {
+  static constexpr int X_BYTES = BM * DP * 2;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + X_BYTES + 1024 + 512;
+};
+}  // namespace r_cfg
+
+struct RoundCtl {
+  uint64_t full[2], empty[2], zfull[2], xfull, xempty, tfull, tempty, drain;
+  uint32_t tmem_base;
+  int abort_w;
+  double bval[8];
+  long long bidx[8];
+};
+
+template <int DP>
+__global__ void __launch_bounds__(256, 1)
+    k_tc_round(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapMh,
+               const __grid_constant__ CUtensorMap mapMl, const short2* __restrict__ tab,
+               const float* __restrict__ Ha, const uint8_t* __restrict__ mask, int64_t m,
+               int64_t n, int c, int n_kc, int kblocks, double eta, double* part_val,
+               int64_t* part_idx, int32_t* err) {
+  using namespace r_cfg;
+  using LL = L<DP>;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* xs = sm + STAGES * STAGE_BYTES;                 // x tile, row i = 2*DP bytes
+  RoundCtl* ctl = (RoundCtl*)(xs + LL::X_BYTES);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < STAGES; ++i) {
+      mbar_init(&ctl->full[i], 1);
+      mbar_init(&ctl->empty[i], 1);
+      mbar_init(&ctl->zfull[i], NBUILD);
+    }
+    mbar_init(&ctl->xfull, 1);
+    mbar_init(&ctl->xempty, NBUILD);
+    mbar_init(&ctl->tfull, 1);
+    mbar_init(&ctl->tempty, 4);
+    mbar_init(&ctl->drain, 1);
+    ctl->abort_w = 0;
+    mbar_fence_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(&ctl->tmem_base, 256);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = ctl->tmem_base;
+  volatile int* abort_w = &ctl->abort_w;
+  const int n_mt = (int)((n + BM - 1) / BM);
+  constexpr uint32_t TX = 2 * M_BYTES;
+
+  if (warp == 0 && lane == 0) {
+    tma_prefetch(&mapX);
+    tma_prefetch(&mapMh);
+    tma_prefetch(&mapMl);
+    int stage = 0;
+    uint32_t phase = 0, xphase = 0;
+    bool ok = true;
+    for (int mt = blockIdx.x; mt < n_mt && ok && !*abort_w; mt += gridDim.x) {
+      if (!mbar_wait(&ctl->xempty, xphase ^ 1, abort_w)) {
+        atomicExch(err, 31);
+        ctl->abort_w = 1;
+        break;
+      }
+      mbar_expect_tx(&ctl->xfull, LL::X_BYTES);
+      tma_load_2d(xs, &mapX, &ctl->xfull, 0, (int)(m + (int64_t)mt * BM));
+      xphase ^= 1;
+      for (int kc = 0; kc < n_kc && ok; ++kc) {
+        for (int kb = 0; kb < kblocks; ++kb) {
+          if (!mbar_wait(&ctl->empty[stage], phase ^ 1, abort_w)) {
+            atomicExch(err, 32);
+            ctl->abort_w = 1;
+            ok = false;
+            break;
+          }
+          unsigned char* st = sm + stage * STAGE_BYTES;
+          mbar_expect_tx(&ctl->full[stage], TX);
+          tma_load_2d(st + Z_BYTES, &mapMh, &ctl->full[stage], kb * BK, kc * BN);
+          tma_load_2d(st + Z_BYTES + M_BYTES, &mapMl, &ctl->full[stage], kb * BK, kc * BN);
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1;
+          }
+        }
+      }
+    }
+    for (int i = 0; i < STAGES; ++i) {
+      if (!mbar_wait(&ctl->empty[stage], phase ^ 1, abort_w)) break;
+      if (++stage == STAGES) {
+        stage = 0;
+        phase ^= 1;
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    constexpr uint32_t idesc = idesc_bf16_f32(BM, BN);
+    int stage = 0;
+    uint32_t phase = 0, acc_phase = 0;
+    bool ok = true;
+    for (int mt = blockIdx.x; mt < n_mt && ok && !*abort_w; mt += gridDim.x) {
+      for (int kc = 0; kc < n_kc && ok; ++kc) {
+        if (!mbar_wait(&ctl->tempty, acc_phase ^ 1, abort_w)) {
+          atomicExch(err, 33);
+          ctl->abort_w = 1;
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        for (int kb = 0; kb < kblocks; ++kb) {
+          if (!mbar_wait(&ctl->zfull[stage], phase, abort_w) ||
+              !mbar_wait(&ctl->full[stage], phase, abort_w)) {
+            atomicExch(err, 34);
+            ctl->abort_w = 1;
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t z0 = smem_u32(sm + stage * STAGE_BYTES);
+          const uint32_t mh = z0 + Z_BYTES, ml = mh + M_BYTES;
+#pragma unroll
+          for (int k = 0; k < BK / 16; ++k) {
+            const uint64_t dz = sdesc_sw128(z0 + k * 32);
+            umma_bf16(tmem, dz, sdesc_sw128(mh + k * 32), idesc, (kb | k) != 0);
+            umma_bf16(tmem, dz, sdesc_sw128(ml + k * 32), idesc, 1u);
+          }
+          umma_commit(&ctl->empty[stage]);
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1;
+          }
+        }
+        if (!ok) break;
+        umma_commit(&ctl->tfull);
+        acc_phase ^= 1;
+      }
+    }
+    umma_commit(&ctl->drain);
+    mbar_wait_drain(&ctl->drain, 0);
+  } else if (warp >= 2) {
+    const int bw = warp - 2;
+    const int tid_b = bw * 32 + lane;
+    int stage = 0;
+    uint32_t phase = 0, xphase = 0, acc_phase = 0;
+    bool ok = true;
+    double best = -INFINITY;
+    long long besti = LLONG_MAX;
+    for (int mt = blockIdx.x; mt < n_mt && ok && !*abort_w; mt += gridDim.x) {
+      if (!mbar_wait(&ctl->xfull, xphase, abort_w)) {
+        atomicExch(err, 35);
+        ctl->abort_w = 1;
+        break;
+      }
+      xphase ^= 1;
+      double score = 0.0;   // epilogue threads: this point's eq. 14 sum over class chunks
+      for (int kc = 0; kc < n_kc && ok; ++kc) {
+        for (int kb = 0; kb < kblocks; ++kb) {
+          // the MMA warp must have released this stage (previous round) before Z is rewritten
+          if (!mbar_wait(&ctl->empty[stage], phase ^ 1, abort_w)) {
+            atomicExch(err, 36);
+            ctl->abort_w = 1;
+            ok = false;
+            break;
+          }
+          // Z chunks: (row i, 8-pair chunk c8); 8 consecutive threads share row i
+          for (int ch = tid_b; ch < BM * 8; ch += NBUILD * 32) {
+            const int i = ch >> 3, c8 = ch & 7;
+            const short2 ee = tab[kb * 8 + c8];
+            uint4 zv = make_uint4(0, 0, 0, 0);
+            if (ee.x >= 0) {
+              const __nv_bfloat16 xe = *reinterpret_cast<const __nv_bfloat16*>(
+                  xs + i * (2 * DP) + ee.x * 2);
+              const uint4 xv = *reinterpret_cast<const uint4*>(xs + i * (2 * DP) + ee.y * 2);
+              const __nv_bfloat162 x2e = __halves2bfloat162(xe, xe);
+              const __nv_bfloat162* a2 = reinterpret_cast<const __nv_bfloat162*>(&xv);
+              __nv_bfloat162* z2 = reinterpret_cast<__nv_bfloat162*>(&zv);
+#pragma unroll
+              for (int h = 0; h < 4; ++h) z2[h] = __hmul2(x2e, a2[h]);
+            }
+            *reinterpret_cast<uint4*>(sm + stage * STAGE_BYTES + i * 128 + ((c8 ^ (i & 7)) << 4)) = zv;
+          }
+          fence_async_smem();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&ctl->zfull[stage]);
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1;
+          }
+        }
+        if (!ok) break;
+        if (warp >= 4) {
+          const int q = warp & 3;
+          if (!mbar_wait(&ctl->tfull, acc_phase, abort_w)) {
+            atomicExch(err, 37);
+            ctl->abort_w = 1;
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const int64_t row = (int64_t)mt * BM + q * 32 + lane;    // pool index
+          const float* hrow = Ha + (m + (row < n ? row : 0)) * c;
+          for (int cc = 0; cc < 128; cc += 32) {
+            float q1[32], q2[32];
+            tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + cc, q1);
+            tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + 128 + cc, q2);
+            if (row < n) {
+#pragma unroll
+              for (int t = 0; t < 32; ++t) {
+                const int k = kc * 128 + cc + t;
+                if (k < c) {
+                  const double hv = (double)hrow[k];
+                  const double wk = hv * (1.0 - hv);
+                  score += wk * (double)q1[t] / (1.0 + eta * wk * (double)q2[t]);
+                }
+              }
+            }
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&ctl->tempty);
+        }
+        acc_phase ^= 1;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&ctl->xempty);
+      if (warp >= 4) {
+        const int64_t row = (int64_t)mt * BM + (warp & 3) * 32 + lane;
+        if (row < n && !mask[row] && score == score &&
+            (score > best || (score == best && row < besti))) {
+          best = score;
+          besti = row;
+        }
+      }
+    }
+    if (warp >= 4) {
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const long long oi = __shfl_xor_sync(0xffffffffu, besti, o);
+        if (ov > best || (ov == best && oi < besti)) {
+          best = ov;
+          besti = oi;
+        }
+      }
+      if (lane == 0) {
+        ctl->bval[warp - 4] = best;
+        ctl->bidx[warp - 4] = besti;
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = ctl->bval[0];
+    long long bi = ctl->bidx[0];
+    for (int w = 1; w < 4; ++w)
+      if (ctl->bval[w] > b || (ctl->bval[w] == b && ctl->bidx[w] < bi)) {
+        b = ctl->bval[w];
+        bi = ctl->bidx[w];
+      }
+    part_val[blockIdx.x] = b;
+    part_idx[blockIdx.x] = bi;
+  }
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc(tmem, 256);
+  }
+}
+
+// M~ rows for one Round iteration: row (kc, which, kk) = M_{which, k} symmetric pair weights
+// at pair p of the 8-aligned table (0 where e' < e or beyond d), bf16 hi and lo
+template <class T>
+__global__ void k_round_mpairs(bf16* Mh, bf16* Ml, const T* M1, const T* M2, const short2* tab,
+                               int c, int d, int kpad) {
+  const int row = blockIdx.x;                 // kc*256 + which*128 + kk
+  const int kc = row / 256, which = (row / 128) & 1, kk = row & 127;
+  const int k = kc * 128 + kk;
+  const T* M = (which == 0 ? M1 : M2) + (int64_t)k * d * d;
+  for (int p = threadIdx.x; p < kpad; p += blockDim.x) {
+    float v = 0.0f;
+    const short2 ee = tab[p >> 3];
+    const int e = ee.x, e2 = ee.y + (p & 7);
+    if (k < c && e >= 0 && e2 < d && e2 >= e)
+      v = e == e2 ? (float)M[e * d + e] : (float)(M[e * d + e2] + M[e2 * d + e]);
+    const bf16 hi = __float2bfloat16_rn(v);
+    Mh[(int64_t)row * kpad + p] = hi;
+    Ml[(int64_t)row * kpad + p] = __float2bfloat16_rn(v - __bfloat162float(hi));
+  }
+}
+
+// ------------------------------------------------------------------------------------------
 // host side
 // ------------------------------------------------------------------------------------------
 bool tc_available() { return true; }
@@ -1270,6 +1578,73 @@ static int32_t tc_quad_t(firal_problem* P, const float* A, const float* B, int s
       part1, n_nt1, a32, s, P->m, P->N, Np, scale, g);
   FIRAL_CUDA_TRY(cudaGetLastError());
   return FIRAL_OK;
+}
+
+template <int DP>
+static int32_t tc_round_scores_t(firal_problem* P, const float* M1, const float* M2,
+                                 const uint8_t* mask, double eta, double* pv, int64_t* pi,
+                                 int* np_out) {
+  using namespace r_cfg;
+  cudaStream_t st = P->H->stream;
+  const int d = P->d, c = P->c;
+  const int sms = P->H->sm_count;
+  // 8-pair chunk table (e, first e') with e' running over [8 floor(e/8), d8)
+  if (P->rtab_d != d) {
+    std::vector<short2> tab;
+    const int d8 = (d + 7) / 8 * 8;
+    for (int e = 0; e < d; ++e)
+      for (int e2 = (e / 8) * 8; e2 < d8; e2 += 8) tab.push_back(make_short2((short)e, (short)e2));
+    while (tab.size() % 8) tab.push_back(make_short2(-1, 0));
+    FIRAL_TRY(P->rtab.ensure(tab.size() * sizeof(short2)));
+    FIRAL_CUDA_TRY(cudaMemcpyAsync(P->rtab.p, tab.data(), tab.size() * sizeof(short2),
+                                   cudaMemcpyHostToDevice, st));
+    FIRAL_CUDA_TRY(cudaStreamSynchronize(st));
+    P->rtab_d = d;
+    P->rtab_chunks = (int)tab.size();
+  }
+  const int kblocks = P->rtab_chunks / 8;
+  const int kpad = kblocks * BK;
+  const int n_kc = (c + 127) / 128;
+  const size_t mbytes = (size_t)n_kc * BN * kpad * 2;
+  FIRAL_TRY(P->rM.ensure(2 * mbytes));
+  bf16* Mh = P->rM.as<bf16>();
+  bf16* Ml = Mh + mbytes / 2;
+  ProfScope ps(st, PF_ROUND);
+  count_launch(2);
+  k_round_mpairs<float><<<n_kc * BN, 256, 0, st>>>(Mh, Ml, M1, M2, P->rtab.as<short2>(), c, d,
+                                                   kpad);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  CUtensorMap mX, mMh, mMl;
+  FIRAL_TRY(make_map(&mX, P->Xb.p, P->Np, DP, BM, DP, false));
+  FIRAL_TRY(make_map(&mMh, Mh, (uint64_t)n_kc * BN, kpad, BN, BK, true));
+  FIRAL_TRY(make_map(&mMl, Ml, (uint64_t)n_kc * BN, kpad, BN, BK, true));
+  static bool attr[4] = {false, false, false, false};
+  const int ai = DP == 16 ? 0 : DP == 32 ? 1 : DP == 64 ? 2 : 3;
+  if (!attr[ai]) {
+    FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tc_round<DP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        L<DP>::SMEM));
+    attr[ai] = true;
+  }
+  const int n_mt = (int)((P->n + BM - 1) / BM);
+  const int grid = std::min(n_mt, sms);
+  k_tc_round<DP><<<grid, 256, L<DP>::SMEM, st>>>(mX, mMh, mMl, P->rtab.as<short2>(),
+                                                  P->Ha.as<float>(), mask, P->m, P->n, c, n_kc,
+                                                  kblocks, eta, pv, pi, tc_error_word(P));
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  *np_out = grid;
+  return FIRAL_OK;
+}
+
+int32_t tc_round_scores(firal_problem* P, const void* M1, const void* M2, const uint8_t* mask,
+                        double eta, double* pv, int64_t* pi, int* np_out) {
+  const float* a = (const float*)M1;
+  const float* b = (const float*)M2;
+  switch (P->dp) {
+    case 16: return tc_round_scores_t<16>(P, a, b, mask, eta, pv, pi, np_out);
+    case 32: return tc_round_scores_t<32>(P, a, b, mask, eta, pv, pi, np_out);
+    case 64: return tc_round_scores_t<64>(P, a, b, mask, eta, pv, pi, np_out);
+    default: return tc_round_scores_t<128>(P, a, b, mask, eta, pv, pi, np_out);
+  }
 }
 
 int32_t tc_hessian_apply(firal_problem* P, const void* w, const void* Sblk, const void* V, int s,

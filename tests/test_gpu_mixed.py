@@ -142,3 +142,29 @@ def test_fixed_iteration_relax_mixed_and_fp32_vs_oracle(api, handle):
         prob.close()
     print("fixed-iteration relax vs oracle (fhat, z):", errs)
     assert errs["mixed"][0] < 1e-3 and errs["mixed"][1] < 1e-3
+
+
+@pytest.mark.parametrize("n,d,c,b", [(3000, 20, 10, 10), (6000, 64, 37, 12), (2500, 128, 5, 8),
+                                     (4000, 16, 150, 10)])
+def test_mixed_round_matches_oracle_while_gaps_are_clear(api, handle, n, d, c, b):
+    """Round (Alg. 3) with tensor-core eq. 14 scores against the FP64 oracle.  While the two
+    histories agree, every pick must equal the oracle's when its top-1/top-2 gap exceeds 1e-3,
+    and otherwise must be a valid near-tie (oracle score within 1e-3 of the best); comparison
+    stops at the first valid divergence (the histories differ from there on)."""
+    p = make_problem(n, d, c, seed=d + c, x_dtype="bf16", h_dtype="float32")
+    prob = make(api, handle, p)
+    z = np.full(p.n, float(b) / p.n)
+    ref, info = approx.round_select(p, z, b, record=True)
+    sel, st = prob.round(dev(z.astype(np.float32)), b)
+    sel = sel.cpu().tolist()
+    compared = 0
+    for t in range(b):
+        if sel[t] == ref[t]:
+            compared += 1
+            continue
+        sc = info["scores"][t]
+        assert info["gap"][t] <= 1e-3, (t, sel[:t + 1], ref[:t + 1])
+        assert sc[sel[t]] >= sc[ref[t]] - 1e-3 * abs(sc[ref[t]]), (t, sc[sel[t]], sc[ref[t]])
+        break
+    print(f"mixed round n={n} d={d} c={c} b={b}: {compared} of {b} picks identical, "
+          f"first gaps {np.round(info['gap'][:4], 4).tolist()}")
