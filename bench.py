@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-round", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--round-selections", type=int, default=20)
     return ap.parse_args()
 
@@ -238,6 +239,51 @@ def round_measure(args, H):
     return out
 
 
+def batched_measure(args, H, K=5):
+    """Batched Relax on the batched_uneven workload (64 pools, n ~ U[2000, 40000], d in
+    {16,32,48,64}, c in {5,10,20}, s = 8): batched MD iterations per second (one iteration of
+    every pool, replayed from a CUDA graph), with HBM and tensor fractions on algorithmic work."""
+    import torch
+
+    from paper_2409_07392_gb300 import api
+    from paper_2409_07392_gb300.synth import batched_problems, make_problem
+    shapes = batched_problems(64, seed=0)
+    dicts, npts, flops_apply, bytes_apply = [], 0, 0.0, 0.0
+    s = 8
+    for i, sh in enumerate(shapes):
+        p = make_problem(sh["n"], sh["d"], sh["c"], seed=i, x_dtype="bf16", h_dtype="float32")
+        dicts.append(dict(X=torch.from_numpy(p.X).cuda().to(torch.bfloat16),
+                          h=torch.from_numpy(p.h).cuda(),
+                          Xo=torch.from_numpy(p.Xo).cuda().to(torch.bfloat16),
+                          ho=torch.from_numpy(p.ho).cuda(), lam=p.lam, budget=float(sh["b"])))
+        n, d, c = sh["n"], sh["d"], sh["c"]
+        npts += n
+        flops_apply += 4.0 * n * c * d * s
+        bytes_apply += n * (2 * d + 4 * c + 4) + 8.0 * d * c * s
+    cg = args.cg_iters
+
+    def run(T):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        api.batched_relax(dicts, s=s, T=T, fixed_iters=cg, seed=1, precision="mixed", handle=H)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0
+
+    run(2)                                   # warm-up (module loading, attributes)
+    t1 = run(2)
+    tk = run(2 + K)
+    per = (tk - t1) / K
+    applies = 2 * cg + 1
+    pk, _ = peaks()
+    return {"workload": f"batched_uneven: 64 pools, {npts} points in all, s={s}, "
+                        f"cg_iters/solve={cg}",
+            "value": 1.0 / per, "unit": "batched MD iters/s", "ms_per_iteration": 1000 * per,
+            "hbm_frac_of_measured": applies * bytes_apply / per / 1e9 / pk["hbm_gbs"],
+            "tensor_frac_of_measured": applies * flops_apply / per / 1e12 /
+            pk["bf16_tflops_sustained"],
+            "note": "fractions on algorithmic Sigma-apply work only (bytes n(2d+4c+4) per apply)"}
+
+
 def run_reference(args):
     world, rank, _ = dist_setup(args)
     if rank != 0:
@@ -407,6 +453,11 @@ def run_ours(args):
                 line["round"] = round_measure(args, H)
             except Exception as exc:   # reported in the line; the Relax metric stands
                 line["round"] = {"error": str(exc)[:300]}
+        if not args.no_batched:
+            try:
+                line["batched"] = batched_measure(args, H)
+            except Exception as exc:
+                line["batched"] = {"error": str(exc)[:300]}
         # ---------------- CPU oracle baseline
         if not args.no_cpu:
             v, sample, cores = oracle_md_iteration_rate(cfg, args.cg_iters, args.cpu_seconds)

@@ -193,13 +193,28 @@ int32_t firal_problem_destroy(firal_problem* problem);
 
 /* ---------------------------------------------------------------- Relax (Algorithm 2) */
 
-/* Full Relax solve.  z0: device, n values of the vec type on the budget simplex
+/* Full Relax solve.  With opts->cg.fixed_iters > 0, no history or stats requested and
+ * md_tol = 0, iterations 1..T-1 are replayed from a CUDA graph (captured on an internal
+ * stream ordered after the handle's stream).
+ * z0: device, n values of the vec type on the budget simplex
  * (z >= 0, sum z = budget) or NULL for z0 = budget/n.  z_out: device, n values; it holds
  * z_diamond on return (the iterates stay on the budget simplex, so no final rescale).
  * fhat_hist: host, opts->T doubles or NULL.  stats: host or NULL. */
 int32_t firal_relax(firal_handle* handle, const firal_pool* pool, const firal_hess0* hess0,
                     double budget, const void* z0, const firal_relax_opts* opts, void* z_out,
                     double* fhat_hist, firal_relax_stats* stats);
+
+/* Relax for many independent pools at once (the batched workload; one problem per pool, each
+ * with its own budget).  pools, hess0s (may be NULL: no labelled set, lambda = 0), budgets and
+ * z_outs have nproblems entries; z_outs[p] is a device buffer of pools[p].n values of the vec
+ * type and receives that problem's z_diamond (iterates start at budget/n).  All problems use
+ * *opts.  With opts->cg.fixed_iters > 0, iteration 0 runs
+ * eagerly and one batched iteration is captured into a CUDA graph (problems spread over up
+ * to 64 internal streams) and replayed T-1 times; otherwise the iterations run eagerly.
+ * Synchronises before returning. */
+int32_t firal_batched_relax(firal_handle* handle, int32_t nproblems, const firal_pool* pools,
+                            const firal_hess0* hess0s, const double* budgets,
+                            const firal_relax_opts* opts, void* const* z_outs);
 
 /* One mirror-descent iteration t (0-based) of Algorithm 2 on a prepared problem:
  * probes V_t (line 4), preconditioner B(Sigma_z)^{-1} (line 5), U = Sigma_z^{-1} V (line 6),

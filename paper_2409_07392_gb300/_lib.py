@@ -73,6 +73,9 @@ SIGNATURES = [
                               POINTER(FiralRelaxStats)]),
     ("firal_relax_step", c_int32, [c_void_p, POINTER(FiralRelaxOpts), c_int32, c_double, c_void_p,
                                    POINTER(FiralStepStats)]),
+    ("firal_batched_relax", c_int32, [c_void_p, c_int32, POINTER(FiralPool), POINTER(FiralHess0),
+                                      POINTER(c_double), POINTER(FiralRelaxOpts),
+                                      POINTER(c_void_p)]),
     ("firal_round", c_int32, [c_void_p, POINTER(FiralPool), POINTER(FiralHess0), c_void_p,
                               c_int32, POINTER(FiralRoundOpts), c_void_p,
                               POINTER(FiralRoundStats)]),

@@ -273,6 +273,26 @@ def relax(X, h, Xo=None, ho=None, lam=1e-3, budget=10.0, *, s=10, T=20, tol=0.1,
     return z, fh
 
 
+def batched_relax(problems, *, s=8, T=10, tol=0.1, maxit=100, fixed_iters=0, beta0=1.0, seed=1,
+                  precision="mixed", estimator=0, handle: Handle | None = None):
+    """Relax (Algorithm 2) on many independent pools in one call.  ``problems`` is a list of
+    dicts with device tensors X, h, Xo, ho and floats lam, budget.  Returns the list of z."""
+    H = handle or Handle()
+    n = len(problems)
+    pools = (L.FiralPool * n)(*[_pool(p["X"], p["h"]) for p in problems])
+    h0s = (L.FiralHess0 * n)(*[_hess0(p.get("Xo"), p.get("ho"), p.get("lam", 1e-3))
+                               for p in problems])
+    budgets = (ctypes.c_double * n)(*[float(p["budget"]) for p in problems])
+    vdt = vec_dtype(precision)
+    zs = [torch.empty(p["X"].shape[0], dtype=vdt, device=p["X"].device) for p in problems]
+    zptr = (ctypes.c_void_p * n)(*[z.data_ptr() for z in zs])
+    opts = L.FiralRelaxOpts(s, T, _cg(tol, maxit, fixed_iters), beta0, seed,
+                            PRECISIONS[precision], estimator, 0.0)
+    L.check(H.lib.firal_batched_relax(H.ptr, n, pools, h0s, budgets, ctypes.byref(opts), zptr),
+            H.ptr)
+    return zs
+
+
 def round_select(X, h, z, budget, Xo=None, ho=None, lam=1e-3, *, eta=0.0, precision="fp32",
                  handle: Handle | None = None, device="cuda"):
     """Round step (Algorithm 3): returns the selected pool indices (int32, selection order)."""

@@ -73,6 +73,8 @@ Profiler& prof() {
 ProfScope::ProfScope(cudaStream_t s, int i) : st(s), id(i) {
   Profiler& P = prof();
   if (!P.on) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
   std::lock_guard<std::mutex> g(P.mu);
   a = P.get();
   cudaEventRecord(a, st);
@@ -334,7 +336,7 @@ int32_t problem_create_impl(firal_handle* H, const firal_pool* pool, const firal
 }
 
 int32_t relax_step_impl(firal_problem* P, const firal_relax_opts* o, int32_t t, double budget,
-                        void* z, firal_step_stats* stats) {
+                        void* z, firal_step_stats* stats, bool device_t = false) {
   if (!P || !o || !z) return fail(FIRAL_ERR_ARG, "problem, opts and z must be non-null");
   if (o->s < 1 || o->s > 256) return fail(FIRAL_ERR_ARG, "s must be in [1, 256]");
   if (!(budget > 0)) return fail(FIRAL_ERR_ARG, "budget must be > 0");
@@ -345,8 +347,10 @@ int32_t relax_step_impl(firal_problem* P, const firal_relax_opts* o, int32_t t, 
   FIRAL_TRY(P->U.ensure(vb));
   FIRAL_TRY(P->W.ensure(vb));
   FIRAL_TRY(P->HU.ensure(vb));
-  // line 4: probes
-  FIRAL_TRY(probes(P->dbl, P->V.p, o->seed, t, s, P->D, st));
+  // line 4: probes (step index from the device counter when replayed from a graph)
+  if (device_t) FIRAL_TRY(P->tdev.ensure(sizeof(int64_t)));
+  FIRAL_TRY(probes(P->dbl, P->V.p, o->seed, t, s, P->D, st,
+                   device_t ? P->tdev.as<int64_t>() : nullptr));
   // line 5: preconditioner from Sigma_z (z copied into the pool part of w_sig)
   FIRAL_TRY(setup_sigma(P, z, true));
   FIRAL_TRY(ensure_sp(P));
@@ -375,6 +379,7 @@ int32_t relax_step_impl(firal_problem* P, const firal_relax_opts* o, int32_t t, 
   void* zdev = (char*)P->w_sig.p + P->m * vsize(P);
   FIRAL_TRY(md_step_simt(P->dbl, zdev, P->g.p, P->n, budget, o->beta0, red, st));
   FIRAL_CUDA_TRY(cudaMemcpyAsync(z, zdev, P->n * vsize(P), cudaMemcpyDeviceToDevice, st));
+  if (device_t) FIRAL_TRY(tick(P->tdev.as<int64_t>(), st));
   if (stats) {
     double h[4];
     FIRAL_CUDA_TRY(cudaMemcpyAsync(h, red + 1536, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -486,6 +491,86 @@ int32_t round_impl(firal_problem* P, const void* zr, int32_t b, const firal_roun
   rel();
 #undef TRYR
   return read_flags(P->H);
+}
+
+// ------------------------------------------------------------------------------------------
+// CUDA-graph replay of MD iterations.  One step runs eagerly (it sizes every workspace), the
+// next is captured with the step index read from the device counter, and the graph is
+// replayed for the remaining iterations.  Only fixed-iteration CG (no host reads) qualifies.
+// ------------------------------------------------------------------------------------------
+struct StreamSet {
+  std::vector<cudaStream_t> st;
+  std::vector<cudaEvent_t> ev;
+  ~StreamSet() {
+    for (auto e : ev) cudaEventDestroy(e);
+    for (auto s : st) cudaStreamDestroy(s);
+  }
+  int32_t make(int n) {
+    for (int i = 0; i < n; ++i) {
+      cudaStream_t s;
+      cudaEvent_t e;
+      FIRAL_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+      st.push_back(s);
+      FIRAL_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      ev.push_back(e);
+    }
+    return FIRAL_OK;
+  }
+};
+
+// Run MD iterations t_begin+1 .. t_end-1 of every problem (step t_begin already run eagerly)
+// by capturing one batched iteration into a graph on `cap` and replaying it.
+int32_t replay_steps(firal_handle* H, std::vector<firal_problem*>& probs,
+                     const std::vector<firal_relax_opts>& opts, const std::vector<double>& budgets,
+                     const std::vector<void*>& zs, int32_t t_next, int32_t t_end) {
+  if (t_next >= t_end) return FIRAL_OK;
+  cudaStream_t user = H->stream;
+  const int np = (int)probs.size();
+  const int nstreams = np < 64 ? np : 64;
+  StreamSet ss;
+  FIRAL_TRY(ss.make(nstreams + 1));
+  cudaStream_t cap = ss.st[nstreams];
+  cudaEvent_t fork = ss.ev[nstreams];
+  // device step counters start at t_next; wait for the eager work first
+  FIRAL_CUDA_TRY(cudaEventRecord(fork, user));
+  FIRAL_CUDA_TRY(cudaStreamWaitEvent(cap, fork, 0));
+  for (int p = 0; p < np; ++p) {
+    FIRAL_TRY(probs[p]->tdev.ensure(sizeof(int64_t)));
+    FIRAL_TRY(set_step(probs[p]->tdev.as<int64_t>(), t_next, cap));
+  }
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int32_t rc = FIRAL_OK;
+  FIRAL_CUDA_TRY(cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed));
+  cudaEventRecord(fork, cap);
+  for (int i = 0; i < nstreams; ++i) cudaStreamWaitEvent(ss.st[i], fork, 0);
+  for (int p = 0; p < np && rc == FIRAL_OK; ++p) {
+    H->stream = ss.st[p % nstreams];
+    rc = relax_step_impl(probs[p], &opts[p], 0, budgets[p], zs[p], nullptr, true);
+  }
+  H->stream = user;
+  for (int i = 0; i < nstreams; ++i) {
+    cudaEventRecord(ss.ev[i], ss.st[i]);
+    cudaStreamWaitEvent(cap, ss.ev[i], 0);
+  }
+  cudaError_t e = cudaStreamEndCapture(cap, &graph);
+  if (rc != FIRAL_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return fail(FIRAL_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(FIRAL_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  for (int t = t_next; t < t_end && e == cudaSuccess; ++t) e = cudaGraphLaunch(exec, cap);
+  if (e == cudaSuccess) {
+    cudaEventRecord(fork, cap);
+    e = cudaStreamWaitEvent(user, fork, 0);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cap);
+  cudaGraphExecDestroy(exec);
+  if (e != cudaSuccess) return fail(FIRAL_ERR_CUDA, std::string("graph replay: ") + cudaGetErrorString(e));
+  return FIRAL_OK;
 }
 
 firal_relax_opts default_relax_opts() {
@@ -624,7 +709,7 @@ int32_t firal_problem_destroy(firal_problem* P) {
                   &P->Minv, &P->HoBlk, &P->walpha, &P->Dpart, &P->syrk_part, &P->cgX, &P->cgR,
                   &P->cgP, &P->cgQ, &P->cgZ, &P->cgcols, &P->cgpart1, &P->cgpart2, &P->V, &P->U,
                   &P->W, &P->HU, &P->g, &P->red, &P->zsave, &P->Xb, &P->Hb, &P->HbT, &P->Pb, &P->vmean, &P->qmean, &P->XwT, &P->gq_ab,
-                  &P->gq_m, &P->gq_part, &P->rtab, &P->rM})
+                  &P->gq_m, &P->gq_part, &P->rtab, &P->rM, &P->tdev})
     b->release();
   delete P;
   return FIRAL_OK;
@@ -656,6 +741,16 @@ int32_t firal_relax(firal_handle* H, const firal_pool* pool, const firal_hess0* 
   const bool need_stats = fhat_hist || stats || o.md_tol > 0;
   int it = 0, cg_total = 0;
   double prev = 0.0, last = 0.0;
+  if (rc == FIRAL_OK && !need_stats && o.cg.fixed_iters > 0 && o.T > 1) {
+    // first iteration eagerly, the rest replayed from a CUDA graph
+    rc = relax_step_impl(P, &o, 0, budget, z_out, nullptr);
+    std::vector<firal_problem*> ps{P};
+    std::vector<firal_relax_opts> os{o};
+    std::vector<double> bs{budget};
+    std::vector<void*> zs{z_out};
+    if (rc == FIRAL_OK) rc = replay_steps(H, ps, os, bs, zs, 1, o.T);
+    it = o.T;
+  }
   for (; rc == FIRAL_OK && it < o.T; ++it) {
     rc = relax_step_impl(P, &o, it, budget, z_out, need_stats ? &ss : nullptr);
     if (rc != FIRAL_OK) break;
@@ -677,6 +772,45 @@ int32_t firal_relax(firal_handle* H, const firal_pool* pool, const firal_hess0* 
     stats->cg_iters_total = cg_total;
   }
   firal_problem_destroy(P);
+  return record(H, rc);
+}
+
+int32_t firal_batched_relax(firal_handle* H, int32_t nproblems, const firal_pool* pools,
+                            const firal_hess0* hess0s, const double* budgets,
+                            const firal_relax_opts* opts, void* const* z_outs) {
+  if (!H || nproblems < 1 || !pools || !budgets || !opts || !z_outs)
+    return record(H, fail(FIRAL_ERR_ARG, "bad batched_relax arguments"));
+  const firal_relax_opts& o = *opts;
+  std::vector<firal_problem*> probs(nproblems, nullptr);
+  auto destroy_all = [&]() {
+    for (auto* p : probs) firal_problem_destroy(p);
+  };
+  int32_t rc = FIRAL_OK;
+  for (int p = 0; p < nproblems && rc == FIRAL_OK; ++p) {
+    if (!z_outs[p] || !(budgets[p] > 0)) rc = fail(FIRAL_ERR_ARG, "bad z_out or budget");
+    if (rc == FIRAL_OK)
+      rc = problem_create_impl(H, &pools[p], hess0s ? &hess0s[p] : nullptr, o.precision, &probs[p]);
+    if (rc == FIRAL_OK)
+      rc = fill_weights(probs[p]->dbl, z_outs[p], 0, 0.0, nullptr, budgets[p] / probs[p]->n,
+                        probs[p]->n, H->stream);
+  }
+  std::vector<firal_relax_opts> os(nproblems, o);
+  std::vector<double> bs(budgets, budgets + nproblems);
+  std::vector<void*> zs(z_outs, z_outs + nproblems);
+  // iteration 0 eagerly (sizes the workspaces), on the handle's stream
+  for (int p = 0; p < nproblems && rc == FIRAL_OK && o.T > 0; ++p)
+    rc = relax_step_impl(probs[p], &o, 0, bs[p], zs[p], nullptr);
+  if (rc == FIRAL_OK && o.T > 1) {
+    if (o.cg.fixed_iters > 0) {
+      rc = replay_steps(H, probs, os, bs, zs, 1, o.T);
+    } else {
+      for (int t = 1; t < o.T && rc == FIRAL_OK; ++t)
+        for (int p = 0; p < nproblems && rc == FIRAL_OK; ++p)
+          rc = relax_step_impl(probs[p], &o, t, bs[p], zs[p], nullptr);
+    }
+  }
+  if (rc == FIRAL_OK) rc = read_flags(H);
+  destroy_all();
   return record(H, rc);
 }
 

@@ -127,6 +127,7 @@ struct firal_problem {
   firal::DBuf XwT;               // bf16 (h - bf16(h))^T, the low part of h for the block sums
   firal::DBuf gq_ab, gq_m, gq_part;  // tensor-core quadratic forms: [A;B], M~ pairs, partials
   firal::DBuf rtab, rM;          // Round on tensor cores: 8-pair chunk table, M~ hi/lo rows
+  firal::DBuf tdev;              // device-resident MD step counter (graph replays)
   int rtab_d = -1, rtab_chunks = 0;
   int32_t dp = 0, cp = 0;
   int64_t Np = 0;
@@ -139,7 +140,10 @@ int32_t copy_rows(bool dbl, void* dst, const void* a, int64_t ma, const void* b,
 int32_t transpose(bool dbl, void* dst, const void* src, int64_t rows, int cols, cudaStream_t st);
 int32_t fill_weights(bool dbl, void* w, int64_t m, double lab_val, const void* z, double zconst,
                      int64_t n, cudaStream_t st);
-int32_t probes(bool dbl, void* V, uint64_t seed, int64_t t, int s, int64_t D, cudaStream_t st);
+int32_t probes(bool dbl, void* V, uint64_t seed, int64_t t, int s, int64_t D, cudaStream_t st,
+               const int64_t* t_dev = nullptr);
+int32_t tick(int64_t* t_dev, cudaStream_t st);
+int32_t set_step(int64_t* t_dev, int64_t v, cudaStream_t st);
 int32_t syrk_blocks(firal_problem* P, const void* w, double lamS, void* outS, double lamP,
                     double* outP);
 int32_t syrk_reduce_f32(firal_problem* P, const float* partS, const float* partP, int splits,

@@ -153,7 +153,9 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
 }
 
 template <class T>
-__global__ void k_probes(T* V, uint64_t seed, uint64_t t, int s, int64_t D) {
+__global__ void k_probes(T* V, uint64_t seed, uint64_t t_host, const int64_t* t_dev, int s,
+                         int64_t D) {
+  const uint64_t t = t_dev ? (uint64_t)*t_dev : t_host;
   const int64_t total = (int64_t)s * D;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -164,12 +166,30 @@ __global__ void k_probes(T* V, uint64_t seed, uint64_t t, int s, int64_t D) {
   }
 }
 
-int32_t probes(bool dbl, void* V, uint64_t seed, int64_t t, int s, int64_t D, cudaStream_t st) {
+int32_t probes(bool dbl, void* V, uint64_t seed, int64_t t, int s, int64_t D, cudaStream_t st,
+               const int64_t* t_dev) {
   const int g = grid_for((int64_t)s * D, 256);
   ProfScope ps(st, PF_PROBES);
   count_launch();
-  if (dbl) k_probes<double><<<g, 256, 0, st>>>((double*)V, seed, (uint64_t)t, s, D);
-  else k_probes<float><<<g, 256, 0, st>>>((float*)V, seed, (uint64_t)t, s, D);
+  if (dbl) k_probes<double><<<g, 256, 0, st>>>((double*)V, seed, (uint64_t)t, t_dev, s, D);
+  else k_probes<float><<<g, 256, 0, st>>>((float*)V, seed, (uint64_t)t, t_dev, s, D);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  return FIRAL_OK;
+}
+
+__global__ void k_tick(int64_t* t_dev) { *t_dev += 1; }
+__global__ void k_set(int64_t* t_dev, int64_t v) { *t_dev = v; }
+
+int32_t tick(int64_t* t_dev, cudaStream_t st) {
+  count_launch();
+  k_tick<<<1, 1, 0, st>>>(t_dev);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  return FIRAL_OK;
+}
+
+int32_t set_step(int64_t* t_dev, int64_t v, cudaStream_t st) {
+  count_launch();
+  k_set<<<1, 1, 0, st>>>(t_dev, v);
   FIRAL_CUDA_TRY(cudaGetLastError());
   return FIRAL_OK;
 }
