@@ -419,14 +419,19 @@ __global__ void __launch_bounds__(256, 1)
 // D-GEMM (split over the point range)
 // ------------------------------------------------------------------------------------------
 namespace d_cfg {
-constexpr int BM = 128, BN = 256, BK = 64, STAGES = 3;
-constexpr int A_BYTES = BM * BK * 2;      // H^T tile
+constexpr int BM = 128, BN = 256, BK = 64;
+constexpr int MT = 2;                     // class tiles per CTA sharing one built Y tile
+constexpr int A_BYTES = BM * BK * 2;      // one H^T tile
 constexpr int Y_BYTES = BN * BK * 2;      // built operand
-constexpr int XT_MAX = 128 * BK * 2;      // x^T tile (dp rows)
 constexpr int AT_MAX = 16 * BK * 2;       // walpha^T tile (<= 16 probes)
-constexpr int STAGE_BYTES = A_BYTES + Y_BYTES + XT_MAX + AT_MAX;
-constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr int NBUILD = 6;                 // builder warps (2..7)
+template <int DP> struct Stage {
+  static constexpr int XT_BYTES = DP * BK * 2;
+  static constexpr int RAW = MT * A_BYTES + Y_BYTES + XT_BYTES + AT_MAX;
+  static constexpr int BYTES = (RAW + 1023) / 1024 * 1024;
+  static constexpr int STAGES = (3 * BYTES + 2048 <= 227 * 1024) ? 3 : 2;
+  static constexpr int SMEM = STAGES * BYTES + 1024 + 256;
+};
 }  // namespace d_cfg
 
 template <int DP>
@@ -436,14 +441,19 @@ __global__ void __launch_bounds__(256, 1)
                int c, int d, int s, int n_mt, int n_nt, int splits, int64_t kb_per_split,
                int64_t kb_total, int32_t* err) {
   using namespace d_cfg;
+  using St = Stage<DP>;
+  constexpr int STAGES = St::STAGES;
+  constexpr int STAGE_BYTES = St::BYTES;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   TcCtl* ctl = (TcCtl*)(sm + STAGES * STAGE_BYTES);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int PPN = BN / DP;                 // probes per N tile
-  constexpr int XT_BYTES = DP * BK * 2;
+  constexpr int XT_BYTES = St::XT_BYTES;
   constexpr int AT_BYTES = PPN * BK * 2;
-  constexpr uint32_t TX = A_BYTES + XT_BYTES + AT_BYTES;
+  constexpr uint32_t TX = MT * A_BYTES + XT_BYTES + AT_BYTES;
+  // stage layout: A (MT class tiles) | Y | x^T | walpha^T
+  constexpr int OFF_Y = MT * A_BYTES, OFF_XT = OFF_Y + Y_BYTES, OFF_AT = OFF_XT + XT_BYTES;
   if (threadIdx.x == 0) {
     for (int i = 0; i < STAGES; ++i) {
       mbar_init(&ctl->full[i], 1);
@@ -457,7 +467,7 @@ __global__ void __launch_bounds__(256, 1)
     mbar_fence_init();
   }
   if (warp == 1) {
-    tmem_alloc(&ctl->tmem_base, 256);
+    tmem_alloc(&ctl->tmem_base, 512);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -498,9 +508,11 @@ __global__ void __launch_bounds__(256, 1)
         unsigned char* st = sm + stage * STAGE_BYTES;
         mbar_expect_tx(&ctl->full[stage], TX);
         const int x = (int)(kb * BK);
-        tma_load_2d(st, &mapHT, &ctl->full[stage], x, mt * BM);
-        tma_load_2d(st + A_BYTES + Y_BYTES, &mapXT, &ctl->full[stage], x, 0);
-        tma_load_2d(st + A_BYTES + Y_BYTES + XT_MAX, &mapAT, &ctl->full[stage], x, nt * PPN);
+#pragma unroll
+        for (int a = 0; a < MT; ++a)
+          tma_load_2d(st + a * A_BYTES, &mapHT, &ctl->full[stage], x, (mt * MT + a) * BM);
+        tma_load_2d(st + OFF_XT, &mapXT, &ctl->full[stage], x, 0);
+        tma_load_2d(st + OFF_AT, &mapAT, &ctl->full[stage], x, nt * PPN);
         if (++stage == STAGES) {
           stage = 0;
           phase ^= 1;
@@ -537,11 +549,15 @@ __global__ void __launch_bounds__(256, 1)
         }
         tc_fence_after();
         const uint32_t a0 = smem_u32(sm + stage * STAGE_BYTES);
-        const uint32_t y0 = a0 + A_BYTES;
+        const uint32_t y0 = a0 + OFF_Y;
 #pragma unroll
-        for (int k = 0; k < BK / 16; ++k)
-          umma_bf16(tmem, sdesc_sw128(a0 + k * 32), sdesc_sw128(y0 + k * 32), idesc,
-                    (kb != kb0) || k != 0);
+        for (int k = 0; k < BK / 16; ++k) {
+          const uint64_t dy = sdesc_sw128(y0 + k * 32);
+#pragma unroll
+          for (int a = 0; a < MT; ++a)
+            umma_bf16(tmem + a * BN, sdesc_sw128(a0 + a * A_BYTES + k * 32), dy, idesc,
+                      (kb != kb0) || k != 0);
+        }
         umma_commit(&ctl->empty[stage]);
         if (++stage == STAGES) {
           stage = 0;
@@ -572,9 +588,9 @@ __global__ void __launch_bounds__(256, 1)
           break;
         }
         unsigned char* st = sm + stage * STAGE_BYTES;
-        unsigned char* Y = st + A_BYTES;
-        const unsigned char* XT = st + A_BYTES + Y_BYTES;
-        const unsigned char* AT = XT + XT_MAX;
+        unsigned char* Y = st + OFF_Y;
+        const unsigned char* XT = st + OFF_XT;
+        const unsigned char* AT = st + OFF_AT;
         // item = (feature e, 8 consecutive points c8).  A thread keeps one c8 (NBUILD*32 is a
         // multiple of 8), holds walpha of its 8 points for every probe of the tile in registers,
         // reads each x chunk once and writes one Y chunk per probe: rows r = jl*DP + e.  The 8
@@ -619,19 +635,22 @@ __global__ void __launch_bounds__(256, 1)
           break;
         }
         tc_fence_after();
-        const int k = mt * BM + q * 32 + lane;           // class row of this thread
         const int sp = (u / n_nt) / n_mt;
         const int sd = s * d;
-        float* out = Dpart + ((int64_t)sp * c + k) * sd;
-        for (int cc = 0; cc < BN; cc += 32) {
-          float v[32];
-          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + cc, v);
-          if (k < c) {
+#pragma unroll 1
+        for (int a = 0; a < MT; ++a) {
+          const int k = (mt * MT + a) * BM + q * 32 + lane;   // class row of this thread
+          float* out = Dpart + ((int64_t)sp * c + k) * sd;
+          for (int cc = 0; cc < BN; cc += 32) {
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + a * BN + cc, v);
+            if (k < c) {
 #pragma unroll
-            for (int t = 0; t < 32; ++t) {
-              const int col = nt * BN + cc + t;
-              const int j = col / DP, e = col - j * DP;
-              if (j < s && e < d) out[j * d + e] = v[t];
+              for (int t = 0; t < 32; ++t) {
+                const int col = nt * BN + cc + t;
+                const int j = col / DP, e = col - j * DP;
+                if (j < s && e < d) out[j * d + e] = v[t];
+              }
             }
           }
         }
@@ -646,7 +665,7 @@ __global__ void __launch_bounds__(256, 1)
   if (warp == 1) {
     __syncwarp();
     tc_fence_after();
-    tmem_dealloc(tmem, 256);
+    tmem_dealloc(tmem, 512);
   }
 }
 
@@ -1340,7 +1359,7 @@ static int32_t tc_apply_t(firal_problem* P, const float* w, const float* Sblk, c
     FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tc_alpha<DP, 0>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
     FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tc_dterm<DP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        d_cfg::SMEM));
+                                        d_cfg::Stage<DP>::SMEM));
     attr[ai] = true;
   }
   {
@@ -1355,7 +1374,7 @@ static int32_t tc_apply_t(firal_problem* P, const float* w, const float* Sblk, c
   {
     constexpr int PPN = d_cfg::BN / DP;
     const int sd = s * P->d;
-    const int n_mt2 = cp / d_cfg::BM + (cp % d_cfg::BM ? 1 : 0);
+    const int n_mt2 = (cp + d_cfg::MT * d_cfg::BM - 1) / (d_cfg::MT * d_cfg::BM);
     const int n_nt2 = (s * DP + d_cfg::BN - 1) / d_cfg::BN;
     const int64_t kb_total = Np / d_cfg::BK;
     const int tiles = n_mt2 * n_nt2;
@@ -1374,7 +1393,7 @@ static int32_t tc_apply_t(firal_problem* P, const float* w, const float* Sblk, c
     {
     ProfScope ps(st, PF_DTERM);
     count_launch();
-    k_tc_dterm<DP><<<grid2, 256, d_cfg::SMEM, st>>>(mHT, mXT, mAT, P->Dpart.as<float>(), P->N, P->c,
+    k_tc_dterm<DP><<<grid2, 256, d_cfg::Stage<DP>::SMEM, st>>>(mHT, mXT, mAT, P->Dpart.as<float>(), P->N, P->c,
                                              P->d, s, n_mt2, n_nt2, splits, kbps, kb_total,
                                              tc_error_word(P));
     }
