@@ -61,8 +61,12 @@ typedef enum {
 typedef enum {
   FIRAL_FP64 = 0,       /* every step in double (SIMT kernels)                                  */
   FIRAL_FP32 = 1,       /* contractions and vectors in float (SIMT); FP64 dots and factors       */
-  FIRAL_MIXED_BF16 = 2  /* X, h contractions on bf16 tensor cores (tcgen05), FP32 accumulate;    */
-                        /* float vectors, FP64 dots, FP64 block factorisations                    */
+  FIRAL_MIXED_BF16 = 2, /* X, h contractions on bf16 tensor cores (tcgen05), FP32 accumulate;   */
+                        /* float vectors, FP64 dots, FP64 block factorisations; the CG direction */
+                        /* enters the contraction as bf16 hi + lo (about 2^-17 relative)         */
+  FIRAL_MIXED_BF16_FAST = 3  /* as FIRAL_MIXED_BF16, but the CG direction enters the first      */
+                        /* contraction of the Hessian apply as one bf16 operand (2^-9 relative   */
+                        /* rounding per apply), which halves that contraction's tensor work      */
 } firal_precision;
 
 typedef enum { FIRAL_DT_F64 = 0, FIRAL_DT_F32 = 1, FIRAL_DT_BF16 = 2 } firal_dtype;

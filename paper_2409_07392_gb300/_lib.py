@@ -10,7 +10,7 @@ from ctypes import POINTER, c_char_p, c_double, c_int32, c_int64, c_size_t, c_ui
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libfiral.so")
 
-FIRAL_FP64, FIRAL_FP32, FIRAL_MIXED_BF16 = 0, 1, 2
+FIRAL_FP64, FIRAL_FP32, FIRAL_MIXED_BF16, FIRAL_MIXED_BF16_FAST = 0, 1, 2, 3
 FIRAL_DT_F64, FIRAL_DT_F32, FIRAL_DT_BF16 = 0, 1, 2
 STATUS = {0: "FIRAL_OK", -1: "FIRAL_ERR_ARG", -2: "FIRAL_ERR_CUDA", -3: "FIRAL_ERR_NOT_SPD",
           -4: "FIRAL_ERR_CG_NOT_CONVERGED", -5: "FIRAL_ERR_NONFINITE", -6: "FIRAL_ERR_TIMEOUT",

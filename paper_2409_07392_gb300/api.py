@@ -14,7 +14,8 @@ import torch
 
 from . import _lib as L
 
-PRECISIONS = {"fp64": L.FIRAL_FP64, "fp32": L.FIRAL_FP32, "mixed": L.FIRAL_MIXED_BF16}
+PRECISIONS = {"fp64": L.FIRAL_FP64, "fp32": L.FIRAL_FP32, "mixed": L.FIRAL_MIXED_BF16,
+              "mixed_fast": L.FIRAL_MIXED_BF16_FAST}
 
 
 _LIVE_PROBLEMS = weakref.WeakSet()

@@ -158,20 +158,20 @@ int32_t* not_spd_flag(firal_handle* H) { return &H->flags.as<DevFlags>()->not_sp
 // Hessian apply dispatch (tensor cores for FIRAL_MIXED_BF16)
 int32_t apply(firal_problem* P, const void* w, const void* Sblk, const void* V, int s, void* out,
               double* pq) {
-  if (P->prec == FIRAL_MIXED_BF16)
+  if (is_mixed(P->prec))
     return tc_hessian_apply(P, w, Sblk, V, s, out, pq, w == P->w_sig.p ? P->lambda : 0.0);
   return hessian_apply_simt(P, w, Sblk, V, s, out, pq);
 }
 
 int32_t quad(firal_problem* P, const void* A, const void* B, int s, double scale, void* g) {
-  if (P->prec == FIRAL_MIXED_BF16) return tc_quad_forms(P, A, B, s, scale, g);
+  if (is_mixed(P->prec)) return tc_quad_forms(P, A, B, s, scale, g);
   return quad_forms_simt(P, A, B, s, scale, g);
 }
 
 // weighted block sums of the Relax operators (tensor cores for FIRAL_MIXED_BF16)
 int32_t blocks(firal_problem* P, const void* w, double lamS, void* outS, double lamP,
                double* outP) {
-  if (P->prec == FIRAL_MIXED_BF16) return tc_syrk_blocks(P, w, lamS, outS, lamP, outP);
+  if (is_mixed(P->prec)) return tc_syrk_blocks(P, w, lamS, outS, lamP, outP);
   return syrk_blocks(P, w, lamS, outS, lamP, outP);
 }
 
@@ -278,9 +278,9 @@ int32_t problem_create_impl(firal_handle* H, const firal_pool* pool, const firal
                             int32_t precision, firal_problem** out) {
   if (!H || !out) return fail(FIRAL_ERR_ARG, "handle and out must be non-null");
   FIRAL_TRY(validate_pool(pool, h0));
-  if (precision < FIRAL_FP64 || precision > FIRAL_MIXED_BF16)
+  if (precision < FIRAL_FP64 || precision > FIRAL_MIXED_BF16_FAST)
     return fail(FIRAL_ERR_ARG, "unknown precision");
-  if (precision == FIRAL_MIXED_BF16 && !tc_available())
+  if (is_mixed(precision) && !tc_available())
     return fail(FIRAL_ERR_UNSUPPORTED, "tensor-core path not built");
   FIRAL_CUDA_TRY(cudaSetDevice(H->device));
   auto* P = new firal_problem();
@@ -327,7 +327,7 @@ int32_t problem_create_impl(firal_handle* H, const firal_pool* pool, const firal
   TRYC(P->HoBlk.ensure(blk * sizeof(double)));
   TRYC(P->red.ensure(2048 * sizeof(double)));
   TRYC(P->g.ensure((size_t)P->n * vs));
-  if (precision == FIRAL_MIXED_BF16) TRYC(tc_prepare(P));
+  if (is_mixed(precision)) TRYC(tc_prepare(P));
 #undef TRYC
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cleanup(fail(FIRAL_ERR_CUDA, cudaGetErrorString(e)));
@@ -458,7 +458,7 @@ int32_t round_impl(firal_problem* P, const void* zr, int32_t b, const firal_roun
   for (int t = 0; t < b; ++t) {
     // line 7: eq. 14 scores and the masked argmax (tensor cores for FIRAL_MIXED_BF16)
     int npart = np;
-    if (P->prec == FIRAL_MIXED_BF16)
+    if (is_mixed(P->prec))
       TRYR(tc_round_scores(P, M1.p, M2.p, mask.as<uint8_t>(), eta, pv.as<double>(),
                            pi.as<int64_t>(), &npart));
     else

@@ -12,6 +12,11 @@
 
 namespace firal {
 
+inline bool is_mixed(int32_t prec) {
+  return prec == FIRAL_MIXED_BF16 || prec == FIRAL_MIXED_BF16_FAST;
+}
+
+
 // ------------------------------------------------------------------------------------------
 // Error plumbing: every host helper returns a firal_status; CUDA failures carry a detail.
 // ------------------------------------------------------------------------------------------

@@ -10,7 +10,8 @@
 //                producer warps from TMA-staged x^T and walpha^T tiles.
 //
 // The probe block P (CG direction, f32) enters the alpha-GEMM as two bf16 operands P_hi and
-// P_lo = P - P_hi, so the contraction sees P to ~2^-17 relative.  X is stored in bf16 and h
+// P_lo = P - P_hi, so the contraction sees P to ~2^-17 relative (FIRAL_MIXED_BF16), or as
+// bf16(P) alone, 2^-9 relative and half the tensor work (FIRAL_MIXED_BF16_FAST).  X is stored in bf16 and h
 // is rounded to bf16 (independent per-element rounding, averaged by the sums over points).
 //
 // Warp roles (256 threads): warp 0 = TMA producer, warp 1 = MMA issuer (+ TMEM owner),
@@ -105,6 +106,8 @@ __global__ void k_transpose_bf16(bf16* dst, const bf16* src, int64_t rows_p, int
 }
 
 // P (s x [c][d], f32) -> P~ rows (j, part, e), columns k (bf16, K-major), part 0 = hi, 1 = lo
+// (NPART = 2) or rows (j, e) holding bf16(P) alone (NPART = 1)
+template <int NPART>
 __global__ void k_split_probes(bf16* Pt, const float* P, const float* vmean, int s, int c, int d,
                                int dp, int cp, int64_t D) {
   __shared__ float tile[32][33];
@@ -121,9 +124,9 @@ __global__ void k_split_probes(bf16* Pt, const float* P, const float* vmean, int
     if (e >= dp || k >= cp) continue;
     const float v = tile[threadIdx.x][i];
     const bf16 hi = __float2bfloat16_rn(v);
-    const bf16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-    Pt[((int64_t)(j * 2 + 0) * dp + e) * cp + k] = hi;
-    Pt[((int64_t)(j * 2 + 1) * dp + e) * cp + k] = lo;
+    Pt[((int64_t)(j * NPART + 0) * dp + e) * cp + k] = hi;
+    if (NPART == 2)
+      Pt[((int64_t)(j * NPART + 1) * dp + e) * cp + k] = __float2bfloat16_rn(v - __bfloat162float(hi));
   }
 }
 
@@ -135,12 +138,24 @@ __global__ void k_split_probes(bf16* Pt, const float* P, const float* vmean, int
 //     Sigma V = P_perp (Sigma~ (P_perp V)) + lambda_N P_N V,
 // with P_N V = the class mean of V replicated over classes (exact in real arithmetic).
 // ------------------------------------------------------------------------------------------
+// mean[j][e] = (1/c) sum_k V[j][k][e]; one block per probe, 1024 threads = (class group, e),
+// the groups combined in a fixed order (deterministic)
 __global__ void k_class_mean(const float* V, int s, int c, int d, int64_t D, float* mean) {
-  const int j = blockIdx.x, e = threadIdx.x;
-  if (e >= d) return;
+  __shared__ double part[1024];
+  const int j = blockIdx.x;
+  const int dpad = (d + 31) / 32 * 32;
+  const int groups = 1024 / dpad;
+  const int e = threadIdx.x % dpad, g = threadIdx.x / dpad;
   double acc = 0.0;
-  for (int k = 0; k < c; ++k) acc += (double)V[(int64_t)j * D + (int64_t)k * d + e];
-  mean[j * d + e] = (float)(acc / c);
+  if (e < d && g < groups)
+    for (int k = g; k < c; k += groups) acc += (double)V[(int64_t)j * D + (int64_t)k * d + e];
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x < d) {
+    double tot = 0.0;
+    for (int q = 0; q < groups; ++q) tot += part[q * dpad + threadIdx.x];
+    mean[j * d + threadIdx.x] = (float)(tot / c);
+  }
 }
 
 // out = out - qmean + lam_null * vmean (per class block); pq[j c + k] = <V_j[k], out_j[k]>
@@ -196,7 +211,7 @@ constexpr int SMEM_QUAD(int dp) { return SMEM + dp * BM * 2; }
 }  // namespace alpha_cfg
 
 struct TcCtl {   // < 256 bytes
-  uint64_t full[4], empty[4], yfull[4], tfull[2], tempty[2], drain;
+  uint64_t full[4], empty[4], yfull[4], tfull[2], tempty[2], drain, pempty;
   uint32_t tmem_base;
   int abort_w;
 };
@@ -207,7 +222,7 @@ __device__ __forceinline__ void raise_abort(TcCtl* ctl, int32_t* err, int code) 
   atomicExch(err, code);
 }
 
-template <int DP, int MODE>
+template <int DP, int MODE, int NPART>
 __global__ void __launch_bounds__(256, 1)
     k_tc_alpha(const __grid_constant__ CUtensorMap mapH, const __grid_constant__ CUtensorMap mapP,
                const bf16* __restrict__ Xb, const float* __restrict__ w, bf16* __restrict__ aT,
@@ -218,7 +233,8 @@ __global__ void __launch_bounds__(256, 1)
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   TcCtl* ctl = (TcCtl*)(sm + STAGES * STAGE_BYTES);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int PPN = BN / (2 * DP);   // probes per N tile
+  constexpr int PPN = BN / (NPART * DP);   // probes per N tile
+  static_assert(MODE != 2 || NPART == 2, "the quadratic mode reads hi and lo halves");
   // MODE 2: the thread's x row, transposed (column = thread) so reads are conflict-free
   bf16* xsT = (bf16*)(sm + STAGES * STAGE_BYTES + 256);   // after the control block
   if (threadIdx.x == 0) {
@@ -367,13 +383,13 @@ __global__ void __launch_bounds__(256, 1)
         const int j = nt * PPN + jj;
         float sum = 0.0f;
 #pragma unroll 1
-        for (int part = 0; part < 2; ++part) {
+        for (int part = 0; part < NPART; ++part) {
 #pragma unroll 1
           for (int ec = 0; ec < DP; ec += (DP < 32 ? DP : 32)) {
             float v[32];
             float xv[32];
             const int cw = DP < 32 ? DP : 32;
-            const uint32_t col = (uint32_t)((jj * 2 + part) * DP + ec);
+            const uint32_t col = (uint32_t)((jj * NPART + part) * DP + ec);
             if (cw == 32) tmem_ld32(tbase + col, v);
             else tmem_ld16(tbase + col, v);
             const bf16* xr = Xb + (row < Np ? row : 0) * DP + ec;
@@ -395,9 +411,14 @@ __global__ void __launch_bounds__(256, 1)
               if (t < cw) sum = fmaf(xv[t], v[t], sum);
           }
         }
-        if (row < N && j < s) {
-          if (MODE == 0) aT[(int64_t)j * Np + row] = __float2bfloat16_rn(wi * sum);
-          else out32[(int64_t)j * Np + row] = sum;
+        // MODE 0 also zeroes the padding rows N..Np-1: the D-GEMM multiplies them by zero x
+        // and h, and a stale non-finite value there would turn the whole probe into NaN
+        if (j < s) {
+          if (MODE == 0) {
+            if (row < Np) aT[(int64_t)j * Np + row] = __float2bfloat16_rn(row < N ? wi * sum : 0.0f);
+          } else if (row < N) {
+            out32[(int64_t)j * Np + row] = sum;
+          }
         }
       }
       tc_fence_before();
@@ -425,6 +446,7 @@ constexpr int A_BYTES = BM * BK * 2;      // one H^T tile
 constexpr int Y_BYTES = BN * BK * 2;      // built operand
 constexpr int AT_MAX = 16 * BK * 2;       // walpha^T tile (<= 16 probes)
 constexpr int NBUILD = 6;                 // builder warps (2..7)
+constexpr int64_t D_CHAIN = 512;          // K-steps accumulated in TMEM per split at most
 template <int DP> struct Stage {
   static constexpr int XT_BYTES = DP * BK * 2;
   static constexpr int RAW = MT * A_BYTES + Y_BYTES + XT_BYTES + AT_MAX;
@@ -677,12 +699,25 @@ __global__ void __launch_bounds__(256, 1)
 //   S ~ H_hi Z_hi + H_lo Z_hi + H_hi Z_lo,   Z = w x_e x_e' (f32, split into hi + lo),
 // while P (the preconditioner) uses H_hi(1 - H_hi) Z_hi.  A = H^T tiles by TMA; Z and A_P are
 // built in shared memory.  Unit = (128 classes, 128 pairs, point range).
+//
+// Accumulation length.  The tensor core adds each product block into its f32 accumulator with
+// a rounding that is biased (the sum loses magnitude on every add), so a chain of m adds into
+// one accumulator carries a relative bias of roughly m * 2^-25; a split of 200k points is
+// 37,500 adds, a 1e-3 bias that no averaging removes.  S therefore accumulates in TMEM for at
+// most SUB = 8 K-steps (96 adds) at a time, alternating between two short buffers, and four
+// dedicated epilogue warps fold each finished short buffer into a long TMEM accumulator with
+// ordinary round-to-nearest f32 adds while the MMA fills the other.  P only preconditions CG
+// (a biased P changes the iterates, not the solution) and accumulates over the whole unit.
+// TMEM columns: [0,128) S short 0 | [128,256) S short 1 | [256,384) S long | [384,512) P.
 // ------------------------------------------------------------------------------------------
 namespace s_cfg {
 constexpr int BM = 128, BN = 128, BK = 64;
 constexpr int A_BYTES = BM * BK * 2;
 constexpr int Z_BYTES = BN * BK * 2;
 constexpr int NBUILD = 6;
+constexpr int SUB = 8;           // K-steps per short accumulation
+constexpr int THREADS = 384;     // producer, MMA, 6 builder warps, 4 epilogue warps
+constexpr uint32_t COL_LONG = 256, COL_P = 384;
 template <int DP> struct Stage {
   static constexpr int XT_BYTES = DP * BK * 2;
   static constexpr int RAW = 3 * A_BYTES + 2 * Z_BYTES + XT_BYTES;
@@ -693,7 +728,7 @@ template <int DP> struct Stage {
 }  // namespace s_cfg
 
 template <int DP>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(s_cfg::THREADS, 1)
     k_tc_syrk(const __grid_constant__ CUtensorMap mapHT, const __grid_constant__ CUtensorMap mapHL,
               const __grid_constant__ CUtensorMap mapXT, const float* __restrict__ w,
               float* __restrict__ partS, float* __restrict__ partP, int64_t N, int c, int d,
@@ -716,14 +751,17 @@ __global__ void __launch_bounds__(256, 1)
       mbar_init(&ctl->empty[i], 1);
       mbar_init(&ctl->yfull[i], NBUILD);
     }
-    mbar_init(&ctl->tfull[0], 1);
-    mbar_init(&ctl->tempty[0], 4);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&ctl->tfull[i], 1);
+      mbar_init(&ctl->tempty[i], 4);
+    }
+    mbar_init(&ctl->pempty, 4);
     mbar_init(&ctl->drain, 1);
     ctl->abort_w = 0;
     mbar_fence_init();
   }
   if (warp == 1) {
-    tmem_alloc(&ctl->tmem_base, 256);
+    tmem_alloc(&ctl->tmem_base, 512);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -781,54 +819,65 @@ __global__ void __launch_bounds__(256, 1)
     constexpr uint32_t idesc = idesc_bf16_f32(BM, BN);
     int stage = 0;
     uint32_t phase = 0;
-    uint32_t acc_phase = 0;
+    uint32_t gsub = 0;      // short accumulations issued by this CTA
+    uint32_t uidx = 0;      // units started by this CTA
     bool ok = true;
-    for (int u = blockIdx.x; u < nunits && ok && !*abort_w; u += gridDim.x) {
+    for (int u = blockIdx.x; u < nunits && ok && !*abort_w; u += gridDim.x, ++uidx) {
       int mt, nt, sp;
       int64_t kb0, kb1;
       unit_range(u, mt, nt, sp, kb0, kb1);
-      if (!mbar_wait(&ctl->tempty[0], acc_phase ^ 1, abort_w)) {
-        raise_abort(ctl, err, 22);
+      // P of the previous unit must have been read before this unit overwrites it
+      if (uidx > 0 && !mbar_wait(&ctl->pempty, (uidx - 1) & 1, abort_w)) {
+        raise_abort(ctl, err, 26);
         break;
       }
-      tc_fence_after();
-      for (int64_t kb = kb0; kb < kb1; ++kb) {
-        if (!mbar_wait(&ctl->yfull[stage], phase, abort_w)) {
-          raise_abort(ctl, err, 23);
+      for (int64_t c0 = kb0; c0 < kb1 && ok; c0 += SUB, ++gsub) {
+        const int64_t c1 = c0 + SUB < kb1 ? c0 + SUB : kb1;
+        const uint32_t b = gsub & 1, par = (gsub >> 1) & 1;
+        if (!mbar_wait(&ctl->tempty[b], par ^ 1, abort_w)) {
+          raise_abort(ctl, err, 22);
           ok = false;
           break;
         }
         tc_fence_after();
-        const uint32_t ah = smem_u32(sm + stage * St::BYTES);
-        const uint32_t al = ah + OFF_AL, ap = ah + OFF_AP, zh = ah + OFF_ZH, zl = ah + OFF_ZL;
+        const uint32_t tS = tmem + b * BN, tP = tmem + COL_P;
+        for (int64_t kb = c0; kb < c1; ++kb) {
+          if (!mbar_wait(&ctl->yfull[stage], phase, abort_w)) {
+            raise_abort(ctl, err, 23);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t ah = smem_u32(sm + stage * St::BYTES);
+          const uint32_t al = ah + OFF_AL, ap = ah + OFF_AP, zh = ah + OFF_ZH, zl = ah + OFF_ZL;
 #pragma unroll
-        for (int k = 0; k < BK / 16; ++k) {
-          const uint32_t acc = (kb != kb0) || k != 0;
-          const uint64_t dzh = sdesc_sw128(zh + k * 32);
-          umma_bf16(tmem, sdesc_sw128(ah + k * 32), dzh, idesc, acc);
-          umma_bf16(tmem, sdesc_sw128(al + k * 32), dzh, idesc, 1u);
-          umma_bf16(tmem, sdesc_sw128(ah + k * 32), sdesc_sw128(zl + k * 32), idesc, 1u);
-          umma_bf16(tmem + BN, sdesc_sw128(ap + k * 32), dzh, idesc, acc);
+          for (int k = 0; k < BK / 16; ++k) {
+            const uint32_t accS = (kb != c0) || k != 0;
+            const uint32_t accP = (kb != kb0) || k != 0;
+            const uint64_t dzh = sdesc_sw128(zh + k * 32);
+            umma_bf16(tS, sdesc_sw128(ah + k * 32), dzh, idesc, accS);
+            umma_bf16(tS, sdesc_sw128(al + k * 32), dzh, idesc, 1u);
+            umma_bf16(tS, sdesc_sw128(ah + k * 32), sdesc_sw128(zl + k * 32), idesc, 1u);
+            umma_bf16(tP, sdesc_sw128(ap + k * 32), dzh, idesc, accP);
+          }
+          umma_commit(&ctl->empty[stage]);
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1;
+          }
         }
-        umma_commit(&ctl->empty[stage]);
-        if (++stage == STAGES) {
-          stage = 0;
-          phase ^= 1;
-        }
+        if (!ok) break;
+        umma_commit(&ctl->tfull[b]);
       }
-      if (!ok) break;
-      umma_commit(&ctl->tfull[0]);
-      acc_phase ^= 1;
     }
     umma_commit(&ctl->drain);
     mbar_wait_drain(&ctl->drain, 0);
-  } else if (warp >= 2) {
+  } else if (warp >= 2 && warp < 2 + NBUILD) {
     const int bw = warp - 2;
     const int tid_b = bw * 32 + lane;
     const int c8 = tid_b & 7;            // fixed point chunk of this thread
     int stage = 0;
     uint32_t phase = 0;
-    uint32_t acc_phase = 0;
     bool ok = true;
     const __nv_bfloat162 one2 = __floats2bfloat162_rn(1.0f, 1.0f);
     constexpr int RPT = (BN + NBUILD * 4 - 1) / (NBUILD * 4);   // Z rows per thread
@@ -905,31 +954,70 @@ __global__ void __launch_bounds__(256, 1)
         }
       }
       if (!ok) break;
-      if (warp >= 4) {
-        const int q = warp & 3;
-        if (!mbar_wait(&ctl->tfull[0], acc_phase, abort_w)) {
+    }
+  } else if (warp >= 2 + NBUILD) {
+    // ---------------- epilogue: thread = class row k of the unit (TMEM lane 32 q + lane)
+    const int q = warp & 3;
+    const uint32_t lanes = (uint32_t)(q * 32) << 16;
+    uint32_t gsub = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; u < nunits && ok && !*abort_w; u += gridDim.x) {
+      int mt, nt, sp;
+      int64_t kb0, kb1;
+      unit_range(u, mt, nt, sp, kb0, kb1);
+      const int k = mt * BM + q * 32 + lane;
+      for (int64_t c0 = kb0; c0 < kb1; c0 += SUB, ++gsub) {
+        const bool first = c0 == kb0, last = c0 + SUB >= kb1;
+        const uint32_t b = gsub & 1, par = (gsub >> 1) & 1;
+        if (!mbar_wait(&ctl->tfull[b], par, abort_w)) {
           raise_abort(ctl, err, 25);
+          ok = false;
           break;
         }
         tc_fence_after();
-        const int k = mt * BM + q * 32 + lane;
-        for (int which = 0; which < 2; ++which) {
-          float* out = (which == 0 ? partS : partP) + ((int64_t)sp * c + k) * d * d;
+        const uint32_t tS = tmem + lanes + b * BN, tL = tmem + lanes + COL_LONG;
+        if (!last) {
+          // S long (+)= S short: round-to-nearest f32 adds
           for (int cc = 0; cc < BN; cc += 32) {
             float v[32];
-            tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + which * BN + cc, v);
-            if (k < c) {
-              int e = 0, e2 = 0;
-              const int p0 = nt * BN + cc;
-              if (p0 < npairs) pair_of(p0, d, e, e2);
+            tmem_ld32(tS + cc, v);
+            if (!first) {
+              float l[32];
+              tmem_ld32(tL + cc, l);
 #pragma unroll
-              for (int t = 0; t < 32; ++t) {
-                if (p0 + t < npairs) {
-                  out[e * d + e2] = v[t];
-                  out[e2 * d + e] = v[t];
-                  if (++e2 == d) {
-                    ++e;
-                    e2 = e;
+              for (int t = 0; t < 32; ++t) v[t] += l[t];
+            }
+            tmem_st32(tL + cc, v);
+          }
+        } else {
+          for (int which = 0; which < 2; ++which) {
+            float* out = (which == 0 ? partS : partP) + ((int64_t)sp * c + k) * d * d;
+            for (int cc = 0; cc < BN; cc += 32) {
+              float v[32];
+              if (which == 0) {
+                tmem_ld32(tS + cc, v);
+                if (!first) {
+                  float l[32];
+                  tmem_ld32(tL + cc, l);
+#pragma unroll
+                  for (int t = 0; t < 32; ++t) v[t] += l[t];
+                }
+              } else {
+                tmem_ld32(tmem + lanes + COL_P + cc, v);
+              }
+              if (k < c) {
+                int e = 0, e2 = 0;
+                const int p0 = nt * BN + cc;
+                if (p0 < npairs) pair_of(p0, d, e, e2);
+#pragma unroll
+                for (int t = 0; t < 32; ++t) {
+                  if (p0 + t < npairs) {
+                    out[e * d + e2] = v[t];
+                    out[e2 * d + e] = v[t];
+                    if (++e2 == d) {
+                      ++e;
+                      e2 = e;
+                    }
                   }
                 }
               }
@@ -938,16 +1026,18 @@ __global__ void __launch_bounds__(256, 1)
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&ctl->tempty[0]);
+        if (lane == 0) {
+          mbar_arrive(&ctl->tempty[b]);
+          if (last) mbar_arrive(&ctl->pempty);
+        }
       }
-      acc_phase ^= 1;
     }
   }
   __syncthreads();
   if (warp == 1) {
     __syncwarp();
     tc_fence_after();
-    tmem_dealloc(tmem, 256);
+    tmem_dealloc(tmem, 512);
   }
 }
 
@@ -1320,7 +1410,7 @@ int32_t tc_prepare(firal_problem* P) {
   return FIRAL_OK;
 }
 
-template <int DP>
+template <int DP, int NPART>
 static int32_t tc_apply_t(firal_problem* P, const float* w, const float* Sblk, const float* V,
                           int s, float* out, double* pq, double lam_null) {
   using namespace alpha_cfg;
@@ -1328,11 +1418,15 @@ static int32_t tc_apply_t(firal_problem* P, const float* w, const float* Sblk, c
   const int64_t Np = P->Np;
   const int cp = P->cp;
   const int sp16 = (s + 15) / 16 * 16;
-  // P~ (hi/lo) and walpha^T buffers
-  const int64_t prow = (int64_t)s * 2 * DP;
+  // P~ (hi/lo, or bf16 alone) and walpha^T buffers
+  const int64_t prow = (int64_t)s * NPART * DP;
   const int64_t prow_p = (prow + BN - 1) / BN * BN;
   FIRAL_TRY(P->Pb.ensure((size_t)prow_p * cp * 2));
   FIRAL_TRY(P->walpha.ensure((size_t)sp16 * Np * 2));
+  // probe rows s..sp16-1 of walpha^T feed only D columns that are discarded; keep them finite
+  if (sp16 > s)
+    FIRAL_CUDA_TRY(cudaMemsetAsync(P->walpha.as<bf16>() + (int64_t)s * Np, 0,
+                                   (size_t)(sp16 - s) * Np * 2, st));
   if (prow_p > prow)
     FIRAL_CUDA_TRY(cudaMemsetAsync(P->Pb.as<bf16>() + prow * cp, 0, (prow_p - prow) * cp * 2, st));
   FIRAL_TRY(P->vmean.ensure((size_t)s * P->d * sizeof(float)));
@@ -1341,8 +1435,8 @@ static int32_t tc_apply_t(firal_problem* P, const float* w, const float* Sblk, c
   {
   ProfScope ps(st, PF_SPLIT);
   count_launch(2);
-  k_class_mean<<<s, mthreads, 0, st>>>(V, s, P->c, P->d, P->D, P->vmean.as<float>());
-  k_split_probes<<<dim3((unsigned)(cp + 31) / 32, DP / 32 > 0 ? DP / 32 : 1, s), dim3(32, 8), 0,
+  k_class_mean<<<s, 1024, 0, st>>>(V, s, P->c, P->d, P->D, P->vmean.as<float>());
+  k_split_probes<NPART><<<dim3((unsigned)(cp + 31) / 32, DP / 32 > 0 ? DP / 32 : 1, s), dim3(32, 8), 0,
                    st>>>(P->Pb.as<bf16>(), V, P->vmean.as<float>(), s, P->c, P->d, DP, cp,
                            P->D);
   }
@@ -1356,7 +1450,7 @@ static int32_t tc_apply_t(firal_problem* P, const float* w, const float* Sblk, c
   static bool attr[4] = {false, false, false, false};
   const int ai = DP == 16 ? 0 : DP == 32 ? 1 : DP == 64 ? 2 : 3;
   if (!attr[ai]) {
-    FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tc_alpha<DP, 0>,
+    FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tc_alpha<DP, 0, NPART>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
     FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tc_dterm<DP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         d_cfg::Stage<DP>::SMEM));
@@ -1365,7 +1459,7 @@ static int32_t tc_apply_t(firal_problem* P, const float* w, const float* Sblk, c
   {
   ProfScope ps(st, PF_ALPHA);
   count_launch();
-  k_tc_alpha<DP, 0><<<grid, 256, SMEM, st>>>(mH, mP, P->Xb.as<bf16>(), w, P->walpha.as<bf16>(),
+  k_tc_alpha<DP, 0, NPART><<<grid, 256, SMEM, st>>>(mH, mP, P->Xb.as<bf16>(), w, P->walpha.as<bf16>(),
                                              nullptr, P->N, Np, s, cp / BK, n_mt, n_nt, 0, P->d,
                                              tc_error_word(P));
   }
@@ -1380,6 +1474,17 @@ static int32_t tc_apply_t(firal_problem* P, const float* w, const float* Sblk, c
     const int tiles = n_mt2 * n_nt2;
     int splits = (int)std::max<int64_t>(1, std::min<int64_t>((4LL * sms + tiles - 1) / tiles,
                                                             kb_total / 4 > 0 ? kb_total / 4 : 1));
+    // at most D_CHAIN K-steps (4 adds each) per accumulator: the tensor core's f32 accumulation
+    // loses about 2^-25 of the running sum per add, so the chain length bounds the bias.  When
+    // that raises the split count, round it up to whole waves of units where that costs < 2x.
+    const int64_t need = (kb_total + d_cfg::D_CHAIN - 1) / d_cfg::D_CHAIN;
+    if (need > splits) {
+      int64_t g = tiles, r = sms;
+      while (r) { const int64_t t = g % r; g = r; r = t; }
+      const int64_t m = sms / g;                      // splits per whole wave
+      const int64_t up = (need + m - 1) / m * m;
+      splits = (int)(up < 2 * need ? up : need);
+    }
     if (forced_splits() > 0) splits = (int)std::min<int64_t>(forced_splits(), kb_total);
     const int64_t kbps = (kb_total + splits - 1) / splits;
     splits = (int)((kb_total + kbps - 1) / kbps);
@@ -1401,7 +1506,7 @@ static int32_t tc_apply_t(firal_problem* P, const float* w, const float* Sblk, c
     FIRAL_TRY(combine_f32(P, Sblk, V, splits, s, out, nullptr, P->vmean.as<float>()));
     ProfScope ps(st, PF_COMBINE);
     count_launch(2);
-    k_class_mean<<<s, mthreads, 0, st>>>(out, s, P->c, P->d, P->D, P->qmean.as<float>());
+    k_class_mean<<<s, 1024, 0, st>>>(out, s, P->c, P->d, P->D, P->qmean.as<float>());
     k_project<<<dim3(P->c, (s + 3) / 4), mthreads, 0, st>>>(
         out, P->qmean.as<float>(), P->vmean.as<float>(), V, lam_null, s, P->c, P->d, P->D, pq);
     FIRAL_CUDA_TRY(cudaGetLastError());
@@ -1425,6 +1530,7 @@ static int32_t tc_syrk_t(firal_problem* P, const float* w, double lamS, float* o
   const int tiles = n_mt * n_nt;
   int splits = (int)std::max<int64_t>(1, std::min<int64_t>((4LL * sms + tiles - 1) / tiles,
                                                           kb_total / 8 > 0 ? kb_total / 8 : 1));
+  if (forced_splits() > 0) splits = (int)std::min<int64_t>(forced_splits(), kb_total);
   const int64_t kbps = (kb_total + splits - 1) / splits;
   splits = (int)((kb_total + kbps - 1) / kbps);
   const int64_t per = (int64_t)c * d * d;
@@ -1446,7 +1552,7 @@ static int32_t tc_syrk_t(firal_problem* P, const float* w, double lamS, float* o
   {
     ProfScope ps(st, PF_SYRK);
     count_launch();
-    k_tc_syrk<DP><<<std::min(units, sms), 256, St::SMEM, st>>>(
+    k_tc_syrk<DP><<<std::min(units, sms), THREADS, St::SMEM, st>>>(
         mHT, mHL, mXT, w, pS, pP, P->N, c, d, npairs, n_mt, n_nt, splits, kbps, kb_total,
         tc_error_word(P));
   }
@@ -1532,7 +1638,7 @@ static int32_t tc_quad_t(firal_problem* P, const float* A, const float* B, int s
   FIRAL_TRY(P->vmean.ensure((size_t)2 * s * d * sizeof(float)));
   ProfScope ps(st, PF_QUAD);
   count_launch(1);
-  k_class_mean<<<2 * s, mthreads, 0, st>>>(AB, 2 * s, c, d, D, P->vmean.as<float>());
+  k_class_mean<<<2 * s, 1024, 0, st>>>(AB, 2 * s, c, d, D, P->vmean.as<float>());
   // term 1: M~ pairs (hi | lo per 128-pair tile) and the quadratic alpha-GEMM
   const int npairs = d * (d + 1) / 2;
   const int n_nt1 = (npairs + 127) / 128;
@@ -1552,9 +1658,9 @@ static int32_t tc_quad_t(firal_problem* P, const float* A, const float* B, int s
   static bool attr[4] = {false, false, false, false};
   const int ai = DP == 16 ? 0 : DP == 32 ? 1 : DP == 64 ? 2 : 3;
   if (!attr[ai]) {
-    FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tc_alpha<DP, 1>,
+    FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tc_alpha<DP, 1, 2>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
-    FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tc_alpha<DP, 2>,
+    FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tc_alpha<DP, 2, 2>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         SMEM_QUAD(DP)));
     attr[ai] = true;
@@ -1565,7 +1671,7 @@ static int32_t tc_quad_t(firal_problem* P, const float* A, const float* B, int s
     FIRAL_TRY(make_map(&mH, P->Hb.p, Np, cp, BM, BK, true));
     FIRAL_TRY(make_map(&mM, P->gq_m.p, mrows, cp, BN, BK, true));
     count_launch(1);
-    k_tc_alpha<DP, 2><<<std::min(n_mt * n_nt1, sms), 256, SMEM_QUAD(DP), st>>>(
+    k_tc_alpha<DP, 2, 2><<<std::min(n_mt * n_nt1, sms), 256, SMEM_QUAD(DP), st>>>(
         mH, mM, P->Xb.as<bf16>(), nullptr, nullptr, part1, P->N, Np, 0, cp / BK, n_mt, n_nt1,
         npairs, d, tc_error_word(P));
     FIRAL_CUDA_TRY(cudaGetLastError());
@@ -1579,7 +1685,7 @@ static int32_t tc_quad_t(firal_problem* P, const float* A, const float* B, int s
     if (prow_p > prow)
       FIRAL_CUDA_TRY(cudaMemsetAsync(P->Pb.as<bf16>() + prow * cp, 0, (prow_p - prow) * cp * 2, st));
     count_launch(1);
-    k_split_probes<<<dim3((unsigned)(cp + 31) / 32, DP / 32 > 0 ? DP / 32 : 1, s2), dim3(32, 8), 0,
+    k_split_probes<2><<<dim3((unsigned)(cp + 31) / 32, DP / 32 > 0 ? DP / 32 : 1, s2), dim3(32, 8), 0,
                      st>>>(P->Pb.as<bf16>(), AB, P->vmean.as<float>(), s2, c, d, DP, cp, D);
     FIRAL_CUDA_TRY(cudaGetLastError());
     CUtensorMap mH, mP;
@@ -1587,7 +1693,7 @@ static int32_t tc_quad_t(firal_problem* P, const float* A, const float* B, int s
     FIRAL_TRY(make_map(&mP, P->Pb.p, prow_p, cp, BN, BK, true));
     const int n_nt2 = (int)(prow_p / BN);
     count_launch(1);
-    k_tc_alpha<DP, 1><<<std::min(n_mt * n_nt2, sms), 256, SMEM, st>>>(
+    k_tc_alpha<DP, 1, 2><<<std::min(n_mt * n_nt2, sms), 256, SMEM, st>>>(
         mH, mP, P->Xb.as<bf16>(), nullptr, nullptr, a32, P->N, Np, s2, cp / BK, n_mt, n_nt2, 0,
         d, tc_error_word(P));
     FIRAL_CUDA_TRY(cudaGetLastError());
@@ -1666,14 +1772,25 @@ int32_t tc_round_scores(firal_problem* P, const void* M1, const void* M2, const 
   }
 }
 
+template <int NPART>
+static int32_t tc_apply_dp(firal_problem* P, const void* w, const void* Sblk, const void* V, int s,
+                           void* out, double* pq, double lam_null) {
+  const float* ww = (const float*)w;
+  const float* sb = (const float*)Sblk;
+  const float* vv = (const float*)V;
+  float* o = (float*)out;
+  switch (P->dp) {
+    case 16: return tc_apply_t<16, NPART>(P, ww, sb, vv, s, o, pq, lam_null);
+    case 32: return tc_apply_t<32, NPART>(P, ww, sb, vv, s, o, pq, lam_null);
+    case 64: return tc_apply_t<64, NPART>(P, ww, sb, vv, s, o, pq, lam_null);
+    default: return tc_apply_t<128, NPART>(P, ww, sb, vv, s, o, pq, lam_null);
+  }
+}
+
 int32_t tc_hessian_apply(firal_problem* P, const void* w, const void* Sblk, const void* V, int s,
                          void* out, double* pq, double lam_null) {
-  switch (P->dp) {
-    case 16: return tc_apply_t<16>(P, (const float*)w, (const float*)Sblk, (const float*)V, s, (float*)out, pq, lam_null);
-    case 32: return tc_apply_t<32>(P, (const float*)w, (const float*)Sblk, (const float*)V, s, (float*)out, pq, lam_null);
-    case 64: return tc_apply_t<64>(P, (const float*)w, (const float*)Sblk, (const float*)V, s, (float*)out, pq, lam_null);
-    default: return tc_apply_t<128>(P, (const float*)w, (const float*)Sblk, (const float*)V, s, (float*)out, pq, lam_null);
-  }
+  if (P->prec == FIRAL_MIXED_BF16_FAST) return tc_apply_dp<1>(P, w, Sblk, V, s, out, pq, lam_null);
+  return tc_apply_dp<2>(P, w, Sblk, V, s, out, pq, lam_null);
 }
 
 int32_t tc_quad_forms(firal_problem* P, const void* A, const void* B, int s, double scale,

@@ -36,20 +36,21 @@ def relerr(a, b):
     return np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b)
 
 
-def make(api, handle, p):
+def make(api, handle, p, precision="mixed"):
     X = dev(p.X).to(torch.bfloat16) if p.x_bf16 else dev(p.X)
     Xo = dev(p.Xo).to(torch.bfloat16) if p.x_bf16 else dev(p.Xo)
-    return api.Problem(handle, X, dev(p.h), Xo, dev(p.ho), p.lam, precision="mixed")
+    return api.Problem(handle, X, dev(p.h), Xo, dev(p.ho), p.lam, precision=precision)
 
 
 MIXED_SHAPES = [(300, 20, 10, 3), (1000, 50, 10, 5), (517, 64, 37, 4), (260, 128, 4, 3),
                 (2049, 16, 17, 8), (2049, 33, 17, 20), (2049, 16, 17, 20), (4100, 64, 130, 16)]
 
 
+@pytest.mark.parametrize("precision", ["mixed", "mixed_fast"])
 @pytest.mark.parametrize("n,d,c,s", MIXED_SHAPES)
-def test_mixed_hessian_apply(api, handle, n, d, c, s):
+def test_mixed_hessian_apply(api, handle, n, d, c, s, precision):
     p = make_problem(n, d, c, seed=n + c, x_dtype="bf16", h_dtype="float32", m_o=c)
-    prob = make(api, handle, p)
+    prob = make(api, handle, p, precision)
     rng = np.random.default_rng(0)
     V = rng.standard_normal((d * c, s))
     z = rng.uniform(0.1, 1.0, n)
@@ -67,9 +68,13 @@ def test_mixed_hessian_apply(api, handle, n, d, c, s):
                   f"classes {sorted(set((q // d).tolist()))[:20]} "
                   f"features {sorted(set((q % d).tolist()))[:20]}")
     e1, e2 = relerr(got_sig, ref_sig), relerr(got_hp, ref_hp)
-    print(f"mixed apply n={n} d={d} c={c} s={s}: sigma {e1:.2e}  H_p {e2:.2e}")
+    print(f"{precision} apply n={n} d={d} c={c} s={s}: sigma {e1:.2e}  H_p {e2:.2e}")
     # per-element bf16 rounding (2^-9) of h and of walpha x averages over the n-point sums
     tol = 6.0 * 2.0 ** -9 / np.sqrt(n) + 2e-6
+    if precision == "mixed_fast":
+        # plus the rounding of V itself (2^-9 per entry, shared by every point): the
+        # low-rank term is a linear map of V, so its relative error is at most 2^-9
+        tol += 2.0 ** -9
     assert e1 < tol and e2 < tol
 
 
@@ -88,18 +93,19 @@ def test_mixed_apply_keeps_the_softmax_null_space(api, handle):
     assert np.abs(hp).max() < 1e-6 * np.abs(V).max()
 
 
-def test_mixed_relax_fhat_and_z_vs_exact_solve_oracle(api, handle):
+@pytest.mark.parametrize("precision", ["mixed", "mixed_fast"])
+def test_mixed_relax_fhat_and_z_vs_exact_solve_oracle(api, handle, precision):
     """Mixed Relax (CG to 1e-5) vs the oracle with dense solves and the same probes:
     f^ and z within 1e-3 relative (the stated accuracy target)."""
     p = make_problem(20000, 16, 10, seed=3, x_dtype="bf16", h_dtype="float32")
-    prob = make(api, handle, p)
+    prob = make(api, handle, p, precision)
     b, s, T = 20.0, 8, 3
     z = torch.full((p.n,), b / p.n, dtype=torch.float32, device="cuda")
     opts = prob.relax_opts(s=s, T=T, tol=1e-5, maxit=300, seed=4)
     fh = [prob.relax_step(opts, t, b, z)["fhat"] for t in range(T)]
     z_ref, info = approx.relax(p, b, s=s, T=T, seed=4, solve="direct")
     ef, ez = relerr(fh, np.array(info["fhat"])), relerr(z.cpu().numpy(), z_ref)
-    print(f"mixed relax: fhat {ef:.2e}  z {ez:.2e}")
+    print(f"{precision} relax: fhat {ef:.2e}  z {ez:.2e}")
     assert ef < 1e-3 and ez < 1e-3
 
 
@@ -131,7 +137,7 @@ def test_fixed_iteration_relax_mixed_and_fp32_vs_oracle(api, handle):
     b, s, T = 20.0, 8, 2
     z_ref, info = approx.relax(p, b, s=s, T=T, seed=4, fixed_iters=10)
     errs = {}
-    for prec in ("mixed", "fp32"):
+    for prec in ("mixed", "mixed_fast", "fp32"):
         X = dev(p.X).to(torch.bfloat16)
         Xo = dev(p.Xo).to(torch.bfloat16)
         prob = api.Problem(handle, X, dev(p.h), Xo, dev(p.ho), p.lam, precision=prec)
@@ -142,6 +148,7 @@ def test_fixed_iteration_relax_mixed_and_fp32_vs_oracle(api, handle):
         prob.close()
     print("fixed-iteration relax vs oracle (fhat, z):", errs)
     assert errs["mixed"][0] < 1e-3 and errs["mixed"][1] < 1e-3
+    assert errs["mixed_fast"][0] < 1e-3 and errs["mixed_fast"][1] < 1e-3
 
 
 @pytest.mark.parametrize("n,d,c,b", [(3000, 20, 10, 10), (6000, 64, 37, 12), (2500, 128, 5, 8),
