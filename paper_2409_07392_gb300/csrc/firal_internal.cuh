@@ -129,7 +129,8 @@ struct firal_problem {
   // tensor-core layout (FIRAL_MIXED_BF16): bf16 X (N x dp), bf16 h (Np x cp), its transpose
   firal::DBuf Xb, Hb, HbT, Pb;   // Pb: bf16 (hi/lo) operand of the probe block
   firal::DBuf vmean, qmean;      // class means of the probe block / of the raw apply (s x d)
-  firal::DBuf XwT;               // bf16 (h - bf16(h))^T, the low part of h for the block sums
+  firal::DBuf Aw;                // block sums: (w h)^T hi, lo and (w h (1 - h))^T (3 x cp x Np)
+  firal::DBuf Zp;                // block sums: x (x) x on the pair triangle, bf16 hi and lo
   firal::DBuf gq_ab, gq_m, gq_part;  // tensor-core quadratic forms: [A;B], M~ pairs, partials
   firal::DBuf rtab, rM;          // Round on tensor cores: 8-pair chunk table, M~ hi/lo rows
   firal::DBuf tdev;              // device-resident MD step counter (graph replays)

@@ -88,20 +88,24 @@ __global__ void k_to_bf16_pad(bf16* dst, const float* src, int64_t rows, int col
 }
 
 // dst[cols_p x rows_p] = transpose of a padded bf16 matrix src[rows_p x cols_p]
-__global__ void k_transpose_bf16(bf16* dst, const bf16* src, int64_t rows_p, int cols_p) {
+// src (rows_p x cols_p, row-major) -> dst in the K-block-major layout [r / 64][col][r % 64] with
+// colsb >= cols_p rows per block (rows cols_p..colsb-1 zero): every 64-point tile of a block of
+// rows is one contiguous run, so TMA tiles touch few DRAM pages.  rows_p % 64 == 0.
+__global__ void k_block_transpose_bf16(bf16* dst, const bf16* src, int64_t rows_p, int cols_p,
+                                       int colsb) {
   __shared__ bf16 tile[32][34];
   const int64_t rb = (int64_t)blockIdx.x * 32;
   const int cb = blockIdx.y * 32;
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
     const int64_t r = rb + i;
     const int col = cb + threadIdx.x;
-    if (r < rows_p && col < cols_p) tile[i][threadIdx.x] = src[r * cols_p + col];
+    tile[i][threadIdx.x] = (r < rows_p && col < cols_p) ? src[r * cols_p + col] : __float2bfloat16(0.0f);
   }
   __syncthreads();
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
     const int col = cb + i;
     const int64_t r = rb + threadIdx.x;
-    if (r < rows_p && col < cols_p) dst[(int64_t)col * rows_p + r] = tile[threadIdx.x][i];
+    if (r < rows_p && col < colsb) dst[((r >> 6) * colsb + col) * 64 + (r & 63)] = tile[threadIdx.x][i];
   }
 }
 
@@ -415,7 +419,11 @@ __global__ void __launch_bounds__(256, 1)
         // and h, and a stale non-finite value there would turn the whole probe into NaN
         if (j < s) {
           if (MODE == 0) {
-            if (row < Np) aT[(int64_t)j * Np + row] = __float2bfloat16_rn(row < N ? wi * sum : 0.0f);
+            // walpha^T in the K-block-major layout [row / 64][j][row % 64], sp16 rows per block
+            const int sp16 = (s + 15) / 16 * 16;
+            if (row < Np)
+              aT[((row >> 6) * sp16 + j) * 64 + (row & 63)] =
+                  __float2bfloat16_rn(row < N ? wi * sum : 0.0f);
           } else if (row < N) {
             out32[(int64_t)j * Np + row] = sum;
           }
@@ -461,7 +469,7 @@ __global__ void __launch_bounds__(256, 1)
     k_tc_dterm(const __grid_constant__ CUtensorMap mapHT, const __grid_constant__ CUtensorMap mapXT,
                const __grid_constant__ CUtensorMap mapAT, float* __restrict__ Dpart, int64_t N,
                int c, int d, int s, int n_mt, int n_nt, int splits, int64_t kb_per_split,
-               int64_t kb_total, int32_t* err) {
+               int64_t kb_total, int sp16, int32_t* err) {
   using namespace d_cfg;
   using St = Stage<DP>;
   constexpr int STAGES = St::STAGES;
@@ -529,12 +537,14 @@ __global__ void __launch_bounds__(256, 1)
         }
         unsigned char* st = sm + stage * STAGE_BYTES;
         mbar_expect_tx(&ctl->full[stage], TX);
-        const int x = (int)(kb * BK);
+        // K-block-major operands: block kb holds n_mt * MT class tiles, DP rows of x^T and
+        // sp16 rows of walpha^T, each row 64 points
 #pragma unroll
         for (int a = 0; a < MT; ++a)
-          tma_load_2d(st + a * A_BYTES, &mapHT, &ctl->full[stage], x, (mt * MT + a) * BM);
-        tma_load_2d(st + OFF_XT, &mapXT, &ctl->full[stage], x, 0);
-        tma_load_2d(st + OFF_AT, &mapAT, &ctl->full[stage], x, nt * PPN);
+          tma_load_2d(st + a * A_BYTES, &mapHT, &ctl->full[stage], 0,
+                      (int)((kb * n_mt + mt) * MT + a) * BM);
+        tma_load_2d(st + OFF_XT, &mapXT, &ctl->full[stage], 0, (int)(kb * DP));
+        tma_load_2d(st + OFF_AT, &mapAT, &ctl->full[stage], 0, (int)(kb * sp16 + nt * PPN));
         if (++stage == STAGES) {
           stage = 0;
           phase ^= 1;
@@ -693,69 +703,73 @@ __global__ void __launch_bounds__(256, 1)
 
 // ------------------------------------------------------------------------------------------
 // Block sums on tensor cores (eq. 13 and the diagonal-part operator), split over points:
-//   S[k,(e,e')] = sum_i h_ik (w_i x_ie x_ie'),   P[k,(e,e')] = sum_i h_ik (1 - h_ik) (w_i x_ie x_ie')
-// for the symmetric pairs e <= e' < d (row-major triangle).  S is the dominant term of every
-// Sigma_z apply, so it is carried to ~f32 accuracy with three bf16 products,
-//   S ~ H_hi Z_hi + H_lo Z_hi + H_hi Z_lo,   Z = w x_e x_e' (f32, split into hi + lo),
-// while P (the preconditioner) uses H_hi(1 - H_hi) Z_hi.  A = H^T tiles by TMA; Z and A_P are
-// built in shared memory.  Unit = (128 classes, 128 pairs, point range).
+//   S[k,(e,e')] = sum_i (w_i h_ik) x_ie x_ie',   P[k,(e,e')] = sum_i (w_i h_ik (1 - h_ik)) x_ie x_ie'
+// for the symmetric pairs e <= e' < d (row-major triangle).  The weight goes into the class
+// operand, rebuilt once per call by a streaming kernel,
+//   A = (w o h)^T as bf16 hi + lo,   A_P = bf16((w o h (1 - h))^T)        (c x points),
+// so that the pair operand Z[(e,e'), i] = x_ie x_ie' depends on the problem only: it is built
+// once and stored as bf16 hi + lo, which is exact (a product of two bf16 values has at most 16
+// significant bits).  Both block sums are then plain TMA-fed GEMMs over the points:
+//   MODE 0:  S ~ A_hi Z_hi + A_lo Z_hi + A_hi Z_lo      (relative error ~2^-16)
+//   MODE 1:  P ~ A_P Z_hi                               (preconditioner only)
+// Unit = (128 classes, 128 pairs, point range).
 //
 // Accumulation length.  The tensor core adds each product block into its f32 accumulator with
 // a rounding that is biased (the sum loses magnitude on every add), so a chain of m adds into
 // one accumulator carries a relative bias of roughly m * 2^-25; a split of 200k points is
-// 37,500 adds, a 1e-3 bias that no averaging removes.  S therefore accumulates in TMEM for at
-// most SUB = 8 K-steps (96 adds) at a time, alternating between two short buffers, and four
-// dedicated epilogue warps fold each finished short buffer into a long TMEM accumulator with
-// ordinary round-to-nearest f32 adds while the MMA fills the other.  P only preconditions CG
-// (a biased P changes the iterates, not the solution) and accumulates over the whole unit.
-// TMEM columns: [0,128) S short 0 | [128,256) S short 1 | [256,384) S long | [384,512) P.
+// 37,500 adds, a 1e-3 bias that no averaging removes.  In MODE 0, S therefore accumulates in
+// TMEM for at most SUB = 8 K-steps (96 adds) at a time, alternating between two short
+// buffers, and the epilogue warps fold each finished short buffer into a long TMEM accumulator
+// with round-to-nearest f32 adds while the MMA fills the other.  P only preconditions CG (a
+// biased P changes the iterates, not the solution): MODE 1 accumulates over the whole unit,
+// double-buffered across units.
+// TMEM columns: [0,128) short 0 | [128,256) short 1 | [256,384) S long.
 // ------------------------------------------------------------------------------------------
-namespace s_cfg {
+namespace b_cfg {
 constexpr int BM = 128, BN = 128, BK = 64;
-constexpr int A_BYTES = BM * BK * 2;
-constexpr int Z_BYTES = BN * BK * 2;
-constexpr int NBUILD = 6;
-constexpr int SUB = 8;           // K-steps per short accumulation
-constexpr int THREADS = 384;     // producer, MMA, 6 builder warps, 4 epilogue warps
-constexpr uint32_t COL_LONG = 256, COL_P = 384;
-template <int DP> struct Stage {
-  static constexpr int XT_BYTES = DP * BK * 2;
-  static constexpr int RAW = 3 * A_BYTES + 2 * Z_BYTES + XT_BYTES;
-  static constexpr int BYTES = (RAW + 1023) / 1024 * 1024;
-  static constexpr int STAGES = (3 * BYTES + 2048 <= 227 * 1024) ? 3 : 2;
-  static constexpr int SMEM = STAGES * BYTES + 1024 + 256;
+constexpr int TILE = BM * BK * 2;   // one 128 x 64 bf16 tile (A and Z tiles alike)
+constexpr int SUB = 8;              // K-steps per short accumulation of S
+constexpr uint32_t COL_LONG = 256;
+constexpr int64_t UNIT_KB = 256;    // K-steps per unit at most
+template <int MODE> struct Cfg {
+  static constexpr int NTILE = MODE == 0 ? 4 : 2;   // A_hi A_lo Z_hi Z_lo | A_P Z_hi
+  static constexpr int STAGE = NTILE * TILE;
+  static constexpr int STAGES = MODE == 0 ? 3 : 6;
+  static constexpr int64_t SUBK = MODE == 0 ? SUB : (int64_t)1 << 40;
+  static constexpr int SMEM = STAGES * STAGE + 1024 + 256;
 };
-}  // namespace s_cfg
+}  // namespace b_cfg
 
-template <int DP>
-__global__ void __launch_bounds__(s_cfg::THREADS, 1)
-    k_tc_syrk(const __grid_constant__ CUtensorMap mapHT, const __grid_constant__ CUtensorMap mapHL,
-              const __grid_constant__ CUtensorMap mapXT, const float* __restrict__ w,
-              float* __restrict__ partS, float* __restrict__ partP, int64_t N, int c, int d,
-              int npairs, int n_mt, int n_nt, int splits, int64_t kb_per_split, int64_t kb_total,
-              int32_t* err) {
-  using namespace s_cfg;
-  using St = Stage<DP>;
-  constexpr int STAGES = St::STAGES;
+struct BsCtl {   // < 256 bytes
+  uint64_t full[8], empty[8], tfull[2], tempty[2], drain;
+  uint32_t tmem_base;
+  int abort_w;
+};
+static_assert(sizeof(BsCtl) <= 256, "control block must fit in 256 bytes");
+
+template <int MODE>
+__global__ void __launch_bounds__(256, 1)
+    k_tc_bsum(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUtensorMap mapA1,
+              const __grid_constant__ CUtensorMap mapZ0, const __grid_constant__ CUtensorMap mapZ1,
+              float* __restrict__ part, int c, int d, int npairs, int n_mt, int n_nt,
+              int splits, int64_t kb_per_split, int64_t kb_total, int32_t* err) {
+  using namespace b_cfg;
+  using C = Cfg<MODE>;
+  constexpr int STAGES = C::STAGES;
+  constexpr int64_t SUBK = C::SUBK;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  TcCtl* ctl = (TcCtl*)(sm + STAGES * St::BYTES);
+  BsCtl* ctl = (BsCtl*)(sm + STAGES * C::STAGE);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr uint32_t TX = 2 * A_BYTES + St::XT_BYTES;
-  // stage layout: A_hi | A_lo | A_P | Z_hi | Z_lo | x^T
-  constexpr int OFF_AL = A_BYTES, OFF_AP = 2 * A_BYTES, OFF_ZH = 3 * A_BYTES,
-                OFF_ZL = 3 * A_BYTES + Z_BYTES, OFF_XT = 3 * A_BYTES + 2 * Z_BYTES;
   if (threadIdx.x == 0) {
     for (int i = 0; i < STAGES; ++i) {
       mbar_init(&ctl->full[i], 1);
       mbar_init(&ctl->empty[i], 1);
-      mbar_init(&ctl->yfull[i], NBUILD);
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&ctl->tfull[i], 1);
       mbar_init(&ctl->tempty[i], 4);
     }
-    mbar_init(&ctl->pempty, 4);
     mbar_init(&ctl->drain, 1);
     ctl->abort_w = 0;
     mbar_fence_init();
@@ -769,7 +783,13 @@ __global__ void __launch_bounds__(s_cfg::THREADS, 1)
   tc_fence_after();
   const uint32_t tmem = ctl->tmem_base;
   volatile int* abort_w = &ctl->abort_w;
+  auto give_up = [&](int code) {
+    ctl->abort_w = 1;
+    atomicExch(err, code);
+  };
   const int nunits = n_mt * n_nt * splits;
+  // consecutive units share the point range of a split; the class tiles of one pair tile run
+  // side by side (Z tile reused through L2), and so do the pair tiles of one class tile
   auto unit_range = [&](int u, int& mt, int& nt, int& sp, int64_t& kb0, int64_t& kb1) {
     mt = u % n_mt;
     const int rest = u / n_mt;
@@ -780,9 +800,13 @@ __global__ void __launch_bounds__(s_cfg::THREADS, 1)
   };
 
   if (warp == 0 && lane == 0) {
-    tma_prefetch(&mapHT);
-    tma_prefetch(&mapHL);
-    tma_prefetch(&mapXT);
+    // ---------------- TMA producer
+    tma_prefetch(&mapA0);
+    tma_prefetch(&mapZ0);
+    if (MODE == 0) {
+      tma_prefetch(&mapA1);
+      tma_prefetch(&mapZ1);
+    }
     int stage = 0;
     uint32_t phase = 0;
     bool ok = true;
@@ -792,22 +816,28 @@ __global__ void __launch_bounds__(s_cfg::THREADS, 1)
       unit_range(u, mt, nt, sp, kb0, kb1);
       for (int64_t kb = kb0; kb < kb1; ++kb) {
         if (!mbar_wait(&ctl->empty[stage], phase ^ 1, abort_w)) {
-          raise_abort(ctl, err, 21);
+          give_up(31);
           ok = false;
           break;
         }
-        unsigned char* st = sm + stage * St::BYTES;
-        mbar_expect_tx(&ctl->full[stage], TX);
-        const int x = (int)(kb * BK);
-        tma_load_2d(st, &mapHT, &ctl->full[stage], x, mt * BM);
-        tma_load_2d(st + OFF_AL, &mapHL, &ctl->full[stage], x, mt * BM);
-        tma_load_2d(st + OFF_XT, &mapXT, &ctl->full[stage], x, 0);
+        unsigned char* st = sm + stage * C::STAGE;
+        mbar_expect_tx(&ctl->full[stage], C::STAGE);
+        const int ya = (int)(kb * n_mt + mt) * BM, yz = (int)(kb * n_nt + nt) * BN;
+        tma_load_2d(st, &mapA0, &ctl->full[stage], 0, ya);
+        if (MODE == 0) {
+          tma_load_2d(st + TILE, &mapA1, &ctl->full[stage], 0, ya);
+          tma_load_2d(st + 2 * TILE, &mapZ0, &ctl->full[stage], 0, yz);
+          tma_load_2d(st + 3 * TILE, &mapZ1, &ctl->full[stage], 0, yz);
+        } else {
+          tma_load_2d(st + TILE, &mapZ0, &ctl->full[stage], 0, yz);
+        }
         if (++stage == STAGES) {
           stage = 0;
           phase ^= 1;
         }
       }
     }
+    // let every issued load land before the CTA can exit
     for (int i = 0; i < STAGES; ++i) {
       if (!mbar_wait(&ctl->empty[stage], phase ^ 1, abort_w)) break;
       if (++stage == STAGES) {
@@ -816,49 +846,47 @@ __global__ void __launch_bounds__(s_cfg::THREADS, 1)
       }
     }
   } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
     constexpr uint32_t idesc = idesc_bf16_f32(BM, BN);
     int stage = 0;
     uint32_t phase = 0;
-    uint32_t gsub = 0;      // short accumulations issued by this CTA
-    uint32_t uidx = 0;      // units started by this CTA
+    uint32_t gsub = 0;   // accumulations issued by this CTA (short buffer = gsub & 1)
     bool ok = true;
-    for (int u = blockIdx.x; u < nunits && ok && !*abort_w; u += gridDim.x, ++uidx) {
+    for (int u = blockIdx.x; u < nunits && ok && !*abort_w; u += gridDim.x) {
       int mt, nt, sp;
       int64_t kb0, kb1;
       unit_range(u, mt, nt, sp, kb0, kb1);
-      // P of the previous unit must have been read before this unit overwrites it
-      if (uidx > 0 && !mbar_wait(&ctl->pempty, (uidx - 1) & 1, abort_w)) {
-        raise_abort(ctl, err, 26);
-        break;
-      }
-      for (int64_t c0 = kb0; c0 < kb1 && ok; c0 += SUB, ++gsub) {
-        const int64_t c1 = c0 + SUB < kb1 ? c0 + SUB : kb1;
+      for (int64_t c0 = kb0; c0 < kb1 && ok; c0 += SUBK, ++gsub) {
+        const int64_t c1 = c0 + SUBK < kb1 ? c0 + SUBK : kb1;
         const uint32_t b = gsub & 1, par = (gsub >> 1) & 1;
         if (!mbar_wait(&ctl->tempty[b], par ^ 1, abort_w)) {
-          raise_abort(ctl, err, 22);
+          give_up(32);
           ok = false;
           break;
         }
         tc_fence_after();
-        const uint32_t tS = tmem + b * BN, tP = tmem + COL_P;
+        const uint32_t tS = tmem + b * BN;
         for (int64_t kb = c0; kb < c1; ++kb) {
-          if (!mbar_wait(&ctl->yfull[stage], phase, abort_w)) {
-            raise_abort(ctl, err, 23);
+          if (!mbar_wait(&ctl->full[stage], phase, abort_w)) {
+            give_up(33);
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t ah = smem_u32(sm + stage * St::BYTES);
-          const uint32_t al = ah + OFF_AL, ap = ah + OFF_AP, zh = ah + OFF_ZH, zl = ah + OFF_ZL;
+          const uint32_t a0 = smem_u32(sm + stage * C::STAGE);
 #pragma unroll
           for (int k = 0; k < BK / 16; ++k) {
-            const uint32_t accS = (kb != c0) || k != 0;
-            const uint32_t accP = (kb != kb0) || k != 0;
-            const uint64_t dzh = sdesc_sw128(zh + k * 32);
-            umma_bf16(tS, sdesc_sw128(ah + k * 32), dzh, idesc, accS);
-            umma_bf16(tS, sdesc_sw128(al + k * 32), dzh, idesc, 1u);
-            umma_bf16(tS, sdesc_sw128(ah + k * 32), sdesc_sw128(zl + k * 32), idesc, 1u);
-            umma_bf16(tP, sdesc_sw128(ap + k * 32), dzh, idesc, accP);
+            const uint32_t acc = (kb != c0) || k != 0;
+            if (MODE == 0) {
+              const uint64_t zh = sdesc_sw128(a0 + 2 * TILE + k * 32);
+              const uint64_t ah = sdesc_sw128(a0 + k * 32);
+              umma_bf16(tS, ah, zh, idesc, acc);
+              umma_bf16(tS, sdesc_sw128(a0 + TILE + k * 32), zh, idesc, 1u);
+              umma_bf16(tS, ah, sdesc_sw128(a0 + 3 * TILE + k * 32), idesc, 1u);
+            } else {
+              umma_bf16(tS, sdesc_sw128(a0 + k * 32), sdesc_sw128(a0 + TILE + k * 32), idesc,
+                        acc);
+            }
           }
           umma_commit(&ctl->empty[stage]);
           if (++stage == STAGES) {
@@ -872,90 +900,7 @@ __global__ void __launch_bounds__(s_cfg::THREADS, 1)
     }
     umma_commit(&ctl->drain);
     mbar_wait_drain(&ctl->drain, 0);
-  } else if (warp >= 2 && warp < 2 + NBUILD) {
-    const int bw = warp - 2;
-    const int tid_b = bw * 32 + lane;
-    const int c8 = tid_b & 7;            // fixed point chunk of this thread
-    int stage = 0;
-    uint32_t phase = 0;
-    bool ok = true;
-    const __nv_bfloat162 one2 = __floats2bfloat162_rn(1.0f, 1.0f);
-    constexpr int RPT = (BN + NBUILD * 4 - 1) / (NBUILD * 4);   // Z rows per thread
-    for (int u = blockIdx.x; u < nunits && ok && !*abort_w; u += gridDim.x) {
-      int mt, nt, sp;
-      int64_t kb0, kb1;
-      unit_range(u, mt, nt, sp, kb0, kb1);
-      // pairs of the rows this thread builds (fixed for the unit); -1 = padding row
-      int pe[RPT], pe2[RPT];
-#pragma unroll
-      for (int q = 0; q < RPT; ++q) {
-        const int r = (tid_b >> 3) + q * (NBUILD * 4);
-        const int p = nt * BN + r;
-        pe[q] = -1;
-        pe2[q] = 0;
-        if (r < BN && p < npairs) pair_of(p, d, pe[q], pe2[q]);
-      }
-      for (int64_t kb = kb0; kb < kb1; ++kb) {
-        if (!mbar_wait(&ctl->full[stage], phase, abort_w)) {
-          raise_abort(ctl, err, 24);
-          ok = false;
-          break;
-        }
-        unsigned char* st = sm + stage * St::BYTES;
-        // A_P = A_hi (1 - A_hi), elementwise on the swizzled tile
-        for (int ch = tid_b; ch < BM * 8; ch += NBUILD * 32) {
-          const uint4 hv = *reinterpret_cast<const uint4*>(st + ch * 16);
-          uint4 pv;
-          const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&hv);
-          __nv_bfloat162* p2 = reinterpret_cast<__nv_bfloat162*>(&pv);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) p2[q] = __hmul2(h2[q], __hsub2(one2, h2[q]));
-          *reinterpret_cast<uint4*>(st + OFF_AP + ch * 16) = pv;
-        }
-        // weights of this thread's 8 points (zero beyond N)
-        float wv[8];
-        const int64_t i0 = kb * BK + c8 * 8;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) wv[q] = (i0 + q < N) ? w[i0 + q] : 0.0f;
-        const unsigned char* XT = st + OFF_XT;
-#pragma unroll
-        for (int q = 0; q < RPT; ++q) {
-          const int r = (tid_b >> 3) + q * (NBUILD * 4);
-          if (r >= BN) break;
-          uint4 zh4 = make_uint4(0, 0, 0, 0), zl4 = make_uint4(0, 0, 0, 0);
-          if (pe[q] >= 0) {
-            const uint4 xa = *reinterpret_cast<const uint4*>(XT + pe[q] * (BK * 2) + c8 * 16);
-            const uint4 xb = *reinterpret_cast<const uint4*>(XT + pe2[q] * (BK * 2) + c8 * 16);
-            const __nv_bfloat162* a2 = reinterpret_cast<const __nv_bfloat162*>(&xa);
-            const __nv_bfloat162* b2 = reinterpret_cast<const __nv_bfloat162*>(&xb);
-            __nv_bfloat162* h2 = reinterpret_cast<__nv_bfloat162*>(&zh4);
-            __nv_bfloat162* l2 = reinterpret_cast<__nv_bfloat162*>(&zl4);
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-              const float2 fa = __bfloat1622float2(a2[h]);
-              const float2 fb = __bfloat1622float2(b2[h]);
-              const float z0 = wv[2 * h] * fa.x * fb.x, z1 = wv[2 * h + 1] * fa.y * fb.y;
-              const __nv_bfloat162 hi = __floats2bfloat162_rn(z0, z1);
-              const float2 fh = __bfloat1622float2(hi);
-              h2[h] = hi;
-              l2[h] = __floats2bfloat162_rn(z0 - fh.x, z1 - fh.y);
-            }
-          }
-          const uint32_t off = (uint32_t)r * 128u + ((uint32_t)(c8 ^ (r & 7)) << 4);
-          *reinterpret_cast<uint4*>(st + OFF_ZH + off) = zh4;
-          *reinterpret_cast<uint4*>(st + OFF_ZL + off) = zl4;
-        }
-        fence_async_smem();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&ctl->yfull[stage]);
-        if (++stage == STAGES) {
-          stage = 0;
-          phase ^= 1;
-        }
-      }
-      if (!ok) break;
-    }
-  } else if (warp >= 2 + NBUILD) {
+  } else if (warp >= 4) {
     // ---------------- epilogue: thread = class row k of the unit (TMEM lane 32 q + lane)
     const int q = warp & 3;
     const uint32_t lanes = (uint32_t)(q * 32) << 16;
@@ -966,59 +911,40 @@ __global__ void __launch_bounds__(s_cfg::THREADS, 1)
       int64_t kb0, kb1;
       unit_range(u, mt, nt, sp, kb0, kb1);
       const int k = mt * BM + q * 32 + lane;
-      for (int64_t c0 = kb0; c0 < kb1; c0 += SUB, ++gsub) {
-        const bool first = c0 == kb0, last = c0 + SUB >= kb1;
+      for (int64_t c0 = kb0; c0 < kb1; c0 += SUBK, ++gsub) {
+        const bool first = c0 == kb0, last = c0 + SUBK >= kb1;
         const uint32_t b = gsub & 1, par = (gsub >> 1) & 1;
         if (!mbar_wait(&ctl->tfull[b], par, abort_w)) {
-          raise_abort(ctl, err, 25);
+          give_up(34);
           ok = false;
           break;
         }
         tc_fence_after();
         const uint32_t tS = tmem + lanes + b * BN, tL = tmem + lanes + COL_LONG;
-        if (!last) {
-          // S long (+)= S short: round-to-nearest f32 adds
-          for (int cc = 0; cc < BN; cc += 32) {
-            float v[32];
-            tmem_ld32(tS + cc, v);
-            if (!first) {
-              float l[32];
-              tmem_ld32(tL + cc, l);
+        float* out = part + ((int64_t)sp * c + k) * d * d;
+        for (int cc = 0; cc < BN; cc += 32) {
+          float v[32];
+          tmem_ld32(tS + cc, v);
+          if (!first) {
+            float l[32];
+            tmem_ld32(tL + cc, l);
 #pragma unroll
-              for (int t = 0; t < 32; ++t) v[t] += l[t];
-            }
-            tmem_st32(tL + cc, v);
+            for (int t = 0; t < 32; ++t) v[t] += l[t];
           }
-        } else {
-          for (int which = 0; which < 2; ++which) {
-            float* out = (which == 0 ? partS : partP) + ((int64_t)sp * c + k) * d * d;
-            for (int cc = 0; cc < BN; cc += 32) {
-              float v[32];
-              if (which == 0) {
-                tmem_ld32(tS + cc, v);
-                if (!first) {
-                  float l[32];
-                  tmem_ld32(tL + cc, l);
+          if (!last) {
+            tmem_st32(tL + cc, v);
+          } else if (k < c) {
+            int e = 0, e2 = 0;
+            const int p0 = nt * BN + cc;
+            if (p0 < npairs) pair_of(p0, d, e, e2);
 #pragma unroll
-                  for (int t = 0; t < 32; ++t) v[t] += l[t];
-                }
-              } else {
-                tmem_ld32(tmem + lanes + COL_P + cc, v);
-              }
-              if (k < c) {
-                int e = 0, e2 = 0;
-                const int p0 = nt * BN + cc;
-                if (p0 < npairs) pair_of(p0, d, e, e2);
-#pragma unroll
-                for (int t = 0; t < 32; ++t) {
-                  if (p0 + t < npairs) {
-                    out[e * d + e2] = v[t];
-                    out[e2 * d + e] = v[t];
-                    if (++e2 == d) {
-                      ++e;
-                      e2 = e;
-                    }
-                  }
+            for (int t = 0; t < 32; ++t) {
+              if (p0 + t < npairs) {
+                out[e * d + e2] = v[t];
+                out[e2 * d + e] = v[t];
+                if (++e2 == d) {
+                  ++e;
+                  e2 = e;
                 }
               }
             }
@@ -1026,10 +952,7 @@ __global__ void __launch_bounds__(s_cfg::THREADS, 1)
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) {
-          mbar_arrive(&ctl->tempty[b]);
-          if (last) mbar_arrive(&ctl->pempty);
-        }
+        if (lane == 0) mbar_arrive(&ctl->tempty[b]);
       }
     }
   }
@@ -1041,8 +964,44 @@ __global__ void __launch_bounds__(s_cfg::THREADS, 1)
   }
 }
 
-// h_lo^T = bf16(h - bf16(h)), transposed and padded like HbT
-__global__ void k_h_lo_T(bf16* HlT, const float* Ha, int64_t N, int c, int64_t Np, int cp) {
+// Z[p][i] = x_ie x_ie' for pair p = (e, e') of the row-major triangle, as bf16 hi and lo (exact);
+// rows p >= npairs and columns of padding points are zero.  K-block-major layout
+// [i / 64][p][i % 64] (npp rows per block): every 128 x 64 TMA tile is one contiguous 16 KB
+// run.  Block = 64 points x 128 pairs.
+__global__ void k_build_z(bf16* Zhi, bf16* Zlo, const bf16* Xb, int d, int dp, int npairs,
+                          int64_t npp) {
+  __shared__ bf16 xs[64 * 128];   // 64 points x dp features
+  const int64_t i0 = (int64_t)blockIdx.x * 64;
+  const int p0 = blockIdx.y * 128;
+  for (int t = threadIdx.x; t < 64 * dp; t += blockDim.x) xs[t] = Xb[i0 * dp + t];
+  __syncthreads();
+  for (int item = threadIdx.x; item < 128 * 8; item += blockDim.x) {
+    const int p = p0 + (item >> 3), c8 = item & 7;
+    uint4 hv = make_uint4(0, 0, 0, 0), lv = make_uint4(0, 0, 0, 0);
+    if (p < npairs) {
+      int e, e2;
+      pair_of(p, d, e, e2);
+      bf16* h = reinterpret_cast<bf16*>(&hv);
+      bf16* l = reinterpret_cast<bf16*>(&lv);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int i = c8 * 8 + q;
+        const float z = __bfloat162float(xs[i * dp + e]) * __bfloat162float(xs[i * dp + e2]);
+        h[q] = __float2bfloat16_rn(z);
+        l[q] = __float2bfloat16_rn(z - __bfloat162float(h[q]));
+      }
+    }
+    const int64_t o = ((int64_t)blockIdx.x * npp + p) * 64 + c8 * 8;
+    *reinterpret_cast<uint4*>(Zhi + o) = hv;
+    *reinterpret_cast<uint4*>(Zlo + o) = lv;
+  }
+}
+
+// Class operands of the block sums, zero-padded, in the K-block-major layout
+// [i / 64][k][i % 64] with cpb rows per block:
+//   A_hi = bf16(w h), A_lo = bf16(w h - A_hi), A_P = bf16(w h (1 - h))   (A_P only if AP)
+__global__ void k_weighted_hT(bf16* Ahi, bf16* Alo, bf16* AP, const float* Ha, const float* w,
+                              int64_t N, int c, int64_t Np, int cpb) {
   __shared__ float tile[32][33];
   const int64_t rb = (int64_t)blockIdx.x * 32;
   const int cb = blockIdx.y * 32;
@@ -1052,12 +1011,18 @@ __global__ void k_h_lo_T(bf16* HlT, const float* Ha, int64_t N, int c, int64_t N
     tile[i][threadIdx.x] = (r < N && col < c) ? Ha[r * c + col] : 0.0f;
   }
   __syncthreads();
+  const int64_t r = rb + threadIdx.x;
+  const float wr = r < N ? w[r] : 0.0f;
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
     const int col = cb + i;
-    const int64_t r = rb + threadIdx.x;
-    if (r < Np && col < cp) {
-      const float v = tile[threadIdx.x][i];
-      HlT[(int64_t)col * Np + r] = __float2bfloat16_rn(v - __bfloat162float(__float2bfloat16_rn(v)));
+    if (r < Np && col < cpb) {
+      const float hv = tile[threadIdx.x][i];
+      const float v = wr * hv;
+      const bf16 hi = __float2bfloat16_rn(v);
+      const int64_t o = ((r >> 6) * cpb + col) * 64 + (r & 63);
+      Ahi[o] = hi;
+      Alo[o] = __float2bfloat16_rn(v - __bfloat162float(hi));
+      if (AP) AP[o] = __float2bfloat16_rn(v * (1.0f - hv));
     }
   }
 }
@@ -1387,7 +1352,8 @@ int32_t tc_prepare(firal_problem* P) {
   P->Np = (P->N + 127) / 128 * 128;
   const int64_t Np = P->Np;
   FIRAL_TRY(P->Hb.ensure((size_t)Np * P->cp * 2));
-  FIRAL_TRY(P->HbT.ensure((size_t)Np * P->cp * 2));
+  const int cpb2 = (P->cp + d_cfg::MT * d_cfg::BM - 1) / (d_cfg::MT * d_cfg::BM) * (d_cfg::MT * d_cfg::BM);
+  FIRAL_TRY(P->HbT.ensure((size_t)Np * cpb2 * 2));
   FIRAL_TRY(P->Xb.ensure((size_t)Np * P->dp * 2 * 2));   // X (Np x dp) then X^T (dp x Np)
   const int64_t tot_h = Np * P->cp, tot_x = Np * P->dp;
   ProfScope ps(st, PF_PREP);
@@ -1397,14 +1363,18 @@ int32_t tc_prepare(firal_problem* P) {
   k_to_bf16_pad<<<(unsigned)std::min<int64_t>((tot_x + 255) / 256, 1 << 20), 256, 0, st>>>(
       P->Xb.as<bf16>(), P->Xa.as<float>(), P->N, P->d, Np, P->dp);
   FIRAL_CUDA_TRY(cudaGetLastError());
-  k_transpose_bf16<<<dim3((unsigned)(Np / 32), (unsigned)((P->cp + 31) / 32)), dim3(32, 8), 0,
-                     st>>>(P->HbT.as<bf16>(), P->Hb.as<bf16>(), Np, P->cp);
-  k_transpose_bf16<<<dim3((unsigned)(Np / 32), (unsigned)((P->dp + 31) / 32)), dim3(32, 8), 0,
-                     st>>>(P->Xb.as<bf16>() + tot_x, P->Xb.as<bf16>(), Np, P->dp);
+  // h^T and x^T of the D-GEMM, K-block-major
+  k_block_transpose_bf16<<<dim3((unsigned)(Np / 32), (unsigned)(cpb2 / 32)), dim3(32, 8), 0, st>>>(
+      P->HbT.as<bf16>(), P->Hb.as<bf16>(), Np, P->cp, cpb2);
+  k_block_transpose_bf16<<<dim3((unsigned)(Np / 32), (unsigned)((P->dp + 31) / 32)), dim3(32, 8),
+                           0, st>>>(P->Xb.as<bf16>() + tot_x, P->Xb.as<bf16>(), Np, P->dp, P->dp);
   FIRAL_CUDA_TRY(cudaGetLastError());
-  FIRAL_TRY(P->XwT.ensure((size_t)Np * P->cp * 2));
-  k_h_lo_T<<<dim3((unsigned)(Np / 32), (unsigned)((P->cp + 31) / 32)), dim3(32, 8), 0, st>>>(
-      P->XwT.as<bf16>(), P->Ha.as<float>(), P->N, P->c, Np, P->cp);
+  // pair operand of the block sums (problem constant): Z = x (x) x on the pair triangle
+  const int npairs = P->d * (P->d + 1) / 2;
+  const int64_t npp = (npairs + b_cfg::BN - 1) / b_cfg::BN * b_cfg::BN;
+  FIRAL_TRY(P->Zp.ensure((size_t)2 * npp * Np * 2));
+  k_build_z<<<dim3((unsigned)(Np / 64), (unsigned)(npp / 128)), 256, 0, st>>>(
+      P->Zp.as<bf16>(), P->Zp.as<bf16>() + npp * Np, P->Xb.as<bf16>(), P->d, P->dp, npairs, npp);
   count_launch();
   FIRAL_CUDA_TRY(cudaGetLastError());
   return FIRAL_OK;
@@ -1422,11 +1392,12 @@ static int32_t tc_apply_t(firal_problem* P, const float* w, const float* Sblk, c
   const int64_t prow = (int64_t)s * NPART * DP;
   const int64_t prow_p = (prow + BN - 1) / BN * BN;
   FIRAL_TRY(P->Pb.ensure((size_t)prow_p * cp * 2));
-  FIRAL_TRY(P->walpha.ensure((size_t)sp16 * Np * 2));
   // probe rows s..sp16-1 of walpha^T feed only D columns that are discarded; keep them finite
-  if (sp16 > s)
-    FIRAL_CUDA_TRY(cudaMemsetAsync(P->walpha.as<bf16>() + (int64_t)s * Np, 0,
-                                   (size_t)(sp16 - s) * Np * 2, st));
+  // (zeroed when the buffer is allocated; later calls leave finite values there)
+  const size_t wa_before = P->walpha.bytes;
+  FIRAL_TRY(P->walpha.ensure((size_t)sp16 * Np * 2));
+  if (P->walpha.bytes != wa_before)
+    FIRAL_CUDA_TRY(cudaMemsetAsync(P->walpha.p, 0, P->walpha.bytes, st));
   if (prow_p > prow)
     FIRAL_CUDA_TRY(cudaMemsetAsync(P->Pb.as<bf16>() + prow * cp, 0, (prow_p - prow) * cp * 2, st));
   FIRAL_TRY(P->vmean.ensure((size_t)s * P->d * sizeof(float)));
@@ -1490,9 +1461,13 @@ static int32_t tc_apply_t(firal_problem* P, const float* w, const float* Sblk, c
     splits = (int)((kb_total + kbps - 1) / kbps);
     FIRAL_TRY(P->Dpart.ensure((size_t)splits * P->c * sd * sizeof(float)));
     CUtensorMap mHT, mXT, mAT;
-    FIRAL_TRY(make_map(&mHT, P->HbT.p, cp, Np, d_cfg::BM, d_cfg::BK, true));
-    FIRAL_TRY(make_map(&mXT, P->Xb.as<bf16>() + Np * DP, DP, Np, DP, d_cfg::BK, false));
-    FIRAL_TRY(make_map(&mAT, P->walpha.p, sp16, Np, PPN, d_cfg::BK, false));
+    const uint64_t cpb2 = (uint64_t)n_mt2 * d_cfg::MT * d_cfg::BM;
+    FIRAL_TRY(make_map(&mHT, P->HbT.p, (uint64_t)kb_total * cpb2, d_cfg::BK, d_cfg::BM, d_cfg::BK,
+                       true));
+    FIRAL_TRY(make_map(&mXT, P->Xb.as<bf16>() + Np * DP, (uint64_t)kb_total * DP, d_cfg::BK, DP,
+                       d_cfg::BK, false));
+    FIRAL_TRY(make_map(&mAT, P->walpha.p, (uint64_t)kb_total * sp16, d_cfg::BK, PPN, d_cfg::BK,
+                       false));
     const int units = tiles * splits;
     const int grid2 = std::min(units, sms);
     {
@@ -1500,7 +1475,7 @@ static int32_t tc_apply_t(firal_problem* P, const float* w, const float* Sblk, c
     count_launch();
     k_tc_dterm<DP><<<grid2, 256, d_cfg::Stage<DP>::SMEM, st>>>(mHT, mXT, mAT, P->Dpart.as<float>(), P->N, P->c,
                                              P->d, s, n_mt2, n_nt2, splits, kbps, kb_total,
-                                             tc_error_word(P));
+                                             sp16, tc_error_word(P));
     }
     FIRAL_CUDA_TRY(cudaGetLastError());
     FIRAL_TRY(combine_f32(P, Sblk, V, splits, s, out, nullptr, P->vmean.as<float>()));
@@ -1514,22 +1489,46 @@ static int32_t tc_apply_t(firal_problem* P, const float* w, const float* Sblk, c
   }
 }
 
-template <int DP>
-static int32_t tc_syrk_t(firal_problem* P, const float* w, double lamS, float* outS, double lamP,
-                         double* outP) {
-  using namespace s_cfg;
-  using St = Stage<DP>;
+static int32_t tc_bsum_launch_attrs() {
+  static bool done = false;
+  if (!done) {
+    FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tc_bsum<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        b_cfg::Cfg<0>::SMEM));
+    FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tc_bsum<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        b_cfg::Cfg<1>::SMEM));
+    done = true;
+  }
+  return FIRAL_OK;
+}
+
+// S (and P if outP) = weighted block sums of the problem's rows with weights w (f32, N).
+int32_t tc_syrk_blocks(firal_problem* P, const void* wv, double lamS, void* outS, double lamP,
+                       double* outP) {
+  using namespace b_cfg;
+  const float* w = (const float*)wv;
   cudaStream_t st = P->H->stream;
   const int64_t Np = P->Np;
   const int cp = P->cp, c = P->c, d = P->d;
   const int sms = P->H->sm_count;
   const int npairs = d * (d + 1) / 2;
-  const int n_mt = cp / BM + (cp % BM ? 1 : 0);
-  const int n_nt = (npairs + BN - 1) / BN;
+  const int64_t npp = (npairs + BN - 1) / BN * BN;
+  const int n_mt = (cp + BM - 1) / BM;
+  const int n_nt = (int)(npp / BN);
   const int64_t kb_total = Np / BK;
   const int tiles = n_mt * n_nt;
   int splits = (int)std::max<int64_t>(1, std::min<int64_t>((4LL * sms + tiles - 1) / tiles,
                                                           kb_total / 8 > 0 ? kb_total / 8 : 1));
+  // Units of at most UNIT_KB K-steps: the CTAs that share an A or Z tile stream start each
+  // unit together, which keeps them within L2 reach of one another (over long units they
+  // drift apart and the shared tiles are fetched from DRAM again).  Whole waves of units.
+  const int64_t need = (kb_total + UNIT_KB - 1) / UNIT_KB;
+  if (need > splits) {
+    int64_t g = tiles, r = sms;
+    while (r) { const int64_t t = g % r; g = r; r = t; }
+    const int64_t m = sms / g;
+    const int64_t up = (need + m - 1) / m * m;
+    splits = (int)(up < 2 * need ? up : need);
+  }
   if (forced_splits() > 0) splits = (int)std::min<int64_t>(forced_splits(), kb_total);
   const int64_t kbps = (kb_total + splits - 1) / splits;
   splits = (int)((kb_total + kbps - 1) / kbps);
@@ -1537,37 +1536,41 @@ static int32_t tc_syrk_t(firal_problem* P, const float* w, double lamS, float* o
   FIRAL_TRY(P->syrk_part.ensure((size_t)per * splits * 2 * sizeof(float)));
   float* pS = P->syrk_part.as<float>();
   float* pP = pS + per * splits;
-  CUtensorMap mHT, mHL, mXT;
-  FIRAL_TRY(make_map(&mHT, P->HbT.p, cp, Np, BM, BK, true));
-  FIRAL_TRY(make_map(&mHL, P->XwT.p, cp, Np, BM, BK, true));
-  FIRAL_TRY(make_map(&mXT, P->Xb.as<bf16>() + Np * DP, DP, Np, DP, BK, false));
-  static bool attr[4] = {false, false, false, false};
-  const int ai = DP == 16 ? 0 : DP == 32 ? 1 : DP == 64 ? 2 : 3;
-  if (!attr[ai]) {
-    FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tc_syrk<DP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        St::SMEM));
-    attr[ai] = true;
-  }
+  // class operands for this weight vector: (w h)^T hi | lo | (w h (1 - h))^T, K-block-major
+  const int cpb = n_mt * BM;
+  const int64_t asz = (int64_t)cpb * Np;
+  FIRAL_TRY(P->Aw.ensure((size_t)3 * asz * 2));
+  bf16* Ahi = P->Aw.as<bf16>();
+  bf16* Alo = Ahi + asz;
+  bf16* AP = Ahi + 2 * asz;
+  FIRAL_TRY(tc_bsum_launch_attrs());
   const int units = tiles * splits;
   {
     ProfScope ps(st, PF_SYRK);
-    count_launch();
-    k_tc_syrk<DP><<<std::min(units, sms), THREADS, St::SMEM, st>>>(
-        mHT, mHL, mXT, w, pS, pP, P->N, c, d, npairs, n_mt, n_nt, splits, kbps, kb_total,
-        tc_error_word(P));
+    count_launch(outP ? 3 : 2);
+    k_weighted_hT<<<dim3((unsigned)(Np / 32), (unsigned)(cpb / 32)), dim3(32, 8), 0, st>>>(
+        Ahi, Alo, outP ? AP : nullptr, P->Ha.as<float>(), w, P->N, c, Np, cpb);
+    FIRAL_CUDA_TRY(cudaGetLastError());
+    // blocked operands as 2-D tensors of 64-point rows: tile (kb, row block) = 16 KB run
+    CUtensorMap mA0, mA1, mA2, mZ0, mZ1;
+    const uint64_t arows = (uint64_t)kb_total * cpb, zrows = (uint64_t)kb_total * npp;
+    FIRAL_TRY(make_map(&mA0, Ahi, arows, BK, BM, BK, true));
+    FIRAL_TRY(make_map(&mA1, Alo, arows, BK, BM, BK, true));
+    FIRAL_TRY(make_map(&mA2, AP, arows, BK, BM, BK, true));
+    FIRAL_TRY(make_map(&mZ0, P->Zp.p, zrows, BK, BN, BK, true));
+    FIRAL_TRY(make_map(&mZ1, P->Zp.as<bf16>() + npp * Np, zrows, BK, BN, BK, true));
+    const int grid = std::min(units, sms);
+    k_tc_bsum<0><<<grid, 256, Cfg<0>::SMEM, st>>>(mA0, mA1, mZ0, mZ1, pS, c, d, npairs, n_mt,
+                                                  n_nt, splits, kbps, kb_total, tc_error_word(P));
+    FIRAL_CUDA_TRY(cudaGetLastError());
+    if (outP) {
+      k_tc_bsum<1><<<grid, 256, Cfg<1>::SMEM, st>>>(mA2, mA2, mZ0, mZ0, pP, c, d, npairs, n_mt,
+                                                    n_nt, splits, kbps, kb_total,
+                                                    tc_error_word(P));
+      FIRAL_CUDA_TRY(cudaGetLastError());
+    }
   }
-  FIRAL_CUDA_TRY(cudaGetLastError());
-  return syrk_reduce_f32(P, pS, pP, splits, lamS, outS, lamP, outP);
-}
-
-int32_t tc_syrk_blocks(firal_problem* P, const void* w, double lamS, void* outS, double lamP,
-                       double* outP) {
-  switch (P->dp) {
-    case 16: return tc_syrk_t<16>(P, (const float*)w, lamS, (float*)outS, lamP, outP);
-    case 32: return tc_syrk_t<32>(P, (const float*)w, lamS, (float*)outS, lamP, outP);
-    case 64: return tc_syrk_t<64>(P, (const float*)w, lamS, (float*)outS, lamP, outP);
-    default: return tc_syrk_t<128>(P, (const float*)w, lamS, (float*)outS, lamP, outP);
-  }
+  return syrk_reduce_f32(P, pS, outP ? pP : nullptr, splits, lamS, (float*)outS, lamP, outP);
 }
 
 // ------------------------------------------------------------------------------------------
