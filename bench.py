@@ -37,7 +37,10 @@ def parse():
     ap.add_argument("--workload", default="imagenet_like")
     ap.add_argument("--n", type=int, default=None, help="pool size override (smaller runs)")
     ap.add_argument("--cg-iters", type=int, default=10)
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_fast", "fp32", "fp64"])
+    ap.add_argument("--precision", default="mixed_fast",
+                    choices=["mixed", "mixed_fast", "fp32", "fp64"])
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the m=50, cg_tol=0.1 and hi/lo-direction sub-measurements")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
@@ -149,23 +152,27 @@ def algorithmic_flops(kind, cfg, n_all, s):
     if kind in ("apply_alpha", "apply_dterm"):
         return 2.0 * n_all * c * d * s
     if kind == "syrk_blocks":
-        return 2 * 2.0 * n_all * c * d * d          # S_k and B_k(Sigma_z) blocks together
+        return 2 * 1.0 * n_all * c * d * (d + 1)    # S_k and B_k(Sigma_z), symmetric pairs
     if kind == "quad_forms":
         return 4.0 * n * c * d * s
     return None
 
 
-def dram_traffic(kind, n_rows_padded):
-    """DRAM bytes per launch of a kernel class from the committed ncu capture, scaled by the
-    padded row count; None when the kernel source changed since the capture."""
+def dram_traffic(kind, n_rows_padded, precision):
+    """DRAM bytes per launch of a kernel class from the committed ncu capture (small case):
+    reads and row-proportional writes scale with the padded row count, split-K partial
+    writes are fixed per launch.  None when the kernel source changed since the capture."""
     import hashlib
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))
         src = open(os.path.join(ROOT, rec["source"]), "rb").read()
         if hashlib.sha256(src).hexdigest()[:16] != rec["source_sha256_16"]:
             return None
-        k = rec["kernels"].get(kind)
-        return None if k is None else k["dram_bytes_per_padded_row"] * n_rows_padded
+        k = rec["kernels"].get(f"{kind}/{precision}") or rec["kernels"].get(kind)
+        if k is None:
+            return None
+        return (k["read_bytes_per_padded_row"] + k["write_bytes_per_padded_row"]) * \
+            n_rows_padded + k["write_bytes_fixed"]
     except Exception:
         return None
 
@@ -236,6 +243,29 @@ def round_measure(args, H):
                      "setup_ms": 1000.0 * (t1 - t0)}
         prob.close()
     out["speedup_mixed_over_fp32"] = out["mixed"]["value"] / out["fp32"]["value"]
+    return out
+
+
+def cg_variants(prob, s, b, n):
+    """MD iterations/s at m = 50 CG iterations per solve (the paper's timing setting) and in
+    tolerance mode (cg_tol = 0.1, the paper's default), with the iterations reached."""
+    import torch
+    out = {}
+    for label, kw in (("cg_iters_50", dict(fixed_iters=50)), ("cg_tol_0.1", dict(tol=0.1))):
+        z = torch.full((n,), b / n, dtype=prob.vdt, device="cuda")
+        o = prob.relax_opts(s=s, T=3, seed=1, **kw)
+        prob.relax_step(o, 0, b, z, stats=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        its = []
+        e0.record()
+        for t in (1, 2):
+            its.append(prob.relax_step(o, t, b, z)["cg_iters"])
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 2
+        out[label] = {"value": 1000.0 / ms, "unit": UNIT, "ms_per_step": ms,
+                      "cg_iters_per_solve": its}
     return out
 
 
@@ -377,13 +407,17 @@ def run_ours(args):
     if fl is not None:
         per_launch_ms = kernels[top]["ms_per_step"] / kernels[top]["groups_per_step"]
         achieved = fl / (per_launch_ms / 1000.0) / 1e12
-        tensor = args.precision.startswith("mixed") and top in ("apply_alpha", "apply_dterm")
+        tensor = args.precision.startswith("mixed") and top in ("apply_alpha", "apply_dterm",
+                                                                 "syrk_blocks", "quad_forms")
         peak = pk["bf16_tflops_sustained"] if tensor else FP32_ALU_PEAK_TFLOPS
         n_pad = (n_all + 127) // 128 * 128
+        # executed tensor flops: the hi/lo direction doubles the alpha-GEMM's MMA work
+        execd = achieved * (2.0 if (top == "apply_alpha" and args.precision == "mixed") else 1.0)
         roof = {"kernel": top, "bound": "tensor" if tensor else "alu", "achieved": achieved,
                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": dram_traffic(top, n_pad) if tensor else None,
-                "peak_source": (f"{pk_src} bf16 sustained" if tensor else
+                "traffic": dram_traffic(top, n_pad, args.precision) if tensor else None,
+                "executed_tflops": execd,
+                "peak_source": (f"{pk_src} bf16 sustained (of measured)" if tensor else
                                 "derived FP32 FMA peak: 152 SMs x 128 lanes x 2 x 2.07 GHz")}
     # the Hessian apply as a whole (alpha + D + combine), the operation the metric counts
     apply_ms = sum(kernels.get(k, {}).get("ms_per_step", 0.0)
@@ -425,30 +459,59 @@ def run_ours(args):
                                "H2D copies, problem preparation, one MD iteration, D2H of z"}
 
     if rank == 0:
-        # ---------------- plain FP32 form on the same GPU and its agreement with mixed
+        # ---------------- the paper's timing setting (m = 50) and the tolerance mode
+        if not args.no_variants:
+            try:
+                line["cg_variants"] = cg_variants(prob, s, b, n)
+            except Exception as exc:
+                line["cg_variants"] = {"error": str(exc)[:300]}
+        # ---------------- plain FP32 form on the same GPU and its agreement with the mixed
+        # forms (the timed precision, and the hi/lo-direction variant when it is not timed)
         if not args.no_fp32 and args.precision.startswith("mixed"):
             del prob
             torch.cuda.empty_cache()
             p32 = api.Problem(H, X, h, Xo, ho, p.lam, precision="fp32")
-            pmx = api.Problem(H, X, h, Xo, ho, p.lam, precision=args.precision)
             z32 = torch.full((n,), b / n, dtype=torch.float32, device="cuda")
-            zmx = z32.clone()
-            o = p32.relax_opts(s=s, T=4, fixed_iters=args.cg_iters, seed=1)
+            o = p32.relax_opts(s=s, T=8, fixed_iters=args.cg_iters, seed=1)
             st32 = p32.relax_step(o, 0, b, z32)
-            stmx = pmx.relax_step(o, 0, b, zmx)
-            fdiff = abs(stmx["fhat"] - st32["fhat"]) / abs(st32["fhat"])
-            zdiff = float((zmx.double() - z32.double()).norm() / z32.double().norm())
+            precs = [args.precision] + (["mixed"] if args.precision == "mixed_fast" and
+                                        not args.no_variants else [])
+            agree = {}
+            for prec in precs:
+                pm = api.Problem(H, X, h, Xo, ho, p.lam, precision=prec)
+                zm = torch.full((n,), b / n, dtype=torch.float32, device="cuda")
+                stm = pm.relax_step(o, 0, b, zm)
+                rec = {"fhat_rel_diff_vs_fp32": abs(stm["fhat"] - st32["fhat"]) / abs(st32["fhat"]),
+                       "z_rel_diff_vs_fp32": float((zm.double() - z32.double()).norm() /
+                                                   z32.double().norm())}
+                if prec != args.precision:
+                    # time the variant: 3 MD iterations between events
+                    torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    for t in range(1, 4):
+                        pm.relax_step(o, t, b, zm, stats=False)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    ms = e0.elapsed_time(e1) / 3
+                    rec.update({"value": 1000.0 / ms, "unit": UNIT, "ms_per_step": ms,
+                                "note": "CG direction as bf16 hi + lo in the alpha-GEMM "
+                                        "(twice its tensor work)"})
+                agree[prec] = rec
+                pm.close()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             p32.relax_step(o, 1, b, z32, stats=False)
             torch.cuda.synchronize()
             dt32 = time.perf_counter() - t0
             line["fp32"] = {"value": 1.0 / dt32, "unit": UNIT, "steps": 1, "warmup": 1,
-                            "fhat_rel_diff_mixed_vs_fp32": fdiff,
-                            "z_rel_diff_mixed_vs_fp32": zdiff,
+                            "fhat_rel_diff_mixed_vs_fp32": agree[args.precision]["fhat_rel_diff_vs_fp32"],
+                            "z_rel_diff_mixed_vs_fp32": agree[args.precision]["z_rel_diff_vs_fp32"],
                             "compared": "one MD iteration from the uniform z, same probes",
                             "speedup_mixed_over_fp32": value / world * dt32}
-            del p32, pmx
+            if "mixed" in agree and args.precision != "mixed":
+                line["mixed_hilo"] = agree["mixed"]
+            del p32
         # ---------------- Round (Algorithm 3) on the full-pipeline workload
         if not args.no_round:
             try:

@@ -289,6 +289,7 @@ __global__ void k_syrk_reduce(const T* part, int splits, int64_t per, int d, dou
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < per;
        idx += (int64_t)gridDim.x * blockDim.x) {
     double acc = 0.0;
+#pragma unroll 8
     for (int sp = 0; sp < splits; ++sp) acc += (double)part[(int64_t)sp * per + idx];
     const int64_t ef = idx % ((int64_t)d * d);
     const int e = (int)(ef / d), f = (int)(ef % d);

@@ -730,7 +730,7 @@ constexpr int BM = 128, BN = 128, BK = 64;
 constexpr int TILE = BM * BK * 2;   // one 128 x 64 bf16 tile (A and Z tiles alike)
 constexpr int SUB = 8;              // K-steps per short accumulation of S
 constexpr uint32_t COL_LONG = 256;
-constexpr int64_t UNIT_KB = 256;    // K-steps per unit at most
+constexpr int64_t UNIT_KB = 1024;   // K-steps per unit at most
 template <int MODE> struct Cfg {
   static constexpr int NTILE = MODE == 0 ? 4 : 2;   // A_hi A_lo Z_hi Z_lo | A_P Z_hi
   static constexpr int STAGE = NTILE * TILE;
@@ -1000,30 +1000,36 @@ __global__ void k_build_z(bf16* Zhi, bf16* Zlo, const bf16* Xb, int d, int dp, i
 // Class operands of the block sums, zero-padded, in the K-block-major layout
 // [i / 64][k][i % 64] with cpb rows per block:
 //   A_hi = bf16(w h), A_lo = bf16(w h - A_hi), A_P = bf16(w h (1 - h))   (A_P only if AP)
+// Block = one 64-point block x 32 classes; each warp store writes one 128-byte row run.
 __global__ void k_weighted_hT(bf16* Ahi, bf16* Alo, bf16* AP, const float* Ha, const float* w,
                               int64_t N, int c, int64_t Np, int cpb) {
-  __shared__ float tile[32][33];
-  const int64_t rb = (int64_t)blockIdx.x * 32;
+  __shared__ float tile[64][33];
+  __shared__ float ws[64];
+  const int64_t rb = (int64_t)blockIdx.x * 64;
   const int cb = blockIdx.y * 32;
-  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+  for (int i = threadIdx.y; i < 64; i += blockDim.y) {
     const int64_t r = rb + i;
     const int col = cb + threadIdx.x;
     tile[i][threadIdx.x] = (r < N && col < c) ? Ha[r * c + col] : 0.0f;
   }
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  if (tid < 64) ws[tid] = rb + tid < N ? w[rb + tid] : 0.0f;
   __syncthreads();
-  const int64_t r = rb + threadIdx.x;
-  const float wr = r < N ? w[r] : 0.0f;
+  const int t2 = 2 * threadIdx.x;   // points rb + t2, rb + t2 + 1
+  const float w0 = ws[t2], w1 = ws[t2 + 1];
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
     const int col = cb + i;
-    if (r < Np && col < cpb) {
-      const float hv = tile[threadIdx.x][i];
-      const float v = wr * hv;
-      const bf16 hi = __float2bfloat16_rn(v);
-      const int64_t o = ((r >> 6) * cpb + col) * 64 + (r & 63);
-      Ahi[o] = hi;
-      Alo[o] = __float2bfloat16_rn(v - __bfloat162float(hi));
-      if (AP) AP[o] = __float2bfloat16_rn(v * (1.0f - hv));
-    }
+    if (col >= cpb) continue;
+    const float h0 = tile[t2][i], h1 = tile[t2 + 1][i];
+    const float v0 = w0 * h0, v1 = w1 * h1;
+    const __nv_bfloat162 hi = __floats2bfloat162_rn(v0, v1);
+    const float2 fh = __bfloat1622float2(hi);
+    const int64_t o = ((int64_t)blockIdx.x * cpb + col) * 64 + t2;
+    *reinterpret_cast<__nv_bfloat162*>(Ahi + o) = hi;
+    *reinterpret_cast<__nv_bfloat162*>(Alo + o) = __floats2bfloat162_rn(v0 - fh.x, v1 - fh.y);
+    if (AP)
+      *reinterpret_cast<__nv_bfloat162*>(AP + o) =
+          __floats2bfloat162_rn(v0 * (1.0f - h0), v1 * (1.0f - h1));
   }
 }
 
@@ -1548,7 +1554,7 @@ int32_t tc_syrk_blocks(firal_problem* P, const void* wv, double lamS, void* outS
   {
     ProfScope ps(st, PF_SYRK);
     count_launch(outP ? 3 : 2);
-    k_weighted_hT<<<dim3((unsigned)(Np / 32), (unsigned)(cpb / 32)), dim3(32, 8), 0, st>>>(
+    k_weighted_hT<<<dim3((unsigned)(Np / 64), (unsigned)(cpb / 32)), dim3(32, 8), 0, st>>>(
         Ahi, Alo, outP ? AP : nullptr, P->Ha.as<float>(), w, P->N, c, Np, cpb);
     FIRAL_CUDA_TRY(cudaGetLastError());
     // blocked operands as 2-D tensors of 64-point rows: tile (kb, row block) = 16 KB run
