@@ -708,7 +708,7 @@ int32_t firal_problem_destroy(firal_problem* P) {
   for (DBuf* b : {&P->Xa, &P->Ha, &P->HaT, &P->w_sig, &P->w_p, &P->S_p, &P->S_sig, &P->Pblk,
                   &P->Minv, &P->HoBlk, &P->walpha, &P->Dpart, &P->syrk_part, &P->cgX, &P->cgR,
                   &P->cgP, &P->cgQ, &P->cgZ, &P->cgcols, &P->cgpart1, &P->cgpart2, &P->V, &P->U,
-                  &P->W, &P->HU, &P->g, &P->red, &P->zsave, &P->Xb, &P->Hb, &P->HbT, &P->Pb, &P->vmean, &P->qmean, &P->Aw, &P->Zp, &P->gq_ab,
+                  &P->W, &P->HU, &P->g, &P->red, &P->zsave, &P->Xb, &P->Hb, &P->HbT, &P->Pb, &P->vmean, &P->qmean, &P->Aw, &P->Zp, &P->Hlo, &P->gq_ab,
                   &P->gq_m, &P->gq_part, &P->rtab, &P->rM, &P->tdev})
     b->release();
   delete P;

@@ -87,6 +87,19 @@ __global__ void k_to_bf16_pad(bf16* dst, const float* src, int64_t rows, int col
   }
 }
 
+// dst = bf16(src - bf16(src)), the low part, same padding as k_to_bf16_pad
+__global__ void k_to_bf16_lo_pad(bf16* dst, const float* src, int64_t rows, int cols,
+                                 int64_t rows_p, int cols_p) {
+  const int64_t total = rows_p * cols_p;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = idx / cols_p;
+    const int col = (int)(idx - r * cols_p);
+    const float v = (r < rows && col < cols) ? src[r * cols + col] : 0.0f;
+    dst[idx] = __float2bfloat16_rn(v - __bfloat162float(__float2bfloat16_rn(v)));
+  }
+}
+
 // dst[cols_p x rows_p] = transpose of a padded bf16 matrix src[rows_p x cols_p]
 // src (rows_p x cols_p, row-major) -> dst in the K-block-major layout [r / 64][col][r % 64] with
 // colsb >= cols_p rows per block (rows cols_p..colsb-1 zero): every 64-point tile of a block of
@@ -212,6 +225,10 @@ constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr int SMEM_QUAD(int dp) { return SMEM + dp * BM * 2; }
+// with the low part of h as a second A operand (gradient modes): 3 stages of A_hi|A_lo|B
+constexpr int STAGES_H = 3;
+constexpr int SMEM_H = STAGES_H * (2 * A_BYTES + B_BYTES) + 1024 + 256;
+constexpr int SMEM_QUAD_H(int dp) { return SMEM_H + dp * BM * 2; }
 }  // namespace alpha_cfg
 
 struct TcCtl {   // < 256 bytes
@@ -226,23 +243,31 @@ __device__ __forceinline__ void raise_abort(TcCtl* ctl, int32_t* err, int code) 
   atomicExch(err, code);
 }
 
-template <int DP, int MODE, int NPART>
+// HLO = 1: h enters as bf16 hi + lo.  Every k-step adds H_lo times the hi columns of B
+// (MODE 2: the first 128 rows of the tile; MODE 1: the DP hi rows of each probe) into the
+// same accumulator columns, so the epilogue sees (H_hi + H_lo) B_hi + H_hi B_lo.
+template <int DP, int MODE, int NPART, int HLO = 0>
 __global__ void __launch_bounds__(256, 1)
     k_tc_alpha(const __grid_constant__ CUtensorMap mapH, const __grid_constant__ CUtensorMap mapP,
-               const bf16* __restrict__ Xb, const float* __restrict__ w, bf16* __restrict__ aT,
-               float* __restrict__ out32, int64_t N, int64_t Np, int s, int kblocks, int n_mt,
-               int n_nt, int npairs, int d, int32_t* err) {
+               const __grid_constant__ CUtensorMap mapHL, const bf16* __restrict__ Xb,
+               const float* __restrict__ w, bf16* __restrict__ aT, float* __restrict__ out32,
+               int64_t N, int64_t Np, int s, int kblocks, int n_mt, int n_nt, int npairs, int d,
+               int32_t* err) {
   using namespace alpha_cfg;
+  constexpr int NST = HLO ? STAGES_H : STAGES;
+  constexpr int SB = STAGE_BYTES + (HLO ? A_BYTES : 0);
+  constexpr int OFF_B = (HLO ? 2 : 1) * A_BYTES;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  TcCtl* ctl = (TcCtl*)(sm + STAGES * STAGE_BYTES);
+  TcCtl* ctl = (TcCtl*)(sm + NST * SB);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int PPN = BN / (NPART * DP);   // probes per N tile
   static_assert(MODE != 2 || NPART == 2, "the quadratic mode reads hi and lo halves");
+  static_assert(!HLO || (MODE != 0 && NPART == 2), "h_lo is used by the gradient modes");
   // MODE 2: the thread's x row, transposed (column = thread) so reads are conflict-free
-  bf16* xsT = (bf16*)(sm + STAGES * STAGE_BYTES + 256);   // after the control block
+  bf16* xsT = (bf16*)(sm + NST * SB + 256);   // after the control block
   if (threadIdx.x == 0) {
-    for (int i = 0; i < STAGES; ++i) {
+    for (int i = 0; i < NST; ++i) {
       mbar_init(&ctl->full[i], 1);
       mbar_init(&ctl->empty[i], 1);
     }
@@ -269,6 +294,7 @@ __global__ void __launch_bounds__(256, 1)
     // ---------------- TMA producer
     tma_prefetch(&mapH);
     tma_prefetch(&mapP);
+    if (HLO) tma_prefetch(&mapHL);
     int stage = 0;
     uint32_t phase = 0;
     for (int tile = blockIdx.x; tile < ntiles && !*abort_w; tile += gridDim.x) {
@@ -278,20 +304,21 @@ __global__ void __launch_bounds__(256, 1)
           raise_abort(ctl, err, 1);
           break;
         }
-        unsigned char* st = sm + stage * STAGE_BYTES;
-        mbar_expect_tx(&ctl->full[stage], STAGE_BYTES);
+        unsigned char* st = sm + stage * SB;
+        mbar_expect_tx(&ctl->full[stage], SB);
         tma_load_2d(st, &mapH, &ctl->full[stage], kb * BK, mt * BM);
-        tma_load_2d(st + A_BYTES, &mapP, &ctl->full[stage], kb * BK, nt * BN);
-        if (++stage == STAGES) {
+        if (HLO) tma_load_2d(st + A_BYTES, &mapHL, &ctl->full[stage], kb * BK, mt * BM);
+        tma_load_2d(st + OFF_B, &mapP, &ctl->full[stage], kb * BK, nt * BN);
+        if (++stage == NST) {
           stage = 0;
           phase ^= 1;
         }
       }
     }
     // let every issued load land before the CTA can exit
-    for (int i = 0; i < STAGES; ++i) {
+    for (int i = 0; i < NST; ++i) {
       if (!mbar_wait(&ctl->empty[stage], phase ^ 1, abort_w)) break;
-      if (++stage == STAGES) {
+      if (++stage == NST) {
         stage = 0;
         phase ^= 1;
       }
@@ -318,14 +345,28 @@ __global__ void __launch_bounds__(256, 1)
           break;
         }
         tc_fence_after();
-        const uint32_t a0 = smem_u32(sm + stage * STAGE_BYTES);
-        const uint32_t b0 = a0 + A_BYTES;
+        const uint32_t a0 = smem_u32(sm + stage * SB);
+        const uint32_t b0 = a0 + OFF_B;
 #pragma unroll
-        for (int k = 0; k < BK / 16; ++k)
+        for (int k = 0; k < BK / 16; ++k) {
           umma_bf16(d, sdesc_sw128(a0 + k * 32), sdesc_sw128(b0 + k * 32), idesc,
                     (kb | k) != 0);
+          if (HLO) {
+            const uint64_t al = sdesc_sw128(a0 + A_BYTES + k * 32);
+            if (MODE == 2) {
+              constexpr uint32_t idesc_h = idesc_bf16_f32(BM, BN / 2);
+              umma_bf16(d, al, sdesc_sw128(b0 + k * 32), idesc_h, 1u);
+            } else {
+              constexpr uint32_t idesc_p = idesc_bf16_f32(BM, DP);
+#pragma unroll
+              for (int jj = 0; jj < PPN; ++jj)
+                umma_bf16(d + jj * NPART * DP, al,
+                          sdesc_sw128(b0 + jj * NPART * DP * 128 + k * 32), idesc_p, 1u);
+            }
+          }
+        }
         umma_commit(&ctl->empty[stage]);
-        if (++stage == STAGES) {
+        if (++stage == NST) {
           stage = 0;
           phase ^= 1;
         }
@@ -1358,6 +1399,7 @@ int32_t tc_prepare(firal_problem* P) {
   P->Np = (P->N + 127) / 128 * 128;
   const int64_t Np = P->Np;
   FIRAL_TRY(P->Hb.ensure((size_t)Np * P->cp * 2));
+  FIRAL_TRY(P->Hlo.ensure((size_t)Np * P->cp * 2));
   const int cpb2 = (P->cp + d_cfg::MT * d_cfg::BM - 1) / (d_cfg::MT * d_cfg::BM) * (d_cfg::MT * d_cfg::BM);
   FIRAL_TRY(P->HbT.ensure((size_t)Np * cpb2 * 2));
   FIRAL_TRY(P->Xb.ensure((size_t)Np * P->dp * 2 * 2));   // X (Np x dp) then X^T (dp x Np)
@@ -1368,6 +1410,9 @@ int32_t tc_prepare(firal_problem* P) {
       P->Hb.as<bf16>(), P->Ha.as<float>(), P->N, P->c, Np, P->cp);
   k_to_bf16_pad<<<(unsigned)std::min<int64_t>((tot_x + 255) / 256, 1 << 20), 256, 0, st>>>(
       P->Xb.as<bf16>(), P->Xa.as<float>(), P->N, P->d, Np, P->dp);
+  k_to_bf16_lo_pad<<<(unsigned)std::min<int64_t>((tot_h + 255) / 256, 1 << 20), 256, 0, st>>>(
+      P->Hlo.as<bf16>(), P->Ha.as<float>(), P->N, P->c, Np, P->cp);
+  count_launch();
   FIRAL_CUDA_TRY(cudaGetLastError());
   // h^T and x^T of the D-GEMM, K-block-major
   k_block_transpose_bf16<<<dim3((unsigned)(Np / 32), (unsigned)(cpb2 / 32)), dim3(32, 8), 0, st>>>(
@@ -1436,7 +1481,7 @@ static int32_t tc_apply_t(firal_problem* P, const float* w, const float* Sblk, c
   {
   ProfScope ps(st, PF_ALPHA);
   count_launch();
-  k_tc_alpha<DP, 0, NPART><<<grid, 256, SMEM, st>>>(mH, mP, P->Xb.as<bf16>(), w, P->walpha.as<bf16>(),
+  k_tc_alpha<DP, 0, NPART><<<grid, 256, SMEM, st>>>(mH, mP, mH, P->Xb.as<bf16>(), w, P->walpha.as<bf16>(),
                                              nullptr, P->N, Np, s, cp / BK, n_mt, n_nt, 0, P->d,
                                              tc_error_word(P));
   }
@@ -1667,22 +1712,23 @@ static int32_t tc_quad_t(firal_problem* P, const float* A, const float* B, int s
   static bool attr[4] = {false, false, false, false};
   const int ai = DP == 16 ? 0 : DP == 32 ? 1 : DP == 64 ? 2 : 3;
   if (!attr[ai]) {
-    FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tc_alpha<DP, 1, 2>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
-    FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tc_alpha<DP, 2, 2>,
+    FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tc_alpha<DP, 1, 2, 1>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_H));
+    FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tc_alpha<DP, 2, 2, 1>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        SMEM_QUAD(DP)));
+                                        SMEM_QUAD_H(DP)));
     attr[ai] = true;
   }
   const int n_mt = (int)(Np / BM);
   {
-    CUtensorMap mH, mM;
+    CUtensorMap mH, mM, mHL;
     FIRAL_TRY(make_map(&mH, P->Hb.p, Np, cp, BM, BK, true));
+    FIRAL_TRY(make_map(&mHL, P->Hlo.p, Np, cp, BM, BK, true));
     FIRAL_TRY(make_map(&mM, P->gq_m.p, mrows, cp, BN, BK, true));
     count_launch(1);
-    k_tc_alpha<DP, 2, 2><<<std::min(n_mt * n_nt1, sms), 256, SMEM_QUAD(DP), st>>>(
-        mH, mM, P->Xb.as<bf16>(), nullptr, nullptr, part1, P->N, Np, 0, cp / BK, n_mt, n_nt1,
-        npairs, d, tc_error_word(P));
+    k_tc_alpha<DP, 2, 2, 1><<<std::min(n_mt * n_nt1, sms), 256, SMEM_QUAD_H(DP), st>>>(
+        mH, mM, mHL, P->Xb.as<bf16>(), nullptr, nullptr, part1, P->N, Np, 0, cp / BK, n_mt,
+        n_nt1, npairs, d, tc_error_word(P));
     FIRAL_CUDA_TRY(cudaGetLastError());
   }
   // term 2: h.a_ij and h.b_ij for the projected [A; B]
@@ -1697,14 +1743,15 @@ static int32_t tc_quad_t(firal_problem* P, const float* A, const float* B, int s
     k_split_probes<2><<<dim3((unsigned)(cp + 31) / 32, DP / 32 > 0 ? DP / 32 : 1, s2), dim3(32, 8), 0,
                      st>>>(P->Pb.as<bf16>(), AB, P->vmean.as<float>(), s2, c, d, DP, cp, D);
     FIRAL_CUDA_TRY(cudaGetLastError());
-    CUtensorMap mH, mP;
+    CUtensorMap mH, mP, mHL;
     FIRAL_TRY(make_map(&mH, P->Hb.p, Np, cp, BM, BK, true));
+    FIRAL_TRY(make_map(&mHL, P->Hlo.p, Np, cp, BM, BK, true));
     FIRAL_TRY(make_map(&mP, P->Pb.p, prow_p, cp, BN, BK, true));
     const int n_nt2 = (int)(prow_p / BN);
     count_launch(1);
-    k_tc_alpha<DP, 1, 2><<<std::min(n_mt * n_nt2, sms), 256, SMEM, st>>>(
-        mH, mP, P->Xb.as<bf16>(), nullptr, nullptr, a32, P->N, Np, s2, cp / BK, n_mt, n_nt2, 0,
-        d, tc_error_word(P));
+    k_tc_alpha<DP, 1, 2, 1><<<std::min(n_mt * n_nt2, sms), 256, SMEM_H, st>>>(
+        mH, mP, mHL, P->Xb.as<bf16>(), nullptr, nullptr, a32, P->N, Np, s2, cp / BK, n_mt,
+        n_nt2, 0, d, tc_error_word(P));
     FIRAL_CUDA_TRY(cudaGetLastError());
   }
   count_launch(1);

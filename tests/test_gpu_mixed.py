@@ -127,7 +127,8 @@ def test_mixed_quad_forms(api, handle, n, d, c, s):
     got_n = prob.quad_forms(dev(An.T.astype(np.float32)), dev(B.T.astype(np.float32))).cpu().numpy()
     e2 = relerr(got_n, ref)
     print(f"mixed quad n={n} d={d} c={c} s={s}: {e1:.2e}  with N-component {e2:.2e}")
-    assert e1 < 2e-3 and e2 < 2e-3
+    # h enters as bf16 hi + lo and M~ / [A; B] as hi + lo: per-point errors ~2^-16
+    assert e1 < 1e-4 and e2 < 2e-4
 
 
 def test_fixed_iteration_relax_mixed_and_fp32_vs_oracle(api, handle):
