@@ -29,6 +29,15 @@ int forced_splits() {
   return v;
 }
 
+// FIRAL_SM_BUDGET=k caps the CTAs every problem spreads over (0 or unset: no cap)
+int forced_sm_budget() {
+  static int v = [] {
+    const char* e = std::getenv("FIRAL_SM_BUDGET");
+    return e ? std::atoi(e) : 0;
+  }();
+  return v;
+}
+
 namespace {
 struct Pending {
   int id;
@@ -294,6 +303,10 @@ int32_t problem_create_impl(firal_handle* H, const firal_pool* pool, const firal
   P->c = pool->c;
   P->D = (int64_t)P->d * P->c;
   P->lambda = h0 ? h0->lambda : 0.0;
+  {
+    int b = forced_sm_budget() > 0 ? forced_sm_budget() : H->sm_budget;
+    P->sms = (b > 0 && b < H->sm_count) ? b : H->sm_count;
+  }
   cudaStream_t st = H->stream;
   const size_t vs = vsize(P);
   auto cleanup = [&](int32_t code) {
@@ -415,7 +428,7 @@ int32_t round_impl(firal_problem* P, const void* zr, int32_t b, const firal_roun
     for (DBuf* bf : {&Sig, &L, &Bm, &Binv, &Hk, &M1, &M2, &eig, &nu, &mask, &pv, &pi, &score, &Tg})
       bf->release();
   };
-  const int np = (int)std::max<int64_t>((P->n + 127) / 128, P->H->sm_count);
+  const int np = (int)std::max<int64_t>((P->n + 127) / 128, P->sms);
   int32_t rc = FIRAL_OK;
 #define TRYR(x)                    \
   do {                             \

@@ -84,6 +84,7 @@ extern std::atomic<long long> g_launches;
 inline void count_launch(int n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 // Split-count override for tests of the row partition (0 = automatic).
 int forced_splits();
+int forced_sm_budget();
 struct ProfScope {
   ProfScope(cudaStream_t st, int id);
   ~ProfScope();
@@ -96,6 +97,7 @@ struct ProfScope {
 struct firal_handle {
   int device = 0;
   int sm_count = 148;
+  int sm_budget = 0;       // > 0: CTAs a problem created on this handle may spread over
   cudaStream_t stream = nullptr;
   firal::DBuf flags;       // firal::DevFlags
   firal::DBuf scratch;     // small reductions
@@ -103,6 +105,7 @@ struct firal_handle {
 };
 
 struct firal_problem {
+  int sms = 0;            // SM budget for grids and split counts (<= H->sm_count)
   firal_handle* H = nullptr;
   int32_t prec = FIRAL_FP32;
   bool dbl = false;            // vec type is double

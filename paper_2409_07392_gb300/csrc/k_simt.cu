@@ -318,7 +318,7 @@ static int32_t syrk_t(firal_problem* P, const T* w, double lamS, T* outS, double
   const int TE = d <= 32 ? 2 : (d <= 64 ? 4 : 8);
   const int G = (sizeof(T) == 8 || TE == 8) ? 1 : 4;
   const int cgroups = (c + G - 1) / G;
-  const int splits = syrk_splits(P->N, cgroups, P->H->sm_count);
+  const int splits = syrk_splits(P->N, cgroups, P->sms);
   const int64_t rps = (P->N + splits - 1) / splits;
   const int64_t per = (int64_t)c * d * d;
   FIRAL_TRY(P->syrk_part.ensure((size_t)per * splits * 2 * sizeof(T)));
@@ -555,7 +555,7 @@ static int32_t apply_t(firal_problem* P, const T* w, const T* Sblk, const T* V, 
   const int sd = s * d;
   const int tr = (sd + 63) / 64, tk = (c + 63) / 64;
   const int splits = forced_splits() > 0 ? (int)std::min<int64_t>(forced_splits(), (N + 31) / 32)
-                                         : dterm_splits(tr * tk, N, P->H->sm_count);
+                                         : dterm_splits(tr * tk, N, P->sms);
   const int64_t rps = (N + splits - 1) / splits;
   FIRAL_TRY(P->Dpart.ensure((size_t)splits * c * sd * sizeof(T)));
   {

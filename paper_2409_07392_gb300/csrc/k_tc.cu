@@ -1467,7 +1467,7 @@ static int32_t tc_apply_t(firal_problem* P, const float* w, const float* Sblk, c
   FIRAL_TRY(make_map(&mH, P->Hb.p, Np, cp, BM, BK, true));
   FIRAL_TRY(make_map(&mP, P->Pb.p, prow_p, cp, BN, BK, true));
   const int n_mt = (int)(Np / BM), n_nt = (int)(prow_p / BN);
-  const int sms = P->H->sm_count;
+  const int sms = P->sms;
   const int grid = std::min(n_mt * n_nt, sms);
   static bool attr[4] = {false, false, false, false};
   const int ai = DP == 16 ? 0 : DP == 32 ? 1 : DP == 64 ? 2 : 3;
@@ -1560,7 +1560,7 @@ int32_t tc_syrk_blocks(firal_problem* P, const void* wv, double lamS, void* outS
   cudaStream_t st = P->H->stream;
   const int64_t Np = P->Np;
   const int cp = P->cp, c = P->c, d = P->d;
-  const int sms = P->H->sm_count;
+  const int sms = P->sms;
   const int npairs = d * (d + 1) / 2;
   const int64_t npp = (npairs + BN - 1) / BN * BN;
   const int n_mt = (cp + BM - 1) / BM;
@@ -1681,7 +1681,7 @@ static int32_t tc_quad_t(firal_problem* P, const float* A, const float* B, int s
   const int64_t Np = P->Np;
   const int cp = P->cp, c = P->c, d = P->d;
   const int64_t D = P->D;
-  const int sms = P->H->sm_count;
+  const int sms = P->sms;
   const int mthreads = (d + 31) / 32 * 32;
   // probe block [A; B] (2s columns) and its class means
   FIRAL_TRY(P->gq_ab.ensure((size_t)2 * s * D * sizeof(float)));
@@ -1768,7 +1768,7 @@ static int32_t tc_round_scores_t(firal_problem* P, const float* M1, const float*
   using namespace r_cfg;
   cudaStream_t st = P->H->stream;
   const int d = P->d, c = P->c;
-  const int sms = P->H->sm_count;
+  const int sms = P->sms;
   // 8-pair chunk table (e, first e') with e' running over [8 floor(e/8), d8)
   if (P->rtab_d != d) {
     std::vector<short2> tab;

@@ -176,3 +176,31 @@ def test_mixed_round_matches_oracle_while_gaps_are_clear(api, handle, n, d, c, b
         break
     print(f"mixed round n={n} d={d} c={c} b={b}: {compared} of {b} picks identical, "
           f"first gaps {np.round(info['gap'][:4], 4).tolist()}")
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp32"])
+def test_round_full_pipeline_shapes_vs_oracle(api, handle, precision):
+    """Round at the full-pipeline shapes (d = 128, c = 100, anisotropic clusters, Zipf 1.1
+    priors) on a 2000-point pool, from a non-uniform relaxed z: picks equal the oracle's while
+    its top-1/top-2 gap exceeds 1e-3, otherwise they are valid near-ties."""
+    # seed 4: every oracle top-1/top-2 gap exceeds 1e-3, so all picks must agree
+    p = make_problem(2000, 128, 100, seed=4, x_dtype="bf16", h_dtype="float32",
+                     anisotropic=True, zipf=1.1)
+    prob = make(api, handle, p, precision)
+    b = 6
+    z = np.random.default_rng(2).gamma(2.0, 1.0, p.n)
+    z *= b / z.sum()
+    ref, info = approx.round_select(p, z, b, record=True)
+    sel, _ = prob.round(dev(z.astype(np.float32)), b)
+    sel = sel.cpu().tolist()
+    same = 0
+    for t in range(b):
+        if sel[t] == ref[t]:
+            same += 1
+            continue
+        sc = info["scores"][t]
+        assert info["gap"][t] <= 1e-3, (t, sel[:t + 1], ref[:t + 1])
+        assert sc[sel[t]] >= sc[ref[t]] - 1e-3 * abs(sc[ref[t]])
+        break
+    print(f"{precision} round d=128 c=100: {same} of {b} picks identical, "
+          f"gaps {np.round(info['gap'], 4).tolist()}")
