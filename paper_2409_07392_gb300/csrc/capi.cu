@@ -1,5 +1,8 @@
 // C-ABI entry points (include/firal.h) and host orchestration of the Relax and Round steps.
+#include <algorithm>
 #include <cmath>
+#include <map>
+#include <tuple>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -213,7 +216,7 @@ int32_t ensure_cg(firal_problem* P, int s) {
   FIRAL_TRY(P->cgP.ensure(vb));
   FIRAL_TRY(P->cgQ.ensure(vb));
   FIRAL_TRY(P->cgZ.ensure(vb));
-  FIRAL_TRY(P->cgcols.ensure((size_t)s * sizeof(CGCol)));
+  FIRAL_TRY(P->cgcols.ensure((size_t)s * pool_count(P->pt) * sizeof(CGCol)));
   FIRAL_TRY(P->cgpart1.ensure((size_t)s * P->c * sizeof(double)));
   FIRAL_TRY(P->cgpart2.ensure((size_t)s * P->c * sizeof(double)));
   return FIRAL_OK;
@@ -234,14 +237,15 @@ int32_t pcg_run(firal_problem* P, const void* B, int s, const firal_cg_opts& cg,
   const int iters = fixed ? cg.fixed_iters : (cg.maxit > 0 ? cg.maxit : 100);
   const double tol = cg.tol;
   FIRAL_TRY(cg_init(P, B, s, tol, fixed));
-  std::vector<CGCol> cols(s);
+  const int ns = s * pool_count(P->pt);   // one CG scalar set per (column, pool)
+  std::vector<CGCol> cols(ns);
   for (int it = 0; it < iters; ++it) {
     if (!fixed) {
-      FIRAL_CUDA_TRY(cudaMemcpyAsync(cols.data(), P->cgcols.p, s * sizeof(CGCol),
+      FIRAL_CUDA_TRY(cudaMemcpyAsync(cols.data(), P->cgcols.p, ns * sizeof(CGCol),
                                      cudaMemcpyDeviceToHost, st));
       FIRAL_CUDA_TRY(cudaStreamSynchronize(st));
       bool any = false;
-      for (int j = 0; j < s; ++j) any |= cols[j].active != 0;
+      for (int j = 0; j < ns; ++j) any |= cols[j].active != 0;
       if (!any) break;
     }
     FIRAL_TRY(apply(P, P->w_sig.p, P->S_sig.p, P->cgP.p, s, P->cgQ.p, P->cgpart1.as<double>()));
@@ -250,14 +254,14 @@ int32_t pcg_run(firal_problem* P, const void* B, int s, const firal_cg_opts& cg,
   FIRAL_CUDA_TRY(cudaMemcpyAsync(X_out, P->cgX.p, (size_t)s * P->D * vsize(P),
                                  cudaMemcpyDeviceToDevice, st));
   if (want_result || !fixed) {
-    FIRAL_CUDA_TRY(cudaMemcpyAsync(cols.data(), P->cgcols.p, s * sizeof(CGCol),
+    FIRAL_CUDA_TRY(cudaMemcpyAsync(cols.data(), P->cgcols.p, ns * sizeof(CGCol),
                                    cudaMemcpyDeviceToHost, st));
     FIRAL_CUDA_TRY(cudaStreamSynchronize(st));
     if (res) {
       res->max_iters = 0;
       res->max_relres = 0.0;
       res->converged = true;
-      for (int j = 0; j < s; ++j) {
+      for (int j = 0; j < ns; ++j) {
         res->max_iters = std::max(res->max_iters, cols[j].iters);
         res->max_relres = std::max(res->max_relres, cols[j].relres);
         if (!fixed && cols[j].relres > tol && cols[j].bnorm2 > 0) res->converged = false;
@@ -363,7 +367,7 @@ int32_t relax_step_impl(firal_problem* P, const firal_relax_opts* o, int32_t t, 
   // line 4: probes (step index from the device counter when replayed from a graph)
   if (device_t) FIRAL_TRY(P->tdev.ensure(sizeof(int64_t)));
   FIRAL_TRY(probes(P->dbl, P->V.p, o->seed, t, s, P->D, st,
-                   device_t ? P->tdev.as<int64_t>() : nullptr));
+                   device_t ? P->tdev.as<int64_t>() : nullptr, &P->pt, P->d));
   // line 5: preconditioner from Sigma_z (z copied into the pool part of w_sig)
   FIRAL_TRY(setup_sigma(P, z, true));
   FIRAL_TRY(ensure_sp(P));
@@ -390,7 +394,8 @@ int32_t relax_step_impl(firal_problem* P, const firal_relax_opts* o, int32_t t, 
   FIRAL_TRY(quad(P, first, P->W.p, s, 1.0, P->g.p));
   // lines 10-11: MD update on the budget simplex (in the pool part of w_sig), then copy out
   void* zdev = (char*)P->w_sig.p + P->m * vsize(P);
-  FIRAL_TRY(md_step_simt(P->dbl, zdev, P->g.p, P->n, budget, o->beta0, red, st));
+  if (P->pt.Q) FIRAL_TRY(md_step_pooled(P, zdev, P->g.p, o->beta0, st));   // per-pool simplex
+  else FIRAL_TRY(md_step_simt(P->dbl, zdev, P->g.p, P->n, budget, o->beta0, red, st));
   FIRAL_CUDA_TRY(cudaMemcpyAsync(z, zdev, P->n * vsize(P), cudaMemcpyDeviceToDevice, st));
   if (device_t) FIRAL_TRY(tick(P->tdev.as<int64_t>(), st));
   if (stats) {
@@ -601,6 +606,285 @@ firal_relax_opts default_relax_opts() {
   return o;
 }
 
+// ------------------------------------------------------------------------------------------
+// Pooled problems: the pools idx[0..Q) (one padded feature width, one lambda, one storage type)
+// stacked into a single problem.  Rows: all labelled rows (pool by pool), then all pool rows
+// (pool by pool); classes pool by pool; features padded with zeros to the widest pool; each
+// h row holds its pool's probabilities in that pool's class columns and zeros elsewhere, so
+// every Hessian, Sigma_z and the preconditioner are block diagonal over pools.
+// ------------------------------------------------------------------------------------------
+static size_t dtype_size(int32_t dt) {
+  return dt == FIRAL_DT_BF16 ? 2 : dt == FIRAL_DT_F32 ? 4 : 8;
+}
+
+int32_t pooled_create(firal_handle* H, const std::vector<int>& idx, const firal_pool* pools,
+                      const firal_hess0* h0s, const double* budgets, int32_t prec,
+                      firal_problem** out) {
+  const int Q = (int)idx.size();
+  cudaStream_t st = H->stream;
+  const firal_pool& p0 = pools[idx[0]];
+  const size_t xs = dtype_size(p0.x_dtype), hs = dtype_size(p0.h_dtype);
+  int dg = 0;
+  int64_t C = 0, M = 0, n = 0;
+  std::vector<int> coff(Q + 1), pdim(Q);
+  std::vector<int64_t> loff(Q + 1), poff(Q + 1);
+  for (int q = 0; q < Q; ++q) {
+    const firal_pool& pl = pools[idx[q]];
+    FIRAL_TRY(validate_pool(&pl, h0s ? &h0s[idx[q]] : nullptr));
+    dg = std::max(dg, (int)pl.d);
+    coff[q] = (int)C;
+    C += pl.c;
+    pdim[q] = pl.d;
+    loff[q] = M;
+    M += h0s ? h0s[idx[q]].m : 0;
+    poff[q] = n;
+    n += pl.n;
+  }
+  coff[Q] = (int)C;
+  loff[Q] = M;
+  poff[Q] = n;
+  if (C > 4096) return fail(FIRAL_ERR_UNSUPPORTED, "pooled classes exceed 4096");
+  // stacked inputs (temporaries)
+  DBuf Xs, Hs, Xos, Hos;
+  auto rel = [&]() {
+    Xs.release();
+    Hs.release();
+    Xos.release();
+    Hos.release();
+  };
+  int32_t rc = FIRAL_OK;
+#define TRYP(x)                    \
+  do {                             \
+    rc = (x);                      \
+    if (rc != FIRAL_OK) {          \
+      rel();                       \
+      return rc;                   \
+    }                              \
+  } while (0)
+#define CUDP(x)                                                           \
+  do {                                                                    \
+    cudaError_t e_ = (x);                                                 \
+    if (e_ != cudaSuccess) {                                              \
+      rel();                                                              \
+      return fail(FIRAL_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+    }                                                                     \
+  } while (0)
+  TRYP(Xs.ensure((size_t)n * dg * xs));
+  TRYP(Hs.ensure((size_t)n * C * hs));
+  CUDP(cudaMemsetAsync(Xs.p, 0, (size_t)n * dg * xs, st));
+  CUDP(cudaMemsetAsync(Hs.p, 0, (size_t)n * C * hs, st));
+  if (M > 0) {
+    TRYP(Xos.ensure((size_t)M * dg * xs));
+    TRYP(Hos.ensure((size_t)M * C * hs));
+    CUDP(cudaMemsetAsync(Xos.p, 0, (size_t)M * dg * xs, st));
+    CUDP(cudaMemsetAsync(Hos.p, 0, (size_t)M * C * hs, st));
+  }
+  for (int q = 0; q < Q; ++q) {
+    const firal_pool& pl = pools[idx[q]];
+    CUDP(cudaMemcpy2DAsync((char*)Xs.p + (size_t)poff[q] * dg * xs, dg * xs, pl.X, pl.d * xs,
+                           pl.d * xs, pl.n, cudaMemcpyDeviceToDevice, st));
+    CUDP(cudaMemcpy2DAsync((char*)Hs.p + ((size_t)poff[q] * C + coff[q]) * hs, C * hs, pl.h,
+                           pl.c * hs, pl.c * hs, pl.n, cudaMemcpyDeviceToDevice, st));
+    const int64_t mq = loff[q + 1] - loff[q];
+    if (mq > 0) {
+      const firal_hess0& h0 = h0s[idx[q]];
+      CUDP(cudaMemcpy2DAsync((char*)Xos.p + (size_t)loff[q] * dg * xs, dg * xs, h0.Xo,
+                             pl.d * xs, pl.d * xs, mq, cudaMemcpyDeviceToDevice, st));
+      CUDP(cudaMemcpy2DAsync((char*)Hos.p + ((size_t)loff[q] * C + coff[q]) * hs, C * hs, h0.ho,
+                             pl.c * hs, pl.c * hs, mq, cudaMemcpyDeviceToDevice, st));
+    }
+  }
+  firal_pool sp{Xs.p, Hs.p, n, dg, (int32_t)C, p0.x_dtype, p0.h_dtype};
+  firal_hess0 sh{Xos.p, Hos.p, M, h0s ? h0s[idx[0]].lambda : 0.0};
+  firal_problem* P = nullptr;
+  TRYP(problem_create_impl(H, &sp, &sh, prec, &P));
+  rel();
+#undef TRYP
+#undef CUDP
+  auto bail = [&](int32_t code) {
+    firal_problem_destroy(P);
+    return code;
+  };
+  // pool tables
+  std::vector<int> cpool(C);
+  for (int q = 0; q < Q; ++q)
+    for (int k = coff[q]; k < coff[q + 1]; ++k) cpool[k] = q;
+  std::vector<int> tabs;
+  tabs.insert(tabs.end(), cpool.begin(), cpool.end());
+  tabs.insert(tabs.end(), coff.begin(), coff.end());
+  tabs.insert(tabs.end(), pdim.begin(), pdim.end());
+  if ((rc = P->pool_tabs.ensure(tabs.size() * sizeof(int))) != FIRAL_OK) return bail(rc);
+  cudaError_t e = cudaMemcpyAsync(P->pool_tabs.p, tabs.data(), tabs.size() * sizeof(int),
+                                  cudaMemcpyHostToDevice, st);
+  P->pt.Q = Q;
+  P->pt.cpool = P->pool_tabs.as<int>();
+  P->pt.coff = P->pt.cpool + C;
+  P->pt.pdim = P->pt.coff + Q + 1;
+  // budgets (f64, Q) | pool-row offsets (i64, Q + 1)
+  std::vector<double> bz(Q + (Q + 1));
+  for (int q = 0; q < Q; ++q) bz[q] = budgets[idx[q]];
+  std::memcpy(bz.data() + Q, poff.data(), (Q + 1) * sizeof(int64_t));
+  if ((rc = P->pool_z.ensure(bz.size() * sizeof(double))) != FIRAL_OK) return bail(rc);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(P->pool_z.p, bz.data(), bz.size() * sizeof(double), cudaMemcpyHostToDevice,
+                        st);
+  P->pool_zoff_h = poff;
+  // H_p = (1/n_q) sum over pool q's rows, per pool
+  for (int q = 0; q < Q && rc == FIRAL_OK; ++q) {
+    const int64_t nq = poff[q + 1] - poff[q];
+    rc = fill_weights(P->dbl, (char*)P->w_p.p + (size_t)(M + poff[q]) * vsize(P), 0, 0.0, nullptr,
+                      1.0 / nq, nq, st);
+  }
+  if (rc != FIRAL_OK) return bail(rc);
+  // K ranges of the tensor-core GEMM tiles (pool of every row: labelled rows, then pool rows)
+  const int64_t N = M + n;
+  auto pool_of_row = [&](int64_t r) {
+    const std::vector<int64_t>& off = r < M ? loff : poff;
+    const int64_t x = r < M ? r : r - M;
+    return (int)(std::upper_bound(off.begin(), off.end(), x) - off.begin()) - 1;
+  };
+  if (is_mixed(prec)) {
+    const int64_t ntiles = P->Np / 128;
+    std::vector<int2> ka(ntiles);
+    for (int64_t t = 0; t < ntiles; ++t) {
+      int qmin = Q, qmax = -1;
+      for (int64_t r = t * 128; r < std::min<int64_t>(N, t * 128 + 128); ++r) {
+        const int q = pool_of_row(r);
+        qmin = std::min(qmin, q);
+        qmax = std::max(qmax, q);
+      }
+      ka[t] = make_int2(coff[qmin] / 64, (coff[qmax + 1] + 63) / 64);
+    }
+    const int kbL = (int)((M + 63) / 64);
+    P->kbL = kbL;
+    auto klist = [&](int width, int ntile, std::vector<int4>& out, int64_t& Lmax) {
+      out.resize(ntile);
+      Lmax = kbL;
+      for (int t = 0; t < ntile; ++t) {
+        const int k0 = t * width, k1 = std::min<int64_t>(C, (int64_t)t * width + width);
+        int4 v = make_int4(kbL, kbL, kbL, 0);
+        if (k0 < k1) {
+          const int qa = cpool[k0], qb = cpool[k1 - 1];
+          const int64_t lo = (M + poff[qa]) / 64, hi = (M + poff[qb + 1] + 63) / 64;
+          const int64_t lo2 = std::max<int64_t>(lo, kbL);
+          v = make_int4((int)lo2, (int)hi, (int)(kbL + std::max<int64_t>(0, hi - lo2)), 0);
+        }
+        out[t] = v;
+        Lmax = std::max<int64_t>(Lmax, v.z);
+      }
+    };
+    std::vector<int4> kd, kbs;
+    klist(256, (P->cp + 255) / 256, kd, P->kr_dterm_Lmax);
+    klist(128, (P->cp + 127) / 128, kbs, P->kr_bsum_Lmax);
+    if ((rc = P->kr_alpha.ensure(ka.size() * sizeof(int2))) != FIRAL_OK ||
+        (rc = P->kr_dterm.ensure(kd.size() * sizeof(int4))) != FIRAL_OK ||
+        (rc = P->kr_bsum.ensure(kbs.size() * sizeof(int4))) != FIRAL_OK)
+      return bail(rc);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(P->kr_alpha.p, ka.data(), ka.size() * sizeof(int2),
+                          cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(P->kr_dterm.p, kd.data(), kd.size() * sizeof(int4),
+                          cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(P->kr_bsum.p, kbs.data(), kbs.size() * sizeof(int4),
+                          cudaMemcpyHostToDevice, st);
+  }
+  // the host vectors above are read by the copies: wait for them before they go out of scope
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return bail(fail(FIRAL_ERR_CUDA, cudaGetErrorString(e)));
+  *out = P;
+  return FIRAL_OK;
+}
+
+// Batched Relax over pooled problems: pools grouped by padded feature width, lambda and storage
+// types (at most 4096 classes per group); each group is one problem whose MD iterations are
+// replayed, together with the other groups', from one CUDA graph.
+int32_t replay_steps(firal_handle* H, std::vector<firal_problem*>& probs,
+                     const std::vector<firal_relax_opts>& opts, const std::vector<double>& budgets,
+                     const std::vector<void*>& zs, int32_t t_next, int32_t t_end);
+
+int32_t batched_pooled(firal_handle* H, int32_t nq, const firal_pool* pools,
+                       const firal_hess0* hess0s, const double* budgets,
+                       const firal_relax_opts* opts, void* const* z_outs) {
+  const firal_relax_opts& o = *opts;
+  cudaStream_t st = H->stream;
+  for (int q = 0; q < nq; ++q) {
+    if (!z_outs[q] || !(budgets[q] > 0)) return fail(FIRAL_ERR_ARG, "bad z_out or budget");
+    FIRAL_TRY(validate_pool(&pools[q], hess0s ? &hess0s[q] : nullptr));
+  }
+  // groups
+  std::map<std::tuple<int, double, int, int>, std::vector<std::vector<int>>> groups;
+  for (int q = 0; q < nq; ++q) {
+    int dp = 16;
+    while (dp < pools[q].d) dp <<= 1;
+    auto& g = groups[std::make_tuple(dp, hess0s ? hess0s[q].lambda : 0.0, pools[q].x_dtype,
+                                     pools[q].h_dtype)];
+    int cl = 0;
+    if (!g.empty())
+      for (int i : g.back()) cl += pools[i].c;
+    if (g.empty() || cl + pools[q].c > 4096) g.emplace_back();
+    g.back().push_back(q);
+  }
+  std::vector<firal_problem*> probs;
+  std::vector<std::vector<int>> members;
+  std::vector<DBuf> zcat;
+  auto destroy_all = [&]() {
+    for (auto* p : probs) firal_problem_destroy(p);
+    for (auto& z : zcat) z.release();
+  };
+  int32_t rc = FIRAL_OK;
+  for (auto& kv : groups)
+    for (auto& idx : kv.second) {
+      firal_problem* P = nullptr;
+      rc = pooled_create(H, idx, pools, hess0s, budgets, o.precision, &P);
+      if (rc != FIRAL_OK) {
+        destroy_all();
+        return rc;
+      }
+      probs.push_back(P);
+      members.push_back(idx);
+    }
+  const int G = (int)probs.size();
+  zcat.resize(G);
+  std::vector<void*> zs(G);
+  for (int g = 0; g < G && rc == FIRAL_OK; ++g) {
+    firal_problem* P = probs[g];
+    rc = zcat[g].ensure((size_t)P->n * vsize(P));
+    // z starts at b_q / n_q on every pool (the uniform point of each simplex)
+    for (size_t i = 0; i < members[g].size() && rc == FIRAL_OK; ++i) {
+      const int q = members[g][i];
+      const int64_t a = P->pool_zoff_h[i], b = P->pool_zoff_h[i + 1];
+      rc = fill_weights(P->dbl, (char*)zcat[g].p + a * vsize(P), 0, 0.0, nullptr,
+                        budgets[q] / (double)(b - a), b - a, st);
+    }
+    zs[g] = zcat[g].p;
+  }
+  std::vector<firal_relax_opts> os(G, o);
+  std::vector<double> ones(G, 1.0);   // pooled problems take each pool's budget from their table
+  for (int g = 0; g < G && rc == FIRAL_OK && o.T > 0; ++g)
+    rc = relax_step_impl(probs[g], &o, 0, 1.0, zs[g], nullptr);
+  if (rc == FIRAL_OK && o.T > 1) rc = replay_steps(H, probs, os, ones, zs, 1, o.T);
+  // scatter each pool's z back to the caller's buffer
+  for (int g = 0; g < G && rc == FIRAL_OK; ++g) {
+    firal_problem* P = probs[g];
+    for (size_t i = 0; i < members[g].size() && rc == FIRAL_OK; ++i) {
+      const int q = members[g][i];
+      const int64_t a = P->pool_zoff_h[i], b = P->pool_zoff_h[i + 1];
+      const cudaError_t e = cudaMemcpyAsync(z_outs[q], (char*)zs[g] + a * vsize(P),
+                                            (b - a) * vsize(P), cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) rc = fail(FIRAL_ERR_CUDA, cudaGetErrorString(e));
+    }
+  }
+  if (rc == FIRAL_OK) {
+    const cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = fail(FIRAL_ERR_CUDA, cudaGetErrorString(e));
+  }
+  if (rc == FIRAL_OK) rc = read_flags(H);
+  destroy_all();
+  return rc;
+}
+
 }  // namespace
 
 // =========================================================================================
@@ -794,6 +1078,8 @@ int32_t firal_batched_relax(firal_handle* H, int32_t nproblems, const firal_pool
   if (!H || nproblems < 1 || !pools || !budgets || !opts || !z_outs)
     return record(H, fail(FIRAL_ERR_ARG, "bad batched_relax arguments"));
   const firal_relax_opts& o = *opts;
+  if (is_mixed(o.precision) && o.cg.fixed_iters > 0 && nproblems > 1)
+    return record(H, batched_pooled(H, nproblems, pools, hess0s, budgets, opts, z_outs));
   std::vector<firal_problem*> probs(nproblems, nullptr);
   auto destroy_all = [&]() {
     for (auto* p : probs) firal_problem_destroy(p);

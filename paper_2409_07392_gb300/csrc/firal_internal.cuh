@@ -104,8 +104,33 @@ struct firal_handle {
   std::string err;
 };
 
+namespace firal {
+// Pooled problem: Q independent pools stacked into one problem.  Classes and pool rows are
+// grouped by pool and every h row is zero outside its pool's classes, so the Hessians, the
+// preconditioner blocks and Sigma_z are block diagonal over pools; only the reductions that
+// define per-pool scalars (CG alpha/beta, class means, the MD normalisation) see the tables.
+// Q = 0: an ordinary problem (one pool, tables unused).
+struct PoolTab {
+  int Q = 0;
+  const int* cpool = nullptr;    // class -> pool (c entries)
+  const int* coff = nullptr;     // first class of each pool (Q + 1)
+  const int* pdim = nullptr;     // true feature dimension of each pool (Q); features above are 0
+};
+__host__ __device__ inline int pool_count(const PoolTab& t) { return t.Q > 0 ? t.Q : 1; }
+#ifdef __CUDACC__
+__device__ __forceinline__ int pool_of(const PoolTab& t, int k) { return t.Q ? t.cpool[k] : 0; }
+#endif
+}  // namespace firal
+
 struct firal_problem {
   int sms = 0;            // SM budget for grids and split counts (<= H->sm_count)
+  firal::PoolTab pt;      // pooled problems only (device tables below)
+  firal::DBuf pool_tabs;  // cpool | coff | pdim (int32) for pt
+  firal::DBuf pool_z;     // pooled: per-pool budgets (f64, Q) and pool-row offsets (i64, Q + 1)
+  std::vector<int64_t> pool_zoff_h;   // pooled: pool-row offsets, host copy
+  firal::DBuf kr_alpha, kr_dterm, kr_bsum;  // pooled: K ranges of the tensor-core GEMM tiles
+  int kbL = 0;                   // pooled: K-steps holding the labelled rows (every class tile)
+  int64_t kr_dterm_Lmax = 0, kr_bsum_Lmax = 0;   // pooled: longest class-tile K list
   firal_handle* H = nullptr;
   int32_t prec = FIRAL_FP32;
   bool dbl = false;            // vec type is double
@@ -151,7 +176,8 @@ int32_t transpose(bool dbl, void* dst, const void* src, int64_t rows, int cols, 
 int32_t fill_weights(bool dbl, void* w, int64_t m, double lab_val, const void* z, double zconst,
                      int64_t n, cudaStream_t st);
 int32_t probes(bool dbl, void* V, uint64_t seed, int64_t t, int s, int64_t D, cudaStream_t st,
-               const int64_t* t_dev = nullptr);
+               const int64_t* t_dev = nullptr, const PoolTab* pt = nullptr, int d = 0);
+int32_t md_step_pooled(firal_problem* P, void* z, const void* g, double beta0, cudaStream_t st);
 int32_t tick(int64_t* t_dev, cudaStream_t st);
 int32_t set_step(int64_t* t_dev, int64_t v, cudaStream_t st);
 int32_t syrk_blocks(firal_problem* P, const void* w, double lamS, void* outS, double lamP,

@@ -43,6 +43,23 @@ __device__ T block_sum(T v, T* red) {
   return r;
 }
 
+// Sums over groups of `gsz` consecutive threads (gsz a multiple of 32): every thread gets its
+// group's total, added in the same fixed order as block_sum over a gsz-thread block.
+// red must hold blockDim.x / 32 entries.
+template <class T>
+__device__ T group_sum(T v, T* red, int gsz) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, gw = gsz >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  const int g0 = (wid / gw) * gw;
+  T r = 0;
+  for (int i = 0; i < gw; ++i) r += red[g0 + i];
+  __syncthreads();
+  return r;
+}
+
 static inline int grid_for(int64_t total, int threads, int cap = 65535 * 8) {
   int64_t g = (total + threads - 1) / threads;
   if (g < 1) g = 1;
@@ -153,26 +170,40 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
 }
 
 template <class T>
+// Pooled problems: the entries of pool p are those of its own probe vector (dimension
+// d_p c_p, counters local to the pool) and 0 on the padded features e >= d_p.
 __global__ void k_probes(T* V, uint64_t seed, uint64_t t_host, const int64_t* t_dev, int s,
-                         int64_t D) {
+                         int64_t D, PoolTab pt, int d) {
   const uint64_t t = t_dev ? (uint64_t)*t_dev : t_host;
   const int64_t total = (int64_t)s * D;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t j = (uint64_t)(idx / D), q = (uint64_t)(idx % D);
-    const uint64_t ctr = (t * (uint64_t)s + j) * (uint64_t)D + q;
+    const uint64_t j = (uint64_t)(idx / D);
+    uint64_t q = (uint64_t)(idx % D), Dq = (uint64_t)D;
+    if (pt.Q) {
+      const int k = (int)(q / (uint64_t)d), e = (int)(q % (uint64_t)d);
+      const int p = pt.cpool[k], dq = pt.pdim[p];
+      if (e >= dq) {
+        V[idx] = T(0);
+        continue;
+      }
+      q = (uint64_t)(k - pt.coff[p]) * (uint64_t)dq + (uint64_t)e;
+      Dq = (uint64_t)(pt.coff[p + 1] - pt.coff[p]) * (uint64_t)dq;
+    }
+    const uint64_t ctr = (t * (uint64_t)s + j) * Dq + q;
     const uint64_t bits = splitmix64(seed ^ splitmix64(ctr));
     V[idx] = (bits >> 63) ? T(-1) : T(1);
   }
 }
 
 int32_t probes(bool dbl, void* V, uint64_t seed, int64_t t, int s, int64_t D, cudaStream_t st,
-               const int64_t* t_dev) {
+               const int64_t* t_dev, const PoolTab* pt, int d) {
   const int g = grid_for((int64_t)s * D, 256);
+  const PoolTab tab = pt ? *pt : PoolTab{};
   ProfScope ps(st, PF_PROBES);
   count_launch();
-  if (dbl) k_probes<double><<<g, 256, 0, st>>>((double*)V, seed, (uint64_t)t, t_dev, s, D);
-  else k_probes<float><<<g, 256, 0, st>>>((float*)V, seed, (uint64_t)t, t_dev, s, D);
+  if (dbl) k_probes<double><<<g, 256, 0, st>>>((double*)V, seed, (uint64_t)t, t_dev, s, D, tab, d);
+  else k_probes<float><<<g, 256, 0, st>>>((float*)V, seed, (uint64_t)t, t_dev, s, D, tab, d);
   FIRAL_CUDA_TRY(cudaGetLastError());
   return FIRAL_OK;
 }
@@ -479,43 +510,47 @@ __global__ __launch_bounds__(256) void k_dterm(const T* __restrict__ Xa, const T
 }
 
 // out_j[k] = S_k V_j[k] - sum_split Dpart[split][k][j d + .]; optional pq[j c + k] = V_j[k].out_j[k]
+// Block = class k x JB probes; thread (jj, e) with e < dpad = d rounded up to 32.
 template <class T, int JB>
 __global__ void k_combine(const T* __restrict__ S, const T* __restrict__ V,
                           const T* __restrict__ Dpart, int splits, int d, int c, int s, int64_t D,
-                          T* __restrict__ out, double* pq, const T* __restrict__ vmean) {
+                          T* __restrict__ out, double* pq, const T* __restrict__ vmean,
+                          PoolTab pt) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* Ss = (T*)smem_raw;            // d*d
   T* vs = Ss + (size_t)d * d;      // JB*d
   __shared__ double red[32];
   const int k = blockIdx.x;
   const int j0 = blockIdx.y * JB;
-  const int e = threadIdx.x;
+  const int dpad = (d + 31) & ~31;
+  const int jj = threadIdx.x / dpad, e = threadIdx.x - jj * dpad;
   for (int idx = threadIdx.x; idx < d * d; idx += blockDim.x) Ss[idx] = S[(int64_t)k * d * d + idx];
   for (int idx = threadIdx.x; idx < JB * d; idx += blockDim.x) {
-    const int jj = idx / d, f = idx - jj * d;
-    vs[idx] = (j0 + jj < s) ? V[(int64_t)(j0 + jj) * D + (int64_t)k * d + f] -
-                                  (vmean ? vmean[(j0 + jj) * d + f] : T(0))
-                            : T(0);
+    const int q = idx / d, f = idx - q * d;
+    const int vm = ((j0 + q) * pool_count(pt) + pool_of(pt, k)) * d + f;
+    vs[idx] = (j0 + q < s) ? V[(int64_t)(j0 + q) * D + (int64_t)k * d + f] -
+                                 (vmean ? vmean[vm] : T(0))
+                           : T(0);
   }
   __syncthreads();
   const int sd = s * d;
-  for (int jj = 0; jj < JB; ++jj) {
-    const int j = j0 + jj;
-    if (j >= s) break;
-    T q = T(0);
-    if (e < d) {
-      T acc = T(0);
-      for (int f = 0; f < d; ++f) acc = fma(Ss[f * d + e], vs[jj * d + f], acc);   // S symmetric
-      T dsum = T(0);
-      for (int sp = 0; sp < splits; ++sp) dsum += Dpart[((int64_t)sp * c + k) * sd + j * d + e];
-      q = acc - dsum;
-      out[(int64_t)j * D + (int64_t)k * d + e] = q;
-    }
-    if (pq) {
-      const double contrib = e < d ? (double)vs[jj * d + e] * (double)q : 0.0;
-      const double tot = block_sum(contrib, red);
-      if (threadIdx.x == 0) pq[(int64_t)j * c + k] = tot;
-    }
+  const int j = j0 + jj;
+  T q = T(0);
+  if (j < s && e < d) {
+    T acc = T(0);
+    for (int f = 0; f < d; ++f) acc = fma(Ss[f * d + e], vs[jj * d + f], acc);   // S symmetric
+    T dsum = T(0);
+    const T* dp = Dpart + (int64_t)k * sd + j * d + e;
+    const int64_t stride = (int64_t)c * sd;
+#pragma unroll 4
+    for (int sp = 0; sp < splits; ++sp) dsum += dp[sp * stride];
+    q = acc - dsum;
+    out[(int64_t)j * D + (int64_t)k * d + e] = q;
+  }
+  if (pq) {
+    const double contrib = (j < s && e < d) ? (double)vs[jj * d + e] * (double)q : 0.0;
+    const double tot = group_sum(contrib, red, dpad);
+    if (e == 0 && j < s) pq[(int64_t)j * c + k] = tot;
   }
 }
 
@@ -566,13 +601,13 @@ static int32_t apply_t(firal_problem* P, const T* w, const T* Sblk, const T* V, 
                                                    P->Dpart.as<T>());
   }
   FIRAL_CUDA_TRY(cudaGetLastError());
-  const int threads = ((d + 31) / 32) * 32;
+  const int threads = ((d + 31) / 32) * 32 * 4;   // 4 probes in parallel
   const size_t smem_c = ((size_t)d * d + 4 * (size_t)d) * sizeof(T);
   ProfScope ps(st, PF_COMBINE);
   count_launch();
   k_combine<T, 4><<<dim3(c, (s + 3) / 4), threads, smem_c, st>>>(Sblk, V, P->Dpart.as<T>(),
                                                                   splits, d, c, s, D, out, pq,
-                                                                  nullptr);
+                                                                  nullptr, P->pt);
   FIRAL_CUDA_TRY(cudaGetLastError());
   return FIRAL_OK;
 }
@@ -580,14 +615,14 @@ static int32_t apply_t(firal_problem* P, const T* w, const T* Sblk, const T* V, 
 int32_t combine_f32(firal_problem* P, const float* Sblk, const float* V, int splits, int s,
                     float* out, double* pq, const float* vmean) {
   const int d = P->d, c = P->c;
-  const int threads = ((d + 31) / 32) * 32;
+  const int threads = ((d + 31) / 32) * 32 * 4;   // 4 probes in parallel
   const size_t smem_c = ((size_t)d * d + 4 * (size_t)d) * sizeof(float);
   FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_combine<float, 4>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   ProfScope ps(P->H->stream, PF_COMBINE);
   count_launch();
   k_combine<float, 4><<<dim3(c, (s + 3) / 4), threads, smem_c, P->H->stream>>>(
-      Sblk, V, P->Dpart.as<float>(), splits, d, c, s, P->D, out, pq, vmean);
+      Sblk, V, P->Dpart.as<float>(), splits, d, c, s, P->D, out, pq, vmean, P->pt);
   FIRAL_CUDA_TRY(cudaGetLastError());
   return FIRAL_OK;
 }
@@ -610,35 +645,33 @@ __global__ void k_cg_init(const T* __restrict__ Minv, const T* __restrict__ B, i
                           int s, int64_t D, T* X, T* R, T* Z, T* Pd, double* p_rz, double* p_bb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* Ms = (T*)smem_raw;           // d*d
-  T* rs = Ms + (size_t)d * d;     // d
+  T* rs = Ms + (size_t)d * d;     // JB*d
   __shared__ double red[32];
-  const int k = blockIdx.x, e = threadIdx.x;
+  const int k = blockIdx.x;
+  const int dpad = (d + 31) & ~31;
+  const int jj = threadIdx.x / dpad, e = threadIdx.x - jj * dpad;
+  const int j = blockIdx.y * JB + jj;
   for (int idx = threadIdx.x; idx < d * d; idx += blockDim.x) Ms[idx] = Minv[(int64_t)k * d * d + idx];
-  for (int jj = 0; jj < JB; ++jj) {
-    const int j = blockIdx.y * JB + jj;
-    if (j >= s) break;
-    const int64_t base = (int64_t)j * D + (int64_t)k * d;
-    __syncthreads();
-    T r = T(0);
-    if (e < d) {
-      r = B[base + e];
-      rs[e] = r;
-    }
-    __syncthreads();
-    T z = T(0);
-    if (e < d) {
-      for (int f = 0; f < d; ++f) z = fma(Ms[f * d + e], rs[f], z);
-      X[base + e] = T(0);
-      R[base + e] = r;
-      Z[base + e] = z;
-      Pd[base + e] = z;
-    }
-    const double rz = block_sum(e < d ? (double)r * (double)z : 0.0, red);
-    const double bb = block_sum(e < d ? (double)r * (double)r : 0.0, red);
-    if (threadIdx.x == 0) {
-      p_rz[(int64_t)j * c + k] = rz;
-      p_bb[(int64_t)j * c + k] = bb;
-    }
+  const int64_t base = (int64_t)j * D + (int64_t)k * d;
+  T r = T(0);
+  if (j < s && e < d) {
+    r = B[base + e];
+    rs[jj * d + e] = r;
+  }
+  __syncthreads();
+  T z = T(0);
+  if (j < s && e < d) {
+    for (int f = 0; f < d; ++f) z = fma(Ms[f * d + e], rs[jj * d + f], z);
+    X[base + e] = T(0);
+    R[base + e] = r;
+    Z[base + e] = z;
+    Pd[base + e] = z;
+  }
+  const double rz = group_sum(e < d ? (double)r * (double)z : 0.0, red, dpad);
+  const double bb = group_sum(e < d ? (double)r * (double)r : 0.0, red, dpad);
+  if (e == 0 && j < s) {
+    p_rz[(int64_t)j * c + k] = rz;
+    p_bb[(int64_t)j * c + k] = bb;
   }
 }
 
@@ -650,12 +683,27 @@ __device__ __forceinline__ double warp_reduce_partials(const double* p, int c) {
   return warp_sum(acc);
 }
 
+// CG scalars live per (column j, pool p) at cols[j * Qe + p]: the partials of the pool's
+// classes [k0, k1) are reduced (all classes for an ordinary problem).
+__device__ __forceinline__ bool cg_slot(const PoolTab& pt, int c, int s, int& j, int& k0,
+                                        int& k1) {
+  const int Qe = pool_count(pt);
+  const int slot = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (slot >= s * Qe) return false;
+  j = slot / Qe;
+  const int p = slot - j * Qe;
+  k0 = pt.Q ? pt.coff[p] : 0;
+  k1 = pt.Q ? pt.coff[p + 1] : c;
+  return true;
+}
+
 __global__ void k_cg_init_cols(const double* p_rz, const double* p_bb, int c, int s, double tol,
-                               int fixed, CGCol* cols) {
-  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (j >= s) return;
-  const double rz = warp_reduce_partials(p_rz + (int64_t)j * c, c);
-  const double bb = warp_reduce_partials(p_bb + (int64_t)j * c, c);
+                               int fixed, CGCol* cols, PoolTab pt) {
+  int j, k0, k1;
+  if (!cg_slot(pt, c, s, j, k0, k1)) return;
+  const int slot = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const double rz = warp_reduce_partials(p_rz + (int64_t)j * c + k0, k1 - k0);
+  const double bb = warp_reduce_partials(p_bb + (int64_t)j * c + k0, k1 - k0);
   if ((threadIdx.x & 31) == 0) {
     CGCol cc;
     cc.rho = rz;
@@ -665,74 +713,74 @@ __global__ void k_cg_init_cols(const double* p_rz, const double* p_bb, int c, in
     cc.relres = bb > 0 ? 1.0 : 0.0;
     cc.iters = 0;
     cc.active = (bb > 0.0) && (fixed || !(1.0 <= tol)) ? 1 : 0;
-    cols[j] = cc;
+    cols[slot] = cc;
   }
 }
 
-__global__ void k_cg_alpha(const double* p_pq, int c, int s, CGCol* cols) {
-  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (j >= s) return;
-  const double pq = warp_reduce_partials(p_pq + (int64_t)j * c, c);
+__global__ void k_cg_alpha(const double* p_pq, int c, int s, CGCol* cols, PoolTab pt) {
+  int j, k0, k1;
+  if (!cg_slot(pt, c, s, j, k0, k1)) return;
+  const int slot = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const double pq = warp_reduce_partials(p_pq + (int64_t)j * c + k0, k1 - k0);
   if ((threadIdx.x & 31) == 0) {
-    CGCol cc = cols[j];
+    CGCol cc = cols[slot];
     if (cc.active && pq > 0.0 && isfinite(pq)) {
       cc.alpha = cc.rho / pq;
     } else {
       cc.active = 0;
       cc.alpha = 0.0;
     }
-    cols[j] = cc;
+    cols[slot] = cc;
   }
 }
 
 template <class T, int JB>
 __global__ void k_cg_update(const T* __restrict__ Minv, int d, int c, int s, int64_t D,
                             const CGCol* __restrict__ cols, T* X, T* R, const T* Pd,
-                            const T* Q, T* Z, double* p_rr, double* p_rz) {
+                            const T* Q, T* Z, double* p_rr, double* p_rz, PoolTab pt) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* Ms = (T*)smem_raw;
-  T* rs = Ms + (size_t)d * d;
+  T* rs = Ms + (size_t)d * d;     // JB*d
   __shared__ double red[32];
-  const int k = blockIdx.x, e = threadIdx.x;
+  const int k = blockIdx.x;
+  const int dpad = (d + 31) & ~31;
+  const int jj = threadIdx.x / dpad, e = threadIdx.x - jj * dpad;
+  const int j = blockIdx.y * JB + jj;
   for (int idx = threadIdx.x; idx < d * d; idx += blockDim.x) Ms[idx] = Minv[(int64_t)k * d * d + idx];
-  for (int jj = 0; jj < JB; ++jj) {
-    const int j = blockIdx.y * JB + jj;
-    if (j >= s) break;
-    const CGCol cc = cols[j];
-    __syncthreads();
-    if (!cc.active) continue;   // uniform over the block
-    const int64_t base = (int64_t)j * D + (int64_t)k * d;
-    const T a = (T)cc.alpha;
-    T r = T(0);
-    if (e < d) {
-      X[base + e] = fma(a, Pd[base + e], X[base + e]);
-      r = fma(-a, Q[base + e], R[base + e]);
-      R[base + e] = r;
-      rs[e] = r;
-    }
-    __syncthreads();
-    T z = T(0);
-    if (e < d) {
-      for (int f = 0; f < d; ++f) z = fma(Ms[f * d + e], rs[f], z);
-      Z[base + e] = z;
-    }
-    const double rr = block_sum(e < d ? (double)r * (double)r : 0.0, red);
-    const double rz = block_sum(e < d ? (double)r * (double)z : 0.0, red);
-    if (threadIdx.x == 0) {
-      p_rr[(int64_t)j * c + k] = rr;
-      p_rz[(int64_t)j * c + k] = rz;
-    }
+  const int slot = j * pool_count(pt) + pool_of(pt, k);
+  const bool live = j < s && cols[slot].active;   // uniform over the probe's thread group
+  const int64_t base = (int64_t)j * D + (int64_t)k * d;
+  T r = T(0);
+  if (live && e < d) {
+    const T a = (T)cols[slot].alpha;
+    X[base + e] = fma(a, Pd[base + e], X[base + e]);
+    r = fma(-a, Q[base + e], R[base + e]);
+    R[base + e] = r;
+    rs[jj * d + e] = r;
+  }
+  __syncthreads();
+  T z = T(0);
+  if (live && e < d) {
+    for (int f = 0; f < d; ++f) z = fma(Ms[f * d + e], rs[jj * d + f], z);
+    Z[base + e] = z;
+  }
+  const double rr = group_sum(e < d ? (double)r * (double)r : 0.0, red, dpad);
+  const double rz = group_sum(e < d ? (double)r * (double)z : 0.0, red, dpad);
+  if (live && e == 0) {
+    p_rr[(int64_t)j * c + k] = rr;
+    p_rz[(int64_t)j * c + k] = rz;
   }
 }
 
 __global__ void k_cg_beta(const double* p_rr, const double* p_rz, int c, int s, double tol,
-                          int fixed, CGCol* cols) {
-  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (j >= s) return;
-  const double rr = warp_reduce_partials(p_rr + (int64_t)j * c, c);
-  const double rz = warp_reduce_partials(p_rz + (int64_t)j * c, c);
+                          int fixed, CGCol* cols, PoolTab pt) {
+  int j, k0, k1;
+  if (!cg_slot(pt, c, s, j, k0, k1)) return;
+  const int slot = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const double rr = warp_reduce_partials(p_rr + (int64_t)j * c + k0, k1 - k0);
+  const double rz = warp_reduce_partials(p_rz + (int64_t)j * c + k0, k1 - k0);
   if ((threadIdx.x & 31) == 0) {
-    CGCol cc = cols[j];
+    CGCol cc = cols[slot];
     if (cc.active) {
       cc.iters += 1;
       cc.relres = sqrt(rr / cc.bnorm2);
@@ -743,17 +791,20 @@ __global__ void k_cg_beta(const double* p_rr, const double* p_rz, int c, int s, 
         cc.rho = rz;
       }
     }
-    cols[j] = cc;
+    cols[slot] = cc;
   }
 }
 
 template <class T>
-__global__ void k_cg_pupdate(const CGCol* __restrict__ cols, int s, int64_t D, const T* Z, T* Pd) {
+__global__ void k_cg_pupdate(const CGCol* __restrict__ cols, int s, int64_t D, const T* Z, T* Pd,
+                             PoolTab pt, int d) {
   const int64_t total = (int64_t)s * D;
+  const int Qe = pool_count(pt);
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int j = (int)(idx / D);
-    const CGCol cc = cols[j];
+    const int p = pt.Q ? pt.cpool[(int)((idx - (int64_t)j * D) / d)] : 0;
+    const CGCol cc = cols[j * Qe + p];
     if (cc.active) Pd[idx] = fma((T)cc.beta, Pd[idx], Z[idx]);
   }
 }
@@ -774,7 +825,7 @@ static int32_t cg_setup_attrs() {
 int32_t cg_init(firal_problem* P, const void* B, int s, double tol, int fixed) {
   cudaStream_t st = P->H->stream;
   const int d = P->d, c = P->c;
-  const int threads = ((d + 31) / 32) * 32;
+  const int threads = ((d + 31) / 32) * 32 * 4;   // 4 probes in parallel
   double* p1 = P->cgpart1.as<double>();
   double* p2 = P->cgpart2.as<double>();
   CGCol* cols = P->cgcols.as<CGCol>();
@@ -782,19 +833,20 @@ int32_t cg_init(firal_problem* P, const void* B, int s, double tol, int fixed) {
   count_launch(2);
   if (P->dbl) {
     FIRAL_TRY(cg_setup_attrs<double>());
-    const size_t sm = ((size_t)d * d + d) * sizeof(double);
+    const size_t sm = ((size_t)d * d + 4 * (size_t)d) * sizeof(double);
     k_cg_init<double, 4><<<dim3(c, (s + 3) / 4), threads, sm, st>>>(
         P->Minv.as<double>(), (const double*)B, d, c, s, P->D, P->cgX.as<double>(),
         P->cgR.as<double>(), P->cgZ.as<double>(), P->cgP.as<double>(), p1, p2);
   } else {
     FIRAL_TRY(cg_setup_attrs<float>());
-    const size_t sm = ((size_t)d * d + d) * sizeof(float);
+    const size_t sm = ((size_t)d * d + 4 * (size_t)d) * sizeof(float);
     k_cg_init<float, 4><<<dim3(c, (s + 3) / 4), threads, sm, st>>>(
         P->Minv.as<float>(), (const float*)B, d, c, s, P->D, P->cgX.as<float>(),
         P->cgR.as<float>(), P->cgZ.as<float>(), P->cgP.as<float>(), p1, p2);
   }
   FIRAL_CUDA_TRY(cudaGetLastError());
-  k_cg_init_cols<<<(s + 3) / 4, 128, 0, st>>>(p1, p2, c, s, tol, fixed, cols);
+  const int slots = s * pool_count(P->pt);
+  k_cg_init_cols<<<(slots + 3) / 4, 128, 0, st>>>(p1, p2, c, s, tol, fixed, cols, P->pt);
   FIRAL_CUDA_TRY(cudaGetLastError());
   return FIRAL_OK;
 }
@@ -803,33 +855,34 @@ int32_t cg_init(firal_problem* P, const void* B, int s, double tol, int fixed) {
 int32_t cg_iterate_tail(firal_problem* P, int s, double tol, int fixed) {
   cudaStream_t st = P->H->stream;
   const int d = P->d, c = P->c;
-  const int threads = ((d + 31) / 32) * 32;
+  const int threads = ((d + 31) / 32) * 32 * 4;   // 4 probes in parallel
   double* p1 = P->cgpart1.as<double>();
   double* p2 = P->cgpart2.as<double>();
   CGCol* cols = P->cgcols.as<CGCol>();
   ProfScope ps(st, PF_CG);
   count_launch(4);
-  k_cg_alpha<<<(s + 3) / 4, 128, 0, st>>>(p1, c, s, cols);
+  const int slots = s * pool_count(P->pt);
+  k_cg_alpha<<<(slots + 3) / 4, 128, 0, st>>>(p1, c, s, cols, P->pt);
   FIRAL_CUDA_TRY(cudaGetLastError());
   const int64_t total = (int64_t)s * P->D;
   if (P->dbl) {
-    const size_t sm = ((size_t)d * d + d) * sizeof(double);
+    const size_t sm = ((size_t)d * d + 4 * (size_t)d) * sizeof(double);
     k_cg_update<double, 4><<<dim3(c, (s + 3) / 4), threads, sm, st>>>(
         P->Minv.as<double>(), d, c, s, P->D, cols, P->cgX.as<double>(), P->cgR.as<double>(),
-        P->cgP.as<double>(), P->cgQ.as<double>(), P->cgZ.as<double>(), p1, p2);
+        P->cgP.as<double>(), P->cgQ.as<double>(), P->cgZ.as<double>(), p1, p2, P->pt);
     FIRAL_CUDA_TRY(cudaGetLastError());
-    k_cg_beta<<<(s + 3) / 4, 128, 0, st>>>(p1, p2, c, s, tol, fixed, cols);
+    k_cg_beta<<<(slots + 3) / 4, 128, 0, st>>>(p1, p2, c, s, tol, fixed, cols, P->pt);
     k_cg_pupdate<double><<<grid_for(total, 256), 256, 0, st>>>(cols, s, P->D, P->cgZ.as<double>(),
-                                                              P->cgP.as<double>());
+                                                              P->cgP.as<double>(), P->pt, d);
   } else {
-    const size_t sm = ((size_t)d * d + d) * sizeof(float);
+    const size_t sm = ((size_t)d * d + 4 * (size_t)d) * sizeof(float);
     k_cg_update<float, 4><<<dim3(c, (s + 3) / 4), threads, sm, st>>>(
         P->Minv.as<float>(), d, c, s, P->D, cols, P->cgX.as<float>(), P->cgR.as<float>(),
-        P->cgP.as<float>(), P->cgQ.as<float>(), P->cgZ.as<float>(), p1, p2);
+        P->cgP.as<float>(), P->cgQ.as<float>(), P->cgZ.as<float>(), p1, p2, P->pt);
     FIRAL_CUDA_TRY(cudaGetLastError());
-    k_cg_beta<<<(s + 3) / 4, 128, 0, st>>>(p1, p2, c, s, tol, fixed, cols);
+    k_cg_beta<<<(slots + 3) / 4, 128, 0, st>>>(p1, p2, c, s, tol, fixed, cols, P->pt);
     k_cg_pupdate<float><<<grid_for(total, 256), 256, 0, st>>>(cols, s, P->D, P->cgZ.as<float>(),
-                                                             P->cgP.as<float>());
+                                                             P->cgP.as<float>(), P->pt, d);
   }
   FIRAL_CUDA_TRY(cudaGetLastError());
   return FIRAL_OK;
@@ -1051,6 +1104,56 @@ __global__ void k_md_zmax(double* red) {
     for (int i = 0; i < 256; ++i) r = red[768 + i] > r ? red[768 + i] : r;
     red[513] = r;
   }
+}
+
+// Pooled problems: the MD update of every pool on its own simplex (Alg. 2 lines 10-11 with
+// that pool's ||g||_inf and budget).  One block per pool; pool p owns z[zoff[p] .. zoff[p+1]).
+template <class T>
+__global__ void k_md_pooled(T* z, const T* g, const int64_t* zoff, const double* budget,
+                            double beta0) {
+  __shared__ double red[32];
+  __shared__ double s_val;
+  const int p = blockIdx.x;
+  const int64_t a = zoff[p], b = zoff[p + 1];
+  double mx = 0.0;
+  for (int64_t i = a + threadIdx.x; i < b; i += blockDim.x) {
+    const double v = fabs((double)g[i]);
+    mx = (v > mx || v != v) ? v : mx;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double other = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = (other > mx || other != other) ? other : mx;
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r = (red[i] > r || red[i] != red[i]) ? red[i] : r;
+    s_val = r > 0.0 ? beta0 / r : 0.0;
+  }
+  __syncthreads();
+  const double beta = s_val;
+  double acc = 0.0;
+  for (int64_t i = a + threadIdx.x; i < b; i += blockDim.x) {
+    const T zn = (T)((double)z[i] * exp(-beta * (double)g[i]));
+    z[i] = zn;
+    acc += (double)zn;
+  }
+  const double tot = block_sum(acc, red);
+  const double sc = budget[p] / tot;
+  for (int64_t i = a + threadIdx.x; i < b; i += blockDim.x) z[i] = (T)((double)z[i] * sc);
+}
+
+int32_t md_step_pooled(firal_problem* P, void* z, const void* g, double beta0, cudaStream_t st) {
+  const int Q = P->pt.Q;
+  const double* budget = P->pool_z.as<double>();
+  const int64_t* zoff = reinterpret_cast<const int64_t*>(budget + Q);
+  ProfScope ps(st, PF_MD);
+  count_launch();
+  if (P->dbl) k_md_pooled<double><<<Q, 1024, 0, st>>>((double*)z, (const double*)g, zoff, budget, beta0);
+  else k_md_pooled<float><<<Q, 1024, 0, st>>>((float*)z, (const float*)g, zoff, budget, beta0);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  return FIRAL_OK;
 }
 
 int32_t md_step_simt(bool dbl, void* z, const void* g, int64_t n, double budget, double beta0,

@@ -126,14 +126,17 @@ __global__ void k_block_transpose_bf16(bf16* dst, const bf16* src, int64_t rows_
 // (NPART = 2) or rows (j, e) holding bf16(P) alone (NPART = 1)
 template <int NPART>
 __global__ void k_split_probes(bf16* Pt, const float* P, const float* vmean, int s, int c, int d,
-                               int dp, int cp, int64_t D) {
+                               int dp, int cp, int64_t D, PoolTab pt) {
   __shared__ float tile[32][33];
   const int j = blockIdx.z;
   const int k0 = blockIdx.x * 32, e0 = blockIdx.y * 32;
+  const int Qe = pool_count(pt);
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
     const int k = k0 + i, e = e0 + threadIdx.x;
     tile[i][threadIdx.x] =
-        (k < c && e < d) ? P[(int64_t)j * D + (int64_t)k * d + e] - vmean[j * d + e] : 0.0f;
+        (k < c && e < d)
+            ? P[(int64_t)j * D + (int64_t)k * d + e] - vmean[(j * Qe + pool_of(pt, k)) * d + e]
+            : 0.0f;
   }
   __syncthreads();
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
@@ -155,38 +158,45 @@ __global__ void k_split_probes(bf16* Pt, const float* P, const float* vmean, int
 //     Sigma V = P_perp (Sigma~ (P_perp V)) + lambda_N P_N V,
 // with P_N V = the class mean of V replicated over classes (exact in real arithmetic).
 // ------------------------------------------------------------------------------------------
-// mean[j][e] = (1/c) sum_k V[j][k][e]; one block per probe, 1024 threads = (class group, e),
-// the groups combined in a fixed order (deterministic)
-__global__ void k_class_mean(const float* V, int s, int c, int d, int64_t D, float* mean) {
+// mean[j][p][e] = mean over the classes k of pool p of V[j][k][e] (all classes for an ordinary
+// problem); one block per (probe, pool), 1024 threads = (class group, e), the groups combined
+// in a fixed order (deterministic)
+__global__ void k_class_mean(const float* V, int s, int c, int d, int64_t D, float* mean,
+                             PoolTab pt) {
   __shared__ double part[1024];
-  const int j = blockIdx.x;
+  const int Qe = pool_count(pt);
+  const int j = blockIdx.x / Qe, p = blockIdx.x - j * Qe;
+  const int k0 = pt.Q ? pt.coff[p] : 0, k1 = pt.Q ? pt.coff[p + 1] : c;
   const int dpad = (d + 31) / 32 * 32;
   const int groups = 1024 / dpad;
   const int e = threadIdx.x % dpad, g = threadIdx.x / dpad;
   double acc = 0.0;
   if (e < d && g < groups)
-    for (int k = g; k < c; k += groups) acc += (double)V[(int64_t)j * D + (int64_t)k * d + e];
+    for (int k = k0 + g; k < k1; k += groups) acc += (double)V[(int64_t)j * D + (int64_t)k * d + e];
   part[threadIdx.x] = acc;
   __syncthreads();
   if (threadIdx.x < d) {
     double tot = 0.0;
     for (int q = 0; q < groups; ++q) tot += part[q * dpad + threadIdx.x];
-    mean[j * d + threadIdx.x] = (float)(tot / c);
+    mean[(j * Qe + p) * d + threadIdx.x] = (float)(tot / (k1 - k0));
   }
 }
 
 // out = out - qmean + lam_null * vmean (per class block); pq[j c + k] = <V_j[k], out_j[k]>
 __global__ void k_project(float* out, const float* qmean, const float* vmean, const float* V,
-                          double lam_null, int s, int c, int d, int64_t D, double* pq) {
+                          double lam_null, int s, int c, int d, int64_t D, double* pq,
+                          PoolTab pt) {
   __shared__ double red[32];
   const int k = blockIdx.x, e = threadIdx.x;
+  const int Qe = pool_count(pt), pk = pool_of(pt, k);
   for (int jj = 0; jj < 4; ++jj) {
     const int j = blockIdx.y * 4 + jj;
     if (j >= s) break;
     double contrib = 0.0;
     if (e < d) {
       const int64_t o = (int64_t)j * D + (int64_t)k * d + e;
-      const float q = out[o] - qmean[j * d + e] + (float)(lam_null * (double)vmean[j * d + e]);
+      const int m = (j * Qe + pk) * d + e;
+      const float q = out[o] - qmean[m] + (float)(lam_null * (double)vmean[m]);
       out[o] = q;
       contrib = (double)V[o] * (double)q;
     }
@@ -252,7 +262,7 @@ __global__ void __launch_bounds__(256, 1)
                const __grid_constant__ CUtensorMap mapHL, const bf16* __restrict__ Xb,
                const float* __restrict__ w, bf16* __restrict__ aT, float* __restrict__ out32,
                int64_t N, int64_t Np, int s, int kblocks, int n_mt, int n_nt, int npairs, int d,
-               int32_t* err) {
+               int32_t* err, const int2* __restrict__ krange) {
   using namespace alpha_cfg;
   constexpr int NST = HLO ? STAGES_H : STAGES;
   constexpr int SB = STAGE_BYTES + (HLO ? A_BYTES : 0);
@@ -299,7 +309,9 @@ __global__ void __launch_bounds__(256, 1)
     uint32_t phase = 0;
     for (int tile = blockIdx.x; tile < ntiles && !*abort_w; tile += gridDim.x) {
       const int mt = tile / n_nt, nt = tile % n_nt;
-      for (int kb = 0; kb < kblocks; ++kb) {
+      // pooled problems: only the class blocks of the pools in this point tile are non-zero
+      const int kb_lo = krange ? krange[mt].x : 0, kb_hi = krange ? krange[mt].y : kblocks;
+      for (int kb = kb_lo; kb < kb_hi; ++kb) {
         if (!mbar_wait(&ctl->empty[stage], phase ^ 1, abort_w)) {
           raise_abort(ctl, err, 1);
           break;
@@ -338,7 +350,9 @@ __global__ void __launch_bounds__(256, 1)
       tc_fence_after();
       const uint32_t d = tmem + acc * BN;
       bool ok = true;
-      for (int kb = 0; kb < kblocks; ++kb) {
+      const int mt = tile / n_nt;
+      const int kb_lo = krange ? krange[mt].x : 0, kb_hi = krange ? krange[mt].y : kblocks;
+      for (int kb = kb_lo; kb < kb_hi; ++kb) {
         if (!mbar_wait(&ctl->full[stage], phase, abort_w)) {
           raise_abort(ctl, err, 3);
           ok = false;
@@ -350,7 +364,7 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll
         for (int k = 0; k < BK / 16; ++k) {
           umma_bf16(d, sdesc_sw128(a0 + k * 32), sdesc_sw128(b0 + k * 32), idesc,
-                    (kb | k) != 0);
+                    (kb != kb_lo || k != 0) ? 1u : 0u);
           if (HLO) {
             const uint64_t al = sdesc_sw128(a0 + A_BYTES + k * 32);
             if (MODE == 2) {
@@ -386,19 +400,37 @@ __global__ void __launch_bounds__(256, 1)
     uint32_t acc_phase = 0;
     for (int tile = blockIdx.x; tile < ntiles && !*abort_w; tile += gridDim.x) {
       const int mt = tile / n_nt, nt = tile % n_nt;
+      const int64_t row = (int64_t)mt * BM + q * 32 + lane;
+      // the thread's x row (packed bf16 pairs) and weight, fetched before the accumulator
+      // wait so the global-load latency overlaps the tile's MMAs; reused by every probe/part
+      uint32_t xp[DP / 2];
+      {
+        const uint4* src = reinterpret_cast<const uint4*>(Xb + (row < Np ? row : 0) * DP);
+#pragma unroll
+        for (int t = 0; t < DP / 8; ++t) {
+          const uint4 u = src[t];
+          xp[4 * t] = u.x;
+          xp[4 * t + 1] = u.y;
+          xp[4 * t + 2] = u.z;
+          xp[4 * t + 3] = u.w;
+        }
+      }
+      const float wi = (MODE == 0) ? (row < N ? w[row] : 0.0f) : 1.0f;
       if (!mbar_wait(&ctl->tfull[acc], acc_phase, abort_w)) {
         raise_abort(ctl, err, 4);
         break;
       }
       tc_fence_after();
-      const int64_t row = (int64_t)mt * BM + q * 32 + lane;
       const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + acc * BN;
-      const float wi = (MODE == 0) ? (row < N ? w[row] : 0.0f) : 1.0f;
       if (MODE == 2) {
         // term1 partial: sum over the 128 pairs of this tile of x_e x_e' (T_hi + T_lo)
         const int tcol = q * 32 + lane;
-        const bf16* xr = Xb + row * DP;
-        for (int e = 0; e < DP; ++e) xsT[e * BM + tcol] = xr[e];
+#pragma unroll
+        for (int t = 0; t < DP / 2; ++t) {
+          const __nv_bfloat162 pr = *reinterpret_cast<const __nv_bfloat162*>(&xp[t]);
+          xsT[(2 * t) * BM + tcol] = pr.x;
+          xsT[(2 * t + 1) * BM + tcol] = pr.y;
+        }
         float acc1 = 0.0f;
         int e = 0, e2 = 0;
         const int p0 = nt * (BN / 2);
@@ -429,31 +461,20 @@ __global__ void __launch_bounds__(256, 1)
         float sum = 0.0f;
 #pragma unroll 1
         for (int part = 0; part < NPART; ++part) {
-#pragma unroll 1
-          for (int ec = 0; ec < DP; ec += (DP < 32 ? DP : 32)) {
+          constexpr int CW = DP < 32 ? DP : 32;
+#pragma unroll
+          for (int ec = 0; ec < DP; ec += CW) {
             float v[32];
-            float xv[32];
-            const int cw = DP < 32 ? DP : 32;
             const uint32_t col = (uint32_t)((jj * NPART + part) * DP + ec);
-            if (cw == 32) tmem_ld32(tbase + col, v);
+            if (CW == 32) tmem_ld32(tbase + col, v);
             else tmem_ld16(tbase + col, v);
-            const bf16* xr = Xb + (row < Np ? row : 0) * DP + ec;
 #pragma unroll
-            for (int t = 0; t < 32; t += 8) {
-              if (t < cw) {
-                const uint4 u = *reinterpret_cast<const uint4*>(xr + t);
-                const __nv_bfloat162* p2 = reinterpret_cast<const __nv_bfloat162*>(&u);
-#pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                  const float2 f = __bfloat1622float2(p2[h]);
-                  xv[t + 2 * h] = f.x;
-                  xv[t + 2 * h + 1] = f.y;
-                }
-              }
+            for (int t = 0; t < CW; t += 2) {
+              const float2 f =
+                  __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&xp[(ec + t) / 2]));
+              sum = fmaf(f.x, v[t], sum);
+              sum = fmaf(f.y, v[t + 1], sum);
             }
-#pragma unroll
-            for (int t = 0; t < 32; ++t)
-              if (t < cw) sum = fmaf(xv[t], v[t], sum);
           }
         }
         // MODE 0 also zeroes the padding rows N..Np-1: the D-GEMM multiplies them by zero x
@@ -510,7 +531,8 @@ __global__ void __launch_bounds__(256, 1)
     k_tc_dterm(const __grid_constant__ CUtensorMap mapHT, const __grid_constant__ CUtensorMap mapXT,
                const __grid_constant__ CUtensorMap mapAT, float* __restrict__ Dpart, int64_t N,
                int c, int d, int s, int n_mt, int n_nt, int splits, int64_t kb_per_split,
-               int64_t kb_total, int sp16, int32_t* err) {
+               int64_t kb_total, int sp16, int32_t* err, const int4* __restrict__ klist,
+               int kbL) {
   using namespace d_cfg;
   using St = Stage<DP>;
   constexpr int STAGES = St::STAGES;
@@ -555,8 +577,21 @@ __global__ void __launch_bounds__(256, 1)
     const int rest = u / n_nt;
     mt = rest % n_mt;
     const int sp = rest / n_mt;
-    kb0 = (int64_t)sp * kb_per_split;
-    kb1 = kb0 + kb_per_split < kb_total ? kb0 + kb_per_split : kb_total;
+    if (klist) {
+      // pooled: the tile's K list (virtual K-steps 0..L-1) is split evenly; a unit past its
+      // end is empty
+      const int64_t L = klist[mt].z, per = (L + splits - 1) / splits;
+      kb0 = (int64_t)sp * per;
+      kb1 = kb0 + per < L ? kb0 + per : L;
+      if (kb0 > kb1) kb0 = kb1;
+    } else {
+      kb0 = (int64_t)sp * kb_per_split;
+      kb1 = kb0 + kb_per_split < kb_total ? kb0 + kb_per_split : kb_total;
+    }
+  };
+  // virtual K-step of tile mt -> K-step of the points (labelled blocks, then the pools' rows)
+  auto real_kb = [&](int mt, int64_t v) -> int64_t {
+    return (!klist || v < kbL) ? v : klist[mt].x + (v - kbL);
   };
 
   if (warp == 0 && lane == 0) {
@@ -580,12 +615,13 @@ __global__ void __launch_bounds__(256, 1)
         mbar_expect_tx(&ctl->full[stage], TX);
         // K-block-major operands: block kb holds n_mt * MT class tiles, DP rows of x^T and
         // sp16 rows of walpha^T, each row 64 points
+        const int64_t kr = real_kb(mt, kb);
 #pragma unroll
         for (int a = 0; a < MT; ++a)
           tma_load_2d(st + a * A_BYTES, &mapHT, &ctl->full[stage], 0,
-                      (int)((kb * n_mt + mt) * MT + a) * BM);
-        tma_load_2d(st + OFF_XT, &mapXT, &ctl->full[stage], 0, (int)(kb * DP));
-        tma_load_2d(st + OFF_AT, &mapAT, &ctl->full[stage], 0, (int)(kb * sp16 + nt * PPN));
+                      (int)((kr * n_mt + mt) * MT + a) * BM);
+        tma_load_2d(st + OFF_XT, &mapXT, &ctl->full[stage], 0, (int)(kr * DP));
+        tma_load_2d(st + OFF_AT, &mapAT, &ctl->full[stage], 0, (int)(kr * sp16 + nt * PPN));
         if (++stage == STAGES) {
           stage = 0;
           phase ^= 1;
@@ -609,6 +645,7 @@ __global__ void __launch_bounds__(256, 1)
       int mt, nt;
       int64_t kb0, kb1;
       unit_range(u, mt, nt, kb0, kb1);
+      if (kb0 >= kb1) continue;   // empty unit: the epilogue writes zeros without the MMA
       if (!mbar_wait(&ctl->tempty[0], acc_phase ^ 1, abort_w)) {
         raise_abort(ctl, err, 12);
         break;
@@ -701,6 +738,25 @@ __global__ void __launch_bounds__(256, 1)
         }
       }
       if (!ok) break;
+      if (kb0 >= kb1) {
+        // empty unit: its partial block is zero
+        if (warp >= 4) {
+          const int q = warp & 3;
+          const int sp = (u / n_nt) / n_mt;
+          const int sd = s * d;
+          for (int a = 0; a < MT; ++a) {
+            const int k = (mt * MT + a) * BM + q * 32 + lane;
+            if (k >= c) continue;
+            float* out = Dpart + ((int64_t)sp * c + k) * sd;
+            for (int cc = 0; cc < BN; ++cc) {
+              const int col = nt * BN + cc;
+              const int j = col / DP, e = col - j * DP;
+              if (j < s && e < d) out[j * d + e] = 0.0f;
+            }
+          }
+        }
+        continue;
+      }
       if (warp >= 4) {
         const int q = warp & 3;
         if (!mbar_wait(&ctl->tfull[0], acc_phase, abort_w)) {
@@ -758,13 +814,13 @@ __global__ void __launch_bounds__(256, 1)
 // Accumulation length.  The tensor core adds each product block into its f32 accumulator with
 // a rounding that is biased (the sum loses magnitude on every add), so a chain of m adds into
 // one accumulator carries a relative bias of roughly m * 2^-25; a split of 200k points is
-// 37,500 adds, a 1e-3 bias that no averaging removes.  In MODE 0, S therefore accumulates in
-// TMEM for at most SUB = 8 K-steps (96 adds) at a time, alternating between two short
-// buffers, and the epilogue warps fold each finished short buffer into a long TMEM accumulator
-// with round-to-nearest f32 adds while the MMA fills the other.  P only preconditions CG (a
-// biased P changes the iterates, not the solution): MODE 1 accumulates over the whole unit,
-// double-buffered across units.
-// TMEM columns: [0,128) short 0 | [128,256) short 1 | [256,384) S long.
+// 37,500 adds, a 1e-3 bias that no averaging removes.  Both sums therefore accumulate in TMEM
+// for at most SUB = 8 K-steps (96 adds for S, 32 for P) at a time, alternating between two
+// short buffers, and the epilogue warps fold each finished short buffer into a long TMEM
+// accumulator with round-to-nearest f32 adds while the MMA fills the other.  (A biased P
+// would not move the CG solution, but with a fixed number of CG iterations it moves the
+// iterates, and with them z.)
+// TMEM columns: [0,128) short 0 | [128,256) short 1 | [256,384) long.
 // ------------------------------------------------------------------------------------------
 namespace b_cfg {
 constexpr int BM = 128, BN = 128, BK = 64;
@@ -776,7 +832,7 @@ template <int MODE> struct Cfg {
   static constexpr int NTILE = MODE == 0 ? 4 : 2;   // A_hi A_lo Z_hi Z_lo | A_P Z_hi
   static constexpr int STAGE = NTILE * TILE;
   static constexpr int STAGES = MODE == 0 ? 3 : 6;
-  static constexpr int64_t SUBK = MODE == 0 ? SUB : (int64_t)1 << 40;
+  static constexpr int64_t SUBK = SUB;
   static constexpr int SMEM = STAGES * STAGE + 1024 + 256;
 };
 }  // namespace b_cfg
@@ -793,7 +849,8 @@ __global__ void __launch_bounds__(256, 1)
     k_tc_bsum(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUtensorMap mapA1,
               const __grid_constant__ CUtensorMap mapZ0, const __grid_constant__ CUtensorMap mapZ1,
               float* __restrict__ part, int c, int d, int npairs, int n_mt, int n_nt,
-              int splits, int64_t kb_per_split, int64_t kb_total, int32_t* err) {
+              int splits, int64_t kb_per_split, int64_t kb_total, int32_t* err,
+              const int4* __restrict__ klist, int kbL) {
   using namespace b_cfg;
   using C = Cfg<MODE>;
   constexpr int STAGES = C::STAGES;
@@ -836,8 +893,20 @@ __global__ void __launch_bounds__(256, 1)
     const int rest = u / n_mt;
     nt = rest % n_nt;
     sp = rest / n_nt;
-    kb0 = (int64_t)sp * kb_per_split;
-    kb1 = kb0 + kb_per_split < kb_total ? kb0 + kb_per_split : kb_total;
+    if (klist) {
+      // pooled: the class tile's K list (virtual K-steps 0..L-1) split evenly; a unit past
+      // its end is empty and its partial block is written as zeros
+      const int64_t L = klist[mt].z, per = (L + splits - 1) / splits;
+      kb0 = (int64_t)sp * per;
+      kb1 = kb0 + per < L ? kb0 + per : L;
+      if (kb0 > kb1) kb0 = kb1;
+    } else {
+      kb0 = (int64_t)sp * kb_per_split;
+      kb1 = kb0 + kb_per_split < kb_total ? kb0 + kb_per_split : kb_total;
+    }
+  };
+  auto real_kb = [&](int mt, int64_t v) -> int64_t {
+    return (!klist || v < kbL) ? v : klist[mt].x + (v - kbL);
   };
 
   if (warp == 0 && lane == 0) {
@@ -863,7 +932,8 @@ __global__ void __launch_bounds__(256, 1)
         }
         unsigned char* st = sm + stage * C::STAGE;
         mbar_expect_tx(&ctl->full[stage], C::STAGE);
-        const int ya = (int)(kb * n_mt + mt) * BM, yz = (int)(kb * n_nt + nt) * BN;
+        const int64_t kr = real_kb(mt, kb);
+        const int ya = (int)(kr * n_mt + mt) * BM, yz = (int)(kr * n_nt + nt) * BN;
         tma_load_2d(st, &mapA0, &ctl->full[stage], 0, ya);
         if (MODE == 0) {
           tma_load_2d(st + TILE, &mapA1, &ctl->full[stage], 0, ya);
@@ -952,6 +1022,21 @@ __global__ void __launch_bounds__(256, 1)
       int64_t kb0, kb1;
       unit_range(u, mt, nt, sp, kb0, kb1);
       const int k = mt * BM + q * 32 + lane;
+      if (kb0 >= kb1) {
+        // empty unit (pooled problems): zero partial block
+        if (k < c) {
+          float* out = part + ((int64_t)sp * c + k) * d * d;
+          for (int t = 0; t < BN; ++t) {
+            const int p = nt * BN + t;
+            if (p >= npairs) break;
+            int e, e2;
+            pair_of(p, d, e, e2);
+            out[e * d + e2] = 0.0f;
+            out[e2 * d + e] = 0.0f;
+          }
+        }
+        continue;
+      }
       for (int64_t c0 = kb0; c0 < kb1; c0 += SUBK, ++gsub) {
         const bool first = c0 == kb0, last = c0 + SUBK >= kb1;
         const uint32_t b = gsub & 1, par = (gsub >> 1) & 1;
@@ -1451,16 +1536,17 @@ static int32_t tc_apply_t(firal_problem* P, const float* w, const float* Sblk, c
     FIRAL_CUDA_TRY(cudaMemsetAsync(P->walpha.p, 0, P->walpha.bytes, st));
   if (prow_p > prow)
     FIRAL_CUDA_TRY(cudaMemsetAsync(P->Pb.as<bf16>() + prow * cp, 0, (prow_p - prow) * cp * 2, st));
-  FIRAL_TRY(P->vmean.ensure((size_t)s * P->d * sizeof(float)));
-  FIRAL_TRY(P->qmean.ensure((size_t)s * P->d * sizeof(float)));
+  const int Qe = pool_count(P->pt);
+  FIRAL_TRY(P->vmean.ensure((size_t)s * Qe * P->d * sizeof(float)));
+  FIRAL_TRY(P->qmean.ensure((size_t)s * Qe * P->d * sizeof(float)));
   const int mthreads = (P->d + 31) / 32 * 32;
   {
   ProfScope ps(st, PF_SPLIT);
   count_launch(2);
-  k_class_mean<<<s, 1024, 0, st>>>(V, s, P->c, P->d, P->D, P->vmean.as<float>());
+  k_class_mean<<<s * Qe, 1024, 0, st>>>(V, s, P->c, P->d, P->D, P->vmean.as<float>(), P->pt);
   k_split_probes<NPART><<<dim3((unsigned)(cp + 31) / 32, DP / 32 > 0 ? DP / 32 : 1, s), dim3(32, 8), 0,
                    st>>>(P->Pb.as<bf16>(), V, P->vmean.as<float>(), s, P->c, P->d, DP, cp,
-                           P->D);
+                           P->D, P->pt);
   }
   FIRAL_CUDA_TRY(cudaGetLastError());
   CUtensorMap mH, mP;
@@ -1483,7 +1569,7 @@ static int32_t tc_apply_t(firal_problem* P, const float* w, const float* Sblk, c
   count_launch();
   k_tc_alpha<DP, 0, NPART><<<grid, 256, SMEM, st>>>(mH, mP, mH, P->Xb.as<bf16>(), w, P->walpha.as<bf16>(),
                                              nullptr, P->N, Np, s, cp / BK, n_mt, n_nt, 0, P->d,
-                                             tc_error_word(P));
+                                             tc_error_word(P), P->kr_alpha.as<int2>());
   }
   FIRAL_CUDA_TRY(cudaGetLastError());
   // D-GEMM
@@ -1493,13 +1579,17 @@ static int32_t tc_apply_t(firal_problem* P, const float* w, const float* Sblk, c
     const int n_mt2 = (cp + d_cfg::MT * d_cfg::BM - 1) / (d_cfg::MT * d_cfg::BM);
     const int n_nt2 = (s * DP + d_cfg::BN - 1) / d_cfg::BN;
     const int64_t kb_total = Np / d_cfg::BK;
+    // K-steps a class tile runs over: all points, or (pooled) its longest K list
+    const int64_t kL = P->pt.Q ? P->kr_dterm_Lmax : kb_total;
     const int tiles = n_mt2 * n_nt2;
+    // at least 16 K-steps per split: short units spend their time in the pipeline ramp and
+    // the epilogue, and every split adds one partial block to the combine
     int splits = (int)std::max<int64_t>(1, std::min<int64_t>((4LL * sms + tiles - 1) / tiles,
-                                                            kb_total / 4 > 0 ? kb_total / 4 : 1));
+                                                            kL / 16 > 0 ? kL / 16 : 1));
     // at most D_CHAIN K-steps (4 adds each) per accumulator: the tensor core's f32 accumulation
     // loses about 2^-25 of the running sum per add, so the chain length bounds the bias.  When
     // that raises the split count, round it up to whole waves of units where that costs < 2x.
-    const int64_t need = (kb_total + d_cfg::D_CHAIN - 1) / d_cfg::D_CHAIN;
+    const int64_t need = (kL + d_cfg::D_CHAIN - 1) / d_cfg::D_CHAIN;
     if (need > splits) {
       int64_t g = tiles, r = sms;
       while (r) { const int64_t t = g % r; g = r; r = t; }
@@ -1507,9 +1597,9 @@ static int32_t tc_apply_t(firal_problem* P, const float* w, const float* Sblk, c
       const int64_t up = (need + m - 1) / m * m;
       splits = (int)(up < 2 * need ? up : need);
     }
-    if (forced_splits() > 0) splits = (int)std::min<int64_t>(forced_splits(), kb_total);
-    const int64_t kbps = (kb_total + splits - 1) / splits;
-    splits = (int)((kb_total + kbps - 1) / kbps);
+    if (forced_splits() > 0) splits = (int)std::min<int64_t>(forced_splits(), kL);
+    const int64_t kbps = (kL + splits - 1) / splits;
+    splits = (int)((kL + kbps - 1) / kbps);
     FIRAL_TRY(P->Dpart.ensure((size_t)splits * P->c * sd * sizeof(float)));
     CUtensorMap mHT, mXT, mAT;
     const uint64_t cpb2 = (uint64_t)n_mt2 * d_cfg::MT * d_cfg::BM;
@@ -1526,15 +1616,17 @@ static int32_t tc_apply_t(firal_problem* P, const float* w, const float* Sblk, c
     count_launch();
     k_tc_dterm<DP><<<grid2, 256, d_cfg::Stage<DP>::SMEM, st>>>(mHT, mXT, mAT, P->Dpart.as<float>(), P->N, P->c,
                                              P->d, s, n_mt2, n_nt2, splits, kbps, kb_total,
-                                             sp16, tc_error_word(P));
+                                             sp16, tc_error_word(P), P->kr_dterm.as<int4>(),
+                                             P->kbL);
     }
     FIRAL_CUDA_TRY(cudaGetLastError());
     FIRAL_TRY(combine_f32(P, Sblk, V, splits, s, out, nullptr, P->vmean.as<float>()));
     ProfScope ps(st, PF_COMBINE);
     count_launch(2);
-    k_class_mean<<<s, 1024, 0, st>>>(out, s, P->c, P->d, P->D, P->qmean.as<float>());
+    k_class_mean<<<s * Qe, 1024, 0, st>>>(out, s, P->c, P->d, P->D, P->qmean.as<float>(), P->pt);
     k_project<<<dim3(P->c, (s + 3) / 4), mthreads, 0, st>>>(
-        out, P->qmean.as<float>(), P->vmean.as<float>(), V, lam_null, s, P->c, P->d, P->D, pq);
+        out, P->qmean.as<float>(), P->vmean.as<float>(), V, lam_null, s, P->c, P->d, P->D, pq,
+        P->pt);
     FIRAL_CUDA_TRY(cudaGetLastError());
     return FIRAL_OK;
   }
@@ -1566,13 +1658,14 @@ int32_t tc_syrk_blocks(firal_problem* P, const void* wv, double lamS, void* outS
   const int n_mt = (cp + BM - 1) / BM;
   const int n_nt = (int)(npp / BN);
   const int64_t kb_total = Np / BK;
+  const int64_t kL = P->pt.Q ? P->kr_bsum_Lmax : kb_total;   // longest class-tile K list
   const int tiles = n_mt * n_nt;
   int splits = (int)std::max<int64_t>(1, std::min<int64_t>((4LL * sms + tiles - 1) / tiles,
-                                                          kb_total / 8 > 0 ? kb_total / 8 : 1));
+                                                          kL / 8 > 0 ? kL / 8 : 1));
   // Units of at most UNIT_KB K-steps: the CTAs that share an A or Z tile stream start each
   // unit together, which keeps them within L2 reach of one another (over long units they
   // drift apart and the shared tiles are fetched from DRAM again).  Whole waves of units.
-  const int64_t need = (kb_total + UNIT_KB - 1) / UNIT_KB;
+  const int64_t need = (kL + UNIT_KB - 1) / UNIT_KB;
   if (need > splits) {
     int64_t g = tiles, r = sms;
     while (r) { const int64_t t = g % r; g = r; r = t; }
@@ -1580,9 +1673,9 @@ int32_t tc_syrk_blocks(firal_problem* P, const void* wv, double lamS, void* outS
     const int64_t up = (need + m - 1) / m * m;
     splits = (int)(up < 2 * need ? up : need);
   }
-  if (forced_splits() > 0) splits = (int)std::min<int64_t>(forced_splits(), kb_total);
-  const int64_t kbps = (kb_total + splits - 1) / splits;
-  splits = (int)((kb_total + kbps - 1) / kbps);
+  if (forced_splits() > 0) splits = (int)std::min<int64_t>(forced_splits(), kL);
+  const int64_t kbps = (kL + splits - 1) / splits;
+  splits = (int)((kL + kbps - 1) / kbps);
   const int64_t per = (int64_t)c * d * d;
   FIRAL_TRY(P->syrk_part.ensure((size_t)per * splits * 2 * sizeof(float)));
   float* pS = P->syrk_part.as<float>();
@@ -1612,12 +1705,14 @@ int32_t tc_syrk_blocks(firal_problem* P, const void* wv, double lamS, void* outS
     FIRAL_TRY(make_map(&mZ1, P->Zp.as<bf16>() + npp * Np, zrows, BK, BN, BK, true));
     const int grid = std::min(units, sms);
     k_tc_bsum<0><<<grid, 256, Cfg<0>::SMEM, st>>>(mA0, mA1, mZ0, mZ1, pS, c, d, npairs, n_mt,
-                                                  n_nt, splits, kbps, kb_total, tc_error_word(P));
+                                                  n_nt, splits, kbps, kb_total, tc_error_word(P),
+                                                  P->kr_bsum.as<int4>(), P->kbL);
     FIRAL_CUDA_TRY(cudaGetLastError());
     if (outP) {
       k_tc_bsum<1><<<grid, 256, Cfg<1>::SMEM, st>>>(mA2, mA2, mZ0, mZ0, pP, c, d, npairs, n_mt,
                                                     n_nt, splits, kbps, kb_total,
-                                                    tc_error_word(P));
+                                                    tc_error_word(P), P->kr_bsum.as<int4>(),
+                                                    P->kbL);
       FIRAL_CUDA_TRY(cudaGetLastError());
     }
   }
@@ -1635,15 +1730,16 @@ int32_t tc_syrk_blocks(firal_problem* P, const void* wv, double lamS, void* outS
 // ------------------------------------------------------------------------------------------
 __global__ void k_build_mpairs(bf16* Mt, const float* A, const float* B, const float* meanA,
                                const float* meanB, int s, int c, int d, int64_t D, int cp,
-                               int npairs) {
+                               int npairs, PoolTab pt) {
   extern __shared__ float Msh[];   // d*d
   const int k = blockIdx.x;
+  const int Qe = pool_count(pt), pk = pool_of(pt, k);
   for (int t = threadIdx.x; t < d * d; t += blockDim.x) {
     const int e = t / d, e2 = t - e * d;
     double acc = 0.0;
     for (int j = 0; j < s; ++j) {
-      const float a = A[(int64_t)j * D + (int64_t)k * d + e] - meanA[j * d + e];
-      const float b = B[(int64_t)j * D + (int64_t)k * d + e2] - meanB[j * d + e2];
+      const float a = A[(int64_t)j * D + (int64_t)k * d + e] - meanA[(j * Qe + pk) * d + e];
+      const float b = B[(int64_t)j * D + (int64_t)k * d + e2] - meanB[(j * Qe + pk) * d + e2];
       acc += (double)a * (double)b;
     }
     Msh[t] = (float)acc;
@@ -1689,10 +1785,11 @@ static int32_t tc_quad_t(firal_problem* P, const float* A, const float* B, int s
   FIRAL_CUDA_TRY(cudaMemcpyAsync(AB, A, (size_t)s * D * 4, cudaMemcpyDeviceToDevice, st));
   FIRAL_CUDA_TRY(cudaMemcpyAsync(AB + (size_t)s * D, B, (size_t)s * D * 4,
                                  cudaMemcpyDeviceToDevice, st));
-  FIRAL_TRY(P->vmean.ensure((size_t)2 * s * d * sizeof(float)));
+  const int Qe = pool_count(P->pt);
+  FIRAL_TRY(P->vmean.ensure((size_t)2 * s * Qe * d * sizeof(float)));
   ProfScope ps(st, PF_QUAD);
   count_launch(1);
-  k_class_mean<<<2 * s, 1024, 0, st>>>(AB, 2 * s, c, d, D, P->vmean.as<float>());
+  k_class_mean<<<2 * s * Qe, 1024, 0, st>>>(AB, 2 * s, c, d, D, P->vmean.as<float>(), P->pt);
   // term 1: M~ pairs (hi | lo per 128-pair tile) and the quadratic alpha-GEMM
   const int npairs = d * (d + 1) / 2;
   const int n_nt1 = (npairs + 127) / 128;
@@ -1704,7 +1801,7 @@ static int32_t tc_quad_t(firal_problem* P, const float* A, const float* B, int s
   count_launch(1);
   k_build_mpairs<<<c, 256, (size_t)d * d * sizeof(float), st>>>(
       P->gq_m.as<bf16>(), AB, AB + (size_t)s * D, P->vmean.as<float>(),
-      P->vmean.as<float>() + s * d, s, c, d, D, cp, npairs);
+      P->vmean.as<float>() + (size_t)s * Qe * d, s, c, d, D, cp, npairs, P->pt);
   FIRAL_CUDA_TRY(cudaGetLastError());
   FIRAL_TRY(P->gq_part.ensure((size_t)(n_nt1 + 2 * s) * Np * sizeof(float)));
   float* part1 = P->gq_part.as<float>();
@@ -1728,7 +1825,7 @@ static int32_t tc_quad_t(firal_problem* P, const float* A, const float* B, int s
     count_launch(1);
     k_tc_alpha<DP, 2, 2, 1><<<std::min(n_mt * n_nt1, sms), 256, SMEM_QUAD_H(DP), st>>>(
         mH, mM, mHL, P->Xb.as<bf16>(), nullptr, nullptr, part1, P->N, Np, 0, cp / BK, n_mt,
-        n_nt1, npairs, d, tc_error_word(P));
+        n_nt1, npairs, d, tc_error_word(P), P->kr_alpha.as<int2>());
     FIRAL_CUDA_TRY(cudaGetLastError());
   }
   // term 2: h.a_ij and h.b_ij for the projected [A; B]
@@ -1741,7 +1838,8 @@ static int32_t tc_quad_t(firal_problem* P, const float* A, const float* B, int s
       FIRAL_CUDA_TRY(cudaMemsetAsync(P->Pb.as<bf16>() + prow * cp, 0, (prow_p - prow) * cp * 2, st));
     count_launch(1);
     k_split_probes<2><<<dim3((unsigned)(cp + 31) / 32, DP / 32 > 0 ? DP / 32 : 1, s2), dim3(32, 8), 0,
-                     st>>>(P->Pb.as<bf16>(), AB, P->vmean.as<float>(), s2, c, d, DP, cp, D);
+                     st>>>(P->Pb.as<bf16>(), AB, P->vmean.as<float>(), s2, c, d, DP, cp, D,
+                           P->pt);
     FIRAL_CUDA_TRY(cudaGetLastError());
     CUtensorMap mH, mP, mHL;
     FIRAL_TRY(make_map(&mH, P->Hb.p, Np, cp, BM, BK, true));
@@ -1751,7 +1849,7 @@ static int32_t tc_quad_t(firal_problem* P, const float* A, const float* B, int s
     count_launch(1);
     k_tc_alpha<DP, 1, 2, 1><<<std::min(n_mt * n_nt2, sms), 256, SMEM_H, st>>>(
         mH, mP, mHL, P->Xb.as<bf16>(), nullptr, nullptr, a32, P->N, Np, s2, cp / BK, n_mt,
-        n_nt2, 0, d, tc_error_word(P));
+        n_nt2, 0, d, tc_error_word(P), P->kr_alpha.as<int2>());
     FIRAL_CUDA_TRY(cudaGetLastError());
   }
   count_launch(1);

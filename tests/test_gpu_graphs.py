@@ -45,15 +45,36 @@ def test_graph_replay_equals_eager_steps(api, precision):
     assert torch.equal(z_graph, z)
 
 
-def test_batched_relax_equals_individual_solves(api):
+@pytest.mark.parametrize("precision", ["fp32", "mixed", "mixed_fast"])
+def test_batched_relax_equals_individual_solves(api, precision):
+    """firal_batched_relax over pools of different n, d, c and budget against one firal_relax
+    per pool (same seed, so the same probes).  FP32 runs every pool as its own problem and
+    must match bit for bit.  The mixed precisions stack the pools into pooled problems (one
+    per padded feature width) whose tiles sum in other orders, and a reordered f32 sum can
+    flip a later bf16 rounding.  On these small pools (n <= 6000, 4 MD iterations of 5 CG
+    steps) the mixed solve itself sits 5e-4..4e-3 from the FP32 one and the pooled and single
+    solves differ by the same rounding noise; the pooled solve must be as accurate as the
+    single one."""
     shapes = batched_problems(6, seed=0)
     probs = [make_problem(min(sh["n"], 6000), sh["d"], sh["c"], seed=i, x_dtype="bf16",
                           h_dtype="float32") for i, sh in enumerate(shapes)]
     dicts = [prob_dict(p, float(sh["b"])) for p, sh in zip(probs, shapes)]
     H = api.Handle()
-    zs = api.batched_relax(dicts, s=8, T=4, fixed_iters=5, seed=2, precision="mixed", handle=H)
+    zs = api.batched_relax(dicts, s=8, T=4, fixed_iters=5, seed=2, precision=precision, handle=H)
     for dct, z in zip(dicts, zs):
-        z1, _ = api.relax(dct["X"], dct["h"], dct["Xo"], dct["ho"], dct["lam"], dct["budget"],
-                          s=8, T=4, fixed_iters=5, seed=2, precision="mixed", handle=H)
-        assert torch.equal(z, z1)
+        def single(prec):
+            return api.relax(dct["X"], dct["h"], dct["Xo"], dct["ho"], dct["lam"], dct["budget"],
+                             s=8, T=4, fixed_iters=5, seed=2, precision=prec, handle=H)[0]
+        z1 = single(precision)
+        if precision == "fp32":
+            assert torch.equal(z, z1)
+        else:
+            z32 = single("fp32").double()
+            e_pooled = float((z.double() - z32).norm() / z32.norm())
+            e_single = float((z1.double() - z32).norm() / z32.norm())
+            e_ps = float((z.double() - z1.double()).norm() / z1.double().norm())
+            print(f"{precision} pool n={dct['X'].shape[0]} d={dct['X'].shape[1]} "
+                  f"c={dct['h'].shape[1]}: vs FP32 pooled {e_pooled:.2e} single {e_single:.2e}; "
+                  f"pooled vs single {e_ps:.2e}")
+            assert e_pooled < 1.25 * e_single + 1e-5
         assert abs(z.double().sum().item() - dct["budget"]) < 1e-3 * dct["budget"]
