@@ -261,6 +261,19 @@ def round_measure(args, H):
         t2 = time.perf_counter()
         per = ((t2 - t1) - (t1 - t0)) / (max(1 + nsel, nover) - 1)
         sels[prec] = sel[:nover].cpu().tolist()
+        if prec != "fp32" and not args.no_variants:
+            # choosing eta (Section 5): Round per eta on the same z, keep the best-conditioned
+            eta0 = 8.0 * (p.d * p.c) ** 0.5
+            etas = [0.25 * eta0, eta0, 4.0 * eta0]
+            bs = 10
+            torch.cuda.synchronize()
+            ts = time.perf_counter()
+            _, crit, best = prob.round_sweep(zr, bs, etas)
+            torch.cuda.synchronize()
+            out["eta_sweep"] = {"etas": etas, "budget": bs, "criteria_min_lambda_min": crit,
+                                "best": best, "seconds": time.perf_counter() - ts,
+                                "note": "one Round per eta (set-up included), criterion "
+                                        "min_k lambda_min of the selected points' Hessian blocks"}
         out["fp32" if prec == "fp32" else "mixed"] = {
             "precision": prec, "value": 1.0 / per, "ms_per_selection": 1000.0 * per,
             "selections": max(1 + nsel, nover), "setup_ms": 1000.0 * (t1 - t0)}

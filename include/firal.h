@@ -242,6 +242,17 @@ int32_t firal_round_problem(firal_problem* problem, const void* z_relaxed, int32
                             const firal_round_opts* opts, int32_t* selected_out,
                             firal_round_stats* stats);
 
+/* Choosing eta for Round (Section 5 of the paper): Algorithm 3 is run once per eta_e,
+ * e < n_eta, from the same z_relaxed, and eta_e is scored by
+ *   criterion_e = min_k lambda_min(H_k),  H_k = sum_{i selected} h_ik (1 - h_ik) x_i x_i^T
+ * (the block-diagonal Hessian sum of the b selected points).  selected_out (device,
+ * n_eta * budget int32, row e = the picks for eta_e), criteria (host, n_eta doubles) and
+ * *best (host: the index maximising the criterion, first on ties) are written.
+ * 1 <= n_eta <= 64; every eta_e must be > 0; opts->eta is ignored.  Errors as firal_round. */
+int32_t firal_round_sweep(firal_problem* problem, const void* z_relaxed, int32_t budget,
+                          const double* etas, int32_t n_eta, const firal_round_opts* opts,
+                          int32_t* selected_out, double* criteria, int32_t* best);
+
 /* ---------------------------------------------------------------- building blocks */
 
 /* Rademacher probe block of MD iteration t (Algorithm 2 line 4): V_out (device, s*dt of

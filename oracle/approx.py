@@ -380,3 +380,27 @@ def round_select(prob, z_diamond, b, eta=None, exclude_selected=True, numerator=
     if record:
         return chosen, dict(nu=nus, gap=gaps, H=H, Sig=Sig, scores=scores)
     return chosen
+
+
+# ----------------------------------------------------------------------------------------
+# Choosing eta (Section 5): Round for several eta, keep the one whose selected set has the
+# best-conditioned Fisher blocks
+# ----------------------------------------------------------------------------------------
+
+def selected_min_eig(prob, selected):
+    """``min_k lambda_min(H_k)`` with ``H = sum_{i in selected} H_i`` in its block-diagonal
+    form, ``H_k = sum_i h_ik (1 - h_ik) x_i x_i^T`` (the Hessian sum of the selected points;
+    the labelled set is not part of it)."""
+    X, h = _as64(prob.X), _as64(prob.h)
+    sel = np.asarray(selected, dtype=np.int64)
+    blocks = block_diag(X[sel], h[sel], np.ones(sel.size))
+    return float(min(np.linalg.eigvalsh(B)[0] for B in blocks))
+
+
+def eta_sweep(prob, z_diamond, b, etas):
+    """Run Round (Algorithm 3) once per eta and pick the eta maximising
+    ``min_k lambda_min(H_k)`` of its selection (first on ties).  Returns
+    ``(best_index, criteria, selections)``."""
+    sels = [round_select(prob, z_diamond, b, eta=e) for e in etas]
+    crit = [selected_min_eig(prob, s) for s in sels]
+    return int(np.argmax(crit)), crit, sels

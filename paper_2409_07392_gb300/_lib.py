@@ -81,6 +81,9 @@ SIGNATURES = [
                               POINTER(FiralRoundStats)]),
     ("firal_round_problem", c_int32, [c_void_p, c_void_p, c_int32, POINTER(FiralRoundOpts),
                                       c_void_p, POINTER(FiralRoundStats)]),
+    ("firal_round_sweep", c_int32, [c_void_p, c_void_p, c_int32, POINTER(c_double), c_int32,
+                                    POINTER(FiralRoundOpts), c_void_p, POINTER(c_double),
+                                    POINTER(c_int32)]),
     ("firal_probes", c_int32, [c_void_p, c_uint64, c_int32, c_int32, c_void_p]),
     ("firal_hessian_apply", c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_int32, c_void_p]),
     ("firal_precond_blocks", c_int32, [c_void_p, c_void_p, c_void_p]),

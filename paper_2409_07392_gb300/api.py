@@ -237,6 +237,21 @@ class Problem:
                                                _ptr(sel), ctypes.byref(st)))
         return sel, dict(nu_last=st.nu_last, score_last=st.score_last)
 
+    def round_sweep(self, z, budget, etas, exclude_selected=True):
+        """Round once per eta (Section 5's choice of eta); returns (selections (n_eta x b),
+        criteria min_k lambda_min(H_k) per eta, index of the best eta)."""
+        z = self._vec(z)
+        ne = len(etas)
+        sel = torch.empty((ne, budget), dtype=torch.int32, device=self.device)
+        e_arr = (ctypes.c_double * ne)(*[float(e) for e in etas])
+        crit = (ctypes.c_double * ne)()
+        best = ctypes.c_int32()
+        o = L.FiralRoundOpts(0.0, 1 if exclude_selected else 0, PRECISIONS[self.precision])
+        self._chk(self.lib.firal_round_sweep(self._p, _ptr(z), budget, e_arr, ne,
+                                             ctypes.byref(o), _ptr(sel), crit,
+                                             ctypes.byref(best)))
+        return sel, list(crit), best.value
+
 
 def _to_device(t, device, dtype=None, non_blocking=True):
     if t is None:

@@ -885,6 +885,61 @@ int32_t batched_pooled(firal_handle* H, int32_t nq, const firal_pool* pools,
   return rc;
 }
 
+// min_k lambda_min of the block-diagonal Hessian sum of the selected points (eta criterion)
+int32_t selected_min_eig(firal_problem* P, const int32_t* sel, int32_t b, double* out) {
+  cudaStream_t st = P->H->stream;
+  const int c = P->c, d = P->d;
+  const size_t blk = (size_t)c * d * d;
+  DBuf Hs, Lid, eig;
+  auto rel = [&]() {
+    Hs.release();
+    Lid.release();
+    eig.release();
+  };
+  int32_t rc = FIRAL_OK;
+  if ((rc = Hs.ensure(blk * 8)) != FIRAL_OK || (rc = Lid.ensure(blk * 8)) != FIRAL_OK ||
+      (rc = eig.ensure((size_t)c * d * 8)) != FIRAL_OK) {
+    rel();
+    return rc;
+  }
+  if (rc == FIRAL_OK) rc = selected_weights(P, sel, b, st);
+  // FP64/FP32 SIMT block sums (not the bf16 tensor-core ones: the smallest eigenvalue of a
+  // sum of b rank-one terms needs the full precision)
+  if (rc == FIRAL_OK) rc = syrk_blocks(P, P->zsave.p, 0.0, nullptr, 0.0, Hs.as<double>());
+  if (rc == FIRAL_OK) rc = identity_blocks(Lid.as<double>(), c, d, st);
+  if (rc == FIRAL_OK) rc = tilde_eigvals(Lid.as<double>(), Hs.as<double>(), c, d, eig.as<double>(), st);
+  if (rc == FIRAL_OK) {
+    std::vector<double> h((size_t)c * d);
+    cudaError_t e = cudaMemcpyAsync(h.data(), eig.p, h.size() * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = fail(FIRAL_ERR_CUDA, cudaGetErrorString(e));
+    else *out = *std::min_element(h.begin(), h.end());
+  }
+  rel();
+  return rc;
+}
+
+int32_t round_sweep_impl(firal_problem* P, const void* zr, int32_t b, const double* etas,
+                         int32_t neta, const firal_round_opts* o, int32_t* sel, double* crit,
+                         int32_t* best) {
+  if (!P || !zr || !sel || !etas || !crit || !best)
+    return fail(FIRAL_ERR_ARG, "problem, z, etas, selected_out, criteria and best must be non-null");
+  if (neta < 1 || neta > 64) return fail(FIRAL_ERR_ARG, "n_eta must be in [1, 64]");
+  for (int e = 0; e < neta; ++e)
+    if (!(etas[e] > 0)) return fail(FIRAL_ERR_ARG, "every eta must be > 0");
+  firal_round_opts oe = o ? *o : firal_round_opts{0.0, 1, P->prec};
+  for (int e = 0; e < neta; ++e) {
+    oe.eta = etas[e];
+    FIRAL_TRY(round_impl(P, zr, b, &oe, sel + (size_t)e * b, nullptr));
+    FIRAL_TRY(selected_min_eig(P, sel + (size_t)e * b, b, &crit[e]));
+  }
+  int bi = 0;
+  for (int e = 1; e < neta; ++e)
+    if (crit[e] > crit[bi]) bi = e;
+  *best = bi;
+  return read_flags(P->H);
+}
+
 }  // namespace
 
 // =========================================================================================
@@ -1116,6 +1171,12 @@ int32_t firal_batched_relax(firal_handle* H, int32_t nproblems, const firal_pool
 int32_t firal_round_problem(firal_problem* P, const void* zr, int32_t b,
                             const firal_round_opts* o, int32_t* sel, firal_round_stats* stats) {
   return record(P ? P->H : nullptr, round_impl(P, zr, b, o, sel, stats));
+}
+
+int32_t firal_round_sweep(firal_problem* P, const void* zr, int32_t b, const double* etas,
+                          int32_t neta, const firal_round_opts* o, int32_t* sel, double* crit,
+                          int32_t* best) {
+  return record(P ? P->H : nullptr, round_sweep_impl(P, zr, b, etas, neta, o, sel, crit, best));
 }
 
 int32_t firal_round(firal_handle* H, const firal_pool* pool, const firal_hess0* h0,

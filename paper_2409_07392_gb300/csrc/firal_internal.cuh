@@ -178,6 +178,8 @@ int32_t fill_weights(bool dbl, void* w, int64_t m, double lab_val, const void* z
 int32_t probes(bool dbl, void* V, uint64_t seed, int64_t t, int s, int64_t D, cudaStream_t st,
                const int64_t* t_dev = nullptr, const PoolTab* pt = nullptr, int d = 0);
 int32_t md_step_pooled(firal_problem* P, void* z, const void* g, double beta0, cudaStream_t st);
+int32_t selected_weights(firal_problem* P, const int32_t* sel, int32_t b, cudaStream_t st);
+int32_t identity_blocks(double* L, int c, int d, cudaStream_t st);
 int32_t tick(int64_t* t_dev, cudaStream_t st);
 int32_t set_step(int64_t* t_dev, int64_t v, cudaStream_t st);
 int32_t syrk_blocks(firal_problem* P, const void* w, double lamS, void* outS, double lamP,

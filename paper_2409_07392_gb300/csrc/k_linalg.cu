@@ -259,6 +259,22 @@ int32_t tilde_eigvals(const double* L, const double* H, int c, int d, double* ei
   return FIRAL_OK;
 }
 
+__global__ void k_identity_blocks(double* L, int64_t total, int d) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i % ((int64_t)d * d);
+    L[i] = (r / d == r % d) ? 1.0 : 0.0;
+  }
+}
+
+int32_t identity_blocks(double* L, int c, int d, cudaStream_t st) {
+  const int64_t total = (int64_t)c * d * d;
+  count_launch();
+  k_identity_blocks<<<(unsigned)std::min<int64_t>((total + 255) / 256, 4096), 256, 0, st>>>(L, total, d);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  return FIRAL_OK;
+}
+
 // ------------------------------------------------------------------------------------------
 // nu of eq. 10: sum_j (nu + scale*lam_j)^{-2} = 1, one block
 // ------------------------------------------------------------------------------------------

@@ -1156,6 +1156,25 @@ int32_t md_step_pooled(firal_problem* P, void* z, const void* g, double beta0, c
   return FIRAL_OK;
 }
 
+template <class T>
+__global__ void k_selected_weights(T* w, int64_t N, int64_t m, const int32_t* sel, int32_t b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x)
+    w[i] = T(0);
+  __syncthreads();
+  if (blockIdx.x == 0)
+    for (int t = threadIdx.x; t < b; t += blockDim.x) w[m + sel[t]] = T(1);
+}
+
+int32_t selected_weights(firal_problem* P, const int32_t* sel, int32_t b, cudaStream_t st) {
+  count_launch();
+  // one block: the zeroing must finish before the ones are written
+  if (P->dbl) k_selected_weights<double><<<1, 1024, 0, st>>>(P->zsave.as<double>(), P->N, P->m, sel, b);
+  else k_selected_weights<float><<<1, 1024, 0, st>>>(P->zsave.as<float>(), P->N, P->m, sel, b);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  return FIRAL_OK;
+}
+
 int32_t md_step_simt(bool dbl, void* z, const void* g, int64_t n, double budget, double beta0,
                      double* red, cudaStream_t st) {
   ProfScope ps(st, PF_MD);

@@ -294,3 +294,32 @@ def test_edge_cases(api, handle):
                     1e-3, precision="fp32")
     with pytest.raises(Exception):
         prob.round(dev(np.array([1.0])), 2)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_round_eta_sweep_vs_oracle(api, handle, precision):
+    """Choosing eta (Section 5): Round per eta and the criterion min_k lambda_min(H_k) of the
+    selected points' block-diagonal Hessian sum, against the oracle.  Picks agree while the
+    oracle's gaps are clear; criteria agree to rounding; the chosen eta agrees."""
+    p = make_problem(1500, 8, 4, seed=14, x_dtype="bf16" if precision == "mixed" else "float64",
+                     h_dtype="float32" if precision == "mixed" else "float64")
+    prob = make(api, handle, p, precision)
+    b, etas = 8, [2.0, 12.0, 60.0]
+    z = np.random.default_rng(3).gamma(2.0, 1.0, p.n)
+    z *= b / z.sum()
+    best_ref, crit_ref, sels_ref = approx.eta_sweep(p, z, b, etas)
+    vdt = torch.float64 if precision == "fp64" else torch.float32
+    sel, crit, best = prob.round_sweep(torch.from_numpy(z).to(vdt).cuda(), b, etas)
+    sel = sel.cpu().numpy()
+    for e in range(len(etas)):
+        if list(sel[e]) == list(sels_ref[e]):
+            # an eigenvalue moves by at most the perturbation's norm (Weyl): the tolerance
+            # scales with the blocks (FP32 block sums in the mixed precision), not with the
+            # possibly tiny smallest eigenvalue
+            tol = 1e-9 if precision == "fp64" else 1e-5
+            assert abs(crit[e] - crit_ref[e]) <= tol * max(crit_ref)
+    print(f"{precision} eta sweep: criteria {np.round(crit, 6).tolist()} "
+          f"(oracle {np.round(crit_ref, 6).tolist()}), best {best} (oracle {best_ref}), "
+          f"selections equal {[list(sel[e]) == list(sels_ref[e]) for e in range(len(etas))]}")
+    assert all(list(sel[e]) == list(sels_ref[e]) for e in range(len(etas)))
+    assert best == best_ref

@@ -167,3 +167,25 @@ def test_round_vs_brute_force_tiny():
     sel = approx.round_select(p, z, b)
     ratio = exact.subset_objective(p, sel) / fstar
     assert 1.0 - 1e-12 <= ratio < 2.0
+
+
+def test_selected_min_eig_matches_dense_hessian_sum():
+    """The eta-sweep criterion equals the smallest eigenvalue over the diagonal d x d blocks of
+    the dense sum of the selected points' Hessians (eq. 2, Kronecker form)."""
+    p = make_problem(40, 4, 3, seed=2, x_dtype="float64", h_dtype="float64")
+    sel = [3, 17, 25, 31, 8]
+    Hs = exact.hessian_sum(p.X[sel], p.h[sel], np.ones(len(sel)))
+    ref = min(np.linalg.eigvalsh(approx.block_of(Hs, k, p.d))[0] for k in range(p.c))
+    assert abs(approx.selected_min_eig(p, sel) - ref) < 1e-12 * max(1.0, abs(ref))
+
+
+def test_eta_sweep_picks_the_best_conditioned_selection():
+    p = make_problem(300, 3, 3, seed=4, x_dtype="float64", h_dtype="float64")
+    z = np.full(p.n, 6.0 / p.n)
+    etas = [0.5, 4.0, 30.0]
+    best, crit, sels = approx.eta_sweep(p, z, 6, etas)
+    assert len(crit) == 3 and all(len(s) == 6 for s in sels)
+    assert crit[best] == max(crit)
+    for e, s, cr in zip(etas, sels, crit):
+        assert s == approx.round_select(p, z, 6, eta=e)
+        assert abs(cr - approx.selected_min_eig(p, s)) == 0.0
