@@ -296,11 +296,14 @@ def round_measure(args, H):
 
 
 def cg_variants(prob, s, b, n):
-    """MD iterations/s at m = 50 CG iterations per solve (the paper's timing setting) and in
-    tolerance mode (cg_tol = 0.1, the paper's default), with the iterations reached."""
+    """MD iterations/s at m = 50 CG iterations per solve (the paper's timing setting), in
+    tolerance mode (cg_tol = 0.1, the paper's default) and at cg_tol = 1e-3 with independent
+    and with block PCG, each with the iterations reached."""
     import torch
     out = {}
-    for label, kw in (("cg_iters_50", dict(fixed_iters=50)), ("cg_tol_0.1", dict(tol=0.1))):
+    for label, kw in (("cg_iters_50", dict(fixed_iters=50)), ("cg_tol_0.1", dict(tol=0.1)),
+                      ("cg_tol_1e-3", dict(tol=1e-3)),
+                      ("cg_tol_1e-3_block", dict(tol=1e-3, block_cg=True))):
         z = torch.full((n,), b / n, dtype=prob.vdt, device="cuda")
         o = prob.relax_opts(s=s, T=3, seed=1, **kw)
         prob.relax_step(o, 0, b, z, stats=False)

@@ -99,6 +99,11 @@ typedef struct {
   double tol;           /* default 0.1 (Section 5 of the paper)  */
   int32_t maxit;        /* default 100                           */
   int32_t fixed_iters;  /* 0 = tolerance mode                    */
+  int32_t block;        /* 0 (default): s independent PCG recurrences sharing each matvec;   */
+                        /* 1: block PCG (O'Leary 1980), s x s step matrices in FP64 (s <= 32, */
+                        /*    not for pooled problems); the solve stops when every column     */
+                        /*    meets the tolerance, or early if the s x s system loses rank    */
+  int32_t reserved;     /* 0                                                                  */
 } firal_cg_opts;
 
 /* Relax controls.  Defaults: s = 10, T = 20, beta0 = 1, seed = 1, cg = {0.1, 100, 0}. */

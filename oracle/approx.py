@@ -181,6 +181,42 @@ def pcg(apply_A, B, apply_M, tol=0.1, maxit=100, fixed_iters=None):
     return Xs, iters, relres
 
 
+def block_pcg(apply_A, B, apply_M, tol=0.1, maxit=100, fixed_iters=None):
+    """Block preconditioned CG (O'Leary, 1980) on all s columns of B at once (x0 = 0).
+
+    One Krylov space serves the whole block; the step "scalars" are s x s matrices:
+        gamma = Z^T R,  alpha = (P^T A P)^{-1} gamma,  X += P alpha,  R -= (A P) alpha,
+        Z = M^{-1} R,  beta = gamma_old^{-1} gamma_new,  P = Z + P beta.
+    The block stops when every column meets ``||r_j|| <= tol ||b_j||`` (or after
+    ``fixed_iters`` iterations).  With s = 1 this is ``pcg``.  Returns
+    ``(X, iterations, relres)``.
+    """
+    B = _as64(B)
+    Xs = np.zeros_like(B)
+    R = B.copy()
+    bn = np.linalg.norm(B, axis=0)
+    Z = apply_M(R)
+    P = Z.copy()
+    gam = Z.T @ R
+    nsteps = fixed_iters if fixed_iters is not None else maxit
+    it = 0
+    for _ in range(nsteps):
+        if fixed_iters is None and np.all(np.linalg.norm(R, axis=0) <= tol * bn):
+            break
+        Q = apply_A(P)
+        alpha = np.linalg.solve(P.T @ Q, gam)
+        Xs += P @ alpha
+        R -= Q @ alpha
+        Z = apply_M(R)
+        gam_new = Z.T @ R
+        beta = np.linalg.solve(gam, gam_new)
+        P = Z + P @ beta
+        gam = gam_new
+        it += 1
+    relres = np.linalg.norm(B - apply_A(Xs), axis=0) / np.where(bn > 0, bn, 1.0)
+    return Xs, it, relres
+
+
 # ----------------------------------------------------------------------------------------
 # Hutchinson estimates (eq. 11) and the objective
 # ----------------------------------------------------------------------------------------

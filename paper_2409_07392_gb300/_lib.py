@@ -27,7 +27,8 @@ class FiralHess0(ctypes.Structure):
 
 
 class FiralCGOpts(ctypes.Structure):
-    _fields_ = [("tol", c_double), ("maxit", c_int32), ("fixed_iters", c_int32)]
+    _fields_ = [("tol", c_double), ("maxit", c_int32), ("fixed_iters", c_int32),
+                ("block", c_int32), ("reserved", c_int32)]
 
 
 class FiralRelaxOpts(ctypes.Structure):

@@ -104,8 +104,8 @@ def _hess0(Xo, ho, lam):
                         Xo.shape[0], lam)
 
 
-def _cg(tol=0.1, maxit=100, fixed_iters=0):
-    return L.FiralCGOpts(tol, maxit, fixed_iters)
+def _cg(tol=0.1, maxit=100, fixed_iters=0, block=False):
+    return L.FiralCGOpts(tol, maxit, fixed_iters, 1 if block else 0, 0)
 
 
 class Problem:
@@ -170,13 +170,13 @@ class Problem:
         self._chk(self.lib.firal_precond_blocks(self._p, _ptr(zz), _ptr(out)))
         return out
 
-    def pcg(self, z, B, tol=0.1, maxit=100, fixed_iters=0, check=True):
+    def pcg(self, z, B, tol=0.1, maxit=100, fixed_iters=0, check=True, block=False):
         z, B = self._vec(z), self._vec(B)
         s = B.shape[0]
         X = torch.empty_like(B)
         iters = (ctypes.c_int32 * s)()
         relres = (ctypes.c_double * s)()
-        cg = _cg(tol, maxit, fixed_iters)
+        cg = _cg(tol, maxit, fixed_iters, block)
         code = self.lib.firal_pcg(self._p, _ptr(z), _ptr(B), s, ctypes.byref(cg), _ptr(X), iters,
                                   relres)
         if check or code not in (0, -4):
@@ -196,8 +196,8 @@ class Problem:
         return z
 
     def relax_opts(self, s=10, T=20, tol=0.1, maxit=100, fixed_iters=0, beta0=1.0, seed=1,
-                   estimator=0, md_tol=0.0):
-        return L.FiralRelaxOpts(s, T, _cg(tol, maxit, fixed_iters), beta0, seed,
+                   estimator=0, md_tol=0.0, block_cg=False):
+        return L.FiralRelaxOpts(s, T, _cg(tol, maxit, fixed_iters, block_cg), beta0, seed,
                                 PRECISIONS[self.precision], estimator, md_tol)
 
     def relax_step(self, opts, t, budget, z, stats=True):

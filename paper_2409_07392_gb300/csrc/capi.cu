@@ -219,6 +219,8 @@ int32_t ensure_cg(firal_problem* P, int s) {
   FIRAL_TRY(P->cgcols.ensure((size_t)s * pool_count(P->pt) * sizeof(CGCol)));
   FIRAL_TRY(P->cgpart1.ensure((size_t)s * P->c * sizeof(double)));
   FIRAL_TRY(P->cgpart2.ensure((size_t)s * P->c * sizeof(double)));
+  // block PCG: c * s * s partials, six s x s matrices, flag
+  FIRAL_TRY(P->bcg.ensure(((size_t)P->c * s * s + 6 * (size_t)s * s + 1) * sizeof(double)));
   return FIRAL_OK;
 }
 
@@ -228,9 +230,95 @@ struct CGResult {
   bool converged = true;
 };
 
+// Block PCG (O'Leary 1980) on Sigma_z: one Krylov space for all s columns, s x s step
+// matrices in FP64 (oracle: approx.block_pcg).  Fixed-iteration mode reads nothing back.
+int32_t block_pcg_run(firal_problem* P, const void* B, int s, const firal_cg_opts& cg,
+                      void* X_out, bool want_result, CGResult* res,
+                      std::vector<CGCol>* cols_out) {
+  if (s > 32) return fail(FIRAL_ERR_UNSUPPORTED, "block CG supports s <= 32");
+  if (P->pt.Q) return fail(FIRAL_ERR_UNSUPPORTED, "block CG is not available on pooled problems");
+  cudaStream_t st = P->H->stream;
+  FIRAL_TRY(ensure_cg(P, s));
+  const int fixed = cg.fixed_iters > 0 ? 1 : 0;
+  const int iters = fixed ? cg.fixed_iters : (cg.maxit > 0 ? cg.maxit : 100);
+  const size_t vb = (size_t)s * P->D * vsize(P);
+  const size_t ss = (size_t)s * s;
+  double* part = P->bcg.as<double>();
+  double* gam = part + (size_t)P->c * ss;
+  double* gnew = gam + ss;
+  double* pq = gnew + ss;
+  double* alpha = pq + ss;
+  double* beta = alpha + ss;
+  double* rr = beta + ss;
+  int* flag = reinterpret_cast<int*>(rr + ss);
+  FIRAL_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), st));
+  FIRAL_CUDA_TRY(cudaMemsetAsync(P->cgX.p, 0, vb, st));
+  FIRAL_CUDA_TRY(cudaMemcpyAsync(P->cgR.p, B, vb, cudaMemcpyDeviceToDevice, st));
+  FIRAL_TRY(precond_apply(P, P->cgR.p, s, P->cgZ.p));
+  FIRAL_CUDA_TRY(cudaMemcpyAsync(P->cgP.p, P->cgZ.p, vb, cudaMemcpyDeviceToDevice, st));
+  FIRAL_TRY(block_gram(P, P->cgZ.p, P->cgR.p, s, part, gam));
+  std::vector<double> bn2(s, 0.0), rn2(s, 0.0), hmat(ss);
+  auto diag_rr = [&](std::vector<double>& out) -> int32_t {
+    FIRAL_TRY(block_gram(P, P->cgR.p, P->cgR.p, s, part, rr));
+    FIRAL_CUDA_TRY(cudaMemcpyAsync(hmat.data(), rr, ss * sizeof(double), cudaMemcpyDeviceToHost, st));
+    FIRAL_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int j = 0; j < s; ++j) out[j] = hmat[(size_t)j * s + j];
+    return FIRAL_OK;
+  };
+  if (!fixed || want_result) FIRAL_TRY(diag_rr(bn2));
+  int it = 0;
+  for (; it < iters; ++it) {
+    if (!fixed) {
+      FIRAL_TRY(diag_rr(rn2));
+      int hflag = 0;
+      FIRAL_CUDA_TRY(cudaMemcpy(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost));
+      bool done = hflag != 0;
+      if (!done) {
+        done = true;
+        for (int j = 0; j < s; ++j) done &= rn2[j] <= cg.tol * cg.tol * bn2[j];
+      }
+      if (done) break;
+    }
+    FIRAL_TRY(apply(P, P->w_sig.p, P->S_sig.p, P->cgP.p, s, P->cgQ.p, nullptr));
+    FIRAL_TRY(block_gram(P, P->cgP.p, P->cgQ.p, s, part, pq));
+    FIRAL_TRY(small_spd_solve(pq, gam, s, alpha, flag, st));            // alpha = (P^T A P)^-1 gamma
+    FIRAL_TRY(block_axpy(P, P->cgX.p, P->cgX.p, P->cgP.p, alpha, 1.0, s));   // X += P alpha
+    FIRAL_TRY(block_axpy(P, P->cgR.p, P->cgR.p, P->cgQ.p, alpha, -1.0, s));  // R -= Q alpha
+    FIRAL_TRY(precond_apply(P, P->cgR.p, s, P->cgZ.p));                 // Z = M^-1 R
+    FIRAL_TRY(block_gram(P, P->cgZ.p, P->cgR.p, s, part, gnew));        // gamma_new = Z^T R
+    FIRAL_TRY(small_spd_solve(gam, gnew, s, beta, flag, st));           // beta = gamma^-1 gamma_new
+    FIRAL_TRY(block_axpy(P, P->cgP.p, P->cgZ.p, P->cgP.p, beta, 1.0, s));    // P = Z + P beta
+    std::swap(gam, gnew);
+  }
+  FIRAL_CUDA_TRY(cudaMemcpyAsync(X_out, P->cgX.p, vb, cudaMemcpyDeviceToDevice, st));
+  if (want_result || !fixed) {
+    FIRAL_TRY(diag_rr(rn2));
+    std::vector<CGCol> cols(s);
+    if (res) {
+      res->max_iters = it;
+      res->max_relres = 0.0;
+      res->converged = true;
+    }
+    for (int j = 0; j < s; ++j) {
+      const double rel = bn2[j] > 0 ? std::sqrt(rn2[j] / bn2[j]) : 0.0;
+      cols[j].iters = it;
+      cols[j].relres = rel;
+      cols[j].bnorm2 = bn2[j];
+      cols[j].active = 0;
+      if (res) {
+        res->max_relres = std::max(res->max_relres, rel);
+        if (!fixed && rel > cg.tol && bn2[j] > 0) res->converged = false;
+      }
+    }
+    if (cols_out) *cols_out = cols;
+  }
+  return FIRAL_OK;
+}
+
 // PCG on Sigma_z (w_sig, S_sig, Minv already set up).  X_out may alias nothing of the CG state.
 int32_t pcg_run(firal_problem* P, const void* B, int s, const firal_cg_opts& cg, void* X_out,
                 bool want_result, CGResult* res, std::vector<CGCol>* cols_out) {
+  if (cg.block) return block_pcg_run(P, B, s, cg, X_out, want_result, res, cols_out);
   cudaStream_t st = P->H->stream;
   FIRAL_TRY(ensure_cg(P, s));
   const int fixed = cg.fixed_iters > 0 ? 1 : 0;
@@ -598,6 +686,8 @@ firal_relax_opts default_relax_opts() {
   o.cg.tol = 0.1;
   o.cg.maxit = 100;
   o.cg.fixed_iters = 0;
+  o.cg.block = 0;
+  o.cg.reserved = 0;
   o.beta0 = 1.0;
   o.seed = 1;
   o.precision = FIRAL_FP32;

@@ -151,6 +151,7 @@ struct firal_problem {
   firal::DBuf walpha, Dpart, syrk_part;
   // PCG
   firal::DBuf cgX, cgR, cgP, cgQ, cgZ, cgcols, cgpart1, cgpart2;
+  firal::DBuf bcg;               // block PCG: class partials, s x s matrices, breakdown flag
   // Relax iteration buffers
   firal::DBuf V, U, W, HU, g, red, zsave;
 
@@ -180,6 +181,13 @@ int32_t probes(bool dbl, void* V, uint64_t seed, int64_t t, int s, int64_t D, cu
 int32_t md_step_pooled(firal_problem* P, void* z, const void* g, double beta0, cudaStream_t st);
 int32_t selected_weights(firal_problem* P, const int32_t* sel, int32_t b, cudaStream_t st);
 int32_t identity_blocks(double* L, int c, int d, cudaStream_t st);
+int32_t block_gram(firal_problem* P, const void* A, const void* B, int s, double* part,
+                   double* G);
+int32_t small_spd_solve(const double* A, const double* Y, int s, double* X, int* flag,
+                        cudaStream_t st);
+int32_t block_axpy(firal_problem* P, void* Y, const void* Z, const void* Pm, const double* M,
+                   double sign, int s);
+int32_t precond_apply(firal_problem* P, const void* R, int s, void* Z);
 int32_t tick(int64_t* t_dev, cudaStream_t st);
 int32_t set_step(int64_t* t_dev, int64_t v, cudaStream_t st);
 int32_t syrk_blocks(firal_problem* P, const void* w, double lamS, void* outS, double lamP,

@@ -1156,6 +1156,183 @@ int32_t md_step_pooled(firal_problem* P, void* z, const void* g, double beta0, c
   return FIRAL_OK;
 }
 
+// ------------------------------------------------------------------------------------------
+// Block PCG (O'Leary 1980): s x s Gram matrices, small FP64 solves and block updates.
+// Vector blocks are probe-major: column j of a block is V[j * D .. j * D + D).
+// ------------------------------------------------------------------------------------------
+// part[k][a][b] = sum over class block k of A_a . B_b (a, b < s); one block per class
+template <class T>
+__global__ void k_gram_part(const T* __restrict__ A, const T* __restrict__ B, int s, int64_t D,
+                            int d, double* part) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* As = (T*)smem_raw;            // s x d
+  T* Bs = As + (size_t)s * d;      // s x d
+  const int k = blockIdx.x;
+  for (int i = threadIdx.x; i < s * d; i += blockDim.x) {
+    const int a = i / d, e = i - a * d;
+    As[i] = A[(int64_t)a * D + (int64_t)k * d + e];
+    Bs[i] = B[(int64_t)a * D + (int64_t)k * d + e];
+  }
+  __syncthreads();
+  for (int ab = threadIdx.x; ab < s * s; ab += blockDim.x) {
+    const int a = ab / s, b = ab - a * s;
+    double acc = 0.0;
+    for (int e = 0; e < d; ++e) acc += (double)As[a * d + e] * (double)Bs[b * d + e];
+    part[((int64_t)k * s + a) * s + b] = acc;
+  }
+}
+
+// G[a][b] = sum_k part[k][a][b] in a fixed order
+__global__ void k_gram_sum(const double* part, int c, int s, double* G) {
+  for (int ab = threadIdx.x; ab < s * s; ab += blockDim.x) {
+    double acc = 0.0;
+    for (int k = 0; k < c; ++k) acc += part[(int64_t)k * s * s + ab];
+    G[ab] = acc;
+  }
+}
+
+// X = A^{-1} Y for s x s SPD A (Cholesky, FP64), one thread; flag = 1 when A is not SPD
+__global__ void k_small_spd_solve(const double* A, const double* Y, int s, double* X, int* flag) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (*flag) {   // an earlier step lost rank: the block iterate stays where it is
+    for (int q = 0; q < s * s; ++q) X[q] = 0.0;
+    return;
+  }
+  double L[32 * 32];
+  for (int i = 0; i < s; ++i)
+    for (int j = 0; j <= i; ++j) {
+      double v = 0.5 * (A[i * s + j] + A[j * s + i]);
+      for (int k = 0; k < j; ++k) v -= L[i * s + k] * L[j * s + k];
+      if (i == j) {
+        if (!(v > 0.0)) {
+          *flag = 1;
+          for (int q = 0; q < s * s; ++q) X[q] = 0.0;
+          return;
+        }
+        L[i * s + i] = sqrt(v);
+      } else {
+        L[i * s + j] = v / L[j * s + j];
+      }
+    }
+  for (int col = 0; col < s; ++col) {
+    double y[32];
+    for (int i = 0; i < s; ++i) {
+      double v = Y[i * s + col];
+      for (int k = 0; k < i; ++k) v -= L[i * s + k] * y[k];
+      y[i] = v / L[i * s + i];
+    }
+    for (int i = s - 1; i >= 0; --i) {
+      double v = y[i];
+      for (int k = i + 1; k < s; ++k) v -= L[k * s + i] * X[k * s + col];
+      X[i * s + col] = v / L[i * s + i];
+    }
+  }
+}
+
+// Y[j] = Z[j] + sign * sum_l P[l] M[l][j] for every column j (Y may alias Z or P: each
+// thread reads all s entries of its element before writing)
+template <class T>
+__global__ void k_block_axpy(T* Y, const T* Z, const T* P, const double* M, double sign, int s,
+                             int64_t D) {
+  __shared__ double Ms[32 * 32];
+  for (int i = threadIdx.x; i < s * s; i += blockDim.x) Ms[i] = M[i];
+  __syncthreads();
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < D;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    double p[32], z[32];
+    for (int l = 0; l < s; ++l) {
+      p[l] = (double)P[(int64_t)l * D + q];
+      z[l] = (double)Z[(int64_t)l * D + q];
+    }
+    for (int j = 0; j < s; ++j) {
+      double acc = 0.0;
+      for (int l = 0; l < s; ++l) acc += p[l] * Ms[l * s + j];
+      Y[(int64_t)j * D + q] = (T)(z[j] + sign * acc);
+    }
+  }
+}
+
+// Z[j][k] = Minv_k R[j][k] (block-Jacobi preconditioner), block = class k x 4 probes
+template <class T>
+__global__ void k_precond_apply(const T* __restrict__ Minv, const T* R, int d, int s, int64_t D,
+                                T* Z) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Ms = (T*)smem_raw;
+  T* rs = Ms + (size_t)d * d;
+  const int k = blockIdx.x;
+  const int dpad = (d + 31) & ~31;
+  const int jj = threadIdx.x / dpad, e = threadIdx.x - jj * dpad;
+  const int j = blockIdx.y * 4 + jj;
+  for (int i = threadIdx.x; i < d * d; i += blockDim.x) Ms[i] = Minv[(int64_t)k * d * d + i];
+  if (j < s && e < d) rs[jj * d + e] = R[(int64_t)j * D + (int64_t)k * d + e];
+  __syncthreads();
+  if (j < s && e < d) {
+    T z = T(0);
+    for (int f = 0; f < d; ++f) z = fma(Ms[f * d + e], rs[jj * d + f], z);
+    Z[(int64_t)j * D + (int64_t)k * d + e] = z;
+  }
+}
+
+int32_t block_gram(firal_problem* P, const void* A, const void* B, int s, double* part,
+                   double* G) {
+  cudaStream_t st = P->H->stream;
+  const int d = P->d, c = P->c;
+  const size_t smem = (size_t)2 * s * d * (P->dbl ? 8 : 4);
+  if (P->dbl) FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_gram_part<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  else FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_gram_part<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  ProfScope ps(st, PF_CG);
+  count_launch(2);
+  if (P->dbl) k_gram_part<double><<<c, 256, smem, st>>>((const double*)A, (const double*)B, s, P->D, d, part);
+  else k_gram_part<float><<<c, 256, smem, st>>>((const float*)A, (const float*)B, s, P->D, d, part);
+  k_gram_sum<<<1, 1024, 0, st>>>(part, c, s, G);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  return FIRAL_OK;
+}
+
+int32_t small_spd_solve(const double* A, const double* Y, int s, double* X, int* flag,
+                        cudaStream_t st) {
+  count_launch();
+  k_small_spd_solve<<<1, 32, 0, st>>>(A, Y, s, X, flag);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  return FIRAL_OK;
+}
+
+int32_t block_axpy(firal_problem* P, void* Y, const void* Z, const void* Pm, const double* M,
+                   double sign, int s) {
+  cudaStream_t st = P->H->stream;
+  const int g = grid_for(P->D, 256, 4096);
+  ProfScope ps(st, PF_CG);
+  count_launch();
+  if (P->dbl)
+    k_block_axpy<double><<<g, 256, 0, st>>>((double*)Y, (const double*)Z, (const double*)Pm, M, sign, s, P->D);
+  else
+    k_block_axpy<float><<<g, 256, 0, st>>>((float*)Y, (const float*)Z, (const float*)Pm, M, sign, s, P->D);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  return FIRAL_OK;
+}
+
+int32_t precond_apply(firal_problem* P, const void* R, int s, void* Z) {
+  cudaStream_t st = P->H->stream;
+  const int d = P->d, c = P->c;
+  const int threads = ((d + 31) / 32) * 32 * 4;
+  const size_t smem = ((size_t)d * d + 4 * (size_t)d) * (P->dbl ? 8 : 4);
+  ProfScope ps(st, PF_CG);
+  count_launch();
+  if (P->dbl) {
+    FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_precond_apply<double>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    k_precond_apply<double><<<dim3(c, (s + 3) / 4), threads, smem, st>>>(
+        P->Minv.as<double>(), (const double*)R, d, s, P->D, (double*)Z);
+  } else {
+    FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_precond_apply<float>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    k_precond_apply<float><<<dim3(c, (s + 3) / 4), threads, smem, st>>>(
+        P->Minv.as<float>(), (const float*)R, d, s, P->D, (float*)Z);
+  }
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  return FIRAL_OK;
+}
+
 template <class T>
 __global__ void k_selected_weights(T* w, int64_t N, int64_t m, const int32_t* sel, int32_t b) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;

@@ -323,3 +323,46 @@ def test_round_eta_sweep_vs_oracle(api, handle, precision):
           f"selections equal {[list(sel[e]) == list(sels_ref[e]) for e in range(len(etas))]}")
     assert all(list(sel[e]) == list(sels_ref[e]) for e in range(len(etas)))
     assert best == best_ref
+
+
+def test_block_pcg_fixed_iterations_match_oracle_fp64(api, handle):
+    """Block PCG (O'Leary) through firal_pcg: the FP64 iterate after k steps equals the
+    oracle's block_pcg iterate (same s x s recurrences).  k stays below d~/s, where the block
+    Krylov space is exhausted and the s x s systems become singular (the GPU then freezes
+    the iterate; there is no unique iterate to compare)."""
+    p = make_problem(600, 10, 6, seed=5, x_dtype="float64", h_dtype="float64")
+    prob = make(api, handle, p, "fp64")
+    z = np.linspace(0.2, 1.0, p.n)
+    ops = approx.Operators(p)
+    chol = approx.block_cholesky(ops.precond_blocks(z))
+    B = rademacher(9, 1, 6, 60)
+    for k in (1, 4, 7):
+        ref, _, _ = approx.block_pcg(lambda P: ops.sigma_apply(z, P), B,
+                                     lambda R: approx.block_solve(chol, R), fixed_iters=k)
+        X, iters, _ = prob.pcg(dev(z), dev(B.T), fixed_iters=k, block=True)
+        assert relerr(X.cpu().numpy().T, ref) < 1e-10, k
+        assert iters == [k] * 6
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_block_pcg_converges_in_fewer_iterations(api, handle, precision):
+    """Block PCG to a tight tolerance reaches the direct solution and needs no more iterations
+    than the slowest of the s independent PCG recurrences (one shared Krylov space)."""
+    p = make_problem(3000, 16, 10, seed=8, x_dtype="bf16" if precision == "mixed" else "float64",
+                     h_dtype="float32" if precision == "mixed" else "float64")
+    prob = make(api, handle, p, precision)
+    z = np.full(p.n, 8.0 / p.n)
+    ops = approx.Operators(p)
+    B = rademacher(4, 0, 8, p.d * p.c)
+    ref = np.linalg.solve(ops.sigma_dense(z), B)
+    vdt = torch.float64 if precision == "fp64" else torch.float32
+    zt, Bt = torch.from_numpy(z).to(vdt).cuda(), torch.from_numpy(B.T.copy()).to(vdt).cuda()
+    tol = 1e-10 if precision == "fp64" else 1e-5
+    Xb, itb, _ = prob.pcg(zt, Bt, tol=tol, maxit=500, block=True, check=False)
+    Xc, itc, _ = prob.pcg(zt, Bt, tol=tol, maxit=500, check=False)
+    eb = relerr(Xb.cpu().numpy().T, ref)
+    ec = relerr(Xc.cpu().numpy().T, ref)
+    print(f"{precision} block PCG: {itb[0]} iterations (independent: max {max(itc)}), "
+          f"error {eb:.2e} (independent {ec:.2e})")
+    assert eb < (1e-8 if precision == "fp64" else 2e-3)
+    assert itb[0] <= max(itc)

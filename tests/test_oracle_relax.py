@@ -192,3 +192,31 @@ def test_relax_decreases_objective():
     z0 = np.full(p.n, 8.0 / p.n)
     z, _ = exact.relax(p, 8, 15, beta0=0.5)
     assert exact.objective(p, z) < exact.objective(p, z0)
+
+
+def _spd_system(n, s, cond, seed):
+    rng = np.random.default_rng(seed)
+    Qm, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    A = (Qm * np.geomspace(1.0, cond, n)) @ Qm.T
+    Md = np.diag(A).copy()
+    return A, (lambda V: A @ V), (lambda V: V / Md[:, None]), rng.standard_normal((n, s))
+
+
+def test_block_pcg_with_one_column_is_pcg():
+    """O'Leary's block CG with s = 1 reduces to preconditioned CG, iterate for iterate."""
+    A, app, prec, B = _spd_system(60, 1, 1e3, 1)
+    for k in (1, 3, 7):
+        Xb, _, _ = approx.block_pcg(app, B, prec, fixed_iters=k)
+        Xc, _, _ = approx.pcg(app, B, prec, fixed_iters=k)
+        np.testing.assert_allclose(Xb, Xc, rtol=1e-11, atol=1e-13)
+
+
+def test_block_pcg_reaches_the_direct_solution_in_fewer_iterations():
+    """Block CG converges to A^{-1} B, and its shared Krylov space needs no more iterations
+    than the slowest independent column (here strictly fewer)."""
+    A, app, prec, B = _spd_system(120, 8, 1e5, 2)
+    Xb, itb, rb = approx.block_pcg(app, B, prec, tol=1e-10, maxit=500)
+    Xc, itc, _ = approx.pcg(app, B, prec, tol=1e-10, maxit=500)
+    np.testing.assert_allclose(Xb, np.linalg.solve(A, B), rtol=1e-7, atol=1e-9)
+    assert rb.max() < 1e-9
+    assert itb < int(np.max(itc))
