@@ -71,6 +71,24 @@ static int32_t make_map(CUtensorMap* m, const void* base, uint64_t rows, uint64_
   return FIRAL_OK;
 }
 
+// 2-D f32 tensor map with 128-byte swizzle: box = box_rows x 32 columns (128 B rows).
+// cols * 4 must be a multiple of 16.
+static int32_t make_map_f32(CUtensorMap* m, const void* base, uint64_t rows, uint64_t cols,
+                            uint32_t box_rows) {
+  FIRAL_TRY(get_encoder());
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {cols * sizeof(float)};
+  cuuint32_t box[2] = {32, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    return fail(FIRAL_ERR_CUDA, "cuTensorMapEncodeTiled (f32) failed (" + std::to_string((int)r) + ")");
+  return FIRAL_OK;
+}
+
 static int32_t* tc_error_word(firal_problem* P) { return &P->H->flags.as<DevFlags>()->pad[0]; }
 
 // ------------------------------------------------------------------------------------------
@@ -239,10 +257,22 @@ constexpr int SMEM_QUAD(int dp) { return SMEM + dp * BM * 2; }
 constexpr int STAGES_H = 3;
 constexpr int SMEM_H = STAGES_H * (2 * A_BYTES + B_BYTES) + 1024 + 256;
 constexpr int SMEM_QUAD_H(int dp) { return SMEM_H + dp * BM * 2; }
+// feature-contracted quadratic forms: 2 stages of x | coefficients hi | lo (128 rows each),
+// then 2 buffers of the f32 h tile (128 points x 64 classes, two 128-byte-swizzled boxes)
+constexpr int C3_BYTES = 128 * BK * 2;
+constexpr int H3_BYTES = 128 * 64 * 4;
+// MODE 3: the x tile of a point tile stays resident (double buffer of dp/64 K-blocks) and the
+// ring stages hold only the coefficient tiles (hi + lo, 32 KB): 4 stages at dp = 64, 3 at 128
+constexpr int NST3(int dp) { return dp <= 64 ? 4 : 3; }
+constexpr int XB3(int dp) { return (dp / 64) * A_BYTES; }
+constexpr int SMEM3(int dp) {
+  return NST3(dp) * 2 * C3_BYTES + 2 * XB3(dp) + 2 * H3_BYTES + 1024 + 256;
+}
 }  // namespace alpha_cfg
 
 struct TcCtl {   // < 256 bytes
-  uint64_t full[4], empty[4], yfull[4], tfull[2], tempty[2], drain, pempty;
+  uint64_t full[4], empty[4], yfull[4], tfull[2], tempty[2], drain, pempty, hfull[2], hempty[2],
+      xfull[2], xempty[2];
   uint32_t tmem_base;
   int abort_w;
 };
@@ -262,20 +292,27 @@ __global__ void __launch_bounds__(256, 1)
                const __grid_constant__ CUtensorMap mapHL, const bf16* __restrict__ Xb,
                const float* __restrict__ w, bf16* __restrict__ aT, float* __restrict__ out32,
                int64_t N, int64_t Np, int s, int kblocks, int n_mt, int n_nt, int npairs, int d,
-               int32_t* err, const int2* __restrict__ krange) {
+               int32_t* err, const int2* __restrict__ krange,
+               const float* __restrict__ hrow = nullptr, int c = 0, int64_t m = 0,
+               float gscale = 0.0f) {
   using namespace alpha_cfg;
-  constexpr int NST = HLO ? STAGES_H : STAGES;
-  constexpr int SB = STAGE_BYTES + (HLO ? A_BYTES : 0);
+  // MODE 3 stages hold the x tile and two 128-row coefficient tiles (hi and lo), followed by
+  // a double buffer of f32 h tiles
+  constexpr int NST = MODE == 3 ? NST3(DP) : HLO ? STAGES_H : STAGES;
+  constexpr int SB = MODE == 3 ? 2 * C3_BYTES : STAGE_BYTES + (HLO ? A_BYTES : 0);
   constexpr int OFF_B = (HLO ? 2 : 1) * A_BYTES;
+  constexpr int HBUF = NST * SB;                        // MODE 3 h buffers
+  constexpr int XBUF = HBUF + (MODE == 3 ? 2 * H3_BYTES : 0);   // MODE 3 resident x tiles
+  constexpr int CTL_OFF = XBUF + (MODE == 3 ? 2 * XB3(DP) : 0);
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  TcCtl* ctl = (TcCtl*)(sm + NST * SB);
+  TcCtl* ctl = (TcCtl*)(sm + CTL_OFF);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int PPN = BN / (NPART * DP);   // probes per N tile
   static_assert(MODE != 2 || NPART == 2, "the quadratic mode reads hi and lo halves");
   static_assert(!HLO || (MODE != 0 && NPART == 2), "h_lo is used by the gradient modes");
   // MODE 2: the thread's x row, transposed (column = thread) so reads are conflict-free
-  bf16* xsT = (bf16*)(sm + NST * SB + 256);   // after the control block
+  bf16* xsT = (bf16*)(sm + CTL_OFF + 256);   // after the control block
   if (threadIdx.x == 0) {
     for (int i = 0; i < NST; ++i) {
       mbar_init(&ctl->full[i], 1);
@@ -284,6 +321,10 @@ __global__ void __launch_bounds__(256, 1)
     for (int i = 0; i < 2; ++i) {
       mbar_init(&ctl->tfull[i], 1);
       mbar_init(&ctl->tempty[i], 4);
+      mbar_init(&ctl->hfull[i], 1);
+      mbar_init(&ctl->hempty[i], 4);
+      mbar_init(&ctl->xfull[i], 1);
+      mbar_init(&ctl->xempty[i], 1);
     }
     mbar_init(&ctl->drain, 1);
     ctl->abort_w = 0;
@@ -299,18 +340,58 @@ __global__ void __launch_bounds__(256, 1)
   const uint32_t tmem = ctl->tmem_base;
   volatile int* abort_w = &ctl->abort_w;
   const int ntiles = n_mt * n_nt;
+  // tile sequence of this CTA: MODE 3 takes every N tile of one point tile in a row (its
+  // epilogue accumulates a row over all of them); the other modes stride over all tiles
+  auto tile_at = [&](int it, int& mt, int& nt) -> bool {
+    if (MODE == 3) {
+      mt = blockIdx.x + (it / n_nt) * gridDim.x;
+      nt = it % n_nt;
+      return mt < n_mt;
+    }
+    const int tile = blockIdx.x + it * gridDim.x;
+    mt = tile / n_nt;
+    nt = tile % n_nt;
+    return tile < ntiles;
+  };
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer
     tma_prefetch(&mapH);
     tma_prefetch(&mapP);
-    if (HLO) tma_prefetch(&mapHL);
+    if (HLO || MODE == 3) tma_prefetch(&mapHL);
     int stage = 0;
     uint32_t phase = 0;
-    for (int tile = blockIdx.x; tile < ntiles && !*abort_w; tile += gridDim.x) {
-      const int mt = tile / n_nt, nt = tile % n_nt;
+    int xcount = 0;   // MODE 3: point tiles whose x rows were loaded
+    int mt, nt;
+    for (int it = 0; tile_at(it, mt, nt) && !*abort_w; ++it) {
       // pooled problems: only the class blocks of the pools in this point tile are non-zero
       const int kb_lo = krange ? krange[mt].x : 0, kb_hi = krange ? krange[mt].y : kblocks;
+      if (MODE == 3 && nt == 0) {
+        // the point tile's x rows, resident for all its N tiles
+        const int xb = xcount & 1;
+        if (!mbar_wait(&ctl->xempty[xb], ((xcount >> 1) & 1) ^ 1, abort_w)) {
+          raise_abort(ctl, err, 6);
+          break;
+        }
+        unsigned char* xbuf = sm + XBUF + xb * XB3(DP);
+        mbar_expect_tx(&ctl->xfull[xb], XB3(DP));
+        for (int kb = 0; kb < kblocks; ++kb)
+          tma_load_2d(xbuf + kb * A_BYTES, &mapH, &ctl->xfull[xb], kb * BK, mt * BM);
+        ++xcount;
+      }
+      if (MODE == 3) {
+        // the f32 h tile of (point tile, 64-class chunk) for the epilogue
+        const int hb = it & 1;
+        if (!mbar_wait(&ctl->hempty[hb], ((it >> 1) & 1) ^ 1, abort_w)) {
+          raise_abort(ctl, err, 5);
+          break;
+        }
+        const int kc = nt % (n_nt / s);
+        unsigned char* hbuf = sm + HBUF + hb * H3_BYTES;
+        mbar_expect_tx(&ctl->hfull[hb], H3_BYTES);
+        tma_load_2d(hbuf, &mapHL, &ctl->hfull[hb], kc * 64, mt * BM);
+        tma_load_2d(hbuf + H3_BYTES / 2, &mapHL, &ctl->hfull[hb], kc * 64 + 32, mt * BM);
+      }
       for (int kb = kb_lo; kb < kb_hi; ++kb) {
         if (!mbar_wait(&ctl->empty[stage], phase ^ 1, abort_w)) {
           raise_abort(ctl, err, 1);
@@ -318,9 +399,14 @@ __global__ void __launch_bounds__(256, 1)
         }
         unsigned char* st = sm + stage * SB;
         mbar_expect_tx(&ctl->full[stage], SB);
-        tma_load_2d(st, &mapH, &ctl->full[stage], kb * BK, mt * BM);
-        if (HLO) tma_load_2d(st + A_BYTES, &mapHL, &ctl->full[stage], kb * BK, mt * BM);
-        tma_load_2d(st + OFF_B, &mapP, &ctl->full[stage], kb * BK, nt * BN);
+        if (MODE == 3) {
+          tma_load_2d(st, &mapP, &ctl->full[stage], kb * BK, (2 * nt) * 128);
+          tma_load_2d(st + C3_BYTES, &mapP, &ctl->full[stage], kb * BK, (2 * nt + 1) * 128);
+        } else {
+          tma_load_2d(st, &mapH, &ctl->full[stage], kb * BK, mt * BM);
+          if (HLO) tma_load_2d(st + A_BYTES, &mapHL, &ctl->full[stage], kb * BK, mt * BM);
+          tma_load_2d(st + OFF_B, &mapP, &ctl->full[stage], kb * BK, nt * BN);
+        }
         if (++stage == NST) {
           stage = 0;
           phase ^= 1;
@@ -337,12 +423,21 @@ __global__ void __launch_bounds__(256, 1)
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
-    constexpr uint32_t idesc = idesc_bf16_f32(BM, BN);
+    constexpr uint32_t idesc = idesc_bf16_f32(BM, MODE == 3 ? 128 : BN);
     int stage = 0;
     uint32_t phase = 0;
     int acc = 0;
     uint32_t acc_phase = 0;
-    for (int tile = blockIdx.x; tile < ntiles && !*abort_w; tile += gridDim.x) {
+    int mt, nt;
+    int xcount = 0;
+    for (int it = 0; tile_at(it, mt, nt) && !*abort_w; ++it) {
+      if (MODE == 3 && nt == 0) {
+        if (!mbar_wait(&ctl->xfull[xcount & 1], (xcount >> 1) & 1, abort_w)) {
+          raise_abort(ctl, err, 7);
+          break;
+        }
+        ++xcount;
+      }
       if (!mbar_wait(&ctl->tempty[acc], acc_phase ^ 1, abort_w)) {
         raise_abort(ctl, err, 2);
         break;
@@ -350,7 +445,6 @@ __global__ void __launch_bounds__(256, 1)
       tc_fence_after();
       const uint32_t d = tmem + acc * BN;
       bool ok = true;
-      const int mt = tile / n_nt;
       const int kb_lo = krange ? krange[mt].x : 0, kb_hi = krange ? krange[mt].y : kblocks;
       for (int kb = kb_lo; kb < kb_hi; ++kb) {
         if (!mbar_wait(&ctl->full[stage], phase, abort_w)) {
@@ -359,12 +453,16 @@ __global__ void __launch_bounds__(256, 1)
           break;
         }
         tc_fence_after();
-        const uint32_t a0 = smem_u32(sm + stage * SB);
-        const uint32_t b0 = a0 + OFF_B;
+        const uint32_t a0 = MODE == 3
+                                ? smem_u32(sm + XBUF + ((xcount - 1) & 1) * XB3(DP) + kb * A_BYTES)
+                                : smem_u32(sm + stage * SB);
+        const uint32_t b0 = MODE == 3 ? smem_u32(sm + stage * SB) : a0 + OFF_B;
 #pragma unroll
         for (int k = 0; k < BK / 16; ++k) {
           umma_bf16(d, sdesc_sw128(a0 + k * 32), sdesc_sw128(b0 + k * 32), idesc,
                     (kb != kb_lo || k != 0) ? 1u : 0u);
+          if (MODE == 3)   // x (A_lo; B_lo) into the same columns: a and b to ~2^-16
+            umma_bf16(d, sdesc_sw128(a0 + k * 32), sdesc_sw128(b0 + C3_BYTES + k * 32), idesc, 1u);
           if (HLO) {
             const uint64_t al = sdesc_sw128(a0 + A_BYTES + k * 32);
             if (MODE == 2) {
@@ -387,6 +485,8 @@ __global__ void __launch_bounds__(256, 1)
       }
       if (!ok) break;
       umma_commit(&ctl->tfull[acc]);
+      // MODE 3: the resident x tile is free once the point tile's last MMAs complete
+      if (MODE == 3 && nt == n_nt - 1) umma_commit(&ctl->xempty[(xcount - 1) & 1]);
       acc ^= 1;
       if (acc == 0) acc_phase ^= 1;
     }
@@ -398,9 +498,72 @@ __global__ void __launch_bounds__(256, 1)
     const int q = warp & 3;
     int acc = 0;
     uint32_t acc_phase = 0;
-    for (int tile = blockIdx.x; tile < ntiles && !*abort_w; tile += gridDim.x) {
-      const int mt = tile / n_nt, nt = tile % n_nt;
+    // MODE 3 running sums of the thread's row: over the classes of the current probe
+    // (sum h a b, sum h a, sum h b) and over the probes (q)
+    float sab = 0.0f, sa = 0.0f, sb = 0.0f, qacc = 0.0f;
+    const int nkc = MODE == 3 ? n_nt / s : 1;
+    int mt, nt;
+    for (int it = 0; tile_at(it, mt, nt) && !*abort_w; ++it) {
       const int64_t row = (int64_t)mt * BM + q * 32 + lane;
+      if (MODE == 3) {
+        // per-point quadratic forms (eq. 11) from a = x.A_j[:,k], b = x.B_j[:,k] (K = d), the
+        // hi and lo coefficient products summed in TMEM; 64 classes per tile, columns
+        // [a (64) | b (64)]; term 1 = sum_k h a b, term 2 = (sum_k h a)(sum_k h b) with the
+        // exact f32 h, staged by TMA in 128-byte-swizzled boxes of 32 classes
+        const int kc = nt % nkc;
+        const int hb = it & 1;
+        if (!mbar_wait(&ctl->hfull[hb], (it >> 1) & 1, abort_w) ||
+            !mbar_wait(&ctl->tfull[acc], acc_phase, abort_w)) {
+          raise_abort(ctl, err, 4);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + acc * BN;
+        const unsigned char* hbuf = sm + HBUF + hb * H3_BYTES;
+        const int r = q * 32 + lane;
+#pragma unroll 1
+        for (int box = 0; box < 2; ++box) {
+          uint32_t ra[32], rb[32];
+          tmem_ld32_async(tb + box * 32, ra);
+          tmem_ld32_async(tb + 64 + box * 32, rb);
+          float hv[32];
+          const unsigned char* hrow_s = hbuf + box * (H3_BYTES / 2) + r * 128;
+#pragma unroll
+          for (int ch = 0; ch < 8; ++ch) {
+            const float4 h4 = *reinterpret_cast<const float4*>(hrow_s + ((ch ^ (r & 7)) << 4));
+            hv[4 * ch] = h4.x;
+            hv[4 * ch + 1] = h4.y;
+            hv[4 * ch + 2] = h4.z;
+            hv[4 * ch + 3] = h4.w;
+          }
+          tmem_wait_ld();
+#pragma unroll
+          for (int t = 0; t < 32; ++t) {
+            const float h = hv[t], av = __uint_as_float(ra[t]), bv = __uint_as_float(rb[t]);
+            const float ha = h * av;
+            sab = fmaf(ha, bv, sab);
+            sa += ha;
+            sb = fmaf(h, bv, sb);
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&ctl->tempty[acc]);
+          mbar_arrive(&ctl->hempty[hb]);
+        }
+        acc ^= 1;
+        if (acc == 0) acc_phase ^= 1;
+        if (kc == nkc - 1) {
+          qacc += sab - sa * sb;
+          sab = sa = sb = 0.0f;
+        }
+        if (nt == n_nt - 1) {
+          if (row >= m && row < N) out32[row - m] = -gscale * qacc;
+          qacc = 0.0f;
+        }
+        continue;
+      }
       // the thread's x row (packed bf16 pairs) and weight, fetched before the accumulator
       // wait so the global-load latency overlaps the tile's MMAs; reused by every probe/part
       uint32_t xp[DP / 2];
@@ -958,7 +1121,7 @@ __global__ void __launch_bounds__(256, 1)
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
-    constexpr uint32_t idesc = idesc_bf16_f32(BM, BN);
+    constexpr uint32_t idesc = idesc_bf16_f32(BM, MODE == 3 ? 128 : BN);
     int stage = 0;
     uint32_t phase = 0;
     uint32_t gsub = 0;   // accumulations issued by this CTA (short buffer = gsub & 1)
@@ -1728,6 +1891,29 @@ int32_t tc_syrk_blocks(firal_problem* P, const void* wv, double lamS, void* outS
 // term1 = rowdot(x (x) x, H . M~) with the symmetric part of M_k (alpha-GEMM, MODE 2);
 // term2 from the alpha-GEMM on [A; B] with f32 output (MODE 1).
 // ------------------------------------------------------------------------------------------
+// Coefficient rows of the feature-contracted quadratic forms: row ((j nkc + kc) 2 + hl) 128 + r
+// holds, over the features e < dp, the class-mean-projected A_j (r < 64, class 64 kc + r) or
+// B_j (r >= 64, class 64 kc + r - 64), as bf16 hi (hl = 0) or lo (hl = 1); zero for classes
+// >= c or e >= d.  means: [A; B] class means, (2 s) x pools x d.
+__global__ void k_build_coef(bf16* Cf, const float* A, const float* B, const float* mean, int s,
+                             int c, int d, int dp, int64_t D, int nkc, PoolTab pt) {
+  const int rb = blockIdx.x;                 // ((j nkc + kc) 2 + hl)
+  const int hl = rb & 1, kc = (rb >> 1) % nkc, j = (rb >> 1) / nkc;
+  const int Qe = pool_count(pt);
+  for (int idx = threadIdx.x; idx < 128 * dp; idx += blockDim.x) {
+    const int r = idx / dp, e = idx - r * dp;
+    const bool isb = r >= 64;
+    const int k = kc * 64 + (isb ? r - 64 : r);
+    const float* src = isb ? B : A;
+    const int jm = isb ? s + j : j;
+    float v = 0.0f;
+    if (k < c && e < d)
+      v = src[(int64_t)j * D + (int64_t)k * d + e] - mean[(jm * Qe + pool_of(pt, k)) * d + e];
+    const bf16 hi = __float2bfloat16_rn(v);
+    Cf[((int64_t)rb * 128 + r) * dp + e] = hl ? __float2bfloat16_rn(v - __bfloat162float(hi)) : hi;
+  }
+}
+
 __global__ void k_build_mpairs(bf16* Mt, const float* A, const float* B, const float* meanA,
                                const float* meanB, int s, int c, int d, int64_t D, int cp,
                                int npairs, PoolTab pt) {
@@ -1790,6 +1976,37 @@ static int32_t tc_quad_t(firal_problem* P, const float* A, const float* B, int s
   ProfScope ps(st, PF_QUAD);
   count_launch(1);
   k_class_mean<<<2 * s * Qe, 1024, 0, st>>>(AB, 2 * s, c, d, D, P->vmean.as<float>(), P->pt);
+  if (DP >= 64 && !P->pt.Q && (c % 4) == 0) {
+    // a_ijk = x_i.A_j[:,k], b_ijk = x_i.B_j[:,k] on tensor cores (K = features, x exact in
+    // bf16, A and B as hi + lo); the epilogue forms sum_k h a b - (sum_k h a)(sum_k h b)
+    // with the exact f32 h row and accumulates over the probes (MODE 3)
+    const int nkc = cp / 64;
+    const int64_t crow = (int64_t)s * nkc * 2 * 128;
+    FIRAL_TRY(P->gq_m.ensure((size_t)crow * DP * 2));
+    count_launch(2);
+    k_build_coef<<<(unsigned)(s * nkc * 2), 256, 0, st>>>(P->gq_m.as<bf16>(), AB, AB + (size_t)s * D,
+                                                         P->vmean.as<float>(), s, c, d, DP, D,
+                                                         nkc, P->pt);
+    FIRAL_CUDA_TRY(cudaGetLastError());
+    static bool attr3[4] = {false, false, false, false};
+    const int a3 = DP == 64 ? 2 : 3;
+    if (!attr3[a3]) {
+      FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tc_alpha<DP, 3, 2, 0>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          SMEM3(DP)));
+      attr3[a3] = true;
+    }
+    CUtensorMap mX, mC, mHf;
+    FIRAL_TRY(make_map(&mX, P->Xb.p, Np, DP, BM, BK, true));
+    FIRAL_TRY(make_map(&mC, P->gq_m.p, crow, DP, 128, BK, true));
+    FIRAL_TRY(make_map_f32(&mHf, P->Ha.p, P->N, c, BM));
+    const int n_mt = (int)(Np / BM), n_nt = s * nkc;
+    k_tc_alpha<DP, 3, 2, 0><<<std::min(n_mt, sms), 256, SMEM3(DP), st>>>(
+        mX, mC, mHf, P->Xb.as<bf16>(), nullptr, nullptr, g, P->N, Np, s, DP / BK, n_mt, n_nt, 0,
+        d, tc_error_word(P), nullptr, P->Ha.as<float>(), c, P->m, (float)(scale / s));
+    FIRAL_CUDA_TRY(cudaGetLastError());
+    return FIRAL_OK;
+  }
   // term 1: M~ pairs (hi | lo per 128-pair tile) and the quadratic alpha-GEMM
   const int npairs = d * (d + 1) / 2;
   const int n_nt1 = (npairs + 127) / 128;
