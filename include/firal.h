@@ -341,6 +341,46 @@ int32_t firal_block_eigvals(firal_handle* handle, int32_t c, int32_t d, const do
  * mu (device doubles); nu_out: host double (synchronises). */
 int32_t firal_nu_bisect(firal_handle* handle, const double* mu, int64_t count, double* nu_out);
 
+/* ---------------------------------------------------------------- Exact-FIRAL (Algorithm 1) */
+
+/* Exact-FIRAL on dense d~ x d~ matrices (d~ = d c <= 16384), for pools small enough to form
+ * Sigma_z.  Runs on a prepared, non-pooled problem in its vec type (FIRAL_FP64: double, every
+ * other precision: float; the tile factorisations, the Round's c x c systems and all scalar
+ * reductions use double).  Device workspace: up to 12 d~ x d~ matrices of the vec type,
+ * allocated on first use and kept with the problem.  Errors: FIRAL_ERR_UNSUPPORTED for pooled
+ * problems or d~ > 16384, FIRAL_ERR_NOT_SPD when Sigma_z (or a Round matrix) has no Cholesky
+ * factor, FIRAL_ERR_NONFINITE for a non-finite objective or score. */
+
+/* Objective and exact gradient (Section 2, eqs. 4-7; Algorithm 1 lines 5-6):
+ * f = Tr(Sigma_z^{-1} H_p) with Sigma_z = H_o + sum_pool z_i H_i, and
+ * g_i = -Tr(H_i Sigma_z^{-1} H_p Sigma_z^{-1}) for the n pool points.
+ * z: device, n values of the vec type.  f_out: host double (the call synchronises), may be
+ * NULL.  g_out: device, n values of the vec type, or NULL to skip the gradient. */
+int32_t firal_exact_objective(firal_problem* problem, const void* z, double* f_out,
+                              void* g_out);
+
+/* Exact Relax (Algorithm 1 lines 2-10): T mirror-descent steps z <- z exp(-beta_t g),
+ * z <- budget z / sum(z), beta_t = beta0 / ||g||_inf, with the exact gradient.
+ * z0: device, n values on the budget simplex, or NULL for budget / n (may equal z_out).
+ * z_out: device, n values; holds z_diamond on return.  f_hist: host, T doubles (f before each
+ * step) or NULL.  Synchronises before returning. */
+int32_t firal_exact_relax(firal_problem* problem, double budget, int32_t T, double beta0,
+                          const void* z0, void* z_out, double* f_hist);
+
+/* Exact Round (Algorithm 1 lines 11-20; eqs. 8-10) on the full Hessians: budget picks of
+ *   i_t = argmin_i Tr[(A_t + (eta/b) H~_o + eta H~_i)^{-1}],  A_1 = sqrt(d~) I,
+ *   A_{t+1} = nu_{t+1} I + eta H~_t,  H~_t = sum_{s <= t} (H~_o / b + H~_{i_s}),
+ * with nu_{t+1} the root of sum_j (nu + lambda_j(eta H~_t))^{-2} = 1 and X~ = Sigma^{-1/2} X
+ * Sigma^{-1/2}, Sigma = H_o + H_{z_relaxed}.  eta <= 0 selects 8 sqrt(d~).  c <= 112.
+ * z_relaxed: device, n values of the vec type.  selected_out: device, budget int32 pool
+ * indices in selection order (ties to the lowest index; exclude_selected != 0 never picks a
+ * point twice).  r_out: host, budget doubles (the minimised trace of each pick) or NULL.
+ * nu_out: host, budget doubles (nu_t used for pick t; nu_1 = sqrt(d~)) or NULL.
+ * Synchronises before returning. */
+int32_t firal_exact_round(firal_problem* problem, const void* z_relaxed, int32_t budget,
+                          double eta, int32_t exclude_selected, int32_t* selected_out,
+                          double* r_out, double* nu_out);
+
 #ifdef __cplusplus
 }
 #endif

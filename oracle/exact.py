@@ -109,14 +109,17 @@ def _block_diagonal(M, d, c):
     return out
 
 
-def round_exact(prob, z_diamond, b, eta=None, block_diag=False, exclude_selected=True):
+def round_exact(prob, z_diamond, b, eta=None, block_diag=False, exclude_selected=True,
+                details=False):
     """Exact Round: FTRL greedy selection of ``b`` points (Algorithm 1, Round part).
 
     Each iteration picks ``argmin_i Tr[(A_t + eta/b H~_o + eta H~_i)^{-1}]``
     (eq. 9) with ``A_1 = sqrt(d~) I`` and ``A_{t+1} = nu I + eta H~_t``, ``nu``
     such that ``Tr(A^{-2}) = 1`` (eq. 10).  ``block_diag=True`` replaces every
     Hessian (``H_i``, ``H_o`` and ``Sigma_diamond``) by its block diagonal, the
-    assumption under which Proposition 1 holds.
+    assumption under which Proposition 1 holds.  ``details=True`` also returns the
+    minimised trace of every pick and the ``nu`` that defined ``A_t`` for it
+    (``nu_1 = sqrt(d~)``).
     """
     X = np.asarray(prob.X, np.float64)
     h = np.asarray(prob.h, np.float64)
@@ -134,7 +137,7 @@ def round_exact(prob, z_diamond, b, eta=None, block_diag=False, exclude_selected
     Hi_t = [tilde(bd(hessian_dense(X[i], h[i]))) for i in range(n)]
     A = np.sqrt(D) * np.eye(D)
     Ht = np.zeros((D, D))
-    chosen = []
+    chosen, r_pick, nus = [], [], [np.sqrt(D)]
     for _ in range(b):
         base = A + (eta / b) * Ho_t
         r = np.full(n, np.inf)
@@ -144,10 +147,14 @@ def round_exact(prob, z_diamond, b, eta=None, block_diag=False, exclude_selected
             r[i] = np.trace(np.linalg.inv(base + eta * Hi_t[i]))
         it = int(np.argmin(r))
         chosen.append(it)
+        r_pick.append(float(r[it]))
         Ht = Ht + Ho_t / b + Hi_t[it]
         lam, V = np.linalg.eigh(eta * Ht)
         nu = nu_bisect(lam)
+        nus.append(float(nu))
         A = (V * (nu + lam)) @ V.T
+    if details:
+        return chosen, r_pick, nus[:b]
     return chosen
 
 

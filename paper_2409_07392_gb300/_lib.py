@@ -15,6 +15,8 @@ FIRAL_DT_F64, FIRAL_DT_F32, FIRAL_DT_BF16 = 0, 1, 2
 STATUS = {0: "FIRAL_OK", -1: "FIRAL_ERR_ARG", -2: "FIRAL_ERR_CUDA", -3: "FIRAL_ERR_NOT_SPD",
           -4: "FIRAL_ERR_CG_NOT_CONVERGED", -5: "FIRAL_ERR_NONFINITE", -6: "FIRAL_ERR_TIMEOUT",
           -7: "FIRAL_ERR_NOMEM", -8: "FIRAL_ERR_UNSUPPORTED"}
+(FIRAL_OK, FIRAL_ERR_ARG, FIRAL_ERR_CUDA, FIRAL_ERR_NOT_SPD, FIRAL_ERR_CG_NOT_CONVERGED,
+ FIRAL_ERR_NONFINITE, FIRAL_ERR_TIMEOUT, FIRAL_ERR_NOMEM, FIRAL_ERR_UNSUPPORTED) = range(0, -9, -1)
 
 
 class FiralPool(ctypes.Structure):
@@ -103,6 +105,11 @@ SIGNATURES = [
     ("firal_block_eigvals", c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_void_p,
                                       c_void_p]),
     ("firal_nu_bisect", c_int32, [c_void_p, c_void_p, c_int64, POINTER(c_double)]),
+    ("firal_exact_objective", c_int32, [c_void_p, c_void_p, POINTER(c_double), c_void_p]),
+    ("firal_exact_relax", c_int32, [c_void_p, c_double, c_int32, c_double, c_void_p, c_void_p,
+                                    POINTER(c_double)]),
+    ("firal_exact_round", c_int32, [c_void_p, c_void_p, c_int32, c_double, c_int32, c_void_p,
+                                    POINTER(c_double), POINTER(c_double)]),
 ]
 
 _lib = None

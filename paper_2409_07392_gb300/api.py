@@ -252,6 +252,35 @@ class Problem:
                                              ctypes.byref(best)))
         return sel, list(crit), best.value
 
+    # ---- Exact-FIRAL (Algorithm 1) on dense d~ x d~ matrices
+    def exact_objective(self, z, grad=True):
+        """``(f, g)``: f = Tr(Sigma_z^{-1} H_p) and the exact gradient g (eq. 6, None when
+        grad is False)."""
+        z = self._vec(z)
+        f = ctypes.c_double()
+        g = torch.empty(self.n, dtype=self.vdt, device=self.device) if grad else None
+        self._chk(self.lib.firal_exact_objective(self._p, _ptr(z), ctypes.byref(f), _ptr(g)))
+        return f.value, g
+
+    def exact_relax(self, budget, T, beta0=1.0, z0=None):
+        """Exact Relax: ``(z_diamond, f history)``."""
+        z = torch.empty(self.n, dtype=self.vdt, device=self.device)
+        z0 = self._vec(z0) if z0 is not None else None
+        hist = (ctypes.c_double * max(T, 1))()
+        self._chk(self.lib.firal_exact_relax(self._p, float(budget), T, float(beta0), _ptr(z0),
+                                             _ptr(z), hist))
+        return z, list(hist)[:T]
+
+    def exact_round(self, z, budget, eta=0.0, exclude_selected=True):
+        """Exact Round: ``(selected (device int32), trace of each pick, nu_t of each pick)``."""
+        z = self._vec(z)
+        sel = torch.empty(budget, dtype=torch.int32, device=self.device)
+        r = (ctypes.c_double * budget)()
+        nu = (ctypes.c_double * budget)()
+        self._chk(self.lib.firal_exact_round(self._p, _ptr(z), budget, float(eta),
+                                             1 if exclude_selected else 0, _ptr(sel), r, nu))
+        return sel, list(r), list(nu)
+
 
 def _to_device(t, device, dtype=None, non_blocking=True):
     if t is None:

@@ -1084,7 +1084,8 @@ const char* firal_profile_name(int32_t id) {
   static const char* names[PF_COUNT] = {"prep", "probes", "syrk_blocks", "chol_inv",
                                         "apply_alpha", "apply_dterm", "apply_combine", "cg_vec",
                                         "quad_forms", "md_step", "dot", "round",
-                                        "apply_split"};
+                                        "apply_split", "exact_build", "exact_factor",
+                                        "exact_gemm", "exact_quad", "exact_score"};
   return (id >= 0 && id < PF_COUNT) ? names[id] : "unknown";
 }
 
@@ -1147,6 +1148,7 @@ int32_t firal_problem_create(firal_handle* H, const firal_pool* pool, const fira
 int32_t firal_problem_destroy(firal_problem* P) {
   if (!P) return FIRAL_OK;
   cudaStreamSynchronize(P->H->stream);
+  exact_release(P);
   for (DBuf* b : {&P->Xa, &P->Ha, &P->HaT, &P->w_sig, &P->w_p, &P->S_p, &P->S_sig, &P->Pblk,
                   &P->Minv, &P->HoBlk, &P->walpha, &P->Dpart, &P->syrk_part, &P->cgX, &P->cgR,
                   &P->cgP, &P->cgQ, &P->cgZ, &P->cgcols, &P->cgpart1, &P->cgpart2, &P->V, &P->U,
@@ -1429,3 +1431,64 @@ int32_t firal_nu_bisect(firal_handle* H, const double* mu, int64_t count, double
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------------
+// Exact-FIRAL (Algorithm 1) on dense d~ x d~ matrices
+// ------------------------------------------------------------------------------------------
+namespace firal {
+namespace {
+constexpr int64_t kExactMaxDim = 16384;
+int32_t exact_check(firal_problem* P) {
+  if (!P) return fail(FIRAL_ERR_ARG, "problem must be non-null");
+  if (P->pt.Q) return fail(FIRAL_ERR_UNSUPPORTED, "Exact-FIRAL does not take pooled problems");
+  if (P->D > kExactMaxDim) return fail(FIRAL_ERR_UNSUPPORTED, "Exact-FIRAL needs d c <= 16384");
+  return FIRAL_OK;
+}
+}  // namespace
+}  // namespace firal
+
+int32_t firal_exact_objective(firal_problem* P, const void* z, double* f_out, void* g_out) {
+  firal_handle* H = P ? P->H : nullptr;
+  int32_t rc = exact_check(P);
+  if (rc == FIRAL_OK && !z) rc = fail(FIRAL_ERR_ARG, "z must be non-null");
+  if (rc == FIRAL_OK) rc = exact_objective(P, z, f_out, g_out);
+  return record(H, rc);
+}
+
+int32_t firal_exact_relax(firal_problem* P, double budget, int32_t T, double beta0,
+                          const void* z0, void* z_out, double* f_hist) {
+  firal_handle* H = P ? P->H : nullptr;
+  int32_t rc = exact_check(P);
+  if (rc == FIRAL_OK && (!z_out || !(budget > 0) || T < 0 || !(beta0 > 0)))
+    rc = fail(FIRAL_ERR_ARG, "bad exact_relax arguments");
+  if (rc == FIRAL_OK) rc = exact_relax(P, budget, T, beta0, z0, z_out, f_hist);
+  if (rc == FIRAL_OK) {
+    cudaError_t e = cudaStreamSynchronize(P->H->stream);
+    if (e != cudaSuccess) rc = fail(FIRAL_ERR_CUDA, cudaGetErrorString(e));
+  }
+  return record(H, rc);
+}
+
+int32_t firal_exact_round(firal_problem* P, const void* z_relaxed, int32_t budget, double eta,
+                          int32_t exclude_selected, int32_t* selected_out, double* r_out,
+                          double* nu_out) {
+  firal_handle* H = P ? P->H : nullptr;
+  int32_t rc = exact_check(P);
+  if (rc == FIRAL_OK && (!z_relaxed || !selected_out))
+    rc = fail(FIRAL_ERR_ARG, "z_relaxed and selected_out must be non-null");
+  if (rc == FIRAL_OK && (budget < 1 || budget > P->n))
+    rc = fail(FIRAL_ERR_ARG, "budget must be in [1, n]");
+  if (rc == FIRAL_OK && P->c > 112)
+    rc = fail(FIRAL_ERR_UNSUPPORTED, "exact Round needs c <= 112");
+  if (rc == FIRAL_OK) {
+    const double e = eta > 0 ? eta : 8.0 * std::sqrt((double)P->D);
+    int evals = 0;
+    rc = exact_round(P, z_relaxed, budget, e, exclude_selected ? 1 : 0, selected_out, r_out,
+                     nu_out, &evals);
+  }
+  if (rc == FIRAL_OK) {
+    cudaError_t e = cudaStreamSynchronize(P->H->stream);
+    if (e != cudaSuccess) rc = fail(FIRAL_ERR_CUDA, cudaGetErrorString(e));
+  }
+  return record(H, rc);
+}

@@ -78,7 +78,8 @@ namespace firal {
 // Kernel-class timers and the launch counter (see firal_profile* in firal.h).
 enum ProfId {
   PF_PREP = 0, PF_PROBES, PF_SYRK, PF_CHOL, PF_ALPHA, PF_DTERM, PF_COMBINE, PF_CG, PF_QUAD,
-  PF_MD, PF_DOT, PF_ROUND, PF_SPLIT, PF_COUNT
+  PF_MD, PF_DOT, PF_ROUND, PF_SPLIT, PF_EXACT_BUILD, PF_EXACT_FACTOR, PF_EXACT_GEMM,
+  PF_EXACT_QUAD, PF_EXACT_SCORE, PF_COUNT
 };
 extern std::atomic<long long> g_launches;
 inline void count_launch(int n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
@@ -122,7 +123,28 @@ __device__ __forceinline__ int pool_of(const PoolTab& t, int k) { return t.Q ? t
 #endif
 }  // namespace firal
 
+namespace firal {
+// Dense d~ x d~ workspace of Exact-FIRAL (Algorithm 1), allocated on first use.
+enum ExactMat {
+  EX_HO = 0, EX_HP, EX_A, EX_W, EX_S, EX_T, EX_M,   // Relax (objective and gradient)
+  EX_MATS_RELAX,
+  EX_SIG = EX_MATS_RELAX, EX_LINV, EX_HSUM, EX_HHO, EX_MHAT,   // Round
+  EX_MATS
+};
+struct ExactWs {
+  DBuf m[EX_MATS];
+  DBuf pairs;           // int2 (k, l), k <= l, row by row
+  int npairs = 0;
+  bool ho_ready = false, hp_ready = false;
+  DBuf part, gpart;     // class-pair partial sums / gradient partials per pair group
+  DBuf K, YZ;           // Round: c x c matrices per candidate chunk; rank-c factors (d~ x c)
+  DBuf negr, mask, argp;
+  DBuf flag, scal;      // not-SPD flag; device scalars and reduction partials
+};
+}  // namespace firal
+
 struct firal_problem {
+  firal::ExactWs* ex = nullptr;   // Exact-FIRAL dense workspace (null until used)
   int sms = 0;            // SM budget for grids and split counts (<= H->sm_count)
   firal::PoolTab pt;      // pooled problems only (device tables below)
   firal::DBuf pool_tabs;  // cpool | coff | pdim (int32) for pt
@@ -225,4 +247,11 @@ int32_t lincomb(double* out, double a, const double* X, double b, const double* 
                 const double* Z, int64_t total, cudaStream_t st);
 int32_t lincomb_nu(double* out, const double* nu, const double* X, double b, const double* Y,
                    double cc, const double* Z, int64_t total, cudaStream_t st);
+// ---- k_exact.cu (Exact-FIRAL, dense d~ x d~)
+int32_t exact_objective(firal_problem* P, const void* z, double* f_host, void* g);
+int32_t exact_relax(firal_problem* P, double budget, int T, double beta0, const void* z0,
+                    void* z, double* hist);
+int32_t exact_round(firal_problem* P, const void* zd, int b, double eta, int exclude,
+                    int32_t* sel, double* r_host, double* nu_host, int* evals);
+void exact_release(firal_problem* P);
 }  // namespace firal

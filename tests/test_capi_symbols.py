@@ -39,13 +39,35 @@ def test_status_strings_and_build_info(lib):
     assert lib.firal_build_info() & 1
 
 
-def test_struct_layouts_match_header():
+def test_struct_layouts_match_header(tmp_path):
+    """The ctypes mirrors agree with the C compiler's layout of include/firal.h."""
+    import shutil
+    import subprocess
     from paper_2409_07392_gb300 import _lib as L
-    assert ctypes.sizeof(L.FiralPool) == 40
-    assert ctypes.sizeof(L.FiralCGOpts) == 16
-    assert ctypes.sizeof(L.FiralRelaxOpts) == 56
-    assert L.FiralRelaxOpts.beta0.offset == 24 and L.FiralRelaxOpts.md_tol.offset == 48
-    assert ctypes.sizeof(L.FiralStepStats) == 48
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    checks = {
+        "sizeof(firal_pool)": ctypes.sizeof(L.FiralPool),
+        "sizeof(firal_hess0)": ctypes.sizeof(L.FiralHess0),
+        "sizeof(firal_cg_opts)": ctypes.sizeof(L.FiralCGOpts),
+        "offsetof(firal_cg_opts, block)": L.FiralCGOpts.block.offset,
+        "sizeof(firal_relax_opts)": ctypes.sizeof(L.FiralRelaxOpts),
+        "offsetof(firal_relax_opts, cg)": L.FiralRelaxOpts.cg.offset,
+        "offsetof(firal_relax_opts, beta0)": L.FiralRelaxOpts.beta0.offset,
+        "offsetof(firal_relax_opts, seed)": L.FiralRelaxOpts.seed.offset,
+        "offsetof(firal_relax_opts, md_tol)": L.FiralRelaxOpts.md_tol.offset,
+        "sizeof(firal_step_stats)": ctypes.sizeof(L.FiralStepStats),
+        "sizeof(firal_round_opts)": ctypes.sizeof(L.FiralRoundOpts),
+    }
+    src = tmp_path / "layout.c"
+    body = "".join(f'  printf("%zu\\n", (size_t)({k}));\n' for k in checks)
+    src.write_text("#include <stdio.h>\n#include <stddef.h>\n#include \"firal.h\"\n"
+                   "int main(void) {\n" + body + "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    assert [int(v) for v in got] == list(checks.values()), dict(zip(checks, got))
 
 
 def test_null_arguments_rejected_without_gpu(lib):
