@@ -381,6 +381,59 @@ int32_t firal_exact_round(firal_problem* problem, const void* z_relaxed, int32_t
                           double eta, int32_t exclude_selected, int32_t* selected_out,
                           double* r_out, double* nu_out);
 
+/* ---------------------------------------------------------------- active learning (Section 5) */
+
+/* Class probabilities of the multinomial logistic-regression classifier (eq. 1):
+ * h_i = softmax(W x_i) for the rows of X.  X: device, rows x d of x_dtype.  W: device, c x d
+ * (row k = class k) of the vec type of `precision` (FIRAL_FP64: double, otherwise float).
+ * h_out: device, rows x c of that type.  Synchronises. */
+int32_t firal_lr_probs(firal_handle* handle, const void* X, int32_t x_dtype, const void* W,
+                       int64_t rows, int32_t d, int32_t c, int32_t precision, void* h_out);
+
+/* Classifier refit: W minimising sum_i -log softmax(W x_i)_{y_i} + (gamma / 2) ||W||_F^2 over
+ * m labelled rows, by damped Newton steps (Armijo backtracking) whose systems
+ * (sum_i H_i + gamma I) dW = grad, H_i of eq. 2, are solved with the block-Jacobi PCG of
+ * Algorithm 2 (FP64 for FIRAL_FP64, FP32 otherwise).  X: device, m x d of x_dtype.  y: device,
+ * m int32 labels in [0, c) (checked; FIRAL_ERR_ARG otherwise).  W: device, c x d of the vec type;
+ * in: starting point, out: the fit.  Stops when ||grad|| <= tol max(1, ||grad(W_start)||)
+ * (tol <= 0: 1e-8; in FP32 tol is raised to at least 2e-5, the float noise floor of the
+ * gradient), when no Armijo step lowers the loss, or after max_newton steps.  iters_out,
+ * gnorm_out: host or NULL. */
+int32_t firal_lr_fit(firal_handle* handle, const void* X, int32_t x_dtype, const int32_t* y,
+                     int64_t m, int32_t d, int32_t c, double gamma, int32_t precision,
+                     int32_t max_newton, double tol, void* W, int32_t* iters_out,
+                     double* gnorm_out);
+
+/* Controls of the active-learning loop. */
+typedef struct {
+  int32_t rounds;          /* AL rounds (>= 1)                                              */
+  int32_t budget;          /* points selected per round (>= 1; rounds * budget < n)         */
+  double lambda;           /* ridge of H_o in Relax and Round (eq. 3)                       */
+  double lr_gamma;         /* ridge of the classifier refit (> 0)                           */
+  int32_t lr_max_newton;   /* Newton steps per refit (<= 0: 30)                             */
+  int32_t reserved;        /* 0                                                             */
+  double lr_tol;           /* refit gradient tolerance (<= 0: 1e-8)                         */
+  firal_relax_opts relax;  /* Relax of every round; round r draws its probes with seed       */
+                           /* relax.seed + r; relax.precision also sets Round's precision  */
+  double eta;              /* Round eta (<= 0: 8 sqrt(d c))                                 */
+} firal_al_opts;
+
+/* Multi-round active learning (the outer loop of Section 5).  Round r = 0 .. rounds-1: refit W
+ * on the labelled set (the m initial rows, then the pool rows picked so far, in selection
+ * order; warm start from the previous round, W = 0 at first), set h = softmax(W x) on the
+ * labelled set and on the remaining pool (pool rows not picked yet, in index order), run Relax
+ * (Algorithm 2) with budget = opts->budget and Round (Algorithm 3) on that pool, and move the
+ * picks to the labelled set.  X_pool: device, n x d of x_dtype; y_pool: device, n int32 labels
+ * (a pool label enters only once its point is picked).  X_lab, y_lab: device, m rows / labels
+ * (m >= 0).  selected_out: device, rounds * budget int32 pool indices, round-major in
+ * selection order.  W_out: device, c x d of the vec type: the classifier refit on the final
+ * labelled set, or NULL.  fhat_out: host, rounds doubles (last f^ of each Relax) or NULL.
+ * Synchronises before returning. */
+int32_t firal_active_learning(firal_handle* handle, const void* X_pool, const int32_t* y_pool,
+                              int64_t n, const void* X_lab, const int32_t* y_lab, int64_t m,
+                              int32_t d, int32_t c, int32_t x_dtype, const firal_al_opts* opts,
+                              int32_t* selected_out, void* W_out, double* fhat_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -15,6 +15,8 @@ Modules
   exact   -- Exact-FIRAL (Algorithm 1): dense dc x dc Hessians on tiny inputs.
   approx  -- Approx-FIRAL (Algorithms 2 and 3): matrix-free Relax and
              block-diagonal Round.
+  al      -- the active-learning outer loop of Section 5: classifier refit
+             (ridge multinomial logistic regression by Newton) and the rounds.
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test in
 ``tests/test_oracle_*.py`` against a closed form, an invariant, an

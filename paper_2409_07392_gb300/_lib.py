@@ -39,6 +39,12 @@ class FiralRelaxOpts(ctypes.Structure):
                 ("md_tol", c_double)]
 
 
+class FiralAlOpts(ctypes.Structure):
+    _fields_ = [("rounds", c_int32), ("budget", c_int32), ("lam", c_double),
+                ("lr_gamma", c_double), ("lr_max_newton", c_int32), ("reserved", c_int32),
+                ("lr_tol", c_double), ("relax", FiralRelaxOpts), ("eta", c_double)]
+
+
 class FiralStepStats(ctypes.Structure):
     _fields_ = [("fhat", c_double), ("gmax", c_double), ("zmax", c_double),
                 ("cg_iters", c_int32 * 2), ("cg_relres", c_double * 2)]
@@ -110,6 +116,15 @@ SIGNATURES = [
                                     POINTER(c_double)]),
     ("firal_exact_round", c_int32, [c_void_p, c_void_p, c_int32, c_double, c_int32, c_void_p,
                                     POINTER(c_double), POINTER(c_double)]),
+    ("firal_lr_probs", c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_int64, c_int32,
+                                 c_int32, c_int32, c_void_p]),
+    ("firal_lr_fit", c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_int64, c_int32, c_int32,
+                               c_double, c_int32, c_int32, c_double, c_void_p,
+                               POINTER(c_int32), POINTER(c_double)]),
+    ("firal_active_learning", c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p,
+                                        c_void_p, c_int64, c_int32, c_int32, c_int32,
+                                        POINTER(FiralAlOpts), c_void_p, c_void_p,
+                                        POINTER(c_double)]),
 ]
 
 _lib = None

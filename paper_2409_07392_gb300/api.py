@@ -282,6 +282,62 @@ class Problem:
         return sel, list(r), list(nu)
 
 
+# ---- active learning (the outer loop of Section 5)
+def lr_probs(X, W, precision="fp32", handle: Handle | None = None):
+    """h = softmax(X W^T) row by row (eq. 1); X (rows x d) and W (c x d) on the device."""
+    H = handle or Handle()
+    vdt = vec_dtype(precision)
+    X = X.contiguous()
+    W = W.to(vdt).contiguous()
+    h = torch.empty((X.shape[0], W.shape[0]), dtype=vdt, device=X.device)
+    L.check(H.lib.firal_lr_probs(H.ptr, _ptr(X), _dt(X), _ptr(W), X.shape[0], X.shape[1],
+                                 W.shape[0], PRECISIONS[precision], _ptr(h)), H.ptr)
+    return h
+
+
+def lr_fit(X, y, c, gamma=1.0, precision="fp32", W0=None, max_newton=30, tol=1e-8,
+           handle: Handle | None = None):
+    """Ridge-regularised multinomial logistic regression by damped Newton-PCG; returns
+    ``(W (c x d), newton_steps, final gradient norm)``."""
+    H = handle or Handle()
+    vdt = vec_dtype(precision)
+    X = X.contiguous()
+    y = y.to(torch.int32).contiguous()
+    W = (torch.zeros((c, X.shape[1]), dtype=vdt, device=X.device) if W0 is None
+         else W0.to(vdt).contiguous().clone())
+    it, gn = ctypes.c_int32(), ctypes.c_double()
+    L.check(H.lib.firal_lr_fit(H.ptr, _ptr(X), _dt(X), _ptr(y), X.shape[0], X.shape[1], c,
+                               float(gamma), PRECISIONS[precision], max_newton, float(tol),
+                               _ptr(W), ctypes.byref(it), ctypes.byref(gn)), H.ptr)
+    return W, it.value, gn.value
+
+
+def active_learning(X_pool, y_pool, X_lab, y_lab, c, rounds, budget, *, lam=1e-3,
+                    lr_gamma=1.0, precision="fp32", s=10, T=20, tol=0.1, maxit=100,
+                    fixed_iters=0, beta0=1.0, seed=1, md_tol=0.0, eta=0.0, lr_max_newton=30,
+                    lr_tol=1e-8, handle: Handle | None = None):
+    """Multi-round active learning on device tensors: returns ``(selected (rounds x budget)
+    pool indices, final classifier W (c x d), last f^ of each round's Relax)``."""
+    H = handle or Handle()
+    X_pool, y_pool = X_pool.contiguous(), y_pool.to(torch.int32).contiguous()
+    m = 0 if X_lab is None else X_lab.shape[0]
+    if m:
+        X_lab = X_lab.to(X_pool.dtype).contiguous()
+        y_lab = y_lab.to(torch.int32).contiguous()
+    n, d = X_pool.shape
+    ro = L.FiralRelaxOpts(s, T, _cg(tol, maxit, fixed_iters), beta0, seed, PRECISIONS[precision],
+                          0, md_tol)
+    o = L.FiralAlOpts(rounds, budget, lam, lr_gamma, lr_max_newton, 0, lr_tol, ro, eta)
+    sel = torch.empty((rounds, budget), dtype=torch.int32, device=X_pool.device)
+    W = torch.empty((c, d), dtype=vec_dtype(precision), device=X_pool.device)
+    fh = (ctypes.c_double * rounds)()
+    L.check(H.lib.firal_active_learning(H.ptr, _ptr(X_pool), _ptr(y_pool), n,
+                                        _ptr(X_lab) if m else None, _ptr(y_lab) if m else None,
+                                        m, d, c, _dt(X_pool), ctypes.byref(o), _ptr(sel),
+                                        _ptr(W), fh), H.ptr)
+    return sel, W, list(fh)
+
+
 def _to_device(t, device, dtype=None, non_blocking=True):
     if t is None:
         return None

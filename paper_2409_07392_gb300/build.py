@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libfiral.so")
-SOURCES = ["capi.cu", "k_simt.cu", "k_linalg.cu", "k_tc.cu", "k_noalloc.cu", "k_exact.cu"]
+SOURCES = ["capi.cu", "k_simt.cu", "k_linalg.cu", "k_tc.cu", "k_noalloc.cu", "k_exact.cu", "k_al.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include"), "-I", SRC]

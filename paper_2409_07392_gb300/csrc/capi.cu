@@ -1085,7 +1085,8 @@ const char* firal_profile_name(int32_t id) {
                                         "apply_alpha", "apply_dterm", "apply_combine", "cg_vec",
                                         "quad_forms", "md_step", "dot", "round",
                                         "apply_split", "exact_build", "exact_factor",
-                                        "exact_gemm", "exact_quad", "exact_score"};
+                                        "exact_gemm", "exact_quad", "exact_score",
+                                        "lr_refit"};
   return (id >= 0 && id < PF_COUNT) ? names[id] : "unknown";
 }
 
@@ -1491,4 +1492,283 @@ int32_t firal_exact_round(firal_problem* P, const void* z_relaxed, int32_t budge
     if (e != cudaSuccess) rc = fail(FIRAL_ERR_CUDA, cudaGetErrorString(e));
   }
   return record(H, rc);
+}
+
+// ------------------------------------------------------------------------------------------
+// Active learning (the outer loop of Section 5): classifier refit and the round driver
+// ------------------------------------------------------------------------------------------
+namespace {
+
+int32_t labels_in_range(const int32_t* y, int64_t m, int c, cudaStream_t st) {
+  if (m <= 0) return FIRAL_OK;
+  std::vector<int32_t> hy((size_t)m);
+  FIRAL_CUDA_TRY(cudaMemcpyAsync(hy.data(), y, (size_t)m * sizeof(int32_t),
+                                 cudaMemcpyDeviceToHost, st));
+  FIRAL_CUDA_TRY(cudaStreamSynchronize(st));
+  for (int32_t v : hy)
+    if (v < 0 || v >= c) return fail(FIRAL_ERR_ARG, "labels must lie in [0, c)");
+  return FIRAL_OK;
+}
+
+// Damped Newton for W = argmin sum_i -log softmax(W x_i)_{y_i} + (gamma / 2) ||W||^2 on the
+// labelled rows Xv (m x d, vec type).  Each step solves (sum_i H_i(W) + gamma I) dW = grad
+// with the block-Jacobi PCG (a problem whose pool is the labelled set with unit weights),
+// then backtracks along -dW until the Armijo condition holds.
+int32_t lr_fit_impl(firal_handle* H, const void* Xv, const int32_t* y, int64_t m, int d, int c,
+                    double gamma, bool dbl, int max_newton, double tol, void* W, int* iters_out,
+                    double* gnorm_out) {
+  cudaStream_t st = H->stream;
+  const size_t vs = dbl ? 8 : 4;
+  const int64_t D = (int64_t)c * d;
+  DBuf h, R, g, dW, Wt, ones, part;
+  auto rel = [&] {
+    for (DBuf* b : {&h, &R, &g, &dW, &Wt, &ones, &part}) b->release();
+  };
+  int32_t rc = FIRAL_OK;
+#define TRYL(x)          \
+  do {                   \
+    rc = (x);            \
+    if (rc != FIRAL_OK) { \
+      rel();             \
+      return rc;         \
+    }                    \
+  } while (0)
+  TRYL(h.ensure((size_t)m * c * vs));
+  TRYL(R.ensure((size_t)m * c * vs));
+  TRYL(g.ensure((size_t)D * vs));
+  TRYL(dW.ensure((size_t)D * vs));
+  TRYL(Wt.ensure((size_t)D * vs));
+  TRYL(ones.ensure((size_t)m * vs));
+  TRYL(part.ensure(272 * sizeof(double)));
+  TRYL(fill_weights(dbl, ones.p, 0, 0.0, nullptr, 1.0, m, st));
+  double* pp = part.as<double>();
+  double* dv = pp + 256;
+  auto read = [&](double* host, int k) -> int32_t {
+    FIRAL_CUDA_TRY(cudaMemcpyAsync(host, dv, k * sizeof(double), cudaMemcpyDeviceToHost, st));
+    FIRAL_CUDA_TRY(cudaStreamSynchronize(st));
+    return FIRAL_OK;
+  };
+  auto loss = [&](const void* Wc, double* out) -> int32_t {
+    FIRAL_TRY(lr_probs(dbl, Xv, Wc, m, d, c, h.p, st));
+    FIRAL_TRY(lr_nll(dbl, h.p, y, m, c, pp, dv, st));
+    FIRAL_TRY(dot_scaled(dbl, Wc, Wc, D, 1.0, pp, dv + 1, st));
+    double hv[2];
+    FIRAL_TRY(read(hv, 2));
+    *out = hv[0] + 0.5 * gamma * hv[1];
+    return FIRAL_OK;
+  };
+  // a float gradient stops shrinking near 1e-5 of its start: do not ask for more
+  if (!dbl) tol = std::max(tol, 2e-5);
+  int it = 0;
+  double gn = 0.0, gn0 = 0.0;
+  for (; it < max_newton; ++it) {
+    double f0 = 0.0;
+    TRYL(loss(W, &f0));
+    TRYL(lr_grad(dbl, Xv, y, h.p, W, m, d, c, gamma, R.p, g.p, st));
+    TRYL(dot_scaled(dbl, g.p, g.p, D, 1.0, pp, dv, st));
+    double g2 = 0.0;
+    TRYL(read(&g2, 1));
+    gn = std::sqrt(g2);
+    if (it == 0) gn0 = gn;
+    if (!(gn == gn)) TRYL(fail(FIRAL_ERR_NONFINITE, "classifier gradient is not finite"));
+    if (gn <= tol * std::max(1.0, gn0)) break;
+    firal_pool pool{Xv, h.p, m, d, c, dbl ? FIRAL_DT_F64 : FIRAL_DT_F32,
+                    dbl ? FIRAL_DT_F64 : FIRAL_DT_F32};
+    firal_hess0 h0{nullptr, nullptr, 0, gamma};
+    firal_problem* P = nullptr;
+    TRYL(problem_create_impl(H, &pool, &h0, dbl ? FIRAL_FP64 : FIRAL_FP32, &P));
+    firal_cg_opts cg{dbl ? 1e-11 : 1e-6, 4000, 0, 0, 0};
+    CGResult res;
+    rc = setup_sigma(P, ones.p, true);
+    if (rc == FIRAL_OK) rc = pcg_run(P, g.p, 1, cg, dW.p, true, &res, nullptr);
+    firal_problem_destroy(P);
+    if (rc != FIRAL_OK) {
+      rel();
+      return rc;
+    }
+    TRYL(dot_scaled(dbl, g.p, dW.p, D, 1.0, pp, dv, st));
+    double gd = 0.0;
+    TRYL(read(&gd, 1));
+    double step = 1.0;
+    bool ok = false;
+    for (int ls = 0; ls < 40 && gd > 0.0; ++ls) {
+      TRYL(axpby(dbl, Wt.p, 1.0, W, -step, dW.p, D, st));
+      double ft = 0.0;
+      TRYL(loss(Wt.p, &ft));
+      if (ft <= f0 - 1e-4 * step * gd) {
+        ok = true;
+        break;
+      }
+      step *= 0.5;
+    }
+    if (!ok) break;
+    FIRAL_CUDA_TRY(cudaMemcpyAsync(W, Wt.p, (size_t)D * vs, cudaMemcpyDeviceToDevice, st));
+  }
+#undef TRYL
+  if (iters_out) *iters_out = it;
+  if (gnorm_out) *gnorm_out = gn;
+  FIRAL_CUDA_TRY(cudaStreamSynchronize(st));
+  rel();
+  return read_flags(H);
+}
+
+int32_t al_impl(firal_handle* H, const void* Xp, const int32_t* yp, int64_t n, const void* Xl0,
+                const int32_t* yl0, int64_t m, int d, int c, int32_t x_dtype,
+                const firal_al_opts& o, int32_t* sel_out, void* W_out, double* fhat_out) {
+  cudaStream_t st = H->stream;
+  const bool dbl = o.relax.precision == FIRAL_FP64;
+  const size_t vs = dbl ? 8 : 4;
+  const int32_t vdt = dbl ? FIRAL_DT_F64 : FIRAL_DT_F32;
+  const int R = o.rounds, b = o.budget;
+  const int64_t mt = m + (int64_t)R * b;
+  const int newton = o.lr_max_newton > 0 ? o.lr_max_newton : 30;
+  const double ltol = o.lr_tol > 0 ? o.lr_tol : 1e-8;
+  FIRAL_TRY(labels_in_range(yp, n, c, st));
+  FIRAL_TRY(labels_in_range(yl0, m, c, st));
+  DBuf Xpv, Xl, yl, Xr, hr, hl, W, z, idx, sl;
+  auto rel = [&] {
+    for (DBuf* bf : {&Xpv, &Xl, &yl, &Xr, &hr, &hl, &W, &z, &idx, &sl}) bf->release();
+  };
+  int32_t rc = FIRAL_OK;
+#define TRYA(x)          \
+  do {                   \
+    rc = (x);            \
+    if (rc != FIRAL_OK) { \
+      rel();             \
+      return rc;         \
+    }                    \
+  } while (0)
+  TRYA(Xpv.ensure((size_t)n * d * vs));
+  TRYA(Xl.ensure((size_t)mt * d * vs));
+  TRYA(yl.ensure((size_t)mt * sizeof(int32_t)));
+  TRYA(Xr.ensure((size_t)n * d * vs));
+  TRYA(hr.ensure((size_t)n * c * vs));
+  TRYA(hl.ensure((size_t)mt * c * vs));
+  TRYA(W.ensure((size_t)c * d * vs));
+  TRYA(z.ensure((size_t)n * vs));
+  TRYA(idx.ensure((size_t)n * sizeof(int32_t)));
+  TRYA(sl.ensure((size_t)b * sizeof(int32_t)));
+  // the pool and the initial labelled rows in the vec type
+  TRYA(copy_rows(dbl, Xpv.p, nullptr, 0, Xp, n, d, x_dtype, st));
+  if (m > 0) {
+    TRYA(copy_rows(dbl, Xl.p, nullptr, 0, Xl0, m, d, x_dtype, st));
+    FIRAL_CUDA_TRY(cudaMemcpyAsync(yl.p, yl0, (size_t)m * sizeof(int32_t),
+                                   cudaMemcpyDeviceToDevice, st));
+  }
+  FIRAL_CUDA_TRY(cudaMemsetAsync(W.p, 0, (size_t)c * d * vs, st));
+  std::vector<int32_t> remaining((size_t)n), picks((size_t)b), orig((size_t)b);
+  for (int64_t i = 0; i < n; ++i) remaining[(size_t)i] = (int32_t)i;
+  for (int r = 0; r < R; ++r) {
+    const int64_t ml = m + (int64_t)r * b, nr = n - (int64_t)r * b;
+    // remaining pool rows, in index order
+    FIRAL_CUDA_TRY(cudaMemcpyAsync(idx.p, remaining.data(), (size_t)nr * sizeof(int32_t),
+                                   cudaMemcpyHostToDevice, st));
+    TRYA(gather_rows(dbl, false, Xpv.p, idx.as<int32_t>(), nr, d, Xr.p, st));
+    // classifier refit on the labelled set (warm start from the previous round), then h
+    if (ml > 0)
+      TRYA(lr_fit_impl(H, Xl.p, yl.as<int32_t>(), ml, d, c, o.lr_gamma, dbl, newton, ltol, W.p,
+                       nullptr, nullptr));
+    TRYA(lr_probs(dbl, Xl.p, W.p, ml, d, c, hl.p, st));
+    TRYA(lr_probs(dbl, Xr.p, W.p, nr, d, c, hr.p, st));
+    // Relax (Algorithm 2) and Round (Algorithm 3) on the remaining pool
+    firal_pool pool{Xr.p, hr.p, nr, d, c, vdt, vdt};
+    firal_hess0 h0{ml > 0 ? Xl.p : nullptr, ml > 0 ? hl.p : nullptr, ml, o.lambda};
+    firal_relax_opts ro = o.relax;
+    ro.seed = o.relax.seed + (uint64_t)r;
+    firal_relax_stats rs{};
+    TRYA(firal_relax(H, &pool, &h0, (double)b, nullptr, &ro, z.p, nullptr, &rs));
+    if (fhat_out) fhat_out[r] = rs.fhat_last;
+    firal_round_opts rop{o.eta, 1, o.relax.precision};
+    TRYA(firal_round(H, &pool, &h0, z.p, b, &rop, sl.as<int32_t>(), nullptr));
+    FIRAL_CUDA_TRY(cudaMemcpyAsync(picks.data(), sl.p, (size_t)b * sizeof(int32_t),
+                                   cudaMemcpyDeviceToHost, st));
+    FIRAL_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int j = 0; j < b; ++j) {
+      if (picks[j] < 0 || picks[j] >= nr) TRYA(fail(FIRAL_ERR_NONFINITE, "Round pick out of range"));
+      orig[j] = remaining[(size_t)picks[j]];
+    }
+    FIRAL_CUDA_TRY(cudaMemcpyAsync(sel_out + (size_t)r * b, orig.data(), (size_t)b * sizeof(int32_t),
+                                   cudaMemcpyHostToDevice, st));
+    // the picked points join the labelled set, in selection order
+    FIRAL_CUDA_TRY(cudaMemcpyAsync(idx.p, orig.data(), (size_t)b * sizeof(int32_t),
+                                   cudaMemcpyHostToDevice, st));
+    TRYA(gather_rows(dbl, false, Xpv.p, idx.as<int32_t>(), b, d, (char*)Xl.p + ml * d * vs, st));
+    TRYA(gather_rows(dbl, true, yp, idx.as<int32_t>(), b, 1, yl.as<int32_t>() + ml, st));
+    FIRAL_CUDA_TRY(cudaStreamSynchronize(st));
+    std::vector<char> taken((size_t)n, 0);
+    for (int j = 0; j < b; ++j) taken[(size_t)orig[j]] = 1;
+    std::vector<int32_t> next;
+    next.reserve((size_t)(nr - b));
+    for (int64_t q = 0; q < nr; ++q)
+      if (!taken[(size_t)remaining[(size_t)q]]) next.push_back(remaining[(size_t)q]);
+    remaining.swap(next);
+  }
+  if (W_out) {
+    TRYA(lr_fit_impl(H, Xl.p, yl.as<int32_t>(), mt, d, c, o.lr_gamma, dbl, newton, ltol, W.p,
+                     nullptr, nullptr));
+    FIRAL_CUDA_TRY(cudaMemcpyAsync(W_out, W.p, (size_t)c * d * vs, cudaMemcpyDeviceToDevice, st));
+  }
+  FIRAL_CUDA_TRY(cudaStreamSynchronize(st));
+#undef TRYA
+  rel();
+  return FIRAL_OK;
+}
+
+bool valid_shape(int64_t rows, int d, int c) { return rows >= 0 && d >= 1 && d <= 128 && c >= 2 && c <= 4096; }
+
+}  // namespace
+
+int32_t firal_lr_probs(firal_handle* H, const void* X, int32_t x_dtype, const void* W,
+                       int64_t rows, int32_t d, int32_t c, int32_t precision, void* h_out) {
+  if (!H || !X || !W || !h_out || !valid_shape(rows, d, c) || x_dtype < 0 || x_dtype > 2)
+    return record(H, fail(FIRAL_ERR_ARG, "bad lr_probs arguments"));
+  const bool dbl = precision == FIRAL_FP64;
+  const size_t vs = dbl ? 8 : 4;
+  DBuf Xv;
+  int32_t rc = Xv.ensure((size_t)rows * d * vs);
+  if (rc == FIRAL_OK) rc = copy_rows(dbl, Xv.p, nullptr, 0, X, rows, d, x_dtype, H->stream);
+  if (rc == FIRAL_OK) rc = lr_probs(dbl, Xv.p, W, rows, d, c, h_out, H->stream);
+  if (rc == FIRAL_OK && cudaStreamSynchronize(H->stream) != cudaSuccess)
+    rc = fail(FIRAL_ERR_CUDA, "lr_probs failed");
+  Xv.release();
+  return record(H, rc);
+}
+
+int32_t firal_lr_fit(firal_handle* H, const void* X, int32_t x_dtype, const int32_t* y, int64_t m,
+                     int32_t d, int32_t c, double gamma, int32_t precision, int32_t max_newton,
+                     double tol, void* W, int32_t* iters_out, double* gnorm_out) {
+  if (!H || !X || !y || !W || m < 1 || !valid_shape(m, d, c) || x_dtype < 0 || x_dtype > 2 ||
+      !(gamma > 0) || max_newton < 0)
+    return record(H, fail(FIRAL_ERR_ARG, "bad lr_fit arguments"));
+  const bool dbl = precision == FIRAL_FP64;
+  const size_t vs = dbl ? 8 : 4;
+  int32_t rc = labels_in_range(y, m, c, H->stream);
+  DBuf Xv;
+  if (rc == FIRAL_OK) rc = Xv.ensure((size_t)m * d * vs);
+  if (rc == FIRAL_OK) rc = copy_rows(dbl, Xv.p, nullptr, 0, X, m, d, x_dtype, H->stream);
+  int it = 0;
+  double gn = 0.0;
+  if (rc == FIRAL_OK)
+    rc = lr_fit_impl(H, Xv.p, y, m, d, c, gamma, dbl, max_newton, tol > 0 ? tol : 1e-8, W, &it,
+                     &gn);
+  if (iters_out) *iters_out = it;
+  if (gnorm_out) *gnorm_out = gn;
+  Xv.release();
+  return record(H, rc);
+}
+
+int32_t firal_active_learning(firal_handle* H, const void* X_pool, const int32_t* y_pool,
+                              int64_t n, const void* X_lab, const int32_t* y_lab, int64_t m,
+                              int32_t d, int32_t c, int32_t x_dtype, const firal_al_opts* opts,
+                              int32_t* selected_out, void* W_out, double* fhat_out) {
+  if (!H || !X_pool || !y_pool || !opts || !selected_out || !valid_shape(n, d, c) || n < 1 ||
+      m < 0 || (m > 0 && (!X_lab || !y_lab)) || x_dtype < 0 || x_dtype > 2)
+    return record(H, fail(FIRAL_ERR_ARG, "bad active_learning arguments"));
+  if (opts->rounds < 1 || opts->budget < 1 || (int64_t)opts->rounds * opts->budget >= n ||
+      !(opts->lr_gamma > 0) || !(opts->lambda >= 0))
+    return record(H, fail(FIRAL_ERR_ARG, "rounds, budget, lr_gamma or lambda out of range"));
+  if (opts->relax.precision < FIRAL_FP64 || opts->relax.precision > FIRAL_MIXED_BF16_FAST)
+    return record(H, fail(FIRAL_ERR_ARG, "unknown precision"));
+  return record(H, al_impl(H, X_pool, y_pool, n, X_lab, y_lab, m, d, c, x_dtype, *opts,
+                           selected_out, W_out, fhat_out));
 }

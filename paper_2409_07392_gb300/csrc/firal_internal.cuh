@@ -79,7 +79,7 @@ namespace firal {
 enum ProfId {
   PF_PREP = 0, PF_PROBES, PF_SYRK, PF_CHOL, PF_ALPHA, PF_DTERM, PF_COMBINE, PF_CG, PF_QUAD,
   PF_MD, PF_DOT, PF_ROUND, PF_SPLIT, PF_EXACT_BUILD, PF_EXACT_FACTOR, PF_EXACT_GEMM,
-  PF_EXACT_QUAD, PF_EXACT_SCORE, PF_COUNT
+  PF_EXACT_QUAD, PF_EXACT_SCORE, PF_LR, PF_COUNT
 };
 extern std::atomic<long long> g_launches;
 inline void count_launch(int n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
@@ -254,4 +254,18 @@ int32_t exact_relax(firal_problem* P, double budget, int T, double beta0, const 
 int32_t exact_round(firal_problem* P, const void* zd, int b, double eta, int exclude,
                     int32_t* sel, double* r_host, double* nu_host, int* evals);
 void exact_release(firal_problem* P);
+int32_t dense_gemm(bool dbl, cudaStream_t st, bool ta, bool tb, int M, int N, int K,
+                   double alpha, const void* A, int64_t lda, const void* B, int64_t ldb,
+                   double beta, void* C, int64_t ldc);
+// ---- k_al.cu (classifier refit and gathers of the active-learning loop)
+int32_t lr_probs(bool dbl, const void* X, const void* W, int64_t rows, int d, int c, void* h,
+                 cudaStream_t st);
+int32_t lr_grad(bool dbl, const void* X, const int32_t* y, const void* h, const void* W,
+                int64_t m, int d, int c, double gamma, void* R, void* g, cudaStream_t st);
+int32_t lr_nll(bool dbl, const void* h, const int32_t* y, int64_t m, int c, double* part,
+               double* out, cudaStream_t st);
+int32_t axpby(bool dbl, void* out, double a, const void* X, double b, const void* Y, int64_t n,
+              cudaStream_t st);
+int32_t gather_rows(bool dbl, bool labels, const void* src, const int32_t* idx, int64_t rows,
+                    int cols, void* dst, cudaStream_t st);
 }  // namespace firal

@@ -1160,6 +1160,16 @@ int32_t round_t(firal_problem* P, const T* zd, int b, double eta, int exclude, i
 
 }  // namespace
 
+int32_t dense_gemm(bool dbl, cudaStream_t st, bool ta, bool tb, int M, int N, int K,
+                   double alpha, const void* A, int64_t lda, const void* B, int64_t ldb,
+                   double beta, void* C, int64_t ldc) {
+  if (dbl)
+    return gemm<double>(st, ta, tb, M, N, K, alpha, (const double*)A, lda, (const double*)B, ldb,
+                        beta, (double*)C, ldc);
+  return gemm<float>(st, ta, tb, M, N, K, alpha, (const float*)A, lda, (const float*)B, ldb,
+                     beta, (float*)C, ldc);
+}
+
 int32_t exact_objective(firal_problem* P, const void* z, double* f_host, void* g) {
   if (P->dbl) return objective_t<double>(P, (const double*)z, f_host, (double*)g);
   return objective_t<float>(P, (const float*)z, f_host, (float*)g);

@@ -59,6 +59,9 @@ def test_struct_layouts_match_header(tmp_path):
         "offsetof(firal_relax_opts, md_tol)": L.FiralRelaxOpts.md_tol.offset,
         "sizeof(firal_step_stats)": ctypes.sizeof(L.FiralStepStats),
         "sizeof(firal_round_opts)": ctypes.sizeof(L.FiralRoundOpts),
+        "sizeof(firal_al_opts)": ctypes.sizeof(L.FiralAlOpts),
+        "offsetof(firal_al_opts, relax)": L.FiralAlOpts.relax.offset,
+        "offsetof(firal_al_opts, eta)": L.FiralAlOpts.eta.offset,
     }
     src = tmp_path / "layout.c"
     body = "".join(f'  printf("%zu\\n", (size_t)({k}));\n' for k in checks)
