@@ -268,10 +268,20 @@ constexpr int XB3(int dp) { return (dp / 64) * A_BYTES; }
 constexpr int SMEM3(int dp) {
   return NST3(dp) * 2 * C3_BYTES + 2 * XB3(dp) + 2 * H3_BYTES + 1024 + 256;
 }
+// MODE 4 = MODE 3 in class-chunk-major order: the 16 probes of one 64-class chunk run back to
+// back on the same h tile (loaded once per chunk instead of once per probe); the per-probe
+// running sums sum h a b, sum h a, sum h b of each row live in shared memory (s <= 16), paid
+// for with one coefficient stage less
+constexpr int S4MAX = 16;
+constexpr int NST4(int dp) { return dp <= 64 ? 3 : 2; }
+constexpr int PSUM4 = 3 * S4MAX * 128 * 4;
+constexpr int SMEM4(int dp) {
+  return NST4(dp) * 2 * C3_BYTES + 2 * XB3(dp) + 2 * H3_BYTES + 1024 + 256 + PSUM4;
+}
 }  // namespace alpha_cfg
 
 struct TcCtl {   // < 256 bytes
-  uint64_t full[4], empty[4], yfull[4], tfull[2], tempty[2], drain, pempty, hfull[2], hempty[2],
+  uint64_t full[4], empty[4], yfull[4], tfull[4], tempty[4], drain, pempty, hfull[2], hempty[2],
       xfull[2], xempty[2];
   uint32_t tmem_base;
   int abort_w;
@@ -298,12 +308,18 @@ __global__ void __launch_bounds__(256, 1)
   using namespace alpha_cfg;
   // MODE 3 stages hold the x tile and two 128-row coefficient tiles (hi and lo), followed by
   // a double buffer of f32 h tiles
-  constexpr int NST = MODE == 3 ? NST3(DP) : HLO ? STAGES_H : STAGES;
-  constexpr int SB = MODE == 3 ? 2 * C3_BYTES : STAGE_BYTES + (HLO ? A_BYTES : 0);
+  constexpr bool Q3 = MODE == 3 || MODE == 4;   // feature-contracted quadratic forms
+  constexpr bool KCM = MODE == 4;                // ... in class-chunk-major tile order
+  constexpr int NST = KCM ? NST4(DP) : MODE == 3 ? NST3(DP) : HLO ? STAGES_H : STAGES;
+  constexpr int SB = Q3 ? 2 * C3_BYTES : STAGE_BYTES + (HLO ? A_BYTES : 0);
   constexpr int OFF_B = (HLO ? 2 : 1) * A_BYTES;
   constexpr int HBUF = NST * SB;                        // MODE 3 h buffers
-  constexpr int XBUF = HBUF + (MODE == 3 ? 2 * H3_BYTES : 0);   // MODE 3 resident x tiles
-  constexpr int CTL_OFF = XBUF + (MODE == 3 ? 2 * XB3(DP) : 0);
+  constexpr int XBUF = HBUF + (Q3 ? 2 * H3_BYTES : 0);   // MODE 3/4 resident x tiles
+  constexpr int CTL_OFF = XBUF + (Q3 ? 2 * XB3(DP) : 0);
+  // TMEM accumulators: four of 128 columns for the quadratic forms (the MMAs run up to three
+  // tiles ahead of the epilogue), two of 256 columns otherwise
+  constexpr int NACC = Q3 ? 4 : 2;
+  constexpr uint32_t ACC_COLS = Q3 ? 128 : BN;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   TcCtl* ctl = (TcCtl*)(sm + CTL_OFF);
@@ -318,9 +334,11 @@ __global__ void __launch_bounds__(256, 1)
       mbar_init(&ctl->full[i], 1);
       mbar_init(&ctl->empty[i], 1);
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < 4; ++i) {
       mbar_init(&ctl->tfull[i], 1);
       mbar_init(&ctl->tempty[i], 4);
+    }
+    for (int i = 0; i < 2; ++i) {
       mbar_init(&ctl->hfull[i], 1);
       mbar_init(&ctl->hempty[i], 4);
       mbar_init(&ctl->xfull[i], 1);
@@ -342,8 +360,17 @@ __global__ void __launch_bounds__(256, 1)
   const int ntiles = n_mt * n_nt;
   // tile sequence of this CTA: MODE 3 takes every N tile of one point tile in a row (its
   // epilogue accumulates a row over all of them); the other modes stride over all tiles
+  // MODE 4: the chunk and probe order of each CTA is rotated by its index, so the CTAs (which
+  // run through their point tiles in step) read different coefficient tiles at any moment
+  // instead of all hitting the same lines; returns the chunk and probe that iteration nt of a
+  // point tile addresses
+  const int nkc4 = KCM ? n_nt / s : 1;
+  const int rot_k = KCM ? (int)(blockIdx.x % nkc4) : 0;
+  const int rot_j = KCM ? (int)((blockIdx.x / nkc4) % s) : 0;
+  auto chunk_of = [&](int nt) { return (nt / s + rot_k) % nkc4; };
+  auto probe_of = [&](int nt) { return (nt % s + rot_j) % s; };
   auto tile_at = [&](int it, int& mt, int& nt) -> bool {
-    if (MODE == 3) {
+    if (Q3) {
       mt = blockIdx.x + (it / n_nt) * gridDim.x;
       nt = it % n_nt;
       return mt < n_mt;
@@ -358,7 +385,7 @@ __global__ void __launch_bounds__(256, 1)
     // ---------------- TMA producer
     tma_prefetch(&mapH);
     tma_prefetch(&mapP);
-    if (HLO || MODE == 3) tma_prefetch(&mapHL);
+    if (HLO || Q3) tma_prefetch(&mapHL);
     int stage = 0;
     uint32_t phase = 0;
     int xcount = 0;   // MODE 3: point tiles whose x rows were loaded
@@ -366,7 +393,7 @@ __global__ void __launch_bounds__(256, 1)
     for (int it = 0; tile_at(it, mt, nt) && !*abort_w; ++it) {
       // pooled problems: only the class blocks of the pools in this point tile are non-zero
       const int kb_lo = krange ? krange[mt].x : 0, kb_hi = krange ? krange[mt].y : kblocks;
-      if (MODE == 3 && nt == 0) {
+      if (Q3 && nt == 0) {
         // the point tile's x rows, resident for all its N tiles
         const int xb = xcount & 1;
         if (!mbar_wait(&ctl->xempty[xb], ((xcount >> 1) & 1) ^ 1, abort_w)) {
@@ -379,14 +406,16 @@ __global__ void __launch_bounds__(256, 1)
           tma_load_2d(xbuf + kb * A_BYTES, &mapH, &ctl->xfull[xb], kb * BK, mt * BM);
         ++xcount;
       }
-      if (MODE == 3) {
-        // the f32 h tile of (point tile, 64-class chunk) for the epilogue
-        const int hb = it & 1;
-        if (!mbar_wait(&ctl->hempty[hb], ((it >> 1) & 1) ^ 1, abort_w)) {
+      if (MODE == 3 || (KCM && nt % s == 0)) {
+        // the f32 h tile of (point tile, 64-class chunk) for the epilogue (MODE 4: once per
+        // chunk, shared by its s probes)
+        const int hi = KCM ? it / s : it;
+        const int hb = hi & 1;
+        if (!mbar_wait(&ctl->hempty[hb], ((hi >> 1) & 1) ^ 1, abort_w)) {
           raise_abort(ctl, err, 5);
           break;
         }
-        const int kc = nt % (n_nt / s);
+        const int kc = KCM ? chunk_of(nt) : nt % (n_nt / s);
         unsigned char* hbuf = sm + HBUF + hb * H3_BYTES;
         mbar_expect_tx(&ctl->hfull[hb], H3_BYTES);
         tma_load_2d(hbuf, &mapHL, &ctl->hfull[hb], kc * 64, mt * BM);
@@ -399,9 +428,12 @@ __global__ void __launch_bounds__(256, 1)
         }
         unsigned char* st = sm + stage * SB;
         mbar_expect_tx(&ctl->full[stage], SB);
-        if (MODE == 3) {
-          tma_load_2d(st, &mapP, &ctl->full[stage], kb * BK, (2 * nt) * 128);
-          tma_load_2d(st + C3_BYTES, &mapP, &ctl->full[stage], kb * BK, (2 * nt + 1) * 128);
+        if (Q3) {
+          // coefficient tiles of (probe j, chunk kc) sit at row block (j nkc + kc) 2 + hl
+          const int nkc3 = n_nt / s;
+          const int ntc = KCM ? probe_of(nt) * nkc3 + chunk_of(nt) : nt;
+          tma_load_2d(st, &mapP, &ctl->full[stage], kb * BK, (2 * ntc) * 128);
+          tma_load_2d(st + C3_BYTES, &mapP, &ctl->full[stage], kb * BK, (2 * ntc + 1) * 128);
         } else {
           tma_load_2d(st, &mapH, &ctl->full[stage], kb * BK, mt * BM);
           if (HLO) tma_load_2d(st + A_BYTES, &mapHL, &ctl->full[stage], kb * BK, mt * BM);
@@ -423,7 +455,7 @@ __global__ void __launch_bounds__(256, 1)
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
-    constexpr uint32_t idesc = idesc_bf16_f32(BM, MODE == 3 ? 128 : BN);
+    constexpr uint32_t idesc = idesc_bf16_f32(BM, Q3 ? 128 : BN);
     int stage = 0;
     uint32_t phase = 0;
     int acc = 0;
@@ -431,7 +463,7 @@ __global__ void __launch_bounds__(256, 1)
     int mt, nt;
     int xcount = 0;
     for (int it = 0; tile_at(it, mt, nt) && !*abort_w; ++it) {
-      if (MODE == 3 && nt == 0) {
+      if (Q3 && nt == 0) {
         if (!mbar_wait(&ctl->xfull[xcount & 1], (xcount >> 1) & 1, abort_w)) {
           raise_abort(ctl, err, 7);
           break;
@@ -443,7 +475,7 @@ __global__ void __launch_bounds__(256, 1)
         break;
       }
       tc_fence_after();
-      const uint32_t d = tmem + acc * BN;
+      const uint32_t d = tmem + acc * ACC_COLS;
       bool ok = true;
       const int kb_lo = krange ? krange[mt].x : 0, kb_hi = krange ? krange[mt].y : kblocks;
       for (int kb = kb_lo; kb < kb_hi; ++kb) {
@@ -453,15 +485,15 @@ __global__ void __launch_bounds__(256, 1)
           break;
         }
         tc_fence_after();
-        const uint32_t a0 = MODE == 3
+        const uint32_t a0 = Q3
                                 ? smem_u32(sm + XBUF + ((xcount - 1) & 1) * XB3(DP) + kb * A_BYTES)
                                 : smem_u32(sm + stage * SB);
-        const uint32_t b0 = MODE == 3 ? smem_u32(sm + stage * SB) : a0 + OFF_B;
+        const uint32_t b0 = Q3 ? smem_u32(sm + stage * SB) : a0 + OFF_B;
 #pragma unroll
         for (int k = 0; k < BK / 16; ++k) {
           umma_bf16(d, sdesc_sw128(a0 + k * 32), sdesc_sw128(b0 + k * 32), idesc,
                     (kb != kb_lo || k != 0) ? 1u : 0u);
-          if (MODE == 3)   // x (A_lo; B_lo) into the same columns: a and b to ~2^-16
+          if (Q3)   // x (A_lo; B_lo) into the same columns: a and b to ~2^-16
             umma_bf16(d, sdesc_sw128(a0 + k * 32), sdesc_sw128(b0 + C3_BYTES + k * 32), idesc, 1u);
           if (HLO) {
             const uint64_t al = sdesc_sw128(a0 + A_BYTES + k * 32);
@@ -486,9 +518,11 @@ __global__ void __launch_bounds__(256, 1)
       if (!ok) break;
       umma_commit(&ctl->tfull[acc]);
       // MODE 3: the resident x tile is free once the point tile's last MMAs complete
-      if (MODE == 3 && nt == n_nt - 1) umma_commit(&ctl->xempty[(xcount - 1) & 1]);
-      acc ^= 1;
-      if (acc == 0) acc_phase ^= 1;
+      if (Q3 && nt == n_nt - 1) umma_commit(&ctl->xempty[(xcount - 1) & 1]);
+      if (++acc == NACC) {
+        acc = 0;
+        acc_phase ^= 1;
+      }
     }
     // drain: the commit below fires once every MMA issued above has completed
     umma_commit(&ctl->drain);
@@ -501,24 +535,26 @@ __global__ void __launch_bounds__(256, 1)
     // MODE 3 running sums of the thread's row: over the classes of the current probe
     // (sum h a b, sum h a, sum h b) and over the probes (q)
     float sab = 0.0f, sa = 0.0f, sb = 0.0f, qacc = 0.0f;
-    const int nkc = MODE == 3 ? n_nt / s : 1;
+    const int nkc = Q3 ? n_nt / s : 1;
+    float* psum = (float*)(sm + CTL_OFF + 256);   // MODE 4: [3][S4MAX][128] per-probe sums
     int mt, nt;
     for (int it = 0; tile_at(it, mt, nt) && !*abort_w; ++it) {
       const int64_t row = (int64_t)mt * BM + q * 32 + lane;
-      if (MODE == 3) {
+      if (Q3) {
         // per-point quadratic forms (eq. 11) from a = x.A_j[:,k], b = x.B_j[:,k] (K = d), the
         // hi and lo coefficient products summed in TMEM; 64 classes per tile, columns
         // [a (64) | b (64)]; term 1 = sum_k h a b, term 2 = (sum_k h a)(sum_k h b) with the
         // exact f32 h, staged by TMA in 128-byte-swizzled boxes of 32 classes
-        const int kc = nt % nkc;
-        const int hb = it & 1;
-        if (!mbar_wait(&ctl->hfull[hb], (it >> 1) & 1, abort_w) ||
+        const int kc = KCM ? nt / s : nt % nkc;
+        const int hi = KCM ? it / s : it;
+        const int hb = hi & 1;
+        if (!mbar_wait(&ctl->hfull[hb], (hi >> 1) & 1, abort_w) ||
             !mbar_wait(&ctl->tfull[acc], acc_phase, abort_w)) {
           raise_abort(ctl, err, 4);
           break;
         }
         tc_fence_after();
-        const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + acc * BN;
+        const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + acc * ACC_COLS;
         const unsigned char* hbuf = sm + HBUF + hb * H3_BYTES;
         const int r = q * 32 + lane;
 #pragma unroll 1
@@ -537,24 +573,49 @@ __global__ void __launch_bounds__(256, 1)
             hv[4 * ch + 3] = h4.w;
           }
           tmem_wait_ld();
+          // four partial sums per quantity: short dependency chains
+          float pab[4] = {0.0f, 0.0f, 0.0f, 0.0f}, pa[4] = {0.0f, 0.0f, 0.0f, 0.0f},
+                pb[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
           for (int t = 0; t < 32; ++t) {
             const float h = hv[t], av = __uint_as_float(ra[t]), bv = __uint_as_float(rb[t]);
             const float ha = h * av;
-            sab = fmaf(ha, bv, sab);
-            sa += ha;
-            sb = fmaf(h, bv, sb);
+            pab[t & 3] = fmaf(ha, bv, pab[t & 3]);
+            pa[t & 3] += ha;
+            pb[t & 3] = fmaf(h, bv, pb[t & 3]);
           }
+          sab += (pab[0] + pab[1]) + (pab[2] + pab[3]);
+          sa += (pa[0] + pa[1]) + (pa[2] + pa[3]);
+          sb += (pb[0] + pb[1]) + (pb[2] + pb[3]);
         }
         tc_fence_before();
         __syncwarp();
         if (lane == 0) {
           mbar_arrive(&ctl->tempty[acc]);
-          mbar_arrive(&ctl->hempty[hb]);
+          if (!KCM || nt % s == s - 1) mbar_arrive(&ctl->hempty[hb]);
         }
-        acc ^= 1;
-        if (acc == 0) acc_phase ^= 1;
-        if (kc == nkc - 1) {
+        if (++acc == NACC) {
+          acc = 0;
+          acc_phase ^= 1;
+        }
+        if (KCM) {
+          // probe j's sums over the chunks so far: kept per row in shared memory
+          const int j = probe_of(nt);
+          float* ps = psum + j * 128 + r;
+          if (kc > 0) {
+            sab += ps[0];
+            sa += ps[S4MAX * 128];
+            sb += ps[2 * S4MAX * 128];
+          }
+          if (kc == nkc - 1) {
+            qacc += sab - sa * sb;
+          } else {
+            ps[0] = sab;
+            ps[S4MAX * 128] = sa;
+            ps[2 * S4MAX * 128] = sb;
+          }
+          sab = sa = sb = 0.0f;
+        } else if (kc == nkc - 1) {
           qacc += sab - sa * sb;
           sab = sa = sb = 0.0f;
         }
@@ -1988,12 +2049,19 @@ static int32_t tc_quad_t(firal_problem* P, const float* A, const float* B, int s
                                                          P->vmean.as<float>(), s, c, d, DP, D,
                                                          nkc, P->pt);
     FIRAL_CUDA_TRY(cudaGetLastError());
+    // s <= 16: class-chunk-major order (MODE 4), each h tile loaded once per chunk
+    const bool kcm = s <= S4MAX;
     static bool attr3[4] = {false, false, false, false};
-    const int a3 = DP == 64 ? 2 : 3;
+    const int a3 = (DP == 64 ? 0 : 2) + (kcm ? 1 : 0);
     if (!attr3[a3]) {
-      FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tc_alpha<DP, 3, 2, 0>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          SMEM3(DP)));
+      if (kcm)
+        FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tc_alpha<DP, 4, 2, 0>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            SMEM4(DP)));
+      else
+        FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tc_alpha<DP, 3, 2, 0>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            SMEM3(DP)));
       attr3[a3] = true;
     }
     CUtensorMap mX, mC, mHf;
@@ -2001,9 +2069,14 @@ static int32_t tc_quad_t(firal_problem* P, const float* A, const float* B, int s
     FIRAL_TRY(make_map(&mC, P->gq_m.p, crow, DP, 128, BK, true));
     FIRAL_TRY(make_map_f32(&mHf, P->Ha.p, P->N, c, BM));
     const int n_mt = (int)(Np / BM), n_nt = s * nkc;
-    k_tc_alpha<DP, 3, 2, 0><<<std::min(n_mt, sms), 256, SMEM3(DP), st>>>(
-        mX, mC, mHf, P->Xb.as<bf16>(), nullptr, nullptr, g, P->N, Np, s, DP / BK, n_mt, n_nt, 0,
-        d, tc_error_word(P), nullptr, P->Ha.as<float>(), c, P->m, (float)(scale / s));
+    if (kcm)
+      k_tc_alpha<DP, 4, 2, 0><<<std::min(n_mt, sms), 256, SMEM4(DP), st>>>(
+          mX, mC, mHf, P->Xb.as<bf16>(), nullptr, nullptr, g, P->N, Np, s, DP / BK, n_mt, n_nt,
+          0, d, tc_error_word(P), nullptr, P->Ha.as<float>(), c, P->m, (float)(scale / s));
+    else
+      k_tc_alpha<DP, 3, 2, 0><<<std::min(n_mt, sms), 256, SMEM3(DP), st>>>(
+          mX, mC, mHf, P->Xb.as<bf16>(), nullptr, nullptr, g, P->N, Np, s, DP / BK, n_mt, n_nt,
+          0, d, tc_error_word(P), nullptr, P->Ha.as<float>(), c, P->m, (float)(scale / s));
     FIRAL_CUDA_TRY(cudaGetLastError());
     return FIRAL_OK;
   }
