@@ -2025,7 +2025,6 @@ static int32_t tc_quad_t(firal_problem* P, const float* A, const float* B, int s
   const int cp = P->cp, c = P->c, d = P->d;
   const int64_t D = P->D;
   const int sms = P->sms;
-  const int mthreads = (d + 31) / 32 * 32;
   // probe block [A; B] (2s columns) and its class means
   FIRAL_TRY(P->gq_ab.ensure((size_t)2 * s * D * sizeof(float)));
   float* AB = P->gq_ab.as<float>();
