@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-exact", action="store_true")
     ap.add_argument("--no-al", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--round-selections", type=int, default=20)
     return ap.parse_args()
 
@@ -455,9 +456,18 @@ def batched_measure(args, H, K=5):
         return time.perf_counter() - t0
 
     run(2)                                   # warm-up (module loading, attributes)
+    tuned = None
+    if not args.no_autotune:
+        from paper_2409_07392_gb300 import autotune
+
+        def one_iter_ms():
+            a = run(2)
+            return 1000.0 * (run(4) - a) / 2
+        tuned = autotune.tune_handle(H, one_iter_ms)
     t1 = run(2)
     tk = run(2 + K)
     per = (tk - t1) / K
+    H.set_default_tuning(0, 0, 0)
     applies = 2 * cg + 1
     pk, _ = peaks()
     return {"workload": f"batched_uneven: 64 pools, {npts} points in all, s={s}, "
@@ -466,6 +476,7 @@ def batched_measure(args, H, K=5):
             "hbm_frac_of_measured": applies * bytes_apply / per / 1e9 / pk["hbm_gbs"],
             "tensor_frac_of_measured": applies * flops_apply / per / 1e12 /
             pk["bf16_tflops_sustained"],
+            "tuning": tuned,
             "note": "fractions on algorithmic Sigma-apply work only (bytes n(2d+4c+4) per apply)"}
 
 
@@ -518,6 +529,12 @@ def run_ours(args):
     X, h, Xo, ho = (t.cuda(non_blocking=True) for t in (Xh, hh, Xoh, hoh))
     H = api.Handle()
     prob = api.Problem(H, X, h, Xo, ho, p.lam, precision=args.precision)
+    # launch tuning: the autotuner times split-count candidates on MD iterations (outside the
+    # timed region) and leaves the fastest set on the problem
+    tuning = None
+    if args.precision.startswith("mixed") and not args.no_autotune:
+        from paper_2409_07392_gb300 import autotune
+        tuning = autotune.tune_problem(prob, s, cg_iters=args.cg_iters, budget=b, reps=2)
     z = torch.full((n,), b / n, dtype=prob.vdt, device="cuda")
     opts = prob.relax_opts(s=s, T=args.warmup + args.steps, fixed_iters=args.cg_iters, seed=1)
     for t in range(args.warmup):
@@ -589,7 +606,12 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": describe(cfg, args), "precision": args.precision,
                        "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "inputs larger than L2 (h alone is %.1f GB)" % (p.h.nbytes / 1e9)},
+                       "l2": "inputs larger than L2 (h alone is %.1f GB)" % (p.h.nbytes / 1e9),
+                       "tuning": ({k: tuning[k] for k in ("dterm_splits", "bsum_splits",
+                                                          "sm_budget", "ms", "default_ms",
+                                                          "candidates")}
+                                  if tuning else None),
+                       "tuning_used": prob.get_tuning()},
             "roofline": roof, "gpu_launches": int(launches), "clocks": clk,
             "kernels": kernels,
             "hessian_apply": {"tflops_algorithmic": apply_tflops,

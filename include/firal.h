@@ -381,6 +381,31 @@ int32_t firal_exact_round(firal_problem* problem, const void* z_relaxed, int32_t
                           double eta, int32_t exclude_selected, int32_t* selected_out,
                           double* r_out, double* nu_out);
 
+/* ---------------------------------------------------------------- launch tuning */
+
+/* Launch parameters an autotuner chooses for the tensor-core path (FIRAL_MIXED_BF16*); 0 keeps
+ * the built-in shape rule for that field.  dterm_splits: point-range splits (the K extent of a
+ * CTA's tile) of the Hessian apply's second GEMM; a value below what the accumulation-chain
+ * bound of that GEMM needs is raised to it.  bsum_splits: point-range splits of the block sums
+ * of eq. 13.  sm_budget: CTAs the problem's grids spread over (capped at the SM count).  The
+ * FIRAL_SPLITS / FIRAL_SM_BUDGET environment overrides still take precedence. */
+typedef struct {
+  int32_t dterm_splits;
+  int32_t bsum_splits;
+  int32_t sm_budget;
+  int32_t reserved;       /* 0 */
+} firal_tuning;
+
+/* Set a prepared problem's tuning (applies to its next launches). */
+int32_t firal_problem_set_tuning(firal_problem* problem, const firal_tuning* tuning);
+
+/* The values the problem's last launches used (0 for a kernel not launched yet). */
+int32_t firal_problem_get_tuning(firal_problem* problem, firal_tuning* out);
+
+/* Default tuning of every problem created on the handle afterwards, including the pooled
+ * problems firal_batched_relax builds internally. */
+int32_t firal_set_default_tuning(firal_handle* handle, const firal_tuning* tuning);
+
 /* ---------------------------------------------------------------- active learning (Section 5) */
 
 /* Class probabilities of the multinomial logistic-regression classifier (eq. 1):

@@ -45,6 +45,11 @@ class FiralAlOpts(ctypes.Structure):
                 ("lr_tol", c_double), ("relax", FiralRelaxOpts), ("eta", c_double)]
 
 
+class FiralTuning(ctypes.Structure):
+    _fields_ = [("dterm_splits", c_int32), ("bsum_splits", c_int32), ("sm_budget", c_int32),
+                ("reserved", c_int32)]
+
+
 class FiralStepStats(ctypes.Structure):
     _fields_ = [("fhat", c_double), ("gmax", c_double), ("zmax", c_double),
                 ("cg_iters", c_int32 * 2), ("cg_relres", c_double * 2)]
@@ -116,6 +121,9 @@ SIGNATURES = [
                                     POINTER(c_double)]),
     ("firal_exact_round", c_int32, [c_void_p, c_void_p, c_int32, c_double, c_int32, c_void_p,
                                     POINTER(c_double), POINTER(c_double)]),
+    ("firal_problem_set_tuning", c_int32, [c_void_p, POINTER(FiralTuning)]),
+    ("firal_problem_get_tuning", c_int32, [c_void_p, POINTER(FiralTuning)]),
+    ("firal_set_default_tuning", c_int32, [c_void_p, POINTER(FiralTuning)]),
     ("firal_lr_probs", c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_int64, c_int32,
                                  c_int32, c_int32, c_void_p]),
     ("firal_lr_fit", c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_int64, c_int32, c_int32,

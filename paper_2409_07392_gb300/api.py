@@ -74,6 +74,11 @@ class Handle:
         except Exception:
             pass
 
+    def set_default_tuning(self, dterm_splits=0, bsum_splits=0, sm_budget=0):
+        """Tuning of every problem created on this handle afterwards (batched pools too)."""
+        t = L.FiralTuning(int(dterm_splits), int(bsum_splits), int(sm_budget), 0)
+        L.check(self.lib.firal_set_default_tuning(self._h, ctypes.byref(t)), self._h)
+
     # ---- standalone building blocks
     def block_eigvals(self, Sig: torch.Tensor, H: torch.Tensor) -> torch.Tensor:
         c, d, _ = Sig.shape
@@ -251,6 +256,18 @@ class Problem:
                                              ctypes.byref(o), _ptr(sel), crit,
                                              ctypes.byref(best)))
         return sel, list(crit), best.value
+
+    # ---- launch tuning (see autotune.py)
+    def set_tuning(self, dterm_splits=0, bsum_splits=0, sm_budget=0):
+        t = L.FiralTuning(int(dterm_splits), int(bsum_splits), int(sm_budget), 0)
+        self._chk(self.lib.firal_problem_set_tuning(self._p, ctypes.byref(t)))
+
+    def get_tuning(self):
+        """The split counts and SM budget the problem's last launches used."""
+        t = L.FiralTuning()
+        self._chk(self.lib.firal_problem_get_tuning(self._p, ctypes.byref(t)))
+        return dict(dterm_splits=t.dterm_splits, bsum_splits=t.bsum_splits,
+                    sm_budget=t.sm_budget)
 
     # ---- Exact-FIRAL (Algorithm 1) on dense d~ x d~ matrices
     def exact_objective(self, z, grad=True):

@@ -395,10 +395,13 @@ int32_t problem_create_impl(firal_handle* H, const firal_pool* pool, const firal
   P->c = pool->c;
   P->D = (int64_t)P->d * P->c;
   P->lambda = h0 ? h0->lambda : 0.0;
+  P->tune = H->tune;
   {
-    int b = forced_sm_budget() > 0 ? forced_sm_budget() : H->sm_budget;
+    int b = forced_sm_budget() > 0 ? forced_sm_budget()
+                                   : (P->tune.sm_budget > 0 ? P->tune.sm_budget : H->sm_budget);
     P->sms = (b > 0 && b < H->sm_count) ? b : H->sm_count;
   }
+  P->tune_used.sm_budget = P->sms;
   cudaStream_t st = H->stream;
   const size_t vs = vsize(P);
   auto cleanup = [&](int32_t code) {
@@ -1771,4 +1774,51 @@ int32_t firal_active_learning(firal_handle* H, const void* X_pool, const int32_t
     return record(H, fail(FIRAL_ERR_ARG, "unknown precision"));
   return record(H, al_impl(H, X_pool, y_pool, n, X_lab, y_lab, m, d, c, x_dtype, *opts,
                            selected_out, W_out, fhat_out));
+}
+
+// ------------------------------------------------------------------------------------------
+// Launch tuning (set by the autotuner)
+// ------------------------------------------------------------------------------------------
+namespace {
+int32_t tuning_check(const firal_tuning* t) {
+  if (!t) return fail(FIRAL_ERR_ARG, "tuning must be non-null");
+  if (t->dterm_splits < 0 || t->bsum_splits < 0 || t->sm_budget < 0 || t->reserved != 0)
+    return fail(FIRAL_ERR_ARG, "tuning values must be >= 0 (reserved = 0)");
+  return FIRAL_OK;
+}
+}  // namespace
+
+int32_t firal_problem_set_tuning(firal_problem* P, const firal_tuning* t) {
+  firal_handle* H = P ? P->H : nullptr;
+  if (!P) return record(H, fail(FIRAL_ERR_ARG, "problem must be non-null"));
+  int32_t rc = tuning_check(t);
+  if (rc != FIRAL_OK) return record(H, rc);
+  P->tune.dterm_splits = t->dterm_splits;
+  P->tune.bsum_splits = t->bsum_splits;
+  P->tune.sm_budget = t->sm_budget;
+  const int b = forced_sm_budget() > 0 ? forced_sm_budget()
+                                       : (t->sm_budget > 0 ? t->sm_budget : H->sm_budget);
+  P->sms = (b > 0 && b < H->sm_count) ? b : H->sm_count;
+  P->tune_used.sm_budget = P->sms;
+  return FIRAL_OK;
+}
+
+int32_t firal_problem_get_tuning(firal_problem* P, firal_tuning* out) {
+  firal_handle* H = P ? P->H : nullptr;
+  if (!P || !out) return record(H, fail(FIRAL_ERR_ARG, "problem and out must be non-null"));
+  out->dterm_splits = P->tune_used.dterm_splits;
+  out->bsum_splits = P->tune_used.bsum_splits;
+  out->sm_budget = P->tune_used.sm_budget;
+  out->reserved = 0;
+  return FIRAL_OK;
+}
+
+int32_t firal_set_default_tuning(firal_handle* H, const firal_tuning* t) {
+  if (!H) return fail(FIRAL_ERR_ARG, "handle must be non-null");
+  int32_t rc = tuning_check(t);
+  if (rc != FIRAL_OK) return record(H, rc);
+  H->tune.dterm_splits = t->dterm_splits;
+  H->tune.bsum_splits = t->bsum_splits;
+  H->tune.sm_budget = t->sm_budget;
+  return FIRAL_OK;
 }

@@ -95,10 +95,20 @@ struct ProfScope {
 };
 }  // namespace firal
 
+namespace firal {
+// Launch tuning of a prepared problem (firal_tuning in firal.h; 0 = the built-in shape rule).
+struct Tuning {
+  int dterm_splits = 0;    // point-range splits of the Hessian apply's D-GEMM
+  int bsum_splits = 0;     // point-range splits of the block sums
+  int sm_budget = 0;       // CTAs the problem's grids spread over
+};
+}  // namespace firal
+
 struct firal_handle {
   int device = 0;
   int sm_count = 148;
   int sm_budget = 0;       // > 0: CTAs a problem created on this handle may spread over
+  firal::Tuning tune;      // default tuning of problems created on this handle
   cudaStream_t stream = nullptr;
   firal::DBuf flags;       // firal::DevFlags
   firal::DBuf scratch;     // small reductions
@@ -145,6 +155,8 @@ struct ExactWs {
 
 struct firal_problem {
   firal::ExactWs* ex = nullptr;   // Exact-FIRAL dense workspace (null until used)
+  firal::Tuning tune;             // requested launch tuning (0 = shape rule)
+  firal::Tuning tune_used;        // what the last launches used
   int sms = 0;            // SM budget for grids and split counts (<= H->sm_count)
   firal::PoolTab pt;      // pooled problems only (device tables below)
   firal::DBuf pool_tabs;  // cpool | coff | pdim (int32) for pt

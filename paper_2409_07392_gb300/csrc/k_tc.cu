@@ -1821,9 +1821,13 @@ static int32_t tc_apply_t(firal_problem* P, const float* w, const float* Sblk, c
       const int64_t up = (need + m - 1) / m * m;
       splits = (int)(up < 2 * need ? up : need);
     }
+    // a tuned split count (autotuner) may replace the rule, but never below the chain bound
+    if (P->tune.dterm_splits > 0)
+      splits = (int)std::min<int64_t>(std::max<int64_t>(P->tune.dterm_splits, need), kL);
     if (forced_splits() > 0) splits = (int)std::min<int64_t>(forced_splits(), kL);
     const int64_t kbps = (kL + splits - 1) / splits;
     splits = (int)((kL + kbps - 1) / kbps);
+    P->tune_used.dterm_splits = splits;
     FIRAL_TRY(P->Dpart.ensure((size_t)splits * P->c * sd * sizeof(float)));
     CUtensorMap mHT, mXT, mAT;
     const uint64_t cpb2 = (uint64_t)n_mt2 * d_cfg::MT * d_cfg::BM;
@@ -1897,9 +1901,11 @@ int32_t tc_syrk_blocks(firal_problem* P, const void* wv, double lamS, void* outS
     const int64_t up = (need + m - 1) / m * m;
     splits = (int)(up < 2 * need ? up : need);
   }
+  if (P->tune.bsum_splits > 0) splits = (int)std::min<int64_t>(P->tune.bsum_splits, kL);
   if (forced_splits() > 0) splits = (int)std::min<int64_t>(forced_splits(), kL);
   const int64_t kbps = (kL + splits - 1) / splits;
   splits = (int)((kL + kbps - 1) / kbps);
+  P->tune_used.bsum_splits = splits;
   const int64_t per = (int64_t)c * d * d;
   FIRAL_TRY(P->syrk_part.ensure((size_t)per * splits * 2 * sizeof(float)));
   float* pS = P->syrk_part.as<float>();

@@ -215,3 +215,33 @@ def test_round_full_pipeline_shapes_vs_oracle(api, handle, precision):
         break
     print(f"{precision} round d=128 c=100: {same} of {b} picks identical, "
           f"gaps {np.round(info['gap'], 4).tolist()}")
+
+
+def test_tuning_round_trip_chain_bound_and_numerics(api, handle, tmp_path):
+    """Per-problem launch tuning: the values used are reported, the D-GEMM split count is held
+    at the accumulation-chain bound, other split counts reorder sums only, and the autotuner
+    stores its pick in the cache."""
+    from paper_2409_07392_gb300 import autotune
+    p = make_problem(100_000, 64, 40, seed=31, x_dtype="bf16", h_dtype="float32", m_o=40)
+    prob = make(api, handle, p, "mixed_fast")
+    rng = np.random.default_rng(2)
+    V = dev(rng.standard_normal((8, 64 * 40)).astype(np.float32))
+    z = dev(rng.uniform(0.1, 1.0, p.n).astype(np.float32))
+    ref = prob.hessian_apply(V, z, op=0).cpu().numpy()
+    used = prob.get_tuning()
+    assert used["dterm_splits"] >= 4 and used["bsum_splits"] >= 1 and used["sm_budget"] > 0
+    prob.set_tuning(dterm_splits=1, bsum_splits=3)
+    got = prob.hessian_apply(V, z, op=0).cpu().numpy()
+    t = prob.get_tuning()
+    # 100,000 points = 1,563 K-steps: the chain bound (512 K-steps per split) needs 4 splits
+    assert t["dterm_splits"] == 4 and t["bsum_splits"] == 3
+    # other split counts only regroup the f32 partial sums (chains of <= 512 K-steps)
+    assert relerr(got, ref) < 2e-4
+    prob.set_tuning(dterm_splits=2 * used["dterm_splits"])
+    got2 = prob.hessian_apply(V, z, op=0).cpu().numpy()
+    assert relerr(got2, ref) < 2e-4
+    cache = autotune.TuneCache(str(tmp_path / "tune.json"))
+    rec = autotune.tune_problem(prob, 8, cg_iters=2, reps=1, cache=cache)
+    assert rec["ms"] <= rec["default_ms"] and rec["candidates"] >= 2
+    assert cache.get(autotune.shape_key("mixed_fast", p.n, 64, 40, 8)) is not None
+    prob.close()
