@@ -150,7 +150,8 @@ class ClockSampler:
 
 # ------------------------------------------------------------------------------ roofline
 def algorithmic_flops(kind, cfg, n_all, s):
-    """Algorithmic flops of one timed group of a kernel class."""
+    """Algorithmic flops of one timed group of a kernel class: 2 N c d s for each GEMM of the
+    Hessian apply, 2 N c d (d + 1) for the block sums, 4 n c d s for the gradient."""
     n, d, c = cfg["n"], cfg["d"], cfg["c"]
     if kind in ("apply_alpha", "apply_dterm"):
         return 2.0 * n_all * c * d * s

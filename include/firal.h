@@ -55,7 +55,7 @@ typedef enum {
   FIRAL_ERR_NONFINITE = -5,        /* NaN or Inf in the objective or gradient               */
   FIRAL_ERR_TIMEOUT = -6,          /* a bounded device-side wait gave up                      */
   FIRAL_ERR_NOMEM = -7,            /* workspace allocation failed                             */
-  FIRAL_ERR_UNSUPPORTED = -8       /* shape or precision outside what this build supports   */
+  FIRAL_ERR_UNSUPPORTED = -8       /* shape or precision the library does not support       */
 } firal_status;
 
 typedef enum {
@@ -166,7 +166,7 @@ int32_t firal_set_stream(firal_handle* handle, void* stream);
 /* Copy the last error detail of `handle` (NUL-terminated, truncated to len). */
 int32_t firal_last_error(firal_handle* handle, char* buf, size_t len);
 
-/* Bit-width and precision flags this build was compiled with: bit 0 = SIMT paths,
+/* Bit-width and precision flags the library was compiled with: bit 0 = SIMT paths,
  * bit 1 = tcgen05 (sm_103a) tensor-core path. */
 int32_t firal_build_info(void);
 

@@ -14,7 +14,7 @@ loop on synthetic labels (the Gaussian-mixture component of each point):
   backtracking;
 * ``active_learning`` -- the loop, with ``approx.relax`` and ``approx.round_select``.
 
-Readings (the paper does not state them; listed in the design doc): the classifier is refit by
+Readings (the paper does not state them): the classifier is refit by
 ridge-regularised maximum likelihood with its own ridge ``gamma`` (1.0 by default, the
 usual unit-strength penalty), warm-started from the previous round's ``W`` (zero at first);
 ``H_o`` keeps the problem's ridge ``lam``; the labelled set is the initial rows followed by

@@ -17,7 +17,7 @@ Each function restates one step of the paper in plain numpy:
 Layout: a vector of length ``d~ = d c`` is ``vec(V)`` of a d x c matrix, so its
 element ``k d + e`` is ``V[e, k]``.  A block of ``s`` vectors is a (d~, s) array.
 
-Readings where the paper is silent or loose (listed again in the design doc):
+Readings where the paper is silent or loose:
 full c-class softmax; ``H_o = sum_{X_o} H_i + lam I``; ``H_p`` is the pool
 average; z lives on the budget simplex; ``beta_t = beta0 / ||g_t||_inf``; CG
 starts from zero, stops a column when its true recursive residual satisfies

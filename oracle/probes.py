@@ -1,7 +1,7 @@
 """Rademacher probe vectors for the Hutchinson estimator (eq. 11, Algorithm 2).
 
 The paper draws ``s`` fresh Rademacher vectors of length ``d~ = d c`` every
-mirror-descent iteration but does not say how.  This build fixes a
+mirror-descent iteration but does not say how.  This package fixes a
 counter-based rule so the oracle and the GPU produce the same probes without
 sharing code:
 
