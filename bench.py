@@ -448,11 +448,12 @@ def batched_measure(args, H, K=5):
         flops_apply += 4.0 * n * c * d * s
         bytes_apply += n * (2 * d + 4 * c + 4) + 8.0 * d * c * s
     cg = args.cg_iters
+    bprec = args.precision if args.precision.startswith("mixed") else "mixed_fast"
 
     def run(T):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        api.batched_relax(dicts, s=s, T=T, fixed_iters=cg, seed=1, precision="mixed", handle=H)
+        api.batched_relax(dicts, s=s, T=T, fixed_iters=cg, seed=1, precision=bprec, handle=H)
         torch.cuda.synchronize()
         return time.perf_counter() - t0
 
@@ -472,7 +473,7 @@ def batched_measure(args, H, K=5):
     applies = 2 * cg + 1
     pk, _ = peaks()
     return {"workload": f"batched_uneven: 64 pools, {npts} points in all, s={s}, "
-                        f"cg_iters/solve={cg}",
+                        f"cg_iters/solve={cg}", "precision": bprec,
             "value": 1.0 / per, "unit": "batched MD iters/s", "ms_per_iteration": 1000 * per,
             "hbm_frac_of_measured": applies * bytes_apply / per / 1e9 / pk["hbm_gbs"],
             "tensor_frac_of_measured": applies * flops_apply / per / 1e12 /
