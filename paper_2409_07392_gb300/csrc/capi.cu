@@ -509,19 +509,44 @@ int32_t relax_step_impl(firal_problem* P, const firal_relax_opts* o, int32_t t, 
   return FIRAL_OK;
 }
 
-int32_t round_impl(firal_problem* P, const void* zr, int32_t b, const firal_round_opts* o,
-                   int32_t* sel, firal_round_stats* stats) {
-  if (!P || !zr || !sel) return fail(FIRAL_ERR_ARG, "problem, z and selected_out must be non-null");
-  if (b < 1 || b > P->n) return fail(FIRAL_ERR_ARG, "budget must be in [1, n]");
-  if (P->dbl && P->d > 90) return fail(FIRAL_ERR_UNSUPPORTED, "FP64 Round supports d <= 90");
+// The eta-independent part of Round (Algorithm 3 line 3): B(H_o), the Sigma_diamond blocks and
+// their Cholesky factors, shared by every eta of a sweep.
+struct RoundSetup {
+  DBuf Sig, L;
+  ~RoundSetup() {
+    Sig.release();
+    L.release();
+  }
+};
+
+int32_t round_setup(firal_problem* P, const void* zr, RoundSetup& rs) {
+  cudaStream_t st = P->H->stream;
+  const size_t blk = (size_t)P->c * P->d * P->d;
+  FIRAL_TRY(rs.Sig.ensure(blk * 8));
+  FIRAL_TRY(rs.L.ensure(blk * 8));
+  // B(H_o): weights 1 on labelled rows, 0 on the pool; Sigma_diamond: z on the pool (C-15)
+  FIRAL_TRY(fill_weights(P->dbl, P->zsave.p, P->m, 1.0, nullptr, 0.0, P->n, st));
+  FIRAL_TRY(syrk_blocks(P, P->zsave.p, 0.0, nullptr, P->lambda, P->HoBlk.as<double>()));
+  FIRAL_TRY(fill_weights(P->dbl, P->zsave.p, P->m, 1.0, zr, 0.0, P->n, st));
+  FIRAL_TRY(syrk_blocks(P, P->zsave.p, 0.0, nullptr, P->lambda, rs.Sig.as<double>()));
+  FIRAL_TRY(chol_inv(P->dbl, rs.Sig.as<double>(), P->c, P->d, nullptr, nullptr, rs.L.as<double>(),
+                     not_spd_flag(P->H), st));
+  return FIRAL_OK;
+}
+
+// One Round chain (Algorithm 3 lines 4-12) for one eta on a prepared set-up.
+int32_t round_chain(firal_problem* P, const RoundSetup& rs, int32_t b, const firal_round_opts* o,
+                    int32_t* sel, firal_round_stats* stats) {
   cudaStream_t st = P->H->stream;
   const int c = P->c, d = P->d;
   const int64_t D = P->D;
   const double eta = (o && o->eta > 0) ? o->eta : 8.0 * std::sqrt((double)D);
   const size_t blk = (size_t)c * d * d;
-  DBuf Sig, L, Bm, Binv, Hk, M1, M2, eig, nu, mask, pv, pi, score, Tg;
+  const double* Sig = rs.Sig.as<double>();
+  const double* L = rs.L.as<double>();
+  DBuf Bm, Binv, Hk, M1, M2, eig, nu, mask, pv, pi, score, Tg;
   auto rel = [&]() {
-    for (DBuf* bf : {&Sig, &L, &Bm, &Binv, &Hk, &M1, &M2, &eig, &nu, &mask, &pv, &pi, &score, &Tg})
+    for (DBuf* bf : {&Bm, &Binv, &Hk, &M1, &M2, &eig, &nu, &mask, &pv, &pi, &score, &Tg})
       bf->release();
   };
   const int np = (int)std::max<int64_t>((P->n + 127) / 128, P->sms);
@@ -534,8 +559,6 @@ int32_t round_impl(firal_problem* P, const void* zr, int32_t b, const firal_roun
       return rc;                   \
     }                              \
   } while (0)
-  TRYR(Sig.ensure(blk * 8));
-  TRYR(L.ensure(blk * 8));
   TRYR(Bm.ensure(blk * 8));
   TRYR(Binv.ensure(blk * 8));
   TRYR(Hk.ensure(blk * 8));
@@ -548,20 +571,13 @@ int32_t round_impl(firal_problem* P, const void* zr, int32_t b, const firal_roun
   TRYR(pi.ensure((size_t)np * 8));
   TRYR(score.ensure(8));
   TRYR(Tg.ensure(blk * 8));
-  // B(H_o): weights 1 on labelled rows, 0 on the pool; Sigma_diamond: z on the pool (C-15)
-  TRYR(fill_weights(P->dbl, P->zsave.p, P->m, 1.0, nullptr, 0.0, P->n, st));
-  TRYR(syrk_blocks(P, P->zsave.p, 0.0, nullptr, P->lambda, P->HoBlk.as<double>()));
-  TRYR(fill_weights(P->dbl, P->zsave.p, P->m, 1.0, zr, 0.0, P->n, st));
-  TRYR(syrk_blocks(P, P->zsave.p, 0.0, nullptr, P->lambda, Sig.as<double>()));
-  TRYR(chol_inv(P->dbl, Sig.as<double>(), c, d, nullptr, nullptr, L.as<double>(),
-                not_spd_flag(P->H), st));
   const int64_t tot = (int64_t)blk;
   // line 4: B_1 = sqrt(d~) Sigma + (eta/b) H_o
-  TRYR(lincomb(Bm.as<double>(), std::sqrt((double)D), Sig.as<double>(), eta / b,
-               P->HoBlk.as<double>(), 0.0, nullptr, tot, st));
+  TRYR(lincomb(Bm.as<double>(), std::sqrt((double)D), Sig, eta / b, P->HoBlk.as<double>(), 0.0,
+               nullptr, tot, st));
   TRYR(chol_inv(P->dbl, Bm.as<double>(), c, d, nullptr, Binv.as<double>(), nullptr,
                 not_spd_flag(P->H), st));
-  TRYR(round_m(P->dbl, Binv.as<double>(), Sig.as<double>(), c, d, M1.p, M2.p, Tg.as<double>(), st));
+  TRYR(round_m(P->dbl, Binv.as<double>(), Sig, c, d, M1.p, M2.p, Tg.as<double>(), st));
   FIRAL_CUDA_TRY(cudaMemsetAsync(Hk.p, 0, blk * 8, st));
   FIRAL_CUDA_TRY(cudaMemsetAsync(mask.p, 0, (size_t)P->n, st));
   for (int t = 0; t < b; ++t) {
@@ -578,15 +594,15 @@ int32_t round_impl(firal_problem* P, const void* zr, int32_t b, const firal_roun
     // line 8: H_k += B_k(H_o)/b + w x x^T
     TRYR(round_hupdate(P, Hk.as<double>(), P->HoBlk.as<double>(), 1.0 / b, sel, t));
     // line 9: eigenvalues of H~_k
-    TRYR(tilde_eigvals(L.as<double>(), Hk.as<double>(), c, d, eig.as<double>(), st));
+    TRYR(tilde_eigvals(L, Hk.as<double>(), c, d, eig.as<double>(), st));
     // line 10: nu
     TRYR(nu_bisect_dev(eig.as<double>(), (int64_t)c * d, eta, nu.as<double>(), st));
     // line 11: B = nu Sigma + eta H + (eta/b) H_o, inverted
-    TRYR(lincomb_nu(Bm.as<double>(), nu.as<double>(), Sig.as<double>(), eta, Hk.as<double>(),
-                    eta / b, P->HoBlk.as<double>(), tot, st));
+    TRYR(lincomb_nu(Bm.as<double>(), nu.as<double>(), Sig, eta, Hk.as<double>(), eta / b,
+                    P->HoBlk.as<double>(), tot, st));
     TRYR(chol_inv(P->dbl, Bm.as<double>(), c, d, nullptr, Binv.as<double>(), nullptr,
                   not_spd_flag(P->H), st));
-    TRYR(round_m(P->dbl, Binv.as<double>(), Sig.as<double>(), c, d, M1.p, M2.p, Tg.as<double>(), st));
+    TRYR(round_m(P->dbl, Binv.as<double>(), Sig, c, d, M1.p, M2.p, Tg.as<double>(), st));
   }
   if (stats) {
     double h[2];
@@ -599,6 +615,17 @@ int32_t round_impl(firal_problem* P, const void* zr, int32_t b, const firal_roun
   FIRAL_CUDA_TRY(cudaStreamSynchronize(st));
   rel();
 #undef TRYR
+  return FIRAL_OK;
+}
+
+int32_t round_impl(firal_problem* P, const void* zr, int32_t b, const firal_round_opts* o,
+                   int32_t* sel, firal_round_stats* stats) {
+  if (!P || !zr || !sel) return fail(FIRAL_ERR_ARG, "problem, z and selected_out must be non-null");
+  if (b < 1 || b > P->n) return fail(FIRAL_ERR_ARG, "budget must be in [1, n]");
+  if (P->dbl && P->d > 90) return fail(FIRAL_ERR_UNSUPPORTED, "FP64 Round supports d <= 90");
+  RoundSetup rs;
+  FIRAL_TRY(round_setup(P, zr, rs));
+  FIRAL_TRY(round_chain(P, rs, b, o, sel, stats));
   return read_flags(P->H);
 }
 
@@ -1020,10 +1047,15 @@ int32_t round_sweep_impl(firal_problem* P, const void* zr, int32_t b, const doub
   if (neta < 1 || neta > 64) return fail(FIRAL_ERR_ARG, "n_eta must be in [1, 64]");
   for (int e = 0; e < neta; ++e)
     if (!(etas[e] > 0)) return fail(FIRAL_ERR_ARG, "every eta must be > 0");
+  if (b < 1 || b > P->n) return fail(FIRAL_ERR_ARG, "budget must be in [1, n]");
+  if (P->dbl && P->d > 90) return fail(FIRAL_ERR_UNSUPPORTED, "FP64 Round supports d <= 90");
   firal_round_opts oe = o ? *o : firal_round_opts{0.0, 1, P->prec};
+  // the eta-independent set-up once, then one chain per eta
+  RoundSetup rs;
+  FIRAL_TRY(round_setup(P, zr, rs));
   for (int e = 0; e < neta; ++e) {
     oe.eta = etas[e];
-    FIRAL_TRY(round_impl(P, zr, b, &oe, sel + (size_t)e * b, nullptr));
+    FIRAL_TRY(round_chain(P, rs, b, &oe, sel + (size_t)e * b, nullptr));
     FIRAL_TRY(selected_min_eig(P, sel + (size_t)e * b, b, &crit[e]));
   }
   int bi = 0;
