@@ -381,6 +381,16 @@ int32_t firal_exact_round(firal_problem* problem, const void* z_relaxed, int32_t
                           double eta, int32_t exclude_selected, int32_t* selected_out,
                           double* r_out, double* nu_out);
 
+/* ---------------------------------------------------------------- device memory */
+
+/* Destroyed problems park their device buffers in a process-wide cache (bounded by the
+ * FIRAL_CACHE_BYTES environment variable, default 64 GiB; 0 disables it), from which later
+ * problems on the same device take buffers of a similar size instead of calling cudaMalloc.
+ * firal_cache_trim returns every parked buffer to the driver; firal_cache_bytes reports how
+ * many bytes are parked. */
+int32_t firal_cache_trim(void);
+int64_t firal_cache_bytes(void);
+
 /* ---------------------------------------------------------------- launch tuning */
 
 /* Launch parameters an autotuner chooses for the tensor-core path (FIRAL_MIXED_BF16*); 0 keeps

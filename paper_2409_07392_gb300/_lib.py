@@ -121,6 +121,8 @@ SIGNATURES = [
                                     POINTER(c_double)]),
     ("firal_exact_round", c_int32, [c_void_p, c_void_p, c_int32, c_double, c_int32, c_void_p,
                                     POINTER(c_double), POINTER(c_double)]),
+    ("firal_cache_trim", c_int32, []),
+    ("firal_cache_bytes", c_int64, []),
     ("firal_problem_set_tuning", c_int32, [c_void_p, POINTER(FiralTuning)]),
     ("firal_problem_get_tuning", c_int32, [c_void_p, POINTER(FiralTuning)]),
     ("firal_set_default_tuning", c_int32, [c_void_p, POINTER(FiralTuning)]),

@@ -101,6 +101,66 @@ ProfScope::~ProfScope() {
   if (P.pending.size() > 4096) P.drain();
 }
 
+// ---------------------------------------------------------------------------- block cache
+// Buffers of destroyed problems are parked here and handed to later allocations on the same
+// device instead of going back to the driver: freeing a large problem's buffers costs about
+// 20 ms, and a caller that builds one problem per call (firal_relax, firal_round) pays it
+// every time.  Only firal_problem_destroy parks, after synchronising the problem's stream, so
+// a parked block has no kernel in flight; every other release still calls cudaFree (which
+// synchronises the device).  Bounded by FIRAL_CACHE_BYTES (default 64 GiB, 0 disables);
+// firal_cache_trim returns every parked block.
+namespace {
+struct ParkedBlock {
+  void* p;
+  size_t bytes;
+  int dev;
+};
+struct BlockCache {
+  std::mutex mu;
+  std::vector<ParkedBlock> blocks;
+  size_t held = 0;
+  size_t cap = [] {
+    const char* e = std::getenv("FIRAL_CACHE_BYTES");
+    return e ? (size_t)std::strtoull(e, nullptr, 10) : ((size_t)64 << 30);
+  }();
+};
+BlockCache& block_cache() {
+  static BlockCache* c = new BlockCache();   // never destroyed: no CUDA calls at process exit
+  return *c;
+}
+// The smallest parked block of this device holding nbytes, if it is at most twice that size.
+void* cache_take(size_t nbytes, size_t* got) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  BlockCache& c = block_cache();
+  std::lock_guard<std::mutex> g(c.mu);
+  int best = -1;
+  for (int i = 0; i < (int)c.blocks.size(); ++i) {
+    const ParkedBlock& b = c.blocks[i];
+    if (b.dev == dev && b.bytes >= nbytes && b.bytes <= 2 * nbytes + (1u << 20) &&
+        (best < 0 || b.bytes < c.blocks[best].bytes))
+      best = i;
+  }
+  if (best < 0) return nullptr;
+  void* p = c.blocks[best].p;
+  *got = c.blocks[best].bytes;
+  c.held -= *got;
+  c.blocks.erase(c.blocks.begin() + best);
+  return p;
+}
+// Park a block whose last use has completed; false when the cache is full (caller frees).
+bool cache_park(void* p, size_t bytes) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  BlockCache& c = block_cache();
+  std::lock_guard<std::mutex> g(c.mu);
+  if (c.held + bytes > c.cap) return false;
+  c.blocks.push_back({p, bytes, dev});
+  c.held += bytes;
+  return true;
+}
+}  // namespace
+
 int32_t DBuf::ensure(size_t nbytes) {
   if (nbytes <= bytes && p) return FIRAL_OK;
   if (p) {
@@ -109,6 +169,12 @@ int32_t DBuf::ensure(size_t nbytes) {
     bytes = 0;
   }
   if (nbytes == 0) nbytes = 16;
+  size_t got = 0;
+  if (void* q = cache_take(nbytes, &got)) {
+    p = q;
+    bytes = got;
+    return FIRAL_OK;
+  }
   cudaError_t e = cudaMalloc(&p, nbytes);
   if (e != cudaSuccess) {
     p = nullptr;
@@ -121,6 +187,12 @@ int32_t DBuf::ensure(size_t nbytes) {
 
 void DBuf::release() {
   if (p) cudaFree(p);
+  p = nullptr;
+  bytes = 0;
+}
+
+void DBuf::park() {
+  if (p && !cache_park(p, bytes)) cudaFree(p);
   p = nullptr;
   bytes = 0;
 }
@@ -1183,14 +1255,18 @@ int32_t firal_problem_create(firal_handle* H, const firal_pool* pool, const fira
 
 int32_t firal_problem_destroy(firal_problem* P) {
   if (!P) return FIRAL_OK;
-  cudaStreamSynchronize(P->H->stream);
+  // every kernel of the problem ran on the handle's stream (graph replays join it before
+  // returning): after this synchronisation its buffers can be parked for reuse
+  const bool synced = cudaStreamSynchronize(P->H->stream) == cudaSuccess;
   exact_release(P);
   for (DBuf* b : {&P->Xa, &P->Ha, &P->HaT, &P->w_sig, &P->w_p, &P->S_p, &P->S_sig, &P->Pblk,
                   &P->Minv, &P->HoBlk, &P->walpha, &P->Dpart, &P->syrk_part, &P->cgX, &P->cgR,
                   &P->cgP, &P->cgQ, &P->cgZ, &P->cgcols, &P->cgpart1, &P->cgpart2, &P->V, &P->U,
                   &P->W, &P->HU, &P->g, &P->red, &P->zsave, &P->Xb, &P->Hb, &P->HbT, &P->Pb, &P->vmean, &P->qmean, &P->Aw, &P->Zp, &P->Hlo, &P->gq_ab,
-                  &P->gq_m, &P->gq_part, &P->rtab, &P->rM, &P->tdev})
-    b->release();
+                  &P->gq_m, &P->gq_part, &P->rtab, &P->rM, &P->tdev}) {
+    if (synced) b->park();
+    else b->release();
+  }
   delete P;
   return FIRAL_OK;
 }
@@ -1853,4 +1929,28 @@ int32_t firal_set_default_tuning(firal_handle* H, const firal_tuning* t) {
   H->tune.bsum_splits = t->bsum_splits;
   H->tune.sm_budget = t->sm_budget;
   return FIRAL_OK;
+}
+
+int32_t firal_cache_trim(void) {
+  BlockCache& c = block_cache();
+  std::vector<ParkedBlock> blocks;
+  {
+    std::lock_guard<std::mutex> g(c.mu);
+    blocks.swap(c.blocks);
+    c.held = 0;
+  }
+  int cur = 0;
+  cudaGetDevice(&cur);
+  for (const ParkedBlock& b : blocks) {
+    cudaSetDevice(b.dev);
+    cudaFree(b.p);
+  }
+  cudaSetDevice(cur);
+  return FIRAL_OK;
+}
+
+int64_t firal_cache_bytes(void) {
+  BlockCache& c = block_cache();
+  std::lock_guard<std::mutex> g(c.mu);
+  return (int64_t)c.held;
 }

@@ -50,7 +50,8 @@ struct DBuf {
   void* p = nullptr;
   size_t bytes = 0;
   int32_t ensure(size_t nbytes);   // grow (never shrink); contents not preserved
-  void release();
+  void release();                  // cudaFree
+  void park();                     // to the block cache (no kernel may still use the buffer)
   template <class T> T* as() const { return static_cast<T*>(p); }
 };
 
