@@ -78,3 +78,9 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert lib.firal_problem_destroy(None) == 0
     lib.firal_destroy.argtypes = [ctypes.c_void_p]
     assert lib.firal_destroy(None) == 0
+
+
+def test_block_cache_entry_points_without_gpu(lib):
+    lib.firal_cache_bytes.restype = ctypes.c_int64
+    assert lib.firal_cache_bytes() == 0
+    assert lib.firal_cache_trim() == 0
