@@ -488,12 +488,13 @@ int32_t problem_create_impl(firal_handle* H, const firal_pool* pool, const firal
   } while (0)
   TRYC(P->Xa.ensure((size_t)P->N * P->d * vs));
   TRYC(P->Ha.ensure((size_t)P->N * P->c * vs));
-  TRYC(P->HaT.ensure((size_t)P->N * P->c * vs));
   TRYC(copy_rows(P->dbl, P->Xa.p, h0 ? h0->Xo : nullptr, P->m, pool->X, P->n, P->d,
                  pool->x_dtype, st));
   TRYC(copy_rows(P->dbl, P->Ha.p, h0 ? h0->ho : nullptr, P->m, pool->h, P->n, P->c,
                  pool->h_dtype, st));
-  TRYC(transpose(P->dbl, P->HaT.p, P->Ha.p, P->N, P->c, st));
+  // class-major copy of h for the CUDA-core kernels; the tensor-core path reads its own bf16
+  // operands, prepared below, and makes this copy only if Round asks for it
+  if (!is_mixed(precision)) TRYC(class_major_h(P));
   TRYC(P->w_sig.ensure((size_t)P->N * vs));
   TRYC(P->w_p.ensure((size_t)P->N * vs));
   TRYC(P->zsave.ensure((size_t)P->N * vs));

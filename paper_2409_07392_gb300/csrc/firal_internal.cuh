@@ -209,6 +209,7 @@ namespace firal {
 int32_t copy_rows(bool dbl, void* dst, const void* a, int64_t ma, const void* b, int64_t nb,
                   int cols, int32_t src_dtype, cudaStream_t st);
 int32_t transpose(bool dbl, void* dst, const void* src, int64_t rows, int cols, cudaStream_t st);
+int32_t class_major_h(firal_problem* P);
 int32_t fill_weights(bool dbl, void* w, int64_t m, double lab_val, const void* z, double zconst,
                      int64_t n, cudaStream_t st);
 int32_t probes(bool dbl, void* V, uint64_t seed, int64_t t, int s, int64_t D, cudaStream_t st,

@@ -531,6 +531,7 @@ static int32_t round_scores_t(firal_problem* P, const void* M1, const void* M2,
 
 int32_t round_scores(firal_problem* P, const void* M1, const void* M2, const uint8_t* mask,
                      double eta, double* pv, int64_t* pi, int np) {
+  FIRAL_TRY(class_major_h(P));
   if (P->dbl) return round_scores_t<double>(P, M1, M2, mask, eta, pv, pi, np);
   return round_scores_t<float>(P, M1, M2, mask, eta, pv, pi, np);
 }

@@ -137,6 +137,17 @@ int32_t transpose(bool dbl, void* dst, const void* src, int64_t rows, int cols, 
   return FIRAL_OK;
 }
 
+// Class-major copy h^T (c x N) read by the CUDA-core kernels.  FP32 / FP64 problems make it
+// when they are created; a mixed-precision problem needs it only for the FP64-accumulated
+// block sums of Round and makes it on first use (never inside a stream capture: Round and the
+// block-sum entry points are not captured).
+int32_t class_major_h(firal_problem* P) {
+  if (P->HaT.p) return FIRAL_OK;
+  const size_t vs = P->dbl ? sizeof(double) : sizeof(float);
+  FIRAL_TRY(P->HaT.ensure((size_t)P->N * P->c * vs));
+  return transpose(P->dbl, P->HaT.p, P->Ha.p, P->N, P->c, P->H->stream);
+}
+
 // weights over all rows: [lab_val] * m, then z (or zconst) on the pool rows
 template <class T>
 __global__ void k_fill_w(T* w, int64_t m, T lab_val, const T* z, T zconst, int64_t n) {
@@ -389,6 +400,7 @@ int32_t syrk_reduce_f32(firal_problem* P, const float* partS, const float* partP
 
 int32_t syrk_blocks(firal_problem* P, const void* w, double lamS, void* outS, double lamP,
                     double* outP) {
+  FIRAL_TRY(class_major_h(P));
   if (P->dbl) return syrk_t<double>(P, (const double*)w, lamS, (double*)outS, lamP, outP);
   return syrk_t<float>(P, (const float*)w, lamS, (float*)outS, lamP, outP);
 }
@@ -629,6 +641,7 @@ int32_t combine_f32(firal_problem* P, const float* Sblk, const float* V, int spl
 
 int32_t hessian_apply_simt(firal_problem* P, const void* w, const void* Sblk, const void* V,
                            int s, void* out, double* pq) {
+  FIRAL_TRY(class_major_h(P));
   if (P->dbl)
     return apply_t<double>(P, (const double*)w, (const double*)Sblk, (const double*)V, s,
                            (double*)out, pq);
@@ -956,6 +969,7 @@ __global__ __launch_bounds__(128) void k_quad(const T* __restrict__ Xa, const T*
 
 int32_t quad_forms_simt(firal_problem* P, const void* A, const void* B, int s, double scale,
                         void* g) {
+  FIRAL_TRY(class_major_h(P));
   cudaStream_t st = P->H->stream;
   const int d = P->d, c = P->c;
   constexpr int KC = 16;

@@ -297,7 +297,7 @@ __device__ __forceinline__ void raise_abort(TcCtl* ctl, int32_t* err, int code) 
 // (MODE 2: the first 128 rows of the tile; MODE 1: the DP hi rows of each probe) into the
 // same accumulator columns, so the epilogue sees (H_hi + H_lo) B_hi + H_hi B_lo.
 template <int DP, int MODE, int NPART, int HLO = 0>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(MODE == 4 ? 384 : 256, 1)
     k_tc_alpha(const __grid_constant__ CUtensorMap mapH, const __grid_constant__ CUtensorMap mapP,
                const __grid_constant__ CUtensorMap mapHL, const bf16* __restrict__ Xb,
                const float* __restrict__ w, bf16* __restrict__ aT, float* __restrict__ out32,
@@ -325,6 +325,13 @@ __global__ void __launch_bounds__(256, 1)
   TcCtl* ctl = (TcCtl*)(sm + CTL_OFF);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int PPN = BN / (NPART * DP);   // probes per N tile
+  // MODE 4 tiles carry only 8 MMAs (K = 64, hi and lo), little next to the serial barrier,
+  // fence and commit latency of issuing them; two issuer threads (warps 1 and 3) take
+  // alternate tiles so that one's hand-offs overlap the other's MMAs.  The operand stages are
+  // shared by both, and a parity wait cannot tell a stage's next phase from the one after, so
+  // a token passes between the issuers (turn[i]: issuer i may wait for its next tile's stages)
+  // and every stage wait happens after the previous use of that stage was seen complete.
+  constexpr int NMMA = KCM ? 2 : 1;
   static_assert(MODE != 2 || NPART == 2, "the quadratic mode reads hi and lo halves");
   static_assert(!HLO || (MODE != 0 && NPART == 2), "h_lo is used by the gradient modes");
   // MODE 2: the thread's x row, transposed (column = thread) so reads are conflict-free
@@ -340,11 +347,13 @@ __global__ void __launch_bounds__(256, 1)
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&ctl->hfull[i], 1);
-      mbar_init(&ctl->hempty[i], 4);
+      mbar_init(&ctl->hempty[i], KCM ? 8 : 4);   // MODE 4: both epilogue groups release it
       mbar_init(&ctl->xfull[i], 1);
-      mbar_init(&ctl->xempty[i], 1);
+      mbar_init(&ctl->xempty[i], NMMA);          // MODE 4: both MMA issuers release it
     }
-    mbar_init(&ctl->drain, 1);
+    mbar_init(&ctl->drain, NMMA);
+    if (NMMA == 2)
+      for (int i = 0; i < 2; ++i) mbar_init(&ctl->yfull[i], 1);   // issuer tokens (turn)
     ctl->abort_w = 0;
     mbar_fence_init();
   }
@@ -364,21 +373,58 @@ __global__ void __launch_bounds__(256, 1)
   // run through their point tiles in step) read different coefficient tiles at any moment
   // instead of all hitting the same lines; returns the chunk and probe that iteration nt of a
   // point tile addresses
-  const int nkc4 = KCM ? n_nt / s : 1;
-  const int rot_k = KCM ? (int)(blockIdx.x % nkc4) : 0;
-  const int rot_j = KCM ? (int)((blockIdx.x / nkc4) % s) : 0;
-  auto chunk_of = [&](int nt) { return (nt / s + rot_k) % nkc4; };
-  auto probe_of = [&](int nt) { return (nt % s + rot_j) % s; };
-  auto tile_at = [&](int it, int& mt, int& nt) -> bool {
-    if (Q3) {
-      mt = blockIdx.x + (it / n_nt) * gridDim.x;
-      nt = it % n_nt;
-      return mt < n_mt;
-    }
-    const int tile = blockIdx.x + it * gridDim.x;
-    mt = tile / n_nt;
-    nt = tile % n_nt;
+  const int nkcq = Q3 ? n_nt / s : 1;   // 64-class chunks per probe
+  const int rot_k = KCM ? (int)(blockIdx.x % nkcq) : 0;
+  const int rot_j = KCM ? (int)((blockIdx.x / nkcq) % s) : 0;
+  // Tile cursor.  The quadratic-form modes keep the chunk, probe and h-buffer indices of the
+  // current tile incrementally: the producer and MMA roles are single threads whose per-tile
+  // work is a handful of instructions, and integer divisions by run-time values on every tile
+  // would dominate it.
+  //   MODE 4: nt = kr s + jr; chunk (kr + rot_k) mod nkc, probe (jr + rot_j) mod s, hi = it / s
+  //   MODE 3: nt = probe nkc + kr; chunk = kr, hi = it
+  struct Cur {
+    int it, mt, nt, jr, kr, chunk, probe, hi;
+  };
+  auto cur_set = [&](Cur& q) -> bool {   // other modes: (mt, nt) of q.it
+    if (Q3) return q.mt < n_mt;
+    const int tile = blockIdx.x + q.it * gridDim.x;
+    q.mt = tile / n_nt;
+    q.nt = tile % n_nt;
     return tile < ntiles;
+  };
+  auto cur_first = [&]() -> Cur {
+    Cur q{0, (int)blockIdx.x, 0, 0, 0, KCM ? rot_k : 0, KCM ? rot_j : 0, 0};
+    cur_set(q);
+    return q;
+  };
+  auto cur_next = [&](Cur& q) -> bool {
+    ++q.it;
+    if (!Q3) return cur_set(q);
+    ++q.nt;
+    if (KCM) {
+      if (++q.probe == s) q.probe = 0;
+      if (++q.jr == s) {
+        q.jr = 0;
+        q.probe = rot_j;
+        ++q.kr;
+        ++q.hi;
+        if (++q.chunk == nkcq) q.chunk = 0;
+      }
+    } else {
+      ++q.hi;
+      if (++q.kr == nkcq) {
+        q.kr = 0;
+        ++q.probe;
+      }
+      q.chunk = q.kr;
+    }
+    if (q.nt == n_nt) {
+      q.nt = q.jr = q.kr = 0;
+      q.chunk = KCM ? rot_k : 0;
+      q.probe = KCM ? rot_j : 0;
+      q.mt += gridDim.x;
+    }
+    return q.mt < n_mt;
   };
 
   if (warp == 0 && lane == 0) {
@@ -389,8 +435,9 @@ __global__ void __launch_bounds__(256, 1)
     int stage = 0;
     uint32_t phase = 0;
     int xcount = 0;   // MODE 3: point tiles whose x rows were loaded
-    int mt, nt;
-    for (int it = 0; tile_at(it, mt, nt) && !*abort_w; ++it) {
+    Cur cu = cur_first();
+    for (bool more = Q3 ? cu.mt < n_mt : cur_set(cu); more && !*abort_w; more = cur_next(cu)) {
+      const int mt = cu.mt, nt = cu.nt;
       // pooled problems: only the class blocks of the pools in this point tile are non-zero
       const int kb_lo = krange ? krange[mt].x : 0, kb_hi = krange ? krange[mt].y : kblocks;
       if (Q3 && nt == 0) {
@@ -406,16 +453,16 @@ __global__ void __launch_bounds__(256, 1)
           tma_load_2d(xbuf + kb * A_BYTES, &mapH, &ctl->xfull[xb], kb * BK, mt * BM);
         ++xcount;
       }
-      if (MODE == 3 || (KCM && nt % s == 0)) {
+      if (MODE == 3 || (KCM && cu.jr == 0)) {
         // the f32 h tile of (point tile, 64-class chunk) for the epilogue (MODE 4: once per
         // chunk, shared by its s probes)
-        const int hi = KCM ? it / s : it;
+        const int hi = cu.hi;
         const int hb = hi & 1;
         if (!mbar_wait(&ctl->hempty[hb], ((hi >> 1) & 1) ^ 1, abort_w)) {
           raise_abort(ctl, err, 5);
           break;
         }
-        const int kc = KCM ? chunk_of(nt) : nt % (n_nt / s);
+        const int kc = cu.chunk;
         unsigned char* hbuf = sm + HBUF + hb * H3_BYTES;
         mbar_expect_tx(&ctl->hfull[hb], H3_BYTES);
         tma_load_2d(hbuf, &mapHL, &ctl->hfull[hb], kc * 64, mt * BM);
@@ -430,8 +477,7 @@ __global__ void __launch_bounds__(256, 1)
         mbar_expect_tx(&ctl->full[stage], SB);
         if (Q3) {
           // coefficient tiles of (probe j, chunk kc) sit at row block (j nkc + kc) 2 + hl
-          const int nkc3 = n_nt / s;
-          const int ntc = KCM ? probe_of(nt) * nkc3 + chunk_of(nt) : nt;
+          const int ntc = KCM ? cu.probe * nkcq + cu.chunk : nt;
           tma_load_2d(st, &mapP, &ctl->full[stage], kb * BK, (2 * ntc) * 128);
           tma_load_2d(st + C3_BYTES, &mapP, &ctl->full[stage], kb * BK, (2 * ntc + 1) * 128);
         } else {
@@ -453,16 +499,21 @@ __global__ void __launch_bounds__(256, 1)
         phase ^= 1;
       }
     }
-  } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer
+  } else if ((warp == 1 || (NMMA == 2 && warp == 3)) && lane == 0) {
+    // ---------------- MMA issuer(s)
+    const int mi = warp == 3 ? 1 : 0;
+    uint64_t* turn = ctl->yfull;   // MODE 4 issuer tokens (the D-GEMM's y barriers, unused here)
+    int nturn = 0;                 // token waits done by this issuer
+    bool first_tile = true;
     constexpr uint32_t idesc = idesc_bf16_f32(BM, Q3 ? 128 : BN);
     int stage = 0;
     uint32_t phase = 0;
     int acc = 0;
     uint32_t acc_phase = 0;
-    int mt, nt;
     int xcount = 0;
-    for (int it = 0; tile_at(it, mt, nt) && !*abort_w; ++it) {
+    Cur cu = cur_first();
+    for (bool more = Q3 ? cu.mt < n_mt : cur_set(cu); more && !*abort_w; more = cur_next(cu)) {
+      const int mt = cu.mt, nt = cu.nt;
       if (Q3 && nt == 0) {
         if (!mbar_wait(&ctl->xfull[xcount & 1], (xcount >> 1) & 1, abort_w)) {
           raise_abort(ctl, err, 7);
@@ -470,20 +521,44 @@ __global__ void __launch_bounds__(256, 1)
         }
         ++xcount;
       }
+      const int kb_lo = krange ? krange[mt].x : 0, kb_hi = krange ? krange[mt].y : kblocks;
+      if (NMMA == 2 && (cu.it & 1) != mi) {
+        // the other issuer's tile: step over its ring stages and accumulator
+        for (int kb = kb_lo; kb < kb_hi; ++kb)
+          if (++stage == NST) {
+            stage = 0;
+            phase ^= 1;
+          }
+        if (Q3 && nt == n_nt - 1) umma_commit(&ctl->xempty[(xcount - 1) & 1]);
+        if (++acc == NACC) {
+          acc = 0;
+          acc_phase ^= 1;
+        }
+        continue;
+      }
       if (!mbar_wait(&ctl->tempty[acc], acc_phase ^ 1, abort_w)) {
         raise_abort(ctl, err, 2);
         break;
       }
+      // issuer 0 holds the token for the CTA's first tile; every other tile waits for it
+      if (NMMA == 2 && !(mi == 0 && first_tile)) {
+        if (!mbar_wait(&turn[mi], nturn & 1, abort_w)) {
+          raise_abort(ctl, err, 8);
+          break;
+        }
+        ++nturn;
+      }
+      first_tile = false;
       tc_fence_after();
       const uint32_t d = tmem + acc * ACC_COLS;
       bool ok = true;
-      const int kb_lo = krange ? krange[mt].x : 0, kb_hi = krange ? krange[mt].y : kblocks;
       for (int kb = kb_lo; kb < kb_hi; ++kb) {
         if (!mbar_wait(&ctl->full[stage], phase, abort_w)) {
           raise_abort(ctl, err, 3);
           ok = false;
           break;
         }
+        if (NMMA == 2 && kb == kb_hi - 1) mbar_arrive(&turn[mi ^ 1]);   // pass the token
         tc_fence_after();
         const uint32_t a0 = Q3
                                 ? smem_u32(sm + XBUF + ((xcount - 1) & 1) * XB3(DP) + kb * A_BYTES)
@@ -517,39 +592,48 @@ __global__ void __launch_bounds__(256, 1)
       }
       if (!ok) break;
       umma_commit(&ctl->tfull[acc]);
-      // MODE 3: the resident x tile is free once the point tile's last MMAs complete
+      // MODE 3/4: the resident x tile is free once the point tile's last MMAs complete (each
+      // issuer commits for its own)
       if (Q3 && nt == n_nt - 1) umma_commit(&ctl->xempty[(xcount - 1) & 1]);
       if (++acc == NACC) {
         acc = 0;
         acc_phase ^= 1;
       }
     }
-    // drain: the commit below fires once every MMA issued above has completed
+    // drain: the barrier completes once every MMA issued above (by each issuer) has completed
     umma_commit(&ctl->drain);
     mbar_wait_drain(&ctl->drain, 0);
   } else if (warp >= 4) {
     // ---------------- epilogue: one pool row per thread
+    // MODE 4 runs two groups of four warps (384 threads): group g takes the tiles of the probes
+    // of parity g, so each SM sub-partition has two epilogue warps to interleave, and the
+    // per-probe shared-memory sums of a probe are only ever touched by one group
     const int q = warp & 3;
+    const int grp = KCM ? (warp - 4) >> 2 : 0;
     int acc = 0;
     uint32_t acc_phase = 0;
     // MODE 3 running sums of the thread's row: over the classes of the current probe
     // (sum h a b, sum h a, sum h b) and over the probes (q)
     float sab = 0.0f, sa = 0.0f, sb = 0.0f, qacc = 0.0f;
-    const int nkc = Q3 ? n_nt / s : 1;
+    const int nkc = nkcq;
     float* psum = (float*)(sm + CTL_OFF + 256);   // MODE 4: [3][S4MAX][128] per-probe sums
-    int mt, nt;
-    for (int it = 0; tile_at(it, mt, nt) && !*abort_w; ++it) {
+    Cur cu = cur_first();
+    for (bool more = Q3 ? cu.mt < n_mt : cur_set(cu); more && !*abort_w; more = cur_next(cu)) {
+      const int mt = cu.mt, nt = cu.nt;
       const int64_t row = (int64_t)mt * BM + q * 32 + lane;
       if (Q3) {
         // per-point quadratic forms (eq. 11) from a = x.A_j[:,k], b = x.B_j[:,k] (K = d), the
         // hi and lo coefficient products summed in TMEM; 64 classes per tile, columns
         // [a (64) | b (64)]; term 1 = sum_k h a b, term 2 = (sum_k h a)(sum_k h b) with the
         // exact f32 h, staged by TMA in 128-byte-swizzled boxes of 32 classes
-        const int kc = KCM ? nt / s : nt % nkc;
-        const int hi = KCM ? it / s : it;
+        const int kc = cu.kr;   // position of the tile's chunk in this point tile's order
+        const int hi = cu.hi;
         const int hb = hi & 1;
+        const bool own = !KCM || (cu.probe & 1) == grp;
+        // every group waits for the h tile (even on tiles it does not own) so that its release
+        // below can never count toward a later load of the same buffer
         if (!mbar_wait(&ctl->hfull[hb], (hi >> 1) & 1, abort_w) ||
-            !mbar_wait(&ctl->tfull[acc], acc_phase, abort_w)) {
+            (own && !mbar_wait(&ctl->tfull[acc], acc_phase, abort_w))) {
           raise_abort(ctl, err, 4);
           break;
         }
@@ -558,7 +642,7 @@ __global__ void __launch_bounds__(256, 1)
         const unsigned char* hbuf = sm + HBUF + hb * H3_BYTES;
         const int r = q * 32 + lane;
 #pragma unroll 1
-        for (int box = 0; box < 2; ++box) {
+        for (int box = 0; box < (own ? 2 : 0); ++box) {
           uint32_t ra[32], rb[32];
           tmem_ld32_async(tb + box * 32, ra);
           tmem_ld32_async(tb + 64 + box * 32, rb);
@@ -591,16 +675,16 @@ __global__ void __launch_bounds__(256, 1)
         tc_fence_before();
         __syncwarp();
         if (lane == 0) {
-          mbar_arrive(&ctl->tempty[acc]);
-          if (!KCM || nt % s == s - 1) mbar_arrive(&ctl->hempty[hb]);
+          if (own) mbar_arrive(&ctl->tempty[acc]);
+          if (!KCM || cu.jr == s - 1) mbar_arrive(&ctl->hempty[hb]);
         }
         if (++acc == NACC) {
           acc = 0;
           acc_phase ^= 1;
         }
-        if (KCM) {
+        if (KCM && own) {
           // probe j's sums over the chunks so far: kept per row in shared memory
-          const int j = probe_of(nt);
+          const int j = cu.probe;
           float* ps = psum + j * 128 + r;
           if (kc > 0) {
             sab += ps[0];
@@ -620,7 +704,12 @@ __global__ void __launch_bounds__(256, 1)
           sab = sa = sb = 0.0f;
         }
         if (nt == n_nt - 1) {
-          if (row >= m && row < N) out32[row - m] = -gscale * qacc;
+          // MODE 4: the two groups' shares land on a zeroed output; with two addends the
+          // rounded sum does not depend on their order
+          if (row >= m && row < N) {
+            if (KCM) atomicAdd(out32 + (row - m), -gscale * qacc);
+            else out32[row - m] = -gscale * qacc;
+          }
           qacc = 0.0f;
         }
         continue;
@@ -2074,14 +2163,17 @@ static int32_t tc_quad_t(firal_problem* P, const float* A, const float* B, int s
     FIRAL_TRY(make_map(&mC, P->gq_m.p, crow, DP, 128, BK, true));
     FIRAL_TRY(make_map_f32(&mHf, P->Ha.p, P->N, c, BM));
     const int n_mt = (int)(Np / BM), n_nt = s * nkc;
-    if (kcm)
-      k_tc_alpha<DP, 4, 2, 0><<<std::min(n_mt, sms), 256, SMEM4(DP), st>>>(
+    if (kcm) {
+      // two epilogue groups add their shares of g
+      FIRAL_CUDA_TRY(cudaMemsetAsync(g, 0, (size_t)P->n * sizeof(float), st));
+      k_tc_alpha<DP, 4, 2, 0><<<std::min(n_mt, sms), 384, SMEM4(DP), st>>>(
           mX, mC, mHf, P->Xb.as<bf16>(), nullptr, nullptr, g, P->N, Np, s, DP / BK, n_mt, n_nt,
           0, d, tc_error_word(P), nullptr, P->Ha.as<float>(), c, P->m, (float)(scale / s));
-    else
+    } else {
       k_tc_alpha<DP, 3, 2, 0><<<std::min(n_mt, sms), 256, SMEM3(DP), st>>>(
           mX, mC, mHf, P->Xb.as<bf16>(), nullptr, nullptr, g, P->N, Np, s, DP / BK, n_mt, n_nt,
           0, d, tc_error_word(P), nullptr, P->Ha.as<float>(), c, P->m, (float)(scale / s));
+    }
     FIRAL_CUDA_TRY(cudaGetLastError());
     return FIRAL_OK;
   }

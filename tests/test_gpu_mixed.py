@@ -114,11 +114,13 @@ def test_mixed_relax_fhat_and_z_vs_exact_solve_oracle(api, handle, precision, d,
 @pytest.mark.parametrize("precision", ["mixed", "mixed_fast"])
 @pytest.mark.parametrize("n,d,c,s", [(3000, 20, 10, 4), (2049, 64, 37, 8), (1500, 128, 5, 3),
                                      (4100, 16, 130, 16), (2049, 64, 36, 8), (1500, 128, 8, 3),
-                                     (3000, 50, 12, 5), (2049, 64, 36, 20), (1000, 128, 8, 17)])
+                                     (3000, 50, 12, 5), (2049, 64, 36, 20), (1000, 128, 8, 17),
+                                     (2049, 64, 36, 1), (1300, 96, 40, 15), (2300, 64, 64, 16)])
 def test_mixed_quad_forms(api, handle, n, d, c, s, precision):
     """Tensor-core per-point quadratic forms (eq. 11) vs the oracle; a large N-component added
     to A must not change the result (H_i vanishes on N = {1_c (x) u}).  d >= 64 with c a
-    multiple of 4 takes the feature-contracted kernel: class-chunk-major for s <= 16,
+    multiple of 4 takes the feature-contracted kernel: class-chunk-major for s <= 16 (its two
+    epilogue groups split the probes by parity: s = 1, odd s = 3, 15 and s = 16 included),
     probe-major for s = 17, 20."""
     p = make_problem(n, d, c, seed=n + 7, x_dtype="bf16", h_dtype="float64", m_o=c)
     p.h = p.h.astype(np.float32).astype(np.float64)
