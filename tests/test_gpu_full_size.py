@@ -1,0 +1,113 @@
+"""Parity at the full size the bench times: the ImageNet-shaped pool (n = 1,000,000, d = 64,
+c = 1000, 1,000 labelled points, X bf16, h f32) in the bench's precision (bf16-direction
+mixed), on outputs the FP64 oracle can afford:
+
+* one probe of Sigma_z V in full (all 64,000 entries).  Sigma_z is a sum over points, so the
+  oracle's Lemma 1 apply runs on chunks of 100,000 points and the chunk results are added;
+* the gradient quadratic forms (eq. 11) at 2,000 sampled points plus the first and last
+  rows (the ragged tail of the last 128-point tile), each a per-point quantity;
+* the MD step (Algorithm 2 lines 10-11) on all n points;
+* one whole MD iteration in the bench's launch configuration (s = 16, 10 CG iterations per
+  solve), checked by the properties that hold at any size: z on the budget simplex, finite
+  positive objective estimate.
+
+Needs a GPU (about 30 GB of device memory); the oracle's share takes well under a minute.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import approx  # noqa: E402
+from paper_2409_07392_gb300.synth import config_problem  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+BUDGET = 1000.0
+S = 16
+CHUNK = 100_000
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def relerr(a, b):
+    return np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b)
+
+
+@pytest.fixture(scope="module")
+def full():
+    from paper_2409_07392_gb300 import api, build
+    build.build()
+    p = config_problem("imagenet_like")
+    H = api.Handle()
+    prob = api.Problem(H, dev(p.X).to(torch.bfloat16), dev(p.h), dev(p.Xo).to(torch.bfloat16),
+                       dev(p.ho), p.lam, precision="mixed_fast")
+    yield p, prob
+    prob.close()
+
+
+def test_full_size_sigma_apply_one_probe(full):
+    p, prob = full
+    rng = np.random.default_rng(0)
+    D = p.d * p.c
+    V = rng.standard_normal((S, D))
+    z = rng.uniform(0.5, 1.5, p.n) * (BUDGET / p.n)
+    got = prob.hessian_apply(dev(V.astype(np.float32)), dev(z.astype(np.float32)), op=0)
+    got = got[0].double().cpu().numpy()
+    assert np.isfinite(got).all()
+    v = V[0][:, None]
+    ref = p.lam * v + approx.hessian_apply(p.Xo, p.ho, np.ones(p.Xo.shape[0]), v)
+    for a in range(0, p.n, CHUNK):
+        ref += approx.hessian_apply(p.X[a:a + CHUNK], p.h[a:a + CHUNK], z[a:a + CHUNK], v)
+    e = relerr(got, ref[:, 0])
+    print(f"full-size Sigma_z v (probe 0 of {S}): {e:.2e}")
+    # the mixed-path bound of the Hessian-apply parity tests at this n (bf16 rounding of h
+    # and walpha x averaged over the point sums, plus 2^-9 for the bf16 probe direction)
+    assert e < 6.0 * 2.0 ** -9 / np.sqrt(p.n) + 2e-6 + 2.0 ** -9
+
+
+def test_full_size_gradient_forms_sampled(full):
+    p, prob = full
+    rng = np.random.default_rng(1)
+    D = p.d * p.c
+    A, B = rng.standard_normal((D, S)), rng.standard_normal((D, S))
+    g = prob.quad_forms(dev(A.T.astype(np.float32)), dev(B.T.astype(np.float32)))
+    g = g.double().cpu().numpy()
+    assert g.shape == (p.n,) and np.isfinite(g).all()
+    idx = np.unique(np.concatenate([np.arange(10), np.arange(p.n - 10, p.n),
+                                    rng.choice(p.n, 2000, replace=False)]))
+    ref = -approx.quad_forms(p.X[idx], p.h[idx], A, B)
+    e = relerr(g[idx], ref)
+    print(f"full-size gradient forms at {idx.size} points: {e:.2e}")
+    # the bound of the quadratic-form parity tests in this precision (bf16 [A; B])
+    assert e < 2.0 ** -9
+
+
+def test_full_size_md_step(full):
+    p, prob = full
+    rng = np.random.default_rng(2)
+    z = rng.uniform(0.5, 1.5, p.n).astype(np.float32)
+    z *= np.float32(BUDGET / z.sum(dtype=np.float64))
+    g = rng.standard_normal(p.n).astype(np.float32)
+    got = prob.md_step(dev(z), dev(g), BUDGET).double().cpu().numpy()
+    ref = approx.md_step(z, g, BUDGET)
+    e = relerr(got, ref)
+    print(f"full-size MD step: {e:.2e}")
+    assert e < 1e-5 and (got >= 0).all()
+    assert abs(got.sum() - BUDGET) < 1e-4 * BUDGET
+
+
+def test_full_size_md_iteration_properties(full):
+    p, prob = full
+    z = torch.full((p.n,), BUDGET / p.n, dtype=torch.float32, device="cuda")
+    opts = prob.relax_opts(s=S, T=1, fixed_iters=10, seed=1)
+    st = prob.relax_step(opts, 0, BUDGET, z)
+    zz = z.double().cpu().numpy()
+    print(f"full-size MD iteration: fhat {st['fhat']:.6g}, gmax {st['gmax']:.3g}")
+    assert np.isfinite(st["fhat"]) and st["fhat"] > 0 and np.isfinite(st["gmax"])
+    assert np.isfinite(zz).all() and (zz >= 0).all()
+    assert abs(zz.sum() - BUDGET) < 1e-4 * BUDGET
+    # the step moved z off the uniform start
+    assert np.abs(zz - BUDGET / p.n).max() > 0
