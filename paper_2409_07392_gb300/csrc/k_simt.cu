@@ -566,6 +566,62 @@ __global__ void k_combine(const T* __restrict__ S, const T* __restrict__ V,
   }
 }
 
+// The same combination for the f32 tensor-core path, four features per thread with 16-byte
+// loads: one CTA per class block covers JB probes (all 16 of the usual probe block), so the
+// d x d block is staged once per class, and each thread keeps 8 split-partial loads in flight.
+// Per output the additions run in the same order as in k_combine (features f ascending, then
+// splits ascending), so both give identical results.  Needs d % 4 == 0 and 16-byte aligned
+// S, Dpart and out; blockDim = JB * d / 4.
+template <int JB>
+__global__ void k_combine4(const float* __restrict__ S, const float* __restrict__ V,
+                           const float* __restrict__ Dpart, int splits, int d, int c, int s,
+                           int64_t D, float* __restrict__ out, const float* __restrict__ vmean,
+                           PoolTab pt) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* Ss = (float*)smem_raw;      // d*d
+  float* vs = Ss + (size_t)d * d;    // JB*d
+  const int k = blockIdx.x;
+  const int j0 = blockIdx.y * JB;
+  const int d4 = d >> 2;
+  const int jj = threadIdx.x / d4, e4 = threadIdx.x - jj * d4;
+  const float4* S4 = reinterpret_cast<const float4*>(S + (int64_t)k * d * d);
+  for (int idx = threadIdx.x; idx < d * d4; idx += blockDim.x)
+    reinterpret_cast<float4*>(Ss)[idx] = S4[idx];
+  for (int idx = threadIdx.x; idx < JB * d; idx += blockDim.x) {
+    const int q = idx / d, f = idx - q * d;
+    const int vm = ((j0 + q) * pool_count(pt) + pool_of(pt, k)) * d + f;
+    vs[idx] = (j0 + q < s) ? V[(int64_t)(j0 + q) * D + (int64_t)k * d + f] -
+                                 (vmean ? vmean[vm] : 0.0f)
+                           : 0.0f;
+  }
+  __syncthreads();
+  const int j = j0 + jj;
+  if (jj >= JB || j >= s) return;
+  float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  for (int f = 0; f < d; ++f) {   // S symmetric: row f of the block
+    const float4 sv = reinterpret_cast<const float4*>(Ss + f * d)[e4];
+    const float v = vs[jj * d + f];
+    acc.x = fmaf(sv.x, v, acc.x);
+    acc.y = fmaf(sv.y, v, acc.y);
+    acc.z = fmaf(sv.z, v, acc.z);
+    acc.w = fmaf(sv.w, v, acc.w);
+  }
+  const int64_t sd = (int64_t)s * d;
+  const float4* dp = reinterpret_cast<const float4*>(Dpart + (int64_t)k * sd + (int64_t)j * d) + e4;
+  const int64_t stride4 = ((int64_t)c * sd) >> 2;
+  float4 dsum = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll 8
+  for (int sp = 0; sp < splits; ++sp) {
+    const float4 t = dp[sp * stride4];
+    dsum.x += t.x;
+    dsum.y += t.y;
+    dsum.z += t.z;
+    dsum.w += t.w;
+  }
+  reinterpret_cast<float4*>(out + (int64_t)j * D + (int64_t)k * d)[e4] =
+      make_float4(acc.x - dsum.x, acc.y - dsum.y, acc.z - dsum.z, acc.w - dsum.w);
+}
+
 static int dterm_splits(int tiles, int64_t N, int sms) {
   int64_t want = (3LL * sms + tiles - 1) / tiles;
   int64_t max_by_rows = (N + 1023) / 1024;
@@ -627,6 +683,25 @@ static int32_t apply_t(firal_problem* P, const T* w, const T* Sblk, const T* V, 
 int32_t combine_f32(firal_problem* P, const float* Sblk, const float* V, int splits, int s,
                     float* out, double* pq, const float* vmean) {
   const int d = P->d, c = P->c;
+  const auto a16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
+  if (!pq && d % 4 == 0 && a16(Sblk) && a16(P->Dpart.p) && a16(out)) {
+    // 16 probes per CTA (d / 4 threads each, at most 512 threads at d = 128)
+    constexpr int JB = 16;
+    const int threads = JB * (d / 4);
+    const size_t smem4 = ((size_t)d * d + (size_t)JB * d) * sizeof(float);
+    static bool attr4 = false;
+    if (!attr4) {
+      FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_combine4<JB>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      attr4 = true;
+    }
+    ProfScope ps(P->H->stream, PF_COMBINE);
+    count_launch();
+    k_combine4<JB><<<dim3(c, (s + JB - 1) / JB), threads, smem4, P->H->stream>>>(
+        Sblk, V, P->Dpart.as<float>(), splits, d, c, s, P->D, out, vmean, P->pt);
+    FIRAL_CUDA_TRY(cudaGetLastError());
+    return FIRAL_OK;
+  }
   const int threads = ((d + 31) / 32) * 32 * 4;   // 4 probes in parallel
   const size_t smem_c = ((size_t)d * d + 4 * (size_t)d) * sizeof(float);
   FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_combine<float, 4>,
