@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=120.0,
+                    help="--impl reference: oracle work over all warm-up and timed steps")
     ap.add_argument("--no-round", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-exact", action="store_true")
@@ -490,9 +492,10 @@ def run_reference(args):
     rates = []
     sample = cores = None
     for i in range(args.warmup + args.steps):
-        r, sample, cores = oracle_md_iteration_rate(cfg, args.cg_iters,
-                                                    seconds=max(2.0, 120.0 / (args.warmup +
-                                                                              args.steps)))
+        # each step a bounded sample: the total over all steps is about --ref-seconds, and
+        # no step is shorter than 2 s (or the whole total, when that is smaller)
+        per_step = max(min(2.0, args.ref_seconds), args.ref_seconds / (args.warmup + args.steps))
+        r, sample, cores = oracle_md_iteration_rate(cfg, args.cg_iters, seconds=per_step)
         if i >= args.warmup:
             rates.append(r)
     v = float(np.mean(rates))
