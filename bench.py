@@ -647,6 +647,32 @@ def run_ours(args):
                        "warmup": 1, "ms_per_step": per_step,
                        "note": "each step is one api.relax(T=1) call on pinned host tensors: "
                                "H2D copies, problem preparation, one MD iteration, D2H of z"}
+        # diagnostic only (not the e2e value): the same call split into its H2D copies, the
+        # library call on the device copies and the D2H of z, with the collector's counts
+        try:
+            import gc
+            parts = []
+            for t in range(3):
+                gc0 = gc.get_count()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                dX, dh = Xh.to("cuda", non_blocking=True), hh.to("cuda", non_blocking=True)
+                dXo, dho = Xoh.to("cuda", non_blocking=True), hoh.to("cuda", non_blocking=True)
+                dz0 = zh.to("cuda", non_blocking=True)
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                zd, _ = api.relax(dX, dh, dXo, dho, p.lam, b, s=s, T=1, fixed_iters=args.cg_iters,
+                                  seed=100 + t, precision=args.precision, z0=dz0, handle=H)
+                torch.cuda.synchronize()
+                t2 = time.perf_counter()
+                zh.copy_(zd.cpu())
+                t3 = time.perf_counter()
+                del dX, dh, dXo, dho, dz0, zd
+                parts.append({"h2d_ms": 1e3 * (t1 - t0), "call_ms": 1e3 * (t2 - t1),
+                              "d2h_ms": 1e3 * (t3 - t2), "gc_counts": list(gc0)})
+            line["e2e_breakdown"] = parts
+        except Exception as exc:
+            line["e2e_breakdown"] = {"error": str(exc)[:300]}
 
     if rank == 0:
         # ---------------- the paper's timing setting (m = 50) and the tolerance mode
