@@ -596,6 +596,22 @@ def run_ours(args):
                 "executed_tflops": execd,
                 "peak_source": (f"{pk_src} bf16 sustained (of measured)" if tensor else
                                 "derived FP32 FMA peak: 152 SMs x 128 lanes x 2 x 2.07 GHz")}
+    # every tensor-core class against the same peak: algorithmic flops per MD iteration (one
+    # unit per Hessian apply for the two apply GEMMs; one block-sum pass and one gradient per
+    # iteration) over the class's time per iteration, with DRAM traffic per launch where
+    # captured
+    if args.precision.startswith("mixed"):
+        n_pad = (n_all + 127) // 128 * 128
+        for k in ("apply_alpha", "apply_dterm", "syrk_blocks", "quad_forms"):
+            kk = kernels.get(k)
+            f_k = algorithmic_flops(k, cfg, n_all, s)
+            if not kk or f_k is None or kk["ms_per_step"] <= 0:
+                continue
+            units = kk["groups_per_step"] if k.startswith("apply_") else 1.0
+            a_k = f_k * units / (kk["ms_per_step"] / 1000.0) / 1e12
+            kk.update({"tflops_algorithmic": a_k,
+                       "frac_of_bf16_sustained": a_k / pk["bf16_tflops_sustained"],
+                       "traffic_bytes_per_launch": dram_traffic(k, n_pad, args.precision)})
     # the Hessian apply as a whole (alpha + D + combine), the operation the metric counts
     apply_ms = sum(kernels.get(k, {}).get("ms_per_step", 0.0)
                    for k in ("apply_alpha", "apply_dterm", "apply_combine"))
