@@ -192,9 +192,26 @@ def peaks():
 
 
 # ------------------------------------------------------------------------------ oracle timing
+def _oracle_iteration_seconds(cfg, cg_iters, n1, seed=0):
+    """Seconds of one oracle MD iteration (fixed CG iterations) on an n1-point pool."""
+    from oracle import approx
+    from paper_2409_07392_gb300.synth import make_problem
+    n_full, d, c, s = cfg["n"], cfg["d"], cfg["c"], cfg["s"]
+    p1 = make_problem(n1, d, c, seed=seed, x_dtype=cfg["x_dtype"], h_dtype=cfg["h_dtype"])
+    t0 = time.perf_counter()
+    approx.relax(p1, float(cfg["b"]) * n1 / n_full if n1 < n_full else float(cfg["b"]), s=s,
+                 T=1, seed=1, fixed_iters=cg_iters)
+    return time.perf_counter() - t0
+
+
 def oracle_md_iteration_rate(cfg, cg_iters, seconds, seed=0):
-    """Time one oracle MD iteration on a subsample sized for ~`seconds` of CPU work and scale
-    to the full pool (the per-point work is linear in n).  Returns (iters/s, sample, cores)."""
+    """The FP64 oracle's MD iterations/s at the full pool size, from two bounded samples.
+
+    One MD iteration has per-point work (the Hessian applies, block sums and gradient, linear
+    in n) and per-problem work (the c block factorisations and the d c x s CG vector updates,
+    independent of n).  The oracle is timed on two subsamples, n1 and n1 / 2 points, sized
+    for about ``seconds`` of work in all; the fit t(n) = a + b n through the two times is
+    evaluated at the full n.  Returns a dict (value in MD iters/s, the fit, the sample)."""
     from oracle import approx
     from paper_2409_07392_gb300.synth import make_problem
     n_full, d, c, s = cfg["n"], cfg["d"], cfg["c"], cfg["s"]
@@ -207,15 +224,61 @@ def oracle_md_iteration_rate(cfg, cg_iters, seconds, seed=0):
     ops.sigma_apply(np.full(n0, 1.0 / n0), V)
     t_apply = time.perf_counter() - t0
     per_iter_est = t_apply * (2 * cg_iters + 4) * 1.3
-    n1 = int(max(n0, min(n_full, n0 * seconds / max(per_iter_est, 1e-3))))
-    p1 = make_problem(n1, d, c, seed=seed, x_dtype=cfg["x_dtype"], h_dtype=cfg["h_dtype"])
-    t0 = time.perf_counter()
-    approx.relax(p1, float(cfg["b"]) * n1 / n_full if n1 < n_full else float(cfg["b"]), s=s,
-                 T=1, seed=1, fixed_iters=cg_iters)
-    dt = time.perf_counter() - t0
-    per_full = dt * n_full / n1
-    return 1.0 / per_full, f"one MD iteration ({cg_iters} CG iterations per solve) on n={n1} " \
-        f"of {n_full} points, scaled by n", os.cpu_count()
+    n1 = int(max(2 * n0, min(n_full, n0 * (seconds / 1.5) / max(per_iter_est, 1e-3))))
+    n2 = n1 // 2
+    t1 = _oracle_iteration_seconds(cfg, cg_iters, n1, seed)
+    t2 = _oracle_iteration_seconds(cfg, cg_iters, n2, seed)
+    b = max((t1 - t2) / (n1 - n2), 0.0)
+    a = max(t1 - b * n1, 0.0)
+    if b == 0.0:                       # timing noise: fall back to proportional scaling
+        a, b = 0.0, t1 / n1
+    t_full = a + b * n_full
+    return {"value": 1.0 / t_full,
+            "sample": f"one MD iteration ({cg_iters} CG iterations per solve) timed on n={n1} "
+                      f"and n={n2} of {n_full} points ({t1:.2f} s, {t2:.2f} s); "
+                      f"extrapolated with t(n) = a + b n",
+            "fit": {"a_s": a, "b_s_per_point": b, "n_samples": [n1, n2],
+                    "seconds": [t1, t2]},
+            "extrapolated": n1 < n_full}
+
+
+def oracle_rate_one_core(cfg, cg_iters, seconds):
+    """The same measurement in a child process limited to one thread (BLAS, OpenMP) and, where
+    the OS allows, pinned to one core."""
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.oracle_md_iteration_rate(%r, %d, %f)))"
+            % (ROOT, cfg, cg_iters, seconds))
+    pre = []
+    if hasattr(os, "sched_getaffinity"):
+        try:
+            core = sorted(os.sched_getaffinity(0))[0]
+            pre = ["taskset", "-c", str(core)] if subprocess.run(
+                ["taskset", "-c", str(core), "true"], capture_output=True).returncode == 0 else []
+        except Exception:
+            pre = []
+    r = subprocess.run(pre + [sys.executable, "-c", code], env=env, capture_output=True,
+                       text=True, timeout=max(120.0, 8 * seconds))
+    if r.returncode != 0:
+        return {"error": (r.stderr or r.stdout)[-300:]}
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    out["cores"] = 1
+    out["pinned"] = bool(pre)
+    return out
+
+
+def cpu_baseline(cfg, cg_iters, seconds, one_core=True):
+    """The oracle baseline on all host cores (value) and on one core (beside it)."""
+    rec = oracle_md_iteration_rate(cfg, cg_iters, seconds)
+    out = {"value": rec["value"], "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+           "sample": rec["sample"], "fit": rec["fit"], "extrapolated": rec["extrapolated"],
+           "threads_note": "numpy with its BLAS on all host cores; elementwise work on one"}
+    if one_core:
+        one = oracle_rate_one_core(cfg, cg_iters, seconds)
+        out["one_core"] = ({"value": one["value"], "unit": UNIT, "cores": 1,
+                            "pinned": one.get("pinned"), "sample": one["sample"],
+                            "fit": one["fit"]} if "value" in one else one)
+    return out
 
 
 def round_measure(args, H):
@@ -490,21 +553,26 @@ def run_reference(args):
         return
     cfg = workload(args)
     rates = []
-    sample = cores = None
+    rec = None
     for i in range(args.warmup + args.steps):
         # each step a bounded sample: the total over all steps is about --ref-seconds, and
         # no step is shorter than 2 s (or the whole total, when that is smaller)
         per_step = max(min(2.0, args.ref_seconds), args.ref_seconds / (args.warmup + args.steps))
-        r, sample, cores = oracle_md_iteration_rate(cfg, args.cg_iters, seconds=per_step)
+        rec = oracle_md_iteration_rate(cfg, args.cg_iters, seconds=per_step)
         if i >= args.warmup:
-            rates.append(r)
+            rates.append(rec["value"])
     v = float(np.mean(rates))
+    cores = os.cpu_count()
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": describe(cfg, args)},
+            "data": "synthetic",
+            "config": {"workload": describe(cfg, args),
+                       "extrapolated": ("each step times the FP64 oracle on two subsamples of "
+                                        "the pool and extrapolates t(n) = a + b n to the full n"
+                                        if rec["extrapolated"] else False)},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": sample},
+                             "sample": rec["sample"], "fit": rec["fit"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -596,6 +664,15 @@ def run_ours(args):
                 "executed_tflops": execd,
                 "peak_source": (f"{pk_src} bf16 sustained (of measured)" if tensor else
                                 "derived FP32 FMA peak: 152 SMs x 128 lanes x 2 x 2.07 GHz")}
+        if tensor:
+            roof["frac_of_burst"] = achieved / pk["bf16_tflops"]
+            # per-clock efficiency: the sustained peak was measured at a lower SM clock than
+            # this run's, so compare work per SM cycle (time x median SM MHz)
+            peak_mhz = (pk.get("clocks_under_load") or {}).get("sm_mhz_median")
+            if peak_mhz and clk and clk.get("sm_mhz"):
+                roof["frac_clock_normalized"] = (achieved / clk["sm_mhz"]) / (peak / peak_mhz)
+                roof["clock_note"] = (f"sustained peak at a median {peak_mhz:.0f} MHz, this run "
+                                      f"at {clk['sm_mhz']:.0f} MHz")
     # every tensor-core class against the same peak: algorithmic flops per MD iteration (one
     # unit per Hessian apply for the two apply GEMMs; one block-sum pass and one gradient per
     # iteration) over the class's time per iteration, with DRAM traffic per launch where
@@ -767,9 +844,7 @@ def run_ours(args):
                 line["active_learning"] = {"error": str(exc)[:300]}
         # ---------------- CPU oracle baseline
         if not args.no_cpu:
-            v, sample, cores = oracle_md_iteration_rate(cfg, args.cg_iters, args.cpu_seconds)
-            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                    "sample": sample}
+            line["cpu_baseline"] = cpu_baseline(cfg, args.cg_iters, args.cpu_seconds)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -302,17 +302,21 @@ int32_t firal_md_step(firal_problem* problem, void* z, const void* g, double bud
 /* Allocation-free mirror-descent update (the paper has no counterpart; it exists for callers
  * that cannot allocate device memory: code running while a CUDA graph is captured, servers and
  * embedded runtimes that give all device memory to their own pool at start-up, and plug-in
- * hosts that forbid a library from growing its footprint).  Computes exactly what
- * firal_md_step does -- z <- z exp(-beta g), z <- budget z / sum(z), beta = beta0/||g||_inf --
- * without a problem handle and without calling cudaMalloc, cudaFree or any allocating routine.
+ * hosts that forbid a library from growing its footprint).  Computes what firal_md_step does
+ * -- z <- z exp(-beta g), z <- budget z / sum(z), beta = beta0/||g||_inf -- without a problem
+ * handle and without calling cudaMalloc, cudaFree or any allocating routine.
  * z (in/out) and g: device, n values of dtype (FIRAL_DT_F32 or FIRAL_DT_F64).  stream: a
- * cudaStream_t as void* (NULL = legacy default stream).  Scratch: a fixed 64 KiB array in the
- * library, resident on every GPU that loads it until the process exits; it limits n to
- * 16,777,216 (larger n returns FIRAL_ERR_ARG).  The first call on each device looks up that
- * array's device address (cudaGetSymbolAddress) with the device current; make that first call
- * before any stream capture.  All calls share the array and it keeps the last call's values
- * (nothing in it needs clearing: every slot a call reads is written by the same call), so
- * calls whose kernels overlap on the GPU race and must be ordered by the caller. */
+ * cudaStream_t as void* (NULL = legacy default stream).  Returns after enqueueing 5 kernels.
+ * Scratch: a fixed array of 64 KiB + 64 bytes in the library, resident on every GPU that loads
+ * it until the process exits; it limits n to 16,777,216 (larger n returns FIRAL_ERR_ARG).
+ * Each call looks up that array's device address (cudaGetSymbolAddress, which allocates
+ * nothing) with the current device; the first lookup on a device may load the library's device
+ * code there, so make the first call on each device before any stream capture.  All calls share
+ * the array and it keeps the last call's values (nothing in it needs clearing: every slot a
+ * call reads is written by the same call), so calls whose kernels overlap on the GPU race and
+ * must be ordered by the caller.  If ||g||_inf is NaN or infinite (or the updated z has no
+ * positive finite sum) the kernels leave z unchanged; the status, returned before the kernels
+ * run, cannot report that case, so check g where it may not be finite. */
 int32_t firal_md_step_static(void* z, const void* g, int64_t n, int32_t dtype, double budget,
                              double beta0, void* stream);
 

@@ -63,9 +63,16 @@ def test_full_size_sigma_apply_one_probe(full):
         ref += approx.hessian_apply(p.X[a:a + CHUNK], p.h[a:a + CHUNK], z[a:a + CHUNK], v)
     e = relerr(got, ref[:, 0])
     print(f"full-size Sigma_z v (probe 0 of {S}): {e:.2e}")
-    # the mixed-path bound of the Hessian-apply parity tests at this n (bf16 rounding of h
-    # and walpha x averaged over the point sums, plus 2^-9 for the bf16 probe direction)
-    assert e < 6.0 * 2.0 ** -9 / np.sqrt(p.n) + 2e-6 + 2.0 ** -9
+    # bound: (1) bf16 rounding of h and walpha x, independent per (point, class) and averaged
+    # over the point sums: 6 * 2^-9 / sqrt(n); (2) the tensor-core accumulation bias of one
+    # D-GEMM split (at most 512 K-steps = 2048 adds, about 2^-25 of the running sum each);
+    # (3) the bf16 probe direction of this precision enters only the low-rank term, whose size
+    # relative to the diagonal term is the mean purity sum_k h_ik^2 (about e/c for these flat
+    # softmax rows): 2^-9 times that
+    purity = float(np.mean(np.sum(p.h.astype(np.float64) ** 2, axis=1)))
+    tol = 6.0 * 2.0 ** -9 / np.sqrt(p.n) + 2048 * 2.0 ** -25 + 2.0 ** -9 * purity
+    print(f"  bound {tol:.2e} (mean purity {purity:.2e})")
+    assert e < tol
 
 
 def test_full_size_gradient_forms_sampled(full):
@@ -81,8 +88,8 @@ def test_full_size_gradient_forms_sampled(full):
     ref = -approx.quad_forms(p.X[idx], p.h[idx], A, B)
     e = relerr(g[idx], ref)
     print(f"full-size gradient forms at {idx.size} points: {e:.2e}")
-    # the bound of the quadratic-form parity tests in this precision (bf16 [A; B])
-    assert e < 2.0 ** -9
+    # the bound of the quadratic-form parity tests (coefficients as bf16 hi + lo)
+    assert e < 1e-4
 
 
 def test_full_size_md_step(full):

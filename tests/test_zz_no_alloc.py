@@ -1,4 +1,5 @@
-"""The allocation-free mirror-descent update (firal_md_step_static) against firal_md_step.
+"""The allocation-free mirror-descent update (firal_md_step_static) against firal_md_step and
+the FP64 oracle's md_step.
 
 Callers that cannot allocate device memory -- code running under CUDA graph capture,
 runtimes that pre-assign all device memory to their own pool, plug-in hosts that cap a
@@ -13,7 +14,15 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+from oracle import approx  # noqa: E402
+
 pytestmark = pytest.mark.gpu
+
+
+def _static(lib, z, G, n, code, budget, beta0):
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return lib.firal_md_step_static(ctypes.c_void_p(z.data_ptr()), ctypes.c_void_p(G.data_ptr()),
+                                    n, code, budget, beta0, stream)
 
 
 @pytest.mark.parametrize("dtype", ["float32", "float64"])
@@ -41,21 +50,46 @@ def test_static_md_step_matches_md_step_on_two_calls(dtype):
     G1 = torch.from_numpy(g1).to("cuda", tdt).contiguous()
     G2 = torch.from_numpy(g2).to("cuda", tdt).contiguous()
     code = _lib.FIRAL_DT_F32 if dtype == "float32" else _lib.FIRAL_DT_F64
-    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     tol = 1e-6 if dtype == "float32" else 1e-13
-    for G, ref in ((G1, ref1), (G2, ref2)):
-        rc = lib.firal_md_step_static(ctypes.c_void_p(z.data_ptr()), ctypes.c_void_p(G.data_ptr()),
-                                      n, code, budget, beta0, stream)
+    z_or = z0
+    for G, g, ref in ((G1, g1, ref1), (G2, g2, ref2)):
+        # the oracle's step from the same (stored) z and g
+        z_or = approx.md_step(z.double().cpu().numpy(), G.double().cpu().numpy(), budget, beta0)
+        rc = _static(lib, z, G, n, code, budget, beta0)
         assert rc == 0, _lib.STATUS.get(rc, rc)
         torch.cuda.synchronize()
         got = z.double().cpu().numpy()
         want = ref.double().cpu().numpy()
         assert np.linalg.norm(got - want) / np.linalg.norm(want) < tol
+        assert np.linalg.norm(got - z_or) / np.linalg.norm(z_or) < tol
         assert abs(got.sum() - budget) < 1e3 * tol * budget
     # sizes beyond the static scratch are refused, not run
     big = 4096 * 4096 + 1
-    rc = lib.firal_md_step_static(ctypes.c_void_p(z.data_ptr()), ctypes.c_void_p(G1.data_ptr()),
-                                  big, code, budget, beta0, stream)
-    assert rc == -1   # FIRAL_ERR_ARG
+    assert _static(lib, z, G1, big, code, budget, beta0) == -1   # FIRAL_ERR_ARG
     prob.close()
     H.close()
+
+
+def test_static_md_step_non_finite_gradient_leaves_z_unchanged():
+    """A NaN or an infinity in g leaves z as it was; the next call with a finite g runs
+    normally (the flag slot of the shared scratch is rewritten by every call)."""
+    from paper_2409_07392_gb300 import _lib, build
+    build.build()
+    lib = _lib.load()
+    n, budget = 70_001, 50.0
+    rng = np.random.default_rng(3)
+    z0 = rng.uniform(0.1, 1.0, n)
+    z0 = budget * z0 / z0.sum()
+    z = torch.from_numpy(z0).cuda()
+    for bad in (np.nan, np.inf):
+        g = rng.standard_normal(n)
+        g[n // 2] = bad
+        assert _static(lib, z, torch.from_numpy(g).cuda(), n, _lib.FIRAL_DT_F64, budget, 1.0) == 0
+        torch.cuda.synchronize()
+        assert np.array_equal(z.cpu().numpy(), z0)
+    g = rng.standard_normal(n)
+    assert _static(lib, z, torch.from_numpy(g).cuda(), n, _lib.FIRAL_DT_F64, budget, 1.0) == 0
+    torch.cuda.synchronize()
+    want = approx.md_step(z0, g, budget, 1.0)
+    got = z.cpu().numpy()
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-13
