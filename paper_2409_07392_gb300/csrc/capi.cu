@@ -1264,7 +1264,8 @@ int32_t firal_problem_destroy(firal_problem* P) {
                   &P->Minv, &P->HoBlk, &P->walpha, &P->Dpart, &P->syrk_part, &P->cgX, &P->cgR,
                   &P->cgP, &P->cgQ, &P->cgZ, &P->cgcols, &P->cgpart1, &P->cgpart2, &P->V, &P->U,
                   &P->W, &P->HU, &P->g, &P->red, &P->zsave, &P->Xb, &P->Hb, &P->HbT, &P->Pb, &P->vmean, &P->qmean, &P->Aw, &P->Zp, &P->Hlo, &P->gq_ab,
-                  &P->gq_m, &P->gq_part, &P->rtab, &P->rM, &P->tdev}) {
+                  &P->gq_m, &P->gq_part, &P->rtab, &P->rM, &P->tdev, &P->cen, &P->cen_off,
+                  &P->cen_idx, &P->Ub, &P->UbT, &P->cen_am, &P->cen_rho, &P->cen_lab}) {
     if (synced) b->park();
     else b->release();
   }

@@ -199,6 +199,12 @@ struct firal_problem {
   firal::DBuf gq_ab, gq_m, gq_part;  // tensor-core quadratic forms: [A;B], M~ pairs, partials
   firal::DBuf rtab, rM;          // Round on tensor cores: 8-pair chunk table, M~ hi/lo rows
   firal::DBuf tdev;              // device-resident MD step counter (graph replays)
+  // confident rows (max_k h_ik > 1/2), centred at their class m: u_i = h_i - e_m in the
+  // Hessian apply (cen[i] = m or -1; rows grouped by class in cen_idx, cen_off per class);
+  // bf16 u row-major and K-block-major; a_m and w (u . a) per (row, probe) of an apply
+  int64_t n_cen = 0;
+  // (the labelled rows of such a problem are applied on CUDA cores: cen_lab, m x s x c)
+  firal::DBuf cen, cen_off, cen_idx, Ub, UbT, cen_am, cen_rho, cen_lab;
   int rtab_d = -1, rtab_chunks = 0;
   int32_t dp = 0, cp = 0;
   int64_t Np = 0;

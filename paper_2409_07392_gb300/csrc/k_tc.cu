@@ -118,6 +118,163 @@ __global__ void k_to_bf16_lo_pad(bf16* dst, const float* src, int64_t rows, int 
   }
 }
 
+// ------------------------------------------------------------------------------------------
+// Confident rows.  With h_i = e_m + u_i (m = the row's most probable class, u_i = h_i - e_m),
+// diag(h) - h h^T = diag(u) - e_m u^T - u e_m^T - u u^T exactly, so per point (a = V^T x_i)
+//     [(diag(h) - h h^T) a]_k = u_k a_k - u_k alpha - [k = m] (u . a),   alpha = h . a = a_m + u . a.
+// Every term is of the size of u (1 - h_m, h_k for k != m), so no two large terms cancel:
+// rounding u to bf16 is relative to u, where rounding h_m ~ 1 to bf16 errs by up to 2^-9 in
+// the same direction on every confident row and that bias is as large as the Hessian itself.
+// Rows with h_m > 1/2 (cen[i] = m, else -1) take this form in the tensor-core apply:
+//   diagonal part  sum_i w_i u_ik x_i x_i^T V_k          (block sums with u in the class operand)
+//   low-rank part  sum_i w_i u_ik alpha_i x_i             (alpha-GEMM on u: u . a; plus a_m)
+//   class-m part   sum_{i: m_i = k} w_i (u_i . a_i) x_i   (a per-class sum over its rows)
+// ------------------------------------------------------------------------------------------
+// cen[r] = argmax_k h_rk (lowest index on ties) when that probability exceeds 1/2, else -1;
+// *count gains the number of such rows.  One warp per row.
+__global__ void k_row_top(int* cen, unsigned long long* count, const float* src, int64_t rows,
+                          int cols) {
+  const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r >= rows) return;
+  float best = -1.0f;
+  int bi = 0x7fffffff;
+  for (int k = lane; k < cols; k += 32) {
+    const float v = src[r * cols + k];
+    if (v > best) {
+      best = v;
+      bi = k;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ob > best || (ob == best && oi < bi)) {
+      best = ob;
+      bi = oi;
+    }
+  }
+  if (lane == 0) {
+    cen[r] = best > 0.5f ? bi : -1;
+    if (best > 0.5f) atomicAdd(count, 1ULL);
+  }
+}
+
+// dst = bf16(h - e_m) on centred rows (h_m - 1 is exact in f32 for h_m >= 1/2), bf16(h)
+// elsewhere; padding as k_to_bf16_pad
+__global__ void k_to_bf16_centred_pad(bf16* dst, const float* src, const int* cen, int64_t rows,
+                                      int cols, int64_t rows_p, int cols_p) {
+  const int64_t total = rows_p * cols_p;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = idx / cols_p;
+    const int cc = (int)(idx - r * cols_p);
+    float v = 0.0f;
+    if (r < rows && cc < cols) {
+      v = src[r * cols + cc];
+      if (cen[r] == cc) v -= 1.0f;
+    }
+    dst[idx] = __float2bfloat16_rn(v);
+  }
+}
+
+// a_m for the centred rows of class k (block k): am[i][j] = x_i . P~_j[:, k], the probe block
+// as the alpha-GEMM sees it (its bf16 parts summed), rows listed by class in idx[off[k]..).
+__global__ void k_centre_am(float* am, const bf16* Pb, const bf16* Xb, const int* off,
+                            const int* idx, int s, int npart, int dp, int cp) {
+  extern __shared__ float pv[];   // s x dp
+  const int k = blockIdx.x;
+  const int r0 = off[k], r1 = off[k + 1];
+  if (r0 == r1) return;
+  for (int t = threadIdx.x; t < s * dp; t += blockDim.x) {
+    const int j = t / dp, e = t - j * dp;
+    float v = 0.0f;
+    for (int part = 0; part < npart; ++part)
+      v += __bfloat162float(Pb[((int64_t)(j * npart + part) * dp + e) * cp + k]);
+    pv[t] = v;
+  }
+  __syncthreads();
+  const int64_t items = (int64_t)(r1 - r0) * s;
+  for (int64_t t = threadIdx.x; t < items; t += blockDim.x) {
+    const int rr = (int)(t / s), j = (int)(t - (int64_t)rr * s);
+    const int64_t row = idx[r0 + rr];
+    const __nv_bfloat162* x2 = reinterpret_cast<const __nv_bfloat162*>(Xb + row * dp);
+    const float* pj = pv + j * dp;
+    float acc = 0.0f;
+    for (int e = 0; e < dp; e += 2) {
+      const float2 xf = __bfloat1622float2(x2[e >> 1]);
+      acc = fmaf(xf.x, pj[e], acc);
+      acc = fmaf(xf.y, pj[e + 1], acc);
+    }
+    am[row * s + j] = acc;
+  }
+}
+
+// class-m part of the centred rows: out[k][j d + e] = sum_{rows i of class k} rho[i][j] x_ie
+// (rho = w (u . a) from the alpha epilogue), rows in a fixed order; zero for classes without
+// centred rows.  It is added to the split-K partials of the D-GEMM (block k).
+__global__ void k_centre_termc(float* out, const float* rho, const bf16* Xb, const int* off,
+                               const int* idx, int s, int d, int dp) {
+  const int k = blockIdx.x;
+  const int r0 = off[k], r1 = off[k + 1];
+  const int sd = s * d;
+  for (int t = threadIdx.x; t < sd; t += blockDim.x) {
+    const int j = t / d, e = t - j * d;
+    float acc = 0.0f;
+    for (int rr = r0; rr < r1; ++rr) {
+      const int64_t row = idx[rr];
+      acc = fmaf(rho[row * s + j], __bfloat162float(Xb[row * dp + e]), acc);
+    }
+    out[(int64_t)k * sd + t] = acc;
+  }
+}
+
+// Labelled rows of a problem with confident rows.  They are few and carry weight 1 each (a
+// large share of Sigma_z), so their bf16 roundings do not average out over many points: their
+// Hessians are applied here on CUDA cores in f32 by Lemma 1, per point, and the tensor-core
+// part skips them.  G[i][j][k] = w_i ((a_k - alpha) h_ik) with a_k = x_i . V~_j[:, k],
+// alpha = h_i . a, V~ = V minus its class mean (the direction the rest of the apply uses).
+// Block (i, j); dynamic shared memory c floats.
+__global__ void k_lab_gamma(float* G, const float* V, const float* vmean, const float* Xa,
+                            const float* Ha, const float* w, int s, int c, int d, int64_t D) {
+  extern __shared__ float a_s[];   // c
+  __shared__ float red[32];
+  const int64_t i = blockIdx.x;
+  const int j = blockIdx.y;
+  const float* x = Xa + i * d;
+  const float* h = Ha + i * c;
+  float part = 0.0f;
+  for (int k = threadIdx.x; k < c; k += blockDim.x) {
+    const float* v = V + (int64_t)j * D + (int64_t)k * d;
+    const float* vm = vmean + (int64_t)j * d;
+    float acc = 0.0f;
+    for (int e = 0; e < d; ++e) acc = fmaf(x[e], v[e] - vm[e], acc);
+    a_s[k] = acc;
+    part = fmaf(h[k], acc, part);
+  }
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+  __syncthreads();
+  float alpha = 0.0f;
+  for (int q = 0; q < (int)(blockDim.x >> 5); ++q) alpha += red[q];
+  const float wi = w[i];
+  for (int k = threadIdx.x; k < c; k += blockDim.x)
+    G[(i * s + j) * c + k] = wi * ((a_s[k] - alpha) * h[k]);
+}
+
+// out[k][j d + e] = -sum_{i < m} G[i][j][k] x_ie (negated: the combine subtracts its partials)
+__global__ void k_lab_scatter(float* out, const float* G, const float* Xa, int64_t m, int s,
+                              int c, int d) {
+  const int k = blockIdx.x;
+  const int sd = s * d;
+  for (int t = threadIdx.x; t < sd; t += blockDim.x) {
+    const int j = t / d, e = t - j * d;
+    float acc = 0.0f;
+    for (int64_t i = 0; i < m; ++i) acc = fmaf(G[(i * s + j) * c + k], Xa[i * d + e], acc);
+    out[(int64_t)k * sd + t] = -acc;
+  }
+}
+
 // dst[cols_p x rows_p] = transpose of a padded bf16 matrix src[rows_p x cols_p]
 // src (rows_p x cols_p, row-major) -> dst in the K-block-major layout [r / 64][col][r % 64] with
 // colsb >= cols_p rows per block (rows cols_p..colsb-1 zero): every 64-point tile of a block of
@@ -304,7 +461,9 @@ __global__ void __launch_bounds__(MODE == 4 ? 384 : 256, 1)
                int64_t N, int64_t Np, int s, int kblocks, int n_mt, int n_nt, int npairs, int d,
                int32_t* err, const int2* __restrict__ krange,
                const float* __restrict__ hrow = nullptr, int c = 0, int64_t m = 0,
-               float gscale = 0.0f) {
+               float gscale = 0.0f, const int* __restrict__ cen = nullptr,
+               const float* __restrict__ cen_am = nullptr, float* __restrict__ cen_rho = nullptr,
+               int64_t wskip = 0) {
   using namespace alpha_cfg;
   // MODE 3 stages hold the x tile and two 128-row coefficient tiles (hi and lo), followed by
   // a double buffer of f32 h tiles
@@ -728,7 +887,10 @@ __global__ void __launch_bounds__(MODE == 4 ? 384 : 256, 1)
           xp[4 * t + 3] = u.w;
         }
       }
-      const float wi = (MODE == 0) ? (row < N ? w[row] : 0.0f) : 1.0f;
+      // rows below wskip (labelled rows applied on CUDA cores) take no part here
+      const float wi = (MODE == 0) ? (row < N && row >= wskip ? w[row] : 0.0f) : 1.0f;
+      // MODE 0 on a centred row: the accumulator holds u . a; alpha = a_m + u . a
+      const bool crow = MODE == 0 && cen != nullptr && row < N && cen[row] >= 0;
       if (!mbar_wait(&ctl->tfull[acc], acc_phase, abort_w)) {
         raise_abort(ctl, err, 4);
         break;
@@ -796,9 +958,14 @@ __global__ void __launch_bounds__(MODE == 4 ? 384 : 256, 1)
           if (MODE == 0) {
             // walpha^T in the K-block-major layout [row / 64][j][row % 64], sp16 rows per block
             const int sp16 = (s + 15) / 16 * 16;
+            float al = sum;
+            if (crow) {
+              cen_rho[row * s + j] = wi * sum;
+              al = cen_am[row * s + j] + sum;
+            }
             if (row < Np)
               aT[((row >> 6) * sp16 + j) * 64 + (row & 63)] =
-                  __float2bfloat16_rn(row < N ? wi * sum : 0.0f);
+                  __float2bfloat16_rn(row < N ? wi * al : 0.0f);
           } else if (row < N) {
             out32[(int64_t)j * Np + row] = sum;
           }
@@ -1438,12 +1605,16 @@ __global__ void k_build_z(bf16* Zhi, bf16* Zlo, const bf16* Xb, int d, int dp, i
 
 // Class operands of the block sums, zero-padded, in the K-block-major layout
 // [i / 64][k][i % 64] with cpb rows per block:
-//   A_hi = bf16(w h), A_lo = bf16(w h - A_hi), A_P = bf16(w h (1 - h))   (A_P only if AP)
+//   A_hi = bf16(w u), A_lo = bf16(w u - A_hi), A_P = bf16(w h (1 - h))   (A_P only if AP)
+// with u = h, or u = h - e_m on centred rows (cen, may be NULL); rows below wskip take weight
+// 0 in A_hi and A_lo (their part of the Hessian apply runs on CUDA cores).
 // Block = one 64-point block x 32 classes; each warp store writes one 128-byte row run.
 __global__ void k_weighted_hT(bf16* Ahi, bf16* Alo, bf16* AP, const float* Ha, const float* w,
-                              int64_t N, int c, int64_t Np, int cpb) {
+                              int64_t N, int c, int64_t Np, int cpb, const int* cen,
+                              int64_t wskip) {
   __shared__ float tile[64][33];
-  __shared__ float ws[64];
+  __shared__ float ws[64], wS[64];
+  __shared__ int cs[64];
   const int64_t rb = (int64_t)blockIdx.x * 64;
   const int cb = blockIdx.y * 32;
   for (int i = threadIdx.y; i < 64; i += blockDim.y) {
@@ -1452,15 +1623,22 @@ __global__ void k_weighted_hT(bf16* Ahi, bf16* Alo, bf16* AP, const float* Ha, c
     tile[i][threadIdx.x] = (r < N && col < c) ? Ha[r * c + col] : 0.0f;
   }
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  if (tid < 64) ws[tid] = rb + tid < N ? w[rb + tid] : 0.0f;
+  if (tid < 64) {
+    ws[tid] = rb + tid < N ? w[rb + tid] : 0.0f;
+    wS[tid] = rb + tid >= wskip ? ws[tid] : 0.0f;
+    cs[tid] = (cen != nullptr && rb + tid < N) ? cen[rb + tid] : -1;
+  }
   __syncthreads();
   const int t2 = 2 * threadIdx.x;   // points rb + t2, rb + t2 + 1
   const float w0 = ws[t2], w1 = ws[t2 + 1];
+  const float ws0 = wS[t2], ws1 = wS[t2 + 1];
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
     const int col = cb + i;
     if (col >= cpb) continue;
     const float h0 = tile[t2][i], h1 = tile[t2 + 1][i];
-    const float v0 = w0 * h0, v1 = w1 * h1;
+    // the diagonal-part operator takes u = h - e_m on centred rows
+    const float v0 = ws0 * (cs[t2] == col ? h0 - 1.0f : h0);
+    const float v1 = ws1 * (cs[t2 + 1] == col ? h1 - 1.0f : h1);
     const __nv_bfloat162 hi = __floats2bfloat162_rn(v0, v1);
     const float2 fh = __bfloat1622float2(hi);
     const int64_t o = ((int64_t)blockIdx.x * cpb + col) * 64 + t2;
@@ -1468,7 +1646,7 @@ __global__ void k_weighted_hT(bf16* Ahi, bf16* Alo, bf16* AP, const float* Ha, c
     *reinterpret_cast<__nv_bfloat162*>(Alo + o) = __floats2bfloat162_rn(v0 - fh.x, v1 - fh.y);
     if (AP)
       *reinterpret_cast<__nv_bfloat162*>(AP + o) =
-          __floats2bfloat162_rn(v0 * (1.0f - h0), v1 * (1.0f - h1));
+          __floats2bfloat162_rn(w0 * h0 * (1.0f - h0), w1 * h1 * (1.0f - h1));
   }
 }
 
@@ -1789,6 +1967,85 @@ static int pow2_dim(int d) {
   return p;
 }
 
+// Confident rows of a mixed problem (h_m > 1/2): their class m (cen), the rows grouped by class
+// in row order (cen_off, cen_idx: a counting sort on the host, so every later per-class sum runs
+// in a fixed order) and the centred bf16 copies of h that the Hessian apply's two GEMMs take
+// instead of h (Ub row-major, UbT K-block-major).  A problem without confident rows keeps none
+// of this and runs exactly as before.
+// Labelled rows whose Hessian apply runs on CUDA cores (problems with confident rows; not
+// pooled ones): rows [0, lab_rows) take weight 0 in the tensor-core terms.
+static int64_t lab_rows(const firal_problem* P) {
+  return (P->n_cen > 0 && P->pt.Q == 0) ? P->m : 0;
+}
+
+static int32_t tc_prepare_centred(firal_problem* P, int cpb2) {
+  cudaStream_t st = P->H->stream;
+  const int64_t N = P->N, Np = P->Np;
+  const int c = P->c;
+  P->n_cen = 0;
+  // N class indices, then (8-byte aligned) the count of confident rows
+  const int64_t cnt_off = (N + 1) / 2 * 2;
+  FIRAL_TRY(P->cen.ensure((size_t)(cnt_off + 2) * sizeof(int)));
+  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(P->cen.as<int>() + cnt_off);
+  FIRAL_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st));
+  {
+    ProfScope ps(st, PF_PREP);
+    count_launch();
+    k_row_top<<<(unsigned)((N * 32 + 255) / 256), 256, 0, st>>>(P->cen.as<int>(), cnt,
+                                                                P->Ha.as<float>(), N, c);
+  }
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  unsigned long long nconf = 0;
+  FIRAL_CUDA_TRY(cudaMemcpyAsync(&nconf, cnt, sizeof(nconf), cudaMemcpyDeviceToHost, st));
+  FIRAL_CUDA_TRY(cudaStreamSynchronize(st));
+  if (nconf == 0) {
+    P->cen.release();
+    return FIRAL_OK;
+  }
+  std::vector<int> cen(N);
+  FIRAL_CUDA_TRY(cudaMemcpyAsync(cen.data(), P->cen.p, (size_t)N * sizeof(int),
+                                 cudaMemcpyDeviceToHost, st));
+  FIRAL_CUDA_TRY(cudaStreamSynchronize(st));
+  std::vector<int> off(c + 1, 0);
+  int64_t nc = 0;
+  for (int64_t i = 0; i < N; ++i)
+    if (cen[i] >= 0) {
+      ++off[cen[i] + 1];
+      ++nc;
+    }
+  if (nc == 0) {
+    P->cen.release();
+    return FIRAL_OK;
+  }
+  if (nc > INT_MAX) return fail(FIRAL_ERR_UNSUPPORTED, "too many confident rows");
+  for (int k = 0; k < c; ++k) off[k + 1] += off[k];
+  std::vector<int> idx(nc), pos(off.begin(), off.end() - 1);
+  for (int64_t i = 0; i < N; ++i)
+    if (cen[i] >= 0) idx[pos[cen[i]]++] = (int)i;
+  FIRAL_TRY(P->cen_off.ensure((size_t)(c + 1) * sizeof(int)));
+  FIRAL_TRY(P->cen_idx.ensure((size_t)nc * sizeof(int)));
+  FIRAL_CUDA_TRY(cudaMemcpyAsync(P->cen_off.p, off.data(), (size_t)(c + 1) * sizeof(int),
+                                 cudaMemcpyHostToDevice, st));
+  FIRAL_CUDA_TRY(cudaMemcpyAsync(P->cen_idx.p, idx.data(), (size_t)nc * sizeof(int),
+                                 cudaMemcpyHostToDevice, st));
+  FIRAL_TRY(P->Ub.ensure((size_t)Np * P->cp * 2));
+  FIRAL_TRY(P->UbT.ensure((size_t)Np * cpb2 * 2));
+  const int64_t tot_h = Np * P->cp;
+  {
+    ProfScope ps(st, PF_PREP);
+    count_launch(2);
+    k_to_bf16_centred_pad<<<(unsigned)std::min<int64_t>((tot_h + 255) / 256, 1 << 20), 256, 0, st>>>(
+        P->Ub.as<bf16>(), P->Ha.as<float>(), P->cen.as<int>(), N, c, Np, P->cp);
+    k_block_transpose_bf16<<<dim3((unsigned)(Np / 32), (unsigned)(cpb2 / 32)), dim3(32, 8), 0, st>>>(
+        P->UbT.as<bf16>(), P->Ub.as<bf16>(), Np, P->cp, cpb2);
+  }
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  // the host vectors are read by the copies: wait before they go out of scope
+  FIRAL_CUDA_TRY(cudaStreamSynchronize(st));
+  P->n_cen = nc;
+  return FIRAL_OK;
+}
+
 int32_t tc_prepare(firal_problem* P) {
   cudaStream_t st = P->H->stream;
   if (P->d > 128) return fail(FIRAL_ERR_UNSUPPORTED, "mixed path supports d <= 128");
@@ -1818,6 +2075,7 @@ int32_t tc_prepare(firal_problem* P) {
   k_block_transpose_bf16<<<dim3((unsigned)(Np / 32), (unsigned)((P->dp + 31) / 32)), dim3(32, 8),
                            0, st>>>(P->Xb.as<bf16>() + tot_x, P->Xb.as<bf16>(), Np, P->dp, P->dp);
   FIRAL_CUDA_TRY(cudaGetLastError());
+  FIRAL_TRY(tc_prepare_centred(P, cpb2));
   // pair operand of the block sums (problem constant): Z = x (x) x on the pair triangle
   const int npairs = P->d * (P->d + 1) / 2;
   const int64_t npp = (npairs + b_cfg::BN - 1) / b_cfg::BN * b_cfg::BN;
@@ -1862,8 +2120,27 @@ static int32_t tc_apply_t(firal_problem* P, const float* w, const float* Sblk, c
                            P->D, P->pt);
   }
   FIRAL_CUDA_TRY(cudaGetLastError());
+  // confident rows: a_m = x . P~[:, m] for each, before the alpha-GEMM's epilogue needs it
+  const bool centred = P->n_cen > 0;
+  // with confident rows the labelled rows (weights 1 in Sigma_z) are applied on CUDA cores
+  const int64_t wskip = lab_rows(P);
+  const bool lab = wskip > 0 && w == (const float*)P->w_sig.p;
+  if (centred) {
+    FIRAL_TRY(P->cen_am.ensure((size_t)P->N * s * sizeof(float)));
+    FIRAL_TRY(P->cen_rho.ensure((size_t)P->N * s * sizeof(float)));
+    const size_t smem_am = (size_t)s * DP * sizeof(float);
+    if (smem_am > 48 * 1024)
+      FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_centre_am, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem_am));
+    ProfScope ps(st, PF_SPLIT);
+    count_launch();
+    k_centre_am<<<P->c, 256, smem_am, st>>>(P->cen_am.as<float>(), P->Pb.as<bf16>(),
+                                            P->Xb.as<bf16>(), P->cen_off.as<int>(),
+                                            P->cen_idx.as<int>(), s, NPART, DP, cp);
+    FIRAL_CUDA_TRY(cudaGetLastError());
+  }
   CUtensorMap mH, mP;
-  FIRAL_TRY(make_map(&mH, P->Hb.p, Np, cp, BM, BK, true));
+  FIRAL_TRY(make_map(&mH, centred ? P->Ub.p : P->Hb.p, Np, cp, BM, BK, true));
   FIRAL_TRY(make_map(&mP, P->Pb.p, prow_p, cp, BN, BK, true));
   const int n_mt = (int)(Np / BM), n_nt = (int)(prow_p / BN);
   const int sms = P->sms;
@@ -1882,7 +2159,10 @@ static int32_t tc_apply_t(firal_problem* P, const float* w, const float* Sblk, c
   count_launch();
   k_tc_alpha<DP, 0, NPART><<<grid, 256, SMEM, st>>>(mH, mP, mH, P->Xb.as<bf16>(), w, P->walpha.as<bf16>(),
                                              nullptr, P->N, Np, s, cp / BK, n_mt, n_nt, 0, P->d,
-                                             tc_error_word(P), P->kr_alpha.as<int2>());
+                                             tc_error_word(P), P->kr_alpha.as<int2>(), nullptr,
+                                             0, 0, 0.0f, centred ? P->cen.as<int>() : nullptr,
+                                             centred ? P->cen_am.as<float>() : nullptr,
+                                             centred ? P->cen_rho.as<float>() : nullptr, wskip);
   }
   FIRAL_CUDA_TRY(cudaGetLastError());
   // D-GEMM
@@ -1917,11 +2197,13 @@ static int32_t tc_apply_t(firal_problem* P, const float* w, const float* Sblk, c
     const int64_t kbps = (kL + splits - 1) / splits;
     splits = (int)((kL + kbps - 1) / kbps);
     P->tune_used.dterm_splits = splits;
-    FIRAL_TRY(P->Dpart.ensure((size_t)splits * P->c * sd * sizeof(float)));
+    // more partial blocks: the class-m part of the centred rows, the labelled rows
+    const int extra = (centred ? 1 : 0) + (lab ? 1 : 0);
+    FIRAL_TRY(P->Dpart.ensure((size_t)(splits + extra) * P->c * sd * sizeof(float)));
     CUtensorMap mHT, mXT, mAT;
     const uint64_t cpb2 = (uint64_t)n_mt2 * d_cfg::MT * d_cfg::BM;
-    FIRAL_TRY(make_map(&mHT, P->HbT.p, (uint64_t)kb_total * cpb2, d_cfg::BK, d_cfg::BM, d_cfg::BK,
-                       true));
+    FIRAL_TRY(make_map(&mHT, centred ? P->UbT.p : P->HbT.p, (uint64_t)kb_total * cpb2, d_cfg::BK,
+                       d_cfg::BM, d_cfg::BK, true));
     FIRAL_TRY(make_map(&mXT, P->Xb.as<bf16>() + Np * DP, (uint64_t)kb_total * DP, d_cfg::BK, DP,
                        d_cfg::BK, false));
     FIRAL_TRY(make_map(&mAT, P->walpha.p, (uint64_t)kb_total * sp16, d_cfg::BK, PPN, d_cfg::BK,
@@ -1937,7 +2219,31 @@ static int32_t tc_apply_t(firal_problem* P, const float* w, const float* Sblk, c
                                              P->kbL);
     }
     FIRAL_CUDA_TRY(cudaGetLastError());
-    FIRAL_TRY(combine_f32(P, Sblk, V, splits, s, out, nullptr, P->vmean.as<float>()));
+    if (centred) {
+      ProfScope ps(st, PF_COMBINE);
+      count_launch();
+      k_centre_termc<<<P->c, 256, 0, st>>>(P->Dpart.as<float>() + (size_t)splits * P->c * sd,
+                                           P->cen_rho.as<float>(), P->Xb.as<bf16>(),
+                                           P->cen_off.as<int>(), P->cen_idx.as<int>(), s, P->d, DP);
+      FIRAL_CUDA_TRY(cudaGetLastError());
+    }
+    if (lab) {
+      FIRAL_TRY(P->cen_lab.ensure((size_t)P->m * s * P->c * sizeof(float)));
+      const size_t smem_g = (size_t)P->c * sizeof(float);
+      if (smem_g > 48 * 1024)
+        FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_lab_gamma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem_g));
+      ProfScope ps(st, PF_COMBINE);
+      count_launch(2);
+      k_lab_gamma<<<dim3((unsigned)P->m, s), 256, smem_g, st>>>(
+          P->cen_lab.as<float>(), V, P->vmean.as<float>(), P->Xa.as<float>(), P->Ha.as<float>(),
+          w, s, P->c, P->d, P->D);
+      k_lab_scatter<<<P->c, 256, 0, st>>>(
+          P->Dpart.as<float>() + (size_t)(splits + (centred ? 1 : 0)) * P->c * sd,
+          P->cen_lab.as<float>(), P->Xa.as<float>(), P->m, s, P->c, P->d);
+      FIRAL_CUDA_TRY(cudaGetLastError());
+    }
+    FIRAL_TRY(combine_f32(P, Sblk, V, splits + extra, s, out, nullptr, P->vmean.as<float>()));
     ProfScope ps(st, PF_COMBINE);
     count_launch(2);
     k_class_mean<<<s * Qe, 1024, 0, st>>>(out, s, P->c, P->d, P->D, P->qmean.as<float>(), P->pt);
@@ -2012,7 +2318,8 @@ int32_t tc_syrk_blocks(firal_problem* P, const void* wv, double lamS, void* outS
     ProfScope ps(st, PF_SYRK);
     count_launch(outP ? 3 : 2);
     k_weighted_hT<<<dim3((unsigned)(Np / 64), (unsigned)(cpb / 32)), dim3(32, 8), 0, st>>>(
-        Ahi, Alo, outP ? AP : nullptr, P->Ha.as<float>(), w, P->N, c, Np, cpb);
+        Ahi, Alo, outP ? AP : nullptr, P->Ha.as<float>(), w, P->N, c, Np, cpb,
+        P->n_cen > 0 ? P->cen.as<int>() : nullptr, lab_rows(P));
     FIRAL_CUDA_TRY(cudaGetLastError());
     // blocked operands as 2-D tensors of 64-point rows: tile (kb, row block) = 16 KB run
     CUtensorMap mA0, mA1, mA2, mZ0, mZ1;
@@ -2330,7 +2637,10 @@ static int32_t tc_apply_dp(firal_problem* P, const void* w, const void* Sblk, co
 
 int32_t tc_hessian_apply(firal_problem* P, const void* w, const void* Sblk, const void* V, int s,
                          void* out, double* pq, double lam_null) {
-  if (P->prec == FIRAL_MIXED_BF16_FAST) return tc_apply_dp<1>(P, w, Sblk, V, s, out, pq, lam_null);
+  // the bf16 direction's rounding enters only the low-rank term; with confident rows that term
+  // is as large as the result, so such problems take the hi + lo direction in both modes
+  if (P->prec == FIRAL_MIXED_BF16_FAST && P->n_cen == 0)
+    return tc_apply_dp<1>(P, w, Sblk, V, s, out, pq, lam_null);
   return tc_apply_dp<2>(P, w, Sblk, V, s, out, pq, lam_null);
 }
 

@@ -1,0 +1,77 @@
+"""The ImageNet class count (d = 64, c = 1000, s = 16 probes, 10 PCG iterations per solve) on
+a reduced pool of 20,000 points plus 1,000 labelled ones, against the FP64 oracle (needs a
+GPU).
+
+The oracle values are stored in ``golden/imagenet_classes_n20k.npz`` by
+``golden/make_imagenet_classes.py``, which calls only ``oracle/`` (the oracle takes several
+minutes at this size).  The test regenerates the inputs from the same seed and checks their
+fingerprint against the stored one before comparing:
+
+* f^ of two MD iterations of Algorithm 2 (paper estimator, eq. 11) and the z they reach;
+* the autograd gradient d f^/d z (the exact derivative of the same-probe estimate) at the
+  uniform start, element by element over all 20,000 points;
+
+in the bench's precision (bf16 CG direction), in the hi/lo-direction mixed precision and in
+the plain FP32 form.  The target is the stated accuracy bar: 1e-3 relative.
+"""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2409_07392_gb300.synth import make_problem  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "imagenet_classes_n20k.npz")
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def relerr(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.fixture(scope="module")
+def case():
+    from paper_2409_07392_gb300 import api, build
+    build.build()
+    ref = np.load(GOLD)
+    n, d, c, s, T, iters = (int(v) for v in ref["shape"])
+    data_seed, probe_seed = (int(v) for v in ref["seeds"])
+    p = make_problem(n, d, c, seed=data_seed, x_dtype="bf16", h_dtype="float32", m_o=c)
+    fp = np.array([p.X.astype(np.float64).sum(), p.h.astype(np.float64).sum(),
+                   p.Xo.astype(np.float64).sum(), p.ho.astype(np.float64).sum(),
+                   (p.h.astype(np.float64) ** 2).sum()])
+    np.testing.assert_allclose(fp, ref["fingerprint"], rtol=1e-12,
+                               err_msg="regenerated inputs differ from the stored oracle's")
+    H = api.Handle()
+    return api, H, p, ref, dict(n=n, d=d, c=c, s=s, T=T, iters=iters, seed=probe_seed,
+                                budget=float(ref["budget"]))
+
+
+@pytest.mark.parametrize("precision", ["mixed_fast", "mixed", "fp32"])
+def test_c1000_fhat_z_and_gradient_vs_oracle(case, precision):
+    api, H, p, ref, k = case
+    prob = api.Problem(H, dev(p.X).to(torch.bfloat16), dev(p.h), dev(p.Xo).to(torch.bfloat16),
+                       dev(p.ho), p.lam, precision=precision)
+    z = torch.full((k["n"],), k["budget"] / k["n"], dtype=torch.float32, device="cuda")
+    z0 = z.clone()
+    opts = prob.relax_opts(s=k["s"], T=k["T"], fixed_iters=k["iters"], seed=k["seed"])
+    fh = [prob.relax_step(opts, t, k["budget"], z)["fhat"] for t in range(k["T"])]
+    g = prob.objective_bwd(z0, k["seed"], 0, k["s"], fixed_iters=k["iters"]).cpu().numpy()
+    f_ag, _, _ = prob.objective_fwd(z0, k["seed"], 0, k["s"], fixed_iters=k["iters"],
+                                    keep=False)
+    prob.close()
+    ef = relerr(fh, ref["fhat"])
+    ez = relerr(z.cpu().numpy(), ref["z"])
+    eg = relerr(g, ref["g_autograd"])
+    efa = abs(f_ag - float(ref["fhat_autograd"][0])) / abs(float(ref["fhat_autograd"][0]))
+    print(f"c=1000 {precision}: fhat {ef:.2e}  z {ez:.2e}  dfdz {eg:.2e}  fhat(fwd) {efa:.2e}")
+    assert ef < 1e-3 and ez < 1e-3 and eg < 1e-3 and efa < 1e-3
