@@ -53,6 +53,12 @@ def parse():
     ap.add_argument("--no-al", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--round-selections", type=int, default=20)
+    ap.add_argument("--replicas", action="store_true",
+                    help="N > 1: N independent problems instead of one row-sharded problem")
+    ap.add_argument("--data-backend", default="nccl", choices=["nccl", "gloo"],
+                    help="row-sharded runs: device allreduces over NCCL, or staged through host "
+                         "memory over gloo (several ranks may then share one GPU: a functional "
+                         "check, not a measurement)")
     return ap.parse_args()
 
 
@@ -70,13 +76,17 @@ def describe(cfg, args):
 
 
 # ------------------------------------------------------------------------------ distributed
-def dist_setup(args):
+def dist_setup(args, data_backend=False):
+    """Join the job's process group.  Host tensors (barrier, max over ranks) go over gloo;
+    with ``data_backend`` device tensors (the row-sharded MD iteration's allreduces) go over
+    NCCL, unless --data-backend gloo stages them through host memory."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("gloo")
+        nccl = data_backend and getattr(args, "data_backend", "nccl") == "nccl"
+        dist.init_process_group("cpu:gloo,cuda:nccl" if nccl else "gloo")
     return world, rank, local
 
 
@@ -584,31 +594,41 @@ def run_ours(args):
     from paper_2409_07392_gb300 import _lib, api, build
     from paper_2409_07392_gb300.synth import make_problem
 
-    world, rank, local = dist_setup(args)
-    torch.cuda.set_device(local)
+    world0 = int(os.environ.get("WORLD_SIZE", "1"))
+    # N > 1: one pool row-sharded over the ranks (the paper's decomposition; strong scaling),
+    # unless --replicas asks for N independent problems (weak scaling)
+    shard = world0 > 1 and not args.replicas
+    world, rank, local = dist_setup(args, data_backend=shard)
+    torch.cuda.set_device(local % torch.cuda.device_count())
     build.build()
     lib = _lib.load()
     cfg = workload(args)
     n, d, c, s, b = cfg["n"], cfg["d"], cfg["c"], cfg["s"], float(cfg["b"])
-    p = make_problem(n, d, c, seed=rank, x_dtype=cfg["x_dtype"], h_dtype=cfg["h_dtype"],
-                     anisotropic=cfg.get("anisotropic", False), zipf=cfg.get("zipf"))
+    p = make_problem(n, d, c, seed=0 if shard else rank, x_dtype=cfg["x_dtype"],
+                     h_dtype=cfg["h_dtype"], anisotropic=cfg.get("anisotropic", False),
+                     zipf=cfg.get("zipf"))
+    lo, hi = api.shard_rows(n, world, rank) if shard else (0, n)
+    n_loc = hi - lo
     xdt = torch.bfloat16 if p.x_bf16 else torch.float32
 
     def host(a, dt=None):
         t = torch.from_numpy(np.ascontiguousarray(a))
         return (t.to(dt) if dt is not None else t).pin_memory()
 
-    Xh, hh, Xoh, hoh = host(p.X, xdt), host(p.h), host(p.Xo, xdt), host(p.ho)
+    Xh, hh, Xoh, hoh = host(p.X[lo:hi], xdt), host(p.h[lo:hi]), host(p.Xo, xdt), host(p.ho)
     X, h, Xo, ho = (t.cuda(non_blocking=True) for t in (Xh, hh, Xoh, hoh))
     H = api.Handle()
     prob = api.Problem(H, X, h, Xo, ho, p.lam, precision=args.precision)
+    if shard:
+        prob.set_comm(rank, world, api.torch_allreduce())
     # launch tuning: the autotuner times split-count candidates on MD iterations (outside the
-    # timed region) and leaves the fastest set on the problem
+    # timed region) and leaves the fastest set on the problem (not on a sharded problem: every
+    # rank must make the same allreduce calls)
     tuning = None
-    if args.precision.startswith("mixed") and not args.no_autotune:
+    if args.precision.startswith("mixed") and not args.no_autotune and not shard:
         from paper_2409_07392_gb300 import autotune
         tuning = autotune.tune_problem(prob, s, cg_iters=args.cg_iters, budget=b, reps=2)
-    z = torch.full((n,), b / n, dtype=prob.vdt, device="cuda")
+    z = torch.full((n_loc,), b / n, dtype=prob.vdt, device="cuda")
     opts = prob.relax_opts(s=s, T=args.warmup + args.steps, fixed_iters=args.cg_iters, seed=1)
     for t in range(args.warmup):
         prob.relax_step(opts, t, b, z, stats=False)
@@ -641,13 +661,15 @@ def run_ours(args):
     kernels = {lib.firal_profile_name(i).decode(): {"ms_per_step": ms_k[i] / args.steps,
                                                    "groups_per_step": calls_k[i] / args.steps}
                for i in range(ncls) if calls_k[i] > 0}
-    value = world * args.steps / (ms_max / 1000.0)
+    # replicas: every rank ran its own problem; sharded: the ranks ran one problem together
+    value = (1 if shard else world) * args.steps / (ms_max / 1000.0)
 
     # ---------------- roofline of the dominant kernel class
     pk, pk_src = peaks()
     top = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
-    n_all = n + p.Xo.shape[0]
-    fl = algorithmic_flops(top, cfg, n_all, s)
+    n_all = n_loc + p.Xo.shape[0]          # rows this rank's kernels run over
+    cfg_loc = dict(cfg, n=n_loc)
+    fl = algorithmic_flops(top, cfg_loc, n_all, s)
     roof = None
     if fl is not None:
         per_launch_ms = kernels[top]["ms_per_step"] / kernels[top]["groups_per_step"]
@@ -681,7 +703,7 @@ def run_ours(args):
         n_pad = (n_all + 127) // 128 * 128
         for k in ("apply_alpha", "apply_dterm", "syrk_blocks", "quad_forms"):
             kk = kernels.get(k)
-            f_k = algorithmic_flops(k, cfg, n_all, s)
+            f_k = algorithmic_flops(k, cfg_loc, n_all, s)
             if not kk or f_k is None or kk["ms_per_step"] <= 0:
                 continue
             units = kk["groups_per_step"] if k.startswith("apply_") else 1.0
@@ -698,12 +720,14 @@ def run_ours(args):
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "higher_is_better": True, "scaling": "strong" if shard else "weak",
+            "vs_baseline": None,
             "dtype": {"mixed": "bf16", "mixed_fast": "bf16", "fp32": "f32",
                       "fp64": "f64"}[args.precision],
             "data": "synthetic",
             "config": {"workload": describe(cfg, args), "precision": args.precision,
-                       "parallelism": "replicas" if world > 1 else "single",
+                       "parallelism": (f"rows{world} (pool rows sharded, allreduce per apply)"
+                                       if shard else "replicas" if world > 1 else "single"),
                        "l2": "inputs larger than L2 (h alone is %.1f GB)" % (p.h.nbytes / 1e9),
                        "tuning": ({k: tuning[k] for k in ("dterm_splits", "bsum_splits",
                                                           "sm_budget", "ms", "default_ms",
@@ -718,13 +742,27 @@ def run_ours(args):
 
     # ---------------- end to end through the public API with host (pinned) buffers
     if not args.no_e2e:
-        zh = torch.full((n,), b / n, dtype=prob.vdt).pin_memory()
+        zh = torch.full((n_loc,), b / n, dtype=prob.vdt).pin_memory()
         k_e2e = max(1, min(args.steps, 10))   # every call timed and listed in ms_per_step
 
         def e2e_step(t):
-            zout, _ = api.relax(Xh, hh, Xoh, hoh, p.lam, b, s=s, T=1, fixed_iters=args.cg_iters,
-                                seed=1 + t, precision=args.precision, z0=zh, handle=H)
-            zh.copy_(zout)
+            if not shard:
+                zout, _ = api.relax(Xh, hh, Xoh, hoh, p.lam, b, s=s, T=1,
+                                    fixed_iters=args.cg_iters, seed=1 + t,
+                                    precision=args.precision, z0=zh, handle=H)
+                zh.copy_(zout)
+                return
+            # row-sharded: this rank's slice to the device, a problem joined to the group, one
+            # MD iteration, its z slice back
+            tX, th = Xh.to("cuda", non_blocking=True), hh.to("cuda", non_blocking=True)
+            tXo, tho = Xoh.to("cuda", non_blocking=True), hoh.to("cuda", non_blocking=True)
+            pr = api.Problem(H, tX, th, tXo, tho, p.lam, precision=args.precision)
+            pr.set_comm(rank, world, api.torch_allreduce())
+            zd = zh.to("cuda", non_blocking=True)
+            pr.relax_step(pr.relax_opts(s=s, T=1, fixed_iters=args.cg_iters, seed=1 + t), 0, b,
+                          zd, stats=False)
+            zh.copy_(zd.cpu())
+            pr.close()
         e2e_step(0)                                  # untimed warm-up call
         barrier(world)
         t0 = time.perf_counter()
@@ -735,7 +773,8 @@ def run_ours(args):
             per_step.append(1000.0 * (time.perf_counter() - ts))
         dt = max_over_ranks(time.perf_counter() - t0, world)
         bi = sum(t.numel() * t.element_size() for t in (Xh, hh, Xoh, hoh, zh))
-        line["e2e"] = {"value": world * k_e2e / dt, "unit": UNIT, "h2d_bytes_per_step": bi,
+        line["e2e"] = {"value": (1 if shard else world) * k_e2e / dt, "unit": UNIT,
+                       "h2d_bytes_per_step": bi,
                        "d2h_bytes_per_step": zh.numel() * zh.element_size(), "steps": k_e2e,
                        "warmup": 1, "ms_per_step": per_step,
                        "note": "each step is one api.relax(T=1) call on pinned host tensors: "
@@ -743,6 +782,8 @@ def run_ours(args):
         # diagnostic only (not the e2e value): the same call split into its H2D copies, the
         # library call on the device copies and the D2H of z, with the collector's counts
         try:
+            if shard:
+                raise RuntimeError("not measured on a row-sharded run")
             import gc
             parts = []
             for t in range(3):
@@ -767,7 +808,7 @@ def run_ours(args):
         except Exception as exc:
             line["e2e_breakdown"] = {"error": str(exc)[:300]}
 
-    if rank == 0:
+    if rank == 0 and world == 1:
         # ---------------- the paper's timing setting (m = 50) and the tolerance mode
         if not args.no_variants:
             try:
@@ -845,6 +886,7 @@ def run_ours(args):
         # ---------------- CPU oracle baseline
         if not args.no_cpu:
             line["cpu_baseline"] = cpu_baseline(cfg, args.cg_iters, args.cpu_seconds)
+    if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

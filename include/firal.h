@@ -55,7 +55,8 @@ typedef enum {
   FIRAL_ERR_NONFINITE = -5,        /* NaN or Inf in the objective or gradient               */
   FIRAL_ERR_TIMEOUT = -6,          /* a bounded device-side wait gave up                      */
   FIRAL_ERR_NOMEM = -7,            /* workspace allocation failed                             */
-  FIRAL_ERR_UNSUPPORTED = -8       /* shape or precision the library does not support       */
+  FIRAL_ERR_UNSUPPORTED = -8,      /* shape or precision the library does not support       */
+  FIRAL_ERR_COMM = -9              /* the allreduce callback of a row-sharded problem failed */
 } firal_status;
 
 typedef enum {
@@ -419,6 +420,44 @@ int32_t firal_problem_get_tuning(firal_problem* problem, firal_tuning* out);
 /* Default tuning of every problem created on the handle afterwards, including the pooled
  * problems firal_batched_relax builds internally. */
 int32_t firal_set_default_tuning(firal_handle* handle, const firal_tuning* tuning);
+
+/* ---------------------------------------------------------------- row sharding (Section 3.3) */
+
+/* The paper's data decomposition: each process (one GPU) holds a contiguous slice of the pool's
+ * rows (x_i, h_i, z_i), every process holds the same labelled set, probes and dc x s vectors,
+ * and the per-process partial sums are added across processes where the method sums over
+ * points.  A problem joins such a group through firal_problem_set_comm; the library calls the
+ * caller's allreduce at these points:
+ *   - once per Hessian apply (Sigma_z V or H_p V): the d c x s partial, before the null-space
+ *     projection and the CG dot products (vec type, sum);
+ *   - once per MD iteration: the c preconditioner blocks (double) of eq. 13, before their
+ *     Cholesky factorisation (sum);
+ *   - the mirror-descent scalars: ||g||_inf (double, max) and sum_i z_i exp(-beta g_i)
+ *     (double, sum), so that z stays on the budget simplex over all processes;
+ *   - at set-up, the pool size (double, sum), so that H_p = (1/n) sum_pool H_i uses the total n.
+ * The labelled rows and lambda count once, on rank 0.  Every process must make the same calls
+ * in the same order.  Round, Exact-FIRAL and pooled problems do not take a communicator.
+ *
+ * allreduce(buf, count, dtype, op, stream, user): in-place allreduce of `count` elements of
+ * `dtype` (FIRAL_DT_F32 or FIRAL_DT_F64) at device pointer buf, op 0 = sum, 1 = max; the data is
+ * ready once the work enqueued on `stream` (the handle's cudaStream_t as void*) completes, and
+ * the result must be in place for work enqueued on `stream` after the callback returns (an
+ * NCCL allreduce on that stream, or a host-staged exchange after a stream synchronisation,
+ * both qualify).  It returns 0 on success; anything else ends the library call with
+ * FIRAL_ERR_COMM. */
+typedef int32_t (*firal_allreduce_fn)(void* buf, int64_t count, int32_t dtype, int32_t op,
+                                      void* stream, void* user);
+
+typedef struct {
+  int32_t rank;                 /* this process, 0 .. world - 1                     */
+  int32_t world;                /* number of processes; 1 (or a NULL comm) = alone */
+  firal_allreduce_fn allreduce; /* see above; may be NULL only when world == 1      */
+  void* user;                   /* passed back to allreduce                         */
+} firal_comm;
+
+/* Join (comm->world > 1) or leave (NULL or world == 1) a row-sharded group.  Calls allreduce
+ * once (the pool size) and synchronises.  FIRAL_ERR_UNSUPPORTED for pooled problems. */
+int32_t firal_problem_set_comm(firal_problem* problem, const firal_comm* comm);
 
 /* ---------------------------------------------------------------- active learning (Section 5) */
 

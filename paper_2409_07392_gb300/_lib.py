@@ -14,9 +14,14 @@ FIRAL_FP64, FIRAL_FP32, FIRAL_MIXED_BF16, FIRAL_MIXED_BF16_FAST = 0, 1, 2, 3
 FIRAL_DT_F64, FIRAL_DT_F32, FIRAL_DT_BF16 = 0, 1, 2
 STATUS = {0: "FIRAL_OK", -1: "FIRAL_ERR_ARG", -2: "FIRAL_ERR_CUDA", -3: "FIRAL_ERR_NOT_SPD",
           -4: "FIRAL_ERR_CG_NOT_CONVERGED", -5: "FIRAL_ERR_NONFINITE", -6: "FIRAL_ERR_TIMEOUT",
-          -7: "FIRAL_ERR_NOMEM", -8: "FIRAL_ERR_UNSUPPORTED"}
+          -7: "FIRAL_ERR_NOMEM", -8: "FIRAL_ERR_UNSUPPORTED", -9: "FIRAL_ERR_COMM"}
 (FIRAL_OK, FIRAL_ERR_ARG, FIRAL_ERR_CUDA, FIRAL_ERR_NOT_SPD, FIRAL_ERR_CG_NOT_CONVERGED,
- FIRAL_ERR_NONFINITE, FIRAL_ERR_TIMEOUT, FIRAL_ERR_NOMEM, FIRAL_ERR_UNSUPPORTED) = range(0, -9, -1)
+ FIRAL_ERR_NONFINITE, FIRAL_ERR_TIMEOUT, FIRAL_ERR_NOMEM, FIRAL_ERR_UNSUPPORTED,
+ FIRAL_ERR_COMM) = range(0, -10, -1)
+FIRAL_REDUCE_SUM, FIRAL_REDUCE_MAX = 0, 1
+
+# int32 allreduce(void* buf, int64 count, int32 dtype, int32 op, void* stream, void* user)
+ALLREDUCE_FN = ctypes.CFUNCTYPE(c_int32, c_void_p, c_int64, c_int32, c_int32, c_void_p, c_void_p)
 
 
 class FiralPool(ctypes.Structure):
@@ -57,6 +62,11 @@ class FiralStepStats(ctypes.Structure):
 
 class FiralRelaxStats(ctypes.Structure):
     _fields_ = [("iters_done", c_int32), ("fhat_last", c_double), ("cg_iters_total", c_int32)]
+
+
+class FiralComm(ctypes.Structure):
+    _fields_ = [("rank", c_int32), ("world", c_int32), ("allreduce", ALLREDUCE_FN),
+                ("user", c_void_p)]
 
 
 class FiralRoundOpts(ctypes.Structure):
@@ -126,6 +136,7 @@ SIGNATURES = [
     ("firal_problem_set_tuning", c_int32, [c_void_p, POINTER(FiralTuning)]),
     ("firal_problem_get_tuning", c_int32, [c_void_p, POINTER(FiralTuning)]),
     ("firal_set_default_tuning", c_int32, [c_void_p, POINTER(FiralTuning)]),
+    ("firal_problem_set_comm", c_int32, [c_void_p, POINTER(FiralComm)]),
     ("firal_lr_probs", c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_int64, c_int32,
                                  c_int32, c_int32, c_void_p]),
     ("firal_lr_fit", c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_int64, c_int32, c_int32,

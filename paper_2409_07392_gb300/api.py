@@ -97,6 +97,45 @@ class Handle:
         return nu.value
 
 
+class _CudaArray:
+    """A device buffer owned by the library, seen by torch without a copy."""
+
+    def __init__(self, ptr, count, dtype):
+        typestr = {torch.float32: "<f4", torch.float64: "<f8"}[dtype]
+        self.__cuda_array_interface__ = {"shape": (count,), "typestr": typestr,
+                                         "data": (ptr, False), "version": 3, "strides": None,
+                                         "stream": None}
+
+
+def _device_view(ptr, count, dtype, device):
+    return torch.as_tensor(_CudaArray(ptr, count, dtype), device=device)
+
+
+def torch_allreduce(group=None):
+    """An allreduce over a torch.distributed process group for ``Problem.set_comm``.  With
+    NCCL the device tensor is reduced in place on torch's current stream (the library's); with
+    gloo it is staged through host memory."""
+    import torch.distributed as dist
+
+    def reduce(t, op):
+        rop = dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM
+        if t.is_cuda and "nccl" not in str(dist.get_backend(group)):
+            h = t.cpu()
+            dist.all_reduce(h, op=rop, group=group)
+            t.copy_(h)
+        else:
+            dist.all_reduce(t, op=rop, group=group)
+    return reduce
+
+
+def shard_rows(n: int, world: int, rank: int):
+    """Contiguous slice [start, stop) of n pool rows held by ``rank`` of ``world`` processes
+    (sizes differ by at most one; the first n % world ranks hold one more)."""
+    base, extra = divmod(n, world)
+    start = rank * base + min(rank, extra)
+    return start, start + base + (1 if rank < extra else 0)
+
+
 def _pool(X, h):
     return L.FiralPool(ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(h.data_ptr()), X.shape[0],
                        X.shape[1], h.shape[1], _dt(X), _dt(h))
@@ -256,6 +295,28 @@ class Problem:
                                              ctypes.byref(o), _ptr(sel), crit,
                                              ctypes.byref(best)))
         return sel, list(crit), best.value
+
+    # ---- row sharding (the paper's data decomposition over processes, Section 3.3)
+    def set_comm(self, rank: int, world: int, allreduce=None):
+        """Join a row-sharded group: this problem holds this process's slice of the pool, and
+        ``allreduce(tensor, op)`` (in place, op "sum" or "max"; see ``torch_allreduce``) adds
+        the partial sums over points across the group.  ``world == 1`` leaves the group."""
+        if world > 1 and allreduce is None:
+            raise ValueError("a row-sharded problem needs an allreduce")
+        dtypes = {L.FIRAL_DT_F32: torch.float32, L.FIRAL_DT_F64: torch.float64}
+        device = self.device
+
+        def cb(ptr, count, dtype, op, stream, user):
+            try:
+                t = _device_view(ptr, int(count), dtypes[dtype], device)
+                allreduce(t, "max" if op == L.FIRAL_REDUCE_MAX else "sum")
+                return 0
+            except Exception as exc:   # reported as FIRAL_ERR_COMM; no exception crosses the ABI
+                self.comm_error = exc
+                return 1
+        self._comm_cb = L.ALLREDUCE_FN(cb) if world > 1 else L.ALLREDUCE_FN()
+        comm = L.FiralComm(int(rank), int(world), self._comm_cb, None)
+        self._chk(self.lib.firal_problem_set_comm(self._p, ctypes.byref(comm)))
 
     # ---- launch tuning (see autotune.py)
     def set_tuning(self, dterm_splits=0, bsum_splits=0, sm_budget=0):

@@ -239,12 +239,20 @@ int32_t read_flags(firal_handle* H) {
 
 int32_t* not_spd_flag(firal_handle* H) { return &H->flags.as<DevFlags>()->not_spd; }
 
+// lambda of H_o = sum_labelled H_i + lambda I counts once over a row-sharded group (rank 0)
+double lam_r(const firal_problem* P) { return P->comm.rank == 0 ? P->lambda : 0.0; }
+
 // Hessian apply dispatch (tensor cores for FIRAL_MIXED_BF16)
 int32_t apply(firal_problem* P, const void* w, const void* Sblk, const void* V, int s, void* out,
               double* pq) {
+  // (the tensor-core apply adds the partials of a row-sharded group itself, before its
+  // null-space projection; lambda_N of that projection acts on the summed result)
   if (is_mixed(P->prec))
     return tc_hessian_apply(P, w, Sblk, V, s, out, pq, w == P->w_sig.p ? P->lambda : 0.0);
-  return hessian_apply_simt(P, w, Sblk, V, s, out, pq);
+  if (!sharded(P)) return hessian_apply_simt(P, w, Sblk, V, s, out, pq);
+  FIRAL_TRY(hessian_apply_simt(P, w, Sblk, V, s, out, nullptr));
+  FIRAL_TRY(shard_allreduce(P, out, (int64_t)s * P->D, P->dbl ? FIRAL_DT_F64 : FIRAL_DT_F32, 0));
+  return pq ? block_dots(P, V, out, s, pq) : FIRAL_OK;
 }
 
 int32_t quad(firal_problem* P, const void* A, const void* B, int s, double scale, void* g) {
@@ -266,8 +274,13 @@ int32_t setup_sigma(firal_problem* P, const void* z, bool want_precond) {
     FIRAL_CUDA_TRY(cudaMemcpyAsync((char*)P->w_sig.p + P->m * vsize(P), z, P->n * vsize(P),
                                    cudaMemcpyDeviceToDevice, st));
   }
-  FIRAL_TRY(blocks(P, P->w_sig.p, P->lambda, P->S_sig.p, P->lambda,
+  FIRAL_TRY(blocks(P, P->w_sig.p, lam_r(P), P->S_sig.p, lam_r(P),
                    want_precond ? P->Pblk.as<double>() : nullptr));
+  // a row-sharded group sums the preconditioner blocks of eq. 13 over all rows; the
+  // diagonal-part operator S stays this rank's own (each rank's apply adds S_rank V to its
+  // partial, and the partials are summed)
+  if (sharded(P) && want_precond)
+    FIRAL_TRY(shard_allreduce(P, P->Pblk.p, (int64_t)P->c * P->d * P->d, FIRAL_DT_F64, 0));
   if (want_precond)
     FIRAL_TRY(chol_inv(P->dbl, P->Pblk.as<double>(), P->c, P->d, P->Minv.p, nullptr, nullptr,
                        not_spd_flag(P->H), st));
@@ -559,6 +572,7 @@ int32_t relax_step_impl(firal_problem* P, const firal_relax_opts* o, int32_t t, 
   // lines 10-11: MD update on the budget simplex (in the pool part of w_sig), then copy out
   void* zdev = (char*)P->w_sig.p + P->m * vsize(P);
   if (P->pt.Q) FIRAL_TRY(md_step_pooled(P, zdev, P->g.p, o->beta0, st));   // per-pool simplex
+  else if (sharded(P)) FIRAL_TRY(md_step_sharded(P, zdev, P->g.p, budget, o->beta0, red, st));
   else FIRAL_TRY(md_step_simt(P->dbl, zdev, P->g.p, P->n, budget, o->beta0, red, st));
   FIRAL_CUDA_TRY(cudaMemcpyAsync(z, zdev, P->n * vsize(P), cudaMemcpyDeviceToDevice, st));
   if (device_t) FIRAL_TRY(tick(P->tdev.as<int64_t>(), st));
@@ -694,6 +708,7 @@ int32_t round_chain(firal_problem* P, const RoundSetup& rs, int32_t b, const fir
 int32_t round_impl(firal_problem* P, const void* zr, int32_t b, const firal_round_opts* o,
                    int32_t* sel, firal_round_stats* stats) {
   if (!P || !zr || !sel) return fail(FIRAL_ERR_ARG, "problem, z and selected_out must be non-null");
+  if (sharded(P)) return fail(FIRAL_ERR_UNSUPPORTED, "Round does not take a row-sharded problem");
   if (b < 1 || b > P->n) return fail(FIRAL_ERR_ARG, "budget must be in [1, n]");
   if (P->dbl && P->d > 90) return fail(FIRAL_ERR_UNSUPPORTED, "FP64 Round supports d <= 90");
   RoundSetup rs;
@@ -1121,6 +1136,7 @@ int32_t round_sweep_impl(firal_problem* P, const void* zr, int32_t b, const doub
   for (int e = 0; e < neta; ++e)
     if (!(etas[e] > 0)) return fail(FIRAL_ERR_ARG, "every eta must be > 0");
   if (b < 1 || b > P->n) return fail(FIRAL_ERR_ARG, "budget must be in [1, n]");
+  if (sharded(P)) return fail(FIRAL_ERR_UNSUPPORTED, "Round does not take a row-sharded problem");
   if (P->dbl && P->d > 90) return fail(FIRAL_ERR_UNSUPPORTED, "FP64 Round supports d <= 90");
   firal_round_opts oe = o ? *o : firal_round_opts{0.0, 1, P->prec};
   // the eta-independent set-up once, then one chain per eta
@@ -1156,6 +1172,7 @@ const char* firal_status_string(int32_t s) {
     case FIRAL_ERR_TIMEOUT: return "FIRAL_ERR_TIMEOUT";
     case FIRAL_ERR_NOMEM: return "FIRAL_ERR_NOMEM";
     case FIRAL_ERR_UNSUPPORTED: return "FIRAL_ERR_UNSUPPORTED";
+    case FIRAL_ERR_COMM: return "FIRAL_ERR_COMM";
     default: return "FIRAL_ERR_UNKNOWN";
   }
 }
@@ -1265,7 +1282,7 @@ int32_t firal_problem_destroy(firal_problem* P) {
                   &P->cgP, &P->cgQ, &P->cgZ, &P->cgcols, &P->cgpart1, &P->cgpart2, &P->V, &P->U,
                   &P->W, &P->HU, &P->g, &P->red, &P->zsave, &P->Xb, &P->Hb, &P->HbT, &P->Pb, &P->vmean, &P->qmean, &P->Aw, &P->Zp, &P->Hlo, &P->gq_ab,
                   &P->gq_m, &P->gq_part, &P->rtab, &P->rM, &P->tdev, &P->cen, &P->cen_off,
-                  &P->cen_idx, &P->Ub, &P->UbT, &P->cen_am, &P->cen_rho, &P->cen_lab}) {
+                  &P->cen_idx, &P->Ub, &P->UbT, &P->cen_am, &P->cen_rho, &P->cen_lab, &P->cen_items, &P->cen_part}) {
     if (synced) b->park();
     else b->release();
   }
@@ -1555,6 +1572,7 @@ constexpr int64_t kExactMaxDim = 16384;
 int32_t exact_check(firal_problem* P) {
   if (!P) return fail(FIRAL_ERR_ARG, "problem must be non-null");
   if (P->pt.Q) return fail(FIRAL_ERR_UNSUPPORTED, "Exact-FIRAL does not take pooled problems");
+  if (sharded(P)) return fail(FIRAL_ERR_UNSUPPORTED, "Exact-FIRAL does not take a row-sharded problem");
   if (P->D > kExactMaxDim) return fail(FIRAL_ERR_UNSUPPORTED, "Exact-FIRAL needs d c <= 16384");
   return FIRAL_OK;
 }
@@ -1955,4 +1973,60 @@ int64_t firal_cache_bytes(void) {
   BlockCache& c = block_cache();
   std::lock_guard<std::mutex> g(c.mu);
   return (int64_t)c.held;
+}
+
+// ------------------------------------------------------------------------------------------
+// Row sharding (Section 3.3 of the paper): the problem holds this process's rows; the partial
+// sums over points are added across the group by the caller's allreduce.
+// ------------------------------------------------------------------------------------------
+namespace firal {
+bool sharded(const firal_problem* P) { return P->comm.world > 1 && P->comm.allreduce; }
+
+int32_t shard_allreduce(firal_problem* P, void* buf, int64_t count, int32_t dtype, int32_t op) {
+  if (!sharded(P)) return FIRAL_OK;
+  const int32_t rc = P->comm.allreduce(buf, count, dtype, op, P->H->stream, P->comm.user);
+  if (rc != 0)
+    return fail(FIRAL_ERR_COMM, "allreduce callback returned " + std::to_string(rc) + " (rank " +
+                                    std::to_string(P->comm.rank) + " of " +
+                                    std::to_string(P->comm.world) + ")");
+  return FIRAL_OK;
+}
+}  // namespace firal
+
+int32_t firal_problem_set_comm(firal_problem* P, const firal_comm* comm) {
+  firal_handle* H = P ? P->H : nullptr;
+  if (!P) return record(H, fail(FIRAL_ERR_ARG, "problem must be non-null"));
+  if (P->pt.Q) return record(H, fail(FIRAL_ERR_UNSUPPORTED, "pooled problems are not sharded"));
+  firal_comm c = comm ? *comm : firal_comm{0, 1, nullptr, nullptr};
+  if (c.world < 1 || c.rank < 0 || c.rank >= c.world || (c.world > 1 && !c.allreduce))
+    return record(H, fail(FIRAL_ERR_ARG, "need 0 <= rank < world and an allreduce for world > 1"));
+  if (c.world == 1) c = firal_comm{0, 1, nullptr, nullptr};
+  cudaStream_t st = H->stream;
+  P->comm = c;
+  // total pool size over the group
+  double* red = P->red.as<double>();
+  const double nl = (double)P->n;
+  int32_t rc = FIRAL_OK;
+  if (cudaMemcpyAsync(red + 2000, &nl, sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    rc = fail(FIRAL_ERR_CUDA, "copy of the pool size failed");
+  if (rc == FIRAL_OK) rc = shard_allreduce(P, red + 2000, 1, FIRAL_DT_F64, 0);
+  double nt = nl;
+  if (rc == FIRAL_OK &&
+      (cudaMemcpyAsync(&nt, red + 2000, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+       cudaStreamSynchronize(st) != cudaSuccess))
+    rc = fail(FIRAL_ERR_CUDA, "read of the total pool size failed");
+  if (rc != FIRAL_OK) {
+    P->comm = firal_comm{0, 1, nullptr, nullptr};
+    return record(H, rc);
+  }
+  P->n_total = (int64_t)std::llround(nt);
+  // H_p = (1/n_total) sum over the pool rows; labelled rows (and lambda) only on rank 0
+  rc = fill_weights(P->dbl, P->w_p.p, P->m, 0.0, nullptr, 1.0 / (double)P->n_total, P->n, st);
+  if (rc == FIRAL_OK)
+    rc = fill_weights(P->dbl, P->w_sig.p, P->m, P->comm.rank == 0 ? 1.0 : 0.0, nullptr,
+                      1.0 / (double)P->n_total, P->n, st);
+  P->S_p_ready = false;
+  if (rc == FIRAL_OK && cudaStreamSynchronize(st) != cudaSuccess)
+    rc = fail(FIRAL_ERR_CUDA, "set_comm synchronisation failed");
+  return record(H, rc);
 }

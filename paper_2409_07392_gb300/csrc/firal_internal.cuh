@@ -202,15 +202,24 @@ struct firal_problem {
   // confident rows (max_k h_ik > 1/2), centred at their class m: u_i = h_i - e_m in the
   // Hessian apply (cen[i] = m or -1; rows grouped by class in cen_idx, cen_off per class);
   // bf16 u row-major and K-block-major; a_m and w (u . a) per (row, probe) of an apply
+  // row sharding (firal_problem_set_comm): allreduce callback, rank, world, total pool size
+  firal_comm comm{0, 1, nullptr, nullptr};
+  int64_t n_total = 0;
   int64_t n_cen = 0;
   // (the labelled rows of such a problem are applied on CUDA cores: cen_lab, m x s x c)
-  firal::DBuf cen, cen_off, cen_idx, Ub, UbT, cen_am, cen_rho, cen_lab;
+  // (cen_items: the grouped rows cut into work items, cen_off then holds each class's first
+  // item; cen_part: per-item partial sums)
+  firal::DBuf cen, cen_off, cen_idx, Ub, UbT, cen_am, cen_rho, cen_lab, cen_items, cen_part;
+  int n_cen_items = 0;
   int rtab_d = -1, rtab_chunks = 0;
   int32_t dp = 0, cp = 0;
   int64_t Np = 0;
 };
 
 namespace firal {
+// ---- capi.cu: row sharding (no-op on a problem that is alone)
+bool sharded(const firal_problem* P);
+int32_t shard_allreduce(firal_problem* P, void* buf, int64_t count, int32_t dtype, int32_t op);
 // ---- k_simt.cu
 int32_t copy_rows(bool dbl, void* dst, const void* a, int64_t ma, const void* b, int64_t nb,
                   int cols, int32_t src_dtype, cudaStream_t st);
@@ -248,6 +257,9 @@ int32_t dot_scaled(bool dbl, const void* a, const void* b, int64_t total, double
                    double* part, double* out, cudaStream_t st);
 int32_t md_step_simt(bool dbl, void* z, const void* g, int64_t n, double budget, double beta0,
                      double* red, cudaStream_t st);
+int32_t md_step_sharded(firal_problem* P, void* z, const void* g, double budget, double beta0,
+                        double* red, cudaStream_t st);
+int32_t block_dots(firal_problem* P, const void* V, const void* out, int s, double* pq);
 // ---- k_linalg.cu
 int32_t chol_inv(bool dbl, const double* A, int c, int d, void* inv_t, double* inv_d,
                  double* L_out, int32_t* not_spd, cudaStream_t st);

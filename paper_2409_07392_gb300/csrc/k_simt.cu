@@ -1459,4 +1459,78 @@ int32_t md_step_simt(bool dbl, void* z, const void* g, int64_t n, double budget,
   return FIRAL_OK;
 }
 
+// ------------------------------------------------------------------------------------------
+// Row-sharded problems: the MD update with its two scalars added across processes, and the
+// per-block dot products of an apply recomputed after its partial was added up.
+// ------------------------------------------------------------------------------------------
+// red[off] = max (op 1) or sum (op 0) of red[off .. off + count), fixed order; the rest zeroed
+__global__ void k_collapse(double* red, int off, int count, int op) {
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int i = 0; i < count; ++i) {
+      const double v = red[off + i];
+      r = op == 1 ? ((v > r || v != v) ? v : r) : r + v;
+      red[off + i] = 0.0;
+    }
+    red[off] = r;
+  }
+}
+
+int32_t md_step_sharded(firal_problem* P, void* z, const void* g, double budget, double beta0,
+                        double* red, cudaStream_t st) {
+  const int64_t n = P->n;
+  ProfScope ps(st, PF_MD);
+  count_launch(2);
+  if (P->dbl) k_absmax_partial<double><<<256, 256, 0, st>>>((const double*)g, n, red);
+  else k_absmax_partial<float><<<256, 256, 0, st>>>((const float*)g, n, red);
+  k_collapse<<<1, 32, 0, st>>>(red, 0, 256, 1);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  FIRAL_TRY(shard_allreduce(P, red, 1, FIRAL_DT_F64, 1));            // ||g||_inf
+  count_launch(2);
+  if (P->dbl) k_md_exp<double><<<256, 256, 0, st>>>((double*)z, (const double*)g, n, beta0, red);
+  else k_md_exp<float><<<256, 256, 0, st>>>((float*)z, (const float*)g, n, beta0, red);
+  k_collapse<<<1, 32, 0, st>>>(red, 256, 256, 0);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  FIRAL_TRY(shard_allreduce(P, red + 256, 1, FIRAL_DT_F64, 0));      // sum z exp(-beta g)
+  count_launch(2);
+  if (P->dbl) k_md_scale<double><<<256, 256, 0, st>>>((double*)z, n, budget, red);
+  else k_md_scale<float><<<256, 256, 0, st>>>((float*)z, n, budget, red);
+  k_md_zmax<<<1, 32, 0, st>>>(red);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  return shard_allreduce(P, red + 513, 1, FIRAL_DT_F64, 1);         // max z (stats)
+}
+
+// pq[j c + k] = <V_j[k], out_j[k]> (double), one block per (class, probe)
+template <class T>
+__global__ void k_block_dots(const T* V, const T* out, int c, int d, int64_t D, double* pq) {
+  __shared__ double red[32];
+  const int k = blockIdx.x, j = blockIdx.y;
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < d; e += blockDim.x) {
+    const int64_t o = (int64_t)j * D + (int64_t)k * d + e;
+    acc += (double)V[o] * (double)out[o];
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    pq[(int64_t)j * c + k] = t;
+  }
+}
+
+int32_t block_dots(firal_problem* P, const void* V, const void* out, int s, double* pq) {
+  const int threads = ((P->d + 31) / 32) * 32;
+  count_launch();
+  if (P->dbl)
+    k_block_dots<double><<<dim3(P->c, s), threads, 0, P->H->stream>>>(
+        (const double*)V, (const double*)out, P->c, P->d, P->D, pq);
+  else
+    k_block_dots<float><<<dim3(P->c, s), threads, 0, P->H->stream>>>(
+        (const float*)V, (const float*)out, P->c, P->d, P->D, pq);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  return FIRAL_OK;
+}
+
 }  // namespace firal

@@ -125,12 +125,21 @@ __global__ void k_to_bf16_lo_pad(bf16* dst, const float* src, int64_t rows, int 
 // Every term is of the size of u (1 - h_m, h_k for k != m), so no two large terms cancel:
 // rounding u to bf16 is relative to u, where rounding h_m ~ 1 to bf16 errs by up to 2^-9 in
 // the same direction on every confident row and that bias is as large as the Hessian itself.
-// Rows with h_m > 1/2 (cen[i] = m, else -1) take this form in the tensor-core apply:
+// Rows with h_m > 1/2 (cen[i] = m, else -1; kCentre below) take this form in the tensor-core
+// apply:
 //   diagonal part  sum_i w_i u_ik x_i x_i^T V_k          (block sums with u in the class operand)
 //   low-rank part  sum_i w_i u_ik alpha_i x_i             (alpha-GEMM on u: u . a; plus a_m)
 //   class-m part   sum_{i: m_i = k} w_i (u_i . a_i) x_i   (a per-class sum over its rows)
 // ------------------------------------------------------------------------------------------
-// cen[r] = argmax_k h_rk (lowest index on ties) when that probability exceeds 1/2, else -1;
+// Rows whose top probability exceeds kCentre are centred.  On a plain row the bf16 rounding
+// of h_m (spacing 2^-9 on [1/2, 1)) errs by up to 2^-10 / (1 - h_m) of the row's Hessian: in
+// a random direction from row to row, unless h_m sits within a few spacings of 1, where it
+// rounds toward 1 on every row.  A threshold of 0.9 keeps that ratio below 1% per row but,
+// measured on a classifier with weights x 20, left 2.6e-3 in H_p V at 60 points per class
+// against 1.3e-3 with 1/2; 1/2 is also where h_m - 1 becomes exact in f32.
+constexpr float kCentre = 0.5f;
+
+// cen[r] = argmax_k h_rk (lowest index on ties) when that probability exceeds kCentre, else -1;
 // *count gains the number of such rows.  One warp per row.
 __global__ void k_row_top(int* cen, unsigned long long* count, const float* src, int64_t rows,
                           int cols) {
@@ -155,8 +164,8 @@ __global__ void k_row_top(int* cen, unsigned long long* count, const float* src,
     }
   }
   if (lane == 0) {
-    cen[r] = best > 0.5f ? bi : -1;
-    if (best > 0.5f) atomicAdd(count, 1ULL);
+    cen[r] = best > kCentre ? bi : -1;
+    if (best > kCentre) atomicAdd(count, 1ULL);
   }
 }
 
@@ -178,14 +187,18 @@ __global__ void k_to_bf16_centred_pad(bf16* dst, const float* src, const int* ce
   }
 }
 
-// a_m for the centred rows of class k (block k): am[i][j] = x_i . P~_j[:, k], the probe block
-// as the alpha-GEMM sees it (its bf16 parts summed), rows listed by class in idx[off[k]..).
-__global__ void k_centre_am(float* am, const bf16* Pb, const bf16* Xb, const int* off,
+// The centred rows grouped by class are cut into work items of at most CEN_ITEM rows
+// (int4: class, first row, end row in idx, unused), so one large class does not serialise on
+// one block.
+constexpr int CEN_ITEM = 512;
+
+// a_m for the centred rows of one work item (block): am[i][j] = x_i . P~_j[:, k], the probe
+// block as the alpha-GEMM sees it (its bf16 parts summed).
+__global__ void k_centre_am(float* am, const bf16* Pb, const bf16* Xb, const int4* items,
                             const int* idx, int s, int npart, int dp, int cp) {
   extern __shared__ float pv[];   // s x dp
-  const int k = blockIdx.x;
-  const int r0 = off[k], r1 = off[k + 1];
-  if (r0 == r1) return;
+  const int4 it = items[blockIdx.x];
+  const int k = it.x, r0 = it.y, r1 = it.z;
   for (int t = threadIdx.x; t < s * dp; t += blockDim.x) {
     const int j = t / dp, e = t - j * dp;
     float v = 0.0f;
@@ -194,9 +207,9 @@ __global__ void k_centre_am(float* am, const bf16* Pb, const bf16* Xb, const int
     pv[t] = v;
   }
   __syncthreads();
-  const int64_t items = (int64_t)(r1 - r0) * s;
-  for (int64_t t = threadIdx.x; t < items; t += blockDim.x) {
-    const int rr = (int)(t / s), j = (int)(t - (int64_t)rr * s);
+  const int items_n = (r1 - r0) * s;
+  for (int t = threadIdx.x; t < items_n; t += blockDim.x) {
+    const int rr = t / s, j = t - rr * s;
     const int64_t row = idx[r0 + rr];
     const __nv_bfloat162* x2 = reinterpret_cast<const __nv_bfloat162*>(Xb + row * dp);
     const float* pj = pv + j * dp;
@@ -210,22 +223,65 @@ __global__ void k_centre_am(float* am, const bf16* Pb, const bf16* Xb, const int
   }
 }
 
-// class-m part of the centred rows: out[k][j d + e] = sum_{rows i of class k} rho[i][j] x_ie
-// (rho = w (u . a) from the alpha epilogue), rows in a fixed order; zero for classes without
-// centred rows.  It is added to the split-K partials of the D-GEMM (block k).
-__global__ void k_centre_termc(float* out, const float* rho, const bf16* Xb, const int* off,
+// class-m part of the centred rows, per work item: part[item][j d + e] = sum over the item's
+// rows of rho[i][j] x_ie (rho = w (u . a) from the alpha epilogue), in row order.  The rows are
+// staged 64 at a time in shared memory (their rho and x rows loaded together), so the sums run
+// from shared memory; dynamic shared memory 64 (s + dp) floats.  Block (item, y) of 256
+// threads covers outputs [2048 y, 2048 y + 2048).
+__global__ void k_centre_termc(float* part, const float* rho, const bf16* Xb, const int4* items,
                                const int* idx, int s, int d, int dp) {
-  const int k = blockIdx.x;
-  const int r0 = off[k], r1 = off[k + 1];
+  extern __shared__ float stg[];   // rho chunk [64][s] | x chunk [64][dp]
+  float* rs = stg;
+  float* xs = stg + 64 * s;
+  const int4 it = items[blockIdx.x];
+  const int r0 = it.y, r1 = it.z;
   const int sd = s * d;
-  for (int t = threadIdx.x; t < sd; t += blockDim.x) {
-    const int j = t / d, e = t - j * d;
-    float acc = 0.0f;
-    for (int rr = r0; rr < r1; ++rr) {
-      const int64_t row = idx[rr];
-      acc = fmaf(rho[row * s + j], __bfloat162float(Xb[row * dp + e]), acc);
+  constexpr int MAXO = 8;   // outputs per thread
+  const int o0 = blockIdx.y * MAXO * blockDim.x;
+  float acc[MAXO];
+#pragma unroll
+  for (int q = 0; q < MAXO; ++q) acc[q] = 0.0f;
+  for (int c0 = r0; c0 < r1; c0 += 64) {
+    const int nr = r1 - c0 < 64 ? r1 - c0 : 64;
+    __syncthreads();
+    for (int t = threadIdx.x; t < nr * s; t += blockDim.x) {
+      const int rr = t / s, j = t - rr * s;
+      rs[t] = rho[(int64_t)idx[c0 + rr] * s + j];
     }
-    out[(int64_t)k * sd + t] = acc;
+    for (int t = threadIdx.x; t < nr * dp; t += blockDim.x) {
+      const int rr = t / dp, e = t - rr * dp;
+      xs[t] = __bfloat162float(Xb[(int64_t)idx[c0 + rr] * dp + e]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < MAXO; ++q) {
+      const int t = o0 + threadIdx.x + q * blockDim.x;
+      if (t < sd) {
+        const int j = t / d, e = t - j * d;
+        float a = acc[q];
+        for (int rr = 0; rr < nr; ++rr) a = fmaf(rs[rr * s + j], xs[rr * dp + e], a);
+        acc[q] = a;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < MAXO; ++q) {
+    const int t = o0 + threadIdx.x + q * blockDim.x;
+    if (t < sd) part[(int64_t)blockIdx.x * sd + t] = acc[q];
+  }
+}
+
+// out[k][o] = sum of the class's item partials in item order (zero for a class without centred
+// rows); it is added to the split-K partials of the D-GEMM.  Block (k, y) as above.
+__global__ void k_centre_reduce(float* out, const float* part, const int* ioff, int sd) {
+  const int k = blockIdx.x;
+  const int i0 = ioff[k], i1 = ioff[k + 1];
+  for (int q = 0; q < 8; ++q) {
+    const int t = blockIdx.y * 8 * blockDim.x + threadIdx.x + q * blockDim.x;
+    if (t >= sd) break;
+    float a = 0.0f;
+    for (int i = i0; i < i1; ++i) a += part[(int64_t)i * sd + t];
+    out[(int64_t)k * sd + t] = a;
   }
 }
 
@@ -1967,7 +2023,7 @@ static int pow2_dim(int d) {
   return p;
 }
 
-// Confident rows of a mixed problem (h_m > 1/2): their class m (cen), the rows grouped by class
+// Confident rows of a mixed problem (h_m > kCentre): their class m (cen), the rows grouped by class
 // in row order (cen_off, cen_idx: a counting sort on the host, so every later per-class sum runs
 // in a fixed order) and the centred bf16 copies of h that the Hessian apply's two GEMMs take
 // instead of h (Ub row-major, UbT K-block-major).  A problem without confident rows keeps none
@@ -2022,9 +2078,22 @@ static int32_t tc_prepare_centred(firal_problem* P, int cpb2) {
   std::vector<int> idx(nc), pos(off.begin(), off.end() - 1);
   for (int64_t i = 0; i < N; ++i)
     if (cen[i] >= 0) idx[pos[cen[i]]++] = (int)i;
+  // work items of at most CEN_ITEM rows of one class; ioff[k] = the class's first item
+  std::vector<int4> items;
+  std::vector<int> ioff(c + 1, 0);
+  for (int k = 0; k < c; ++k) {
+    ioff[k] = (int)items.size();
+    for (int r = off[k]; r < off[k + 1]; r += CEN_ITEM)
+      items.push_back(make_int4(k, r, std::min(r + CEN_ITEM, off[k + 1]), 0));
+  }
+  ioff[c] = (int)items.size();
+  P->n_cen_items = (int)items.size();
   FIRAL_TRY(P->cen_off.ensure((size_t)(c + 1) * sizeof(int)));
   FIRAL_TRY(P->cen_idx.ensure((size_t)nc * sizeof(int)));
-  FIRAL_CUDA_TRY(cudaMemcpyAsync(P->cen_off.p, off.data(), (size_t)(c + 1) * sizeof(int),
+  FIRAL_TRY(P->cen_items.ensure(items.size() * sizeof(int4)));
+  FIRAL_CUDA_TRY(cudaMemcpyAsync(P->cen_items.p, items.data(), items.size() * sizeof(int4),
+                                 cudaMemcpyHostToDevice, st));
+  FIRAL_CUDA_TRY(cudaMemcpyAsync(P->cen_off.p, ioff.data(), (size_t)(c + 1) * sizeof(int),
                                  cudaMemcpyHostToDevice, st));
   FIRAL_CUDA_TRY(cudaMemcpyAsync(P->cen_idx.p, idx.data(), (size_t)nc * sizeof(int),
                                  cudaMemcpyHostToDevice, st));
@@ -2134,9 +2203,9 @@ static int32_t tc_apply_t(firal_problem* P, const float* w, const float* Sblk, c
                                           (int)smem_am));
     ProfScope ps(st, PF_SPLIT);
     count_launch();
-    k_centre_am<<<P->c, 256, smem_am, st>>>(P->cen_am.as<float>(), P->Pb.as<bf16>(),
-                                            P->Xb.as<bf16>(), P->cen_off.as<int>(),
-                                            P->cen_idx.as<int>(), s, NPART, DP, cp);
+    k_centre_am<<<P->n_cen_items, 256, smem_am, st>>>(P->cen_am.as<float>(), P->Pb.as<bf16>(),
+                                                      P->Xb.as<bf16>(), P->cen_items.as<int4>(),
+                                                      P->cen_idx.as<int>(), s, NPART, DP, cp);
     FIRAL_CUDA_TRY(cudaGetLastError());
   }
   CUtensorMap mH, mP;
@@ -2222,9 +2291,19 @@ static int32_t tc_apply_t(firal_problem* P, const float* w, const float* Sblk, c
     if (centred) {
       ProfScope ps(st, PF_COMBINE);
       count_launch();
-      k_centre_termc<<<P->c, 256, 0, st>>>(P->Dpart.as<float>() + (size_t)splits * P->c * sd,
-                                           P->cen_rho.as<float>(), P->Xb.as<bf16>(),
-                                           P->cen_off.as<int>(), P->cen_idx.as<int>(), s, P->d, DP);
+      const size_t smem_c = (size_t)64 * (s + DP) * sizeof(float);
+      if (smem_c > 48 * 1024)
+        FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_centre_termc,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem_c));
+      FIRAL_TRY(P->cen_part.ensure((size_t)P->n_cen_items * sd * sizeof(float)));
+      count_launch();
+      k_centre_termc<<<dim3(P->n_cen_items, (sd + 2047) / 2048), 256, smem_c, st>>>(
+          P->cen_part.as<float>(), P->cen_rho.as<float>(), P->Xb.as<bf16>(),
+          P->cen_items.as<int4>(), P->cen_idx.as<int>(), s, P->d, DP);
+      k_centre_reduce<<<dim3(P->c, (sd + 2047) / 2048), 256, 0, st>>>(
+          P->Dpart.as<float>() + (size_t)splits * P->c * sd, P->cen_part.as<float>(),
+          P->cen_off.as<int>(), sd);
       FIRAL_CUDA_TRY(cudaGetLastError());
     }
     if (lab) {
@@ -2244,6 +2323,9 @@ static int32_t tc_apply_t(firal_problem* P, const float* w, const float* Sblk, c
       FIRAL_CUDA_TRY(cudaGetLastError());
     }
     FIRAL_TRY(combine_f32(P, Sblk, V, splits + extra, s, out, nullptr, P->vmean.as<float>()));
+    // a row-sharded group adds its partials here: the projection below and its dot products
+    // act on the whole sum
+    FIRAL_TRY(shard_allreduce(P, out, (int64_t)s * P->D, FIRAL_DT_F32, 0));
     ProfScope ps(st, PF_COMBINE);
     count_launch(2);
     k_class_mean<<<s * Qe, 1024, 0, st>>>(out, s, P->c, P->d, P->D, P->qmean.as<float>(), P->pt);
@@ -2637,9 +2719,10 @@ static int32_t tc_apply_dp(firal_problem* P, const void* w, const void* Sblk, co
 
 int32_t tc_hessian_apply(firal_problem* P, const void* w, const void* Sblk, const void* V, int s,
                          void* out, double* pq, double lam_null) {
-  // the bf16 direction's rounding enters only the low-rank term; with confident rows that term
-  // is as large as the result, so such problems take the hi + lo direction in both modes
-  if (P->prec == FIRAL_MIXED_BF16_FAST && P->n_cen == 0)
+  // the bf16 direction's rounding enters only the low-rank term; on confident rows that term
+  // is as large as the result, so a problem with more than 1% of them takes the hi + lo
+  // direction in both modes
+  if (P->prec == FIRAL_MIXED_BF16_FAST && P->n_cen * 100 <= P->N)
     return tc_apply_dp<1>(P, w, Sblk, V, s, out, pq, lam_null);
   return tc_apply_dp<2>(P, w, Sblk, V, s, out, pq, lam_null);
 }
