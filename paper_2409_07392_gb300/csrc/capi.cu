@@ -631,9 +631,10 @@ int32_t round_chain(firal_problem* P, const RoundSetup& rs, int32_t b, const fir
   const size_t blk = (size_t)c * d * d;
   const double* Sig = rs.Sig.as<double>();
   const double* L = rs.L.as<double>();
-  DBuf Bm, Binv, Hk, M1, M2, eig, nu, mask, pv, pi, score, Tg;
+  DBuf Bm, Binv, Hk, M1, M2, eig, nu, mask, pv, pi, score, Tg, Ht, Hot;
   auto rel = [&]() {
-    for (DBuf* bf : {&Bm, &Binv, &Hk, &M1, &M2, &eig, &nu, &mask, &pv, &pi, &score, &Tg})
+    for (DBuf* bf : {&Bm, &Binv, &Hk, &M1, &M2, &eig, &nu, &mask, &pv, &pi, &score, &Tg, &Ht,
+                     &Hot})
       bf->release();
   };
   const int np = (int)std::max<int64_t>((P->n + 127) / 128, P->sms);
@@ -651,13 +652,17 @@ int32_t round_chain(firal_problem* P, const RoundSetup& rs, int32_t b, const fir
   TRYR(Hk.ensure(blk * 8));
   TRYR(M1.ensure(blk * vsize(P)));
   TRYR(M2.ensure(blk * vsize(P)));
-  TRYR(eig.ensure((size_t)c * d * 8));
+  // tridiagonal forms, Gershgorin bounds, nu step state (4) and per-SM partials (3 each)
+  TRYR(eig.ensure(((size_t)2 * c * d + 2 * c + 4 + 3 * 1024) * 8));
   TRYR(nu.ensure(8));
   TRYR(mask.ensure((size_t)P->n));
   TRYR(pv.ensure((size_t)np * 8));
   TRYR(pi.ensure((size_t)np * 8));
   TRYR(score.ensure(8));
   TRYR(Tg.ensure(blk * 8));
+  // H~ = L^{-1} H L^{-T} kept up to date pick by pick (rank one plus L^{-1} H_o L^{-T} / b)
+  TRYR(Ht.ensure(blk * 8));
+  TRYR(Hot.ensure(blk * 8));
   const int64_t tot = (int64_t)blk;
   // line 4: B_1 = sqrt(d~) Sigma + (eta/b) H_o
   TRYR(lincomb(Bm.as<double>(), std::sqrt((double)D), Sig, eta / b, P->HoBlk.as<double>(), 0.0,
@@ -666,6 +671,8 @@ int32_t round_chain(firal_problem* P, const RoundSetup& rs, int32_t b, const fir
                 not_spd_flag(P->H), st));
   TRYR(round_m(P->dbl, Binv.as<double>(), Sig, c, d, M1.p, M2.p, Tg.as<double>(), st));
   FIRAL_CUDA_TRY(cudaMemsetAsync(Hk.p, 0, blk * 8, st));
+  FIRAL_CUDA_TRY(cudaMemsetAsync(Ht.p, 0, blk * 8, st));
+  TRYR(similarity_blocks(L, P->HoBlk.as<double>(), c, d, Hot.as<double>(), st));
   FIRAL_CUDA_TRY(cudaMemsetAsync(mask.p, 0, (size_t)P->n, st));
   for (int t = 0; t < b; ++t) {
     // line 7: eq. 14 scores and the masked argmax (tensor cores for FIRAL_MIXED_BF16)
@@ -679,11 +686,12 @@ int32_t round_chain(firal_problem* P, const RoundSetup& rs, int32_t b, const fir
     TRYR(round_pick(pv.as<double>(), pi.as<int64_t>(), npart, mask.as<uint8_t>(), sel, t,
                     score.as<double>(), st));
     // line 8: H_k += B_k(H_o)/b + w x x^T
-    TRYR(round_hupdate(P, Hk.as<double>(), P->HoBlk.as<double>(), 1.0 / b, sel, t));
-    // line 9: eigenvalues of H~_k
-    TRYR(tilde_eigvals(L, Hk.as<double>(), c, d, eig.as<double>(), st));
-    // line 10: nu
-    TRYR(nu_bisect_dev(eig.as<double>(), (int64_t)c * d, eta, nu.as<double>(), st));
+    TRYR(round_hupdate(P, Hk.as<double>(), P->HoBlk.as<double>(), 1.0 / b, sel, t, L,
+                       Ht.as<double>(), Hot.as<double>()));
+    // lines 9-10: nu with sum_j (nu + eta lambda_j(H~_k))^-2 = 1, from the tridiagonal forms
+    // of H~_k (the eigenvalues enter only through that trace)
+    TRYR(sym_tri_nu(Ht.as<double>(), c, d, eta, eig.as<double>(),
+                    eig.as<double>() + (size_t)2 * c * d, nu.as<double>(), st));
     // line 11: B = nu Sigma + eta H + (eta/b) H_o, inverted
     TRYR(lincomb_nu(Bm.as<double>(), nu.as<double>(), Sig, eta, Hk.as<double>(), eta / b,
                     P->HoBlk.as<double>(), tot, st));

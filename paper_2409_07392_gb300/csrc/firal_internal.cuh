@@ -265,6 +265,12 @@ int32_t chol_inv(bool dbl, const double* A, int c, int d, void* inv_t, double* i
                  double* L_out, int32_t* not_spd, cudaStream_t st);
 int32_t tilde_eigvals(const double* L, const double* H, int c, int d, double* eig,
                       cudaStream_t st);
+int32_t tilde_nu(const double* L, const double* H, int c, int d, double eta, double* tri,
+                 double* gb, double* nu_out, cudaStream_t st);
+int32_t sym_tri_nu(const double* Ht, int c, int d, double eta, double* tri, double* gb,
+                   double* nu_out, cudaStream_t st);
+int32_t similarity_blocks(const double* L, const double* H, int c, int d, double* out,
+                          cudaStream_t st);
 int32_t nu_bisect_dev(const double* lam, int64_t count, double scale, double* nu_out,
                       cudaStream_t st);
 int32_t round_scores(firal_problem* P, const void* M1, const void* M2, const uint8_t* mask,
@@ -274,7 +280,8 @@ int32_t round_pick(const double* pv, const int64_t* pi, int np, uint8_t* mask, i
 int32_t round_m(bool dbl, const double* Binv, const double* Sig, int c, int d, void* M1, void* M2,
                 double* Tg, cudaStream_t st);
 int32_t round_hupdate(firal_problem* P, double* H, const double* Ho, double invb,
-                      const int32_t* sel, int32_t t);
+                      const int32_t* sel, int32_t t, const double* L = nullptr,
+                      double* Ht = nullptr, const double* Hot = nullptr);
 int32_t lincomb(double* out, double a, const double* X, double b, const double* Y, double cc,
                 const double* Z, int64_t total, cudaStream_t st);
 int32_t lincomb_nu(double* out, const double* nu, const double* X, double b, const double* Y,

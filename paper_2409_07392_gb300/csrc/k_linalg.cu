@@ -9,7 +9,11 @@
 //  * k_nu         -- the root of sum_j (nu + mu_j)^{-2} = 1 (eq. 10) by bisection.
 //  * Round kernels -- eq. 14 scores with a masked argmax, the block update of H, and the
 //                    assembly of B_t (Algorithm 3 lines 7-11).
+#include <cooperative_groups.h>
+
 #include "firal_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace firal {
 
@@ -139,25 +143,25 @@ __device__ int sturm_count(const double* dg, const double* e2, int d, double x) 
   return cnt;
 }
 
-__global__ void k_tilde_eig(const double* __restrict__ L, const double* __restrict__ H, int d,
-                            double* __restrict__ eig) {
-  extern __shared__ double sh[];
-  double* M = sh;              // d*d
-  double* v = M + d * d;       // d
-  double* p = v + d;           // d
-  double* dg = p + d;          // d
-  double* e2 = dg + d;         // d  (squared off-diagonal)
-  __shared__ double red[32];
-  __shared__ double s_bcast[4];
-  const int k = blockIdx.x, tid = threadIdx.x, bd = blockDim.x;
-  const double* Lk = L + (int64_t)k * d * d;
-  const double* Hk = H + (int64_t)k * d * d;
+// Tridiagonal form of L^{-1} H L^{-T} for one block, in the block's shared memory: the
+// similarity (two triangular solves with the reciprocal pivots of L), symmetrisation and
+// Householder reduction.  On return dg holds the diagonal and e2 the squared off-diagonal
+// (e2[i] couples i and i + 1).  M: d*d doubles; v, p, dg, e2, rl: d doubles each.
+__device__ void householder_tridiag(int d, double* M, double* v, double* p, double* dg,
+                                    double* e2, double* red);
+
+__device__ void tilde_tridiag(const double* __restrict__ Lk, const double* __restrict__ Hk,
+                              int d, double* M, double* v, double* p, double* dg, double* e2,
+                              double* rl, double* red) {
+  const int tid = threadIdx.x, bd = blockDim.x;
+  for (int i = tid; i < d; i += bd) rl[i] = 1.0 / Lk[(int64_t)i * d + i];
+  __syncthreads();
   // pass 1: column col of A = L^{-1} H, stored transposed in row col of M
   for (int col = tid; col < d; col += bd) {
     for (int i = 0; i < d; ++i) {
       double acc = Hk[(int64_t)i * d + col];
       for (int q = 0; q < i; ++q) acc -= Lk[(int64_t)i * d + q] * M[col * d + q];
-      M[col * d + i] = acc / Lk[(int64_t)i * d + i];
+      M[col * d + i] = acc * rl[i];
     }
   }
   __syncthreads();
@@ -166,7 +170,7 @@ __global__ void k_tilde_eig(const double* __restrict__ L, const double* __restri
     for (int i = 0; i < d; ++i) {
       double acc = M[i * d + col];
       for (int q = 0; q < i; ++q) acc -= Lk[(int64_t)i * d + q] * M[q * d + col];
-      M[i * d + col] = acc / Lk[(int64_t)i * d + i];
+      M[i * d + col] = acc * rl[i];
     }
   }
   __syncthreads();
@@ -180,7 +184,14 @@ __global__ void k_tilde_eig(const double* __restrict__ L, const double* __restri
     }
   }
   __syncthreads();
-  // Householder tridiagonalisation
+  householder_tridiag(d, M, v, p, dg, e2, red);
+}
+
+// Householder reduction of the symmetric d x d matrix M (shared memory, overwritten) to
+// tridiagonal form: dg = diagonal, e2 = squared off-diagonal (e2[i] couples i and i + 1).
+__device__ void householder_tridiag(int d, double* M, double* v, double* p, double* dg,
+                                    double* e2, double* red) {
+  const int tid = threadIdx.x, bd = blockDim.x;
   for (int kk = 0; kk + 2 < d; ++kk) {
     double part = 0.0;
     for (int i = kk + 2 + tid; i < d; i += bd) part += M[i * d + kk] * M[i * d + kk];
@@ -221,6 +232,21 @@ __global__ void k_tilde_eig(const double* __restrict__ L, const double* __restri
   }
   for (int i = tid; i < d; i += bd) dg[i] = M[i * d + i];
   __syncthreads();
+}
+
+__global__ void k_tilde_eig(const double* __restrict__ L, const double* __restrict__ H, int d,
+                            double* __restrict__ eig) {
+  extern __shared__ double sh[];
+  double* M = sh;              // d*d
+  double* v = M + d * d;       // d
+  double* p = v + d;           // d
+  double* dg = p + d;          // d
+  double* e2 = dg + d;         // d  (squared off-diagonal)
+  double* rl = e2 + d;         // d  (reciprocal pivots of L)
+  __shared__ double red[32];
+  __shared__ double s_bcast[4];
+  const int k = blockIdx.x, tid = threadIdx.x, bd = blockDim.x;
+  tilde_tridiag(L + (int64_t)k * d * d, H + (int64_t)k * d * d, d, M, v, p, dg, e2, rl, red);
   // Gershgorin interval (thread 0)
   if (tid == 0) {
     double lo = 1e300, hi = -1e300;
@@ -247,9 +273,356 @@ __global__ void k_tilde_eig(const double* __restrict__ L, const double* __restri
   }
 }
 
+// The tridiagonal forms alone (Round's nu needs no individual eigenvalue): tri[k] = dg (d) then
+// e2 (d) of block k; gb[k] = its Gershgorin interval (lo, hi).
+__global__ void k_tilde_tri(const double* __restrict__ L, const double* __restrict__ H, int d,
+                            double* __restrict__ tri, double* __restrict__ gb) {
+  extern __shared__ double sh[];
+  double* M = sh;
+  double* v = M + d * d;
+  double* p = v + d;
+  double* dg = p + d;
+  double* e2 = dg + d;
+  double* rl = e2 + d;
+  __shared__ double red[32];
+  const int k = blockIdx.x, tid = threadIdx.x, bd = blockDim.x;
+  tilde_tridiag(L + (int64_t)k * d * d, H + (int64_t)k * d * d, d, M, v, p, dg, e2, rl, red);
+  for (int i = tid; i < d; i += bd) {
+    tri[(int64_t)k * 2 * d + i] = dg[i];
+    tri[(int64_t)k * 2 * d + d + i] = i + 1 < d ? e2[i] : 0.0;
+  }
+  if (tid == 0) {
+    double lo = 1e300, hi = -1e300;
+    for (int i = 0; i < d; ++i) {
+      const double r = (i > 0 ? sqrt(e2[i - 1]) : 0.0) + (i + 1 < d ? sqrt(e2[i]) : 0.0);
+      lo = fmin(lo, dg[i] - r);
+      hi = fmax(hi, dg[i] + r);
+    }
+    gb[2 * k] = lo;
+    gb[2 * k + 1] = hi;
+  }
+}
+
+// Tridiagonal forms (as k_tilde_tri) of blocks that are already L^{-1} H L^{-T} (Ht, kept up
+// to date by k_round_hupdate): copy to shared memory, Householder reduction.
+__global__ void k_sym_tri(const double* __restrict__ Ht, int d, double* __restrict__ tri,
+                          double* __restrict__ gb) {
+  extern __shared__ double sh[];
+  double* M = sh;
+  double* v = M + d * d;
+  double* p = v + d;
+  double* dg = p + d;
+  double* e2 = dg + d;
+  __shared__ double red[32];
+  const int k = blockIdx.x, tid = threadIdx.x, bd = blockDim.x;
+  const double* Hk = Ht + (int64_t)k * d * d;
+  for (int t = tid; t < d * d; t += bd) M[t] = Hk[t];
+  __syncthreads();
+  householder_tridiag(d, M, v, p, dg, e2, red);
+  for (int i = tid; i < d; i += bd) {
+    tri[(int64_t)k * 2 * d + i] = dg[i];
+    tri[(int64_t)k * 2 * d + d + i] = i + 1 < d ? e2[i] : 0.0;
+  }
+  if (tid == 0) {
+    double lo = 1e300, hi = -1e300;
+    for (int i = 0; i < d; ++i) {
+      const double r = (i > 0 ? sqrt(e2[i - 1]) : 0.0) + (i + 1 < d ? sqrt(e2[i]) : 0.0);
+      lo = fmin(lo, dg[i] - r);
+      hi = fmax(hi, dg[i] + r);
+    }
+    gb[2 * k] = lo;
+    gb[2 * k + 1] = hi;
+  }
+}
+
+// out_k = L_k^{-1} H_k L_k^{-T} (symmetrised), one block per k
+__global__ void k_similarity(const double* __restrict__ L, const double* __restrict__ H, int d,
+                             double* __restrict__ out) {
+  extern __shared__ double sh[];
+  double* M = sh;
+  double* rl = M + d * d;
+  const int k = blockIdx.x, tid = threadIdx.x, bd = blockDim.x;
+  const double* Lk = L + (int64_t)k * d * d;
+  const double* Hk = H + (int64_t)k * d * d;
+  for (int i = tid; i < d; i += bd) rl[i] = 1.0 / Lk[(int64_t)i * d + i];
+  __syncthreads();
+  for (int col = tid; col < d; col += bd) {
+    for (int i = 0; i < d; ++i) {
+      double acc = Hk[(int64_t)i * d + col];
+      for (int q = 0; q < i; ++q) acc -= Lk[(int64_t)i * d + q] * M[col * d + q];
+      M[col * d + i] = acc * rl[i];
+    }
+  }
+  __syncthreads();
+  for (int col = tid; col < d; col += bd) {
+    for (int i = 0; i < d; ++i) {
+      double acc = M[i * d + col];
+      for (int q = 0; q < i; ++q) acc -= Lk[(int64_t)i * d + q] * M[q * d + col];
+      M[i * d + col] = acc * rl[i];
+    }
+  }
+  __syncthreads();
+  for (int t = tid; t < d * d; t += bd) {
+    const int i = t / d, j = t % d;
+    out[(int64_t)k * d * d + t] = i == j ? M[t] : 0.5 * (M[i * d + j] + M[j * d + i]);
+  }
+}
+
+// For A = nu I + eta T (T tridiagonal: diagonal dg, squared off-diagonal e2), the leading
+// principal minors theta_i of A (the continuants theta_i = a_i theta_{i-1} - b_i theta_{i-2},
+// a_i = nu + eta dg_i, b_i = eta^2 e2_{i-1}) and their first three nu-derivatives follow the
+// same three-term recurrence, with no division (rescaled by 2^-400 or 2^400 as they grow or
+// shrink; only ratios are used).  With p = theta'/theta, q = theta''/theta, u = theta'''/theta
+// of the last minor (theta_d = det A, so p = Tr A^-1):
+//   Tr A^-2 = p^2 - q,   d/dnu Tr A^-2 = -2 Tr A^-3 = 3 p q - 2 p^3 - u.
+// Returns false when a minor is not positive (nu at or left of -eta lambda_min).
+__device__ bool tri_trace2(const double* dg, const double* e2, int d, double nu, double eta,
+                           double* f, double* fp) {
+  double u0 = 1.0, u1 = 0.0, u2 = 0.0, u3 = 0.0;                  // theta_{i-2} and derivatives
+  double v0 = nu + eta * dg[0], v1 = 1.0, v2 = 0.0, v3 = 0.0;     // theta_{i-1}
+  if (!(v0 > 0.0)) return false;
+  const double eta2 = eta * eta;
+  for (int i = 1; i < d; ++i) {
+    const double a = nu + eta * dg[i], b = eta2 * e2[i - 1];
+    const double w0 = a * v0 - b * u0;
+    const double w1 = fma(a, v1, v0) - b * u1;
+    const double w2 = fma(a, v2, 2.0 * v1) - b * u2;
+    const double w3 = fma(a, v3, 3.0 * v2) - b * u3;
+    if (!(w0 > 0.0)) return false;
+    u0 = v0; u1 = v1; u2 = v2; u3 = v3;
+    v0 = w0; v1 = w1; v2 = w2; v3 = w3;
+    const double sc = v0 > 0x1p400 ? 0x1p-400 : (v0 < 0x1p-400 ? 0x1p400 : 1.0);
+    if (sc != 1.0) {
+      u0 *= sc; u1 *= sc; u2 *= sc; u3 *= sc;
+      v0 *= sc; v1 *= sc; v2 *= sc; v3 *= sc;
+    }
+  }
+  const double r = 1.0 / v0;
+  const double p = v1 * r, q = v2 * r, uu = v3 * r;
+  *f = p * p - q;
+  *fp = 3.0 * p * q - 2.0 * p * p * p - uu;
+  return true;
+}
+
+// nu of eq. 10 from the c tridiagonal forms: the root of F(nu) = sum_k Tr((nu I + eta T_k)^-2)
+// = 1, which is what sum_j (nu + eta lambda_j)^-2 = 1 states, the trace taken without the
+// eigenvalues.  Newton runs on psi(nu) = F^(-1/2) - 1: a power mean of the nu + eta lambda_j
+// (exponent -2) minus 1, increasing, concave and close to linear right of -eta lambda_min, so
+// the iterates reach the root in a few steps; they stay inside the bracket
+// [-eta max Gershgorin, sqrt(c d) - eta min Gershgorin], and a step that leaves it, or a trial
+// outside the SPD domain, bisects instead.  One block; thread k evaluates block k (and
+// k + blockDim, ...).
+__global__ void k_nu_tri(const double* __restrict__ tri, const double* __restrict__ gb, int c,
+                         int d, double eta, double* nu_out) {
+  __shared__ double red[32];
+  __shared__ double wmn[32], wmx[32];
+  __shared__ double s_lo, s_hi, s_nu;
+  __shared__ int s_bad, s_done;
+  double mn = 1e300, mx = -1e300;
+  for (int k = threadIdx.x; k < c; k += blockDim.x) {
+    mn = fmin(mn, gb[2 * k]);
+    mx = fmax(mx, gb[2 * k + 1]);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    wmn[threadIdx.x >> 5] = mn;
+    wmx[threadIdx.x >> 5] = mx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 1e300, b = -1e300;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      a = fmin(a, wmn[w]);
+      b = fmax(b, wmx[w]);
+    }
+    s_lo = -eta * b;
+    s_hi = sqrt((double)c * d) - eta * a;
+    s_nu = s_hi;
+    s_done = 0;
+  }
+  __syncthreads();
+  for (int it = 0; it < 300; ++it) {
+    const double nu = s_nu;
+    double f = 0.0, fp = 0.0;
+    int bad = 0;
+    for (int k = threadIdx.x; k < c; k += blockDim.x) {
+      double fk, fpk;
+      if (tri_trace2(tri + (int64_t)k * 2 * d, tri + (int64_t)k * 2 * d + d, d, nu, eta, &fk,
+                     &fpk)) {
+        f += fk;
+        fp += fpk;
+      } else {
+        bad = 1;
+      }
+    }
+    if (threadIdx.x == 0) s_bad = 0;
+    __syncthreads();
+    if (bad) atomicOr(&s_bad, 1);
+    const double F = block_sum_d(f, red);   // (synchronises: s_bad is complete after it)
+    const double FP = block_sum_d(fp, red);
+    if (threadIdx.x == 0) {
+      double lo = s_lo, hi = s_hi;
+      const bool left = s_bad || F - 1.0 > 0.0;   // left of the root, or of the domain
+      if (left) lo = nu;
+      else hi = nu;
+      if (!s_bad && F - 1.0 == 0.0) {
+        s_done = 1;
+      } else {
+        // psi = F^-1/2 - 1, psi' = -F^-3/2 F' / 2: nu - psi / psi' = nu + 2 (F - F^3/2) / F'
+        const bool newton = !s_bad && FP < 0.0 && F > 0.0;
+        const double step = newton ? 2.0 * (F - F * sqrt(F)) / FP : 0.0;
+        if (newton && fabs(step) <= 1e-12 * fabs(nu)) {
+          s_nu = nu + step;   // converged (as in k_nu_coop)
+          s_done = 1;
+        } else {
+          double nx = newton ? nu + step : 0.5 * (lo + hi);
+          if (!(nx > lo && nx < hi)) nx = 0.5 * (lo + hi);
+          if (nx == nu || hi - lo <= 4e-16 * fmax(fabs(lo), fabs(hi))) s_done = 1;
+          s_nu = nx;
+        }
+      }
+      s_lo = lo;
+      s_hi = hi;
+    }
+    __syncthreads();
+    if (s_done) break;
+  }
+  if (threadIdx.x == 0) *nu_out = s_nu;
+}
+
+// The same root on many SMs at once.  GB300 runs FP64 at a small fraction of its FP32 rate per
+// SM, and each block's recursion is sequential, so one block evaluating all c blocks spends
+// most of its time waiting on one SM's FP64 pipe: here block b evaluates classes b, b + grid,
+// ... (its lane 0 runs each recursion), and block 0 combines the partials in a fixed order and
+// takes the step.  Cooperative launch (every block resident), two grid barriers per step.
+// st: [lo, hi, nu, done]; part: 3 doubles per block (F, F', out-of-domain).
+__global__ void k_nu_coop(const double* __restrict__ tri, const double* __restrict__ gb, int c,
+                          int d, double eta, double* st, double* part, double* nu_out) {
+  cg::grid_group grid = cg::this_grid();
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    double a = 1e300, b = -1e300;
+    for (int k = 0; k < c; ++k) {
+      a = fmin(a, gb[2 * k]);
+      b = fmax(b, gb[2 * k + 1]);
+    }
+    st[0] = -eta * b;
+    st[1] = sqrt((double)c * d) - eta * a;
+    st[2] = st[1];
+    st[3] = 0.0;
+  }
+  grid.sync();
+  for (int it = 0; it < 300; ++it) {
+    const double nu = st[2];
+    if (threadIdx.x == 0) {
+      double f = 0.0, fp = 0.0, bad = 0.0;
+      for (int k = blockIdx.x; k < c; k += gridDim.x) {
+        double fk, fpk;
+        if (tri_trace2(tri + (int64_t)k * 2 * d, tri + (int64_t)k * 2 * d + d, d, nu, eta, &fk,
+                       &fpk)) {
+          f += fk;
+          fp += fpk;
+        } else {
+          bad = 1.0;
+        }
+      }
+      part[3 * blockIdx.x] = f;
+      part[3 * blockIdx.x + 1] = fp;
+      part[3 * blockIdx.x + 2] = bad;
+    }
+    grid.sync();
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      double F = 0.0, FP = 0.0;
+      bool bad = false;
+      for (int b = 0; b < (int)gridDim.x; ++b) {
+        F += part[3 * b];
+        FP += part[3 * b + 1];
+        bad = bad || part[3 * b + 2] != 0.0;
+      }
+      double lo = st[0], hi = st[1];
+      if (bad || F - 1.0 > 0.0) lo = nu;   // left of the root, or of the domain
+      else hi = nu;
+      if (!bad && F - 1.0 == 0.0) {
+        st[3] = 1.0;
+      } else {
+        // psi = F^-1/2 - 1, psi' = -F^-3/2 F' / 2: nu - psi / psi' = nu + 2 (F - F^3/2) / F'
+        const bool newton = !bad && FP < 0.0 && F > 0.0;
+        const double step = newton ? 2.0 * (F - F * sqrt(F)) / FP : 0.0;
+        // Newton converges quadratically: a step below 1e-12 nu leaves the next one far below
+        // the accuracy of F itself (~1e-13, the continuant ratios), so take it and stop
+        if (newton && fabs(step) <= 1e-12 * fabs(nu)) {
+          st[2] = nu + step;
+          st[3] = 1.0;
+        } else {
+          double nx = newton ? nu + step : 0.5 * (lo + hi);
+          if (!(nx > lo && nx < hi)) nx = 0.5 * (lo + hi);
+          if (nx == nu || hi - lo <= 4e-16 * fmax(fabs(lo), fabs(hi))) st[3] = 1.0;
+          st[2] = nx;
+        }
+      }
+      st[0] = lo;
+      st[1] = hi;
+    }
+    grid.sync();
+    if (st[3] != 0.0) break;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *nu_out = st[2];
+}
+
+int32_t sym_tri_nu(const double* Ht, int c, int d, double eta, double* tri, double* gb,
+                   double* nu_out, cudaStream_t st) {
+  const size_t smem = ((size_t)d * d + 4 * (size_t)d) * sizeof(double);
+  FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_sym_tri, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      200 * 1024));
+  ProfScope ps(st, PF_ROUND);
+  count_launch(2);
+  k_sym_tri<<<c, threads_for(d), smem, st>>>(Ht, d, tri, gb);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  // nu on up to one block per SM (cooperative launch: all blocks resident); the step state and
+  // the per-block partials live after the tridiagonal forms and bounds in the caller's buffer
+  int dev = 0, sms = 0;
+  FIRAL_CUDA_TRY(cudaGetDevice(&dev));
+  FIRAL_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  int nb = c < sms ? c : sms;
+  double* state = gb + 2 * (size_t)c;
+  double* part = state + 4;
+  void* args[] = {(void*)&tri, (void*)&gb, (void*)&c, (void*)&d, (void*)&eta, (void*)&state,
+                  (void*)&part, (void*)&nu_out};
+  FIRAL_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_nu_coop, dim3(nb), dim3(32), args, 0,
+                                             st));
+  return FIRAL_OK;
+}
+
+int32_t similarity_blocks(const double* L, const double* H, int c, int d, double* out,
+                          cudaStream_t st) {
+  const size_t smem = ((size_t)d * d + (size_t)d) * sizeof(double);
+  FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_similarity, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      200 * 1024));
+  ProfScope ps(st, PF_ROUND);
+  count_launch();
+  k_similarity<<<c, threads_for(d), smem, st>>>(L, H, d, out);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  return FIRAL_OK;
+}
+
+int32_t tilde_nu(const double* L, const double* H, int c, int d, double eta, double* tri,
+                 double* gb, double* nu_out, cudaStream_t st) {
+  const size_t smem = ((size_t)d * d + 5 * (size_t)d) * sizeof(double);
+  FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tilde_tri, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      200 * 1024));
+  ProfScope ps(st, PF_ROUND);
+  count_launch(2);
+  k_tilde_tri<<<c, threads_for(d), smem, st>>>(L, H, d, tri, gb);
+  k_nu_tri<<<1, 256, 0, st>>>(tri, gb, c, d, eta, nu_out);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  return FIRAL_OK;
+}
+
 int32_t tilde_eigvals(const double* L, const double* H, int c, int d, double* eig,
                       cudaStream_t st) {
-  const size_t smem = ((size_t)d * d + 4 * (size_t)d) * sizeof(double);
+  const size_t smem = ((size_t)d * d + 5 * (size_t)d) * sizeof(double);
   FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tilde_eig, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       200 * 1024));
   ProfScope ps(st, PF_ROUND);
@@ -372,11 +745,17 @@ __global__ void k_round_m(const double* __restrict__ Binv, const double* __restr
   }
 }
 
-// H_k += Ho_k / b + h_{it,k}(1 - h_{it,k}) x_it x_it^T   (pool row it, read from the device)
+// H_k += H_o,k / b + w_ik x_i x_i^T for the pick i (Algorithm 3 line 8; pool row i read from
+// the device, w_ik = h_ik (1 - h_ik)); with L and Ht given,
+// the transformed blocks too: Ht_k += Hot_k / b + w_ik y y^T with y = L_k^{-1} x_i
+// (Hot = L^{-1} H_o L^{-T}), so that Ht stays L^{-1} H L^{-T} without a similarity per pick.
+// Dynamic shared memory: d doubles (with L).
 template <class T>
 __global__ void k_round_hupdate(double* H, const double* Ho, double invb, const T* Xa,
                                 const T* Ha, int64_t m, int d, int c, const int32_t* it_ptr,
-                                int32_t t_index) {
+                                int32_t t_index, const double* L, double* Ht,
+                                const double* Hot) {
+  extern __shared__ double ys[];
   const int k = blockIdx.x;
   const int64_t row = m + it_ptr[t_index];
   const double hv = (double)Ha[row * c + k];
@@ -385,6 +764,22 @@ __global__ void k_round_hupdate(double* H, const double* Ho, double invb, const 
     const int e = t / d, f = t % d;
     const double xe = (double)Xa[row * d + e], xf = (double)Xa[row * d + f];
     H[(int64_t)k * d * d + t] += Ho[(int64_t)k * d * d + t] * invb + wk * xe * xf;
+  }
+  if (!L) return;
+  // y = L_k^{-1} x: forward substitution, column by column
+  const double* Lk = L + (int64_t)k * d * d;
+  for (int e = threadIdx.x; e < d; e += blockDim.x) ys[e] = (double)Xa[row * d + e];
+  __syncthreads();
+  for (int q = 0; q < d; ++q) {
+    const double yq = ys[q] / Lk[(int64_t)q * d + q];
+    __syncthreads();
+    if (threadIdx.x == 0) ys[q] = yq;
+    for (int i = q + 1 + threadIdx.x; i < d; i += blockDim.x) ys[i] -= Lk[(int64_t)i * d + q] * yq;
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < d * d; t += blockDim.x) {
+    const int e = t / d, f = t % d;
+    Ht[(int64_t)k * d * d + t] += Hot[(int64_t)k * d * d + t] * invb + wk * ys[e] * ys[f];
   }
 }
 
@@ -564,16 +959,20 @@ int32_t round_m(bool dbl, const double* Binv, const double* Sig, int c, int d, v
 }
 
 int32_t round_hupdate(firal_problem* P, double* H, const double* Ho, double invb,
-                      const int32_t* sel, int32_t t) {
+                      const int32_t* sel, int32_t t, const double* L, double* Ht,
+                      const double* Hot) {
   cudaStream_t st = P->H->stream;
   ProfScope ps(st, PF_ROUND);
   count_launch();
+  const size_t smem = (size_t)P->d * sizeof(double);
   if (P->dbl)
-    k_round_hupdate<double><<<P->c, 256, 0, st>>>(H, Ho, invb, P->Xa.as<double>(),
-                                                  P->Ha.as<double>(), P->m, P->d, P->c, sel, t);
+    k_round_hupdate<double><<<P->c, 256, smem, st>>>(H, Ho, invb, P->Xa.as<double>(),
+                                                     P->Ha.as<double>(), P->m, P->d, P->c, sel,
+                                                     t, L, Ht, Hot);
   else
-    k_round_hupdate<float><<<P->c, 256, 0, st>>>(H, Ho, invb, P->Xa.as<float>(),
-                                                 P->Ha.as<float>(), P->m, P->d, P->c, sel, t);
+    k_round_hupdate<float><<<P->c, 256, smem, st>>>(H, Ho, invb, P->Xa.as<float>(),
+                                                    P->Ha.as<float>(), P->m, P->d, P->c, sel,
+                                                    t, L, Ht, Hot);
   FIRAL_CUDA_TRY(cudaGetLastError());
   return FIRAL_OK;
 }
