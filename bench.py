@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--round-selections", type=int, default=20)
     ap.add_argument("--replicas", action="store_true",
                     help="N > 1: N independent problems instead of one row-sharded problem")
+    ap.add_argument("--only", default=None, choices=["round", "batched", "exact", "al"],
+                    help="run one sub-measurement alone and print its record (profiling runs)")
     ap.add_argument("--data-backend", default="nccl", choices=["nccl", "gloo"],
                     help="row-sharded runs: device allreduces over NCCL, or staged through host "
                          "memory over gloo (several ranks may then share one GPU: a functional "
@@ -349,10 +351,20 @@ def round_measure(args, H):
             ts = time.perf_counter()
             _, crit, best = prob.round_sweep(zr, bs, etas)
             torch.cuda.synchronize()
+            t_sweep = time.perf_counter() - ts
+            # the same chains one after another (one Round call per eta) for comparison
+            ts = time.perf_counter()
+            for e in etas:
+                prob.round(zr, bs, eta=e)
+            torch.cuda.synchronize()
+            t_seq = time.perf_counter() - ts
             out["eta_sweep"] = {"etas": etas, "budget": bs, "criteria_min_lambda_min": crit,
-                                "best": best, "seconds": time.perf_counter() - ts,
-                                "note": "one Round per eta (set-up included), criterion "
-                                        "min_k lambda_min of the selected points' Hessian blocks"}
+                                "best": best, "seconds": t_sweep,
+                                "seconds_one_round_per_eta": t_seq,
+                                "note": "the chains of all eta side by side (one score launch "
+                                        "per pick for all of them, set-up shared), criterion "
+                                        "min_k lambda_min of the selected points' Hessian "
+                                        "blocks; beside it, one Round call per eta"}
         out["fp32" if prec == "fp32" else "mixed"] = {
             "precision": prec, "value": 1.0 / per, "ms_per_selection": 1000.0 * per,
             "selections": max(1 + nsel, nover), "setup_ms": 1000.0 * (t1 - t0)}
@@ -893,9 +905,24 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_only(args):
+    """One sub-measurement on its own (the launch lists under profiles/ come from these)."""
+    import torch
+
+    from paper_2409_07392_gb300 import api, build
+    build.build()
+    torch.cuda.set_device(0)
+    H = api.Handle()
+    fn = {"round": round_measure, "batched": batched_measure, "exact": exact_measure,
+          "al": al_measure}[args.only]
+    print(json.dumps({"only": args.only, "record": fn(args, H)}), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.only:
+        run_only(a)
     else:
         run_ours(a)

@@ -206,7 +206,7 @@ int32_t tc_quad_forms(firal_problem* P, const void* A, const void* B, int s, dou
 int32_t tc_syrk_blocks(firal_problem* P, const void* w, double lamS, void* outS, double lamP,
                        double* outP);
 int32_t tc_round_scores(firal_problem* P, const void* M1, const void* M2, const uint8_t* mask,
-                        double eta, double* pv, int64_t* pi, int* np_out);
+                        const double* etas, int n_chain, double* pv, int64_t* pi, int* np_out);
 bool tc_available();
 
 }  // namespace firal
@@ -621,23 +621,29 @@ int32_t round_setup(firal_problem* P, const void* zr, RoundSetup& rs) {
   return FIRAL_OK;
 }
 
-// One Round chain (Algorithm 3 lines 4-12) for one eta on a prepared set-up.
-int32_t round_chain(firal_problem* P, const RoundSetup& rs, int32_t b, const firal_round_opts* o,
-                    int32_t* sel, firal_round_stats* stats) {
+// Round chains (Algorithm 3 lines 4-12) for n_chain values of eta on one prepared set-up, run
+// side by side pick by pick: one eq. 14 score launch covers every chain (tensor-core path),
+// and each per-pick block step (update, tridiagonal forms, Cholesky, M1/M2) is one launch over
+// the stacked c x n_chain blocks; only the scalar root nu and the pick are per chain.
+// sel: n_chain x b picks (row e = eta etas[e]).  stats (chain 0) may be NULL.
+int32_t round_chains(firal_problem* P, const RoundSetup& rs, int32_t b, const double* etas,
+                     int ne, int32_t* sel, firal_round_stats* stats) {
   cudaStream_t st = P->H->stream;
   const int c = P->c, d = P->d;
   const int64_t D = P->D;
-  const double eta = (o && o->eta > 0) ? o->eta : 8.0 * std::sqrt((double)D);
   const size_t blk = (size_t)c * d * d;
   const double* Sig = rs.Sig.as<double>();
   const double* L = rs.L.as<double>();
-  DBuf Bm, Binv, Hk, M1, M2, eig, nu, mask, pv, pi, score, Tg, Ht, Hot;
+  DBuf Bm, Binv, Hk, M1, M2, eig, nu, mask, pv, pi, score, Tg, Ht, Hot, Sig3;
   auto rel = [&]() {
     for (DBuf* bf : {&Bm, &Binv, &Hk, &M1, &M2, &eig, &nu, &mask, &pv, &pi, &score, &Tg, &Ht,
-                     &Hot})
+                     &Hot, &Sig3})
       bf->release();
   };
   const int np = (int)std::max<int64_t>((P->n + 127) / 128, P->sms);
+  // per chain: tridiagonal forms (2 c d), Gershgorin bounds (2 c), nu step state and
+  // per-SM partials (4 + 3 * 1024)
+  const size_t tri_sz = (size_t)2 * c * d, gb_sz = (size_t)2 * c, work_sz = 4 + 3 * 1024;
   int32_t rc = FIRAL_OK;
 #define TRYR(x)                    \
   do {                             \
@@ -647,57 +653,74 @@ int32_t round_chain(firal_problem* P, const RoundSetup& rs, int32_t b, const fir
       return rc;                   \
     }                              \
   } while (0)
-  TRYR(Bm.ensure(blk * 8));
-  TRYR(Binv.ensure(blk * 8));
-  TRYR(Hk.ensure(blk * 8));
-  TRYR(M1.ensure(blk * vsize(P)));
-  TRYR(M2.ensure(blk * vsize(P)));
-  // tridiagonal forms, Gershgorin bounds, nu step state (4) and per-SM partials (3 each)
-  TRYR(eig.ensure(((size_t)2 * c * d + 2 * c + 4 + 3 * 1024) * 8));
-  TRYR(nu.ensure(8));
-  TRYR(mask.ensure((size_t)P->n));
-  TRYR(pv.ensure((size_t)np * 8));
-  TRYR(pi.ensure((size_t)np * 8));
-  TRYR(score.ensure(8));
-  TRYR(Tg.ensure(blk * 8));
+  TRYR(Bm.ensure(ne * blk * 8));
+  TRYR(Binv.ensure(ne * blk * 8));
+  TRYR(Hk.ensure(ne * blk * 8));
+  TRYR(M1.ensure(ne * blk * vsize(P)));
+  TRYR(M2.ensure(ne * blk * vsize(P)));
+  TRYR(eig.ensure(ne * (tri_sz + gb_sz + work_sz) * 8));
+  TRYR(nu.ensure(ne * 8));
+  TRYR(mask.ensure((size_t)ne * P->n));
+  TRYR(pv.ensure((size_t)ne * np * 8));
+  TRYR(pi.ensure((size_t)ne * np * 8));
+  TRYR(score.ensure(ne * 8));
+  TRYR(Tg.ensure(ne * blk * 8));
   // H~ = L^{-1} H L^{-T} kept up to date pick by pick (rank one plus L^{-1} H_o L^{-T} / b)
-  TRYR(Ht.ensure(blk * 8));
+  TRYR(Ht.ensure(ne * blk * 8));
   TRYR(Hot.ensure(blk * 8));
   const int64_t tot = (int64_t)blk;
-  // line 4: B_1 = sqrt(d~) Sigma + (eta/b) H_o
-  TRYR(lincomb(Bm.as<double>(), std::sqrt((double)D), Sig, eta / b, P->HoBlk.as<double>(), 0.0,
-               nullptr, tot, st));
-  TRYR(chol_inv(P->dbl, Bm.as<double>(), c, d, nullptr, Binv.as<double>(), nullptr,
+  double* tri = eig.as<double>();
+  double* gb = tri + ne * tri_sz;
+  double* work = gb + ne * gb_sz;
+  auto Bm_e = [&](int e) { return Bm.as<double>() + e * blk; };
+  auto Hk_e = [&](int e) { return Hk.as<double>() + e * blk; };
+  auto Ht_e = [&](int e) { return Ht.as<double>() + e * blk; };
+  auto M_e = [&](DBuf& M, int e) { return (void*)((char*)M.p + e * blk * vsize(P)); };
+  // line 4: B_1 = sqrt(d~) Sigma + (eta/b) H_o, for every chain
+  for (int e = 0; e < ne; ++e)
+    TRYR(lincomb(Bm_e(e), std::sqrt((double)D), Sig, etas[e] / b, P->HoBlk.as<double>(), 0.0,
+                 nullptr, tot, st));
+  TRYR(chol_inv(P->dbl, Bm.as<double>(), c * ne, d, nullptr, Binv.as<double>(), nullptr,
                 not_spd_flag(P->H), st));
-  TRYR(round_m(P->dbl, Binv.as<double>(), Sig, c, d, M1.p, M2.p, Tg.as<double>(), st));
-  FIRAL_CUDA_TRY(cudaMemsetAsync(Hk.p, 0, blk * 8, st));
-  FIRAL_CUDA_TRY(cudaMemsetAsync(Ht.p, 0, blk * 8, st));
+  TRYR(round_m(P->dbl, Binv.as<double>(), Sig, c, d, M1.p, M2.p, Tg.as<double>(), st, ne));
+  FIRAL_CUDA_TRY(cudaMemsetAsync(Hk.p, 0, ne * blk * 8, st));
+  FIRAL_CUDA_TRY(cudaMemsetAsync(Ht.p, 0, ne * blk * 8, st));
   TRYR(similarity_blocks(L, P->HoBlk.as<double>(), c, d, Hot.as<double>(), st));
-  FIRAL_CUDA_TRY(cudaMemsetAsync(mask.p, 0, (size_t)P->n, st));
+  FIRAL_CUDA_TRY(cudaMemsetAsync(mask.p, 0, (size_t)ne * P->n, st));
   for (int t = 0; t < b; ++t) {
-    // line 7: eq. 14 scores and the masked argmax (tensor cores for FIRAL_MIXED_BF16)
+    // line 7: eq. 14 scores and the masked argmax of every chain (one tensor-core launch for
+    // FIRAL_MIXED_BF16*)
     int npart = np;
-    if (is_mixed(P->prec))
-      TRYR(tc_round_scores(P, M1.p, M2.p, mask.as<uint8_t>(), eta, pv.as<double>(),
+    if (is_mixed(P->prec)) {
+      TRYR(tc_round_scores(P, M1.p, M2.p, mask.as<uint8_t>(), etas, ne, pv.as<double>(),
                            pi.as<int64_t>(), &npart));
-    else
-      TRYR(round_scores(P, M1.p, M2.p, mask.as<uint8_t>(), eta, pv.as<double>(),
-                        pi.as<int64_t>(), np));
-    TRYR(round_pick(pv.as<double>(), pi.as<int64_t>(), npart, mask.as<uint8_t>(), sel, t,
-                    score.as<double>(), st));
-    // line 8: H_k += B_k(H_o)/b + w x x^T
-    TRYR(round_hupdate(P, Hk.as<double>(), P->HoBlk.as<double>(), 1.0 / b, sel, t, L,
-                       Ht.as<double>(), Hot.as<double>()));
+    } else {
+      for (int e = 0; e < ne; ++e)
+        TRYR(round_scores(P, M_e(M1, e), M_e(M2, e), mask.as<uint8_t>() + (size_t)e * P->n,
+                          etas[e], pv.as<double>() + (size_t)e * np,
+                          pi.as<int64_t>() + (size_t)e * np, np));
+    }
+    for (int e = 0; e < ne; ++e) {
+      TRYR(round_pick(pv.as<double>() + (size_t)e * npart, pi.as<int64_t>() + (size_t)e * npart,
+                      npart, mask.as<uint8_t>() + (size_t)e * P->n, sel + (size_t)e * b, t,
+                      score.as<double>() + e, st));
+      // line 8: H_k += B_k(H_o)/b + w x x^T (and H~_k alongside)
+      TRYR(round_hupdate(P, Hk_e(e), P->HoBlk.as<double>(), 1.0 / b, sel + (size_t)e * b, t, L,
+                         Ht_e(e), Hot.as<double>()));
+    }
     // lines 9-10: nu with sum_j (nu + eta lambda_j(H~_k))^-2 = 1, from the tridiagonal forms
     // of H~_k (the eigenvalues enter only through that trace)
-    TRYR(sym_tri_nu(Ht.as<double>(), c, d, eta, eig.as<double>(),
-                    eig.as<double>() + (size_t)2 * c * d, nu.as<double>(), st));
+    TRYR(sym_tri(Ht.as<double>(), c * ne, d, tri, gb, st));
+    for (int e = 0; e < ne; ++e)
+      TRYR(nu_of_tri(tri + e * tri_sz, gb + e * gb_sz, c, d, etas[e], work + e * work_sz,
+                     nu.as<double>() + e, st));
     // line 11: B = nu Sigma + eta H + (eta/b) H_o, inverted
-    TRYR(lincomb_nu(Bm.as<double>(), nu.as<double>(), Sig, eta, Hk.as<double>(), eta / b,
-                    P->HoBlk.as<double>(), tot, st));
-    TRYR(chol_inv(P->dbl, Bm.as<double>(), c, d, nullptr, Binv.as<double>(), nullptr,
+    for (int e = 0; e < ne; ++e)
+      TRYR(lincomb_nu(Bm_e(e), nu.as<double>() + e, Sig, etas[e], Hk_e(e), etas[e] / b,
+                      P->HoBlk.as<double>(), tot, st));
+    TRYR(chol_inv(P->dbl, Bm.as<double>(), c * ne, d, nullptr, Binv.as<double>(), nullptr,
                   not_spd_flag(P->H), st));
-    TRYR(round_m(P->dbl, Binv.as<double>(), Sig, c, d, M1.p, M2.p, Tg.as<double>(), st));
+    TRYR(round_m(P->dbl, Binv.as<double>(), Sig, c, d, M1.p, M2.p, Tg.as<double>(), st, ne));
   }
   if (stats) {
     double h[2];
@@ -721,7 +744,8 @@ int32_t round_impl(firal_problem* P, const void* zr, int32_t b, const firal_roun
   if (P->dbl && P->d > 90) return fail(FIRAL_ERR_UNSUPPORTED, "FP64 Round supports d <= 90");
   RoundSetup rs;
   FIRAL_TRY(round_setup(P, zr, rs));
-  FIRAL_TRY(round_chain(P, rs, b, o, sel, stats));
+  const double eta = (o && o->eta > 0) ? o->eta : 8.0 * std::sqrt((double)P->D);
+  FIRAL_TRY(round_chains(P, rs, b, &eta, 1, sel, stats));
   return read_flags(P->H);
 }
 
@@ -1146,15 +1170,15 @@ int32_t round_sweep_impl(firal_problem* P, const void* zr, int32_t b, const doub
   if (b < 1 || b > P->n) return fail(FIRAL_ERR_ARG, "budget must be in [1, n]");
   if (sharded(P)) return fail(FIRAL_ERR_UNSUPPORTED, "Round does not take a row-sharded problem");
   if (P->dbl && P->d > 90) return fail(FIRAL_ERR_UNSUPPORTED, "FP64 Round supports d <= 90");
-  firal_round_opts oe = o ? *o : firal_round_opts{0.0, 1, P->prec};
   // the eta-independent set-up once, then one chain per eta
   RoundSetup rs;
   FIRAL_TRY(round_setup(P, zr, rs));
-  for (int e = 0; e < neta; ++e) {
-    oe.eta = etas[e];
-    FIRAL_TRY(round_chain(P, rs, b, &oe, sel + (size_t)e * b, nullptr));
-    FIRAL_TRY(selected_min_eig(P, sel + (size_t)e * b, b, &crit[e]));
+  // the chains of up to 8 values of eta side by side (one score launch per pick for all)
+  for (int e0 = 0; e0 < neta; e0 += 8) {
+    const int ne = std::min(8, neta - e0);
+    FIRAL_TRY(round_chains(P, rs, b, etas + e0, ne, sel + (size_t)e0 * b, nullptr));
   }
+  for (int e = 0; e < neta; ++e) FIRAL_TRY(selected_min_eig(P, sel + (size_t)e * b, b, &crit[e]));
   int bi = 0;
   for (int e = 1; e < neta; ++e)
     if (crit[e] > crit[bi]) bi = e;

@@ -269,6 +269,9 @@ int32_t tilde_nu(const double* L, const double* H, int c, int d, double eta, dou
                  double* gb, double* nu_out, cudaStream_t st);
 int32_t sym_tri_nu(const double* Ht, int c, int d, double eta, double* tri, double* gb,
                    double* nu_out, cudaStream_t st);
+int32_t sym_tri(const double* Ht, int nblocks, int d, double* tri, double* gb, cudaStream_t st);
+int32_t nu_of_tri(const double* tri, const double* gb, int c, int d, double eta, double* work,
+                  double* nu_out, cudaStream_t st);
 int32_t similarity_blocks(const double* L, const double* H, int c, int d, double* out,
                           cudaStream_t st);
 int32_t nu_bisect_dev(const double* lam, int64_t count, double scale, double* nu_out,
@@ -278,7 +281,7 @@ int32_t round_scores(firal_problem* P, const void* M1, const void* M2, const uin
 int32_t round_pick(const double* pv, const int64_t* pi, int np, uint8_t* mask, int32_t* sel,
                    int32_t t, double* score_out, cudaStream_t st);
 int32_t round_m(bool dbl, const double* Binv, const double* Sig, int c, int d, void* M1, void* M2,
-                double* Tg, cudaStream_t st);
+                double* Tg, cudaStream_t st, int n_chain = 1);
 int32_t round_hupdate(firal_problem* P, double* H, const double* Ho, double invb,
                       const int32_t* sel, int32_t t, const double* L = nullptr,
                       double* Ht = nullptr, const double* Hot = nullptr);

@@ -571,28 +571,41 @@ __global__ void k_nu_coop(const double* __restrict__ tri, const double* __restri
   if (blockIdx.x == 0 && threadIdx.x == 0) *nu_out = st[2];
 }
 
-int32_t sym_tri_nu(const double* Ht, int c, int d, double eta, double* tri, double* gb,
-                   double* nu_out, cudaStream_t st) {
+int32_t sym_tri(const double* Ht, int nblocks, int d, double* tri, double* gb, cudaStream_t st) {
   const size_t smem = ((size_t)d * d + 4 * (size_t)d) * sizeof(double);
   FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_sym_tri, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       200 * 1024));
   ProfScope ps(st, PF_ROUND);
-  count_launch(2);
-  k_sym_tri<<<c, threads_for(d), smem, st>>>(Ht, d, tri, gb);
+  count_launch();
+  k_sym_tri<<<nblocks, threads_for(d), smem, st>>>(Ht, d, tri, gb);
   FIRAL_CUDA_TRY(cudaGetLastError());
-  // nu on up to one block per SM (cooperative launch: all blocks resident); the step state and
-  // the per-block partials live after the tridiagonal forms and bounds in the caller's buffer
+  return FIRAL_OK;
+}
+
+// nu from c tridiagonal forms (tri: 2 c d doubles, gb: 2 c) on up to one block per SM;
+// work: 4 + 3 * SMs doubles of step state and per-block partials.
+int32_t nu_of_tri(const double* tri, const double* gb, int c, int d, double eta, double* work,
+                  double* nu_out, cudaStream_t st) {
+  ProfScope ps(st, PF_ROUND);
+  count_launch();
   int dev = 0, sms = 0;
   FIRAL_CUDA_TRY(cudaGetDevice(&dev));
   FIRAL_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   int nb = c < sms ? c : sms;
-  double* state = gb + 2 * (size_t)c;
+  double* state = work;
   double* part = state + 4;
   void* args[] = {(void*)&tri, (void*)&gb, (void*)&c, (void*)&d, (void*)&eta, (void*)&state,
                   (void*)&part, (void*)&nu_out};
   FIRAL_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_nu_coop, dim3(nb), dim3(32), args, 0,
                                              st));
   return FIRAL_OK;
+}
+
+int32_t sym_tri_nu(const double* Ht, int c, int d, double eta, double* tri, double* gb,
+                   double* nu_out, cudaStream_t st) {
+  FIRAL_TRY(sym_tri(Ht, c, d, tri, gb, st));
+  // the step state and the per-block partials live after the bounds in the caller's buffer
+  return nu_of_tri(tri, gb, c, d, eta, gb + 2 * (size_t)c, nu_out, st);
 }
 
 int32_t similarity_blocks(const double* L, const double* H, int c, int d, double* out,
@@ -720,12 +733,13 @@ __global__ void k_axpbypcz_nu(double* out, const double* nu, const double* X, do
 // memory; Sig_k Binv_k goes through the global scratch Tg (c*d*d doubles).
 template <class T>
 __global__ void k_round_m(const double* __restrict__ Binv, const double* __restrict__ Sig, int d,
-                          T* __restrict__ M1, T* __restrict__ M2, double* __restrict__ Tg) {
+                          T* __restrict__ M1, T* __restrict__ M2, double* __restrict__ Tg,
+                          int c_sig) {
   extern __shared__ double sh[];
   double* Bs = sh;           // d*d
   const int k = blockIdx.x, tid = threadIdx.x, bd = blockDim.x;
   const double* Bk = Binv + (int64_t)k * d * d;
-  const double* Sk = Sig + (int64_t)k * d * d;
+  const double* Sk = Sig + (int64_t)(k % c_sig) * d * d;   // Sigma shared by stacked chains
   double* Ts = Tg + (int64_t)k * d * d;
   for (int t = tid; t < d * d; t += bd) Bs[t] = Bk[t];
   __syncthreads();
@@ -941,18 +955,21 @@ int32_t round_pick(const double* pv, const int64_t* pi, int np, uint8_t* mask, i
 }
 
 int32_t round_m(bool dbl, const double* Binv, const double* Sig, int c, int d, void* M1, void* M2,
-                double* Tg, cudaStream_t st) {
+                double* Tg, cudaStream_t st, int n_chain) {
   const size_t smem = (size_t)d * d * sizeof(double);
+  const int nb = c * n_chain;   // chains stacked: block k uses Sigma block k mod c
   ProfScope ps(st, PF_ROUND);
   count_launch();
   if (dbl) {
     FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_round_m<double>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    k_round_m<double><<<c, threads_for(d), smem, st>>>(Binv, Sig, d, (double*)M1, (double*)M2, Tg);
+    k_round_m<double><<<nb, threads_for(d), smem, st>>>(Binv, Sig, d, (double*)M1, (double*)M2,
+                                                        Tg, c);
   } else {
     FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_round_m<float>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    k_round_m<float><<<c, threads_for(d), smem, st>>>(Binv, Sig, d, (float*)M1, (float*)M2, Tg);
+    k_round_m<float><<<nb, threads_for(d), smem, st>>>(Binv, Sig, d, (float*)M1, (float*)M2, Tg,
+                                                       c);
   }
   FIRAL_CUDA_TRY(cudaGetLastError());
   return FIRAL_OK;

@@ -1724,16 +1724,26 @@ constexpr int M_BYTES = BN * BK * 2;
 constexpr int STAGE_BYTES = Z_BYTES + 2 * M_BYTES;       // 80 KB
 template <int DP> struct L {
   static constexpr int X_BYTES = BM * DP * 2;
-  static constexpr int SMEM = STAGES * STAGE_BYTES + X_BYTES + 1024 + 512;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + X_BYTES + 1024 + 1024;
 };
 }  // namespace r_cfg
+
+// Round chains scored in one launch (an eta sweep runs its chains side by side): chain e uses
+// eta[e], its own mask (mask + e * mask_stride) and its own M~ rows; its per-CTA winners land
+// at part[e * gridDim.x + cta].
+constexpr int RC_MAX = 8;
+struct RoundChains {
+  int n;
+  int64_t mask_stride;
+  double eta[RC_MAX];
+};
 
 struct RoundCtl {
   uint64_t full[2], empty[2], zfull[2], xfull, xempty, tfull, tempty, drain;
   uint32_t tmem_base;
   int abort_w;
-  double bval[8];
-  long long bidx[8];
+  double bval[4 * RC_MAX];
+  long long bidx[4 * RC_MAX];
 };
 
 template <int DP>
@@ -1741,8 +1751,8 @@ __global__ void __launch_bounds__(256, 1)
     k_tc_round(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapMh,
                const __grid_constant__ CUtensorMap mapMl, const short2* __restrict__ tab,
                const float* __restrict__ Ha, const uint8_t* __restrict__ mask, int64_t m,
-               int64_t n, int c, int n_kc, int kblocks, double eta, double* part_val,
-               int64_t* part_idx, int32_t* err) {
+               int64_t n, int c, int n_kc, int kblocks, const RoundChains rc,
+               double* part_val, int64_t* part_idx, int32_t* err) {
   using namespace r_cfg;
   using LL = L<DP>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -1774,6 +1784,7 @@ __global__ void __launch_bounds__(256, 1)
   const uint32_t tmem = ctl->tmem_base;
   volatile int* abort_w = &ctl->abort_w;
   const int n_mt = (int)((n + BM - 1) / BM);
+  const int n_ch = rc.n * n_kc;   // (chain, class chunk) pairs, chain-major
   constexpr uint32_t TX = 2 * M_BYTES;
 
   if (warp == 0 && lane == 0) {
@@ -1792,7 +1803,7 @@ __global__ void __launch_bounds__(256, 1)
       mbar_expect_tx(&ctl->xfull, LL::X_BYTES);
       tma_load_2d(xs, &mapX, &ctl->xfull, 0, (int)(m + (int64_t)mt * BM));
       xphase ^= 1;
-      for (int kc = 0; kc < n_kc && ok; ++kc) {
+      for (int kc = 0; kc < n_ch && ok; ++kc) {
         for (int kb = 0; kb < kblocks; ++kb) {
           if (!mbar_wait(&ctl->empty[stage], phase ^ 1, abort_w)) {
             atomicExch(err, 32);
@@ -1824,7 +1835,7 @@ __global__ void __launch_bounds__(256, 1)
     uint32_t phase = 0, acc_phase = 0;
     bool ok = true;
     for (int mt = blockIdx.x; mt < n_mt && ok && !*abort_w; mt += gridDim.x) {
-      for (int kc = 0; kc < n_kc && ok; ++kc) {
+      for (int kc = 0; kc < n_ch && ok; ++kc) {
         if (!mbar_wait(&ctl->tempty, acc_phase ^ 1, abort_w)) {
           atomicExch(err, 33);
           ctl->abort_w = 1;
@@ -1868,8 +1879,13 @@ __global__ void __launch_bounds__(256, 1)
     int stage = 0;
     uint32_t phase = 0, xphase = 0, acc_phase = 0;
     bool ok = true;
-    double best = -INFINITY;
-    long long besti = LLONG_MAX;
+    double best[RC_MAX];
+    long long besti[RC_MAX];
+#pragma unroll
+    for (int e = 0; e < RC_MAX; ++e) {
+      best[e] = -INFINITY;
+      besti[e] = LLONG_MAX;
+    }
     for (int mt = blockIdx.x; mt < n_mt && ok && !*abort_w; mt += gridDim.x) {
       if (!mbar_wait(&ctl->xfull, xphase, abort_w)) {
         atomicExch(err, 35);
@@ -1878,7 +1894,10 @@ __global__ void __launch_bounds__(256, 1)
       }
       xphase ^= 1;
       double score = 0.0;   // epilogue threads: this point's eq. 14 sum over class chunks
-      for (int kc = 0; kc < n_kc && ok; ++kc) {
+      for (int ch = 0; ch < n_ch && ok; ++ch) {
+        const int ce = ch / n_kc, kc = ch - ce * n_kc;   // chain, class chunk
+        const double eta = rc.eta[ce];
+        if (kc == 0) score = 0.0;
         for (int kb = 0; kb < kblocks; ++kb) {
           // the MMA warp must have released this stage (previous round) before Z is rewritten
           if (!mbar_wait(&ctl->empty[stage], phase ^ 1, abort_w)) {
@@ -1943,46 +1962,51 @@ __global__ void __launch_bounds__(256, 1)
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(&ctl->tempty);
+          if (kc == n_kc - 1) {   // the chain's score is complete: masked running argmax
+            const int64_t row = (int64_t)mt * BM + q * 32 + lane;
+            if (row < n && !mask[ce * rc.mask_stride + row] && score == score &&
+                (score > best[ce] || (score == best[ce] && row < besti[ce]))) {
+              best[ce] = score;
+              besti[ce] = row;
+            }
+          }
         }
         acc_phase ^= 1;
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&ctl->xempty);
-      if (warp >= 4) {
-        const int64_t row = (int64_t)mt * BM + (warp & 3) * 32 + lane;
-        if (row < n && !mask[row] && score == score &&
-            (score > best || (score == best && row < besti))) {
-          best = score;
-          besti = row;
-        }
-      }
     }
     if (warp >= 4) {
-      for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_xor_sync(0xffffffffu, best, o);
-        const long long oi = __shfl_xor_sync(0xffffffffu, besti, o);
-        if (ov > best || (ov == best && oi < besti)) {
-          best = ov;
-          besti = oi;
+      for (int e = 0; e < rc.n; ++e) {
+        double bv = best[e];
+        long long bix = besti[e];
+        for (int o = 16; o > 0; o >>= 1) {
+          const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+          const long long oi = __shfl_xor_sync(0xffffffffu, bix, o);
+          if (ov > bv || (ov == bv && oi < bix)) {
+            bv = ov;
+            bix = oi;
+          }
         }
-      }
-      if (lane == 0) {
-        ctl->bval[warp - 4] = best;
-        ctl->bidx[warp - 4] = besti;
+        if (lane == 0) {
+          ctl->bval[e * 4 + warp - 4] = bv;
+          ctl->bidx[e * 4 + warp - 4] = bix;
+        }
       }
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double b = ctl->bval[0];
-    long long bi = ctl->bidx[0];
+  if (threadIdx.x < rc.n) {
+    const int e = threadIdx.x;
+    double b = ctl->bval[e * 4];
+    long long bi = ctl->bidx[e * 4];
     for (int w = 1; w < 4; ++w)
-      if (ctl->bval[w] > b || (ctl->bval[w] == b && ctl->bidx[w] < bi)) {
-        b = ctl->bval[w];
-        bi = ctl->bidx[w];
+      if (ctl->bval[e * 4 + w] > b || (ctl->bval[e * 4 + w] == b && ctl->bidx[e * 4 + w] < bi)) {
+        b = ctl->bval[e * 4 + w];
+        bi = ctl->bidx[e * 4 + w];
       }
-    part_val[blockIdx.x] = b;
-    part_idx[blockIdx.x] = bi;
+    part_val[e * gridDim.x + blockIdx.x] = b;
+    part_idx[e * gridDim.x + blockIdx.x] = bi;
   }
   if (warp == 1) {
     __syncwarp();
@@ -1995,11 +2019,12 @@ __global__ void __launch_bounds__(256, 1)
 // at pair p of the 8-aligned table (0 where e' < e or beyond d), bf16 hi and lo
 template <class T>
 __global__ void k_round_mpairs(bf16* Mh, bf16* Ml, const T* M1, const T* M2, const short2* tab,
-                               int c, int d, int kpad) {
-  const int row = blockIdx.x;                 // kc*256 + which*128 + kk
-  const int kc = row / 256, which = (row / 128) & 1, kk = row & 127;
+                               int c, int d, int kpad, int n_kc) {
+  const int row = blockIdx.x;                 // (chain * n_kc + kc)*256 + which*128 + kk
+  const int ce = row / (n_kc * 256), kc = (row / 256) % n_kc, which = (row / 128) & 1,
+            kk = row & 127;
   const int k = kc * 128 + kk;
-  const T* M = (which == 0 ? M1 : M2) + (int64_t)k * d * d;
+  const T* M = (which == 0 ? M1 : M2) + ((int64_t)ce * c + k) * d * d;
   for (int p = threadIdx.x; p < kpad; p += blockDim.x) {
     float v = 0.0f;
     const short2 ee = tab[p >> 3];
@@ -2637,8 +2662,8 @@ static int32_t tc_quad_t(firal_problem* P, const float* A, const float* B, int s
 
 template <int DP>
 static int32_t tc_round_scores_t(firal_problem* P, const float* M1, const float* M2,
-                                 const uint8_t* mask, double eta, double* pv, int64_t* pi,
-                                 int* np_out) {
+                                 const uint8_t* mask, const double* etas, int n_chain,
+                                 double* pv, int64_t* pi, int* np_out) {
   using namespace r_cfg;
   cudaStream_t st = P->H->stream;
   const int d = P->d, c = P->c;
@@ -2660,19 +2685,25 @@ static int32_t tc_round_scores_t(firal_problem* P, const float* M1, const float*
   const int kblocks = P->rtab_chunks / 8;
   const int kpad = kblocks * BK;
   const int n_kc = (c + 127) / 128;
-  const size_t mbytes = (size_t)n_kc * BN * kpad * 2;
+  if (n_chain < 1 || n_chain > RC_MAX) return fail(FIRAL_ERR_ARG, "1 to 8 Round chains per launch");
+  const int rows = n_chain * n_kc * BN;
+  const size_t mbytes = (size_t)rows * kpad * 2;
   FIRAL_TRY(P->rM.ensure(2 * mbytes));
   bf16* Mh = P->rM.as<bf16>();
   bf16* Ml = Mh + mbytes / 2;
   ProfScope ps(st, PF_ROUND);
   count_launch(2);
-  k_round_mpairs<float><<<n_kc * BN, 256, 0, st>>>(Mh, Ml, M1, M2, P->rtab.as<short2>(), c, d,
-                                                   kpad);
+  k_round_mpairs<float><<<rows, 256, 0, st>>>(Mh, Ml, M1, M2, P->rtab.as<short2>(), c, d, kpad,
+                                              n_kc);
   FIRAL_CUDA_TRY(cudaGetLastError());
   CUtensorMap mX, mMh, mMl;
   FIRAL_TRY(make_map(&mX, P->Xb.p, P->Np, DP, BM, DP, false));
-  FIRAL_TRY(make_map(&mMh, Mh, (uint64_t)n_kc * BN, kpad, BN, BK, true));
-  FIRAL_TRY(make_map(&mMl, Ml, (uint64_t)n_kc * BN, kpad, BN, BK, true));
+  FIRAL_TRY(make_map(&mMh, Mh, (uint64_t)rows, kpad, BN, BK, true));
+  FIRAL_TRY(make_map(&mMl, Ml, (uint64_t)rows, kpad, BN, BK, true));
+  RoundChains rc{};
+  rc.n = n_chain;
+  rc.mask_stride = P->n;
+  for (int e = 0; e < n_chain; ++e) rc.eta[e] = etas[e];
   static bool attr[4] = {false, false, false, false};
   const int ai = DP == 16 ? 0 : DP == 32 ? 1 : DP == 64 ? 2 : 3;
   if (!attr[ai]) {
@@ -2684,21 +2715,23 @@ static int32_t tc_round_scores_t(firal_problem* P, const float* M1, const float*
   const int grid = std::min(n_mt, sms);
   k_tc_round<DP><<<grid, 256, L<DP>::SMEM, st>>>(mX, mMh, mMl, P->rtab.as<short2>(),
                                                   P->Ha.as<float>(), mask, P->m, P->n, c, n_kc,
-                                                  kblocks, eta, pv, pi, tc_error_word(P));
+                                                  kblocks, rc, pv, pi, tc_error_word(P));
   FIRAL_CUDA_TRY(cudaGetLastError());
   *np_out = grid;
   return FIRAL_OK;
 }
 
+// Scores of n_chain Round chains in one launch: chain e has eta etas[e], M1/M2 blocks at
+// M1 + e c d d, mask at mask + e n, and its CTA winners at pv/pi + e * (*np_out).
 int32_t tc_round_scores(firal_problem* P, const void* M1, const void* M2, const uint8_t* mask,
-                        double eta, double* pv, int64_t* pi, int* np_out) {
+                        const double* etas, int n_chain, double* pv, int64_t* pi, int* np_out) {
   const float* a = (const float*)M1;
   const float* b = (const float*)M2;
   switch (P->dp) {
-    case 16: return tc_round_scores_t<16>(P, a, b, mask, eta, pv, pi, np_out);
-    case 32: return tc_round_scores_t<32>(P, a, b, mask, eta, pv, pi, np_out);
-    case 64: return tc_round_scores_t<64>(P, a, b, mask, eta, pv, pi, np_out);
-    default: return tc_round_scores_t<128>(P, a, b, mask, eta, pv, pi, np_out);
+    case 16: return tc_round_scores_t<16>(P, a, b, mask, etas, n_chain, pv, pi, np_out);
+    case 32: return tc_round_scores_t<32>(P, a, b, mask, etas, n_chain, pv, pi, np_out);
+    case 64: return tc_round_scores_t<64>(P, a, b, mask, etas, n_chain, pv, pi, np_out);
+    default: return tc_round_scores_t<128>(P, a, b, mask, etas, n_chain, pv, pi, np_out);
   }
 }
 
