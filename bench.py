@@ -176,18 +176,34 @@ def algorithmic_flops(kind, cfg, n_all, s):
     return None
 
 
+def kernel_source_hash(path, fn):
+    """First 16 hex digits of the SHA-256 of one kernel's source text: from the line that
+    opens the template (or signature) of ``fn``'s definition to the closing brace in column 0.
+    A traffic record stays valid while that text is unchanged."""
+    import hashlib
+    src = open(path).read()
+    key = f" {fn}("
+    i = src.find(key)
+    while i >= 0 and "__global__" not in src[max(0, src.rfind("\n\n", 0, i)):i]:
+        i = src.find(key, i + 1)
+    if i < 0:
+        return None
+    start = src.rfind("\n\n", 0, i) + 2
+    end = src.find("\n}\n", i)
+    return hashlib.sha256(src[start:end + 3].encode()).hexdigest()[:16]
+
+
 def dram_traffic(kind, n_rows_padded, precision):
     """DRAM bytes per launch of a kernel class from the committed ncu capture (small case):
     reads and row-proportional writes scale with the padded row count, split-K partial
-    writes are fixed per launch.  None when the kernel source changed since the capture."""
-    import hashlib
+    writes are fixed per launch.  None when the kernel's source changed since the capture."""
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))
-        src = open(os.path.join(ROOT, rec["source"]), "rb").read()
-        if hashlib.sha256(src).hexdigest()[:16] != rec["source_sha256_16"]:
-            return None
         k = rec["kernels"].get(f"{kind}/{precision}") or rec["kernels"].get(kind)
         if k is None:
+            return None
+        if kernel_source_hash(os.path.join(ROOT, rec["source"]), k["source_fn"]) != \
+                k["source_sha256_16"]:
             return None
         return (k["read_bytes_per_padded_row"] + k["write_bytes_per_padded_row"]) * \
             n_rows_padded + k["write_bytes_fixed"]

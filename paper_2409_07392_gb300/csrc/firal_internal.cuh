@@ -192,7 +192,8 @@ struct firal_problem {
 
   // tensor-core layout (FIRAL_MIXED_BF16): bf16 X (N x dp), bf16 h (Np x cp), its transpose
   firal::DBuf Xb, Hb, HbT, Pb;   // Pb: bf16 (hi/lo) operand of the probe block
-  firal::DBuf Hlo;               // bf16(h - bf16(h)), row-major like Hb (gradient GEMMs)
+  firal::DBuf Hlo;               // bf16(h - bf16(h)), row-major like Hb (pair-form gradient,
+  bool hlo_ready = false;        // made on first use)
   firal::DBuf vmean, qmean;      // class means of the probe block / of the raw apply (s x d)
   firal::DBuf Aw;                // block sums: (w h)^T hi, lo and (w h (1 - h))^T (3 x cp x Np)
   firal::DBuf Zp;                // block sums: x (x) x on the pair triangle, bf16 hi and lo

@@ -2148,20 +2148,16 @@ int32_t tc_prepare(firal_problem* P) {
   P->Np = (P->N + 127) / 128 * 128;
   const int64_t Np = P->Np;
   FIRAL_TRY(P->Hb.ensure((size_t)Np * P->cp * 2));
-  FIRAL_TRY(P->Hlo.ensure((size_t)Np * P->cp * 2));
   const int cpb2 = (P->cp + d_cfg::MT * d_cfg::BM - 1) / (d_cfg::MT * d_cfg::BM) * (d_cfg::MT * d_cfg::BM);
   FIRAL_TRY(P->HbT.ensure((size_t)Np * cpb2 * 2));
   FIRAL_TRY(P->Xb.ensure((size_t)Np * P->dp * 2 * 2));   // X (Np x dp) then X^T (dp x Np)
   const int64_t tot_h = Np * P->cp, tot_x = Np * P->dp;
   ProfScope ps(st, PF_PREP);
-  count_launch(4);
+  count_launch(3);
   k_to_bf16_pad<<<(unsigned)std::min<int64_t>((tot_h + 255) / 256, 1 << 20), 256, 0, st>>>(
       P->Hb.as<bf16>(), P->Ha.as<float>(), P->N, P->c, Np, P->cp);
   k_to_bf16_pad<<<(unsigned)std::min<int64_t>((tot_x + 255) / 256, 1 << 20), 256, 0, st>>>(
       P->Xb.as<bf16>(), P->Xa.as<float>(), P->N, P->d, Np, P->dp);
-  k_to_bf16_lo_pad<<<(unsigned)std::min<int64_t>((tot_h + 255) / 256, 1 << 20), 256, 0, st>>>(
-      P->Hlo.as<bf16>(), P->Ha.as<float>(), P->N, P->c, Np, P->cp);
-  count_launch();
   FIRAL_CUDA_TRY(cudaGetLastError());
   // h^T and x^T of the D-GEMM, K-block-major
   k_block_transpose_bf16<<<dim3((unsigned)(Np / 32), (unsigned)(cpb2 / 32)), dim3(32, 8), 0, st>>>(
@@ -2525,6 +2521,23 @@ __global__ void k_quad_combine(const float* part1, int n_nt1, const float* a32, 
   }
 }
 
+// bf16(h - bf16(h)), the low part of h, for the pair-form gradient GEMMs only (the
+// feature-contracted form reads f32 h): made on first use
+static int32_t ensure_hlo(firal_problem* P) {
+  const size_t bytes = (size_t)P->Np * P->cp * 2;
+  if (P->Hlo.p && P->Hlo.bytes >= bytes && P->hlo_ready) return FIRAL_OK;
+  FIRAL_TRY(P->Hlo.ensure(bytes));
+  const int64_t tot_h = P->Np * P->cp;
+  ProfScope ps(P->H->stream, PF_PREP);
+  count_launch();
+  k_to_bf16_lo_pad<<<(unsigned)std::min<int64_t>((tot_h + 255) / 256, 1 << 20), 256, 0,
+                     P->H->stream>>>(P->Hlo.as<bf16>(), P->Ha.as<float>(), P->N, P->c, P->Np,
+                                     P->cp);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  P->hlo_ready = true;
+  return FIRAL_OK;
+}
+
 template <int DP>
 static int32_t tc_quad_t(firal_problem* P, const float* A, const float* B, int s, double scale,
                          float* g) {
@@ -2591,6 +2604,7 @@ static int32_t tc_quad_t(firal_problem* P, const float* A, const float* B, int s
     FIRAL_CUDA_TRY(cudaGetLastError());
     return FIRAL_OK;
   }
+  FIRAL_TRY(ensure_hlo(P));
   // term 1: M~ pairs (hi | lo per 128-pair tile) and the quadratic alpha-GEMM
   const int npairs = d * (d + 1) / 2;
   const int n_nt1 = (npairs + 127) / 128;
