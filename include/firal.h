@@ -67,7 +67,9 @@ typedef enum {
                         /* enters the contraction as bf16 hi + lo (about 2^-17 relative)         */
   FIRAL_MIXED_BF16_FAST = 3  /* as FIRAL_MIXED_BF16, but the CG direction enters the first      */
                         /* contraction of the Hessian apply as one bf16 operand (2^-9 relative   */
-                        /* rounding per apply), which halves that contraction's tensor work      */
+                        /* rounding of the low-rank term), which halves that contraction's       */
+                        /* tensor work; a problem whose rows' mean sum_k h_ik^2 exceeds 0.1      */
+                        /* (confident or few classes: the low-rank term is large) keeps hi + lo  */
 } firal_precision;
 
 typedef enum { FIRAL_DT_F64 = 0, FIRAL_DT_F32 = 1, FIRAL_DT_BF16 = 2 } firal_dtype;

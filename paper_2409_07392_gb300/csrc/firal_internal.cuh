@@ -207,6 +207,7 @@ struct firal_problem {
   firal_comm comm{0, 1, nullptr, nullptr};
   int64_t n_total = 0;
   int64_t n_cen = 0;
+  double lowrank_share = 0.0;   // mean over rows of sum_k h_ik^2 (1 on centred rows)
   // (the labelled rows of such a problem are applied on CUDA cores: cen_lab, m x s x c)
   // (cen_items: the grouped rows cut into work items, cen_off then holds each class's first
   // item; cen_part: per-item partial sums)

@@ -140,21 +140,26 @@ __global__ void k_to_bf16_lo_pad(bf16* dst, const float* src, int64_t rows, int 
 constexpr float kCentre = 0.5f;
 
 // cen[r] = argmax_k h_rk (lowest index on ties) when that probability exceeds kCentre, else -1;
-// *count gains the number of such rows.  One warp per row.
-__global__ void k_row_top(int* cen, unsigned long long* count, const float* src, int64_t rows,
-                          int cols) {
+// *count gains the number of such rows and *share the row's low-rank share: sum_k h_rk^2 on a
+// plain row (the size of the low-rank term of its Hessian next to the diagonal term), 1 on a
+// centred row (all of its terms are of one size).  One warp per row.
+__global__ void k_row_top(int* cen, unsigned long long* count, double* share, const float* src,
+                          int64_t rows, int cols) {
   const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (r >= rows) return;
   float best = -1.0f;
   int bi = 0x7fffffff;
+  float sq = 0.0f;
   for (int k = lane; k < cols; k += 32) {
     const float v = src[r * cols + k];
+    sq = fmaf(v, v, sq);
     if (v > best) {
       best = v;
       bi = k;
     }
   }
+  for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
   for (int o = 16; o > 0; o >>= 1) {
     const float ob = __shfl_xor_sync(0xffffffffu, best, o);
     const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
@@ -166,6 +171,7 @@ __global__ void k_row_top(int* cen, unsigned long long* count, const float* src,
   if (lane == 0) {
     cen[r] = best > kCentre ? bi : -1;
     if (best > kCentre) atomicAdd(count, 1ULL);
+    atomicAdd(share, best > kCentre ? 1.0 : (double)sq);
   }
 }
 
@@ -2064,21 +2070,26 @@ static int32_t tc_prepare_centred(firal_problem* P, int cpb2) {
   const int64_t N = P->N, Np = P->Np;
   const int c = P->c;
   P->n_cen = 0;
-  // N class indices, then (8-byte aligned) the count of confident rows
+  // N class indices, then (8-byte aligned) the count of confident rows and the summed
+  // low-rank share of the rows
   const int64_t cnt_off = (N + 1) / 2 * 2;
-  FIRAL_TRY(P->cen.ensure((size_t)(cnt_off + 2) * sizeof(int)));
+  FIRAL_TRY(P->cen.ensure((size_t)(cnt_off + 4) * sizeof(int)));
   unsigned long long* cnt = reinterpret_cast<unsigned long long*>(P->cen.as<int>() + cnt_off);
-  FIRAL_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st));
+  double* shr = reinterpret_cast<double*>(P->cen.as<int>() + cnt_off + 2);
+  FIRAL_CUDA_TRY(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), st));
   {
     ProfScope ps(st, PF_PREP);
     count_launch();
-    k_row_top<<<(unsigned)((N * 32 + 255) / 256), 256, 0, st>>>(P->cen.as<int>(), cnt,
+    k_row_top<<<(unsigned)((N * 32 + 255) / 256), 256, 0, st>>>(P->cen.as<int>(), cnt, shr,
                                                                 P->Ha.as<float>(), N, c);
   }
   FIRAL_CUDA_TRY(cudaGetLastError());
   unsigned long long nconf = 0;
+  double share = 0.0;
   FIRAL_CUDA_TRY(cudaMemcpyAsync(&nconf, cnt, sizeof(nconf), cudaMemcpyDeviceToHost, st));
+  FIRAL_CUDA_TRY(cudaMemcpyAsync(&share, shr, sizeof(share), cudaMemcpyDeviceToHost, st));
   FIRAL_CUDA_TRY(cudaStreamSynchronize(st));
+  P->lowrank_share = share / (double)N;
   if (nconf == 0) {
     P->cen.release();
     return FIRAL_OK;
@@ -2766,10 +2777,11 @@ static int32_t tc_apply_dp(firal_problem* P, const void* w, const void* Sblk, co
 
 int32_t tc_hessian_apply(firal_problem* P, const void* w, const void* Sblk, const void* V, int s,
                          void* out, double* pq, double lam_null) {
-  // the bf16 direction's rounding enters only the low-rank term; on confident rows that term
-  // is as large as the result, so a problem with more than 1% of them takes the hi + lo
-  // direction in both modes
-  if (P->prec == FIRAL_MIXED_BF16_FAST && P->n_cen * 100 <= P->N)
+  // the bf16 direction's rounding (2^-9 per entry) enters only the low-rank term, whose size
+  // next to the result is the rows' mean low-rank share (sum_k h_ik^2 on plain rows, 1 on
+  // centred ones: about e / c for flat softmax rows); above 0.1 (errors above ~2e-4 per
+  // apply) the problem takes the hi + lo direction in both modes
+  if (P->prec == FIRAL_MIXED_BF16_FAST && P->lowrank_share <= 0.1)
     return tc_apply_dp<1>(P, w, Sblk, V, s, out, pq, lam_null);
   return tc_apply_dp<2>(P, w, Sblk, V, s, out, pq, lam_null);
 }
