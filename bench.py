@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-al", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--round-selections", type=int, default=20)
+    ap.add_argument("--batched-iters", type=int, default=5,
+                    help="timed batched MD iterations (the batched sub-measurement)")
     ap.add_argument("--replicas", action="store_true",
                     help="N > 1: N independent problems instead of one row-sharded problem")
     ap.add_argument("--only", default=None, choices=["round", "batched", "exact", "al"],
@@ -529,7 +531,7 @@ def cg_variants(prob, s, b, n):
     return out
 
 
-def batched_measure(args, H, K=5):
+def batched_measure(args, H):
     """Batched Relax on the batched_uneven workload (64 pools, n ~ U[2000, 40000], d in
     {16,32,48,64}, c in {5,10,20}, s = 8): batched MD iterations per second (one iteration of
     every pool, replayed from a CUDA graph), with HBM and tensor fractions on algorithmic work."""
@@ -551,6 +553,7 @@ def batched_measure(args, H, K=5):
         flops_apply += 4.0 * n * c * d * s
         bytes_apply += n * (2 * d + 4 * c + 4) + 8.0 * d * c * s
     cg = args.cg_iters
+    K = max(1, args.batched_iters)
     bprec = args.precision if args.precision.startswith("mixed") else "mixed_fast"
 
     def run(T):

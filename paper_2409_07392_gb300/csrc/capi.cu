@@ -205,6 +205,8 @@ int32_t tc_quad_forms(firal_problem* P, const void* A, const void* B, int s, dou
                       void* g);
 int32_t tc_syrk_blocks(firal_problem* P, const void* w, double lamS, void* outS, double lamP,
                        double* outP);
+int32_t tc_setup_pw(firal_problem* P, const std::vector<int>& coff,
+                    const std::vector<int64_t>& loff, const std::vector<int64_t>& poff);
 int32_t tc_round_scores(firal_problem* P, const void* M1, const void* M2, const uint8_t* mask,
                         const double* etas, int n_chain, double* pv, int64_t* pi, int* np_out);
 bool tc_available();
@@ -522,6 +524,11 @@ int32_t problem_create_impl(firal_handle* H, const firal_pool* pool, const firal
   TRYC(P->red.ensure(2048 * sizeof(double)));
   TRYC(P->g.ensure((size_t)P->n * vs));
   if (is_mixed(precision)) TRYC(tc_prepare(P));
+  // at most 32 classes: the fused per-point apply (one pool; a pooled problem replaces these
+  // tables with its pools')
+  if (is_mixed(precision))
+    TRYC(tc_setup_pw(P, std::vector<int>{0, (int)P->c}, std::vector<int64_t>{0, P->m},
+                     std::vector<int64_t>{0, P->n}));
 #undef TRYC
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cleanup(fail(FIRAL_ERR_CUDA, cudaGetErrorString(e)));
@@ -1029,6 +1036,8 @@ int32_t pooled_create(firal_handle* H, const std::vector<int>& idx, const firal_
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(P->kr_bsum.p, kbs.data(), kbs.size() * sizeof(int4),
                           cudaMemcpyHostToDevice, st);
+    // pools of at most 32 classes (and dp <= 64): the fused per-point apply
+    if (e == cudaSuccess && (rc = tc_setup_pw(P, coff, loff, poff)) != FIRAL_OK) return bail(rc);
   }
   // the host vectors above are read by the copies: wait for them before they go out of scope
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

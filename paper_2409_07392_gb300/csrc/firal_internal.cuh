@@ -200,12 +200,12 @@ struct firal_problem {
   firal::DBuf gq_ab, gq_m, gq_part;  // tensor-core quadratic forms: [A;B], M~ pairs, partials
   firal::DBuf rtab, rM;          // Round on tensor cores: 8-pair chunk table, M~ hi/lo rows
   firal::DBuf tdev;              // device-resident MD step counter (graph replays)
-  // confident rows (max_k h_ik > 1/2), centred at their class m: u_i = h_i - e_m in the
-  // Hessian apply (cen[i] = m or -1; rows grouped by class in cen_idx, cen_off per class);
-  // bf16 u row-major and K-block-major; a_m and w (u . a) per (row, probe) of an apply
   // row sharding (firal_problem_set_comm): allreduce callback, rank, world, total pool size
   firal_comm comm{0, 1, nullptr, nullptr};
   int64_t n_total = 0;
+  // confident rows (max_k h_ik > 1/2), centred at their class m: u_i = h_i - e_m in the
+  // Hessian apply (cen[i] = m or -1; rows grouped by class in cen_idx, cen_off per class);
+  // bf16 u row-major and K-block-major; a_m and w (u . a) per (row, probe) of an apply
   int64_t n_cen = 0;
   double lowrank_share = 0.0;   // mean over rows of sum_k h_ik^2 (1 on centred rows)
   // (the labelled rows of such a problem are applied on CUDA cores: cen_lab, m x s x c)
@@ -213,6 +213,15 @@ struct firal_problem {
   // item; cen_part: per-item partial sums)
   firal::DBuf cen, cen_off, cen_idx, Ub, UbT, cen_am, cen_rho, cen_lab, cen_items, cen_part;
   int n_cen_items = 0;
+  // pooled problems with few classes per pool: the fused per-point apply and gradient
+  // (pw_pool: per pool {first class, classes, padded classes, padded classes before it};
+  // pw_seg: segments {pool, first row, end row, classes of the segments before it};
+  // pw_pseg: each pool's segment range; pw_pk: packed bf16 direction; pw_part: partials;
+  // X64: x padded to 64 features when dp < 64)
+  bool pw = false;
+  int pw_cpad_max = 0, pw_nseg = 0;
+  int64_t pw_cpad_total = 0, pw_segcls_total = 0;
+  firal::DBuf pw_pool, pw_seg, pw_pseg, pw_pk, pw_part, X64;
   int rtab_d = -1, rtab_chunks = 0;
   int32_t dp = 0, cp = 0;
   int64_t Np = 0;

@@ -867,31 +867,39 @@ __global__ void __launch_bounds__(MODE == 4 ? 384 : 256, 1)
           uint32_t ra[32], rb[32];
           tmem_ld32_async(tb + box * 32, ra);
           tmem_ld32_async(tb + 64 + box * 32, rb);
-          float hv[32];
+          // h of classes (2u, 2u + 1) as one packed pair
+          uint64_t hv[16];
           const unsigned char* hrow_s = hbuf + box * (H3_BYTES / 2) + r * 128;
 #pragma unroll
           for (int ch = 0; ch < 8; ++ch) {
-            const float4 h4 = *reinterpret_cast<const float4*>(hrow_s + ((ch ^ (r & 7)) << 4));
-            hv[4 * ch] = h4.x;
-            hv[4 * ch + 1] = h4.y;
-            hv[4 * ch + 2] = h4.z;
-            hv[4 * ch + 3] = h4.w;
+            const ulonglong2 h4 =
+                *reinterpret_cast<const ulonglong2*>(hrow_s + ((ch ^ (r & 7)) << 4));
+            hv[2 * ch] = h4.x;
+            hv[2 * ch + 1] = h4.y;
           }
           tmem_wait_ld();
-          // four partial sums per quantity: short dependency chains
-          float pab[4] = {0.0f, 0.0f, 0.0f, 0.0f}, pa[4] = {0.0f, 0.0f, 0.0f, 0.0f},
-                pb[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+          // four partial sums per quantity (classes t mod 4), two per packed pair: short
+          // dependency chains, half the f32 instructions of the scalar form
+          uint64_t pab[2] = {0, 0}, pa[2] = {0, 0}, pb[2] = {0, 0};
 #pragma unroll
-          for (int t = 0; t < 32; ++t) {
-            const float h = hv[t], av = __uint_as_float(ra[t]), bv = __uint_as_float(rb[t]);
-            const float ha = h * av;
-            pab[t & 3] = fmaf(ha, bv, pab[t & 3]);
-            pa[t & 3] += ha;
-            pb[t & 3] = fmaf(h, bv, pb[t & 3]);
+          for (int u = 0; u < 16; ++u) {
+            const uint64_t h2 = hv[u], a2 = f2_pack_u(ra[2 * u], ra[2 * u + 1]),
+                           b2 = f2_pack_u(rb[2 * u], rb[2 * u + 1]);
+            const uint64_t ha2 = f2_mul(h2, a2);
+            pab[u & 1] = f2_fma(ha2, b2, pab[u & 1]);
+            pa[u & 1] = f2_add(pa[u & 1], ha2);
+            pb[u & 1] = f2_fma(h2, b2, pb[u & 1]);
           }
-          sab += (pab[0] + pab[1]) + (pab[2] + pab[3]);
-          sa += (pa[0] + pa[1]) + (pa[2] + pa[3]);
-          sb += (pb[0] + pb[1]) + (pb[2] + pb[3]);
+          float x0, x1, y0, y1;
+          f2_unpack(pab[0], x0, x1);
+          f2_unpack(pab[1], y0, y1);
+          sab += (x0 + x1) + (y0 + y1);
+          f2_unpack(pa[0], x0, x1);
+          f2_unpack(pa[1], y0, y1);
+          sa += (x0 + x1) + (y0 + y1);
+          f2_unpack(pb[0], x0, x1);
+          f2_unpack(pb[1], y0, y1);
+          sb += (x0 + x1) + (y0 + y1);
         }
         tc_fence_before();
         __syncwarp();
@@ -1667,7 +1675,8 @@ __global__ void k_build_z(bf16* Zhi, bf16* Zlo, const bf16* Xb, int d, int dp, i
 
 // Class operands of the block sums, zero-padded, in the K-block-major layout
 // [i / 64][k][i % 64] with cpb rows per block:
-//   A_hi = bf16(w u), A_lo = bf16(w u - A_hi), A_P = bf16(w h (1 - h))   (A_P only if AP)
+//   A_hi = bf16(w u), A_lo = bf16(w u - A_hi), A_P = bf16(w h (1 - h))
+// (A_hi and A_lo only if Ahi, A_P only if AP)
 // with u = h, or u = h - e_m on centred rows (cen, may be NULL); rows below wskip take weight
 // 0 in A_hi and A_lo (their part of the Hessian apply runs on CUDA cores).
 // Block = one 64-point block x 32 classes; each warp store writes one 128-byte row run.
@@ -1701,11 +1710,13 @@ __global__ void k_weighted_hT(bf16* Ahi, bf16* Alo, bf16* AP, const float* Ha, c
     // the diagonal-part operator takes u = h - e_m on centred rows
     const float v0 = ws0 * (cs[t2] == col ? h0 - 1.0f : h0);
     const float v1 = ws1 * (cs[t2 + 1] == col ? h1 - 1.0f : h1);
-    const __nv_bfloat162 hi = __floats2bfloat162_rn(v0, v1);
-    const float2 fh = __bfloat1622float2(hi);
     const int64_t o = ((int64_t)blockIdx.x * cpb + col) * 64 + t2;
-    *reinterpret_cast<__nv_bfloat162*>(Ahi + o) = hi;
-    *reinterpret_cast<__nv_bfloat162*>(Alo + o) = __floats2bfloat162_rn(v0 - fh.x, v1 - fh.y);
+    if (Ahi) {
+      const __nv_bfloat162 hi = __floats2bfloat162_rn(v0, v1);
+      const float2 fh = __bfloat1622float2(hi);
+      *reinterpret_cast<__nv_bfloat162*>(Ahi + o) = hi;
+      *reinterpret_cast<__nv_bfloat162*>(Alo + o) = __floats2bfloat162_rn(v0 - fh.x, v1 - fh.y);
+    }
     if (AP)
       *reinterpret_cast<__nv_bfloat162*>(AP + o) =
           __floats2bfloat162_rn(w0 * h0 * (1.0f - h0), w1 * h1 * (1.0f - h1));
@@ -2390,6 +2401,11 @@ int32_t tc_syrk_blocks(firal_problem* P, const void* wv, double lamS, void* outS
   const int64_t Np = P->Np;
   const int cp = P->cp, c = P->c, d = P->d;
   const int sms = P->sms;
+  // the fused per-point apply of pooled problems has no diagonal-part operator: only the
+  // preconditioner blocks are summed
+  const bool wantS = !P->pw;
+  if (!wantS) outS = nullptr;
+  if (!outS && !outP) return FIRAL_OK;
   const int npairs = d * (d + 1) / 2;
   const int64_t npp = (npairs + BN - 1) / BN * BN;
   const int n_mt = (cp + BM - 1) / BM;
@@ -2430,9 +2446,9 @@ int32_t tc_syrk_blocks(firal_problem* P, const void* wv, double lamS, void* outS
   const int units = tiles * splits;
   {
     ProfScope ps(st, PF_SYRK);
-    count_launch(outP ? 3 : 2);
+    count_launch(1 + (outS ? 1 : 0) + (outP ? 1 : 0));
     k_weighted_hT<<<dim3((unsigned)(Np / 64), (unsigned)(cpb / 32)), dim3(32, 8), 0, st>>>(
-        Ahi, Alo, outP ? AP : nullptr, P->Ha.as<float>(), w, P->N, c, Np, cpb,
+        outS ? Ahi : nullptr, Alo, outP ? AP : nullptr, P->Ha.as<float>(), w, P->N, c, Np, cpb,
         P->n_cen > 0 ? P->cen.as<int>() : nullptr, lab_rows(P));
     FIRAL_CUDA_TRY(cudaGetLastError());
     // blocked operands as 2-D tensors of 64-point rows: tile (kb, row block) = 16 KB run
@@ -2444,10 +2460,13 @@ int32_t tc_syrk_blocks(firal_problem* P, const void* wv, double lamS, void* outS
     FIRAL_TRY(make_map(&mZ0, P->Zp.p, zrows, BK, BN, BK, true));
     FIRAL_TRY(make_map(&mZ1, P->Zp.as<bf16>() + npp * Np, zrows, BK, BN, BK, true));
     const int grid = std::min(units, sms);
-    k_tc_bsum<0><<<grid, 256, Cfg<0>::SMEM, st>>>(mA0, mA1, mZ0, mZ1, pS, c, d, npairs, n_mt,
-                                                  n_nt, splits, kbps, kb_total, tc_error_word(P),
-                                                  P->kr_bsum.as<int4>(), P->kbL);
-    FIRAL_CUDA_TRY(cudaGetLastError());
+    if (outS) {
+      k_tc_bsum<0><<<grid, 256, Cfg<0>::SMEM, st>>>(mA0, mA1, mZ0, mZ1, pS, c, d, npairs, n_mt,
+                                                    n_nt, splits, kbps, kb_total,
+                                                    tc_error_word(P), P->kr_bsum.as<int4>(),
+                                                    P->kbL);
+      FIRAL_CUDA_TRY(cudaGetLastError());
+    }
     if (outP) {
       k_tc_bsum<1><<<grid, 256, Cfg<1>::SMEM, st>>>(mA2, mA2, mZ0, mZ0, pP, c, d, npairs, n_mt,
                                                     n_nt, splits, kbps, kb_total,
@@ -2456,7 +2475,8 @@ int32_t tc_syrk_blocks(firal_problem* P, const void* wv, double lamS, void* outS
       FIRAL_CUDA_TRY(cudaGetLastError());
     }
   }
-  return syrk_reduce_f32(P, pS, outP ? pP : nullptr, splits, lamS, (float*)outS, lamP, outP);
+  return syrk_reduce_f32(P, outS ? pS : nullptr, outP ? pP : nullptr, splits, lamS, (float*)outS,
+                         lamP, outP);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -2760,6 +2780,785 @@ int32_t tc_round_scores(firal_problem* P, const void* M1, const void* M2, const 
   }
 }
 
+// ------------------------------------------------------------------------------------------
+// Pooled problems with few classes per pool: the Hessian apply in the per-point form of
+// Lemma 1, fused into one persistent kernel.  For the rows of one pool q (weights w_i,
+// probabilities h_i over the pool's c_q classes, direction P~ with the pool's class means
+// removed):
+//   a_ikj = x_i . P~_j[:, k]                      MMA1: 128 rows x (probe, class), K = features
+//   alpha_ij = sum_k h_ik a_ikj,   psi_ikj = w_i h_ik (a_ikj - alpha_ij)     f32, CUDA cores
+//   out_j[:, k] += sum_i psi_ikj x_i              MMA2: (probe, class) x features, K = rows
+// P~ and psi enter as bf16 hi + lo (x is exact in bf16), so both products carry about 2^-17
+// relative rounding, and nothing cancels: each psi is the row's own contribution.  Column
+// (probe j, class k) is j cpad + k, cpad = the pool's class count rounded up to 8, 16 or 32,
+// so one 32-column TMEM load holds whole probes.
+// Work list: segments of at most PW_SEG_TILES 128-row tiles of one pool's rows (its labelled
+// rows and its pool rows are separate segments).  A tile that also holds rows of another
+// pool runs once per pool with the other rows masked.  A segment accumulates out in TMEM
+// and writes one partial; a per-class combine adds a pool's partials in segment order.
+// Roles (384 threads): warp 0 TMA producer, warp 1 MMA issuer, warp 2 TMEM owner, warps 4-11
+// epilogue (warp & 3 = TMEM lane quarter, (warp - 4) >> 2 = which 32-column chunks).
+// ------------------------------------------------------------------------------------------
+namespace pw_cfg {
+constexpr int N1MAX = 256;                        // (probe, class) columns at most
+constexpr int SEG_TILES = 16;                     // tiles per segment: 256 adds per accumulator
+constexpr int PT_HALF = N1MAX * 128;              // P~ hi (then lo): 128-byte rows, 64 features
+constexpr int XA_BYTES = 128 * 128;               // x tile: 128 rows x 64 features
+constexpr int XT_BYTES = 2 * 64 * 128;            // x^T tile: 2 K-blocks x (<= 64 features)
+constexpr int PSI_KB = N1MAX * 128;               // psi^T: one K-block (64 rows) of one part
+constexpr int OFF_PT = 0, OFF_XA = 2 * PT_HALF, OFF_XT = OFF_XA + XA_BYTES;
+constexpr int OFF_PSI = OFF_XT + XT_BYTES, OFF_CTL = OFF_PSI + 4 * PSI_KB;
+constexpr int SMEM = OFF_CTL + 256 + 1024;
+constexpr uint32_t TS = 0, TD = 256;              // TMEM columns: S (MMA1) | D (MMA2, 2 x DP)
+}  // namespace pw_cfg
+
+struct PwCtl {   // < 256 bytes
+  uint64_t x_full, x_empty, xt_full, xt_empty, pt_full, pt_empty, s_full, s_empty, psi_full,
+      psi_empty, d_full, d_empty, drain;
+  uint32_t tmem_base;
+  int abort_w;
+};
+static_assert(sizeof(PwCtl) <= 256, "control block must fit in 256 bytes");
+
+// psi for one 32-column chunk (32 / CPAD whole probes) of the thread's row, written as bf16
+// hi and lo to rows t of the chunk's psi^T block; off[r] = the thread's byte position in a
+// 128-byte-swizzled row r (mod 8)
+template <int CPAD>
+__device__ __forceinline__ void pw_psi_chunk(const uint32_t (&ra)[32], const float (&h)[32],
+                                             const float (&wh)[32], unsigned char* hi,
+                                             unsigned char* lo, const uint32_t (&off)[8]) {
+#pragma unroll
+  for (int pl = 0; pl < 32 / CPAD; ++pl) {
+    float a0 = 0.0f, a1 = 0.0f;
+#pragma unroll
+    for (int k = 0; k < CPAD; k += 2) {
+      a0 = fmaf(h[k], __uint_as_float(ra[pl * CPAD + k]), a0);
+      a1 = fmaf(h[k + 1], __uint_as_float(ra[pl * CPAD + k + 1]), a1);
+    }
+    const float al = a0 + a1;
+#pragma unroll
+    for (int k = 0; k < CPAD; ++k) {
+      const int t = pl * CPAD + k;
+      const float psi = wh[k] * (__uint_as_float(ra[t]) - al);
+      const bf16 ph = __float2bfloat16_rn(psi);
+      const bf16 pl2 = __float2bfloat16_rn(psi - __bfloat162float(ph));
+      *reinterpret_cast<bf16*>(hi + t * 128 + off[t & 7]) = ph;
+      *reinterpret_cast<bf16*>(lo + t * 128 + off[t & 7]) = pl2;
+    }
+  }
+}
+
+template <int DP>
+__global__ void __launch_bounds__(384, 1)
+    k_tc_pw(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapXT,
+            const __grid_constant__ CUtensorMap mapPT, const float* __restrict__ Ha,
+            const float* __restrict__ w, float* __restrict__ part,
+            const int4* __restrict__ pool_tab, const int4* __restrict__ seg_tab, int nseg, int C,
+            int s, int sp, int d, int32_t* err) {
+  using namespace pw_cfg;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  PwCtl* ctl = (PwCtl*)(sm + OFF_CTL);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    mbar_init(&ctl->x_full, 1);
+    mbar_init(&ctl->x_empty, 1);
+    mbar_init(&ctl->xt_full, 1);
+    mbar_init(&ctl->xt_empty, 1);
+    mbar_init(&ctl->pt_full, 1);
+    mbar_init(&ctl->pt_empty, 1);
+    mbar_init(&ctl->s_full, 1);
+    mbar_init(&ctl->s_empty, 8);
+    mbar_init(&ctl->psi_full, 8);
+    mbar_init(&ctl->psi_empty, 1);
+    mbar_init(&ctl->d_full, 1);
+    mbar_init(&ctl->d_empty, 8);
+    mbar_init(&ctl->drain, 1);
+    ctl->abort_w = 0;
+    mbar_fence_init();
+  }
+  if (warp == 2) {
+    tmem_alloc(&ctl->tmem_base, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = ctl->tmem_base;
+  volatile int* abort_w = &ctl->abort_w;
+  auto give_up = [&](int code) {
+    ctl->abort_w = 1;
+    atomicExch(err, code);
+  };
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer: P~ of the segment's pool, then x and x^T of each tile
+    tma_prefetch(&mapX);
+    tma_prefetch(&mapXT);
+    tma_prefetch(&mapPT);
+    uint32_t nx = 0, nxt = 0, npt = 0;   // loads issued per buffer
+    bool ok = true;
+    for (int g = blockIdx.x; g < nseg && ok && !*abort_w; g += gridDim.x) {
+      const int4 sg = seg_tab[g];
+      const int4 pq = pool_tab[sg.x];
+      const int n1 = pq.z * sp;
+      const int pbase = 2 * sp * pq.w;
+      if (!mbar_wait(&ctl->pt_empty, (npt & 1) ^ 1, abort_w)) { give_up(41); break; }
+      mbar_expect_tx(&ctl->pt_full, 2 * n1 * 128);
+      for (int part = 0; part < 2; ++part)
+        for (int r = 0; r < n1; r += 64)
+          tma_load_2d(sm + OFF_PT + part * PT_HALF + r * 128, &mapPT, &ctl->pt_full, 0,
+                      pbase + part * n1 + r);
+      ++npt;
+      for (int t = sg.y >> 7; t <= (sg.z - 1) >> 7; ++t) {
+        if (!mbar_wait(&ctl->x_empty, (nx & 1) ^ 1, abort_w)) { give_up(42); ok = false; break; }
+        mbar_expect_tx(&ctl->x_full, XA_BYTES);
+        tma_load_2d(sm + OFF_XA, &mapX, &ctl->x_full, 0, t * 128);
+        ++nx;
+        if (!mbar_wait(&ctl->xt_empty, (nxt & 1) ^ 1, abort_w)) { give_up(43); ok = false; break; }
+        mbar_expect_tx(&ctl->xt_full, 2 * DP * 128);
+        tma_load_2d(sm + OFF_XT, &mapXT, &ctl->xt_full, 0, (2 * t) * DP);
+        tma_load_2d(sm + OFF_XT + DP * 128, &mapXT, &ctl->xt_full, 0, (2 * t + 1) * DP);
+        ++nxt;
+      }
+    }
+    // every issued load lands before the CTA can exit
+    if (nx) mbar_wait_drain(&ctl->x_full, (nx - 1) & 1);
+    if (nxt) mbar_wait_drain(&ctl->xt_full, (nxt - 1) & 1);
+    if (npt) mbar_wait_drain(&ctl->pt_full, (npt - 1) & 1);
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    uint32_t nx = 0, nxt = 0, npt = 0, ns = 0, nseg_done = 0;
+    bool ok = true;
+    constexpr uint32_t idesc2 = idesc_bf16_f32(128, DP);
+    for (int g = blockIdx.x; g < nseg && ok && !*abort_w; g += gridDim.x) {
+      const int4 sg = seg_tab[g];
+      const int4 pq = pool_tab[sg.x];
+      const int n1 = pq.z * sp;
+      const uint32_t idesc1 = idesc_bf16_f32(128, n1);
+      const int nblk = (n1 + 127) >> 7;
+      if (!mbar_wait(&ctl->pt_full, npt & 1, abort_w)) { give_up(44); break; }
+      ++npt;
+      const int t0 = sg.y >> 7, t1 = (sg.z - 1) >> 7;
+      for (int t = t0; t <= t1 && ok; ++t) {
+        // MMA1: S = x P~^T (hi and lo parts of P~ into the same accumulator)
+        if (!mbar_wait(&ctl->x_full, nx & 1, abort_w) ||
+            !mbar_wait(&ctl->s_empty, (ns & 1) ^ 1, abort_w)) { give_up(45); ok = false; break; }
+        tc_fence_after();
+        const uint32_t xa = smem_u32(sm + OFF_XA), pt = smem_u32(sm + OFF_PT);
+#pragma unroll
+        for (int k = 0; k < DP / 16; ++k) {
+          const uint64_t ad = sdesc_sw128(xa + k * 32);
+          umma_bf16(tmem + TS, ad, sdesc_sw128(pt + k * 32), idesc1, k > 0 ? 1u : 0u);
+          umma_bf16(tmem + TS, ad, sdesc_sw128(pt + PT_HALF + k * 32), idesc1, 1u);
+        }
+        umma_commit(&ctl->s_full);
+        umma_commit(&ctl->x_empty);
+        ++nx;
+        ++ns;
+        if (t == t1) umma_commit(&ctl->pt_empty);
+        // MMA2: D_b += psi^T x (rows of block b of the (probe, class) columns)
+        if (!mbar_wait(&ctl->psi_full, (ns - 1) & 1, abort_w) ||
+            !mbar_wait(&ctl->xt_full, nxt & 1, abort_w) ||
+            (t == t0 && !mbar_wait(&ctl->d_empty, (nseg_done & 1) ^ 1, abort_w))) {
+          give_up(46);
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t ps = smem_u32(sm + OFF_PSI), xt = smem_u32(sm + OFF_XT);
+        for (int b = 0; b < nblk; ++b) {
+#pragma unroll
+          for (int kb = 0; kb < 2; ++kb)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const uint64_t bd = sdesc_sw128(xt + kb * DP * 128 + k * 32);
+              const uint32_t a0 = ps + kb * PSI_KB + b * 128 * 128 + k * 32;
+              const uint32_t first = (t == t0 && kb == 0 && k == 0) ? 0u : 1u;
+              umma_bf16(tmem + TD + b * DP, sdesc_sw128(a0), bd, idesc2, first);
+              umma_bf16(tmem + TD + b * DP, sdesc_sw128(a0 + 2 * PSI_KB), bd, idesc2, 1u);
+            }
+        }
+        umma_commit(&ctl->psi_empty);
+        umma_commit(&ctl->xt_empty);
+        ++nxt;
+        if (t == t1) {
+          umma_commit(&ctl->d_full);
+          ++nseg_done;
+        }
+      }
+    }
+    umma_commit(&ctl->drain);
+    mbar_wait_drain(&ctl->drain, 0);
+  } else if (warp >= 4) {
+    // ---------------- epilogue
+    const int quad = warp & 3, half = (warp - 4) >> 2;
+    const int i = quad * 32 + lane;            // row within the tile = TMEM lane
+    const uint32_t lanes = (uint32_t)(quad * 32) << 16;
+    // byte positions of this row's element in a swizzled 128-byte psi^T row r (mod 8)
+    uint32_t off[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) off[r] = ((((i & 63) >> 3) ^ r) << 4) + ((i & 7) << 1);
+    unsigned char* psi_hi0 = sm + OFF_PSI + (i >> 6) * PSI_KB;
+    uint32_t ns = 0, nseg_done = 0;
+    for (int g = blockIdx.x; g < nseg && !*abort_w; g += gridDim.x) {
+      const int4 sg = seg_tab[g];
+      const int4 pq = pool_tab[sg.x];
+      const int cpad = pq.z, cq = pq.y;
+      const int n1 = cpad * sp;
+      const int t0 = sg.y >> 7, t1 = (sg.z - 1) >> 7;
+      bool ok = true;
+      for (int t = t0; t <= t1; ++t) {
+        const int64_t row = (int64_t)t * 128 + i;
+        const bool valid = row >= sg.y && row < sg.z;
+        const float wi = valid ? w[row] : 0.0f;
+        float h[32], wh[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+          h[k] = (valid && k < cq) ? Ha[row * C + pq.x + k] : 0.0f;
+          wh[k] = wi * h[k];
+        }
+        if (!mbar_wait(&ctl->s_full, ns & 1, abort_w) ||
+            !mbar_wait(&ctl->psi_empty, (ns & 1) ^ 1, abort_w)) {
+          give_up(47);
+          ok = false;
+          break;
+        }
+        ++ns;
+        tc_fence_after();
+        for (int ch = half; ch < n1 / 32; ch += 2) {
+          uint32_t ra[32];
+          tmem_ld32_async(tmem + lanes + TS + ch * 32, ra);
+          tmem_wait_ld();
+          unsigned char* hi = psi_hi0 + ch * 32 * 128;
+          unsigned char* lo = hi + 2 * PSI_KB;
+          if (cpad == 8) pw_psi_chunk<8>(ra, h, wh, hi, lo, off);
+          else if (cpad == 16) pw_psi_chunk<16>(ra, h, wh, hi, lo, off);
+          else pw_psi_chunk<32>(ra, h, wh, hi, lo, off);
+        }
+        tc_fence_before();
+        fence_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&ctl->s_empty);
+          mbar_arrive(&ctl->psi_full);
+        }
+      }
+      if (!ok) break;
+      // segment end: D -> this segment's partial, [class][probe][feature]
+      if (!mbar_wait(&ctl->d_full, nseg_done & 1, abort_w)) {
+        give_up(48);
+        break;
+      }
+      ++nseg_done;
+      tc_fence_after();
+      const int nblk = (n1 + 127) >> 7;
+      if (half < nblk) {
+        const int R = half * 128 + i;
+        const int j = R / cpad, kl = R - j * cpad;
+        float* dst = part + ((int64_t)(sg.w + kl) * sp + j) * d;
+        const bool own = kl < cq && j < s;
+#pragma unroll
+        for (int c0 = 0; c0 < DP; c0 += 16) {
+          float v[16];
+          tmem_ld16(tmem + lanes + TD + half * DP + c0, v);
+          if (own)
+#pragma unroll
+            for (int u = 0; u < 16; ++u)
+              if (c0 + u < d) dst[c0 + u] = v[u];
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&ctl->d_empty);
+    }
+  }
+  __syncthreads();
+  if (warp == 2) {
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+// Packed direction of the fused kernel (sp = s rounded up to 8 probes): pool q's rows start
+// at 2 sp cpre_q; row part n1_q + j cpad_q + k (part 0 = bf16 hi, 1 = lo of P_j[:, k] minus
+// the pool's class mean; zero for k >= c_q and for the padding probes j >= s); 64 bf16
+// features per row, zero for e >= d.
+__global__ void k_pw_pack(bf16* Pk, const float* V, const float* vmean, const int4* pool_tab,
+                          int s, int sp, int d, int64_t D, int Qe) {
+  const int q = blockIdx.x, j = blockIdx.y;
+  const int4 pq = pool_tab[q];   // first class, classes, padded classes, padded classes before
+  const int64_t n1 = (int64_t)pq.z * sp;
+  const int64_t r0 = 2LL * sp * pq.w + (int64_t)j * pq.z;
+  for (int idx = threadIdx.x; idx < pq.z * 64; idx += blockDim.x) {
+    const int kl = idx >> 6, e = idx & 63;
+    float v = 0.0f;
+    if (kl < pq.y && e < d && j < s)
+      v = V[(int64_t)j * D + (int64_t)(pq.x + kl) * d + e] - vmean[(j * Qe + q) * d + e];
+    const bf16 hi = __float2bfloat16_rn(v);
+    Pk[(r0 + kl) * 64 + e] = hi;
+    Pk[(r0 + n1 + kl) * 64 + e] = __float2bfloat16_rn(v - __bfloat162float(hi));
+  }
+}
+
+// out_j[:, k] = lam (V_j[:, k] - pool mean) + the pool's segment partials in segment order
+__global__ void k_pw_combine(float* out, const float* V, const float* vmean, const float* part,
+                             const int4* pool_tab, const int2* pseg, const int4* seg_tab,
+                             float lam, int s, int sp, int d, int64_t D, PoolTab pt) {
+  const int k = blockIdx.x;
+  const int q = pool_of(pt, k), Qe = pool_count(pt);
+  const int kl = k - pool_tab[q].x;
+  const int2 sr = pseg[q];
+  for (int idx = threadIdx.x; idx < s * d; idx += blockDim.x) {
+    const int j = idx / d, e = idx - j * d;
+    const int64_t o = (int64_t)j * D + (int64_t)k * d + e;
+    float acc = lam * (V[o] - vmean[(j * Qe + q) * d + e]);
+    for (int g = sr.x; g < sr.y; ++g) acc += part[((int64_t)(seg_tab[g].w + kl) * sp + j) * d + e];
+    out[o] = acc;
+  }
+}
+
+// x padded to 64 features (the fused kernel's MMA1 operand when dp < 64)
+__global__ void k_pad_x64(bf16* X64, const bf16* Xb, int64_t Np, int dp) {
+  const int64_t total = Np * 64;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = idx >> 6;
+    const int e = (int)(idx & 63);
+    X64[idx] = e < dp ? Xb[r * dp + e] : __float2bfloat16(0.0f);
+  }
+}
+
+// Work list of the fused kernel (mixed precision, dp <= 64, every pool with at most 32
+// classes; a problem that is not pooled is one pool): pool table, segments of at most
+// SEG_TILES tiles of each row range (labelled rows loff, pool rows M + poff), each pool's
+// segment range.  Leaves the problem on the general path otherwise.
+int32_t tc_setup_pw(firal_problem* P, const std::vector<int>& coff,
+                    const std::vector<int64_t>& loff, const std::vector<int64_t>& poff) {
+  using namespace pw_cfg;
+  const int Q = (int)coff.size() - 1;
+  P->pw = false;
+  if (Q < 1 || P->dp > 64 || !is_mixed(P->prec)) return FIRAL_OK;
+  std::vector<int4> ptab(Q);
+  int cmax = 0;
+  int64_t cpre = 0;
+  for (int q = 0; q < Q; ++q) {
+    const int cq = coff[q + 1] - coff[q];
+    const int cpad = cq <= 8 ? 8 : cq <= 16 ? 16 : 32;
+    if (cq > 32) return FIRAL_OK;   // more classes: the general path
+    ptab[q] = make_int4(coff[q], cq, cpad, (int)cpre);
+    cpre += cpad;
+    cmax = std::max(cmax, cpad);
+  }
+  const int64_t M = loff[Q];
+  std::vector<int4> segs;
+  std::vector<int2> pseg(Q);
+  int64_t segcls = 0;
+  for (int q = 0; q < Q; ++q) {
+    pseg[q].x = (int)segs.size();
+    const int64_t ranges[2][2] = {{loff[q], loff[q + 1]}, {M + poff[q], M + poff[q + 1]}};
+    for (const auto& rg : ranges) {
+      for (int64_t a = rg[0]; a < rg[1];) {
+        const int64_t tend = (a / 128 + SEG_TILES) * 128;
+        const int64_t b = std::min<int64_t>(rg[1], tend);
+        segs.push_back(make_int4(q, (int)a, (int)b, (int)segcls));
+        segcls += ptab[q].y;
+        a = b;
+      }
+    }
+    pseg[q].y = (int)segs.size();
+  }
+  cudaStream_t st = P->H->stream;
+  FIRAL_TRY(P->pw_pool.ensure(ptab.size() * sizeof(int4)));
+  FIRAL_TRY(P->pw_seg.ensure(std::max<size_t>(1, segs.size()) * sizeof(int4)));
+  FIRAL_TRY(P->pw_pseg.ensure(pseg.size() * sizeof(int2)));
+  FIRAL_CUDA_TRY(cudaMemcpyAsync(P->pw_pool.p, ptab.data(), ptab.size() * sizeof(int4),
+                                 cudaMemcpyHostToDevice, st));
+  if (!segs.empty())
+    FIRAL_CUDA_TRY(cudaMemcpyAsync(P->pw_seg.p, segs.data(), segs.size() * sizeof(int4),
+                                   cudaMemcpyHostToDevice, st));
+  FIRAL_CUDA_TRY(cudaMemcpyAsync(P->pw_pseg.p, pseg.data(), pseg.size() * sizeof(int2),
+                                 cudaMemcpyHostToDevice, st));
+  if (P->dp < 64) {
+    FIRAL_TRY(P->X64.ensure((size_t)P->Np * 64 * 2));
+    count_launch();
+    k_pad_x64<<<(unsigned)std::min<int64_t>((P->Np * 64 + 255) / 256, 1 << 20), 256, 0, st>>>(
+        P->X64.as<bf16>(), P->Xb.as<bf16>(), P->Np, P->dp);
+    FIRAL_CUDA_TRY(cudaGetLastError());
+  }
+  // the host vectors are read by the copies
+  FIRAL_CUDA_TRY(cudaStreamSynchronize(st));
+  P->pw = true;
+  P->pw_cpad_max = cmax;
+  P->pw_cpad_total = cpre;
+  P->pw_nseg = (int)segs.size();
+  P->pw_segcls_total = segcls;
+  return FIRAL_OK;
+}
+
+template <int DP>
+static int32_t tc_apply_pw_t(firal_problem* P, const float* w, const float* V, int s, float* out,
+                             double* pq, double lam) {
+  using namespace pw_cfg;
+  cudaStream_t st = P->H->stream;
+  const int c = P->c, d = P->d;
+  const int Qe = pool_count(P->pt);
+  FIRAL_TRY(P->vmean.ensure((size_t)s * Qe * d * sizeof(float)));
+  FIRAL_TRY(P->qmean.ensure((size_t)s * Qe * d * sizeof(float)));
+  const int sp = (s + 7) / 8 * 8;
+  const int64_t prows = 2LL * sp * P->pw_cpad_total;
+  FIRAL_TRY(P->pw_pk.ensure((size_t)prows * 64 * 2));
+  FIRAL_TRY(P->pw_part.ensure((size_t)std::max<int64_t>(1, P->pw_segcls_total) * sp * d *
+                              sizeof(float)));
+  {
+    ProfScope ps(st, PF_SPLIT);
+    count_launch(2);
+    k_class_mean<<<s * Qe, 1024, 0, st>>>(V, s, c, d, P->D, P->vmean.as<float>(), P->pt);
+    k_pw_pack<<<dim3((unsigned)Qe, (unsigned)sp), 256, 0, st>>>(
+        P->pw_pk.as<bf16>(), V, P->vmean.as<float>(), P->pw_pool.as<int4>(), s, sp, d, P->D, Qe);
+    FIRAL_CUDA_TRY(cudaGetLastError());
+  }
+  static bool attr[3] = {false, false, false};
+  const int ai = DP == 16 ? 0 : DP == 32 ? 1 : 2;
+  if (!attr[ai]) {
+    FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tc_pw<DP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        SMEM));
+    attr[ai] = true;
+  }
+  CUtensorMap mX, mXT, mPT;
+  const int64_t Np = P->Np;
+  FIRAL_TRY(make_map(&mX, DP < 64 ? P->X64.p : P->Xb.p, Np, 64, 128, 64, true));
+  FIRAL_TRY(make_map(&mXT, P->Xb.as<bf16>() + Np * DP, (uint64_t)(Np / 64) * DP, 64, DP, 64,
+                     true));
+  FIRAL_TRY(make_map(&mPT, P->pw_pk.p, prows, 64, 64, 64, true));
+  {
+    ProfScope ps(st, PF_ALPHA);
+    count_launch();
+    const int grid = std::min(P->pw_nseg, P->sms);
+    k_tc_pw<DP><<<grid, 384, SMEM, st>>>(mX, mXT, mPT, P->Ha.as<float>(), w,
+                                         P->pw_part.as<float>(), P->pw_pool.as<int4>(),
+                                         P->pw_seg.as<int4>(), P->pw_nseg, c, s, sp, d,
+                                         tc_error_word(P));
+    FIRAL_CUDA_TRY(cudaGetLastError());
+  }
+  ProfScope ps(st, PF_COMBINE);
+  count_launch(3);
+  // lambda I counts once over a row-sharded group (rank 0); the projection below acts on the
+  // summed result
+  k_pw_combine<<<c, 256, 0, st>>>(out, V, P->vmean.as<float>(), P->pw_part.as<float>(),
+                                  P->pw_pool.as<int4>(), P->pw_pseg.as<int2>(),
+                                  P->pw_seg.as<int4>(), P->comm.rank == 0 ? (float)lam : 0.0f,
+                                  s, sp, d, P->D, P->pt);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  FIRAL_TRY(shard_allreduce(P, out, (int64_t)s * P->D, FIRAL_DT_F32, 0));
+  const int mthreads = (d + 31) / 32 * 32;
+  k_class_mean<<<s * Qe, 1024, 0, st>>>(out, s, c, d, P->D, P->qmean.as<float>(), P->pt);
+  k_project<<<dim3(c, (s + 3) / 4), mthreads, 0, st>>>(out, P->qmean.as<float>(),
+                                                       P->vmean.as<float>(), V, lam, s, c, d,
+                                                       P->D, pq, P->pt);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  return FIRAL_OK;
+}
+
+// the probe block in groups whose (probe, class) columns fit the kernel (sp cpad <= 256):
+// every probe is independent through the apply, its combine and its projection
+static int32_t tc_apply_pw(firal_problem* P, const float* w, const float* V, int s, float* out,
+                           double* pq, double lam) {
+  const int sg = pw_cfg::N1MAX / P->pw_cpad_max;   // a multiple of 8 (cpad <= 32)
+  for (int j0 = 0; j0 < s; j0 += sg) {
+    const int n = std::min(sg, s - j0);
+    const float* Vg = V + (int64_t)j0 * P->D;
+    float* og = out + (int64_t)j0 * P->D;
+    double* pg = pq ? pq + (int64_t)j0 * P->c : nullptr;
+    switch (P->dp) {
+      case 16: FIRAL_TRY(tc_apply_pw_t<16>(P, w, Vg, n, og, pg, lam)); break;
+      case 32: FIRAL_TRY(tc_apply_pw_t<32>(P, w, Vg, n, og, pg, lam)); break;
+      default: FIRAL_TRY(tc_apply_pw_t<64>(P, w, Vg, n, og, pg, lam)); break;
+    }
+  }
+  return FIRAL_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Per-point quadratic forms (eq. 11) on the same work list, for at most 32 classes per pool:
+//   a_ikj = x_i . A~_j[:, k],  b_ikj = x_i . B~_j[:, k]      two MMA1s (hi + lo each) per tile
+//   q_i = sum_j [sum_k h_ik a_ikj b_ikj - (sum_k h_ik a_ikj)(sum_k h_ik b_ikj)]
+// with A~, B~ the probe blocks minus their pool class means (H_i vanishes on those means).
+// Only the pool rows' segments run.  The two epilogue halves of a row meet in shared memory
+// (an mbarrier hand-off), and a later probe group adds to the earlier groups' values, so g is
+// written in a fixed order.
+// ------------------------------------------------------------------------------------------
+namespace pwq_cfg {
+constexpr int PT_HALF = pw_cfg::PT_HALF;
+constexpr int OFF_PA = 0, OFF_PB = 2 * PT_HALF, OFF_XA = 4 * PT_HALF;
+constexpr int OFF_RED = OFF_XA + pw_cfg::XA_BYTES, OFF_CTL = OFF_RED + 1024;
+constexpr int SMEM = OFF_CTL + 256 + 1024;
+constexpr uint32_t TA = 0, TB = 256;              // TMEM columns: S_A | S_B
+}  // namespace pwq_cfg
+
+template <int CPAD>
+__device__ __forceinline__ float pw_quad_chunk(const uint32_t (&ra)[32], const uint32_t (&rb)[32],
+                                               const float (&h)[32]) {
+  float q = 0.0f;
+#pragma unroll
+  for (int pl = 0; pl < 32 / CPAD; ++pl) {
+    float sab = 0.0f, sa = 0.0f, sb = 0.0f;
+#pragma unroll
+    for (int k = 0; k < CPAD; ++k) {
+      const int t = pl * CPAD + k;
+      const float ha = h[k] * __uint_as_float(ra[t]);
+      sab = fmaf(ha, __uint_as_float(rb[t]), sab);
+      sa += ha;
+      sb = fmaf(h[k], __uint_as_float(rb[t]), sb);
+    }
+    q += sab - sa * sb;
+  }
+  return q;
+}
+
+template <int DP>
+__global__ void __launch_bounds__(384, 1)
+    k_tc_pwq(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapPA,
+             const __grid_constant__ CUtensorMap mapPB, const float* __restrict__ Ha,
+             float* __restrict__ g, const int4* __restrict__ pool_tab,
+             const int4* __restrict__ seg_tab, int nseg, int C, int sp, int64_t m, float gscale,
+             int accumulate, int32_t* err) {
+  using namespace pwq_cfg;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  PwCtl* ctl = (PwCtl*)(sm + OFF_CTL);
+  float* red = (float*)(sm + OFF_RED);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    mbar_init(&ctl->x_full, 1);
+    mbar_init(&ctl->x_empty, 1);
+    mbar_init(&ctl->pt_full, 1);
+    mbar_init(&ctl->pt_empty, 1);
+    mbar_init(&ctl->s_full, 1);
+    mbar_init(&ctl->s_empty, 8);
+    mbar_init(&ctl->psi_full, 4);    // here: half 1's shares of the tile's rows are in red
+    mbar_init(&ctl->psi_empty, 4);   // here: half 0 has read them
+    mbar_init(&ctl->drain, 1);
+    ctl->abort_w = 0;
+    mbar_fence_init();
+  }
+  if (warp == 2) {
+    tmem_alloc(&ctl->tmem_base, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = ctl->tmem_base;
+  volatile int* abort_w = &ctl->abort_w;
+  auto give_up = [&](int code) {
+    ctl->abort_w = 1;
+    atomicExch(err, code);
+  };
+  // the labelled rows' segments carry no gradient
+  auto skip = [&](const int4& sg) { return (int64_t)sg.z <= m; };
+
+  if (warp == 0 && lane == 0) {
+    tma_prefetch(&mapX);
+    tma_prefetch(&mapPA);
+    tma_prefetch(&mapPB);
+    uint32_t nx = 0, npt = 0;
+    bool ok = true;
+    for (int gi = blockIdx.x; gi < nseg && ok && !*abort_w; gi += gridDim.x) {
+      const int4 sg = seg_tab[gi];
+      if (skip(sg)) continue;
+      const int4 pq = pool_tab[sg.x];
+      const int n1 = pq.z * sp;
+      const int pbase = 2 * sp * pq.w;
+      if (!mbar_wait(&ctl->pt_empty, (npt & 1) ^ 1, abort_w)) { give_up(51); break; }
+      mbar_expect_tx(&ctl->pt_full, 4 * n1 * 128);
+      for (int part = 0; part < 2; ++part)
+        for (int r = 0; r < n1; r += 64) {
+          tma_load_2d(sm + OFF_PA + part * PT_HALF + r * 128, &mapPA, &ctl->pt_full, 0,
+                      pbase + part * n1 + r);
+          tma_load_2d(sm + OFF_PB + part * PT_HALF + r * 128, &mapPB, &ctl->pt_full, 0,
+                      pbase + part * n1 + r);
+        }
+      ++npt;
+      for (int t = sg.y >> 7; t <= (sg.z - 1) >> 7; ++t) {
+        if (!mbar_wait(&ctl->x_empty, (nx & 1) ^ 1, abort_w)) { give_up(52); ok = false; break; }
+        mbar_expect_tx(&ctl->x_full, pw_cfg::XA_BYTES);
+        tma_load_2d(sm + OFF_XA, &mapX, &ctl->x_full, 0, t * 128);
+        ++nx;
+      }
+    }
+    if (nx) mbar_wait_drain(&ctl->x_full, (nx - 1) & 1);
+    if (npt) mbar_wait_drain(&ctl->pt_full, (npt - 1) & 1);
+  } else if (warp == 1 && lane == 0) {
+    uint32_t nx = 0, npt = 0, ns = 0;
+    bool ok = true;
+    for (int gi = blockIdx.x; gi < nseg && ok && !*abort_w; gi += gridDim.x) {
+      const int4 sg = seg_tab[gi];
+      if (skip(sg)) continue;
+      const int4 pq = pool_tab[sg.x];
+      const uint32_t idesc1 = idesc_bf16_f32(128, pq.z * sp);
+      if (!mbar_wait(&ctl->pt_full, npt & 1, abort_w)) { give_up(53); break; }
+      ++npt;
+      const int t0 = sg.y >> 7, t1 = (sg.z - 1) >> 7;
+      for (int t = t0; t <= t1; ++t) {
+        if (!mbar_wait(&ctl->x_full, nx & 1, abort_w) ||
+            !mbar_wait(&ctl->s_empty, (ns & 1) ^ 1, abort_w)) { give_up(54); ok = false; break; }
+        tc_fence_after();
+        const uint32_t xa = smem_u32(sm + OFF_XA), pa = smem_u32(sm + OFF_PA),
+                       pb = smem_u32(sm + OFF_PB);
+#pragma unroll
+        for (int k = 0; k < DP / 16; ++k) {
+          const uint64_t ad = sdesc_sw128(xa + k * 32);
+          umma_bf16(tmem + TA, ad, sdesc_sw128(pa + k * 32), idesc1, k > 0 ? 1u : 0u);
+          umma_bf16(tmem + TA, ad, sdesc_sw128(pa + PT_HALF + k * 32), idesc1, 1u);
+          umma_bf16(tmem + TB, ad, sdesc_sw128(pb + k * 32), idesc1, k > 0 ? 1u : 0u);
+          umma_bf16(tmem + TB, ad, sdesc_sw128(pb + PT_HALF + k * 32), idesc1, 1u);
+        }
+        umma_commit(&ctl->s_full);
+        umma_commit(&ctl->x_empty);
+        ++nx;
+        ++ns;
+        if (t == t1) umma_commit(&ctl->pt_empty);
+      }
+    }
+    umma_commit(&ctl->drain);
+    mbar_wait_drain(&ctl->drain, 0);
+  } else if (warp >= 4) {
+    const int quad = warp & 3, half = (warp - 4) >> 2;
+    const int i = quad * 32 + lane;
+    const uint32_t lanes = (uint32_t)(quad * 32) << 16;
+    uint32_t ns = 0, nr = 0;
+    bool ok = true;
+    for (int gi = blockIdx.x; gi < nseg && ok && !*abort_w; gi += gridDim.x) {
+      const int4 sg = seg_tab[gi];
+      if (skip(sg)) continue;
+      const int4 pq = pool_tab[sg.x];
+      const int cpad = pq.z, cq = pq.y;
+      const int n1 = cpad * sp;
+      const int t0 = sg.y >> 7, t1 = (sg.z - 1) >> 7;
+      for (int t = t0; t <= t1; ++t) {
+        const int64_t row = (int64_t)t * 128 + i;
+        const bool valid = row >= sg.y && row < sg.z && row >= m;
+        float h[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) h[k] = (valid && k < cq) ? Ha[row * C + pq.x + k] : 0.0f;
+        if (!mbar_wait(&ctl->s_full, ns & 1, abort_w)) {
+          give_up(55);
+          ok = false;
+          break;
+        }
+        ++ns;
+        tc_fence_after();
+        float q = 0.0f;
+        for (int ch = half; ch < n1 / 32; ch += 2) {
+          uint32_t ra[32], rb[32];
+          tmem_ld32_async(tmem + lanes + TA + ch * 32, ra);
+          tmem_ld32_async(tmem + lanes + TB + ch * 32, rb);
+          tmem_wait_ld();
+          if (cpad == 8) q += pw_quad_chunk<8>(ra, rb, h);
+          else if (cpad == 16) q += pw_quad_chunk<16>(ra, rb, h);
+          else q += pw_quad_chunk<32>(ra, rb, h);
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ctl->s_empty);
+        // the two halves of the row: half 1 leaves its share, half 0 writes the sum
+        if (half == 1) {
+          if (!mbar_wait(&ctl->psi_empty, (nr & 1) ^ 1, abort_w)) {
+            give_up(56);
+            ok = false;
+            break;
+          }
+          red[i] = q;
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&ctl->psi_full);
+        } else {
+          if (!mbar_wait(&ctl->psi_full, nr & 1, abort_w)) {
+            give_up(57);
+            ok = false;
+            break;
+          }
+          if (valid) {
+            const float v = -gscale * (q + red[i]);
+            g[row - m] = accumulate ? g[row - m] + v : v;
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&ctl->psi_empty);
+        }
+        ++nr;
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 2) {
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+template <int DP>
+static int32_t tc_quad_pw_t(firal_problem* P, const float* A, const float* B, int s, double scale,
+                            float* g) {
+  using namespace pwq_cfg;
+  cudaStream_t st = P->H->stream;
+  const int c = P->c, d = P->d;
+  const int Qe = pool_count(P->pt);
+  FIRAL_TRY(P->vmean.ensure((size_t)2 * s * Qe * d * sizeof(float)));
+  float* meanA = P->vmean.as<float>();
+  float* meanB = meanA + (size_t)s * Qe * d;
+  ProfScope ps(st, PF_QUAD);
+  count_launch(2);
+  k_class_mean<<<s * Qe, 1024, 0, st>>>(A, s, c, d, P->D, meanA, P->pt);
+  k_class_mean<<<s * Qe, 1024, 0, st>>>(B, s, c, d, P->D, meanB, P->pt);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  static bool attr[3] = {false, false, false};
+  const int ai = DP == 16 ? 0 : DP == 32 ? 1 : 2;
+  if (!attr[ai]) {
+    FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tc_pwq<DP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        SMEM));
+    attr[ai] = true;
+  }
+  const int64_t Np = P->Np;
+  CUtensorMap mX;
+  FIRAL_TRY(make_map(&mX, DP < 64 ? P->X64.p : P->Xb.p, Np, 64, 128, 64, true));
+  // probe groups whose columns fit (sp cpad <= 256); each group adds to the previous ones
+  const int sg = pw_cfg::N1MAX / P->pw_cpad_max;
+  for (int j0 = 0; j0 < s; j0 += sg) {
+    const int n = std::min(sg, s - j0), sp = (n + 7) / 8 * 8;
+    const int64_t prows = 2LL * sp * P->pw_cpad_total;
+    FIRAL_TRY(P->pw_pk.ensure((size_t)2 * prows * 64 * 2));
+    bf16* pkA = P->pw_pk.as<bf16>();
+    bf16* pkB = pkA + prows * 64;
+    count_launch(3);
+    k_pw_pack<<<dim3((unsigned)Qe, (unsigned)sp), 256, 0, st>>>(
+        pkA, A + (int64_t)j0 * P->D, meanA + (size_t)j0 * Qe * d, P->pw_pool.as<int4>(), n, sp, d,
+        P->D, Qe);
+    k_pw_pack<<<dim3((unsigned)Qe, (unsigned)sp), 256, 0, st>>>(
+        pkB, B + (int64_t)j0 * P->D, meanB + (size_t)j0 * Qe * d, P->pw_pool.as<int4>(), n, sp, d,
+        P->D, Qe);
+    FIRAL_CUDA_TRY(cudaGetLastError());
+    CUtensorMap mA, mB;
+    FIRAL_TRY(make_map(&mA, pkA, prows, 64, 64, 64, true));
+    FIRAL_TRY(make_map(&mB, pkB, prows, 64, 64, 64, true));
+    k_tc_pwq<DP><<<std::min(P->pw_nseg, P->sms), 384, SMEM, st>>>(
+        mX, mA, mB, P->Ha.as<float>(), g, P->pw_pool.as<int4>(), P->pw_seg.as<int4>(),
+        P->pw_nseg, c, sp, P->m, (float)(scale / s), j0 > 0 ? 1 : 0, tc_error_word(P));
+    FIRAL_CUDA_TRY(cudaGetLastError());
+  }
+  return FIRAL_OK;
+}
+
+static int32_t tc_quad_pw(firal_problem* P, const float* A, const float* B, int s, double scale,
+                          float* g) {
+  switch (P->dp) {
+    case 16: return tc_quad_pw_t<16>(P, A, B, s, scale, g);
+    case 32: return tc_quad_pw_t<32>(P, A, B, s, scale, g);
+    default: return tc_quad_pw_t<64>(P, A, B, s, scale, g);
+  }
+}
+
 template <int NPART>
 static int32_t tc_apply_dp(firal_problem* P, const void* w, const void* Sblk, const void* V, int s,
                            void* out, double* pq, double lam_null) {
@@ -2781,6 +3580,9 @@ int32_t tc_hessian_apply(firal_problem* P, const void* w, const void* Sblk, cons
   // next to the result is the rows' mean low-rank share (sum_k h_ik^2 on plain rows, 1 on
   // centred ones: about e / c for flat softmax rows); above 0.1 (errors above ~2e-4 per
   // apply) the problem takes the hi + lo direction in both modes
+  // at most 32 classes per pool: the fused per-point kernel (its lambda I term is lam_null,
+  // added on rank 0 of a row-sharded group)
+  if (P->pw) return tc_apply_pw(P, (const float*)w, (const float*)V, s, (float*)out, pq, lam_null);
   if (P->prec == FIRAL_MIXED_BF16_FAST && P->lowrank_share <= 0.1)
     return tc_apply_dp<1>(P, w, Sblk, V, s, out, pq, lam_null);
   return tc_apply_dp<2>(P, w, Sblk, V, s, out, pq, lam_null);
@@ -2791,6 +3593,7 @@ int32_t tc_quad_forms(firal_problem* P, const void* A, const void* B, int s, dou
   const float* a = (const float*)A;
   const float* b = (const float*)B;
   float* gg = (float*)g;
+  if (P->pw && !sharded(P)) return tc_quad_pw(P, a, b, s, scale, gg);
   switch (P->dp) {
     case 16: return tc_quad_t<16>(P, a, b, s, scale, gg);
     case 32: return tc_quad_t<32>(P, a, b, s, scale, gg);

@@ -118,7 +118,8 @@ def test_mixed_relax_fhat_and_z_vs_exact_solve_oracle(api, handle, precision, d,
                                      (2049, 64, 36, 1), (1300, 96, 40, 15), (2300, 64, 64, 16)])
 def test_mixed_quad_forms(api, handle, n, d, c, s, precision):
     """Tensor-core per-point quadratic forms (eq. 11) vs the oracle; a large N-component added
-    to A must not change the result (H_i vanishes on N = {1_c (x) u}).  d >= 64 with c a
+    to A must not change the result (H_i vanishes on N = {1_c (x) u}).  At most 32 classes
+    with d <= 64 take the fused per-point kernel (c = 10, 12 here); otherwise d >= 64 with c a
     multiple of 4 takes the feature-contracted kernel: class-chunk-major for s <= 16 (its two
     epilogue groups split the probes by parity: s = 1, odd s = 3, 15 and s = 16 included),
     probe-major for s = 17, 20."""
