@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--round-selections", type=int, default=20)
     ap.add_argument("--batched-iters", type=int, default=5,
                     help="timed batched MD iterations (the batched sub-measurement)")
+    ap.add_argument("--batched-pools", type=int, default=64,
+                    help="pools of the batched workload (64; fewer for small profiling runs)")
     ap.add_argument("--replicas", action="store_true",
                     help="N > 1: N independent problems instead of one row-sharded problem")
     ap.add_argument("--only", default=None, choices=["round", "batched", "exact", "al"],
@@ -539,7 +541,7 @@ def batched_measure(args, H):
 
     from paper_2409_07392_gb300 import api
     from paper_2409_07392_gb300.synth import batched_problems, make_problem
-    shapes = batched_problems(64, seed=0)
+    shapes = batched_problems(args.batched_pools, seed=0)
     dicts, npts, flops_apply, bytes_apply = [], 0, 0.0, 0.0
     s = 8
     for i, sh in enumerate(shapes):
@@ -578,7 +580,7 @@ def batched_measure(args, H):
     H.set_default_tuning(0, 0, 0)
     applies = 2 * cg + 1
     pk, _ = peaks()
-    return {"workload": f"batched_uneven: 64 pools, {npts} points in all, s={s}, "
+    return {"workload": f"batched_uneven: {len(shapes)} pools, {npts} points in all, s={s}, "
                         f"cg_iters/solve={cg}", "precision": bprec,
             "value": 1.0 / per, "unit": "batched MD iters/s", "ms_per_iteration": 1000 * per,
             "hbm_frac_of_measured": applies * bytes_apply / per / 1e9 / pk["hbm_gbs"],

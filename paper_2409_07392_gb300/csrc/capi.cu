@@ -1323,7 +1323,10 @@ int32_t firal_problem_destroy(firal_problem* P) {
                   &P->cgP, &P->cgQ, &P->cgZ, &P->cgcols, &P->cgpart1, &P->cgpart2, &P->V, &P->U,
                   &P->W, &P->HU, &P->g, &P->red, &P->zsave, &P->Xb, &P->Hb, &P->HbT, &P->Pb, &P->vmean, &P->qmean, &P->Aw, &P->Zp, &P->Hlo, &P->gq_ab,
                   &P->gq_m, &P->gq_part, &P->rtab, &P->rM, &P->tdev, &P->cen, &P->cen_off,
-                  &P->cen_idx, &P->Ub, &P->UbT, &P->cen_am, &P->cen_rho, &P->cen_lab, &P->cen_items, &P->cen_part}) {
+                  &P->cen_idx, &P->Ub, &P->UbT, &P->cen_am, &P->cen_rho, &P->cen_lab, &P->cen_items, &P->cen_part,
+                  &P->pool_tabs, &P->pool_z, &P->md_part, &P->kr_alpha, &P->kr_dterm,
+                  &P->kr_bsum, &P->bcg, &P->pw_pool, &P->pw_seg, &P->pw_pseg, &P->pw_pk,
+                  &P->pw_part, &P->X64}) {
     if (synced) b->park();
     else b->release();
   }

@@ -162,6 +162,7 @@ struct firal_problem {
   firal::PoolTab pt;      // pooled problems only (device tables below)
   firal::DBuf pool_tabs;  // cpool | coff | pdim (int32) for pt
   firal::DBuf pool_z;     // pooled: per-pool budgets (f64, Q) and pool-row offsets (i64, Q + 1)
+  firal::DBuf md_part;    // pooled: per-block partials of the MD step (max, then sum)
   std::vector<int64_t> pool_zoff_h;   // pooled: pool-row offsets, host copy
   firal::DBuf kr_alpha, kr_dterm, kr_bsum;  // pooled: K ranges of the tensor-core GEMM tiles
   int kbL = 0;                   // pooled: K-steps holding the labelled rows (every class tile)

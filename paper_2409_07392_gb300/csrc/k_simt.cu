@@ -1196,16 +1196,19 @@ __global__ void k_md_zmax(double* red) {
 }
 
 // Pooled problems: the MD update of every pool on its own simplex (Alg. 2 lines 10-11 with
-// that pool's ||g||_inf and budget).  One block per pool; pool p owns z[zoff[p] .. zoff[p+1]).
+// that pool's ||g||_inf and budget).  Pool p owns z[zoff[p] .. zoff[p+1]); MD_POOL_BLOCKS
+// blocks share it (blockIdx.y), in three passes with per-block partials reduced in a fixed
+// order: ||g||_inf, then z exp(-beta g) and its sum, then the rescale to the budget.
+constexpr int MD_POOL_BLOCKS = 16;
+
 template <class T>
-__global__ void k_md_pooled(T* z, const T* g, const int64_t* zoff, const double* budget,
-                            double beta0) {
+__global__ void k_md_pooled_max(const T* g, const int64_t* zoff, double* part) {
   __shared__ double red[32];
-  __shared__ double s_val;
-  const int p = blockIdx.x;
-  const int64_t a = zoff[p], b = zoff[p + 1];
+  const int p = blockIdx.x, b = blockIdx.y;
+  const int64_t a = zoff[p], e = zoff[p + 1];
   double mx = 0.0;
-  for (int64_t i = a + threadIdx.x; i < b; i += blockDim.x) {
+  for (int64_t i = a + (int64_t)b * blockDim.x + threadIdx.x; i < e;
+       i += (int64_t)gridDim.y * blockDim.x) {
     const double v = fabs((double)g[i]);
     mx = (v > mx || v != v) ? v : mx;
   }
@@ -1218,29 +1221,76 @@ __global__ void k_md_pooled(T* z, const T* g, const int64_t* zoff, const double*
   if (threadIdx.x == 0) {
     double r = 0.0;
     for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r = (red[i] > r || red[i] != red[i]) ? red[i] : r;
-    s_val = r > 0.0 ? beta0 / r : 0.0;
+    part[(int64_t)p * MD_POOL_BLOCKS + b] = r;
+  }
+}
+
+template <class T>
+__global__ void k_md_pooled_exp(T* z, const T* g, const int64_t* zoff, double beta0,
+                                double* part) {
+  __shared__ double sh[32];
+  __shared__ double s_beta;
+  const int p = blockIdx.x, b = blockIdx.y;
+  const int Q = gridDim.x;
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int i = 0; i < MD_POOL_BLOCKS; ++i) {
+      const double v = part[(int64_t)p * MD_POOL_BLOCKS + i];
+      r = (v > r || v != v) ? v : r;
+    }
+    s_beta = r > 0.0 ? beta0 / r : 0.0;
   }
   __syncthreads();
-  const double beta = s_val;
+  const double beta = s_beta;
+  const int64_t a = zoff[p], e = zoff[p + 1];
   double acc = 0.0;
-  for (int64_t i = a + threadIdx.x; i < b; i += blockDim.x) {
+  for (int64_t i = a + (int64_t)b * blockDim.x + threadIdx.x; i < e;
+       i += (int64_t)gridDim.y * blockDim.x) {
     const T zn = (T)((double)z[i] * exp(-beta * (double)g[i]));
     z[i] = zn;
     acc += (double)zn;
   }
-  const double tot = block_sum(acc, red);
-  const double sc = budget[p] / tot;
-  for (int64_t i = a + threadIdx.x; i < b; i += blockDim.x) z[i] = (T)((double)z[i] * sc);
+  const double tot = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[(int64_t)(Q + p) * MD_POOL_BLOCKS + b] = tot;
+}
+
+template <class T>
+__global__ void k_md_pooled_scale(T* z, const int64_t* zoff, const double* budget,
+                                  const double* part) {
+  __shared__ double s_sc;
+  const int p = blockIdx.x, b = blockIdx.y;
+  const int Q = gridDim.x;
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int i = 0; i < MD_POOL_BLOCKS; ++i) tot += part[(int64_t)(Q + p) * MD_POOL_BLOCKS + i];
+    s_sc = budget[p] / tot;
+  }
+  __syncthreads();
+  const double sc = s_sc;
+  const int64_t a = zoff[p], e = zoff[p + 1];
+  for (int64_t i = a + (int64_t)b * blockDim.x + threadIdx.x; i < e;
+       i += (int64_t)gridDim.y * blockDim.x)
+    z[i] = (T)((double)z[i] * sc);
 }
 
 int32_t md_step_pooled(firal_problem* P, void* z, const void* g, double beta0, cudaStream_t st) {
   const int Q = P->pt.Q;
   const double* budget = P->pool_z.as<double>();
   const int64_t* zoff = reinterpret_cast<const int64_t*>(budget + Q);
+  FIRAL_TRY(P->md_part.ensure((size_t)2 * Q * MD_POOL_BLOCKS * sizeof(double)));
+  double* part = P->md_part.as<double>();
+  const dim3 grid((unsigned)Q, MD_POOL_BLOCKS);
   ProfScope ps(st, PF_MD);
-  count_launch();
-  if (P->dbl) k_md_pooled<double><<<Q, 1024, 0, st>>>((double*)z, (const double*)g, zoff, budget, beta0);
-  else k_md_pooled<float><<<Q, 1024, 0, st>>>((float*)z, (const float*)g, zoff, budget, beta0);
+  count_launch(3);
+  if (P->dbl) {
+    k_md_pooled_max<double><<<grid, 256, 0, st>>>((const double*)g, zoff, part);
+    k_md_pooled_exp<double><<<grid, 256, 0, st>>>((double*)z, (const double*)g, zoff, beta0, part);
+    k_md_pooled_scale<double><<<grid, 256, 0, st>>>((double*)z, zoff, budget, part);
+  } else {
+    k_md_pooled_max<float><<<grid, 256, 0, st>>>((const float*)g, zoff, part);
+    k_md_pooled_exp<float><<<grid, 256, 0, st>>>((float*)z, (const float*)g, zoff, beta0, part);
+    k_md_pooled_scale<float><<<grid, 256, 0, st>>>((float*)z, zoff, budget, part);
+  }
   FIRAL_CUDA_TRY(cudaGetLastError());
   return FIRAL_OK;
 }

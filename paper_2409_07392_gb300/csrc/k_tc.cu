@@ -1682,12 +1682,19 @@ __global__ void k_build_z(bf16* Zhi, bf16* Zlo, const bf16* Xb, int d, int dp, i
 // Block = one 64-point block x 32 classes; each warp store writes one 128-byte row run.
 __global__ void k_weighted_hT(bf16* Ahi, bf16* Alo, bf16* AP, const float* Ha, const float* w,
                               int64_t N, int c, int64_t Np, int cpb, const int* cen,
-                              int64_t wskip) {
+                              int64_t wskip, const int4* klist = nullptr, int kbL = 0) {
   __shared__ float tile[64][33];
   __shared__ float ws[64], wS[64];
   __shared__ int cs[64];
   const int64_t rb = (int64_t)blockIdx.x * 64;
   const int cb = blockIdx.y * 32;
+  // pooled: the block sums read, for each 128-class tile, the labelled rows' K-steps and its
+  // pools' K-steps only (K list {first, end, ...}); the other blocks stay unwritten
+  if (klist) {
+    const int64_t kb = blockIdx.x;
+    const int4 kl = klist[cb / 128];
+    if (kb >= kbL && (kb < kl.x || kb >= kl.y)) return;
+  }
   for (int i = threadIdx.y; i < 64; i += blockDim.y) {
     const int64_t r = rb + i;
     const int col = cb + threadIdx.x;
@@ -2449,7 +2456,8 @@ int32_t tc_syrk_blocks(firal_problem* P, const void* wv, double lamS, void* outS
     count_launch(1 + (outS ? 1 : 0) + (outP ? 1 : 0));
     k_weighted_hT<<<dim3((unsigned)(Np / 64), (unsigned)(cpb / 32)), dim3(32, 8), 0, st>>>(
         outS ? Ahi : nullptr, Alo, outP ? AP : nullptr, P->Ha.as<float>(), w, P->N, c, Np, cpb,
-        P->n_cen > 0 ? P->cen.as<int>() : nullptr, lab_rows(P));
+        P->n_cen > 0 ? P->cen.as<int>() : nullptr, lab_rows(P),
+        P->pt.Q ? P->kr_bsum.as<int4>() : nullptr, P->kbL);
     FIRAL_CUDA_TRY(cudaGetLastError());
     // blocked operands as 2-D tensors of 64-point rows: tile (kb, row block) = 16 KB run
     CUtensorMap mA0, mA1, mA2, mZ0, mZ1;
@@ -2781,61 +2789,77 @@ int32_t tc_round_scores(firal_problem* P, const void* M1, const void* M2, const 
 }
 
 // ------------------------------------------------------------------------------------------
-// Pooled problems with few classes per pool: the Hessian apply in the per-point form of
-// Lemma 1, fused into one persistent kernel.  For the rows of one pool q (weights w_i,
-// probabilities h_i over the pool's c_q classes, direction P~ with the pool's class means
-// removed):
+// At most 32 classes per pool: the Hessian apply in the per-point form of Lemma 1, fused into
+// one persistent kernel.  For the rows of one pool q (weights w_i, probabilities h_i over the
+// pool's c_q classes, direction P~ with the pool's class means removed):
 //   a_ikj = x_i . P~_j[:, k]                      MMA1: 128 rows x (probe, class), K = features
 //   alpha_ij = sum_k h_ik a_ikj,   psi_ikj = w_i h_ik (a_ikj - alpha_ij)     f32, CUDA cores
 //   out_j[:, k] += sum_i psi_ikj x_i              MMA2: (probe, class) x features, K = rows
 // P~ and psi enter as bf16 hi + lo (x is exact in bf16), so both products carry about 2^-17
 // relative rounding, and nothing cancels: each psi is the row's own contribution.  Column
 // (probe j, class k) is j cpad + k, cpad = the pool's class count rounded up to 8, 16 or 32,
-// so one 32-column TMEM load holds whole probes.
-// Work list: segments of at most PW_SEG_TILES 128-row tiles of one pool's rows (its labelled
-// rows and its pool rows are separate segments).  A tile that also holds rows of another
-// pool runs once per pool with the other rows masked.  A segment accumulates out in TMEM
-// and writes one partial; a per-class combine adds a pool's partials in segment order.
+// so one 32-column TMEM load holds whole probes; a probe group of at most 128 columns is one
+// unit of work, so a pool with cpad s > 128 runs as several groups.
+// Work list: segments of at most SEG_TILES 128-row tiles of one pool's rows (its labelled
+// rows and its pool rows are separate segments); a CTA takes every probe group of each of its
+// segments (an item).  A tile that also holds rows of another pool runs once per pool with
+// the other rows masked.  An item accumulates out in TMEM and writes one partial; a
+// per-class combine adds a pool's partials in segment order.
+// Pipeline: the x and x^T tiles, the S accumulator (TMEM), the psi operand (shared memory) and
+// the D accumulator are double-buffered: the TMA loads of tile t+1, MMA1 of tile t+1, the
+// epilogue of tile t and MMA2 of tile t-1 overlap.  Each epilogue thread loads its row's h for
+// the next tile while it works on the current one.
 // Roles (384 threads): warp 0 TMA producer, warp 1 MMA issuer, warp 2 TMEM owner, warps 4-11
 // epilogue (warp & 3 = TMEM lane quarter, (warp - 4) >> 2 = which 32-column chunks).
 // ------------------------------------------------------------------------------------------
 namespace pw_cfg {
-constexpr int N1MAX = 256;                        // (probe, class) columns at most
+constexpr int NU = 128;                           // columns per unit (probe group)
 constexpr int SEG_TILES = 16;                     // tiles per segment: 256 adds per accumulator
-constexpr int PT_HALF = N1MAX * 128;              // P~ hi (then lo): 128-byte rows, 64 features
+constexpr int PT_HALF = NU * 128;                 // P~ hi (then lo) of one group: 16 KB
 constexpr int XA_BYTES = 128 * 128;               // x tile: 128 rows x 64 features
 constexpr int XT_BYTES = 2 * 64 * 128;            // x^T tile: 2 K-blocks x (<= 64 features)
-constexpr int PSI_KB = N1MAX * 128;               // psi^T: one K-block (64 rows) of one part
-constexpr int OFF_PT = 0, OFF_XA = 2 * PT_HALF, OFF_XT = OFF_XA + XA_BYTES;
-constexpr int OFF_PSI = OFF_XT + XT_BYTES, OFF_CTL = OFF_PSI + 4 * PSI_KB;
+constexpr int PSI_KB = NU * 128;                  // psi^T: one K-block (64 rows) of one part
+constexpr int PSI_BUF = 4 * PSI_KB;               // hi | lo, 2 K-blocks each: 64 KB
+constexpr int OFF_PT = 0, OFF_XA = 2 * PT_HALF, OFF_XT = OFF_XA + 2 * XA_BYTES;
+constexpr int OFF_PSI = OFF_XT + 2 * XT_BYTES, OFF_CTL = OFF_PSI + 2 * PSI_BUF;
 constexpr int SMEM = OFF_CTL + 256 + 1024;
-constexpr uint32_t TS = 0, TD = 256;              // TMEM columns: S (MMA1) | D (MMA2, 2 x DP)
+constexpr uint32_t TS = 0, TD = 256;              // TMEM columns: S (2 x 128) | D (2 x DP)
 }  // namespace pw_cfg
 
 struct PwCtl {   // < 256 bytes
-  uint64_t x_full, x_empty, xt_full, xt_empty, pt_full, pt_empty, s_full, s_empty, psi_full,
-      psi_empty, d_full, d_empty, drain;
+  uint64_t x_full[2], x_empty[2], xt_full[2], xt_empty[2], s_full[2], s_empty[2], psi_full[2],
+      psi_empty[2], d_full[2], d_empty[2], pt_full, pt_empty, drain;
   uint32_t tmem_base;
   int abort_w;
 };
 static_assert(sizeof(PwCtl) <= 256, "control block must fit in 256 bytes");
 
+// Probe groups of a pool (cpad, sp): ceil(cpad sp / 128); columns of group grp.
+__device__ __forceinline__ int pw_ngrp(int cpad, int sp) {
+  return (cpad * sp + pw_cfg::NU - 1) / pw_cfg::NU;
+}
+__device__ __forceinline__ int pw_ncols(int cpad, int sp, int grp) {
+  const int r = cpad * sp - grp * pw_cfg::NU;
+  return r < pw_cfg::NU ? r : pw_cfg::NU;
+}
+
 // psi for one 32-column chunk (32 / CPAD whole probes) of the thread's row, written as bf16
-// hi and lo to rows t of the chunk's psi^T block; off[r] = the thread's byte position in a
-// 128-byte-swizzled row r (mod 8)
+// hi and lo to rows t of the chunk's psi^T block.  wh = w h (zero on masked rows and padding
+// classes); alpha = (sum_k wh_k a_k) / w; off[r] = the thread's byte position in a
+// 128-byte-swizzled row r (mod 8).
 template <int CPAD>
-__device__ __forceinline__ void pw_psi_chunk(const uint32_t (&ra)[32], const float (&h)[32],
-                                             const float (&wh)[32], unsigned char* hi,
-                                             unsigned char* lo, const uint32_t (&off)[8]) {
+__device__ __forceinline__ void pw_psi_chunk(const uint32_t (&ra)[32], const float (&wh)[32],
+                                             float winv, unsigned char* hi, unsigned char* lo,
+                                             const uint32_t (&off)[8]) {
 #pragma unroll
   for (int pl = 0; pl < 32 / CPAD; ++pl) {
     float a0 = 0.0f, a1 = 0.0f;
 #pragma unroll
     for (int k = 0; k < CPAD; k += 2) {
-      a0 = fmaf(h[k], __uint_as_float(ra[pl * CPAD + k]), a0);
-      a1 = fmaf(h[k + 1], __uint_as_float(ra[pl * CPAD + k + 1]), a1);
+      a0 = fmaf(wh[k], __uint_as_float(ra[pl * CPAD + k]), a0);
+      a1 = fmaf(wh[k + 1], __uint_as_float(ra[pl * CPAD + k + 1]), a1);
     }
-    const float al = a0 + a1;
+    const float al = (a0 + a1) * winv;
 #pragma unroll
     for (int k = 0; k < CPAD; ++k) {
       const int t = pl * CPAD + k;
@@ -2846,6 +2870,16 @@ __device__ __forceinline__ void pw_psi_chunk(const uint32_t (&ra)[32], const flo
       *reinterpret_cast<bf16*>(lo + t * 128 + off[t & 7]) = pl2;
     }
   }
+}
+
+// loads of the thread's row for a tile: h over the pool's classes (zero beyond c_q and on
+// masked rows) and w
+__device__ __forceinline__ void pw_load_row(float (&hn)[32], float& wn, const float* Ha,
+                                            const float* w, int64_t row, bool valid, int64_t C,
+                                            int coff, int cq) {
+#pragma unroll
+  for (int k = 0; k < 32; ++k) hn[k] = (valid && k < cq) ? Ha[row * C + coff + k] : 0.0f;
+  wn = valid ? w[row] : 0.0f;
 }
 
 template <int DP>
@@ -2861,18 +2895,20 @@ __global__ void __launch_bounds__(384, 1)
   PwCtl* ctl = (PwCtl*)(sm + OFF_CTL);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    mbar_init(&ctl->x_full, 1);
-    mbar_init(&ctl->x_empty, 1);
-    mbar_init(&ctl->xt_full, 1);
-    mbar_init(&ctl->xt_empty, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&ctl->x_full[b], 1);
+      mbar_init(&ctl->x_empty[b], 1);
+      mbar_init(&ctl->xt_full[b], 1);
+      mbar_init(&ctl->xt_empty[b], 1);
+      mbar_init(&ctl->s_full[b], 1);
+      mbar_init(&ctl->s_empty[b], 8);
+      mbar_init(&ctl->psi_full[b], 8);
+      mbar_init(&ctl->psi_empty[b], 1);
+      mbar_init(&ctl->d_full[b], 1);
+      mbar_init(&ctl->d_empty[b], 8);
+    }
     mbar_init(&ctl->pt_full, 1);
     mbar_init(&ctl->pt_empty, 1);
-    mbar_init(&ctl->s_full, 1);
-    mbar_init(&ctl->s_empty, 8);
-    mbar_init(&ctl->psi_full, 8);
-    mbar_init(&ctl->psi_empty, 1);
-    mbar_init(&ctl->d_full, 1);
-    mbar_init(&ctl->d_empty, 8);
     mbar_init(&ctl->drain, 1);
     ctl->abort_w = 0;
     mbar_fence_init();
@@ -2892,102 +2928,125 @@ __global__ void __launch_bounds__(384, 1)
   };
 
   if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer: P~ of the segment's pool, then x and x^T of each tile
+    // ---------------- TMA producer: P~ of each item, x and x^T of each of its tiles
     tma_prefetch(&mapX);
     tma_prefetch(&mapXT);
     tma_prefetch(&mapPT);
-    uint32_t nx = 0, nxt = 0, npt = 0;   // loads issued per buffer
+    uint32_t nt = 0, ni = 0;   // tiles and items loaded
     bool ok = true;
     for (int g = blockIdx.x; g < nseg && ok && !*abort_w; g += gridDim.x) {
       const int4 sg = seg_tab[g];
       const int4 pq = pool_tab[sg.x];
-      const int n1 = pq.z * sp;
-      const int pbase = 2 * sp * pq.w;
-      if (!mbar_wait(&ctl->pt_empty, (npt & 1) ^ 1, abort_w)) { give_up(41); break; }
-      mbar_expect_tx(&ctl->pt_full, 2 * n1 * 128);
-      for (int part = 0; part < 2; ++part)
-        for (int r = 0; r < n1; r += 64)
-          tma_load_2d(sm + OFF_PT + part * PT_HALF + r * 128, &mapPT, &ctl->pt_full, 0,
-                      pbase + part * n1 + r);
-      ++npt;
-      for (int t = sg.y >> 7; t <= (sg.z - 1) >> 7; ++t) {
-        if (!mbar_wait(&ctl->x_empty, (nx & 1) ^ 1, abort_w)) { give_up(42); ok = false; break; }
-        mbar_expect_tx(&ctl->x_full, XA_BYTES);
-        tma_load_2d(sm + OFF_XA, &mapX, &ctl->x_full, 0, t * 128);
-        ++nx;
-        if (!mbar_wait(&ctl->xt_empty, (nxt & 1) ^ 1, abort_w)) { give_up(43); ok = false; break; }
-        mbar_expect_tx(&ctl->xt_full, 2 * DP * 128);
-        tma_load_2d(sm + OFF_XT, &mapXT, &ctl->xt_full, 0, (2 * t) * DP);
-        tma_load_2d(sm + OFF_XT + DP * 128, &mapXT, &ctl->xt_full, 0, (2 * t + 1) * DP);
-        ++nxt;
+      const int n1 = pq.z * sp, pbase = 2 * sp * pq.w;
+      const int ng = pw_ngrp(pq.z, sp);
+      for (int grp = 0; grp < ng && ok; ++grp) {
+        const int nc = pw_ncols(pq.z, sp, grp);
+        if (!mbar_wait(&ctl->pt_empty, (ni & 1) ^ 1, abort_w)) { give_up(41); ok = false; break; }
+        mbar_expect_tx(&ctl->pt_full, 2 * nc * 128);
+        for (int part = 0; part < 2; ++part)
+          for (int r = 0; r < nc; r += 64)
+            tma_load_2d(sm + OFF_PT + part * PT_HALF + r * 128, &mapPT, &ctl->pt_full, 0,
+                        pbase + part * n1 + grp * NU + r);
+        ++ni;
+        for (int t = sg.y >> 7; t <= (sg.z - 1) >> 7; ++t) {
+          const int b = nt & 1;
+          const uint32_t ph = (nt >> 1) & 1;
+          // both buffers free before either load is issued: a wait that gives up leaves no
+          // load of this tile in flight
+          if (!mbar_wait(&ctl->x_empty[b], ph ^ 1, abort_w) ||
+              !mbar_wait(&ctl->xt_empty[b], ph ^ 1, abort_w)) {
+            give_up(42);
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&ctl->x_full[b], XA_BYTES);
+          tma_load_2d(sm + OFF_XA + b * XA_BYTES, &mapX, &ctl->x_full[b], 0, t * 128);
+          mbar_expect_tx(&ctl->xt_full[b], 2 * DP * 128);
+          unsigned char* xt = sm + OFF_XT + b * XT_BYTES;
+          tma_load_2d(xt, &mapXT, &ctl->xt_full[b], 0, (2 * t) * DP);
+          tma_load_2d(xt + DP * 128, &mapXT, &ctl->xt_full[b], 0, (2 * t + 1) * DP);
+          ++nt;
+        }
       }
     }
-    // every issued load lands before the CTA can exit
-    if (nx) mbar_wait_drain(&ctl->x_full, (nx - 1) & 1);
-    if (nxt) mbar_wait_drain(&ctl->xt_full, (nxt - 1) & 1);
-    if (npt) mbar_wait_drain(&ctl->pt_full, (npt - 1) & 1);
+    // every issued load lands before the CTA can exit (buffer b took loads nt = b, b + 2, ...)
+    for (int b = 0; b < 2; ++b) {
+      const uint32_t cnt = (nt + 1 - b) / 2;
+      if (cnt) {
+        mbar_wait_drain(&ctl->x_full[b], (cnt - 1) & 1);
+        mbar_wait_drain(&ctl->xt_full[b], (cnt - 1) & 1);
+      }
+    }
+    if (ni) mbar_wait_drain(&ctl->pt_full, (ni - 1) & 1);
   } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer
-    uint32_t nx = 0, nxt = 0, npt = 0, ns = 0, nseg_done = 0;
-    bool ok = true;
+    // ---------------- MMA issuer: MMA1 of unit u, then MMA2 of unit u - 1
     constexpr uint32_t idesc2 = idesc_bf16_f32(128, DP);
+    struct Pend {
+      uint32_t u, item;
+      bool first, last;
+    };
+    Pend pend{0, 0, false, false};
+    bool have = false;
+    uint32_t nt = 0, ni = 0;
+    bool ok = true;
+    auto mma2 = [&](const Pend& p) -> bool {
+      const int b = p.u & 1, db = p.item & 1;
+      const uint32_t ph = (p.u >> 1) & 1;
+      if (!mbar_wait(&ctl->psi_full[b], ph, abort_w) || !mbar_wait(&ctl->xt_full[b], ph, abort_w) ||
+          (p.first && !mbar_wait(&ctl->d_empty[db], ((p.item >> 1) & 1) ^ 1, abort_w)))
+        return false;
+      tc_fence_after();
+      const uint32_t ps = smem_u32(sm + OFF_PSI + b * PSI_BUF),
+                     xt = smem_u32(sm + OFF_XT + b * XT_BYTES);
+#pragma unroll
+      for (int kb = 0; kb < 2; ++kb)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const uint64_t bd = sdesc_sw128(xt + kb * DP * 128 + k * 32);
+          const uint32_t a0 = ps + kb * PSI_KB + k * 32;
+          const uint32_t acc = (p.first && kb == 0 && k == 0) ? 0u : 1u;
+          umma_bf16(tmem + TD + db * DP, sdesc_sw128(a0), bd, idesc2, acc);
+          umma_bf16(tmem + TD + db * DP, sdesc_sw128(a0 + 2 * PSI_KB), bd, idesc2, 1u);
+        }
+      umma_commit(&ctl->psi_empty[b]);
+      umma_commit(&ctl->xt_empty[b]);
+      if (p.last) umma_commit(&ctl->d_full[db]);
+      return true;
+    };
     for (int g = blockIdx.x; g < nseg && ok && !*abort_w; g += gridDim.x) {
       const int4 sg = seg_tab[g];
       const int4 pq = pool_tab[sg.x];
-      const int n1 = pq.z * sp;
-      const uint32_t idesc1 = idesc_bf16_f32(128, n1);
-      const int nblk = (n1 + 127) >> 7;
-      if (!mbar_wait(&ctl->pt_full, npt & 1, abort_w)) { give_up(44); break; }
-      ++npt;
+      const int ng = pw_ngrp(pq.z, sp);
       const int t0 = sg.y >> 7, t1 = (sg.z - 1) >> 7;
-      for (int t = t0; t <= t1 && ok; ++t) {
-        // MMA1: S = x P~^T (hi and lo parts of P~ into the same accumulator)
-        if (!mbar_wait(&ctl->x_full, nx & 1, abort_w) ||
-            !mbar_wait(&ctl->s_empty, (ns & 1) ^ 1, abort_w)) { give_up(45); ok = false; break; }
-        tc_fence_after();
-        const uint32_t xa = smem_u32(sm + OFF_XA), pt = smem_u32(sm + OFF_PT);
+      for (int grp = 0; grp < ng && ok; ++grp) {
+        const uint32_t idesc1 = idesc_bf16_f32(128, pw_ncols(pq.z, sp, grp));
+        if (!mbar_wait(&ctl->pt_full, ni & 1, abort_w)) { give_up(44); ok = false; break; }
+        const uint32_t item = ni++;
+        for (int t = t0; t <= t1; ++t) {
+          const uint32_t u = nt;
+          const int b = u & 1;
+          const uint32_t ph = (u >> 1) & 1;
+          if (!mbar_wait(&ctl->x_full[b], ph, abort_w) ||
+              !mbar_wait(&ctl->s_empty[b], ph ^ 1, abort_w)) { give_up(45); ok = false; break; }
+          tc_fence_after();
+          const uint32_t xa = smem_u32(sm + OFF_XA + b * XA_BYTES), pt = smem_u32(sm + OFF_PT);
 #pragma unroll
-        for (int k = 0; k < DP / 16; ++k) {
-          const uint64_t ad = sdesc_sw128(xa + k * 32);
-          umma_bf16(tmem + TS, ad, sdesc_sw128(pt + k * 32), idesc1, k > 0 ? 1u : 0u);
-          umma_bf16(tmem + TS, ad, sdesc_sw128(pt + PT_HALF + k * 32), idesc1, 1u);
-        }
-        umma_commit(&ctl->s_full);
-        umma_commit(&ctl->x_empty);
-        ++nx;
-        ++ns;
-        if (t == t1) umma_commit(&ctl->pt_empty);
-        // MMA2: D_b += psi^T x (rows of block b of the (probe, class) columns)
-        if (!mbar_wait(&ctl->psi_full, (ns - 1) & 1, abort_w) ||
-            !mbar_wait(&ctl->xt_full, nxt & 1, abort_w) ||
-            (t == t0 && !mbar_wait(&ctl->d_empty, (nseg_done & 1) ^ 1, abort_w))) {
-          give_up(46);
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        const uint32_t ps = smem_u32(sm + OFF_PSI), xt = smem_u32(sm + OFF_XT);
-        for (int b = 0; b < nblk; ++b) {
-#pragma unroll
-          for (int kb = 0; kb < 2; ++kb)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              const uint64_t bd = sdesc_sw128(xt + kb * DP * 128 + k * 32);
-              const uint32_t a0 = ps + kb * PSI_KB + b * 128 * 128 + k * 32;
-              const uint32_t first = (t == t0 && kb == 0 && k == 0) ? 0u : 1u;
-              umma_bf16(tmem + TD + b * DP, sdesc_sw128(a0), bd, idesc2, first);
-              umma_bf16(tmem + TD + b * DP, sdesc_sw128(a0 + 2 * PSI_KB), bd, idesc2, 1u);
-            }
-        }
-        umma_commit(&ctl->psi_empty);
-        umma_commit(&ctl->xt_empty);
-        ++nxt;
-        if (t == t1) {
-          umma_commit(&ctl->d_full);
-          ++nseg_done;
+          for (int k = 0; k < DP / 16; ++k) {
+            const uint64_t ad = sdesc_sw128(xa + k * 32);
+            umma_bf16(tmem + TS + b * NU, ad, sdesc_sw128(pt + k * 32), idesc1, k > 0 ? 1u : 0u);
+            umma_bf16(tmem + TS + b * NU, ad, sdesc_sw128(pt + PT_HALF + k * 32), idesc1, 1u);
+          }
+          umma_commit(&ctl->s_full[b]);
+          umma_commit(&ctl->x_empty[b]);
+          if (t == t1) umma_commit(&ctl->pt_empty);
+          ++nt;
+          if (have && !mma2(pend)) { give_up(46); ok = false; break; }
+          pend = Pend{u, item, t == t0, t == t1};
+          have = true;
         }
       }
     }
+    if (ok && have && !*abort_w && !mma2(pend)) give_up(46);
     umma_commit(&ctl->drain);
     mbar_wait_drain(&ctl->drain, 0);
   } else if (warp >= 4) {
@@ -2999,78 +3058,91 @@ __global__ void __launch_bounds__(384, 1)
     uint32_t off[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) off[r] = ((((i & 63) >> 3) ^ r) << 4) + ((i & 7) << 1);
-    unsigned char* psi_hi0 = sm + OFF_PSI + (i >> 6) * PSI_KB;
-    uint32_t ns = 0, nseg_done = 0;
-    for (int g = blockIdx.x; g < nseg && !*abort_w; g += gridDim.x) {
+    uint32_t u = 0, ni = 0;
+    bool ok = true;
+    for (int g = blockIdx.x; g < nseg && ok && !*abort_w; g += gridDim.x) {
       const int4 sg = seg_tab[g];
       const int4 pq = pool_tab[sg.x];
       const int cpad = pq.z, cq = pq.y;
-      const int n1 = cpad * sp;
+      const int ng = pw_ngrp(cpad, sp);
       const int t0 = sg.y >> 7, t1 = (sg.z - 1) >> 7;
-      bool ok = true;
-      for (int t = t0; t <= t1; ++t) {
-        const int64_t row = (int64_t)t * 128 + i;
-        const bool valid = row >= sg.y && row < sg.z;
-        const float wi = valid ? w[row] : 0.0f;
-        float h[32], wh[32];
-#pragma unroll
-        for (int k = 0; k < 32; ++k) {
-          h[k] = (valid && k < cq) ? Ha[row * C + pq.x + k] : 0.0f;
-          wh[k] = wi * h[k];
+      for (int grp = 0; grp < ng && ok; ++grp) {
+        const int nc = pw_ncols(cpad, sp, grp);
+        const uint32_t item = ni++;
+        float hn[32], wn;
+        {
+          const int64_t row = (int64_t)t0 * 128 + i;
+          pw_load_row(hn, wn, Ha, w, row, row >= sg.y && row < sg.z, C, pq.x, cq);
         }
-        if (!mbar_wait(&ctl->s_full, ns & 1, abort_w) ||
-            !mbar_wait(&ctl->psi_empty, (ns & 1) ^ 1, abort_w)) {
-          give_up(47);
+        for (int t = t0; t <= t1; ++t) {
+          float wh[32];
+#pragma unroll
+          for (int k = 0; k < 32; ++k) wh[k] = wn * hn[k];
+          const float winv = wn != 0.0f ? 1.0f / wn : 0.0f;
+          if (t < t1) {   // the next tile's row, while this one is worked on
+            const int64_t rn = (int64_t)(t + 1) * 128 + i;
+            pw_load_row(hn, wn, Ha, w, rn, rn >= sg.y && rn < sg.z, C, pq.x, cq);
+          }
+          const int b = u & 1;
+          const uint32_t ph = (u >> 1) & 1;
+          if (!mbar_wait(&ctl->s_full[b], ph, abort_w) ||
+              !mbar_wait(&ctl->psi_empty[b], ph ^ 1, abort_w)) {
+            give_up(47);
+            ok = false;
+            break;
+          }
+          ++u;
+          tc_fence_after();
+          unsigned char* psi_hi = sm + OFF_PSI + b * PSI_BUF + (i >> 6) * PSI_KB;
+          for (int ch = half; ch < nc / 32; ch += 2) {
+            uint32_t ra[32];
+            tmem_ld32_async(tmem + lanes + TS + b * NU + ch * 32, ra);
+            tmem_wait_ld();
+            unsigned char* hi = psi_hi + ch * 32 * 128;
+            unsigned char* lo = hi + 2 * PSI_KB;
+            if (cpad == 8) pw_psi_chunk<8>(ra, wh, winv, hi, lo, off);
+            else if (cpad == 16) pw_psi_chunk<16>(ra, wh, winv, hi, lo, off);
+            else pw_psi_chunk<32>(ra, wh, winv, hi, lo, off);
+          }
+          tc_fence_before();
+          fence_async_smem();
+          __syncwarp();
+          if (lane == 0) {
+            mbar_arrive(&ctl->s_empty[b]);
+            mbar_arrive(&ctl->psi_full[b]);
+          }
+        }
+        if (!ok) break;
+        // item end: D -> the item's partial rows, [class][probe][feature]
+        const int db = item & 1;
+        if (!mbar_wait(&ctl->d_full[db], (item >> 1) & 1, abort_w)) {
+          give_up(48);
           ok = false;
           break;
         }
-        ++ns;
         tc_fence_after();
-        for (int ch = half; ch < n1 / 32; ch += 2) {
-          uint32_t ra[32];
-          tmem_ld32_async(tmem + lanes + TS + ch * 32, ra);
-          tmem_wait_ld();
-          unsigned char* hi = psi_hi0 + ch * 32 * 128;
-          unsigned char* lo = hi + 2 * PSI_KB;
-          if (cpad == 8) pw_psi_chunk<8>(ra, h, wh, hi, lo, off);
-          else if (cpad == 16) pw_psi_chunk<16>(ra, h, wh, hi, lo, off);
-          else pw_psi_chunk<32>(ra, h, wh, hi, lo, off);
+        {
+          const int jl = i / cpad, kl = i - jl * cpad;
+          const int j = grp * (NU / cpad) + jl;
+          const bool own = i < nc && kl < cq && j < s;
+          float* dst = part + ((int64_t)(sg.w + kl) * sp + j) * d;
+          constexpr int CW = DP >= 32 ? DP / 2 : 16;   // columns per half
+          if (half * CW < DP) {
+#pragma unroll
+            for (int c0 = half * CW; c0 < half * CW + CW; c0 += 16) {
+              float v[16];
+              tmem_ld16(tmem + lanes + TD + db * DP + c0, v);
+              if (own)
+#pragma unroll
+                for (int x = 0; x < 16; ++x)
+                  if (c0 + x < d) dst[c0 + x] = v[x];
+            }
+          }
         }
         tc_fence_before();
-        fence_async_smem();
         __syncwarp();
-        if (lane == 0) {
-          mbar_arrive(&ctl->s_empty);
-          mbar_arrive(&ctl->psi_full);
-        }
+        if (lane == 0) mbar_arrive(&ctl->d_empty[db]);
       }
-      if (!ok) break;
-      // segment end: D -> this segment's partial, [class][probe][feature]
-      if (!mbar_wait(&ctl->d_full, nseg_done & 1, abort_w)) {
-        give_up(48);
-        break;
-      }
-      ++nseg_done;
-      tc_fence_after();
-      const int nblk = (n1 + 127) >> 7;
-      if (half < nblk) {
-        const int R = half * 128 + i;
-        const int j = R / cpad, kl = R - j * cpad;
-        float* dst = part + ((int64_t)(sg.w + kl) * sp + j) * d;
-        const bool own = kl < cq && j < s;
-#pragma unroll
-        for (int c0 = 0; c0 < DP; c0 += 16) {
-          float v[16];
-          tmem_ld16(tmem + lanes + TD + half * DP + c0, v);
-          if (own)
-#pragma unroll
-            for (int u = 0; u < 16; ++u)
-              if (c0 + u < d) dst[c0 + u] = v[u];
-        }
-      }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&ctl->d_empty);
     }
   }
   __syncthreads();
@@ -3261,23 +3333,13 @@ static int32_t tc_apply_pw_t(firal_problem* P, const float* w, const float* V, i
   return FIRAL_OK;
 }
 
-// the probe block in groups whose (probe, class) columns fit the kernel (sp cpad <= 256):
-// every probe is independent through the apply, its combine and its projection
 static int32_t tc_apply_pw(firal_problem* P, const float* w, const float* V, int s, float* out,
                            double* pq, double lam) {
-  const int sg = pw_cfg::N1MAX / P->pw_cpad_max;   // a multiple of 8 (cpad <= 32)
-  for (int j0 = 0; j0 < s; j0 += sg) {
-    const int n = std::min(sg, s - j0);
-    const float* Vg = V + (int64_t)j0 * P->D;
-    float* og = out + (int64_t)j0 * P->D;
-    double* pg = pq ? pq + (int64_t)j0 * P->c : nullptr;
-    switch (P->dp) {
-      case 16: FIRAL_TRY(tc_apply_pw_t<16>(P, w, Vg, n, og, pg, lam)); break;
-      case 32: FIRAL_TRY(tc_apply_pw_t<32>(P, w, Vg, n, og, pg, lam)); break;
-      default: FIRAL_TRY(tc_apply_pw_t<64>(P, w, Vg, n, og, pg, lam)); break;
-    }
+  switch (P->dp) {
+    case 16: return tc_apply_pw_t<16>(P, w, V, s, out, pq, lam);
+    case 32: return tc_apply_pw_t<32>(P, w, V, s, out, pq, lam);
+    default: return tc_apply_pw_t<64>(P, w, V, s, out, pq, lam);
   }
-  return FIRAL_OK;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -3285,16 +3347,17 @@ static int32_t tc_apply_pw(firal_problem* P, const float* w, const float* V, int
 //   a_ikj = x_i . A~_j[:, k],  b_ikj = x_i . B~_j[:, k]      two MMA1s (hi + lo each) per tile
 //   q_i = sum_j [sum_k h_ik a_ikj b_ikj - (sum_k h_ik a_ikj)(sum_k h_ik b_ikj)]
 // with A~, B~ the probe blocks minus their pool class means (H_i vanishes on those means).
-// Only the pool rows' segments run.  The two epilogue halves of a row meet in shared memory
-// (an mbarrier hand-off), and a later probe group adds to the earlier groups' values, so g is
-// written in a fixed order.
+// Only the pool rows' segments run.  Same pipeline as the apply (double-buffered x tile and
+// S_A, S_B accumulators, h loaded a tile ahead).  The two epilogue halves of a row meet in
+// shared memory (an mbarrier hand-off); the first probe group writes g and later groups add
+// to it, all from the same thread, so g is written in a fixed order.
 // ------------------------------------------------------------------------------------------
 namespace pwq_cfg {
 constexpr int PT_HALF = pw_cfg::PT_HALF;
 constexpr int OFF_PA = 0, OFF_PB = 2 * PT_HALF, OFF_XA = 4 * PT_HALF;
-constexpr int OFF_RED = OFF_XA + pw_cfg::XA_BYTES, OFF_CTL = OFF_RED + 1024;
+constexpr int OFF_RED = OFF_XA + 2 * pw_cfg::XA_BYTES, OFF_CTL = OFF_RED + 1024;
 constexpr int SMEM = OFF_CTL + 256 + 1024;
-constexpr uint32_t TA = 0, TB = 256;              // TMEM columns: S_A | S_B
+// TMEM columns: S_A of buffer b at 256 b, S_B at 256 b + 128
 }  // namespace pwq_cfg
 
 template <int CPAD>
@@ -3323,22 +3386,25 @@ __global__ void __launch_bounds__(384, 1)
              const __grid_constant__ CUtensorMap mapPB, const float* __restrict__ Ha,
              float* __restrict__ g, const int4* __restrict__ pool_tab,
              const int4* __restrict__ seg_tab, int nseg, int C, int sp, int64_t m, float gscale,
-             int accumulate, int32_t* err) {
+             int32_t* err) {
   using namespace pwq_cfg;
+  using pw_cfg::NU;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   PwCtl* ctl = (PwCtl*)(sm + OFF_CTL);
   float* red = (float*)(sm + OFF_RED);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    mbar_init(&ctl->x_full, 1);
-    mbar_init(&ctl->x_empty, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&ctl->x_full[b], 1);
+      mbar_init(&ctl->x_empty[b], 1);
+      mbar_init(&ctl->s_full[b], 1);
+      mbar_init(&ctl->s_empty[b], 8);
+    }
+    mbar_init(&ctl->psi_full[0], 4);    // here: half 1's shares of the tile's rows are in red
+    mbar_init(&ctl->psi_empty[0], 4);   // here: half 0 has read them
     mbar_init(&ctl->pt_full, 1);
     mbar_init(&ctl->pt_empty, 1);
-    mbar_init(&ctl->s_full, 1);
-    mbar_init(&ctl->s_empty, 8);
-    mbar_init(&ctl->psi_full, 4);    // here: half 1's shares of the tile's rows are in red
-    mbar_init(&ctl->psi_empty, 4);   // here: half 0 has read them
     mbar_init(&ctl->drain, 1);
     ctl->abort_w = 0;
     mbar_fence_init();
@@ -3363,63 +3429,78 @@ __global__ void __launch_bounds__(384, 1)
     tma_prefetch(&mapX);
     tma_prefetch(&mapPA);
     tma_prefetch(&mapPB);
-    uint32_t nx = 0, npt = 0;
+    uint32_t nt = 0, ni = 0;
     bool ok = true;
     for (int gi = blockIdx.x; gi < nseg && ok && !*abort_w; gi += gridDim.x) {
       const int4 sg = seg_tab[gi];
       if (skip(sg)) continue;
       const int4 pq = pool_tab[sg.x];
-      const int n1 = pq.z * sp;
-      const int pbase = 2 * sp * pq.w;
-      if (!mbar_wait(&ctl->pt_empty, (npt & 1) ^ 1, abort_w)) { give_up(51); break; }
-      mbar_expect_tx(&ctl->pt_full, 4 * n1 * 128);
-      for (int part = 0; part < 2; ++part)
-        for (int r = 0; r < n1; r += 64) {
-          tma_load_2d(sm + OFF_PA + part * PT_HALF + r * 128, &mapPA, &ctl->pt_full, 0,
-                      pbase + part * n1 + r);
-          tma_load_2d(sm + OFF_PB + part * PT_HALF + r * 128, &mapPB, &ctl->pt_full, 0,
-                      pbase + part * n1 + r);
+      const int n1 = pq.z * sp, pbase = 2 * sp * pq.w;
+      const int ng = pw_ngrp(pq.z, sp);
+      for (int grp = 0; grp < ng && ok; ++grp) {
+        const int nc = pw_ncols(pq.z, sp, grp);
+        if (!mbar_wait(&ctl->pt_empty, (ni & 1) ^ 1, abort_w)) { give_up(51); ok = false; break; }
+        mbar_expect_tx(&ctl->pt_full, 4 * nc * 128);
+        for (int part = 0; part < 2; ++part)
+          for (int r = 0; r < nc; r += 64) {
+            const int y = pbase + part * n1 + grp * NU + r;
+            tma_load_2d(sm + OFF_PA + part * PT_HALF + r * 128, &mapPA, &ctl->pt_full, 0, y);
+            tma_load_2d(sm + OFF_PB + part * PT_HALF + r * 128, &mapPB, &ctl->pt_full, 0, y);
+          }
+        ++ni;
+        for (int t = sg.y >> 7; t <= (sg.z - 1) >> 7; ++t) {
+          const int b = nt & 1;
+          if (!mbar_wait(&ctl->x_empty[b], ((nt >> 1) & 1) ^ 1, abort_w)) {
+            give_up(52);
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&ctl->x_full[b], pw_cfg::XA_BYTES);
+          tma_load_2d(sm + OFF_XA + b * pw_cfg::XA_BYTES, &mapX, &ctl->x_full[b], 0, t * 128);
+          ++nt;
         }
-      ++npt;
-      for (int t = sg.y >> 7; t <= (sg.z - 1) >> 7; ++t) {
-        if (!mbar_wait(&ctl->x_empty, (nx & 1) ^ 1, abort_w)) { give_up(52); ok = false; break; }
-        mbar_expect_tx(&ctl->x_full, pw_cfg::XA_BYTES);
-        tma_load_2d(sm + OFF_XA, &mapX, &ctl->x_full, 0, t * 128);
-        ++nx;
       }
     }
-    if (nx) mbar_wait_drain(&ctl->x_full, (nx - 1) & 1);
-    if (npt) mbar_wait_drain(&ctl->pt_full, (npt - 1) & 1);
+    for (int b = 0; b < 2; ++b) {
+      const uint32_t cnt = (nt + 1 - b) / 2;
+      if (cnt) mbar_wait_drain(&ctl->x_full[b], (cnt - 1) & 1);
+    }
+    if (ni) mbar_wait_drain(&ctl->pt_full, (ni - 1) & 1);
   } else if (warp == 1 && lane == 0) {
-    uint32_t nx = 0, npt = 0, ns = 0;
+    uint32_t nt = 0, ni = 0;
     bool ok = true;
     for (int gi = blockIdx.x; gi < nseg && ok && !*abort_w; gi += gridDim.x) {
       const int4 sg = seg_tab[gi];
       if (skip(sg)) continue;
       const int4 pq = pool_tab[sg.x];
-      const uint32_t idesc1 = idesc_bf16_f32(128, pq.z * sp);
-      if (!mbar_wait(&ctl->pt_full, npt & 1, abort_w)) { give_up(53); break; }
-      ++npt;
+      const int ng = pw_ngrp(pq.z, sp);
       const int t0 = sg.y >> 7, t1 = (sg.z - 1) >> 7;
-      for (int t = t0; t <= t1; ++t) {
-        if (!mbar_wait(&ctl->x_full, nx & 1, abort_w) ||
-            !mbar_wait(&ctl->s_empty, (ns & 1) ^ 1, abort_w)) { give_up(54); ok = false; break; }
-        tc_fence_after();
-        const uint32_t xa = smem_u32(sm + OFF_XA), pa = smem_u32(sm + OFF_PA),
-                       pb = smem_u32(sm + OFF_PB);
+      for (int grp = 0; grp < ng && ok; ++grp) {
+        const uint32_t idesc1 = idesc_bf16_f32(128, pw_ncols(pq.z, sp, grp));
+        if (!mbar_wait(&ctl->pt_full, ni & 1, abort_w)) { give_up(53); ok = false; break; }
+        ++ni;
+        for (int t = t0; t <= t1; ++t) {
+          const int b = nt & 1;
+          const uint32_t ph = (nt >> 1) & 1;
+          if (!mbar_wait(&ctl->x_full[b], ph, abort_w) ||
+              !mbar_wait(&ctl->s_empty[b], ph ^ 1, abort_w)) { give_up(54); ok = false; break; }
+          tc_fence_after();
+          const uint32_t xa = smem_u32(sm + OFF_XA + b * pw_cfg::XA_BYTES),
+                         pa = smem_u32(sm + OFF_PA), pb = smem_u32(sm + OFF_PB);
+          const uint32_t ta = tmem + 256 * b, tb = ta + 128;
 #pragma unroll
-        for (int k = 0; k < DP / 16; ++k) {
-          const uint64_t ad = sdesc_sw128(xa + k * 32);
-          umma_bf16(tmem + TA, ad, sdesc_sw128(pa + k * 32), idesc1, k > 0 ? 1u : 0u);
-          umma_bf16(tmem + TA, ad, sdesc_sw128(pa + PT_HALF + k * 32), idesc1, 1u);
-          umma_bf16(tmem + TB, ad, sdesc_sw128(pb + k * 32), idesc1, k > 0 ? 1u : 0u);
-          umma_bf16(tmem + TB, ad, sdesc_sw128(pb + PT_HALF + k * 32), idesc1, 1u);
+          for (int k = 0; k < DP / 16; ++k) {
+            const uint64_t ad = sdesc_sw128(xa + k * 32);
+            umma_bf16(ta, ad, sdesc_sw128(pa + k * 32), idesc1, k > 0 ? 1u : 0u);
+            umma_bf16(ta, ad, sdesc_sw128(pa + PT_HALF + k * 32), idesc1, 1u);
+            umma_bf16(tb, ad, sdesc_sw128(pb + k * 32), idesc1, k > 0 ? 1u : 0u);
+            umma_bf16(tb, ad, sdesc_sw128(pb + PT_HALF + k * 32), idesc1, 1u);
+          }
+          umma_commit(&ctl->s_full[b]);
+          umma_commit(&ctl->x_empty[b]);
+          if (t == t1) umma_commit(&ctl->pt_empty);
+          ++nt;
         }
-        umma_commit(&ctl->s_full);
-        umma_commit(&ctl->x_empty);
-        ++nx;
-        ++ns;
-        if (t == t1) umma_commit(&ctl->pt_empty);
       }
     }
     umma_commit(&ctl->drain);
@@ -3428,65 +3509,82 @@ __global__ void __launch_bounds__(384, 1)
     const int quad = warp & 3, half = (warp - 4) >> 2;
     const int i = quad * 32 + lane;
     const uint32_t lanes = (uint32_t)(quad * 32) << 16;
-    uint32_t ns = 0, nr = 0;
+    uint32_t nt = 0, nr = 0;
     bool ok = true;
     for (int gi = blockIdx.x; gi < nseg && ok && !*abort_w; gi += gridDim.x) {
       const int4 sg = seg_tab[gi];
       if (skip(sg)) continue;
       const int4 pq = pool_tab[sg.x];
       const int cpad = pq.z, cq = pq.y;
-      const int n1 = cpad * sp;
+      const int ng = pw_ngrp(cpad, sp);
       const int t0 = sg.y >> 7, t1 = (sg.z - 1) >> 7;
-      for (int t = t0; t <= t1; ++t) {
-        const int64_t row = (int64_t)t * 128 + i;
-        const bool valid = row >= sg.y && row < sg.z && row >= m;
-        float h[32];
+      for (int grp = 0; grp < ng && ok; ++grp) {
+        const int nc = pw_ncols(cpad, sp, grp);
+        float hn[32];
+        {
+          const int64_t row = (int64_t)t0 * 128 + i;
+          const bool v0 = row >= sg.y && row < sg.z && row >= m;
 #pragma unroll
-        for (int k = 0; k < 32; ++k) h[k] = (valid && k < cq) ? Ha[row * C + pq.x + k] : 0.0f;
-        if (!mbar_wait(&ctl->s_full, ns & 1, abort_w)) {
-          give_up(55);
-          ok = false;
-          break;
+          for (int k = 0; k < 32; ++k) hn[k] = (v0 && k < cq) ? Ha[row * C + pq.x + k] : 0.0f;
         }
-        ++ns;
-        tc_fence_after();
-        float q = 0.0f;
-        for (int ch = half; ch < n1 / 32; ch += 2) {
-          uint32_t ra[32], rb[32];
-          tmem_ld32_async(tmem + lanes + TA + ch * 32, ra);
-          tmem_ld32_async(tmem + lanes + TB + ch * 32, rb);
-          tmem_wait_ld();
-          if (cpad == 8) q += pw_quad_chunk<8>(ra, rb, h);
-          else if (cpad == 16) q += pw_quad_chunk<16>(ra, rb, h);
-          else q += pw_quad_chunk<32>(ra, rb, h);
-        }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&ctl->s_empty);
-        // the two halves of the row: half 1 leaves its share, half 0 writes the sum
-        if (half == 1) {
-          if (!mbar_wait(&ctl->psi_empty, (nr & 1) ^ 1, abort_w)) {
-            give_up(56);
+        for (int t = t0; t <= t1; ++t) {
+          const int64_t row = (int64_t)t * 128 + i;
+          const bool valid = row >= sg.y && row < sg.z && row >= m;
+          float h[32];
+#pragma unroll
+          for (int k = 0; k < 32; ++k) h[k] = hn[k];
+          if (t < t1) {   // the next tile's row, while this one is worked on
+            const int64_t rn = row + 128;
+            const bool vn = rn >= sg.y && rn < sg.z && rn >= m;
+#pragma unroll
+            for (int k = 0; k < 32; ++k) hn[k] = (vn && k < cq) ? Ha[rn * C + pq.x + k] : 0.0f;
+          }
+          const int b = nt & 1;
+          if (!mbar_wait(&ctl->s_full[b], (nt >> 1) & 1, abort_w)) {
+            give_up(55);
             ok = false;
             break;
           }
-          red[i] = q;
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&ctl->psi_full);
-        } else {
-          if (!mbar_wait(&ctl->psi_full, nr & 1, abort_w)) {
-            give_up(57);
-            ok = false;
-            break;
+          ++nt;
+          tc_fence_after();
+          float q = 0.0f;
+          for (int ch = half; ch < nc / 32; ch += 2) {
+            uint32_t ra[32], rb[32];
+            tmem_ld32_async(tmem + lanes + 256 * b + ch * 32, ra);
+            tmem_ld32_async(tmem + lanes + 256 * b + 128 + ch * 32, rb);
+            tmem_wait_ld();
+            if (cpad == 8) q += pw_quad_chunk<8>(ra, rb, h);
+            else if (cpad == 16) q += pw_quad_chunk<16>(ra, rb, h);
+            else q += pw_quad_chunk<32>(ra, rb, h);
           }
-          if (valid) {
-            const float v = -gscale * (q + red[i]);
-            g[row - m] = accumulate ? g[row - m] + v : v;
-          }
+          tc_fence_before();
           __syncwarp();
-          if (lane == 0) mbar_arrive(&ctl->psi_empty);
+          if (lane == 0) mbar_arrive(&ctl->s_empty[b]);
+          // the two halves of the row: half 1 leaves its share, half 0 writes the sum
+          if (half == 1) {
+            if (!mbar_wait(&ctl->psi_empty[0], (nr & 1) ^ 1, abort_w)) {
+              give_up(56);
+              ok = false;
+              break;
+            }
+            red[i] = q;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ctl->psi_full[0]);
+          } else {
+            if (!mbar_wait(&ctl->psi_full[0], nr & 1, abort_w)) {
+              give_up(57);
+              ok = false;
+              break;
+            }
+            if (valid) {
+              const float v = -gscale * (q + red[i]);
+              g[row - m] = grp > 0 ? g[row - m] + v : v;
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ctl->psi_empty[0]);
+          }
+          ++nr;
         }
-        ++nr;
       }
     }
   }
@@ -3505,13 +3603,22 @@ static int32_t tc_quad_pw_t(firal_problem* P, const float* A, const float* B, in
   cudaStream_t st = P->H->stream;
   const int c = P->c, d = P->d;
   const int Qe = pool_count(P->pt);
+  const int sp = (s + 7) / 8 * 8;
   FIRAL_TRY(P->vmean.ensure((size_t)2 * s * Qe * d * sizeof(float)));
   float* meanA = P->vmean.as<float>();
   float* meanB = meanA + (size_t)s * Qe * d;
+  const int64_t prows = 2LL * sp * P->pw_cpad_total;
+  FIRAL_TRY(P->pw_pk.ensure((size_t)2 * prows * 64 * 2));
+  bf16* pkA = P->pw_pk.as<bf16>();
+  bf16* pkB = pkA + prows * 64;
   ProfScope ps(st, PF_QUAD);
-  count_launch(2);
+  count_launch(5);
   k_class_mean<<<s * Qe, 1024, 0, st>>>(A, s, c, d, P->D, meanA, P->pt);
   k_class_mean<<<s * Qe, 1024, 0, st>>>(B, s, c, d, P->D, meanB, P->pt);
+  k_pw_pack<<<dim3((unsigned)Qe, (unsigned)sp), 256, 0, st>>>(pkA, A, meanA, P->pw_pool.as<int4>(),
+                                                               s, sp, d, P->D, Qe);
+  k_pw_pack<<<dim3((unsigned)Qe, (unsigned)sp), 256, 0, st>>>(pkB, B, meanB, P->pw_pool.as<int4>(),
+                                                               s, sp, d, P->D, Qe);
   FIRAL_CUDA_TRY(cudaGetLastError());
   static bool attr[3] = {false, false, false};
   const int ai = DP == 16 ? 0 : DP == 32 ? 1 : 2;
@@ -3520,33 +3627,14 @@ static int32_t tc_quad_pw_t(firal_problem* P, const float* A, const float* B, in
                                         SMEM));
     attr[ai] = true;
   }
-  const int64_t Np = P->Np;
-  CUtensorMap mX;
-  FIRAL_TRY(make_map(&mX, DP < 64 ? P->X64.p : P->Xb.p, Np, 64, 128, 64, true));
-  // probe groups whose columns fit (sp cpad <= 256); each group adds to the previous ones
-  const int sg = pw_cfg::N1MAX / P->pw_cpad_max;
-  for (int j0 = 0; j0 < s; j0 += sg) {
-    const int n = std::min(sg, s - j0), sp = (n + 7) / 8 * 8;
-    const int64_t prows = 2LL * sp * P->pw_cpad_total;
-    FIRAL_TRY(P->pw_pk.ensure((size_t)2 * prows * 64 * 2));
-    bf16* pkA = P->pw_pk.as<bf16>();
-    bf16* pkB = pkA + prows * 64;
-    count_launch(3);
-    k_pw_pack<<<dim3((unsigned)Qe, (unsigned)sp), 256, 0, st>>>(
-        pkA, A + (int64_t)j0 * P->D, meanA + (size_t)j0 * Qe * d, P->pw_pool.as<int4>(), n, sp, d,
-        P->D, Qe);
-    k_pw_pack<<<dim3((unsigned)Qe, (unsigned)sp), 256, 0, st>>>(
-        pkB, B + (int64_t)j0 * P->D, meanB + (size_t)j0 * Qe * d, P->pw_pool.as<int4>(), n, sp, d,
-        P->D, Qe);
-    FIRAL_CUDA_TRY(cudaGetLastError());
-    CUtensorMap mA, mB;
-    FIRAL_TRY(make_map(&mA, pkA, prows, 64, 64, 64, true));
-    FIRAL_TRY(make_map(&mB, pkB, prows, 64, 64, 64, true));
-    k_tc_pwq<DP><<<std::min(P->pw_nseg, P->sms), 384, SMEM, st>>>(
-        mX, mA, mB, P->Ha.as<float>(), g, P->pw_pool.as<int4>(), P->pw_seg.as<int4>(),
-        P->pw_nseg, c, sp, P->m, (float)(scale / s), j0 > 0 ? 1 : 0, tc_error_word(P));
-    FIRAL_CUDA_TRY(cudaGetLastError());
-  }
+  CUtensorMap mX, mA, mB;
+  FIRAL_TRY(make_map(&mX, DP < 64 ? P->X64.p : P->Xb.p, P->Np, 64, 128, 64, true));
+  FIRAL_TRY(make_map(&mA, pkA, prows, 64, 64, 64, true));
+  FIRAL_TRY(make_map(&mB, pkB, prows, 64, 64, 64, true));
+  k_tc_pwq<DP><<<std::min(P->pw_nseg, P->sms), 384, SMEM, st>>>(
+      mX, mA, mB, P->Ha.as<float>(), g, P->pw_pool.as<int4>(), P->pw_seg.as<int4>(), P->pw_nseg,
+      c, sp, P->m, (float)(scale / s), tc_error_word(P));
+  FIRAL_CUDA_TRY(cudaGetLastError());
   return FIRAL_OK;
 }
 
