@@ -717,7 +717,8 @@ def run_ours(args):
                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": dram_traffic(top, n_pad, args.precision) if tensor else None,
                 "executed_tflops": execd,
-                "peak_source": (f"{pk_src} bf16 sustained (of measured)" if tensor else
+                "peak_source": (("measured bf16 sustained (of measured)" if pk_src == "measured"
+                                 else "fallback bf16 sustained (of fallback)") if tensor else
                                 "derived FP32 FMA peak: 152 SMs x 128 lanes x 2 x 2.07 GHz")}
         if tensor:
             roof["frac_of_burst"] = achieved / pk["bf16_tflops"]

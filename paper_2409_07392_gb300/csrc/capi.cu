@@ -1326,9 +1326,13 @@ int32_t firal_problem_destroy(firal_problem* P) {
                   &P->cen_idx, &P->Ub, &P->UbT, &P->cen_am, &P->cen_rho, &P->cen_lab, &P->cen_items, &P->cen_part,
                   &P->pool_tabs, &P->pool_z, &P->md_part, &P->kr_alpha, &P->kr_dterm,
                   &P->kr_bsum, &P->bcg, &P->pw_pool, &P->pw_seg, &P->pw_pseg, &P->pw_pk,
-                  &P->pw_part, &P->X64}) {
+                  &P->pw_part, &P->X64, &P->S_lab, &P->w_lab}) {
     if (synced) b->park();
     else b->release();
+  }
+  for (auto& sc : P->pw_sched) {
+    if (synced) sc.buf.park();
+    else sc.buf.release();
   }
   delete P;
   return FIRAL_OK;

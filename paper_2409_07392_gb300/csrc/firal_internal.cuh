@@ -223,6 +223,20 @@ struct firal_problem {
   int pw_cpad_max = 0, pw_nseg = 0;
   int64_t pw_cpad_total = 0, pw_segcls_total = 0;
   firal::DBuf pw_pool, pw_seg, pw_pseg, pw_pk, pw_part, X64;
+  // host copies of the pool table and segments; per (padded probe count, apply or gradient):
+  // the CTAs' segment lists (offsets per CTA, then segment indices), longest first
+  std::vector<int4> pw_pool_h, pw_seg_h;
+  struct PwSched {
+    int sp = 0;
+    bool quad = false;
+    int grid = 0;
+    firal::DBuf buf;
+  };
+  std::vector<PwSched> pw_sched;
+  // fast mixed mode: the labelled rows' diagonal-part block sums (weight 1 in every Sigma_z,
+  // so computed once, as three bf16 products) and their weights (1 on those rows, 0 after)
+  firal::DBuf S_lab, w_lab;
+  bool slab_ready = false;
   int rtab_d = -1, rtab_chunks = 0;
   int32_t dp = 0, cp = 0;
   int64_t Np = 0;
@@ -256,7 +270,8 @@ int32_t set_step(int64_t* t_dev, int64_t v, cudaStream_t st);
 int32_t syrk_blocks(firal_problem* P, const void* w, double lamS, void* outS, double lamP,
                     double* outP);
 int32_t syrk_reduce_f32(firal_problem* P, const float* partS, const float* partP, int splits,
-                        double lamS, float* outS, double lamP, double* outP);
+                        double lamS, float* outS, double lamP, double* outP,
+                        const float* addS = nullptr);
 int32_t hessian_apply_simt(firal_problem* P, const void* w, const void* Sblk, const void* V,
                            int s, void* out, double* pq);
 int32_t combine_f32(firal_problem* P, const float* Sblk, const float* V, int splits, int s,

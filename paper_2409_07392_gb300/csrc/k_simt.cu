@@ -327,10 +327,10 @@ __global__ __launch_bounds__(256) void k_syrk(const T* __restrict__ Xa, const T*
 // out[k][e][f] = sum_split part[split][k][e][f] (+ lam on the diagonal), as double and/or T
 template <class T>
 __global__ void k_syrk_reduce(const T* part, int splits, int64_t per, int d, double lam,
-                              double* out_d, T* out_t) {
+                              double* out_d, T* out_t, const T* add = nullptr) {
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < per;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    double acc = 0.0;
+    double acc = add ? (double)add[idx] : 0.0;
 #pragma unroll 8
     for (int sp = 0; sp < splits; ++sp) acc += (double)part[(int64_t)sp * per + idx];
     const int64_t ef = idx % ((int64_t)d * d);
@@ -386,13 +386,14 @@ static int32_t syrk_t(firal_problem* P, const T* w, double lamS, T* outS, double
 }
 
 int32_t syrk_reduce_f32(firal_problem* P, const float* partS, const float* partP, int splits,
-                        double lamS, float* outS, double lamP, double* outP) {
+                        double lamS, float* outS, double lamP, double* outP, const float* addS) {
   cudaStream_t st = P->H->stream;
   const int64_t per = (int64_t)P->c * P->d * P->d;
   const int g = grid_for(per, 256, 4096);
   ProfScope ps(st, PF_SYRK);
   count_launch((outS ? 1 : 0) + (outP ? 1 : 0));
-  if (outS) k_syrk_reduce<float><<<g, 256, 0, st>>>(partS, splits, per, P->d, lamS, nullptr, outS);
+  if (outS)
+    k_syrk_reduce<float><<<g, 256, 0, st>>>(partS, splits, per, P->d, lamS, nullptr, outS, addS);
   if (outP) k_syrk_reduce<float><<<g, 256, 0, st>>>(partP, splits, per, P->d, lamP, outP, nullptr);
   FIRAL_CUDA_TRY(cudaGetLastError());
   return FIRAL_OK;

@@ -21,6 +21,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <climits>
 #include <mutex>
 #include <vector>
@@ -1359,6 +1360,9 @@ __global__ void __launch_bounds__(256, 1)
 // significant bits).  Both block sums are then plain TMA-fed GEMMs over the points:
 //   MODE 0:  S ~ A_hi Z_hi + A_lo Z_hi + A_hi Z_lo      (relative error ~2^-16)
 //   MODE 1:  P ~ A_P Z_hi                               (preconditioner only)
+//   MODE 2:  S ~ A_hi Z_hi + A_hi Z_lo                  (fast mode, pool rows: the weights'
+//            bf16 roundings are unbiased and average over the points; the pair operand
+//            stays exact)
 // Unit = (128 classes, 128 pairs, point range).
 //
 // Accumulation length.  The tensor core adds each product block into its f32 accumulator with
@@ -1379,9 +1383,10 @@ constexpr int SUB = 8;              // K-steps per short accumulation of S
 constexpr uint32_t COL_LONG = 256;
 constexpr int64_t UNIT_KB = 1024;   // K-steps per unit at most
 template <int MODE> struct Cfg {
-  static constexpr int NTILE = MODE == 0 ? 4 : 2;   // A_hi A_lo Z_hi Z_lo | A_P Z_hi
+  // A_hi A_lo Z_hi Z_lo | A_P Z_hi | A_hi Z_hi Z_lo
+  static constexpr int NTILE = MODE == 0 ? 4 : MODE == 2 ? 3 : 2;
   static constexpr int STAGE = NTILE * TILE;
-  static constexpr int STAGES = MODE == 0 ? 3 : 6;
+  static constexpr int STAGES = MODE == 0 ? 3 : MODE == 2 ? 4 : 6;
   static constexpr int64_t SUBK = SUB;
   static constexpr int SMEM = STAGES * STAGE + 1024 + 256;
 };
@@ -1467,6 +1472,7 @@ __global__ void __launch_bounds__(256, 1)
       tma_prefetch(&mapA1);
       tma_prefetch(&mapZ1);
     }
+    if (MODE == 2) tma_prefetch(&mapZ1);
     int stage = 0;
     uint32_t phase = 0;
     bool ok = true;
@@ -1489,6 +1495,9 @@ __global__ void __launch_bounds__(256, 1)
           tma_load_2d(st + TILE, &mapA1, &ctl->full[stage], 0, ya);
           tma_load_2d(st + 2 * TILE, &mapZ0, &ctl->full[stage], 0, yz);
           tma_load_2d(st + 3 * TILE, &mapZ1, &ctl->full[stage], 0, yz);
+        } else if (MODE == 2) {
+          tma_load_2d(st + TILE, &mapZ0, &ctl->full[stage], 0, yz);
+          tma_load_2d(st + 2 * TILE, &mapZ1, &ctl->full[stage], 0, yz);
         } else {
           tma_load_2d(st + TILE, &mapZ0, &ctl->full[stage], 0, yz);
         }
@@ -1544,6 +1553,10 @@ __global__ void __launch_bounds__(256, 1)
               umma_bf16(tS, ah, zh, idesc, acc);
               umma_bf16(tS, sdesc_sw128(a0 + TILE + k * 32), zh, idesc, 1u);
               umma_bf16(tS, ah, sdesc_sw128(a0 + 3 * TILE + k * 32), idesc, 1u);
+            } else if (MODE == 2) {
+              const uint64_t ah = sdesc_sw128(a0 + k * 32);
+              umma_bf16(tS, ah, sdesc_sw128(a0 + TILE + k * 32), idesc, acc);
+              umma_bf16(tS, ah, sdesc_sw128(a0 + 2 * TILE + k * 32), idesc, 1u);
             } else {
               umma_bf16(tS, sdesc_sw128(a0 + k * 32), sdesc_sw128(a0 + TILE + k * 32), idesc,
                         acc);
@@ -1676,7 +1689,7 @@ __global__ void k_build_z(bf16* Zhi, bf16* Zlo, const bf16* Xb, int d, int dp, i
 // Class operands of the block sums, zero-padded, in the K-block-major layout
 // [i / 64][k][i % 64] with cpb rows per block:
 //   A_hi = bf16(w u), A_lo = bf16(w u - A_hi), A_P = bf16(w h (1 - h))
-// (A_hi and A_lo only if Ahi, A_P only if AP)
+// (A_hi only if Ahi, A_lo only if Ahi and Alo, A_P only if AP)
 // with u = h, or u = h - e_m on centred rows (cen, may be NULL); rows below wskip take weight
 // 0 in A_hi and A_lo (their part of the Hessian apply runs on CUDA cores).
 // Block = one 64-point block x 32 classes; each warp store writes one 128-byte row run.
@@ -1720,9 +1733,11 @@ __global__ void k_weighted_hT(bf16* Ahi, bf16* Alo, bf16* AP, const float* Ha, c
     const int64_t o = ((int64_t)blockIdx.x * cpb + col) * 64 + t2;
     if (Ahi) {
       const __nv_bfloat162 hi = __floats2bfloat162_rn(v0, v1);
-      const float2 fh = __bfloat1622float2(hi);
       *reinterpret_cast<__nv_bfloat162*>(Ahi + o) = hi;
-      *reinterpret_cast<__nv_bfloat162*>(Alo + o) = __floats2bfloat162_rn(v0 - fh.x, v1 - fh.y);
+      if (Alo) {
+        const float2 fh = __bfloat1622float2(hi);
+        *reinterpret_cast<__nv_bfloat162*>(Alo + o) = __floats2bfloat162_rn(v0 - fh.x, v1 - fh.y);
+      }
     }
     if (AP)
       *reinterpret_cast<__nv_bfloat162*>(AP + o) =
@@ -2394,12 +2409,67 @@ static int32_t tc_bsum_launch_attrs() {
                                         b_cfg::Cfg<0>::SMEM));
     FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tc_bsum<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         b_cfg::Cfg<1>::SMEM));
+    FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tc_bsum<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        b_cfg::Cfg<2>::SMEM));
     done = true;
   }
   return FIRAL_OK;
 }
 
 // S (and P if outP) = weighted block sums of the problem's rows with weights w (f32, N).
+// The fast mode's bf16 rounding (2^-9 per entry) of the CG direction in the low-rank term and
+// of the diagonal-part block sums: kept only while the rows' mean low-rank share (sum_k h_ik^2
+// on plain rows, 1 on centred ones: about e / c for flat softmax rows) is at most 0.1;
+// otherwise the problem takes the hi + lo forms of the mixed mode.
+static bool fast_rounding(const firal_problem* P) {
+  return P->prec == FIRAL_MIXED_BF16_FAST && P->lowrank_share <= 0.1;
+}
+
+// The labelled rows' diagonal-part block sums S_lab[k] = sum_{i < m} h_ik x_i x_i^T (their
+// weight is 1 in every Sigma_z): three products over their K-steps only, once per problem.
+// The fast mode's two-product sums leave these rows out: a few rows of weight 1 carry as much
+// of S as the whole pool, and their weights' bf16 roundings would not average out.
+static int32_t tc_labelled_blocks(firal_problem* P) {
+  using namespace b_cfg;
+  cudaStream_t st = P->H->stream;
+  const int64_t Np = P->Np, m = P->m;
+  const int cp = P->cp, c = P->c, d = P->d;
+  const int npairs = d * (d + 1) / 2;
+  const int64_t npp = (npairs + BN - 1) / BN * BN;
+  const int n_mt = (cp + BM - 1) / BM, n_nt = (int)(npp / BN);
+  const int cpb = n_mt * BM;
+  const int64_t asz = (int64_t)cpb * Np, kb_total = Np / BK, kbm = (m + BK - 1) / BK;
+  const int64_t per = (int64_t)c * d * d;
+  FIRAL_TRY(P->S_lab.ensure((size_t)per * sizeof(float)));
+  FIRAL_TRY(P->w_lab.ensure((size_t)P->N * sizeof(float)));
+  FIRAL_TRY(fill_weights(false, P->w_lab.p, m, 1.0, nullptr, 0.0, P->n, st));
+  FIRAL_TRY(P->syrk_part.ensure((size_t)per * sizeof(float)));
+  FIRAL_TRY(P->Aw.ensure((size_t)3 * asz * 2));
+  bf16* Ahi = P->Aw.as<bf16>();
+  bf16* Alo = Ahi + asz;
+  FIRAL_TRY(tc_bsum_launch_attrs());
+  ProfScope ps(st, PF_SYRK);
+  count_launch(2);
+  k_weighted_hT<<<dim3((unsigned)kbm, (unsigned)(cpb / 32)), dim3(32, 8), 0, st>>>(
+      Ahi, Alo, nullptr, P->Ha.as<float>(), P->w_lab.as<float>(), P->N, c, Np, cpb, nullptr, 0);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  CUtensorMap mA0, mA1, mZ0, mZ1;
+  const uint64_t arows = (uint64_t)kb_total * cpb, zrows = (uint64_t)kb_total * npp;
+  FIRAL_TRY(make_map(&mA0, Ahi, arows, BK, BM, BK, true));
+  FIRAL_TRY(make_map(&mA1, Alo, arows, BK, BM, BK, true));
+  FIRAL_TRY(make_map(&mZ0, P->Zp.p, zrows, BK, BN, BK, true));
+  FIRAL_TRY(make_map(&mZ1, P->Zp.as<bf16>() + npp * Np, zrows, BK, BN, BK, true));
+  const int tiles = n_mt * n_nt;
+  k_tc_bsum<0><<<std::min(tiles, P->sms), 256, Cfg<0>::SMEM, st>>>(
+      mA0, mA1, mZ0, mZ1, P->syrk_part.as<float>(), c, d, npairs, n_mt, n_nt, 1, kbm, kbm,
+      tc_error_word(P), nullptr, 0);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  FIRAL_TRY(syrk_reduce_f32(P, P->syrk_part.as<float>(), nullptr, 1, 0.0, P->S_lab.as<float>(),
+                            0.0, nullptr));
+  P->slab_ready = true;
+  return FIRAL_OK;
+}
+
 int32_t tc_syrk_blocks(firal_problem* P, const void* wv, double lamS, void* outS, double lamP,
                        double* outP) {
   using namespace b_cfg;
@@ -2453,10 +2523,20 @@ int32_t tc_syrk_blocks(firal_problem* P, const void* wv, double lamS, void* outS
   const int units = tiles * splits;
   {
     ProfScope ps(st, PF_SYRK);
+    // S as two products (A_hi against the exact pairs Z_hi + Z_lo) in the fast mode, for the
+    // Relax operators' weights: the pool rows' bf16 weight roundings (2^-9) average over each
+    // class's points like those of the fast CG direction.  The labelled rows (weight 1 in
+    // Sigma_z, 0 in H_p) enter Sigma_z's S through S_lab (three products, once per problem)
+    // unless the apply already runs them on CUDA cores (lab_rows).
+    const bool sig = w == P->w_sig.as<float>();
+    const bool s1 = fast_rounding(P) && !P->pt.Q && (sig || w == P->w_p.as<float>());
+    const bool lab_sep = s1 && outS && sig && P->m > 0 && lab_rows(P) == 0;
+    if (lab_sep && !P->slab_ready) FIRAL_TRY(tc_labelled_blocks(P));
     count_launch(1 + (outS ? 1 : 0) + (outP ? 1 : 0));
     k_weighted_hT<<<dim3((unsigned)(Np / 64), (unsigned)(cpb / 32)), dim3(32, 8), 0, st>>>(
-        outS ? Ahi : nullptr, Alo, outP ? AP : nullptr, P->Ha.as<float>(), w, P->N, c, Np, cpb,
-        P->n_cen > 0 ? P->cen.as<int>() : nullptr, lab_rows(P),
+        outS ? Ahi : nullptr, s1 ? nullptr : Alo, outP ? AP : nullptr, P->Ha.as<float>(), w,
+        P->N, c, Np, cpb,
+        P->n_cen > 0 ? P->cen.as<int>() : nullptr, lab_sep ? P->m : lab_rows(P),
         P->pt.Q ? P->kr_bsum.as<int4>() : nullptr, P->kbL);
     FIRAL_CUDA_TRY(cudaGetLastError());
     // blocked operands as 2-D tensors of 64-point rows: tile (kb, row block) = 16 KB run
@@ -2468,7 +2548,13 @@ int32_t tc_syrk_blocks(firal_problem* P, const void* wv, double lamS, void* outS
     FIRAL_TRY(make_map(&mZ0, P->Zp.p, zrows, BK, BN, BK, true));
     FIRAL_TRY(make_map(&mZ1, P->Zp.as<bf16>() + npp * Np, zrows, BK, BN, BK, true));
     const int grid = std::min(units, sms);
-    if (outS) {
+    if (outS && s1) {
+      k_tc_bsum<2><<<grid, 256, Cfg<2>::SMEM, st>>>(mA0, mA0, mZ0, mZ1, pS, c, d, npairs, n_mt,
+                                                    n_nt, splits, kbps, kb_total,
+                                                    tc_error_word(P), P->kr_bsum.as<int4>(),
+                                                    P->kbL);
+      FIRAL_CUDA_TRY(cudaGetLastError());
+    } else if (outS) {
       k_tc_bsum<0><<<grid, 256, Cfg<0>::SMEM, st>>>(mA0, mA1, mZ0, mZ1, pS, c, d, npairs, n_mt,
                                                     n_nt, splits, kbps, kb_total,
                                                     tc_error_word(P), P->kr_bsum.as<int4>(),
@@ -2482,9 +2568,9 @@ int32_t tc_syrk_blocks(firal_problem* P, const void* wv, double lamS, void* outS
                                                     P->kbL);
       FIRAL_CUDA_TRY(cudaGetLastError());
     }
+    return syrk_reduce_f32(P, outS ? pS : nullptr, outP ? pP : nullptr, splits, lamS,
+                           (float*)outS, lamP, outP, lab_sep ? P->S_lab.as<float>() : nullptr);
   }
-  return syrk_reduce_f32(P, outS ? pS : nullptr, outP ? pP : nullptr, splits, lamS, (float*)outS,
-                         lamP, outP);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -2794,36 +2880,40 @@ int32_t tc_round_scores(firal_problem* P, const void* M1, const void* M2, const 
 // pool's c_q classes, direction P~ with the pool's class means removed):
 //   a_ikj = x_i . P~_j[:, k]                      MMA1: 128 rows x (probe, class), K = features
 //   alpha_ij = sum_k h_ik a_ikj,   psi_ikj = w_i h_ik (a_ikj - alpha_ij)     f32, CUDA cores
-//   out_j[:, k] += sum_i psi_ikj x_i              MMA2: (probe, class) x features, K = rows
+//   out_j[:, k] += sum_i psi_ikj x_i              MMA2: features x (probe, class), K = rows
 // P~ and psi enter as bf16 hi + lo (x is exact in bf16), so both products carry about 2^-17
 // relative rounding, and nothing cancels: each psi is the row's own contribution.  Column
 // (probe j, class k) is j cpad + k, cpad = the pool's class count rounded up to 8, 16 or 32,
 // so one 32-column TMEM load holds whole probes; a probe group of at most 128 columns is one
-// unit of work, so a pool with cpad s > 128 runs as several groups.
+// unit of work, so a pool with cpad s > 128 runs as several groups.  MMA2 takes x^T (the
+// staged x^T tile, K-major, 128 rows of which the first dp are features) and psi as an
+// MN-major operand, so each epilogue thread writes its row's psi values as 16-byte runs.
 // Work list: segments of at most SEG_TILES 128-row tiles of one pool's rows (its labelled
-// rows and its pool rows are separate segments); a CTA takes every probe group of each of its
-// segments (an item).  A tile that also holds rows of another pool runs once per pool with
+// rows and its pool rows are separate segments); the host deals the segments to the CTAs
+// longest first (sched: per-CTA offsets, then segment indices), and a CTA takes every probe
+// group of each of its segments (an item).  A tile that also holds rows of another pool runs once per pool with
 // the other rows masked.  An item accumulates out in TMEM and writes one partial; a
 // per-class combine adds a pool's partials in segment order.
 // Pipeline: the x and x^T tiles, the S accumulator (TMEM), the psi operand (shared memory) and
 // the D accumulator are double-buffered: the TMA loads of tile t+1, MMA1 of tile t+1, the
 // epilogue of tile t and MMA2 of tile t-1 overlap.  Each epilogue thread loads its row's h for
-// the next tile while it works on the current one.
+// the next tile while it works on the current one, from the class-major copy of h (one
+// coalesced run of 128 rows per class).
 // Roles (384 threads): warp 0 TMA producer, warp 1 MMA issuer, warp 2 TMEM owner, warps 4-11
 // epilogue (warp & 3 = TMEM lane quarter, (warp - 4) >> 2 = which 32-column chunks).
 // ------------------------------------------------------------------------------------------
 namespace pw_cfg {
 constexpr int NU = 128;                           // columns per unit (probe group)
-constexpr int SEG_TILES = 16;                     // tiles per segment: 256 adds per accumulator
+constexpr int SEG_TILES = 8;                      // tiles per segment: 128 adds per accumulator
 constexpr int PT_HALF = NU * 128;                 // P~ hi (then lo) of one group: 16 KB
 constexpr int XA_BYTES = 128 * 128;               // x tile: 128 rows x 64 features
 constexpr int XT_BYTES = 2 * 64 * 128;            // x^T tile: 2 K-blocks x (<= 64 features)
-constexpr int PSI_KB = NU * 128;                  // psi^T: one K-block (64 rows) of one part
-constexpr int PSI_BUF = 4 * PSI_KB;               // hi | lo, 2 K-blocks each: 64 KB
+constexpr int PSI_ATOM = 128 * 128;               // psi: 128 rows x 64 columns (one MN atom)
+constexpr int PSI_BUF = 4 * PSI_ATOM;             // hi | lo, 2 MN atoms each: 64 KB
 constexpr int OFF_PT = 0, OFF_XA = 2 * PT_HALF, OFF_XT = OFF_XA + 2 * XA_BYTES;
 constexpr int OFF_PSI = OFF_XT + 2 * XT_BYTES, OFF_CTL = OFF_PSI + 2 * PSI_BUF;
 constexpr int SMEM = OFF_CTL + 256 + 1024;
-constexpr uint32_t TS = 0, TD = 256;              // TMEM columns: S (2 x 128) | D (2 x DP)
+constexpr uint32_t TS = 0, TD = 256;              // TMEM columns: S (2 x 128) | D (2 x 128)
 }  // namespace pw_cfg
 
 struct PwCtl {   // < 256 bytes
@@ -2844,51 +2934,65 @@ __device__ __forceinline__ int pw_ncols(int cpad, int sp, int grp) {
 }
 
 // psi for one 32-column chunk (32 / CPAD whole probes) of the thread's row, written as bf16
-// hi and lo to rows t of the chunk's psi^T block.  wh = w h (zero on masked rows and padding
-// classes); alpha = (sum_k wh_k a_k) / w; off[r] = the thread's byte position in a
-// 128-byte-swizzled row r (mod 8).
+// hi and lo into the row's four 16-byte chunks cb .. cb + 3 of the MN-major psi operand
+// (swizzled: chunk u of row i at (u ^ (i mod 8)) 16 bytes).  wh = w h (zero on masked rows and
+// padding classes); alpha = (sum_k wh_k a_k) / w.
 template <int CPAD>
 __device__ __forceinline__ void pw_psi_chunk(const uint32_t (&ra)[32], const float (&wh)[32],
                                              float winv, unsigned char* hi, unsigned char* lo,
-                                             const uint32_t (&off)[8]) {
+                                             int cb, int sw) {
+  uint32_t ph[16], pl[16];
 #pragma unroll
-  for (int pl = 0; pl < 32 / CPAD; ++pl) {
+  for (int pg = 0; pg < 32 / CPAD; ++pg) {
     float a0 = 0.0f, a1 = 0.0f;
 #pragma unroll
     for (int k = 0; k < CPAD; k += 2) {
-      a0 = fmaf(wh[k], __uint_as_float(ra[pl * CPAD + k]), a0);
-      a1 = fmaf(wh[k + 1], __uint_as_float(ra[pl * CPAD + k + 1]), a1);
+      a0 = fmaf(wh[k], __uint_as_float(ra[pg * CPAD + k]), a0);
+      a1 = fmaf(wh[k + 1], __uint_as_float(ra[pg * CPAD + k + 1]), a1);
     }
     const float al = (a0 + a1) * winv;
 #pragma unroll
-    for (int k = 0; k < CPAD; ++k) {
-      const int t = pl * CPAD + k;
-      const float psi = wh[k] * (__uint_as_float(ra[t]) - al);
-      const bf16 ph = __float2bfloat16_rn(psi);
-      const bf16 pl2 = __float2bfloat16_rn(psi - __bfloat162float(ph));
-      *reinterpret_cast<bf16*>(hi + t * 128 + off[t & 7]) = ph;
-      *reinterpret_cast<bf16*>(lo + t * 128 + off[t & 7]) = pl2;
+    for (int k = 0; k < CPAD; k += 2) {
+      const int t = pg * CPAD + k;
+      const float p0 = wh[k] * (__uint_as_float(ra[t]) - al);
+      const float p1 = wh[k + 1] * (__uint_as_float(ra[t + 1]) - al);
+      const __nv_bfloat162 h2 = __floats2bfloat162_rn(p0, p1);
+      const float2 f2 = __bfloat1622float2(h2);
+      const __nv_bfloat162 l2 = __floats2bfloat162_rn(p0 - f2.x, p1 - f2.y);
+      ph[t >> 1] = *reinterpret_cast<const uint32_t*>(&h2);
+      pl[t >> 1] = *reinterpret_cast<const uint32_t*>(&l2);
     }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int o = ((cb + u) ^ sw) << 4;
+    *reinterpret_cast<uint4*>(hi + o) = make_uint4(ph[4 * u], ph[4 * u + 1], ph[4 * u + 2], ph[4 * u + 3]);
+    *reinterpret_cast<uint4*>(lo + o) = make_uint4(pl[4 * u], pl[4 * u + 1], pl[4 * u + 2], pl[4 * u + 3]);
   }
 }
 
-// loads of the thread's row for a tile: h over the pool's classes (zero beyond c_q and on
-// masked rows) and w
-__device__ __forceinline__ void pw_load_row(float (&hn)[32], float& wn, const float* Ha,
-                                            const float* w, int64_t row, bool valid, int64_t C,
+// loads of the thread's row for a tile: h over the pool's classes from the class-major copy
+// HaT (N rows per class; zero beyond c_q and on masked rows) and w
+__device__ __forceinline__ void pw_load_row(float (&hn)[32], float& wn, const float* HaT,
+                                            const float* w, int64_t row, bool valid, int64_t N,
                                             int coff, int cq) {
+  const float* q = HaT + (int64_t)coff * N + row;   // class coff + k at q + k N
+  const int kmax = valid ? cq : 0;
 #pragma unroll
-  for (int k = 0; k < 32; ++k) hn[k] = (valid && k < cq) ? Ha[row * C + coff + k] : 0.0f;
+  for (int k = 0; k < 32; ++k) {
+    hn[k] = k < kmax ? *q : 0.0f;
+    q += N;
+  }
   wn = valid ? w[row] : 0.0f;
 }
 
 template <int DP>
 __global__ void __launch_bounds__(384, 1)
     k_tc_pw(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapXT,
-            const __grid_constant__ CUtensorMap mapPT, const float* __restrict__ Ha,
+            const __grid_constant__ CUtensorMap mapPT, const float* __restrict__ HaT,
             const float* __restrict__ w, float* __restrict__ part,
-            const int4* __restrict__ pool_tab, const int4* __restrict__ seg_tab, int nseg, int C,
-            int s, int sp, int d, int32_t* err) {
+            const int4* __restrict__ pool_tab, const int4* __restrict__ seg_tab,
+            const int* __restrict__ sched, int64_t N, int s, int sp, int d, int32_t* err) {
   using namespace pw_cfg;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -2934,8 +3038,8 @@ __global__ void __launch_bounds__(384, 1)
     tma_prefetch(&mapPT);
     uint32_t nt = 0, ni = 0;   // tiles and items loaded
     bool ok = true;
-    for (int g = blockIdx.x; g < nseg && ok && !*abort_w; g += gridDim.x) {
-      const int4 sg = seg_tab[g];
+    for (int it = sched[blockIdx.x]; it < sched[blockIdx.x + 1] && ok && !*abort_w; ++it) {
+      const int4 sg = seg_tab[sched[gridDim.x + 1 + it]];
       const int4 pq = pool_tab[sg.x];
       const int n1 = pq.z * sp, pbase = 2 * sp * pq.w;
       const int ng = pw_ngrp(pq.z, sp);
@@ -2980,12 +3084,12 @@ __global__ void __launch_bounds__(384, 1)
     if (ni) mbar_wait_drain(&ctl->pt_full, (ni - 1) & 1);
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer: MMA1 of unit u, then MMA2 of unit u - 1
-    constexpr uint32_t idesc2 = idesc_bf16_f32(128, DP);
     struct Pend {
       uint32_t u, item;
       bool first, last;
+      int nc;
     };
-    Pend pend{0, 0, false, false};
+    Pend pend{0, 0, false, false, 0};
     bool have = false;
     uint32_t nt = 0, ni = 0;
     bool ok = true;
@@ -2996,25 +3100,30 @@ __global__ void __launch_bounds__(384, 1)
           (p.first && !mbar_wait(&ctl->d_empty[db], ((p.item >> 1) & 1) ^ 1, abort_w)))
         return false;
       tc_fence_after();
+      // D (lanes = features, columns = the unit's (probe, class) columns) += x^T psi:
+      // A = the x^T tile (K-major; rows past dp are not features and their D rows are unused),
+      // B = psi (MN-major: rows = the tile's rows, 64-column atoms 16 KB apart)
       const uint32_t ps = smem_u32(sm + OFF_PSI + b * PSI_BUF),
                      xt = smem_u32(sm + OFF_XT + b * XT_BYTES);
+      const uint32_t idesc2 = idesc_bf16_f32_bmn(128, p.nc);
 #pragma unroll
       for (int kb = 0; kb < 2; ++kb)
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          const uint64_t bd = sdesc_sw128(xt + kb * DP * 128 + k * 32);
-          const uint32_t a0 = ps + kb * PSI_KB + k * 32;
+          const uint64_t ad = sdesc_sw128(xt + kb * DP * 128 + k * 32);
+          const uint32_t b0 = ps + (kb * 64 + k * 16) * 128;
           const uint32_t acc = (p.first && kb == 0 && k == 0) ? 0u : 1u;
-          umma_bf16(tmem + TD + db * DP, sdesc_sw128(a0), bd, idesc2, acc);
-          umma_bf16(tmem + TD + db * DP, sdesc_sw128(a0 + 2 * PSI_KB), bd, idesc2, 1u);
+          umma_bf16(tmem + TD + db * NU, ad, sdesc_sw128_mn(b0, PSI_ATOM), idesc2, acc);
+          umma_bf16(tmem + TD + db * NU, ad, sdesc_sw128_mn(b0 + 2 * PSI_ATOM, PSI_ATOM), idesc2,
+                    1u);
         }
       umma_commit(&ctl->psi_empty[b]);
       umma_commit(&ctl->xt_empty[b]);
       if (p.last) umma_commit(&ctl->d_full[db]);
       return true;
     };
-    for (int g = blockIdx.x; g < nseg && ok && !*abort_w; g += gridDim.x) {
-      const int4 sg = seg_tab[g];
+    for (int it = sched[blockIdx.x]; it < sched[blockIdx.x + 1] && ok && !*abort_w; ++it) {
+      const int4 sg = seg_tab[sched[gridDim.x + 1 + it]];
       const int4 pq = pool_tab[sg.x];
       const int ng = pw_ngrp(pq.z, sp);
       const int t0 = sg.y >> 7, t1 = (sg.z - 1) >> 7;
@@ -3041,7 +3150,7 @@ __global__ void __launch_bounds__(384, 1)
           if (t == t1) umma_commit(&ctl->pt_empty);
           ++nt;
           if (have && !mma2(pend)) { give_up(46); ok = false; break; }
-          pend = Pend{u, item, t == t0, t == t1};
+          pend = Pend{u, item, t == t0, t == t1, pw_ncols(pq.z, sp, grp)};
           have = true;
         }
       }
@@ -3054,14 +3163,10 @@ __global__ void __launch_bounds__(384, 1)
     const int quad = warp & 3, half = (warp - 4) >> 2;
     const int i = quad * 32 + lane;            // row within the tile = TMEM lane
     const uint32_t lanes = (uint32_t)(quad * 32) << 16;
-    // byte positions of this row's element in a swizzled 128-byte psi^T row r (mod 8)
-    uint32_t off[8];
-#pragma unroll
-    for (int r = 0; r < 8; ++r) off[r] = ((((i & 63) >> 3) ^ r) << 4) + ((i & 7) << 1);
     uint32_t u = 0, ni = 0;
     bool ok = true;
-    for (int g = blockIdx.x; g < nseg && ok && !*abort_w; g += gridDim.x) {
-      const int4 sg = seg_tab[g];
+    for (int it = sched[blockIdx.x]; it < sched[blockIdx.x + 1] && ok && !*abort_w; ++it) {
+      const int4 sg = seg_tab[sched[gridDim.x + 1 + it]];
       const int4 pq = pool_tab[sg.x];
       const int cpad = pq.z, cq = pq.y;
       const int ng = pw_ngrp(cpad, sp);
@@ -3072,7 +3177,7 @@ __global__ void __launch_bounds__(384, 1)
         float hn[32], wn;
         {
           const int64_t row = (int64_t)t0 * 128 + i;
-          pw_load_row(hn, wn, Ha, w, row, row >= sg.y && row < sg.z, C, pq.x, cq);
+          pw_load_row(hn, wn, HaT, w, row, row >= sg.y && row < sg.z, N, pq.x, cq);
         }
         for (int t = t0; t <= t1; ++t) {
           float wh[32];
@@ -3081,7 +3186,7 @@ __global__ void __launch_bounds__(384, 1)
           const float winv = wn != 0.0f ? 1.0f / wn : 0.0f;
           if (t < t1) {   // the next tile's row, while this one is worked on
             const int64_t rn = (int64_t)(t + 1) * 128 + i;
-            pw_load_row(hn, wn, Ha, w, rn, rn >= sg.y && rn < sg.z, C, pq.x, cq);
+            pw_load_row(hn, wn, HaT, w, rn, rn >= sg.y && rn < sg.z, N, pq.x, cq);
           }
           const int b = u & 1;
           const uint32_t ph = (u >> 1) & 1;
@@ -3093,16 +3198,17 @@ __global__ void __launch_bounds__(384, 1)
           }
           ++u;
           tc_fence_after();
-          unsigned char* psi_hi = sm + OFF_PSI + b * PSI_BUF + (i >> 6) * PSI_KB;
+          unsigned char* psi_row = sm + OFF_PSI + b * PSI_BUF + i * 128;
           for (int ch = half; ch < nc / 32; ch += 2) {
             uint32_t ra[32];
             tmem_ld32_async(tmem + lanes + TS + b * NU + ch * 32, ra);
             tmem_wait_ld();
-            unsigned char* hi = psi_hi + ch * 32 * 128;
-            unsigned char* lo = hi + 2 * PSI_KB;
-            if (cpad == 8) pw_psi_chunk<8>(ra, wh, winv, hi, lo, off);
-            else if (cpad == 16) pw_psi_chunk<16>(ra, wh, winv, hi, lo, off);
-            else pw_psi_chunk<32>(ra, wh, winv, hi, lo, off);
+            unsigned char* hi = psi_row + (ch >> 1) * PSI_ATOM;   // 64-column atom of the chunk
+            unsigned char* lo = hi + 2 * PSI_ATOM;
+            const int cb = (ch & 1) * 4;                          // its first 16-byte chunk
+            if (cpad == 8) pw_psi_chunk<8>(ra, wh, winv, hi, lo, cb, i & 7);
+            else if (cpad == 16) pw_psi_chunk<16>(ra, wh, winv, hi, lo, cb, i & 7);
+            else pw_psi_chunk<32>(ra, wh, winv, hi, lo, cb, i & 7);
           }
           tc_fence_before();
           fence_async_smem();
@@ -3113,7 +3219,8 @@ __global__ void __launch_bounds__(384, 1)
           }
         }
         if (!ok) break;
-        // item end: D -> the item's partial rows, [class][probe][feature]
+        // item end: D -> the item's partial rows, [class][probe][feature]; the thread holds
+        // feature e (its TMEM lane) of the columns of its half
         const int db = item & 1;
         if (!mbar_wait(&ctl->d_full[db], (item >> 1) & 1, abort_w)) {
           give_up(48);
@@ -3122,20 +3229,21 @@ __global__ void __launch_bounds__(384, 1)
         }
         tc_fence_after();
         {
-          const int jl = i / cpad, kl = i - jl * cpad;
-          const int j = grp * (NU / cpad) + jl;
-          const bool own = i < nc && kl < cq && j < s;
-          float* dst = part + ((int64_t)(sg.w + kl) * sp + j) * d;
-          constexpr int CW = DP >= 32 ? DP / 2 : 16;   // columns per half
-          if (half * CW < DP) {
+          const int e = i;
+          const int lc = cpad == 8 ? 3 : cpad == 16 ? 4 : 5;
+          for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 32) {
+            if (c0 >= nc) break;
+            uint32_t v[32];
+            tmem_ld32_async(tmem + lanes + TD + db * NU + c0, v);
+            tmem_wait_ld();
+            if (e < d) {
 #pragma unroll
-            for (int c0 = half * CW; c0 < half * CW + CW; c0 += 16) {
-              float v[16];
-              tmem_ld16(tmem + lanes + TD + db * DP + c0, v);
-              if (own)
-#pragma unroll
-                for (int x = 0; x < 16; ++x)
-                  if (c0 + x < d) dst[c0 + x] = v[x];
+              for (int t = 0; t < 32; ++t) {
+                const int col = c0 + t, jl = col >> lc, kl = col - (jl << lc);
+                const int j = grp * (NU >> lc) + jl;
+                if (kl < cq && j < s)
+                  part[((int64_t)(sg.w + kl) * sp + j) * d + e] = __uint_as_float(v[t]);
+              }
             }
           }
         }
@@ -3259,13 +3367,80 @@ int32_t tc_setup_pw(firal_problem* P, const std::vector<int>& coff,
         P->X64.as<bf16>(), P->Xb.as<bf16>(), P->Np, P->dp);
     FIRAL_CUDA_TRY(cudaGetLastError());
   }
+  // h read class-major by the fused kernels (one coalesced run of a tile's rows per class)
+  FIRAL_TRY(class_major_h(P));
   // the host vectors are read by the copies
   FIRAL_CUDA_TRY(cudaStreamSynchronize(st));
+  P->pw_pool_h = ptab;
+  P->pw_seg_h = segs;
+  for (auto& sc : P->pw_sched) sc.buf.release();
+  P->pw_sched.clear();
   P->pw = true;
   P->pw_cpad_max = cmax;
   P->pw_cpad_total = cpre;
   P->pw_nseg = (int)segs.size();
   P->pw_segcls_total = segcls;
+  return FIRAL_OK;
+}
+
+// The CTAs' segment lists for sp padded probes (quad: the gradient, which skips the labelled
+// rows' segments): each segment costs (tiles + 1) x probe groups, and the segments go longest
+// first to the least-loaded CTA (ties to the lowest index), which keeps the slowest CTA within
+// a few percent of the mean where striding left it up to 2x.  Made once per (sp, quad), before
+// any graph capture (the first MD step runs eagerly); each CTA walks its list in pool order.
+static int32_t pw_schedule(firal_problem* P, int sp, bool quad, int* grid_out,
+                           const int** sched_out) {
+  for (auto& sc : P->pw_sched)
+    if (sc.sp == sp && sc.quad == quad) {
+      *grid_out = sc.grid;
+      *sched_out = sc.buf.as<int>();
+      return FIRAL_OK;
+    }
+  std::vector<std::pair<int64_t, int>> items;
+  for (int g = 0; g < (int)P->pw_seg_h.size(); ++g) {
+    const int4 sg = P->pw_seg_h[g];
+    if (quad && (int64_t)sg.z <= P->m) continue;
+    const int4 pq = P->pw_pool_h[sg.x];
+    const int64_t ng = ((int64_t)pq.z * sp + pw_cfg::NU - 1) / pw_cfg::NU;
+    const int64_t tiles = (sg.z - 1) / 128 - sg.y / 128 + 1;
+    items.push_back({(tiles + 1) * ng, g});
+  }
+  const int grid = std::max(1, std::min<int>(P->sms, (int)items.size()));
+  std::stable_sort(items.begin(), items.end(),
+                   [](const std::pair<int64_t, int>& a, const std::pair<int64_t, int>& b) {
+                     return a.first > b.first;
+                   });
+  std::vector<std::vector<int>> lists(grid);
+  std::vector<int64_t> load(grid, 0);
+  for (const auto& it : items) {
+    int best = 0;
+    for (int b = 1; b < grid; ++b)
+      if (load[b] < load[best]) best = b;
+    lists[best].push_back(it.second);
+    load[best] += it.first;
+  }
+  std::vector<int> tab(grid + 1, 0);
+  for (int b = 0; b < grid; ++b) {
+    std::sort(lists[b].begin(), lists[b].end());
+    tab[b + 1] = tab[b] + (int)lists[b].size();
+  }
+  for (int b = 0; b < grid; ++b) tab.insert(tab.end(), lists[b].begin(), lists[b].end());
+  firal_problem::PwSched sc;
+  sc.sp = sp;
+  sc.quad = quad;
+  sc.grid = grid;
+  FIRAL_TRY(sc.buf.ensure(tab.size() * sizeof(int)));
+  cudaStream_t st = P->H->stream;
+  cudaError_t e = cudaMemcpyAsync(sc.buf.p, tab.data(), tab.size() * sizeof(int),
+                                  cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // tab is read by the copy
+  if (e != cudaSuccess) {
+    sc.buf.release();
+    return fail(FIRAL_ERR_CUDA, cudaGetErrorString(e));
+  }
+  P->pw_sched.push_back(sc);
+  *grid_out = grid;
+  *sched_out = P->pw_sched.back().buf.as<int>();
   return FIRAL_OK;
 }
 
@@ -3307,10 +3482,12 @@ static int32_t tc_apply_pw_t(firal_problem* P, const float* w, const float* V, i
   {
     ProfScope ps(st, PF_ALPHA);
     count_launch();
-    const int grid = std::min(P->pw_nseg, P->sms);
-    k_tc_pw<DP><<<grid, 384, SMEM, st>>>(mX, mXT, mPT, P->Ha.as<float>(), w,
+    int grid = 0;
+    const int* sched = nullptr;
+    FIRAL_TRY(pw_schedule(P, sp, false, &grid, &sched));
+    k_tc_pw<DP><<<grid, 384, SMEM, st>>>(mX, mXT, mPT, P->HaT.as<float>(), w,
                                          P->pw_part.as<float>(), P->pw_pool.as<int4>(),
-                                         P->pw_seg.as<int4>(), P->pw_nseg, c, s, sp, d,
+                                         P->pw_seg.as<int4>(), sched, P->N, s, sp, d,
                                          tc_error_word(P));
     FIRAL_CUDA_TRY(cudaGetLastError());
   }
@@ -3383,10 +3560,10 @@ __device__ __forceinline__ float pw_quad_chunk(const uint32_t (&ra)[32], const u
 template <int DP>
 __global__ void __launch_bounds__(384, 1)
     k_tc_pwq(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapPA,
-             const __grid_constant__ CUtensorMap mapPB, const float* __restrict__ Ha,
+             const __grid_constant__ CUtensorMap mapPB, const float* __restrict__ HaT,
              float* __restrict__ g, const int4* __restrict__ pool_tab,
-             const int4* __restrict__ seg_tab, int nseg, int C, int sp, int64_t m, float gscale,
-             int32_t* err) {
+             const int4* __restrict__ seg_tab, const int* __restrict__ sched, int64_t N, int sp,
+             int64_t m, float gscale, int32_t* err) {
   using namespace pwq_cfg;
   using pw_cfg::NU;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -3431,8 +3608,8 @@ __global__ void __launch_bounds__(384, 1)
     tma_prefetch(&mapPB);
     uint32_t nt = 0, ni = 0;
     bool ok = true;
-    for (int gi = blockIdx.x; gi < nseg && ok && !*abort_w; gi += gridDim.x) {
-      const int4 sg = seg_tab[gi];
+    for (int it = sched[blockIdx.x]; it < sched[blockIdx.x + 1] && ok && !*abort_w; ++it) {
+      const int4 sg = seg_tab[sched[gridDim.x + 1 + it]];
       if (skip(sg)) continue;
       const int4 pq = pool_tab[sg.x];
       const int n1 = pq.z * sp, pbase = 2 * sp * pq.w;
@@ -3469,8 +3646,8 @@ __global__ void __launch_bounds__(384, 1)
   } else if (warp == 1 && lane == 0) {
     uint32_t nt = 0, ni = 0;
     bool ok = true;
-    for (int gi = blockIdx.x; gi < nseg && ok && !*abort_w; gi += gridDim.x) {
-      const int4 sg = seg_tab[gi];
+    for (int it = sched[blockIdx.x]; it < sched[blockIdx.x + 1] && ok && !*abort_w; ++it) {
+      const int4 sg = seg_tab[sched[gridDim.x + 1 + it]];
       if (skip(sg)) continue;
       const int4 pq = pool_tab[sg.x];
       const int ng = pw_ngrp(pq.z, sp);
@@ -3511,8 +3688,8 @@ __global__ void __launch_bounds__(384, 1)
     const uint32_t lanes = (uint32_t)(quad * 32) << 16;
     uint32_t nt = 0, nr = 0;
     bool ok = true;
-    for (int gi = blockIdx.x; gi < nseg && ok && !*abort_w; gi += gridDim.x) {
-      const int4 sg = seg_tab[gi];
+    for (int it = sched[blockIdx.x]; it < sched[blockIdx.x + 1] && ok && !*abort_w; ++it) {
+      const int4 sg = seg_tab[sched[gridDim.x + 1 + it]];
       if (skip(sg)) continue;
       const int4 pq = pool_tab[sg.x];
       const int cpad = pq.z, cq = pq.y;
@@ -3524,8 +3701,8 @@ __global__ void __launch_bounds__(384, 1)
         {
           const int64_t row = (int64_t)t0 * 128 + i;
           const bool v0 = row >= sg.y && row < sg.z && row >= m;
-#pragma unroll
-          for (int k = 0; k < 32; ++k) hn[k] = (v0 && k < cq) ? Ha[row * C + pq.x + k] : 0.0f;
+          float wd;
+          pw_load_row(hn, wd, HaT, HaT, row, v0, N, pq.x, cq);
         }
         for (int t = t0; t <= t1; ++t) {
           const int64_t row = (int64_t)t * 128 + i;
@@ -3536,8 +3713,8 @@ __global__ void __launch_bounds__(384, 1)
           if (t < t1) {   // the next tile's row, while this one is worked on
             const int64_t rn = row + 128;
             const bool vn = rn >= sg.y && rn < sg.z && rn >= m;
-#pragma unroll
-            for (int k = 0; k < 32; ++k) hn[k] = (vn && k < cq) ? Ha[rn * C + pq.x + k] : 0.0f;
+            float wd;
+            pw_load_row(hn, wd, HaT, HaT, rn, vn, N, pq.x, cq);
           }
           const int b = nt & 1;
           if (!mbar_wait(&ctl->s_full[b], (nt >> 1) & 1, abort_w)) {
@@ -3631,9 +3808,12 @@ static int32_t tc_quad_pw_t(firal_problem* P, const float* A, const float* B, in
   FIRAL_TRY(make_map(&mX, DP < 64 ? P->X64.p : P->Xb.p, P->Np, 64, 128, 64, true));
   FIRAL_TRY(make_map(&mA, pkA, prows, 64, 64, 64, true));
   FIRAL_TRY(make_map(&mB, pkB, prows, 64, 64, 64, true));
-  k_tc_pwq<DP><<<std::min(P->pw_nseg, P->sms), 384, SMEM, st>>>(
-      mX, mA, mB, P->Ha.as<float>(), g, P->pw_pool.as<int4>(), P->pw_seg.as<int4>(), P->pw_nseg,
-      c, sp, P->m, (float)(scale / s), tc_error_word(P));
+  int grid = 0;
+  const int* sched = nullptr;
+  FIRAL_TRY(pw_schedule(P, sp, true, &grid, &sched));
+  k_tc_pwq<DP><<<grid, 384, SMEM, st>>>(mX, mA, mB, P->HaT.as<float>(), g, P->pw_pool.as<int4>(),
+                                        P->pw_seg.as<int4>(), sched, P->N, sp, P->m,
+                                        (float)(scale / s), tc_error_word(P));
   FIRAL_CUDA_TRY(cudaGetLastError());
   return FIRAL_OK;
 }
@@ -3664,15 +3844,13 @@ static int32_t tc_apply_dp(firal_problem* P, const void* w, const void* Sblk, co
 
 int32_t tc_hessian_apply(firal_problem* P, const void* w, const void* Sblk, const void* V, int s,
                          void* out, double* pq, double lam_null) {
-  // the bf16 direction's rounding (2^-9 per entry) enters only the low-rank term, whose size
-  // next to the result is the rows' mean low-rank share (sum_k h_ik^2 on plain rows, 1 on
-  // centred ones: about e / c for flat softmax rows); above 0.1 (errors above ~2e-4 per
-  // apply) the problem takes the hi + lo direction in both modes
   // at most 32 classes per pool: the fused per-point kernel (its lambda I term is lam_null,
   // added on rank 0 of a row-sharded group)
   if (P->pw) return tc_apply_pw(P, (const float*)w, (const float*)V, s, (float*)out, pq, lam_null);
-  if (P->prec == FIRAL_MIXED_BF16_FAST && P->lowrank_share <= 0.1)
-    return tc_apply_dp<1>(P, w, Sblk, V, s, out, pq, lam_null);
+  // the bf16 direction's rounding (2^-9 per entry) enters only the low-rank term, whose size
+  // next to the result is the rows' mean low-rank share; above 0.1 (errors above ~2e-4 per
+  // apply) the problem takes the hi + lo direction in both modes (fast_rounding)
+  if (fast_rounding(P)) return tc_apply_dp<1>(P, w, Sblk, V, s, out, pq, lam_null);
   return tc_apply_dp<2>(P, w, Sblk, V, s, out, pq, lam_null);
 }
 

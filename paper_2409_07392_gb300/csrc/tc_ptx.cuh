@@ -202,10 +202,27 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
   return d;
 }
 
+// Shared-memory matrix descriptor: MN-major operand in the 128-byte swizzle layout: for each K
+// index a row of 64 MN-consecutive bf16 (128 B), 8-row K groups 1024 B apart (stride
+// dimension), 64-element MN atoms lbo bytes apart (leading dimension); base 1024-byte aligned.
+__device__ __forceinline__ uint64_t sdesc_sw128_mn(uint32_t saddr, uint32_t lbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);          // start address, bits 0-13
+  d |= (uint64_t)((lbo & 0x3FFFFu) >> 4) << 16;      // leading byte offset: MN atoms
+  d |= (uint64_t)(1024u >> 4) << 32;                 // stride byte offset: 8 K rows x 128 B
+  d |= (uint64_t)1 << 46;                            // descriptor version
+  d |= (uint64_t)2 << 61;                            // 128-byte swizzle
+  return d;
+}
+
 // Instruction descriptor of kind::f16: bf16 A and B (K-major), f32 accumulator, M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
+}
+// ... with B MN-major (bit 16)
+__host__ __device__ constexpr uint32_t idesc_bf16_f32_bmn(int M, int N) {
+  return idesc_bf16_f32(M, N) | (1u << 16);
 }
 
 // Byte offset of element (row, k) (k < 64) in a 128-byte-swizzled K-major bf16 tile.
