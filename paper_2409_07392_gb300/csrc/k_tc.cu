@@ -3261,24 +3261,96 @@ __global__ void __launch_bounds__(384, 1)
   }
 }
 
-// Packed direction of the fused kernel (sp = s rounded up to 8 probes): pool q's rows start
-// at 2 sp cpre_q; row part n1_q + j cpad_q + k (part 0 = bf16 hi, 1 = lo of P_j[:, k] minus
-// the pool's class mean; zero for k >= c_q and for the padding probes j >= s); 64 bf16
-// features per row, zero for e >= d.
-__global__ void k_pw_pack(bf16* Pk, const float* V, const float* vmean, const int4* pool_tab,
-                          int s, int sp, int d, int64_t D, int Qe) {
+// Packed direction of the fused kernel (sp = s rounded up to 8 probes), one block per (pool q,
+// probe j): the pool's class mean of V_j (over its c_q classes, in double, groups combined in
+// a fixed order; written to vmean[j][q]), then rows 2 sp cpre_q + part n1_q + j cpad_q + k
+// (part 0 = bf16 hi, 1 = lo of V_j[:, k] minus that mean; zero for k >= c_q and for the
+// padding probes j >= s); 64 bf16 features per row, zero for e >= d.
+__global__ void __launch_bounds__(256) k_pw_pack(bf16* Pk, const float* V, float* vmean,
+                                                 const int4* pool_tab, int s, int sp, int d,
+                                                 int64_t D, int Qe) {
+  __shared__ double red[4][64];
+  __shared__ float mean[64];
   const int q = blockIdx.x, j = blockIdx.y;
   const int4 pq = pool_tab[q];   // first class, classes, padded classes, padded classes before
   const int64_t n1 = (int64_t)pq.z * sp;
   const int64_t r0 = 2LL * sp * pq.w + (int64_t)j * pq.z;
+  {
+    const int e = threadIdx.x & 63, gr = threadIdx.x >> 6;
+    double acc = 0.0;
+    if (j < s && e < d)
+      for (int kl = gr; kl < pq.y; kl += 4) acc += (double)V[(int64_t)j * D + (int64_t)(pq.x + kl) * d + e];
+    red[gr][e] = acc;
+    __syncthreads();
+    if (threadIdx.x < 64) {
+      const double t = ((red[0][e] + red[1][e]) + red[2][e]) + red[3][e];
+      const float m = (j < s && e < d) ? (float)(t / pq.y) : 0.0f;
+      mean[e] = m;
+      if (j < s && e < d) vmean[(j * Qe + q) * d + e] = m;
+    }
+    __syncthreads();
+  }
   for (int idx = threadIdx.x; idx < pq.z * 64; idx += blockDim.x) {
     const int kl = idx >> 6, e = idx & 63;
     float v = 0.0f;
-    if (kl < pq.y && e < d && j < s)
-      v = V[(int64_t)j * D + (int64_t)(pq.x + kl) * d + e] - vmean[(j * Qe + q) * d + e];
+    if (kl < pq.y && e < d && j < s) v = V[(int64_t)j * D + (int64_t)(pq.x + kl) * d + e] - mean[e];
     const bf16 hi = __float2bfloat16_rn(v);
     Pk[(r0 + kl) * 64 + e] = hi;
     Pk[(r0 + n1 + kl) * 64 + e] = __float2bfloat16_rn(v - __bfloat162float(hi));
+  }
+}
+
+// The apply's last steps for one (pool q, probe j), in shared memory:
+//   t_k = lam (V_j[:, k] - vmean) + the pool's segment partials in segment order
+//   out_j[:, k] = t_k - mean_k' t_k' + lam_null vmean      (the class-mean projection)
+//   pq[j c + k] = <V_j[:, k], out_j[:, k]>                 (the CG dot products)
+// lam is the diagonal-part lambda (rank 0 of a row-sharded group only: such a group takes the
+// separate combine / allreduce / projection path instead).
+__global__ void __launch_bounds__(256) k_pw_finish(float* out, const float* V, const float* vmean,
+                                                   const float* part, const int4* pool_tab,
+                                                   const int2* pseg, const int4* seg_tab,
+                                                   float lam, double lam_null, int s, int sp,
+                                                   int c, int d, int64_t D, int Qe, double* pq) {
+  __shared__ float t[32 * 64];
+  __shared__ double red[4][64];
+  __shared__ float qm[64];
+  const int q = blockIdx.x, j = blockIdx.y;
+  const int4 pt = pool_tab[q];
+  const int2 sr = pseg[q];
+  const int cq = pt.y;
+  const float* vm = vmean + (j * Qe + q) * d;
+  for (int idx = threadIdx.x; idx < cq * d; idx += blockDim.x) {
+    const int kl = idx / d, e = idx - kl * d;
+    const int64_t o = (int64_t)j * D + (int64_t)(pt.x + kl) * d + e;
+    float acc = lam * (V[o] - vm[e]);
+    for (int g = sr.x; g < sr.y; ++g) acc += part[((int64_t)(seg_tab[g].w + kl) * sp + j) * d + e];
+    t[kl * 64 + e] = acc;
+  }
+  __syncthreads();
+  {
+    const int e = threadIdx.x & 63, gr = threadIdx.x >> 6;
+    double acc = 0.0;
+    if (e < d)
+      for (int kl = gr; kl < cq; kl += 4) acc += (double)t[kl * 64 + e];
+    red[gr][e] = acc;
+    __syncthreads();
+    if (threadIdx.x < 64 && e < d) qm[e] = (float)((((red[0][e] + red[1][e]) + red[2][e]) + red[3][e]) / cq);
+    __syncthreads();
+  }
+  // one warp per class: the projected block and its dot product with V_j[:, k]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int kl = warp; kl < cq; kl += (int)(blockDim.x >> 5)) {
+    double dot = 0.0;
+    for (int e = lane; e < d; e += 32) {
+      const int64_t o = (int64_t)j * D + (int64_t)(pt.x + kl) * d + e;
+      const float v = t[kl * 64 + e] - qm[e] + (float)(lam_null * (double)vm[e]);
+      out[o] = v;
+      dot += (double)V[o] * (double)v;
+    }
+    if (pq) {
+      for (int o2 = 16; o2 > 0; o2 >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o2);
+      if (lane == 0) pq[(int64_t)j * c + pt.x + kl] = dot;
+    }
   }
 }
 
@@ -3460,8 +3532,7 @@ static int32_t tc_apply_pw_t(firal_problem* P, const float* w, const float* V, i
                               sizeof(float)));
   {
     ProfScope ps(st, PF_SPLIT);
-    count_launch(2);
-    k_class_mean<<<s * Qe, 1024, 0, st>>>(V, s, c, d, P->D, P->vmean.as<float>(), P->pt);
+    count_launch();
     k_pw_pack<<<dim3((unsigned)Qe, (unsigned)sp), 256, 0, st>>>(
         P->pw_pk.as<bf16>(), V, P->vmean.as<float>(), P->pw_pool.as<int4>(), s, sp, d, P->D, Qe);
     FIRAL_CUDA_TRY(cudaGetLastError());
@@ -3492,9 +3563,17 @@ static int32_t tc_apply_pw_t(firal_problem* P, const float* w, const float* V, i
     FIRAL_CUDA_TRY(cudaGetLastError());
   }
   ProfScope ps(st, PF_COMBINE);
+  if (!sharded(P)) {
+    count_launch();
+    k_pw_finish<<<dim3((unsigned)Qe, (unsigned)s), 256, 0, st>>>(
+        out, V, P->vmean.as<float>(), P->pw_part.as<float>(), P->pw_pool.as<int4>(),
+        P->pw_pseg.as<int2>(), P->pw_seg.as<int4>(), (float)lam, lam, s, sp, c, d, P->D, Qe, pq);
+    FIRAL_CUDA_TRY(cudaGetLastError());
+    return FIRAL_OK;
+  }
+  // a row-sharded group: lambda I counts once (rank 0), and the projection and the dots act
+  // on the summed result
   count_launch(3);
-  // lambda I counts once over a row-sharded group (rank 0); the projection below acts on the
-  // summed result
   k_pw_combine<<<c, 256, 0, st>>>(out, V, P->vmean.as<float>(), P->pw_part.as<float>(),
                                   P->pw_pool.as<int4>(), P->pw_pseg.as<int2>(),
                                   P->pw_seg.as<int4>(), P->comm.rank == 0 ? (float)lam : 0.0f,
@@ -3789,9 +3868,7 @@ static int32_t tc_quad_pw_t(firal_problem* P, const float* A, const float* B, in
   bf16* pkA = P->pw_pk.as<bf16>();
   bf16* pkB = pkA + prows * 64;
   ProfScope ps(st, PF_QUAD);
-  count_launch(5);
-  k_class_mean<<<s * Qe, 1024, 0, st>>>(A, s, c, d, P->D, meanA, P->pt);
-  k_class_mean<<<s * Qe, 1024, 0, st>>>(B, s, c, d, P->D, meanB, P->pt);
+  count_launch(3);
   k_pw_pack<<<dim3((unsigned)Qe, (unsigned)sp), 256, 0, st>>>(pkA, A, meanA, P->pw_pool.as<int4>(),
                                                                s, sp, d, P->D, Qe);
   k_pw_pack<<<dim3((unsigned)Qe, (unsigned)sp), 256, 0, st>>>(pkB, B, meanB, P->pw_pool.as<int4>(),
