@@ -10,6 +10,8 @@
 // costs 2 c d^2 s flops per apply once S_k is formed (once per weight vector).
 #include <cuda_bf16.h>
 
+#include <type_traits>
+
 #include "firal_internal.cuh"
 
 
@@ -105,6 +107,14 @@ static int32_t copy_rows_t(void* dst, const void* a, int64_t ma, const void* b, 
                            int cols, cudaStream_t st) {
   const int64_t total = (ma + nb) * cols;
   ProfScope ps(st, PF_PREP);
+  if (std::is_same<T, Tin>::value) {
+    // the same type: two contiguous device-to-device copies at copy bandwidth
+    const size_t ba = (size_t)ma * cols * sizeof(T), bb = (size_t)nb * cols * sizeof(T);
+    if (ba) FIRAL_CUDA_TRY(cudaMemcpyAsync(dst, a, ba, cudaMemcpyDeviceToDevice, st));
+    if (bb)
+      FIRAL_CUDA_TRY(cudaMemcpyAsync((char*)dst + ba, b, bb, cudaMemcpyDeviceToDevice, st));
+    return FIRAL_OK;
+  }
   count_launch();
   k_copy_rows<T, Tin><<<grid_for(total, 256), 256, 0, st>>>(
       (T*)dst, (const Tin*)a, ma, (const Tin*)b, nb, cols);

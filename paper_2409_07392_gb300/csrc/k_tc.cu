@@ -95,27 +95,40 @@ static int32_t* tc_error_word(firal_problem* P) { return &P->H->flags.as<DevFlag
 // ------------------------------------------------------------------------------------------
 // preparation: padded bf16 copies (rows x cols -> rows_p x cols_p) and transposes
 // ------------------------------------------------------------------------------------------
-__global__ void k_to_bf16_pad(bf16* dst, const float* src, int64_t rows, int cols,
-                              int64_t rows_p, int cols_p) {
-  const int64_t total = rows_p * cols_p;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = idx / cols_p;
-    const int cc = (int)(idx - r * cols_p);
-    dst[idx] = __float2bfloat16_rn((r < rows && cc < cols) ? src[r * cols + cc] : 0.0f);
-  }
+// Grid of the padded conversions: blocks walk rows (x, strided) and column pairs (y); a thread
+// converts one pair of columns per row, so no element index is divided by the row length.
+static void bf16_pad_grid(int64_t rows_p, int cols_p, dim3& grid, dim3& block) {
+  const int pairs = cols_p / 2;
+  const int bt = std::min(256, (pairs + 31) / 32 * 32);
+  block = dim3((unsigned)bt);
+  grid = dim3((unsigned)std::min<int64_t>(rows_p, 16384), (unsigned)((pairs + bt - 1) / bt));
 }
 
-// dst = bf16(src - bf16(src)), the low part, same padding as k_to_bf16_pad
-__global__ void k_to_bf16_lo_pad(bf16* dst, const float* src, int64_t rows, int cols,
-                                 int64_t rows_p, int cols_p) {
-  const int64_t total = rows_p * cols_p;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = idx / cols_p;
-    const int col = (int)(idx - r * cols_p);
-    const float v = (r < rows && col < cols) ? src[r * cols + col] : 0.0f;
-    dst[idx] = __float2bfloat16_rn(v - __bfloat162float(__float2bfloat16_rn(v)));
+// MODE 0: bf16(src); 1: bf16(src - bf16(src)), the low part; 2: bf16(src - e_m) on rows with
+// cen[r] = m >= 0 (h_m - 1 is exact in f32 for h_m >= 1/2), bf16(src) elsewhere.  Zero in the
+// padding rows and columns.  cols_p even.
+template <int MODE>
+__global__ void k_bf16_pad(bf16* dst, const float* src, const int* cen, int64_t rows, int cols,
+                           int64_t rows_p, int cols_p) {
+  const int cc = (blockIdx.y * blockDim.x + threadIdx.x) * 2;
+  if (cc >= cols_p) return;
+  for (int64_t r = blockIdx.x; r < rows_p; r += gridDim.x) {
+    float v0 = 0.0f, v1 = 0.0f;
+    if (r < rows) {
+      if (cc < cols) v0 = src[r * cols + cc];
+      if (cc + 1 < cols) v1 = src[r * cols + cc + 1];
+      if (MODE == 2) {
+        const int m = cen[r];
+        if (m == cc) v0 -= 1.0f;
+        if (m == cc + 1) v1 -= 1.0f;
+      }
+    }
+    __nv_bfloat162 o = __floats2bfloat162_rn(v0, v1);
+    if (MODE == 1) {
+      const float2 f = __bfloat1622float2(o);
+      o = __floats2bfloat162_rn(v0 - f.x, v1 - f.y);
+    }
+    *reinterpret_cast<__nv_bfloat162*>(dst + r * cols_p + cc) = o;
   }
 }
 
@@ -144,35 +157,57 @@ constexpr float kCentre = 0.5f;
 // *count gains the number of such rows and *share the row's low-rank share: sum_k h_rk^2 on a
 // plain row (the size of the low-rank term of its Hessian next to the diagonal term), 1 on a
 // centred row (all of its terms are of one size).  One warp per row.
-__global__ void k_row_top(int* cen, unsigned long long* count, double* share, const float* src,
-                          int64_t rows, int cols) {
-  const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (r >= rows) return;
-  float best = -1.0f;
-  int bi = 0x7fffffff;
-  float sq = 0.0f;
-  for (int k = lane; k < cols; k += 32) {
-    const float v = src[r * cols + k];
-    sq = fmaf(v, v, sq);
-    if (v > best) {
-      best = v;
-      bi = k;
+__global__ void __launch_bounds__(256) k_row_top(int* cen, unsigned long long* count,
+                                                 double* share, const float* src, int64_t rows,
+                                                 int cols) {
+  __shared__ double s_sh[8];
+  __shared__ unsigned long long s_cnt[8];
+  const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  double wshare = 0.0;
+  unsigned long long wcnt = 0;
+  // one warp per row, rows strided over all warps; one pair of atomics per block
+  for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + wb; r < rows; r += nwarps) {
+    float best = -1.0f;
+    int bi = 0x7fffffff;
+    float sq = 0.0f;
+    for (int k = lane; k < cols; k += 32) {
+      const float v = src[r * cols + k];
+      sq = fmaf(v, v, sq);
+      if (v > best) {
+        best = v;
+        bi = k;
+      }
     }
-  }
-  for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-  for (int o = 16; o > 0; o >>= 1) {
-    const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-    if (ob > best || (ob == best && oi < bi)) {
-      best = ob;
-      bi = oi;
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) {
+        best = ob;
+        bi = oi;
+      }
+    }
+    if (lane == 0) {
+      cen[r] = best > kCentre ? bi : -1;
+      wcnt += best > kCentre ? 1ULL : 0ULL;
+      wshare += best > kCentre ? 1.0 : (double)sq;
     }
   }
   if (lane == 0) {
-    cen[r] = best > kCentre ? bi : -1;
-    if (best > kCentre) atomicAdd(count, 1ULL);
-    atomicAdd(share, best > kCentre ? 1.0 : (double)sq);
+    s_sh[wb] = wshare;
+    s_cnt[wb] = wcnt;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    unsigned long long cn = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+      t += s_sh[i];
+      cn += s_cnt[i];
+    }
+    if (cn) atomicAdd(count, cn);
+    atomicAdd(share, t);
   }
 }
 
@@ -1656,26 +1691,36 @@ __global__ void __launch_bounds__(256, 1)
 // Z[p][i] = x_ie x_ie' for pair p = (e, e') of the row-major triangle, as bf16 hi and lo (exact);
 // rows p >= npairs and columns of padding points are zero.  K-block-major layout
 // [i / 64][p][i % 64] (npp rows per block): every 128 x 64 TMA tile is one contiguous 16 KB
-// run.  Block = 64 points x 128 pairs.
+// run.  Block = 64 points x 128 pairs; the block's pair indices and its points' features
+// (feature-major) are staged in shared memory.
 __global__ void k_build_z(bf16* Zhi, bf16* Zlo, const bf16* Xb, int d, int dp, int npairs,
                           int64_t npp) {
-  __shared__ bf16 xs[64 * 128];   // 64 points x dp features
+  __shared__ bf16 xs[128 * 64];    // feature-major: xs[e * 64 + point]
+  __shared__ short pe[128], pe2[128];
   const int64_t i0 = (int64_t)blockIdx.x * 64;
   const int p0 = blockIdx.y * 128;
-  for (int t = threadIdx.x; t < 64 * dp; t += blockDim.x) xs[t] = Xb[i0 * dp + t];
+  for (int t = threadIdx.x; t < 64 * dp; t += blockDim.x) {
+    const int i = t / dp, e = t - i * dp;
+    xs[e * 64 + i] = Xb[i0 * dp + t];
+  }
+  if (threadIdx.x < 128 && p0 + (int)threadIdx.x < npairs) {
+    int e, e2;
+    pair_of(p0 + threadIdx.x, d, e, e2);
+    pe[threadIdx.x] = (short)e;
+    pe2[threadIdx.x] = (short)e2;
+  }
   __syncthreads();
   for (int item = threadIdx.x; item < 128 * 8; item += blockDim.x) {
-    const int p = p0 + (item >> 3), c8 = item & 7;
+    const int pl = item >> 3, c8 = item & 7, p = p0 + pl;
     uint4 hv = make_uint4(0, 0, 0, 0), lv = make_uint4(0, 0, 0, 0);
     if (p < npairs) {
-      int e, e2;
-      pair_of(p, d, e, e2);
+      const bf16* xa = xs + pe[pl] * 64 + c8 * 8;
+      const bf16* xb = xs + pe2[pl] * 64 + c8 * 8;
       bf16* h = reinterpret_cast<bf16*>(&hv);
       bf16* l = reinterpret_cast<bf16*>(&lv);
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        const int i = c8 * 8 + q;
-        const float z = __bfloat162float(xs[i * dp + e]) * __bfloat162float(xs[i * dp + e2]);
+        const float z = __bfloat162float(xa[q]) * __bfloat162float(xb[q]);
         h[q] = __float2bfloat16_rn(z);
         l[q] = __float2bfloat16_rn(z - __bfloat162float(h[q]));
       }
@@ -2113,8 +2158,8 @@ static int32_t tc_prepare_centred(firal_problem* P, int cpb2) {
   {
     ProfScope ps(st, PF_PREP);
     count_launch();
-    k_row_top<<<(unsigned)((N * 32 + 255) / 256), 256, 0, st>>>(P->cen.as<int>(), cnt, shr,
-                                                                P->Ha.as<float>(), N, c);
+    k_row_top<<<(unsigned)std::min<int64_t>((N + 7) / 8, 4LL * P->sms), 256, 0, st>>>(
+        P->cen.as<int>(), cnt, shr, P->Ha.as<float>(), N, c);
   }
   FIRAL_CUDA_TRY(cudaGetLastError());
   unsigned long long nconf = 0;
@@ -2168,12 +2213,13 @@ static int32_t tc_prepare_centred(firal_problem* P, int cpb2) {
                                  cudaMemcpyHostToDevice, st));
   FIRAL_TRY(P->Ub.ensure((size_t)Np * P->cp * 2));
   FIRAL_TRY(P->UbT.ensure((size_t)Np * cpb2 * 2));
-  const int64_t tot_h = Np * P->cp;
   {
     ProfScope ps(st, PF_PREP);
     count_launch(2);
-    k_to_bf16_centred_pad<<<(unsigned)std::min<int64_t>((tot_h + 255) / 256, 1 << 20), 256, 0, st>>>(
-        P->Ub.as<bf16>(), P->Ha.as<float>(), P->cen.as<int>(), N, c, Np, P->cp);
+    dim3 g, b;
+    bf16_pad_grid(Np, P->cp, g, b);
+    k_bf16_pad<2><<<g, b, 0, st>>>(P->Ub.as<bf16>(), P->Ha.as<float>(), P->cen.as<int>(), N, c,
+                                   Np, P->cp);
     k_block_transpose_bf16<<<dim3((unsigned)(Np / 32), (unsigned)(cpb2 / 32)), dim3(32, 8), 0, st>>>(
         P->UbT.as<bf16>(), P->Ub.as<bf16>(), Np, P->cp, cpb2);
   }
@@ -2195,13 +2241,18 @@ int32_t tc_prepare(firal_problem* P) {
   const int cpb2 = (P->cp + d_cfg::MT * d_cfg::BM - 1) / (d_cfg::MT * d_cfg::BM) * (d_cfg::MT * d_cfg::BM);
   FIRAL_TRY(P->HbT.ensure((size_t)Np * cpb2 * 2));
   FIRAL_TRY(P->Xb.ensure((size_t)Np * P->dp * 2 * 2));   // X (Np x dp) then X^T (dp x Np)
-  const int64_t tot_h = Np * P->cp, tot_x = Np * P->dp;
+  const int64_t tot_x = Np * P->dp;
   ProfScope ps(st, PF_PREP);
   count_launch(3);
-  k_to_bf16_pad<<<(unsigned)std::min<int64_t>((tot_h + 255) / 256, 1 << 20), 256, 0, st>>>(
-      P->Hb.as<bf16>(), P->Ha.as<float>(), P->N, P->c, Np, P->cp);
-  k_to_bf16_pad<<<(unsigned)std::min<int64_t>((tot_x + 255) / 256, 1 << 20), 256, 0, st>>>(
-      P->Xb.as<bf16>(), P->Xa.as<float>(), P->N, P->d, Np, P->dp);
+  {
+    dim3 g, b;
+    bf16_pad_grid(Np, P->cp, g, b);
+    k_bf16_pad<0><<<g, b, 0, st>>>(P->Hb.as<bf16>(), P->Ha.as<float>(), nullptr, P->N, P->c, Np,
+                                   P->cp);
+    bf16_pad_grid(Np, P->dp, g, b);
+    k_bf16_pad<0><<<g, b, 0, st>>>(P->Xb.as<bf16>(), P->Xa.as<float>(), nullptr, P->N, P->d, Np,
+                                   P->dp);
+  }
   FIRAL_CUDA_TRY(cudaGetLastError());
   // h^T and x^T of the D-GEMM, K-block-major
   k_block_transpose_bf16<<<dim3((unsigned)(Np / 32), (unsigned)(cpb2 / 32)), dim3(32, 8), 0, st>>>(
@@ -2652,12 +2703,12 @@ static int32_t ensure_hlo(firal_problem* P) {
   const size_t bytes = (size_t)P->Np * P->cp * 2;
   if (P->Hlo.p && P->Hlo.bytes >= bytes && P->hlo_ready) return FIRAL_OK;
   FIRAL_TRY(P->Hlo.ensure(bytes));
-  const int64_t tot_h = P->Np * P->cp;
   ProfScope ps(P->H->stream, PF_PREP);
   count_launch();
-  k_to_bf16_lo_pad<<<(unsigned)std::min<int64_t>((tot_h + 255) / 256, 1 << 20), 256, 0,
-                     P->H->stream>>>(P->Hlo.as<bf16>(), P->Ha.as<float>(), P->N, P->c, P->Np,
-                                     P->cp);
+  dim3 g, b;
+  bf16_pad_grid(P->Np, P->cp, g, b);
+  k_bf16_pad<1><<<g, b, 0, P->H->stream>>>(P->Hlo.as<bf16>(), P->Ha.as<float>(), nullptr, P->N,
+                                           P->c, P->Np, P->cp);
   FIRAL_CUDA_TRY(cudaGetLastError());
   P->hlo_ready = true;
   return FIRAL_OK;
