@@ -2986,30 +2986,37 @@ __device__ __forceinline__ int pw_ncols(int cpad, int sp, int grp) {
 
 // psi for one 32-column chunk (32 / CPAD whole probes) of the thread's row, written as bf16
 // hi and lo into the row's four 16-byte chunks cb .. cb + 3 of the MN-major psi operand
-// (swizzled: chunk u of row i at (u ^ (i mod 8)) 16 bytes).  wh = w h (zero on masked rows and
-// padding classes); alpha = (sum_k wh_k a_k) / w.
+// (swizzled: chunk u of row i at (u ^ (i mod 8)) 16 bytes).  wh2 = w h of classes (2m, 2m+1)
+// as packed pairs (zero on masked rows and padding classes); alpha = (sum_k wh_k a_k) / w.
+// The f32 arithmetic runs on packed pairs (f32x2), each lane rounded as the scalar form.
 template <int CPAD>
-__device__ __forceinline__ void pw_psi_chunk(const uint32_t (&ra)[32], const float (&wh)[32],
-                                             float winv, unsigned char* hi, unsigned char* lo,
-                                             int cb, int sw) {
+__device__ __forceinline__ void pw_psi_chunk(const uint32_t (&ra)[32],
+                                             const uint64_t (&wh2)[CPAD / 2], float winv,
+                                             unsigned char* hi, unsigned char* lo, int cb,
+                                             int sw) {
+  const uint64_t m1 = f2_pack(-1.0f, -1.0f);
   uint32_t ph[16], pl[16];
 #pragma unroll
   for (int pg = 0; pg < 32 / CPAD; ++pg) {
-    float a0 = 0.0f, a1 = 0.0f;
+    uint64_t acc = 0;
 #pragma unroll
-    for (int k = 0; k < CPAD; k += 2) {
-      a0 = fmaf(wh[k], __uint_as_float(ra[pg * CPAD + k]), a0);
-      a1 = fmaf(wh[k + 1], __uint_as_float(ra[pg * CPAD + k + 1]), a1);
-    }
-    const float al = (a0 + a1) * winv;
+    for (int k = 0; k < CPAD; k += 2)
+      acc = f2_fma(wh2[k / 2], f2_pack_u(ra[pg * CPAD + k], ra[pg * CPAD + k + 1]), acc);
+    float x0, x1;
+    f2_unpack(acc, x0, x1);
+    const float al = (x0 + x1) * winv;
+    const uint64_t nal = f2_pack(-al, -al);
 #pragma unroll
     for (int k = 0; k < CPAD; k += 2) {
       const int t = pg * CPAD + k;
-      const float p0 = wh[k] * (__uint_as_float(ra[t]) - al);
-      const float p1 = wh[k + 1] * (__uint_as_float(ra[t + 1]) - al);
+      const uint64_t p2 = f2_mul(wh2[k / 2], f2_add(f2_pack_u(ra[t], ra[t + 1]), nal));
+      float p0, p1;
+      f2_unpack(p2, p0, p1);
       const __nv_bfloat162 h2 = __floats2bfloat162_rn(p0, p1);
       const float2 f2 = __bfloat1622float2(h2);
-      const __nv_bfloat162 l2 = __floats2bfloat162_rn(p0 - f2.x, p1 - f2.y);
+      float r0, r1;
+      f2_unpack(f2_fma(f2_pack(f2.x, f2.y), m1, p2), r0, r1);   // p - bf16(p), per lane
+      const __nv_bfloat162 l2 = __floats2bfloat162_rn(r0, r1);
       ph[t >> 1] = *reinterpret_cast<const uint32_t*>(&h2);
       pl[t >> 1] = *reinterpret_cast<const uint32_t*>(&l2);
     }
@@ -3022,8 +3029,23 @@ __device__ __forceinline__ void pw_psi_chunk(const uint32_t (&ra)[32], const flo
   }
 }
 
-// loads of the thread's row for a tile: h over the pool's classes from the class-major copy
-// HaT (N rows per class; zero beyond c_q and on masked rows) and w
+// loads of the thread's row for a tile: h over the pool's CPAD padded classes from the
+// class-major copy HaT (N rows per class; zero beyond c_q and on masked rows) and w
+template <int CPAD>
+__device__ __forceinline__ void pw_load_row_c(float (&hn)[CPAD], float& wn, const float* HaT,
+                                              const float* w, int64_t row, bool valid, int64_t N,
+                                              int coff, int cq) {
+  const float* q = HaT + (int64_t)coff * N + row;   // class coff + k at q + k N
+  const int kmax = valid ? cq : 0;
+#pragma unroll
+  for (int k = 0; k < CPAD; ++k) {
+    hn[k] = k < kmax ? *q : 0.0f;
+    q += N;
+  }
+  wn = valid ? w[row] : 0.0f;
+}
+
+// the same for 32 classes (the gradient kernel)
 __device__ __forceinline__ void pw_load_row(float (&hn)[32], float& wn, const float* HaT,
                                             const float* w, int64_t row, bool valid, int64_t N,
                                             int coff, int cq) {
@@ -3035,6 +3057,109 @@ __device__ __forceinline__ void pw_load_row(float (&hn)[32], float& wn, const fl
     q += N;
   }
   wn = valid ? w[row] : 0.0f;
+}
+
+// Epilogue context of the fused apply kernel (one thread: row i of the tile = TMEM lane,
+// half = which 32-column chunks it takes)
+struct PwEpi {
+  PwCtl* ctl;
+  unsigned char* sm;
+  uint32_t tmem, lanes;
+  int i, half, lane;
+  volatile int* abort_w;
+  int32_t* err;
+  const float* HaT;
+  const float* w;
+  float* part;
+  int64_t N;
+  int s, sp, d;
+};
+
+// One work item (segment sg of pool pq, probe group grp of nc columns) of the epilogue, with
+// the pool's classes padded to CPAD: per tile, psi into the MN-major operand; at the end, the
+// item's partial rows from the D accumulator.  u counts the units seen; false when a wait gave
+// up (the abort word and the error word are set).
+template <int CPAD, int DP>
+__device__ __forceinline__ bool pw_epi_item(const PwEpi& E, uint32_t& u, uint32_t item,
+                                            const int4& sg, const int4& pq, int grp, int nc) {
+  using namespace pw_cfg;
+  const int i = E.i, lane = E.lane, cq = pq.y;
+  const int t0 = sg.y >> 7, t1 = (sg.z - 1) >> 7;
+  auto give_up = [&](int code) {
+    E.ctl->abort_w = 1;
+    atomicExch(E.err, code);
+  };
+  float hn[CPAD], wn;
+  {
+    const int64_t row = (int64_t)t0 * 128 + i;
+    pw_load_row_c<CPAD>(hn, wn, E.HaT, E.w, row, row >= sg.y && row < sg.z, E.N, pq.x, cq);
+  }
+  for (int t = t0; t <= t1; ++t) {
+    uint64_t wh2[CPAD / 2];
+    const uint64_t w2 = f2_pack(wn, wn);
+#pragma unroll
+    for (int k = 0; k < CPAD; k += 2) wh2[k / 2] = f2_mul(w2, f2_pack(hn[k], hn[k + 1]));
+    const float winv = wn != 0.0f ? 1.0f / wn : 0.0f;
+    if (t < t1) {   // the next tile's row, while this one is worked on
+      const int64_t rn = (int64_t)(t + 1) * 128 + i;
+      pw_load_row_c<CPAD>(hn, wn, E.HaT, E.w, rn, rn >= sg.y && rn < sg.z, E.N, pq.x, cq);
+    }
+    const int b = u & 1;
+    const uint32_t ph = (u >> 1) & 1;
+    if (!mbar_wait(&E.ctl->s_full[b], ph, E.abort_w) ||
+        !mbar_wait(&E.ctl->psi_empty[b], ph ^ 1, E.abort_w)) {
+      give_up(47);
+      return false;
+    }
+    ++u;
+    tc_fence_after();
+    unsigned char* psi_row = E.sm + OFF_PSI + b * PSI_BUF + i * 128;
+    for (int ch = E.half; ch < nc / 32; ch += 2) {
+      uint32_t ra[32];
+      tmem_ld32_async(E.tmem + E.lanes + TS + b * NU + ch * 32, ra);
+      tmem_wait_ld();
+      unsigned char* hi = psi_row + (ch >> 1) * PSI_ATOM;   // 64-column atom of the chunk
+      pw_psi_chunk<CPAD>(ra, wh2, winv, hi, hi + 2 * PSI_ATOM, (ch & 1) * 4, i & 7);
+    }
+    tc_fence_before();
+    fence_async_smem();
+    __syncwarp();
+    if (lane == 0) {
+      mbar_arrive(&E.ctl->s_empty[b]);
+      mbar_arrive(&E.ctl->psi_full[b]);
+    }
+  }
+  // item end: D -> the item's partial rows, [class][probe][feature]; the thread holds feature
+  // e (its TMEM lane) of the columns of its half
+  const int db = item & 1;
+  if (!mbar_wait(&E.ctl->d_full[db], (item >> 1) & 1, E.abort_w)) {
+    give_up(48);
+    return false;
+  }
+  tc_fence_after();
+  {
+    constexpr int LC = CPAD == 8 ? 3 : CPAD == 16 ? 4 : 5;
+    const int e = i;
+    for (int c0 = E.half * 64; c0 < E.half * 64 + 64; c0 += 32) {
+      if (c0 >= nc) break;
+      uint32_t v[32];
+      tmem_ld32_async(E.tmem + E.lanes + TD + db * NU + c0, v);
+      tmem_wait_ld();
+      if (e < E.d) {
+#pragma unroll
+        for (int t = 0; t < 32; ++t) {
+          const int col = c0 + t, jl = col >> LC, kl = col - (jl << LC);
+          const int j = grp * (NU >> LC) + jl;
+          if (kl < cq && j < E.s)
+            E.part[((int64_t)(sg.w + kl) * E.sp + j) * E.d + e] = __uint_as_float(v[t]);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncwarp();
+  if (lane == 0) mbar_arrive(&E.ctl->d_empty[db]);
+  return true;
 }
 
 template <int DP>
@@ -3211,96 +3336,21 @@ __global__ void __launch_bounds__(384, 1)
     mbar_wait_drain(&ctl->drain, 0);
   } else if (warp >= 4) {
     // ---------------- epilogue
-    const int quad = warp & 3, half = (warp - 4) >> 2;
-    const int i = quad * 32 + lane;            // row within the tile = TMEM lane
-    const uint32_t lanes = (uint32_t)(quad * 32) << 16;
+    const int quad = warp & 3;
+    const PwEpi E{ctl, sm, tmem, (uint32_t)(quad * 32) << 16, quad * 32 + lane, (warp - 4) >> 2,
+                  lane, abort_w, err, HaT, w, part, N, s, sp, d};
     uint32_t u = 0, ni = 0;
     bool ok = true;
     for (int it = sched[blockIdx.x]; it < sched[blockIdx.x + 1] && ok && !*abort_w; ++it) {
       const int4 sg = seg_tab[sched[gridDim.x + 1 + it]];
       const int4 pq = pool_tab[sg.x];
-      const int cpad = pq.z, cq = pq.y;
-      const int ng = pw_ngrp(cpad, sp);
-      const int t0 = sg.y >> 7, t1 = (sg.z - 1) >> 7;
+      const int ng = pw_ngrp(pq.z, sp);
       for (int grp = 0; grp < ng && ok; ++grp) {
-        const int nc = pw_ncols(cpad, sp, grp);
+        const int nc = pw_ncols(pq.z, sp, grp);
         const uint32_t item = ni++;
-        float hn[32], wn;
-        {
-          const int64_t row = (int64_t)t0 * 128 + i;
-          pw_load_row(hn, wn, HaT, w, row, row >= sg.y && row < sg.z, N, pq.x, cq);
-        }
-        for (int t = t0; t <= t1; ++t) {
-          float wh[32];
-#pragma unroll
-          for (int k = 0; k < 32; ++k) wh[k] = wn * hn[k];
-          const float winv = wn != 0.0f ? 1.0f / wn : 0.0f;
-          if (t < t1) {   // the next tile's row, while this one is worked on
-            const int64_t rn = (int64_t)(t + 1) * 128 + i;
-            pw_load_row(hn, wn, HaT, w, rn, rn >= sg.y && rn < sg.z, N, pq.x, cq);
-          }
-          const int b = u & 1;
-          const uint32_t ph = (u >> 1) & 1;
-          if (!mbar_wait(&ctl->s_full[b], ph, abort_w) ||
-              !mbar_wait(&ctl->psi_empty[b], ph ^ 1, abort_w)) {
-            give_up(47);
-            ok = false;
-            break;
-          }
-          ++u;
-          tc_fence_after();
-          unsigned char* psi_row = sm + OFF_PSI + b * PSI_BUF + i * 128;
-          for (int ch = half; ch < nc / 32; ch += 2) {
-            uint32_t ra[32];
-            tmem_ld32_async(tmem + lanes + TS + b * NU + ch * 32, ra);
-            tmem_wait_ld();
-            unsigned char* hi = psi_row + (ch >> 1) * PSI_ATOM;   // 64-column atom of the chunk
-            unsigned char* lo = hi + 2 * PSI_ATOM;
-            const int cb = (ch & 1) * 4;                          // its first 16-byte chunk
-            if (cpad == 8) pw_psi_chunk<8>(ra, wh, winv, hi, lo, cb, i & 7);
-            else if (cpad == 16) pw_psi_chunk<16>(ra, wh, winv, hi, lo, cb, i & 7);
-            else pw_psi_chunk<32>(ra, wh, winv, hi, lo, cb, i & 7);
-          }
-          tc_fence_before();
-          fence_async_smem();
-          __syncwarp();
-          if (lane == 0) {
-            mbar_arrive(&ctl->s_empty[b]);
-            mbar_arrive(&ctl->psi_full[b]);
-          }
-        }
-        if (!ok) break;
-        // item end: D -> the item's partial rows, [class][probe][feature]; the thread holds
-        // feature e (its TMEM lane) of the columns of its half
-        const int db = item & 1;
-        if (!mbar_wait(&ctl->d_full[db], (item >> 1) & 1, abort_w)) {
-          give_up(48);
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        {
-          const int e = i;
-          const int lc = cpad == 8 ? 3 : cpad == 16 ? 4 : 5;
-          for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 32) {
-            if (c0 >= nc) break;
-            uint32_t v[32];
-            tmem_ld32_async(tmem + lanes + TD + db * NU + c0, v);
-            tmem_wait_ld();
-            if (e < d) {
-#pragma unroll
-              for (int t = 0; t < 32; ++t) {
-                const int col = c0 + t, jl = col >> lc, kl = col - (jl << lc);
-                const int j = grp * (NU >> lc) + jl;
-                if (kl < cq && j < s)
-                  part[((int64_t)(sg.w + kl) * sp + j) * d + e] = __uint_as_float(v[t]);
-              }
-            }
-          }
-        }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&ctl->d_empty[db]);
+        if (pq.z == 8) ok = pw_epi_item<8, DP>(E, u, item, sg, pq, grp, nc);
+        else if (pq.z == 16) ok = pw_epi_item<16, DP>(E, u, item, sg, pq, grp, nc);
+        else ok = pw_epi_item<32, DP>(E, u, item, sg, pq, grp, nc);
       }
     }
   }
