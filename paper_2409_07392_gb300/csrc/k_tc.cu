@@ -2714,6 +2714,323 @@ static int32_t ensure_hlo(firal_problem* P) {
   return FIRAL_OK;
 }
 
+// ------------------------------------------------------------------------------------------
+// Per-point quadratic forms (eq. 11) at d <= 64 with many classes, s <= 16: class-chunk-major,
+// two probes per MMA.  For point tile i and 64-class chunk kc, the probes run in pairs
+// (j, j'), one unit each:
+//   S_A = x [A_j | A_j'][:, chunk]^T,  S_B = x [B_j | B_j'][:, chunk]^T      (N = 128 each)
+// with A~ and B~ as bf16 hi + lo, except an A that is the probe block itself: its entries
+// (+-1) are exact in bf16 and it needs neither a low part nor the class-mean projection (the
+// forms are unchanged by adding a per-row constant to a, since the row's h sums to one).
+// Epilogue: 8 warps, warp (quarter, half) takes TMEM lanes of its quarter and probe 2 jp + half;
+// per probe the running sums sum_k h a b, sum_k h a, sum_k h b over the chunks stay in
+// registers (the h tile of a chunk is loaded once, for all its probe pairs), and after the
+// last chunk q = sum_j (sum h a b - (sum h a)(sum h b)); the two halves' shares of a row go to
+// g as two atomic adds on zeroed memory (the sum of two addends does not depend on order).
+// Pipeline: double-buffered x tile, h tile, coefficient blocks and TMEM accumulators.
+// ------------------------------------------------------------------------------------------
+namespace qf_cfg {
+constexpr int NP2MAX = 8;                     // probe pairs (s <= 16)
+constexpr int CBLK = 512 * 128;               // coefficient block: up to 4 x 128 rows of 128 B
+constexpr int HT = 128 * 64 * 4;              // f32 h tile, two 128-byte-swizzled boxes
+constexpr int XT = 128 * 128;                 // x tile
+constexpr int OFF_C = 0, OFF_H = 2 * CBLK, OFF_X = OFF_H + 2 * HT, OFF_CTL = OFF_X + 2 * XT;
+constexpr int SMEM = OFF_CTL + 256 + 1024;
+}  // namespace qf_cfg
+
+struct QfCtl {   // < 256 bytes
+  uint64_t x_full[2], x_empty[2], h_full[2], h_empty[2], c_full[2], c_empty[2], s_full[2],
+      s_empty[2], drain;
+  uint32_t tmem_base;
+  int abort_w;
+};
+static_assert(sizeof(QfCtl) <= 256, "control block must fit in 256 bytes");
+
+// h of 32 classes (box of the tile) times 32 a and b columns: the running sums of one probe
+__device__ __forceinline__ void qf_box(const uint32_t (&ra)[32], const uint32_t (&rb)[32],
+                                       const unsigned char* hrow, int r, float& sab, float& sa,
+                                       float& sb) {
+  uint64_t pab = 0, pa = 0, pb = 0;
+#pragma unroll
+  for (int ch = 0; ch < 8; ++ch) {
+    const ulonglong2 h4 = *reinterpret_cast<const ulonglong2*>(hrow + ((ch ^ (r & 7)) << 4));
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      const uint64_t h2 = v ? h4.y : h4.x;
+      const int t = 4 * ch + 2 * v;
+      const uint64_t a2 = f2_pack_u(ra[t], ra[t + 1]), b2 = f2_pack_u(rb[t], rb[t + 1]);
+      const uint64_t ha2 = f2_mul(h2, a2);
+      pab = f2_fma(ha2, b2, pab);
+      pa = f2_add(pa, ha2);
+      pb = f2_fma(h2, b2, pb);
+    }
+  }
+  float x0, x1;
+  f2_unpack(pab, x0, x1);
+  sab += x0 + x1;
+  f2_unpack(pa, x0, x1);
+  sa += x0 + x1;
+  f2_unpack(pb, x0, x1);
+  sb += x0 + x1;
+}
+
+template <bool AEXACT>
+__global__ void __launch_bounds__(384, 1)
+    k_tc_qf(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapC,
+            const __grid_constant__ CUtensorMap mapH, float* __restrict__ g, int64_t N,
+            int64_t m, int n_mt, int nkc, int np2, float gscale, int32_t* err) {
+  using namespace qf_cfg;
+  constexpr int NR = AEXACT ? 384 : 512;      // coefficient rows per unit
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  QfCtl* ctl = (QfCtl*)(sm + OFF_CTL);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&ctl->x_full[b], 1);
+      mbar_init(&ctl->x_empty[b], 1);
+      mbar_init(&ctl->h_full[b], 1);
+      mbar_init(&ctl->h_empty[b], 8);
+      mbar_init(&ctl->c_full[b], 1);
+      mbar_init(&ctl->c_empty[b], 1);
+      mbar_init(&ctl->s_full[b], 1);
+      mbar_init(&ctl->s_empty[b], 8);
+    }
+    mbar_init(&ctl->drain, 1);
+    ctl->abort_w = 0;
+    mbar_fence_init();
+  }
+  if (warp == 2) {
+    tmem_alloc(&ctl->tmem_base, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = ctl->tmem_base;
+  volatile int* abort_w = &ctl->abort_w;
+  auto give_up = [&](int code) {
+    ctl->abort_w = 1;
+    atomicExch(err, code);
+  };
+  const int rot = (int)(blockIdx.x % nkc);   // CTAs start on different chunks
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    tma_prefetch(&mapX);
+    tma_prefetch(&mapC);
+    tma_prefetch(&mapH);
+    uint32_t nx = 0, nh = 0, nc = 0;
+    bool ok = true;
+    for (int mt = blockIdx.x; mt < n_mt && ok && !*abort_w; mt += gridDim.x) {
+      {
+        const int b = nx & 1;
+        if (!mbar_wait(&ctl->x_empty[b], ((nx >> 1) & 1) ^ 1, abort_w)) { give_up(61); break; }
+        mbar_expect_tx(&ctl->x_full[b], XT);
+        tma_load_2d(sm + OFF_X + b * XT, &mapX, &ctl->x_full[b], 0, mt * 128);
+        ++nx;
+      }
+      for (int kk = 0; kk < nkc && ok; ++kk) {
+        const int kc = kk + rot < nkc ? kk + rot : kk + rot - nkc;
+        {
+          const int b = nh & 1;
+          if (!mbar_wait(&ctl->h_empty[b], ((nh >> 1) & 1) ^ 1, abort_w)) { give_up(62); ok = false; break; }
+          unsigned char* hb = sm + OFF_H + b * HT;
+          mbar_expect_tx(&ctl->h_full[b], HT);
+          tma_load_2d(hb, &mapH, &ctl->h_full[b], kc * 64, mt * 128);
+          tma_load_2d(hb + HT / 2, &mapH, &ctl->h_full[b], kc * 64 + 32, mt * 128);
+          ++nh;
+        }
+        for (int jp = 0; jp < np2; ++jp) {
+          const int b = nc & 1;
+          if (!mbar_wait(&ctl->c_empty[b], ((nc >> 1) & 1) ^ 1, abort_w)) { give_up(63); ok = false; break; }
+          unsigned char* cb = sm + OFF_C + b * CBLK;
+          mbar_expect_tx(&ctl->c_full[b], NR * 128);
+          const int y0 = (kc * np2 + jp) * 512;
+#pragma unroll
+          for (int r = 0; r < NR; r += 128) tma_load_2d(cb + r * 128, &mapC, &ctl->c_full[b], 0, y0 + r);
+          ++nc;
+        }
+      }
+    }
+    for (int b = 0; b < 2; ++b) {
+      if ((nx + 1 - b) / 2) mbar_wait_drain(&ctl->x_full[b], (((nx + 1 - b) / 2) - 1) & 1);
+      if ((nh + 1 - b) / 2) mbar_wait_drain(&ctl->h_full[b], (((nh + 1 - b) / 2) - 1) & 1);
+      if ((nc + 1 - b) / 2) mbar_wait_drain(&ctl->c_full[b], (((nc + 1 - b) / 2) - 1) & 1);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    constexpr uint32_t idesc = idesc_bf16_f32(128, 128);
+    uint32_t nx = 0, nc = 0;
+    bool ok = true;
+    for (int mt = blockIdx.x; mt < n_mt && ok && !*abort_w; mt += gridDim.x) {
+      const int bx = nx & 1;
+      if (!mbar_wait(&ctl->x_full[bx], (nx >> 1) & 1, abort_w)) { give_up(64); break; }
+      const uint32_t xa = smem_u32(sm + OFF_X + bx * XT);
+      const int units = nkc * np2;
+      for (int un = 0; un < units && ok; ++un) {
+        const int b = nc & 1;
+        const uint32_t ph = (nc >> 1) & 1;
+        if (!mbar_wait(&ctl->c_full[b], ph, abort_w) ||
+            !mbar_wait(&ctl->s_empty[b], ph ^ 1, abort_w)) { give_up(65); ok = false; break; }
+        tc_fence_after();
+        const uint32_t cb = smem_u32(sm + OFF_C + b * CBLK);
+        const uint32_t ta = tmem + 256 * b, tb = ta + 128;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const uint64_t ad = sdesc_sw128(xa + k * 32);
+          umma_bf16(ta, ad, sdesc_sw128(cb + k * 32), idesc, k > 0 ? 1u : 0u);
+          if (!AEXACT) umma_bf16(ta, ad, sdesc_sw128(cb + 3 * 16384 + k * 32), idesc, 1u);
+          umma_bf16(tb, ad, sdesc_sw128(cb + 16384 + k * 32), idesc, k > 0 ? 1u : 0u);
+          umma_bf16(tb, ad, sdesc_sw128(cb + 2 * 16384 + k * 32), idesc, 1u);
+        }
+        umma_commit(&ctl->c_empty[b]);
+        umma_commit(&ctl->s_full[b]);
+        ++nc;
+      }
+      umma_commit(&ctl->x_empty[bx]);
+      ++nx;
+    }
+    umma_commit(&ctl->drain);
+    mbar_wait_drain(&ctl->drain, 0);
+  } else if (warp >= 4) {
+    // ---------------- epilogue: row r = TMEM lane, probe 2 jp + half of every pair
+    const int quad = warp & 3, half = (warp - 4) >> 2;
+    const int r = quad * 32 + lane;
+    const uint32_t lanes = (uint32_t)(quad * 32) << 16;
+    uint32_t nh = 0, nc = 0;
+    bool ok = true;
+    for (int mt = blockIdx.x; mt < n_mt && ok && !*abort_w; mt += gridDim.x) {
+      float sum[NP2MAX][3];
+#pragma unroll
+      for (int jp = 0; jp < NP2MAX; ++jp) sum[jp][0] = sum[jp][1] = sum[jp][2] = 0.0f;
+      for (int kk = 0; kk < nkc && ok; ++kk) {
+        const int hb = nh & 1;
+        if (!mbar_wait(&ctl->h_full[hb], (nh >> 1) & 1, abort_w)) {
+          give_up(66);
+          ok = false;
+          break;
+        }
+        const unsigned char* hrow = sm + OFF_H + hb * HT + r * 128;
+#pragma unroll
+        for (int jp = 0; jp < NP2MAX; ++jp) {
+          if (jp < np2 && ok) {
+            const int b = nc & 1;
+            if (!mbar_wait(&ctl->s_full[b], (nc >> 1) & 1, abort_w)) {
+              give_up(67);
+              ok = false;
+            } else {
+              ++nc;
+              tc_fence_after();
+              const uint32_t ta = tmem + lanes + 256 * b + 64 * half, tb = ta + 128;
+#pragma unroll
+              for (int box = 0; box < 2; ++box) {
+                uint32_t ra[32], rb[32];
+                tmem_ld32_async(ta + box * 32, ra);
+                tmem_ld32_async(tb + box * 32, rb);
+                tmem_wait_ld();
+                qf_box(ra, rb, hrow + box * (HT / 2), r, sum[jp][0], sum[jp][1], sum[jp][2]);
+              }
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(&ctl->s_empty[b]);
+            }
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ctl->h_empty[hb]);
+        ++nh;
+      }
+      if (!ok) break;
+      float q = 0.0f;
+#pragma unroll
+      for (int jp = 0; jp < NP2MAX; ++jp)
+        if (jp < np2) q += sum[jp][0] - sum[jp][1] * sum[jp][2];
+      const int64_t row = (int64_t)mt * 128 + r;
+      if (row >= m && row < N) atomicAdd(g + (row - m), -gscale * q);
+    }
+  }
+  __syncthreads();
+  if (warp == 2) {
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+// Coefficient blocks of k_tc_qf, block (kc, jp) = 512 rows of 64 bf16 features:
+//   rows [0, 128) A hi | [128, 256) B hi | [256, 384) B lo | [384, 512) A lo; in each part rows
+//   0-63 are probe 2 jp, 64-127 probe 2 jp + 1, class kc 64 + (row mod 64).
+// A~ = A minus its class mean (amean; A as is when amean is null), B~ likewise; zero for classes
+// >= c, probes >= s and features >= d.
+__global__ void k_build_qcoef(bf16* Cf, const float* A, const float* B, const float* amean,
+                              const float* bmean, int s, int c, int d, int64_t D, int np2) {
+  const int blk = blockIdx.x;
+  const int kc = blk / np2, jp = blk - kc * np2;
+  for (int idx = threadIdx.x; idx < 512 * 64; idx += blockDim.x) {
+    const int row = idx >> 6, e = idx & 63;
+    const int part = row >> 7, rr = row & 127;
+    const int j = 2 * jp + (rr >> 6), k = kc * 64 + (rr & 63);
+    const bool isb = part == 1 || part == 2;
+    float v = 0.0f;
+    if (j < s && k < c && e < d) {
+      const float* src = isb ? B : A;
+      const float* mn = isb ? bmean : amean;
+      v = src[(int64_t)j * D + (int64_t)k * d + e] - (mn ? mn[j * d + e] : 0.0f);
+    }
+    const bf16 hi = __float2bfloat16_rn(v);
+    Cf[((int64_t)blk * 512 + row) * 64 + e] =
+        (part == 2 || part == 3) ? __float2bfloat16_rn(v - __bfloat162float(hi)) : hi;
+  }
+}
+
+// q via k_tc_qf (d <= 64, not pooled, c a multiple of 4, s <= 16).  aexact: A is the problem's
+// probe block (entries +-1, exact in bf16).
+static int32_t tc_quad_qf(firal_problem* P, const float* A, const float* B, int s, double scale,
+                          float* g, bool aexact) {
+  using namespace qf_cfg;
+  cudaStream_t st = P->H->stream;
+  const int c = P->c, d = P->d;
+  const int64_t Np = P->Np;
+  const int nkc = P->cp / 64, np2 = (s + 1) / 2;
+  FIRAL_TRY(P->vmean.ensure((size_t)2 * s * d * sizeof(float)));
+  float* meanA = P->vmean.as<float>();
+  float* meanB = meanA + (size_t)s * d;
+  const int64_t crow = (int64_t)nkc * np2 * 512;
+  FIRAL_TRY(P->gq_m.ensure((size_t)crow * 64 * 2));
+  ProfScope ps(st, PF_QUAD);
+  count_launch(aexact ? 3 : 4);
+  if (!aexact) k_class_mean<<<s, 1024, 0, st>>>(A, s, c, d, P->D, meanA, P->pt);
+  k_class_mean<<<s, 1024, 0, st>>>(B, s, c, d, P->D, meanB, P->pt);
+  k_build_qcoef<<<(unsigned)(nkc * np2), 256, 0, st>>>(P->gq_m.as<bf16>(), A, B,
+                                                      aexact ? nullptr : meanA, meanB, s, c, d,
+                                                      P->D, np2);
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  static bool attr[2] = {false, false};
+  if (!attr[aexact]) {
+    if (aexact)
+      FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tc_qf<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
+    else
+      FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tc_qf<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
+    attr[aexact] = true;
+  }
+  CUtensorMap mX, mC, mH;
+  FIRAL_TRY(make_map(&mX, P->Xb.p, Np, 64, 128, 64, true));
+  FIRAL_TRY(make_map(&mC, P->gq_m.p, crow, 64, 128, 64, true));
+  FIRAL_TRY(make_map_f32(&mH, P->Ha.p, P->N, c, 128));
+  FIRAL_CUDA_TRY(cudaMemsetAsync(g, 0, (size_t)P->n * sizeof(float), st));
+  const int n_mt = (int)(Np / 128);
+  const int grid = std::min(n_mt, P->sms);
+  if (aexact)
+    k_tc_qf<true><<<grid, 384, SMEM, st>>>(mX, mC, mH, g, P->N, P->m, n_mt, nkc, np2,
+                                           (float)(scale / s), tc_error_word(P));
+  else
+    k_tc_qf<false><<<grid, 384, SMEM, st>>>(mX, mC, mH, g, P->N, P->m, n_mt, nkc, np2,
+                                            (float)(scale / s), tc_error_word(P));
+  FIRAL_CUDA_TRY(cudaGetLastError());
+  return FIRAL_OK;
+}
+
 template <int DP>
 static int32_t tc_quad_t(firal_problem* P, const float* A, const float* B, int s, double scale,
                          float* g) {
@@ -2723,6 +3040,10 @@ static int32_t tc_quad_t(firal_problem* P, const float* A, const float* B, int s
   const int cp = P->cp, c = P->c, d = P->d;
   const int64_t D = P->D;
   const int sms = P->sms;
+  // d <= 64, many classes, s <= 16: probe pairs per MMA (k_tc_qf); the MD step's first
+  // operand is the probe block itself, exact in bf16
+  if (DP == 64 && !P->pt.Q && (c % 4) == 0 && s <= qf_cfg::NP2MAX * 2)
+    return tc_quad_qf(P, A, B, s, scale, g, A == P->V.as<float>());
   // probe block [A; B] (2s columns) and its class means
   FIRAL_TRY(P->gq_ab.ensure((size_t)2 * s * D * sizeof(float)));
   float* AB = P->gq_ab.as<float>();
