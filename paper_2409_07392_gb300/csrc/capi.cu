@@ -1326,7 +1326,7 @@ int32_t firal_problem_destroy(firal_problem* P) {
                   &P->cen_idx, &P->Ub, &P->UbT, &P->cen_am, &P->cen_rho, &P->cen_lab, &P->cen_items, &P->cen_part,
                   &P->pool_tabs, &P->pool_z, &P->md_part, &P->kr_alpha, &P->kr_dterm,
                   &P->kr_bsum, &P->bcg, &P->pw_pool, &P->pw_seg, &P->pw_pseg, &P->pw_pk,
-                  &P->pw_part, &P->X64, &P->S_lab, &P->w_lab}) {
+                  &P->pw_part, &P->X64, &P->S_lab, &P->w_lab, &P->cm_scr}) {
     if (synced) b->park();
     else b->release();
   }

@@ -236,6 +236,8 @@ struct firal_problem {
   // fast mixed mode: the labelled rows' diagonal-part block sums (weight 1 in every Sigma_z,
   // so computed once, as three bf16 products) and their weights (1 on those rows, 0 after)
   firal::DBuf S_lab, w_lab;
+  firal::DBuf cm_scr;   // class means over many classes: split partials (f64), then tickets
+  int cm_np = 0;        // probes cm_scr has room for
   bool slab_ready = false;
   int rtab_d = -1, rtab_chunks = 0;
   int32_t dp = 0, cp = 0;

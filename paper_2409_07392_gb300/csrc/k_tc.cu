@@ -432,27 +432,74 @@ __global__ void k_split_probes(bf16* Pt, const float* P, const float* vmean, int
 // with P_N V = the class mean of V replicated over classes (exact in real arithmetic).
 // ------------------------------------------------------------------------------------------
 // mean[j][p][e] = mean over the classes k of pool p of V[j][k][e] (all classes for an ordinary
-// problem); one block per (probe, pool), 1024 threads = (class group, e), the groups combined
-// in a fixed order (deterministic)
+// problem).  Block (probe j and pool p, split g of G): 1024 threads = (class group, e) over its
+// share of the classes, the groups combined in a fixed order.  With G > 1 each split writes a
+// partial (part), and the last split of (j, p) to finish (a ticket in cnt, reset by it) adds
+// the partials in split order: deterministic, and no other launch.
 __global__ void k_class_mean(const float* V, int s, int c, int d, int64_t D, float* mean,
-                             PoolTab pt) {
-  __shared__ double part[1024];
+                             PoolTab pt, double* part, unsigned* cnt) {
+  __shared__ double red[1024];
+  __shared__ bool last;
   const int Qe = pool_count(pt);
-  const int j = blockIdx.x / Qe, p = blockIdx.x - j * Qe;
+  const int jp = blockIdx.x, j = jp / Qe, p = jp - j * Qe;
+  const int g = blockIdx.y, G = gridDim.y;
   const int k0 = pt.Q ? pt.coff[p] : 0, k1 = pt.Q ? pt.coff[p + 1] : c;
+  const int len = (k1 - k0 + G - 1) / G;
+  const int kb = k0 + g * len, ke = kb + len < k1 ? kb + len : k1;
   const int dpad = (d + 31) / 32 * 32;
   const int groups = 1024 / dpad;
-  const int e = threadIdx.x % dpad, g = threadIdx.x / dpad;
+  const int e = threadIdx.x % dpad, gr = threadIdx.x / dpad;
   double acc = 0.0;
-  if (e < d && g < groups)
-    for (int k = k0 + g; k < k1; k += groups) acc += (double)V[(int64_t)j * D + (int64_t)k * d + e];
-  part[threadIdx.x] = acc;
+  if (e < d && gr < groups)
+    for (int k = kb + gr; k < ke; k += groups) acc += (double)V[(int64_t)j * D + (int64_t)k * d + e];
+  red[threadIdx.x] = acc;
   __syncthreads();
-  if (threadIdx.x < d) {
-    double tot = 0.0;
-    for (int q = 0; q < groups; ++q) tot += part[q * dpad + threadIdx.x];
-    mean[(j * Qe + p) * d + threadIdx.x] = (float)(tot / (k1 - k0));
+  double tot = 0.0;
+  if (threadIdx.x < d)
+    for (int q = 0; q < groups; ++q) tot += red[q * dpad + threadIdx.x];
+  if (G == 1) {
+    if (threadIdx.x < d) mean[jp * d + threadIdx.x] = (float)(tot / (k1 - k0));
+    return;
   }
+  if (threadIdx.x < d) part[((int64_t)jp * G + g) * d + threadIdx.x] = tot;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&cnt[jp], 1u) == (unsigned)(G - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x < d) {
+    double t = 0.0;
+    for (int q = 0; q < G; ++q) t += __ldcg(&part[((int64_t)jp * G + q) * d + threadIdx.x]);
+    mean[jp * d + threadIdx.x] = (float)(t / (k1 - k0));
+  }
+  if (threadIdx.x == 0) cnt[jp] = 0u;
+}
+
+// Class means of the s probes of V into mean (s x pools x d): ordinary problems with many
+// classes split each probe's classes over CM_SPLIT blocks.
+constexpr int CM_SPLIT = 8;
+static int32_t class_mean(firal_problem* P, const float* V, int s, float* mean, cudaStream_t st) {
+  const int Qe = pool_count(P->pt);
+  const int G = (P->pt.Q == 0 && P->c >= 256) ? CM_SPLIT : 1;
+  double* part = nullptr;
+  unsigned* cnt = nullptr;
+  if (G > 1) {
+    // partials then tickets for cm_np probes (at least 512); the tickets are zeroed when the
+    // buffer is (re)allocated, and every launch leaves them zero
+    if (P->cm_np < s) {
+      const int np = s > 512 ? s : 512;
+      const size_t bytes = (size_t)np * (CM_SPLIT * P->d * sizeof(double) + sizeof(unsigned));
+      FIRAL_TRY(P->cm_scr.ensure(bytes));
+      FIRAL_CUDA_TRY(cudaMemsetAsync(P->cm_scr.p, 0, bytes, st));
+      P->cm_np = np;
+    }
+    part = P->cm_scr.as<double>();
+    cnt = reinterpret_cast<unsigned*>(part + (size_t)P->cm_np * CM_SPLIT * P->d);
+  }
+  k_class_mean<<<dim3((unsigned)(s * Qe), (unsigned)G), 1024, 0, st>>>(V, s, P->c, P->d, P->D,
+                                                                      mean, P->pt, part, cnt);
+  return FIRAL_OK;
 }
 
 // out = out - qmean + lam_null * vmean (per class block); pq[j c + k] = <V_j[k], out_j[k]>
@@ -1691,43 +1738,59 @@ __global__ void __launch_bounds__(256, 1)
 // Z[p][i] = x_ie x_ie' for pair p = (e, e') of the row-major triangle, as bf16 hi and lo (exact);
 // rows p >= npairs and columns of padding points are zero.  K-block-major layout
 // [i / 64][p][i % 64] (npp rows per block): every 128 x 64 TMA tile is one contiguous 16 KB
-// run.  Block = 64 points x 128 pairs; the block's pair indices and its points' features
-// (feature-major) are staged in shared memory.
-__global__ void k_build_z(bf16* Zhi, bf16* Zlo, const bf16* Xb, int d, int dp, int npairs,
-                          int64_t npp) {
-  __shared__ bf16 xs[128 * 64];    // feature-major: xs[e * 64 + point]
-  __shared__ short pe[128], pe2[128];
+// run.  Block = 64 points (staged point-major in shared memory) x every pair; a thread takes
+// pairs p, p + 256, ... (consecutive threads read consecutive e' of the staged rows) and
+// writes each pair's 64 points as four 32-byte pieces.
+__global__ void __launch_bounds__(256) k_build_z(bf16* Zhi, bf16* Zlo, const bf16* Xb, int d,
+                                                 int dp, int npairs, int64_t npp) {
+  __shared__ __align__(16) bf16 xs[64 * 128];
   const int64_t i0 = (int64_t)blockIdx.x * 64;
-  const int p0 = blockIdx.y * 128;
-  for (int t = threadIdx.x; t < 64 * dp; t += blockDim.x) {
-    const int i = t / dp, e = t - i * dp;
-    xs[e * 64 + i] = Xb[i0 * dp + t];
-  }
-  if (threadIdx.x < 128 && p0 + (int)threadIdx.x < npairs) {
-    int e, e2;
-    pair_of(p0 + threadIdx.x, d, e, e2);
-    pe[threadIdx.x] = (short)e;
-    pe2[threadIdx.x] = (short)e2;
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(Xb + i0 * dp);
+    uint4* dst = reinterpret_cast<uint4*>(xs);
+    for (int t = threadIdx.x; t < 64 * dp / 8; t += blockDim.x) dst[t] = src[t];
   }
   __syncthreads();
-  for (int item = threadIdx.x; item < 128 * 8; item += blockDim.x) {
-    const int pl = item >> 3, c8 = item & 7, p = p0 + pl;
-    uint4 hv = make_uint4(0, 0, 0, 0), lv = make_uint4(0, 0, 0, 0);
-    if (p < npairs) {
-      const bf16* xa = xs + pe[pl] * 64 + c8 * 8;
-      const bf16* xb = xs + pe2[pl] * 64 + c8 * 8;
-      bf16* h = reinterpret_cast<bf16*>(&hv);
-      bf16* l = reinterpret_cast<bf16*>(&lv);
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const float z = __bfloat162float(xa[q]) * __bfloat162float(xb[q]);
-        h[q] = __float2bfloat16_rn(z);
-        l[q] = __float2bfloat16_rn(z - __bfloat162float(h[q]));
-      }
+  const int d2 = 2 * d + 1;
+  for (int p = threadIdx.x; p < npp; p += blockDim.x) {
+    // row e of the triangle: the largest e with e d - e (e - 1) / 2 <= p
+    int e = 0, e2 = 0;
+    const bool real = p < npairs;
+    if (real) {
+      e = (int)((d2 - sqrtf((float)(d2 * d2 - 8 * p))) * 0.5f);
+      e = e < 0 ? 0 : (e >= d ? d - 1 : e);
+      while (e > 0 && e * d - e * (e - 1) / 2 > p) --e;
+      while (e + 1 < d && (e + 1) * d - (e + 1) * e / 2 <= p) ++e;
+      e2 = e + (p - (e * d - e * (e - 1) / 2));
     }
-    const int64_t o = ((int64_t)blockIdx.x * npp + p) * 64 + c8 * 8;
-    *reinterpret_cast<uint4*>(Zhi + o) = hv;
-    *reinterpret_cast<uint4*>(Zlo + o) = lv;
+    bf16* zh = Zhi + ((int64_t)blockIdx.x * npp + p) * 64;
+    bf16* zl = Zlo + ((int64_t)blockIdx.x * npp + p) * 64;
+#pragma unroll 1
+    for (int c16 = 0; c16 < 4; ++c16) {
+      uint4 hv[2], lv[2];
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        hv[hh] = make_uint4(0, 0, 0, 0);
+        lv[hh] = make_uint4(0, 0, 0, 0);
+        if (real) {
+          bf16* h = reinterpret_cast<bf16*>(&hv[hh]);
+          bf16* l = reinterpret_cast<bf16*>(&lv[hh]);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int i = c16 * 16 + hh * 8 + q;
+            const float z = __bfloat162float(xs[i * dp + e]) * __bfloat162float(xs[i * dp + e2]);
+            h[q] = __float2bfloat16_rn(z);
+            l[q] = __float2bfloat16_rn(z - __bfloat162float(h[q]));
+          }
+        }
+      }
+      uint4* oh = reinterpret_cast<uint4*>(zh + c16 * 16);
+      uint4* ol = reinterpret_cast<uint4*>(zl + c16 * 16);
+      oh[0] = hv[0];
+      oh[1] = hv[1];
+      ol[0] = lv[0];
+      ol[1] = lv[1];
+    }
   }
 }
 
@@ -2265,7 +2328,7 @@ int32_t tc_prepare(firal_problem* P) {
   const int npairs = P->d * (P->d + 1) / 2;
   const int64_t npp = (npairs + b_cfg::BN - 1) / b_cfg::BN * b_cfg::BN;
   FIRAL_TRY(P->Zp.ensure((size_t)2 * npp * Np * 2));
-  k_build_z<<<dim3((unsigned)(Np / 64), (unsigned)(npp / 128)), 256, 0, st>>>(
+  k_build_z<<<(unsigned)(Np / 64), 256, 0, st>>>(
       P->Zp.as<bf16>(), P->Zp.as<bf16>() + npp * Np, P->Xb.as<bf16>(), P->d, P->dp, npairs, npp);
   count_launch();
   FIRAL_CUDA_TRY(cudaGetLastError());
@@ -2299,7 +2362,7 @@ static int32_t tc_apply_t(firal_problem* P, const float* w, const float* Sblk, c
   {
   ProfScope ps(st, PF_SPLIT);
   count_launch(2);
-  k_class_mean<<<s * Qe, 1024, 0, st>>>(V, s, P->c, P->d, P->D, P->vmean.as<float>(), P->pt);
+  FIRAL_TRY(class_mean(P, V, s, P->vmean.as<float>(), st));
   k_split_probes<NPART><<<dim3((unsigned)(cp + 31) / 32, DP / 32 > 0 ? DP / 32 : 1, s), dim3(32, 8), 0,
                    st>>>(P->Pb.as<bf16>(), V, P->vmean.as<float>(), s, P->c, P->d, DP, cp,
                            P->D, P->pt);
@@ -2444,7 +2507,7 @@ static int32_t tc_apply_t(firal_problem* P, const float* w, const float* Sblk, c
     FIRAL_TRY(shard_allreduce(P, out, (int64_t)s * P->D, FIRAL_DT_F32, 0));
     ProfScope ps(st, PF_COMBINE);
     count_launch(2);
-    k_class_mean<<<s * Qe, 1024, 0, st>>>(out, s, P->c, P->d, P->D, P->qmean.as<float>(), P->pt);
+    FIRAL_TRY(class_mean(P, out, s, P->qmean.as<float>(), st));
     k_project<<<dim3(P->c, (s + 3) / 4), mthreads, 0, st>>>(
         out, P->qmean.as<float>(), P->vmean.as<float>(), V, lam_null, s, P->c, P->d, P->D, pq,
         P->pt);
@@ -3000,8 +3063,8 @@ static int32_t tc_quad_qf(firal_problem* P, const float* A, const float* B, int 
   FIRAL_TRY(P->gq_m.ensure((size_t)crow * 64 * 2));
   ProfScope ps(st, PF_QUAD);
   count_launch(aexact ? 3 : 4);
-  if (!aexact) k_class_mean<<<s, 1024, 0, st>>>(A, s, c, d, P->D, meanA, P->pt);
-  k_class_mean<<<s, 1024, 0, st>>>(B, s, c, d, P->D, meanB, P->pt);
+  if (!aexact) FIRAL_TRY(class_mean(P, A, s, meanA, st));
+  FIRAL_TRY(class_mean(P, B, s, meanB, st));
   k_build_qcoef<<<(unsigned)(nkc * np2), 256, 0, st>>>(P->gq_m.as<bf16>(), A, B,
                                                       aexact ? nullptr : meanA, meanB, s, c, d,
                                                       P->D, np2);
@@ -3054,7 +3117,7 @@ static int32_t tc_quad_t(firal_problem* P, const float* A, const float* B, int s
   FIRAL_TRY(P->vmean.ensure((size_t)2 * s * Qe * d * sizeof(float)));
   ProfScope ps(st, PF_QUAD);
   count_launch(1);
-  k_class_mean<<<2 * s * Qe, 1024, 0, st>>>(AB, 2 * s, c, d, D, P->vmean.as<float>(), P->pt);
+  FIRAL_TRY(class_mean(P, AB, 2 * s, P->vmean.as<float>(), st));
   if (DP >= 64 && !P->pt.Q && (c % 4) == 0) {
     // a_ijk = x_i.A_j[:,k], b_ijk = x_i.B_j[:,k] on tensor cores (K = features, x exact in
     // bf16, A and B as hi + lo); the epilogue forms sum_k h a b - (sum_k h a)(sum_k h b)
@@ -4003,7 +4066,7 @@ static int32_t tc_apply_pw_t(firal_problem* P, const float* w, const float* V, i
   FIRAL_CUDA_TRY(cudaGetLastError());
   FIRAL_TRY(shard_allreduce(P, out, (int64_t)s * P->D, FIRAL_DT_F32, 0));
   const int mthreads = (d + 31) / 32 * 32;
-  k_class_mean<<<s * Qe, 1024, 0, st>>>(out, s, c, d, P->D, P->qmean.as<float>(), P->pt);
+  FIRAL_TRY(class_mean(P, out, s, P->qmean.as<float>(), st));
   k_project<<<dim3(c, (s + 3) / 4), mthreads, 0, st>>>(out, P->qmean.as<float>(),
                                                        P->vmean.as<float>(), V, lam, s, c, d,
                                                        P->D, pq, P->pt);
