@@ -38,67 +38,82 @@ __device__ double block_sum_d(double v, double* red) {
 // ------------------------------------------------------------------------------------------
 // Cholesky + inverse of c blocks
 // ------------------------------------------------------------------------------------------
+// Shared-memory layout: the block in rows of ld = d + 1 doubles (an odd stride: the threads of
+// a half-warp reading one column each hit distinct banks).  The factor L fills the lower
+// triangle; Y = L^{-1} goes to the strict upper triangle transposed (Y[i][c], i > c, at row c,
+// column i) with its diagonal in yd.  TPR = blockDim / d threads (at least 1) share each row or
+// column, so no index is divided by a run-time size.
 template <class T>
 __global__ void k_chol_inv(const double* __restrict__ A, int d, T* __restrict__ inv_t,
                            double* __restrict__ inv_d, double* __restrict__ L_out,
                            int32_t* not_spd) {
   extern __shared__ double sh[];
-  double* Ls = sh;             // d*d
-  double* yd = sh + d * d;     // d
+  const int ld = d + 1;
+  double* Ls = sh;              // d x ld
+  double* yd = sh + d * ld;     // d
   const int k = blockIdx.x, tid = threadIdx.x, bd = blockDim.x;
+  const int tpr = bd >= d ? bd / d : 1;
+  const int row = tid % d, ph = tid / d;        // this thread's row (or column) and phase
+  const bool act = ph < tpr;
   const double* Ak = A + (int64_t)k * d * d;
-  for (int t = tid; t < d * d; t += bd) Ls[t] = Ak[t];
+  for (int i = 0; i < d; ++i)
+    for (int e = tid; e < d; e += bd) Ls[i * ld + e] = Ak[(int64_t)i * d + e];
   __syncthreads();
+  // right-looking Cholesky: pivot, column below it, trailing lower triangle
   for (int j = 0; j < d; ++j) {
     if (tid == 0) {
-      double v = Ls[j * d + j];
+      double v = Ls[j * ld + j];
       if (!(v > 0.0)) {
         atomicExch(not_spd, 1);
         v = fabs(v) > 1e-300 ? fabs(v) : 1e-300;
       }
-      Ls[j * d + j] = sqrt(v);
+      Ls[j * ld + j] = sqrt(v);
+      yd[j] = 1.0 / Ls[j * ld + j];
     }
     __syncthreads();
-    const double ljj = Ls[j * d + j];
-    for (int i = j + 1 + tid; i < d; i += bd) Ls[i * d + j] /= ljj;
+    const double rjj = yd[j];   // FP64 division is several FMAs: one per pivot
+    for (int i = j + 1 + tid; i < d; i += bd) Ls[i * ld + j] *= rjj;
     __syncthreads();
-    const int rem = d - j - 1;
-    for (int t = tid; t < rem * rem; t += bd) {
-      const int ii = j + 1 + t / rem, kk = j + 1 + t % rem;
-      if (kk <= ii) Ls[ii * d + kk] -= Ls[ii * d + j] * Ls[kk * d + j];
+    if (act && row > j) {
+      const double lij = Ls[row * ld + j];
+      for (int kk = j + 1 + ph; kk <= row; kk += tpr) Ls[row * ld + kk] -= lij * Ls[kk * ld + j];
     }
     __syncthreads();
   }
   if (L_out) {
-    for (int t = tid; t < d * d; t += bd) {
-      const int i = t / d, jj = t % d;
-      L_out[(int64_t)k * d * d + t] = jj <= i ? Ls[t] : 0.0;
-    }
+    for (int i = 0; i < d; ++i)
+      for (int e = tid; e < d; e += bd)
+        L_out[(int64_t)k * d * d + (int64_t)i * d + e] = e <= i ? Ls[i * ld + e] : 0.0;
   }
-  __syncthreads();
   if (!inv_t && !inv_d) return;
-  // Y = L^{-1}: column col by forward substitution; y[i] (i > col) kept in Ls[col][i]
-  for (int col = tid; col < d; col += bd) {
-    yd[col] = 1.0 / Ls[col * d + col];
-    for (int i = col + 1; i < d; ++i) {
-      double acc = Ls[i * d + col] * yd[col];
-      for (int p = col + 1; p < i; ++p) acc += Ls[i * d + p] * Ls[col * d + p];
-      Ls[col * d + i] = -acc / Ls[i * d + i];
+  // Y = L^{-1} by rows: Y[i][c] = -(L[i][c] Y[c][c] + sum_{c < p < i} L[i][p] Y[p][c]) Y[i][i],
+  // Y[i][i] = 1 / L[i][i] (yd, from the factorisation)
+  for (int i = 1; i < d; ++i) {
+    for (int c = tid; c < i; c += bd) {
+      double acc = Ls[i * ld + c] * yd[c];
+      for (int p = c + 1; p < i; ++p) acc += Ls[i * ld + p] * Ls[c * ld + p];
+      Ls[c * ld + i] = -acc * yd[i];
     }
+    __syncthreads();
   }
-  __syncthreads();
-  // A^{-1}[a][b] = sum_{i >= max(a,b)} Y[i][a] Y[i][b]
-  for (int t = tid; t < d * d; t += bd) {
-    const int a = t / d, b = t % d;
-    const int lo = a > b ? a : b;
-    double acc = 0.0;
-    for (int i = lo; i < d; ++i) {
-      const double ya = i == a ? yd[a] : Ls[a * d + i];
-      const double yb = i == b ? yd[b] : Ls[b * d + i];
-      acc += ya * yb;
+  // A^{-1}[a][b] = sum_{i >= max(a,b)} Y[i][a] Y[i][b]: thread (column b, phase) takes
+  // a = ph, ph + TPR, ... <= b and writes both (a, b) and (b, a)
+  if (act) {
+    const int b = row;
+    for (int a = ph; a <= b; a += tpr) {
+      double acc = (a == b ? yd[a] : Ls[a * ld + b]) * yd[b];
+      for (int i = b + 1; i < d; ++i) acc += Ls[a * ld + i] * Ls[b * ld + i];
+      const int64_t o1 = (int64_t)k * d * d + (int64_t)a * d + b;
+      const int64_t o2 = (int64_t)k * d * d + (int64_t)b * d + a;
+      if (inv_t) {
+        inv_t[o1] = (T)acc;
+        inv_t[o2] = (T)acc;
+      }
+      if (inv_d) {
+        inv_d[o1] = acc;
+        inv_d[o2] = acc;
+      }
     }
-    if (inv_t) inv_t[(int64_t)k * d * d + t] = (T)acc;
-    if (inv_d) inv_d[(int64_t)k * d * d + t] = acc;
   }
 }
 
@@ -111,8 +126,10 @@ static int threads_for(int d) {
 
 int32_t chol_inv(bool dbl, const double* A, int c, int d, void* inv_t, double* inv_d,
                  double* L_out, int32_t* not_spd, cudaStream_t st) {
-  const size_t smem = ((size_t)d * d + d) * sizeof(double);
+  const size_t smem = ((size_t)d * (d + 1) + d) * sizeof(double);
   const int thr = threads_for(d);
+  if (smem > 200 * 1024 || thr < d)
+    return fail(FIRAL_ERR_UNSUPPORTED, "block factorisation needs d <= 158");
   ProfScope ps(st, PF_CHOL);
   count_launch();
   if (dbl) {

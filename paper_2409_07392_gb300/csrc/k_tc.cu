@@ -2785,25 +2785,39 @@ static int32_t ensure_hlo(firal_problem* P) {
 // with A~ and B~ as bf16 hi + lo, except an A that is the probe block itself: its entries
 // (+-1) are exact in bf16 and it needs neither a low part nor the class-mean projection (the
 // forms are unchanged by adding a per-row constant to a, since the row's h sums to one).
-// Epilogue: 8 warps, warp (quarter, half) takes TMEM lanes of its quarter and probe 2 jp + half;
-// per probe the running sums sum_k h a b, sum_k h a, sum_k h b over the chunks stay in
-// registers (the h tile of a chunk is loaded once, for all its probe pairs), and after the
-// last chunk q = sum_j (sum h a b - (sum h a)(sum h b)); the two halves' shares of a row go to
-// g as two atomic adds on zeroed memory (the sum of two addends does not depend on order).
-// Pipeline: double-buffered x tile, h tile, coefficient blocks and TMEM accumulators.
+// Epilogue: 8 warps; per probe the running sums sum_k h a b, sum_k h a, sum_k h b over the
+// chunks stay in registers, and after the last chunk q = sum_j (sum h a b - (sum h a)(sum h b)).
+// Each row's q reaches g as two atomic adds on zeroed memory (the sum of two addends does not
+// depend on order).  General A: warp (quarter, half) takes TMEM lanes of its quarter and
+// probe 2 jp + half, reading the chunk's h tile from shared memory for each pair.  Exact A:
+// warp (quarter, box) takes class box `box` (32 classes) of both probes, with the box's h in
+// registers for all the chunk's pairs, so the h tile is released as soon as it is read and one
+// h buffer suffices; the freed space holds a third coefficient stage (three units in flight:
+// each 48 KB block feeds only 768 MMA cycles) and the boxes' exchange of per-probe sums.
+// Pipeline: x tile and TMEM accumulators double-buffered; coefficient blocks 2 (general A)
+// or 3 (exact A) deep.
 // ------------------------------------------------------------------------------------------
 namespace qf_cfg {
 constexpr int NP2MAX = 8;                     // probe pairs (s <= 16)
 constexpr int CBLK = 512 * 128;               // coefficient block: up to 4 x 128 rows of 128 B
 constexpr int HT = 128 * 64 * 4;              // f32 h tile, two 128-byte-swizzled boxes
 constexpr int XT = 128 * 128;                 // x tile
-constexpr int OFF_C = 0, OFF_H = 2 * CBLK, OFF_X = OFF_H + 2 * HT, OFF_CTL = OFF_X + 2 * XT;
-constexpr int SMEM = OFF_CTL + 256 + 1024;
+constexpr int QX = 2 * 2 * NP2MAX * 128 * 4;  // box 1's per-probe sums (exact A)
+template <bool AEXACT> struct L {
+  static constexpr int CST = AEXACT ? 384 * 128 : CBLK;   // coefficient stage
+  static constexpr int NCS = AEXACT ? 3 : 2;              // coefficient stages
+  static constexpr int NHB = AEXACT ? 1 : 2;              // h buffers
+  static constexpr int OFF_C = 0, OFF_H = NCS * CST, OFF_X = OFF_H + NHB * HT;
+  static constexpr int OFF_Q = OFF_X + 2 * XT;
+  static constexpr int OFF_CTL = OFF_Q + (AEXACT ? QX : 0);
+  static constexpr int SMEM = OFF_CTL + 256 + 1024;
+};
+static_assert(L<true>::SMEM <= 232448 && L<false>::SMEM <= 232448, "shared memory per CTA");
 }  // namespace qf_cfg
 
 struct QfCtl {   // < 256 bytes
-  uint64_t x_full[2], x_empty[2], h_full[2], h_empty[2], c_full[2], c_empty[2], s_full[2],
-      s_empty[2], drain;
+  uint64_t x_full[2], x_empty[2], h_full[2], h_empty[2], c_full[3], c_empty[3], s_full[2],
+      s_empty[2], drain, q_full, q_empty;
   uint32_t tmem_base;
   int abort_w;
 };
@@ -2837,13 +2851,39 @@ __device__ __forceinline__ void qf_box(const uint32_t (&ra)[32], const uint32_t 
   sb += x0 + x1;
 }
 
+// The same sums with h of the box in registers (16 packed pairs), for probe pairs whose box
+// of 32 classes is handled by one thread: sab over all probes, sa and sb per probe.
+__device__ __forceinline__ void qf_box_reg(const uint32_t (&ra)[32], const uint32_t (&rb)[32],
+                                           const uint64_t (&h2)[16], float& sab, float& sa,
+                                           float& sb) {
+  uint64_t pab = 0, pa = 0, pb = 0;
+#pragma unroll
+  for (int t = 0; t < 16; ++t) {
+    const uint64_t a2 = f2_pack_u(ra[2 * t], ra[2 * t + 1]), b2 = f2_pack_u(rb[2 * t], rb[2 * t + 1]);
+    const uint64_t ha2 = f2_mul(h2[t], a2);
+    pab = f2_fma(ha2, b2, pab);
+    pa = f2_add(pa, ha2);
+    pb = f2_fma(h2[t], b2, pb);
+  }
+  float x0, x1;
+  f2_unpack(pab, x0, x1);
+  sab += x0 + x1;
+  f2_unpack(pa, x0, x1);
+  sa += x0 + x1;
+  f2_unpack(pb, x0, x1);
+  sb += x0 + x1;
+}
+
 template <bool AEXACT>
 __global__ void __launch_bounds__(384, 1)
     k_tc_qf(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapC,
             const __grid_constant__ CUtensorMap mapH, float* __restrict__ g, int64_t N,
             int64_t m, int n_mt, int nkc, int np2, float gscale, int32_t* err) {
   using namespace qf_cfg;
+  using Lc = L<AEXACT>;
   constexpr int NR = AEXACT ? 384 : 512;      // coefficient rows per unit
+  constexpr int NCS = Lc::NCS, NHB = Lc::NHB, CST = Lc::CST;
+  constexpr int OFF_C = Lc::OFF_C, OFF_H = Lc::OFF_H, OFF_X = Lc::OFF_X, OFF_CTL = Lc::OFF_CTL;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   QfCtl* ctl = (QfCtl*)(sm + OFF_CTL);
@@ -2854,11 +2894,15 @@ __global__ void __launch_bounds__(384, 1)
       mbar_init(&ctl->x_empty[b], 1);
       mbar_init(&ctl->h_full[b], 1);
       mbar_init(&ctl->h_empty[b], 8);
-      mbar_init(&ctl->c_full[b], 1);
-      mbar_init(&ctl->c_empty[b], 1);
       mbar_init(&ctl->s_full[b], 1);
       mbar_init(&ctl->s_empty[b], 8);
     }
+    for (int b = 0; b < NCS; ++b) {
+      mbar_init(&ctl->c_full[b], 1);
+      mbar_init(&ctl->c_empty[b], 1);
+    }
+    mbar_init(&ctl->q_full, 4);
+    mbar_init(&ctl->q_empty, 4);
     mbar_init(&ctl->drain, 1);
     ctl->abort_w = 0;
     mbar_fence_init();
@@ -2896,8 +2940,8 @@ __global__ void __launch_bounds__(384, 1)
       for (int kk = 0; kk < nkc && ok; ++kk) {
         const int kc = kk + rot < nkc ? kk + rot : kk + rot - nkc;
         {
-          const int b = nh & 1;
-          if (!mbar_wait(&ctl->h_empty[b], ((nh >> 1) & 1) ^ 1, abort_w)) { give_up(62); ok = false; break; }
+          const int b = (int)(nh % NHB);
+          if (!mbar_wait(&ctl->h_empty[b], ((nh / NHB) & 1) ^ 1, abort_w)) { give_up(62); ok = false; break; }
           unsigned char* hb = sm + OFF_H + b * HT;
           mbar_expect_tx(&ctl->h_full[b], HT);
           tma_load_2d(hb, &mapH, &ctl->h_full[b], kc * 64, mt * 128);
@@ -2905,25 +2949,30 @@ __global__ void __launch_bounds__(384, 1)
           ++nh;
         }
         for (int jp = 0; jp < np2; ++jp) {
-          const int b = nc & 1;
-          if (!mbar_wait(&ctl->c_empty[b], ((nc >> 1) & 1) ^ 1, abort_w)) { give_up(63); ok = false; break; }
-          unsigned char* cb = sm + OFF_C + b * CBLK;
+          const int b = (int)(nc % NCS);
+          if (!mbar_wait(&ctl->c_empty[b], ((nc / NCS) & 1) ^ 1, abort_w)) { give_up(63); ok = false; break; }
+          unsigned char* cb = sm + OFF_C + b * CST;
           mbar_expect_tx(&ctl->c_full[b], NR * 128);
           const int y0 = (kc * np2 + jp) * 512;
+          // exact A: [A hi | B hi] then B lo (global rows 384-511) as the third part
 #pragma unroll
-          for (int r = 0; r < NR; r += 128) tma_load_2d(cb + r * 128, &mapC, &ctl->c_full[b], 0, y0 + r);
+          for (int r = 0; r < NR; r += 128)
+            tma_load_2d(cb + r * 128, &mapC, &ctl->c_full[b], 0, y0 + (AEXACT && r == 256 ? 384 : r));
           ++nc;
         }
       }
     }
-    for (int b = 0; b < 2; ++b) {
-      if ((nx + 1 - b) / 2) mbar_wait_drain(&ctl->x_full[b], (((nx + 1 - b) / 2) - 1) & 1);
-      if ((nh + 1 - b) / 2) mbar_wait_drain(&ctl->h_full[b], (((nh + 1 - b) / 2) - 1) & 1);
-      if ((nc + 1 - b) / 2) mbar_wait_drain(&ctl->c_full[b], (((nc + 1 - b) / 2) - 1) & 1);
-    }
+    // let the last load into every buffer land before the CTA can exit
+    auto drain = [&](uint64_t* full, int K, uint32_t n) {
+      for (int i = 0; i < K; ++i)
+        if (n > (uint32_t)i) mbar_wait_drain(&full[i], ((n - i + K - 1) / K - 1) & 1);
+    };
+    drain(ctl->x_full, 2, nx);
+    drain(ctl->h_full, NHB, nh);
+    drain(ctl->c_full, NCS, nc);
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
-    constexpr uint32_t idesc = idesc_bf16_f32(128, 128);
+    constexpr uint32_t idesc = idesc_bf16_f32(128, 128), idesc256 = idesc_bf16_f32(128, 256);
     uint32_t nx = 0, nc = 0;
     bool ok = true;
     for (int mt = blockIdx.x; mt < n_mt && ok && !*abort_w; mt += gridDim.x) {
@@ -2932,22 +2981,24 @@ __global__ void __launch_bounds__(384, 1)
       const uint32_t xa = smem_u32(sm + OFF_X + bx * XT);
       const int units = nkc * np2;
       for (int un = 0; un < units && ok; ++un) {
-        const int b = nc & 1;
-        const uint32_t ph = (nc >> 1) & 1;
-        if (!mbar_wait(&ctl->c_full[b], ph, abort_w) ||
-            !mbar_wait(&ctl->s_empty[b], ph ^ 1, abort_w)) { give_up(65); ok = false; break; }
+        const int cs = (int)(nc % NCS), b = nc & 1;
+        if (!mbar_wait(&ctl->c_full[cs], (nc / NCS) & 1, abort_w) ||
+            !mbar_wait(&ctl->s_empty[b], ((nc >> 1) & 1) ^ 1, abort_w)) { give_up(65); ok = false; break; }
         tc_fence_after();
-        const uint32_t cb = smem_u32(sm + OFF_C + b * CBLK);
+        const uint32_t cb = smem_u32(sm + OFF_C + cs * CST);
         const uint32_t ta = tmem + 256 * b, tb = ta + 128;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const uint64_t ad = sdesc_sw128(xa + k * 32);
-          umma_bf16(ta, ad, sdesc_sw128(cb + k * 32), idesc, k > 0 ? 1u : 0u);
-          if (!AEXACT) umma_bf16(ta, ad, sdesc_sw128(cb + 3 * 16384 + k * 32), idesc, 1u);
-          umma_bf16(tb, ad, sdesc_sw128(cb + 16384 + k * 32), idesc, k > 0 ? 1u : 0u);
-          umma_bf16(tb, ad, sdesc_sw128(cb + 2 * 16384 + k * 32), idesc, 1u);
+          // rows [A hi | B hi] are contiguous: one N = 256 product fills both accumulators;
+          // then B lo alone (exact A) or [A lo | B lo] (general A)
+          umma_bf16(ta, ad, sdesc_sw128(cb + k * 32), idesc256, k > 0 ? 1u : 0u);
+          if (AEXACT)
+            umma_bf16(tb, ad, sdesc_sw128(cb + 2 * 16384 + k * 32), idesc, 1u);
+          else
+            umma_bf16(ta, ad, sdesc_sw128(cb + 2 * 16384 + k * 32), idesc256, 1u);
         }
-        umma_commit(&ctl->c_empty[b]);
+        umma_commit(&ctl->c_empty[cs]);
         umma_commit(&ctl->s_full[b]);
         ++nc;
       }
@@ -2956,6 +3007,102 @@ __global__ void __launch_bounds__(384, 1)
     }
     umma_commit(&ctl->drain);
     mbar_wait_drain(&ctl->drain, 0);
+  } else if (warp >= 4 && AEXACT) {
+    // ---------------- epilogue, exact first operand: row r = TMEM lane, class box `box` (32
+    // classes) of every chunk for both probes of each pair.  The box's h stays in registers
+    // for all the chunk's pairs.  Per row the box sums are split, q = sum_j (sab_j - sa_j sb_j)
+    // with sa_j = sa0_j + sa1_j (likewise sb): box 1 adds sum_j (sab1_j - sa1_j sb1_j) to g and
+    // hands sa1, sb1 over in shared memory (the part of each coefficient buffer past its 384
+    // rows, never written in this form); box 0 adds the rest.
+    const int quad = warp & 3, box = (warp - 4) >> 2;
+    const int r = quad * 32 + lane;
+    const uint32_t lanes = (uint32_t)(quad * 32) << 16;
+    uint32_t nh = 0, nc = 0, nq = 0;
+    bool ok = true;
+    for (int mt = blockIdx.x; mt < n_mt && ok && !*abort_w; mt += gridDim.x) {
+      float sab = 0.0f, sa[2 * NP2MAX], sb[2 * NP2MAX];
+#pragma unroll
+      for (int j = 0; j < 2 * NP2MAX; ++j) sa[j] = sb[j] = 0.0f;
+      for (int kk = 0; kk < nkc && ok; ++kk) {
+        const int hb = (int)(nh % NHB);
+        if (!mbar_wait(&ctl->h_full[hb], (nh / NHB) & 1, abort_w)) {
+          give_up(66);
+          ok = false;
+          break;
+        }
+        uint64_t h2[16];
+        {
+          const unsigned char* hrow = sm + OFF_H + hb * HT + box * (HT / 2) + r * 128;
+#pragma unroll
+          for (int ch = 0; ch < 8; ++ch) {
+            const ulonglong2 h4 = *reinterpret_cast<const ulonglong2*>(hrow + ((ch ^ (r & 7)) << 4));
+            h2[2 * ch] = h4.x;
+            h2[2 * ch + 1] = h4.y;
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ctl->h_empty[hb]);
+        ++nh;
+#pragma unroll
+        for (int jp = 0; jp < NP2MAX; ++jp) {
+          if (jp < np2 && ok) {
+            const int b = nc & 1;
+            if (!mbar_wait(&ctl->s_full[b], (nc >> 1) & 1, abort_w)) {
+              give_up(67);
+              ok = false;
+            } else {
+              ++nc;
+              tc_fence_after();
+              const uint32_t ta = tmem + lanes + 256 * b + 32 * box, tb = ta + 128;
+              uint32_t ra[32], rb[32];
+              tmem_ld32_async(ta, ra);
+              tmem_ld32_async(tb, rb);
+              tmem_wait_ld();
+              qf_box_reg(ra, rb, h2, sab, sa[2 * jp], sb[2 * jp]);
+              tmem_ld32_async(ta + 64, ra);
+              tmem_ld32_async(tb + 64, rb);
+              tmem_wait_ld();
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(&ctl->s_empty[b]);
+              qf_box_reg(ra, rb, h2, sab, sa[2 * jp + 1], sb[2 * jp + 1]);
+            }
+          }
+        }
+      }
+      if (!ok) break;
+      float* xq = reinterpret_cast<float*>(sm + Lc::OFF_Q);
+      float q = sab;
+      if (box == 1) {
+        if (!mbar_wait(&ctl->q_empty, (nq & 1) ^ 1, abort_w)) {
+          give_up(68);
+          break;
+        }
+#pragma unroll
+        for (int j = 0; j < 2 * NP2MAX; ++j) {
+          xq[j * 128 + r] = sa[j];
+          xq[(2 * NP2MAX + j) * 128 + r] = sb[j];
+          q -= sa[j] * sb[j];
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ctl->q_full);
+      } else {
+        if (!mbar_wait(&ctl->q_full, nq & 1, abort_w)) {
+          give_up(69);
+          break;
+        }
+#pragma unroll
+        for (int j = 0; j < 2 * NP2MAX; ++j) {
+          const float a1 = xq[j * 128 + r], b1 = xq[(2 * NP2MAX + j) * 128 + r];
+          q -= sa[j] * (sb[j] + b1) + a1 * sb[j];
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ctl->q_empty);
+      }
+      ++nq;
+      const int64_t row = (int64_t)mt * 128 + r;
+      if (row >= m && row < N) atomicAdd(g + (row - m), -gscale * q);
+    }
   } else if (warp >= 4) {
     // ---------------- epilogue: row r = TMEM lane, probe 2 jp + half of every pair
     const int quad = warp & 3, half = (warp - 4) >> 2;
@@ -2968,8 +3115,8 @@ __global__ void __launch_bounds__(384, 1)
 #pragma unroll
       for (int jp = 0; jp < NP2MAX; ++jp) sum[jp][0] = sum[jp][1] = sum[jp][2] = 0.0f;
       for (int kk = 0; kk < nkc && ok; ++kk) {
-        const int hb = nh & 1;
-        if (!mbar_wait(&ctl->h_full[hb], (nh >> 1) & 1, abort_w)) {
+        const int hb = (int)(nh % NHB);
+        if (!mbar_wait(&ctl->h_full[hb], (nh / NHB) & 1, abort_w)) {
           give_up(66);
           ok = false;
           break;
@@ -3022,7 +3169,7 @@ __global__ void __launch_bounds__(384, 1)
 }
 
 // Coefficient blocks of k_tc_qf, block (kc, jp) = 512 rows of 64 bf16 features:
-//   rows [0, 128) A hi | [128, 256) B hi | [256, 384) B lo | [384, 512) A lo; in each part rows
+//   rows [0, 128) A hi | [128, 256) B hi | [256, 384) A lo | [384, 512) B lo; in each part rows
 //   0-63 are probe 2 jp, 64-127 probe 2 jp + 1, class kc 64 + (row mod 64).
 // A~ = A minus its class mean (amean; A as is when amean is null), B~ likewise; zero for classes
 // >= c, probes >= s and features >= d.
@@ -3034,7 +3181,7 @@ __global__ void k_build_qcoef(bf16* Cf, const float* A, const float* B, const fl
     const int row = idx >> 6, e = idx & 63;
     const int part = row >> 7, rr = row & 127;
     const int j = 2 * jp + (rr >> 6), k = kc * 64 + (rr & 63);
-    const bool isb = part == 1 || part == 2;
+    const bool isb = part == 1 || part == 3;
     float v = 0.0f;
     if (j < s && k < c && e < d) {
       const float* src = isb ? B : A;
@@ -3072,9 +3219,11 @@ static int32_t tc_quad_qf(firal_problem* P, const float* A, const float* B, int 
   static bool attr[2] = {false, false};
   if (!attr[aexact]) {
     if (aexact)
-      FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tc_qf<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
+      FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tc_qf<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          L<true>::SMEM));
     else
-      FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tc_qf<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
+      FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tc_qf<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          L<false>::SMEM));
     attr[aexact] = true;
   }
   CUtensorMap mX, mC, mH;
@@ -3085,10 +3234,10 @@ static int32_t tc_quad_qf(firal_problem* P, const float* A, const float* B, int 
   const int n_mt = (int)(Np / 128);
   const int grid = std::min(n_mt, P->sms);
   if (aexact)
-    k_tc_qf<true><<<grid, 384, SMEM, st>>>(mX, mC, mH, g, P->N, P->m, n_mt, nkc, np2,
+    k_tc_qf<true><<<grid, 384, L<true>::SMEM, st>>>(mX, mC, mH, g, P->N, P->m, n_mt, nkc, np2,
                                            (float)(scale / s), tc_error_word(P));
   else
-    k_tc_qf<false><<<grid, 384, SMEM, st>>>(mX, mC, mH, g, P->N, P->m, n_mt, nkc, np2,
+    k_tc_qf<false><<<grid, 384, L<false>::SMEM, st>>>(mX, mC, mH, g, P->N, P->m, n_mt, nkc, np2,
                                             (float)(scale / s), tc_error_word(P));
   FIRAL_CUDA_TRY(cudaGetLastError());
   return FIRAL_OK;
@@ -4342,7 +4491,7 @@ static int32_t tc_quad_pw_t(firal_problem* P, const float* A, const float* B, in
                             float* g) {
   using namespace pwq_cfg;
   cudaStream_t st = P->H->stream;
-  const int c = P->c, d = P->d;
+  const int d = P->d;
   const int Qe = pool_count(P->pt);
   const int sp = (s + 7) / 8 * 8;
   FIRAL_TRY(P->vmean.ensure((size_t)2 * s * Qe * d * sizeof(float)));

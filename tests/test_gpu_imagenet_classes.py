@@ -75,3 +75,8 @@ def test_c1000_fhat_z_and_gradient_vs_oracle(case, precision):
     efa = abs(f_ag - float(ref["fhat_autograd"][0])) / abs(float(ref["fhat_autograd"][0]))
     print(f"c=1000 {precision}: fhat {ef:.2e}  z {ez:.2e}  dfdz {eg:.2e}  fhat(fwd) {efa:.2e}")
     assert ef < 1e-3 and ez < 1e-3 and eg < 1e-3 and efa < 1e-3
+    if precision != "fp32":
+        # z after two MD iterations moves with the MD step's gradient (eq. 11 with the probe
+        # block as first operand, exact in bf16), and the mixed modes reach 1.3e-5 - 1.5e-5:
+        # a gradient error of 1e-4 would show here
+        assert ez < 1e-4
