@@ -1445,31 +1445,40 @@ __global__ void __launch_bounds__(256, 1)
 //   MODE 2:  S ~ A_hi Z_hi + A_hi Z_lo                  (fast mode, pool rows: the weights'
 //            bf16 roundings are unbiased and average over the points; the pair operand
 //            stays exact)
-// Unit = (128 classes, 128 pairs, point range).
+// Unit = (128 classes, BN pairs, point range); BN = 256 for MODES 0 and 1, 128 for MODE 2.
+//
+// Shared-memory bandwidth.  A tcgen05 product reads its A and B operands from shared memory:
+// an N = 128, K = 16 product moves 8 KB in 64 tensor cycles, the whole per-SM budget, and the
+// TMA writes of the next stages come on top.  N = 256 reads the A tile once for twice the work
+// (12 KB in 128 cycles), so the wide tiles take the products further from that bound.
 //
 // Accumulation length.  The tensor core adds each product block into its f32 accumulator with
 // a rounding that is biased (the sum loses magnitude on every add), so a chain of m adds into
 // one accumulator carries a relative bias of roughly m * 2^-25; a split of 200k points is
 // 37,500 adds, a 1e-3 bias that no averaging removes.  Both sums therefore accumulate in TMEM
-// for at most SUB = 8 K-steps (96 adds for S, 32 for P) at a time, alternating between two
-// short buffers, and the epilogue warps fold each finished short buffer into a long TMEM
-// accumulator with round-to-nearest f32 adds while the MMA fills the other.  (A biased P
-// would not move the CG solution, but with a fixed number of CG iterations it moves the
-// iterates, and with them z.)
-// TMEM columns: [0,128) short 0 | [128,256) short 1 | [256,384) long.
+// for at most SUBK K-steps (96 adds for MODE 0, 128 for MODES 1 and 2) at a time in a short
+// buffer, and the epilogue warps fold each finished short buffer into a long TMEM accumulator
+// with round-to-nearest f32 adds.  (A biased P would not move the CG solution, but with a
+// fixed number of CG iterations it moves the iterates, and with them z.)
+// TMEM columns: BN = 128: [0,128) short 0 | [128,256) short 1 | [256,384) long (the MMA fills
+// one short buffer while the other is folded); BN = 256: [0,256) short | [256,512) long (the
+// MMA waits for each fold, once per SUBK K-steps).
 // ------------------------------------------------------------------------------------------
 namespace b_cfg {
-constexpr int BM = 128, BN = 128, BK = 64;
-constexpr int TILE = BM * BK * 2;   // one 128 x 64 bf16 tile (A and Z tiles alike)
-constexpr int SUB = 8;              // K-steps per short accumulation of S
-constexpr uint32_t COL_LONG = 256;
+constexpr int BM = 128, BK = 64;
+constexpr int ATILE = BM * BK * 2;  // one 128 x 64 bf16 class tile
 constexpr int64_t UNIT_KB = 1024;   // K-steps per unit at most
+constexpr int NPP_ALIGN = 256;      // pair rows of the pair operand: a multiple of every BN
 template <int MODE> struct Cfg {
+  static constexpr int BN = MODE == 2 ? 128 : 256;
+  static constexpr int ZTILE = BN * BK * 2;
   // A_hi A_lo Z_hi Z_lo | A_P Z_hi | A_hi Z_hi Z_lo
-  static constexpr int NTILE = MODE == 0 ? 4 : MODE == 2 ? 3 : 2;
-  static constexpr int STAGE = NTILE * TILE;
-  static constexpr int STAGES = MODE == 0 ? 3 : MODE == 2 ? 4 : 6;
-  static constexpr int64_t SUBK = SUB;
+  static constexpr int NA = MODE == 0 ? 2 : 1, NZ = MODE == 1 ? 1 : 2;
+  static constexpr int STAGE = NA * ATILE + NZ * ZTILE;
+  static constexpr int STAGES = (227 * 1024 - 2048) / STAGE < 6 ? (227 * 1024 - 2048) / STAGE : 6;
+  static constexpr int NSB = BN == 128 ? 2 : 1;            // short TMEM buffers
+  static constexpr uint32_t COL_LONG = NSB * BN;
+  static constexpr int64_t SUBK = MODE == 0 ? 8 : MODE == 1 ? 32 : 16;
   static constexpr int SMEM = STAGES * STAGE + 1024 + 256;
 };
 }  // namespace b_cfg
@@ -1492,6 +1501,10 @@ __global__ void __launch_bounds__(256, 1)
   using C = Cfg<MODE>;
   constexpr int STAGES = C::STAGES;
   constexpr int64_t SUBK = C::SUBK;
+  constexpr int BN = C::BN, ZTILE = C::ZTILE, NSB = C::NSB;
+  constexpr uint32_t COL_LONG = C::COL_LONG;
+  // stage layout: class tile(s), then pair tile(s)
+  constexpr int OZ = C::NA * ATILE;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   BsCtl* ctl = (BsCtl*)(sm + STAGES * C::STAGE);
@@ -1573,16 +1586,9 @@ __global__ void __launch_bounds__(256, 1)
         const int64_t kr = real_kb(mt, kb);
         const int ya = (int)(kr * n_mt + mt) * BM, yz = (int)(kr * n_nt + nt) * BN;
         tma_load_2d(st, &mapA0, &ctl->full[stage], 0, ya);
-        if (MODE == 0) {
-          tma_load_2d(st + TILE, &mapA1, &ctl->full[stage], 0, ya);
-          tma_load_2d(st + 2 * TILE, &mapZ0, &ctl->full[stage], 0, yz);
-          tma_load_2d(st + 3 * TILE, &mapZ1, &ctl->full[stage], 0, yz);
-        } else if (MODE == 2) {
-          tma_load_2d(st + TILE, &mapZ0, &ctl->full[stage], 0, yz);
-          tma_load_2d(st + 2 * TILE, &mapZ1, &ctl->full[stage], 0, yz);
-        } else {
-          tma_load_2d(st + TILE, &mapZ0, &ctl->full[stage], 0, yz);
-        }
+        if (MODE == 0) tma_load_2d(st + ATILE, &mapA1, &ctl->full[stage], 0, ya);
+        tma_load_2d(st + OZ, &mapZ0, &ctl->full[stage], 0, yz);
+        if (MODE != 1) tma_load_2d(st + OZ + ZTILE, &mapZ1, &ctl->full[stage], 0, yz);
         if (++stage == STAGES) {
           stage = 0;
           phase ^= 1;
@@ -1599,10 +1605,10 @@ __global__ void __launch_bounds__(256, 1)
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
-    constexpr uint32_t idesc = idesc_bf16_f32(BM, MODE == 3 ? 128 : BN);
+    constexpr uint32_t idesc = idesc_bf16_f32(BM, BN);
     int stage = 0;
     uint32_t phase = 0;
-    uint32_t gsub = 0;   // accumulations issued by this CTA (short buffer = gsub & 1)
+    uint32_t gsub = 0;   // accumulations issued by this CTA (short buffer gsub % NSB)
     bool ok = true;
     for (int u = blockIdx.x; u < nunits && ok && !*abort_w; u += gridDim.x) {
       int mt, nt, sp;
@@ -1610,7 +1616,7 @@ __global__ void __launch_bounds__(256, 1)
       unit_range(u, mt, nt, sp, kb0, kb1);
       for (int64_t c0 = kb0; c0 < kb1 && ok; c0 += SUBK, ++gsub) {
         const int64_t c1 = c0 + SUBK < kb1 ? c0 + SUBK : kb1;
-        const uint32_t b = gsub & 1, par = (gsub >> 1) & 1;
+        const uint32_t b = gsub % NSB, par = (gsub / NSB) & 1;
         if (!mbar_wait(&ctl->tempty[b], par ^ 1, abort_w)) {
           give_up(32);
           ok = false;
@@ -1629,20 +1635,10 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll
           for (int k = 0; k < BK / 16; ++k) {
             const uint32_t acc = (kb != c0) || k != 0;
-            if (MODE == 0) {
-              const uint64_t zh = sdesc_sw128(a0 + 2 * TILE + k * 32);
-              const uint64_t ah = sdesc_sw128(a0 + k * 32);
-              umma_bf16(tS, ah, zh, idesc, acc);
-              umma_bf16(tS, sdesc_sw128(a0 + TILE + k * 32), zh, idesc, 1u);
-              umma_bf16(tS, ah, sdesc_sw128(a0 + 3 * TILE + k * 32), idesc, 1u);
-            } else if (MODE == 2) {
-              const uint64_t ah = sdesc_sw128(a0 + k * 32);
-              umma_bf16(tS, ah, sdesc_sw128(a0 + TILE + k * 32), idesc, acc);
-              umma_bf16(tS, ah, sdesc_sw128(a0 + 2 * TILE + k * 32), idesc, 1u);
-            } else {
-              umma_bf16(tS, sdesc_sw128(a0 + k * 32), sdesc_sw128(a0 + TILE + k * 32), idesc,
-                        acc);
-            }
+            const uint64_t ah = sdesc_sw128(a0 + k * 32), zh = sdesc_sw128(a0 + OZ + k * 32);
+            umma_bf16(tS, ah, zh, idesc, acc);
+            if (MODE == 0) umma_bf16(tS, sdesc_sw128(a0 + ATILE + k * 32), zh, idesc, 1u);
+            if (MODE != 1) umma_bf16(tS, ah, sdesc_sw128(a0 + OZ + ZTILE + k * 32), idesc, 1u);
           }
           umma_commit(&ctl->empty[stage]);
           if (++stage == STAGES) {
@@ -1684,7 +1680,7 @@ __global__ void __launch_bounds__(256, 1)
       }
       for (int64_t c0 = kb0; c0 < kb1; c0 += SUBK, ++gsub) {
         const bool first = c0 == kb0, last = c0 + SUBK >= kb1;
-        const uint32_t b = gsub & 1, par = (gsub >> 1) & 1;
+        const uint32_t b = gsub % NSB, par = (gsub / NSB) & 1;
         if (!mbar_wait(&ctl->tfull[b], par, abort_w)) {
           give_up(34);
           ok = false;
@@ -2326,7 +2322,7 @@ int32_t tc_prepare(firal_problem* P) {
   FIRAL_TRY(tc_prepare_centred(P, cpb2));
   // pair operand of the block sums (problem constant): Z = x (x) x on the pair triangle
   const int npairs = P->d * (P->d + 1) / 2;
-  const int64_t npp = (npairs + b_cfg::BN - 1) / b_cfg::BN * b_cfg::BN;
+  const int64_t npp = (npairs + b_cfg::NPP_ALIGN - 1) / b_cfg::NPP_ALIGN * b_cfg::NPP_ALIGN;
   FIRAL_TRY(P->Zp.ensure((size_t)2 * npp * Np * 2));
   k_build_z<<<(unsigned)(Np / 64), 256, 0, st>>>(
       P->Zp.as<bf16>(), P->Zp.as<bf16>() + npp * Np, P->Xb.as<bf16>(), P->d, P->dp, npairs, npp);
@@ -2549,7 +2545,8 @@ static int32_t tc_labelled_blocks(firal_problem* P) {
   const int64_t Np = P->Np, m = P->m;
   const int cp = P->cp, c = P->c, d = P->d;
   const int npairs = d * (d + 1) / 2;
-  const int64_t npp = (npairs + BN - 1) / BN * BN;
+  const int64_t npp = (npairs + NPP_ALIGN - 1) / NPP_ALIGN * NPP_ALIGN;
+  constexpr int BN = Cfg<0>::BN;
   const int n_mt = (cp + BM - 1) / BM, n_nt = (int)(npp / BN);
   const int cpb = n_mt * BM;
   const int64_t asz = (int64_t)cpb * Np, kb_total = Np / BK, kbm = (m + BK - 1) / BK;
@@ -2598,9 +2595,10 @@ int32_t tc_syrk_blocks(firal_problem* P, const void* wv, double lamS, void* outS
   if (!wantS) outS = nullptr;
   if (!outS && !outP) return FIRAL_OK;
   const int npairs = d * (d + 1) / 2;
-  const int64_t npp = (npairs + BN - 1) / BN * BN;
+  const int64_t npp = (npairs + NPP_ALIGN - 1) / NPP_ALIGN * NPP_ALIGN;
   const int n_mt = (cp + BM - 1) / BM;
-  const int n_nt = (int)(npp / BN);
+  // pair tiles of each form (the split count follows the 256-pair tiles)
+  const int n_nt = (int)(npp / Cfg<1>::BN), n_nt2 = (int)(npp / Cfg<2>::BN);
   const int64_t kb_total = Np / BK;
   const int64_t kL = P->pt.Q ? P->kr_bsum_Lmax : kb_total;   // longest class-tile K list
   const int tiles = n_mt * n_nt;
@@ -2659,14 +2657,17 @@ int32_t tc_syrk_blocks(firal_problem* P, const void* wv, double lamS, void* outS
     FIRAL_TRY(make_map(&mA0, Ahi, arows, BK, BM, BK, true));
     FIRAL_TRY(make_map(&mA1, Alo, arows, BK, BM, BK, true));
     FIRAL_TRY(make_map(&mA2, AP, arows, BK, BM, BK, true));
-    FIRAL_TRY(make_map(&mZ0, P->Zp.p, zrows, BK, BN, BK, true));
-    FIRAL_TRY(make_map(&mZ1, P->Zp.as<bf16>() + npp * Np, zrows, BK, BN, BK, true));
+    FIRAL_TRY(make_map(&mZ0, P->Zp.p, zrows, BK, Cfg<1>::BN, BK, true));
+    FIRAL_TRY(make_map(&mZ1, P->Zp.as<bf16>() + npp * Np, zrows, BK, Cfg<1>::BN, BK, true));
     const int grid = std::min(units, sms);
     if (outS && s1) {
-      k_tc_bsum<2><<<grid, 256, Cfg<2>::SMEM, st>>>(mA0, mA0, mZ0, mZ1, pS, c, d, npairs, n_mt,
-                                                    n_nt, splits, kbps, kb_total,
-                                                    tc_error_word(P), P->kr_bsum.as<int4>(),
-                                                    P->kbL);
+      CUtensorMap mZ20, mZ21;
+      FIRAL_TRY(make_map(&mZ20, P->Zp.p, zrows, BK, Cfg<2>::BN, BK, true));
+      FIRAL_TRY(make_map(&mZ21, P->Zp.as<bf16>() + npp * Np, zrows, BK, Cfg<2>::BN, BK, true));
+      const int units2 = n_mt * n_nt2 * splits;
+      k_tc_bsum<2><<<std::min(units2, sms), 256, Cfg<2>::SMEM, st>>>(
+          mA0, mA0, mZ20, mZ21, pS, c, d, npairs, n_mt, n_nt2, splits, kbps, kb_total,
+          tc_error_word(P), P->kr_bsum.as<int4>(), P->kbL);
       FIRAL_CUDA_TRY(cudaGetLastError());
     } else if (outS) {
       k_tc_bsum<0><<<grid, 256, Cfg<0>::SMEM, st>>>(mA0, mA1, mZ0, mZ1, pS, c, d, npairs, n_mt,
