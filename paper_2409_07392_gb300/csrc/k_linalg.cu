@@ -776,6 +776,46 @@ __global__ void k_round_m(const double* __restrict__ Binv, const double* __restr
   }
 }
 
+// The same for f32 outputs, in f32 arithmetic.  The consumers keep at most f32 (the SIMT
+// scores) or bf16 hi + lo (2^-17 per entry, the tensor-core scores) of M1 and M2, and an f32
+// product over d terms carries about sqrt(d) 2^-24 of its row norms, so the FP64 products
+// (2 d^3 FMAs per block on a part whose FP64 rate is a small fraction of its FP32 rate) buy
+// nothing the picks can use.  Binv_k, Sig_k Binv_k and (when it fits) Sig_k in shared memory.
+__global__ void k_round_m_f32(const double* __restrict__ Binv, const double* __restrict__ Sig,
+                              int d, float* __restrict__ M1, float* __restrict__ M2, int c_sig,
+                              int stage_sig) {
+  extern __shared__ float shf[];
+  float* Bs = shf;               // d*d
+  float* Ts = shf + d * d;       // d*d
+  float* Ss = shf + 2 * d * d;   // d*d when stage_sig
+  const int k = blockIdx.x, tid = threadIdx.x, bd = blockDim.x;
+  const double* Bk = Binv + (int64_t)k * d * d;
+  const double* Sk = Sig + (int64_t)(k % c_sig) * d * d;   // Sigma shared by stacked chains
+  for (int t = tid; t < d * d; t += bd) {
+    const float b = (float)Bk[t];
+    Bs[t] = b;
+    M2[(int64_t)k * d * d + t] = b;
+    if (stage_sig) Ss[t] = (float)Sk[t];
+  }
+  __syncthreads();
+  for (int t = tid; t < d * d; t += bd) {
+    const int i = t / d, j = t - i * d;
+    float acc = 0.0f;
+    if (stage_sig)
+      for (int q = 0; q < d; ++q) acc = fmaf(Ss[i * d + q], Bs[q * d + j], acc);
+    else
+      for (int q = 0; q < d; ++q) acc = fmaf((float)Sk[(int64_t)i * d + q], Bs[q * d + j], acc);
+    Ts[t] = acc;
+  }
+  __syncthreads();
+  for (int t = tid; t < d * d; t += bd) {
+    const int i = t / d, j = t - i * d;
+    float acc = 0.0f;
+    for (int q = 0; q < d; ++q) acc = fmaf(Bs[i * d + q], Ts[q * d + j], acc);
+    M1[(int64_t)k * d * d + t] = acc;
+  }
+}
+
 // H_k += H_o,k / b + w_ik x_i x_i^T for the pick i (Algorithm 3 line 8; pool row i read from
 // the device, w_ik = h_ik (1 - h_ik)); with L and Ht given,
 // the transformed blocks too: Ht_k += Hot_k / b + w_ik y y^T with y = L_k^{-1} x_i
@@ -983,10 +1023,11 @@ int32_t round_m(bool dbl, const double* Binv, const double* Sig, int c, int d, v
     k_round_m<double><<<nb, threads_for(d), smem, st>>>(Binv, Sig, d, (double*)M1, (double*)M2,
                                                         Tg, c);
   } else {
-    FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_round_m<float>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    k_round_m<float><<<nb, threads_for(d), smem, st>>>(Binv, Sig, d, (float*)M1, (float*)M2, Tg,
-                                                       c);
+    const int stage_sig = (size_t)3 * d * d * sizeof(float) <= 200 * 1024 ? 1 : 0;
+    const size_t smem_f = (size_t)(2 + stage_sig) * d * d * sizeof(float);
+    FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_round_m_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        200 * 1024));
+    k_round_m_f32<<<nb, 256, smem_f, st>>>(Binv, Sig, d, (float*)M1, (float*)M2, c, stage_sig);
   }
   FIRAL_CUDA_TRY(cudaGetLastError());
   return FIRAL_OK;
