@@ -72,6 +72,23 @@ static int32_t make_map(CUtensorMap* m, const void* base, uint64_t rows, uint64_
   return FIRAL_OK;
 }
 
+// The same with the 64-byte swizzle: box = box_rows x box_cols with box_cols * 2 = 64 bytes.
+static int32_t make_map_sw64(CUtensorMap* m, const void* base, uint64_t rows, uint64_t cols,
+                             uint32_t box_rows, uint32_t box_cols) {
+  FIRAL_TRY(get_encoder());
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {cols * sizeof(bf16)};
+  cuuint32_t box[2] = {box_cols, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    return fail(FIRAL_ERR_CUDA, "cuTensorMapEncodeTiled (64B) failed (" + std::to_string((int)r) + ")");
+  return FIRAL_OK;
+}
+
 // 2-D f32 tensor map with 128-byte swizzle: box = box_rows x 32 columns (128 B rows).
 // cols * 4 must be a multiple of 16.
 static int32_t make_map_f32(CUtensorMap* m, const void* base, uint64_t rows, uint64_t cols,
@@ -1445,12 +1462,15 @@ __global__ void __launch_bounds__(256, 1)
 //   MODE 2:  S ~ A_hi Z_hi + A_hi Z_lo                  (fast mode, pool rows: the weights'
 //            bf16 roundings are unbiased and average over the points; the pair operand
 //            stays exact)
-// Unit = (128 classes, BN pairs, point range); BN = 256 for MODES 0 and 1, 128 for MODE 2.
+// Unit = (128 classes, 256 pairs, point range).
 //
 // Shared-memory bandwidth.  A tcgen05 product reads its A and B operands from shared memory:
 // an N = 128, K = 16 product moves 8 KB in 64 tensor cycles, the whole per-SM budget, and the
 // TMA writes of the next stages come on top.  N = 256 reads the A tile once for twice the work
 // (12 KB in 128 cycles), so the wide tiles take the products further from that bound.
+// MODE 2's three tiles per K-step (80 KB at 256 pairs) would fit only two stages deep, so its
+// stages carry half a K-step (32 points: 64-byte rows in the 64-byte swizzle layout, 40 KB),
+// five deep.
 //
 // Accumulation length.  The tensor core adds each product block into its f32 accumulator with
 // a rounding that is biased (the sum loses magnitude on every add), so a chain of m adds into
@@ -1460,21 +1480,21 @@ __global__ void __launch_bounds__(256, 1)
 // buffer, and the epilogue warps fold each finished short buffer into a long TMEM accumulator
 // with round-to-nearest f32 adds.  (A biased P would not move the CG solution, but with a
 // fixed number of CG iterations it moves the iterates, and with them z.)
-// TMEM columns: BN = 128: [0,128) short 0 | [128,256) short 1 | [256,384) long (the MMA fills
-// one short buffer while the other is folded); BN = 256: [0,256) short | [256,512) long (the
-// MMA waits for each fold, once per SUBK K-steps).
+// TMEM columns: [0,256) short | [256,512) long (the MMA waits for each fold, once per SUBK
+// K-steps).
 // ------------------------------------------------------------------------------------------
 namespace b_cfg {
 constexpr int BM = 128, BK = 64;
-constexpr int ATILE = BM * BK * 2;  // one 128 x 64 bf16 class tile
 constexpr int64_t UNIT_KB = 1024;   // K-steps per unit at most
 constexpr int NPP_ALIGN = 256;      // pair rows of the pair operand: a multiple of every BN
 template <int MODE> struct Cfg {
-  static constexpr int BN = MODE == 2 ? 128 : 256;
-  static constexpr int ZTILE = BN * BK * 2;
+  static constexpr int BN = 256;
+  static constexpr int KH = MODE == 2 ? 2 : 1;             // stages per K-step
+  static constexpr int BKS = BK / KH;                      // points per stage
+  static constexpr int ATS = BM * BKS * 2, ZTILE = BN * BKS * 2;
   // A_hi A_lo Z_hi Z_lo | A_P Z_hi | A_hi Z_hi Z_lo
   static constexpr int NA = MODE == 0 ? 2 : 1, NZ = MODE == 1 ? 1 : 2;
-  static constexpr int STAGE = NA * ATILE + NZ * ZTILE;
+  static constexpr int STAGE = NA * ATS + NZ * ZTILE;
   static constexpr int STAGES = (227 * 1024 - 2048) / STAGE < 6 ? (227 * 1024 - 2048) / STAGE : 6;
   static constexpr int NSB = BN == 128 ? 2 : 1;            // short TMEM buffers
   static constexpr uint32_t COL_LONG = NSB * BN;
@@ -1501,10 +1521,11 @@ __global__ void __launch_bounds__(256, 1)
   using C = Cfg<MODE>;
   constexpr int STAGES = C::STAGES;
   constexpr int64_t SUBK = C::SUBK;
-  constexpr int BN = C::BN, ZTILE = C::ZTILE, NSB = C::NSB;
+  constexpr int BN = C::BN, ZTILE = C::ZTILE, NSB = C::NSB, KH = C::KH, BKS = C::BKS;
+  constexpr int ATS = C::ATS;
   constexpr uint32_t COL_LONG = C::COL_LONG;
   // stage layout: class tile(s), then pair tile(s)
-  constexpr int OZ = C::NA * ATILE;
+  constexpr int OZ = C::NA * ATS;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   BsCtl* ctl = (BsCtl*)(sm + STAGES * C::STAGE);
@@ -1575,7 +1596,7 @@ __global__ void __launch_bounds__(256, 1)
       int mt, nt, sp;
       int64_t kb0, kb1;
       unit_range(u, mt, nt, sp, kb0, kb1);
-      for (int64_t kb = kb0; kb < kb1; ++kb) {
+      for (int64_t kh = kb0 * KH; kh < kb1 * KH; ++kh) {
         if (!mbar_wait(&ctl->empty[stage], phase ^ 1, abort_w)) {
           give_up(31);
           ok = false;
@@ -1583,12 +1604,14 @@ __global__ void __launch_bounds__(256, 1)
         }
         unsigned char* st = sm + stage * C::STAGE;
         mbar_expect_tx(&ctl->full[stage], C::STAGE);
+        const int64_t kb = kh / KH;
+        const int x = (int)(kh - kb * KH) * BKS;   // points of the K-step this stage carries
         const int64_t kr = real_kb(mt, kb);
         const int ya = (int)(kr * n_mt + mt) * BM, yz = (int)(kr * n_nt + nt) * BN;
-        tma_load_2d(st, &mapA0, &ctl->full[stage], 0, ya);
-        if (MODE == 0) tma_load_2d(st + ATILE, &mapA1, &ctl->full[stage], 0, ya);
-        tma_load_2d(st + OZ, &mapZ0, &ctl->full[stage], 0, yz);
-        if (MODE != 1) tma_load_2d(st + OZ + ZTILE, &mapZ1, &ctl->full[stage], 0, yz);
+        tma_load_2d(st, &mapA0, &ctl->full[stage], x, ya);
+        if (MODE == 0) tma_load_2d(st + ATS, &mapA1, &ctl->full[stage], x, ya);
+        tma_load_2d(st + OZ, &mapZ0, &ctl->full[stage], x, yz);
+        if (MODE != 1) tma_load_2d(st + OZ + ZTILE, &mapZ1, &ctl->full[stage], x, yz);
         if (++stage == STAGES) {
           stage = 0;
           phase ^= 1;
@@ -1624,7 +1647,9 @@ __global__ void __launch_bounds__(256, 1)
         }
         tc_fence_after();
         const uint32_t tS = tmem + b * BN;
-        for (int64_t kb = c0; kb < c1; ++kb) {
+        // 64-byte rows (half K-steps) or 128-byte rows (whole K-steps)
+        auto sdesc = [](uint32_t addr) { return KH == 2 ? sdesc_sw64(addr) : sdesc_sw128(addr); };
+        for (int64_t kh = c0 * KH; kh < c1 * KH; ++kh) {
           if (!mbar_wait(&ctl->full[stage], phase, abort_w)) {
             give_up(33);
             ok = false;
@@ -1633,12 +1658,12 @@ __global__ void __launch_bounds__(256, 1)
           tc_fence_after();
           const uint32_t a0 = smem_u32(sm + stage * C::STAGE);
 #pragma unroll
-          for (int k = 0; k < BK / 16; ++k) {
-            const uint32_t acc = (kb != c0) || k != 0;
-            const uint64_t ah = sdesc_sw128(a0 + k * 32), zh = sdesc_sw128(a0 + OZ + k * 32);
+          for (int k = 0; k < BKS / 16; ++k) {
+            const uint32_t acc = (kh != c0 * KH) || k != 0;
+            const uint64_t ah = sdesc(a0 + k * 32), zh = sdesc(a0 + OZ + k * 32);
             umma_bf16(tS, ah, zh, idesc, acc);
-            if (MODE == 0) umma_bf16(tS, sdesc_sw128(a0 + ATILE + k * 32), zh, idesc, 1u);
-            if (MODE != 1) umma_bf16(tS, ah, sdesc_sw128(a0 + OZ + ZTILE + k * 32), idesc, 1u);
+            if (MODE == 0) umma_bf16(tS, sdesc(a0 + ATS + k * 32), zh, idesc, 1u);
+            if (MODE != 1) umma_bf16(tS, ah, sdesc(a0 + OZ + ZTILE + k * 32), idesc, 1u);
           }
           umma_commit(&ctl->empty[stage]);
           if (++stage == STAGES) {
@@ -2661,12 +2686,15 @@ int32_t tc_syrk_blocks(firal_problem* P, const void* wv, double lamS, void* outS
     FIRAL_TRY(make_map(&mZ1, P->Zp.as<bf16>() + npp * Np, zrows, BK, Cfg<1>::BN, BK, true));
     const int grid = std::min(units, sms);
     if (outS && s1) {
-      CUtensorMap mZ20, mZ21;
-      FIRAL_TRY(make_map(&mZ20, P->Zp.p, zrows, BK, Cfg<2>::BN, BK, true));
-      FIRAL_TRY(make_map(&mZ21, P->Zp.as<bf16>() + npp * Np, zrows, BK, Cfg<2>::BN, BK, true));
+      // half K-steps: 32-point boxes of 64-byte rows
+      constexpr int BKS = Cfg<2>::BKS;
+      CUtensorMap mA20, mZ20, mZ21;
+      FIRAL_TRY(make_map_sw64(&mA20, Ahi, arows, BK, BM, BKS));
+      FIRAL_TRY(make_map_sw64(&mZ20, P->Zp.p, zrows, BK, Cfg<2>::BN, BKS));
+      FIRAL_TRY(make_map_sw64(&mZ21, P->Zp.as<bf16>() + npp * Np, zrows, BK, Cfg<2>::BN, BKS));
       const int units2 = n_mt * n_nt2 * splits;
       k_tc_bsum<2><<<std::min(units2, sms), 256, Cfg<2>::SMEM, st>>>(
-          mA0, mA0, mZ20, mZ21, pS, c, d, npairs, n_mt, n_nt2, splits, kbps, kb_total,
+          mA20, mA20, mZ20, mZ21, pS, c, d, npairs, n_mt, n_nt2, splits, kbps, kb_total,
           tc_error_word(P), P->kr_bsum.as<int4>(), P->kbL);
       FIRAL_CUDA_TRY(cudaGetLastError());
     } else if (outS) {
