@@ -3969,13 +3969,17 @@ __global__ void __launch_bounds__(256) k_pw_pack(bf16* Pk, const float* V, float
 //   pq[j c + k] = <V_j[:, k], out_j[:, k]>                 (the CG dot products)
 // lam is the diagonal-part lambda (rank 0 of a row-sharded group only: such a group takes the
 // separate combine / allreduce / projection path instead).
-__global__ void __launch_bounds__(256) k_pw_finish(float* out, const float* V, const float* vmean,
-                                                   const float* part, const int4* pool_tab,
-                                                   const int2* pseg, const int4* seg_tab,
-                                                   float lam, double lam_null, int s, int sp,
-                                                   int c, int d, int64_t D, int Qe, double* pq) {
+constexpr int PWF_THREADS = 512;   // eight 64-thread groups: segment partials in flight
+__global__ void __launch_bounds__(PWF_THREADS) k_pw_finish(float* out, const float* V,
+                                                           const float* vmean, const float* part,
+                                                           const int4* pool_tab,
+                                                           const int2* pseg, const int4* seg_tab,
+                                                           float lam, double lam_null, int s,
+                                                           int sp, int c, int d, int64_t D,
+                                                           int Qe, double* pq) {
+  constexpr int NG = PWF_THREADS / 64;
   __shared__ float t[32 * 64];
-  __shared__ double red[4][64];
+  __shared__ double red[NG][64];
   __shared__ float qm[64];
   const int q = blockIdx.x, j = blockIdx.y;
   const int4 pt = pool_tab[q];
@@ -3994,10 +3998,14 @@ __global__ void __launch_bounds__(256) k_pw_finish(float* out, const float* V, c
     const int e = threadIdx.x & 63, gr = threadIdx.x >> 6;
     double acc = 0.0;
     if (e < d)
-      for (int kl = gr; kl < cq; kl += 4) acc += (double)t[kl * 64 + e];
+      for (int kl = gr; kl < cq; kl += NG) acc += (double)t[kl * 64 + e];
     red[gr][e] = acc;
     __syncthreads();
-    if (threadIdx.x < 64 && e < d) qm[e] = (float)((((red[0][e] + red[1][e]) + red[2][e]) + red[3][e]) / cq);
+    if (threadIdx.x < 64 && e < d) {
+      double tot = 0.0;
+      for (int g = 0; g < NG; ++g) tot += red[g][e];
+      qm[e] = (float)(tot / cq);
+    }
     __syncthreads();
   }
   // one warp per class: the projected block and its dot product with V_j[:, k]
@@ -4228,7 +4236,7 @@ static int32_t tc_apply_pw_t(firal_problem* P, const float* w, const float* V, i
   ProfScope ps(st, PF_COMBINE);
   if (!sharded(P)) {
     count_launch();
-    k_pw_finish<<<dim3((unsigned)Qe, (unsigned)s), 256, 0, st>>>(
+    k_pw_finish<<<dim3((unsigned)Qe, (unsigned)s), PWF_THREADS, 0, st>>>(
         out, V, P->vmean.as<float>(), P->pw_part.as<float>(), P->pw_pool.as<int4>(),
         P->pw_pseg.as<int2>(), P->pw_seg.as<int4>(), (float)lam, lam, s, sp, c, d, P->D, Qe, pq);
     FIRAL_CUDA_TRY(cudaGetLastError());
