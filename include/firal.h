@@ -68,9 +68,10 @@ typedef enum {
   FIRAL_MIXED_BF16_FAST = 3  /* as FIRAL_MIXED_BF16, but the CG direction enters the first      */
                         /* contraction of the Hessian apply as one bf16 operand (2^-9 relative   */
                         /* rounding of the low-rank term), which halves that contraction's       */
-                        /* tensor work, and the diagonal-part block sums take their weights as   */
-                        /* one bf16 operand (per-element 2^-9 roundings that average over each   */
-                        /* class's points; two products instead of three);                       */
+                        /* tensor work, and the diagonal-part block sums over the pool rows take */
+                        /* their weights and the products x_e x_e' as one bf16 operand each      */
+                        /* (per-element 2^-9 roundings that average over each class's points;   */
+                        /* one product instead of three; labelled rows stay exact);              */
                         /* a problem whose rows' mean sum_k h_ik^2 exceeds 0.1 (confident or     */
                         /* few classes: the low-rank term is large) keeps hi + lo for both; with */
                         /* at most 32 classes per pool both modes run the same fused kernels     */

@@ -72,23 +72,6 @@ static int32_t make_map(CUtensorMap* m, const void* base, uint64_t rows, uint64_
   return FIRAL_OK;
 }
 
-// The same with the 64-byte swizzle: box = box_rows x box_cols with box_cols * 2 = 64 bytes.
-static int32_t make_map_sw64(CUtensorMap* m, const void* base, uint64_t rows, uint64_t cols,
-                             uint32_t box_rows, uint32_t box_cols) {
-  FIRAL_TRY(get_encoder());
-  cuuint64_t dims[2] = {cols, rows};
-  cuuint64_t strides[1] = {cols * sizeof(bf16)};
-  cuuint32_t box[2] = {box_cols, box_rows};
-  cuuint32_t estr[2] = {1, 1};
-  CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
-                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS)
-    return fail(FIRAL_ERR_CUDA, "cuTensorMapEncodeTiled (64B) failed (" + std::to_string((int)r) + ")");
-  return FIRAL_OK;
-}
-
 // 2-D f32 tensor map with 128-byte swizzle: box = box_rows x 32 columns (128 B rows).
 // cols * 4 must be a multiple of 16.
 static int32_t make_map_f32(CUtensorMap* m, const void* base, uint64_t rows, uint64_t cols,
@@ -1458,25 +1441,22 @@ __global__ void __launch_bounds__(256, 1)
 // once and stored as bf16 hi + lo, which is exact (a product of two bf16 values has at most 16
 // significant bits).  Both block sums are then plain TMA-fed GEMMs over the points:
 //   MODE 0:  S ~ A_hi Z_hi + A_lo Z_hi + A_hi Z_lo      (relative error ~2^-16)
-//   MODE 1:  P ~ A_P Z_hi                               (preconditioner only)
-//   MODE 2:  S ~ A_hi Z_hi + A_hi Z_lo                  (fast mode, pool rows: the weights'
-//            bf16 roundings are unbiased and average over the points; the pair operand
-//            stays exact)
+//   MODE 1:  one product A Z_hi: P ~ A_P Z_hi (preconditioner), and in the fast mode also
+//            S ~ A_hi Z_hi over the pool rows (the bf16 roundings of w h and of x_ie x_ie' are
+//            unbiased and independent from point to point, so they average over each class's
+//            points)
 // Unit = (128 classes, 256 pairs, point range).
 //
 // Shared-memory bandwidth.  A tcgen05 product reads its A and B operands from shared memory:
 // an N = 128, K = 16 product moves 8 KB in 64 tensor cycles, the whole per-SM budget, and the
 // TMA writes of the next stages come on top.  N = 256 reads the A tile once for twice the work
 // (12 KB in 128 cycles), so the wide tiles take the products further from that bound.
-// MODE 2's three tiles per K-step (80 KB at 256 pairs) would fit only two stages deep, so its
-// stages carry half a K-step (32 points: 64-byte rows in the 64-byte swizzle layout, 40 KB),
-// five deep.
 //
 // Accumulation length.  The tensor core adds each product block into its f32 accumulator with
 // a rounding that is biased (the sum loses magnitude on every add), so a chain of m adds into
 // one accumulator carries a relative bias of roughly m * 2^-25; a split of 200k points is
 // 37,500 adds, a 1e-3 bias that no averaging removes.  Both sums therefore accumulate in TMEM
-// for at most SUBK K-steps (96 adds for MODE 0, 128 for MODES 1 and 2) at a time in a short
+// for at most SUBK K-steps (96 adds for MODE 0, 128 for MODE 1) at a time in a short
 // buffer, and the epilogue warps fold each finished short buffer into a long TMEM accumulator
 // with round-to-nearest f32 adds.  (A biased P would not move the CG solution, but with a
 // fixed number of CG iterations it moves the iterates, and with them z.)
@@ -1486,19 +1466,16 @@ __global__ void __launch_bounds__(256, 1)
 namespace b_cfg {
 constexpr int BM = 128, BK = 64;
 constexpr int64_t UNIT_KB = 1024;   // K-steps per unit at most
-constexpr int NPP_ALIGN = 256;      // pair rows of the pair operand: a multiple of every BN
+constexpr int BN = 256;             // pairs per unit
+constexpr int NPP_ALIGN = BN;       // pair rows of the pair operand
+constexpr int ATILE = BM * BK * 2, ZTILE = BN * BK * 2;
+constexpr uint32_t COL_LONG = BN;   // TMEM: short accumulator, then long
 template <int MODE> struct Cfg {
-  static constexpr int BN = 256;
-  static constexpr int KH = MODE == 2 ? 2 : 1;             // stages per K-step
-  static constexpr int BKS = BK / KH;                      // points per stage
-  static constexpr int ATS = BM * BKS * 2, ZTILE = BN * BKS * 2;
-  // A_hi A_lo Z_hi Z_lo | A_P Z_hi | A_hi Z_hi Z_lo
-  static constexpr int NA = MODE == 0 ? 2 : 1, NZ = MODE == 1 ? 1 : 2;
-  static constexpr int STAGE = NA * ATS + NZ * ZTILE;
+  // A_hi A_lo Z_hi Z_lo | A Z_hi
+  static constexpr int NT2 = MODE == 0 ? 2 : 1;            // class tiles = pair tiles
+  static constexpr int STAGE = NT2 * (ATILE + ZTILE);
   static constexpr int STAGES = (227 * 1024 - 2048) / STAGE < 6 ? (227 * 1024 - 2048) / STAGE : 6;
-  static constexpr int NSB = BN == 128 ? 2 : 1;            // short TMEM buffers
-  static constexpr uint32_t COL_LONG = NSB * BN;
-  static constexpr int64_t SUBK = MODE == 0 ? 8 : MODE == 1 ? 32 : 16;
+  static constexpr int64_t SUBK = MODE == 0 ? 8 : 32;
   static constexpr int SMEM = STAGES * STAGE + 1024 + 256;
 };
 }  // namespace b_cfg
@@ -1521,11 +1498,8 @@ __global__ void __launch_bounds__(256, 1)
   using C = Cfg<MODE>;
   constexpr int STAGES = C::STAGES;
   constexpr int64_t SUBK = C::SUBK;
-  constexpr int BN = C::BN, ZTILE = C::ZTILE, NSB = C::NSB, KH = C::KH, BKS = C::BKS;
-  constexpr int ATS = C::ATS;
-  constexpr uint32_t COL_LONG = C::COL_LONG;
   // stage layout: class tile(s), then pair tile(s)
-  constexpr int OZ = C::NA * ATS;
+  constexpr int OZ = C::NT2 * ATILE;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   BsCtl* ctl = (BsCtl*)(sm + STAGES * C::STAGE);
@@ -1596,7 +1570,7 @@ __global__ void __launch_bounds__(256, 1)
       int mt, nt, sp;
       int64_t kb0, kb1;
       unit_range(u, mt, nt, sp, kb0, kb1);
-      for (int64_t kh = kb0 * KH; kh < kb1 * KH; ++kh) {
+      for (int64_t kb = kb0; kb < kb1; ++kb) {
         if (!mbar_wait(&ctl->empty[stage], phase ^ 1, abort_w)) {
           give_up(31);
           ok = false;
@@ -1604,14 +1578,12 @@ __global__ void __launch_bounds__(256, 1)
         }
         unsigned char* st = sm + stage * C::STAGE;
         mbar_expect_tx(&ctl->full[stage], C::STAGE);
-        const int64_t kb = kh / KH;
-        const int x = (int)(kh - kb * KH) * BKS;   // points of the K-step this stage carries
         const int64_t kr = real_kb(mt, kb);
         const int ya = (int)(kr * n_mt + mt) * BM, yz = (int)(kr * n_nt + nt) * BN;
-        tma_load_2d(st, &mapA0, &ctl->full[stage], x, ya);
-        if (MODE == 0) tma_load_2d(st + ATS, &mapA1, &ctl->full[stage], x, ya);
-        tma_load_2d(st + OZ, &mapZ0, &ctl->full[stage], x, yz);
-        if (MODE != 1) tma_load_2d(st + OZ + ZTILE, &mapZ1, &ctl->full[stage], x, yz);
+        tma_load_2d(st, &mapA0, &ctl->full[stage], 0, ya);
+        if (MODE == 0) tma_load_2d(st + ATILE, &mapA1, &ctl->full[stage], 0, ya);
+        tma_load_2d(st + OZ, &mapZ0, &ctl->full[stage], 0, yz);
+        if (MODE == 0) tma_load_2d(st + OZ + ZTILE, &mapZ1, &ctl->full[stage], 0, yz);
         if (++stage == STAGES) {
           stage = 0;
           phase ^= 1;
@@ -1631,7 +1603,7 @@ __global__ void __launch_bounds__(256, 1)
     constexpr uint32_t idesc = idesc_bf16_f32(BM, BN);
     int stage = 0;
     uint32_t phase = 0;
-    uint32_t gsub = 0;   // accumulations issued by this CTA (short buffer gsub % NSB)
+    uint32_t gsub = 0;   // accumulations issued by this CTA
     bool ok = true;
     for (int u = blockIdx.x; u < nunits && ok && !*abort_w; u += gridDim.x) {
       int mt, nt, sp;
@@ -1639,17 +1611,15 @@ __global__ void __launch_bounds__(256, 1)
       unit_range(u, mt, nt, sp, kb0, kb1);
       for (int64_t c0 = kb0; c0 < kb1 && ok; c0 += SUBK, ++gsub) {
         const int64_t c1 = c0 + SUBK < kb1 ? c0 + SUBK : kb1;
-        const uint32_t b = gsub % NSB, par = (gsub / NSB) & 1;
+        const uint32_t b = 0, par = gsub & 1;
         if (!mbar_wait(&ctl->tempty[b], par ^ 1, abort_w)) {
           give_up(32);
           ok = false;
           break;
         }
         tc_fence_after();
-        const uint32_t tS = tmem + b * BN;
-        // 64-byte rows (half K-steps) or 128-byte rows (whole K-steps)
-        auto sdesc = [](uint32_t addr) { return KH == 2 ? sdesc_sw64(addr) : sdesc_sw128(addr); };
-        for (int64_t kh = c0 * KH; kh < c1 * KH; ++kh) {
+        const uint32_t tS = tmem;
+        for (int64_t kb = c0; kb < c1; ++kb) {
           if (!mbar_wait(&ctl->full[stage], phase, abort_w)) {
             give_up(33);
             ok = false;
@@ -1658,12 +1628,14 @@ __global__ void __launch_bounds__(256, 1)
           tc_fence_after();
           const uint32_t a0 = smem_u32(sm + stage * C::STAGE);
 #pragma unroll
-          for (int k = 0; k < BKS / 16; ++k) {
-            const uint32_t acc = (kh != c0 * KH) || k != 0;
-            const uint64_t ah = sdesc(a0 + k * 32), zh = sdesc(a0 + OZ + k * 32);
+          for (int k = 0; k < BK / 16; ++k) {
+            const uint32_t acc = (kb != c0) || k != 0;
+            const uint64_t ah = sdesc_sw128(a0 + k * 32), zh = sdesc_sw128(a0 + OZ + k * 32);
             umma_bf16(tS, ah, zh, idesc, acc);
-            if (MODE == 0) umma_bf16(tS, sdesc(a0 + ATS + k * 32), zh, idesc, 1u);
-            if (MODE != 1) umma_bf16(tS, ah, sdesc(a0 + OZ + ZTILE + k * 32), idesc, 1u);
+            if (MODE == 0) {
+              umma_bf16(tS, sdesc_sw128(a0 + ATILE + k * 32), zh, idesc, 1u);
+              umma_bf16(tS, ah, sdesc_sw128(a0 + OZ + ZTILE + k * 32), idesc, 1u);
+            }
           }
           umma_commit(&ctl->empty[stage]);
           if (++stage == STAGES) {
@@ -1705,14 +1677,14 @@ __global__ void __launch_bounds__(256, 1)
       }
       for (int64_t c0 = kb0; c0 < kb1; c0 += SUBK, ++gsub) {
         const bool first = c0 == kb0, last = c0 + SUBK >= kb1;
-        const uint32_t b = gsub % NSB, par = (gsub / NSB) & 1;
+        const uint32_t b = 0, par = gsub & 1;
         if (!mbar_wait(&ctl->tfull[b], par, abort_w)) {
           give_up(34);
           ok = false;
           break;
         }
         tc_fence_after();
-        const uint32_t tS = tmem + lanes + b * BN, tL = tmem + lanes + COL_LONG;
+        const uint32_t tS = tmem + lanes, tL = tmem + lanes + COL_LONG;
         float* out = part + ((int64_t)sp * c + k) * d * d;
         for (int cc = 0; cc < BN; cc += 32) {
           float v[32];
@@ -2544,8 +2516,6 @@ static int32_t tc_bsum_launch_attrs() {
                                         b_cfg::Cfg<0>::SMEM));
     FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tc_bsum<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         b_cfg::Cfg<1>::SMEM));
-    FIRAL_CUDA_TRY(cudaFuncSetAttribute(k_tc_bsum<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        b_cfg::Cfg<2>::SMEM));
     done = true;
   }
   return FIRAL_OK;
@@ -2562,8 +2532,8 @@ static bool fast_rounding(const firal_problem* P) {
 
 // The labelled rows' diagonal-part block sums S_lab[k] = sum_{i < m} h_ik x_i x_i^T (their
 // weight is 1 in every Sigma_z): three products over their K-steps only, once per problem.
-// The fast mode's two-product sums leave these rows out: a few rows of weight 1 carry as much
-// of S as the whole pool, and their weights' bf16 roundings would not average out.
+// The fast mode's one-product sums leave these rows out: a few rows of weight 1 carry as much
+// of S as the whole pool, and their bf16 roundings would not average out.
 static int32_t tc_labelled_blocks(firal_problem* P) {
   using namespace b_cfg;
   cudaStream_t st = P->H->stream;
@@ -2571,7 +2541,6 @@ static int32_t tc_labelled_blocks(firal_problem* P) {
   const int cp = P->cp, c = P->c, d = P->d;
   const int npairs = d * (d + 1) / 2;
   const int64_t npp = (npairs + NPP_ALIGN - 1) / NPP_ALIGN * NPP_ALIGN;
-  constexpr int BN = Cfg<0>::BN;
   const int n_mt = (cp + BM - 1) / BM, n_nt = (int)(npp / BN);
   const int cpb = n_mt * BM;
   const int64_t asz = (int64_t)cpb * Np, kb_total = Np / BK, kbm = (m + BK - 1) / BK;
@@ -2622,8 +2591,7 @@ int32_t tc_syrk_blocks(firal_problem* P, const void* wv, double lamS, void* outS
   const int npairs = d * (d + 1) / 2;
   const int64_t npp = (npairs + NPP_ALIGN - 1) / NPP_ALIGN * NPP_ALIGN;
   const int n_mt = (cp + BM - 1) / BM;
-  // pair tiles of each form (the split count follows the 256-pair tiles)
-  const int n_nt = (int)(npp / Cfg<1>::BN), n_nt2 = (int)(npp / Cfg<2>::BN);
+  const int n_nt = (int)(npp / BN);
   const int64_t kb_total = Np / BK;
   const int64_t kL = P->pt.Q ? P->kr_bsum_Lmax : kb_total;   // longest class-tile K list
   const int tiles = n_mt * n_nt;
@@ -2660,11 +2628,12 @@ int32_t tc_syrk_blocks(firal_problem* P, const void* wv, double lamS, void* outS
   const int units = tiles * splits;
   {
     ProfScope ps(st, PF_SYRK);
-    // S as two products (A_hi against the exact pairs Z_hi + Z_lo) in the fast mode, for the
-    // Relax operators' weights: the pool rows' bf16 weight roundings (2^-9) average over each
-    // class's points like those of the fast CG direction.  The labelled rows (weight 1 in
-    // Sigma_z, 0 in H_p) enter Sigma_z's S through S_lab (three products, once per problem)
-    // unless the apply already runs them on CUDA cores (lab_rows).
+    // S as one product (A_hi against the pairs' bf16 part Z_hi) in the fast mode, for the
+    // Relax operators' weights: the pool rows' bf16 roundings of w h and of x_ie x_ie' (2^-9
+    // each) average over each class's points like those of the fast CG direction.  The
+    // labelled rows (weight 1 in Sigma_z, 0 in H_p) enter Sigma_z's S through S_lab (three
+    // products, once per problem) unless the apply already runs them on CUDA cores
+    // (lab_rows).
     const bool sig = w == P->w_sig.as<float>();
     const bool s1 = fast_rounding(P) && !P->pt.Q && (sig || w == P->w_p.as<float>());
     const bool lab_sep = s1 && outS && sig && P->m > 0 && lab_rows(P) == 0;
@@ -2682,20 +2651,15 @@ int32_t tc_syrk_blocks(firal_problem* P, const void* wv, double lamS, void* outS
     FIRAL_TRY(make_map(&mA0, Ahi, arows, BK, BM, BK, true));
     FIRAL_TRY(make_map(&mA1, Alo, arows, BK, BM, BK, true));
     FIRAL_TRY(make_map(&mA2, AP, arows, BK, BM, BK, true));
-    FIRAL_TRY(make_map(&mZ0, P->Zp.p, zrows, BK, Cfg<1>::BN, BK, true));
-    FIRAL_TRY(make_map(&mZ1, P->Zp.as<bf16>() + npp * Np, zrows, BK, Cfg<1>::BN, BK, true));
+    FIRAL_TRY(make_map(&mZ0, P->Zp.p, zrows, BK, BN, BK, true));
+    FIRAL_TRY(make_map(&mZ1, P->Zp.as<bf16>() + npp * Np, zrows, BK, BN, BK, true));
     const int grid = std::min(units, sms);
     if (outS && s1) {
-      // half K-steps: 32-point boxes of 64-byte rows
-      constexpr int BKS = Cfg<2>::BKS;
-      CUtensorMap mA20, mZ20, mZ21;
-      FIRAL_TRY(make_map_sw64(&mA20, Ahi, arows, BK, BM, BKS));
-      FIRAL_TRY(make_map_sw64(&mZ20, P->Zp.p, zrows, BK, Cfg<2>::BN, BKS));
-      FIRAL_TRY(make_map_sw64(&mZ21, P->Zp.as<bf16>() + npp * Np, zrows, BK, Cfg<2>::BN, BKS));
-      const int units2 = n_mt * n_nt2 * splits;
-      k_tc_bsum<2><<<std::min(units2, sms), 256, Cfg<2>::SMEM, st>>>(
-          mA20, mA20, mZ20, mZ21, pS, c, d, npairs, n_mt, n_nt2, splits, kbps, kb_total,
-          tc_error_word(P), P->kr_bsum.as<int4>(), P->kbL);
+      // one product: A_hi against the pair operand's bf16 part
+      k_tc_bsum<1><<<grid, 256, Cfg<1>::SMEM, st>>>(mA0, mA0, mZ0, mZ0, pS, c, d, npairs, n_mt,
+                                                    n_nt, splits, kbps, kb_total,
+                                                    tc_error_word(P), P->kr_bsum.as<int4>(),
+                                                    P->kbL);
       FIRAL_CUDA_TRY(cudaGetLastError());
     } else if (outS) {
       k_tc_bsum<0><<<grid, 256, Cfg<0>::SMEM, st>>>(mA0, mA1, mZ0, mZ1, pS, c, d, npairs, n_mt,

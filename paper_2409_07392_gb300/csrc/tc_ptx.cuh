@@ -202,18 +202,6 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
   return d;
 }
 
-// The same for K-major rows of 64 bytes (32 bf16) in the 64-byte swizzle layout: 8-row groups
-// 512 B apart (stride byte offset); base 512-byte aligned.
-__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);          // start address, bits 0-13
-  d |= (uint64_t)(16u >> 4) << 16;                   // leading byte offset (unused here)
-  d |= (uint64_t)(512u >> 4) << 32;                  // stride byte offset: 8 rows x 64 B
-  d |= (uint64_t)1 << 46;                            // descriptor version
-  d |= (uint64_t)4 << 61;                            // 64-byte swizzle
-  return d;
-}
-
 // Shared-memory matrix descriptor: MN-major operand in the 128-byte swizzle layout: for each K
 // index a row of 64 MN-consecutive bf16 (128 B), 8-row K groups 1024 B apart (stride
 // dimension), 64-element MN atoms lbo bytes apart (leading dimension); base 1024-byte aligned.
