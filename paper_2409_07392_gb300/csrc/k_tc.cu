@@ -1562,7 +1562,6 @@ __global__ void __launch_bounds__(256, 1)
       tma_prefetch(&mapA1);
       tma_prefetch(&mapZ1);
     }
-    if (MODE == 2) tma_prefetch(&mapZ1);
     int stage = 0;
     uint32_t phase = 0;
     bool ok = true;
