@@ -114,5 +114,5 @@ def test_bench_row_sharded_two_ranks(tmp_path):
     assert len(lines) == 1
     line = json.loads(lines[0])
     assert line["n_gpus"] == 2 and line["scaling"] == "strong" and line["value"] > 0
-    assert line["config"]["parallelism"].startswith("rows2")
+    assert line["setup"]["parallelism"].startswith("rows2")
     assert line["e2e"]["value"] > 0 and line["gpu_launches"] > 0
