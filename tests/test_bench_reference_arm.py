@@ -22,6 +22,9 @@ def test_reference_arm_json_line():
     assert line["steps"] == 1 and line["warmup"] == 0 and line["n_gpus"] == 1
     assert line["dtype"] == "f64" and line["data"] == "synthetic"
     assert line["config"]["workload"].startswith("fp64_small")
+    # the same config object as our arm prints: the workload and how it meets L2
+    assert set(line["config"]) == {"workload", "l2"}
+    assert "extrapolated" in line
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1
     assert "n=" in cb["sample"]
